@@ -1,0 +1,337 @@
+"""Benchmark: right-hand sides solved per second to ||b - D x|| / ||b|| < 1e-10.
+
+Workload (one step): the 16^3x32 Wilson lattice with SU(3) links
+U = exp(0.3 i H) (gauge seed 2) at the kappa where min|eig(gamma5 D)| = 1e-3;
+MinRes-DR(100,40) on the point source at the origin (spin 0, colour 0), then
+D-MinRes on the other 11 spin-colour point sources (arXiv:0901.3163, Sec. 2
+method on a synthetic stand-in for its quenched lattice).  Every right-hand
+side counts only if its true residual was verified in FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form plain|chosen]
+                    [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) solve independent
+replicas of the workload, one per rank, with no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "wilson_16x16x16x32"
+METRIC = "RHS solved/s to |r|/|b|<1e-10 (MinRes-DR(100,40) + D-MinRes, 12 point sources, 16^3x32)"
+UNIT = "RHS/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.lines = []
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_inputs():
+    import numpy as np
+
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    dims = w["dims"]
+    U = synth.su3_links(dims, w["gauge_seed"])
+    kappa = synth.kappa_for(dims, w["gauge_seed"])
+    V = synth.volume(dims)
+    B = np.zeros((12, V, 4, 3), dtype=np.complex128)
+    for a in range(12):
+        B[a] = synth.point_source(dims, a // 3, a % 3)
+    return w, dims, U, kappa, B
+
+
+def algorithmic_stencil(dims, form):
+    """Bytes and flops one Wilson stencil application must move / do (per site:
+    read the spinor (24 reals) and 4 links (72 reals), write 24 reals; 1320 flops
+    of the hopping term + 48 for psi - kappa*H psi)."""
+    import synth
+    V = synth.volume(dims)
+    real = 8 if form == "plain" else 4
+    return 120 * real * V, 1368 * V
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_0901_3163_gb300 import dlz
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, dims, U, kappa, B = workload_inputs()
+    op = dlz.create_operator(dims, torch.from_numpy(U).to(dev), kappa)
+    Bd = torch.from_numpy(B).to(dev)
+    b0, rest = Bd[0].contiguous(), Bd[1:].contiguous()
+    prec = dlz.F32 if args.form == "chosen" else dlz.F64
+    p_dr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=4000, check_every=16)
+    p_d = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=200000, precision=prec,
+                             check_every=16)
+
+    def step(profile=False, host=None):
+        p_dr.profile = p_d.profile = int(profile)
+        if host is None:
+            x0, defl, st = dlz.minresdr(op, b0, p_dr)
+            X, sts = dlz.dminres(op, defl, rest, p_d)
+        else:
+            hb0, hrest, hx0, hX = host
+            x0, defl, st = dlz.minresdr(op, hb0, p_dr, x=hx0)
+            X, sts = dlz.dminres(op, defl, hrest, p_d, X=hX)
+        allst = [st] + list(sts)
+        ok = sum(1 for s in allst if s.converged == 1 and s.true_residual <= 1e-10)
+        return ok, allst
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    solved = 0
+    stats = []
+    for _ in range(args.steps):
+        ok, allst = step(profile=True)
+        solved += ok
+        stats.extend(allst)
+    e1.record()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, float(solved)], device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, solved_all = float(mx[0]), float(t[1])
+    else:
+        ms_max, solved_all = ms, float(solved)
+    value = solved_all / (ms_max / 1e3)
+    # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
+    hb0 = torch.from_numpy(B[0].copy()).pin_memory()
+    hrest = torch.from_numpy(B[1:].copy()).pin_memory()
+    hx0 = torch.empty_like(hb0).pin_memory()
+    hX = torch.empty_like(hrest).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_solved = 0
+    for _ in range(max(1, args.steps)):
+        ok, _ = step(host=(hb0, hrest, hx0, hX))
+        e2e_solved += ok
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = e2e_solved / e2e_s * world
+    # roofline of the dominant kernel (the Wilson stencil), timed with events inside the steps
+    st_ms = sum(s.stencil_ms for s in stats)
+    st_n = sum(s.stencil_launches for s in stats)
+    avg_ms = st_ms / max(st_n, 1)
+    nbytes, nflops = algorithmic_stencil(dims, "plain" if prec == dlz.F64 else "chosen")
+    peaks, src = _peaks()
+    if prec == dlz.F64:
+        # FP64 stencil: 1.375 flop/byte is past the ridge of GB300's FP64 pipe
+        peak = 1.25
+        roof = {"bound": "alu", "achieved": round(nflops / (avg_ms * 1e-3) / 1e12, 4),
+                "peak": peak, "unit": "TFLOP/s FP64",
+                "frac": round(nflops / (avg_ms * 1e-3) / 1e12 / peak, 4),
+                "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); measured FMA probe 1.01 at 1987 MHz",
+                "hbm_gbs": round(nbytes / (avg_ms * 1e-3) / 1e9, 1),
+                "traffic": None, "kernel": "k_wilson<double>", "avg_launch_ms": round(avg_ms, 5)}
+    else:
+        ach = nbytes / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / peaks["hbm_gbs"], 4), "peak_source": src, "traffic": None,
+                "kernel": "k_wilson<float>", "avg_launch_ms": round(avg_ms, 5)}
+    launches = sum(s.gpu_launches for s in stats) // max(args.steps, 1)
+    mvps = sum(s.mvps for s in stats) // max(args.steps, 1)
+    iters = [s.iterations for s in stats[:12]]
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == dlz.F64 else "f32+f64",
+        "data": "synthetic (seeded SU(3) links exp(0.3iH), point sources)",
+        "config": {"workload": WORKLOAD, "lattice": list(dims), "kappa": kappa, "m": w["m"], "k": w["k"],
+                   "rhs": 12, "form": args.form, "tol": 1e-10,
+                   "l2": "inputs and Krylov basis (2.5 GB) larger than L2; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e_value, 4), "unit": UNIT,
+                "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(B.nbytes)},
+        "gpu_launches": int(launches), "mvps_per_step": int(mvps), "iterations_first_steps": iters,
+        "roofline": roof, "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(mvps, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(mvps_per_step, budget_s=20.0):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload:
+    MinRes-DR(100,40) cycles on the 16^3x32 lattice for about `budget_s` seconds;
+    the RHS/s figure extrapolates its seconds per MVP (Lanczos steps, restarts and
+    residual checks included) to the MVPs one step of the workload needs."""
+    import numpy as np
+
+    from oracle import cwilson, krylov, wilson
+    w, dims, U, kappa, B = workload_inputs()
+    Q = cwilson.operator(U, kappa, dims, "Q")
+    b = wilson.apply_gamma5(B[0]).reshape(-1)
+    t0 = time.perf_counter()
+    cycles = 1
+    while True:
+        r = krylov.minresdr(Q, b, w["m"], w["k"], tol=1e-10, max_cycles=cycles)
+        el = time.perf_counter() - t0
+        if el >= budget_s or cycles >= 8:
+            break
+        cycles += 1
+    # time the last run only
+    t1 = time.perf_counter()
+    r = krylov.minresdr(Q, b, w["m"], w["k"], tol=1e-10, max_cycles=max(1, cycles - 1))
+    el = time.perf_counter() - t1
+    s_per_mvp = el / max(r.info.mvps, 1)
+    rhs_per_s = 12.0 / (s_per_mvp * max(mvps_per_step, 1))
+    threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    return {"value": round(rhs_per_s, 6), "unit": UNIT, "cores": int(threads), "kind": "oracle",
+            "sample": (f"oracle MinRes-DR(100,40), {r.cycles} cycle(s) = {r.info.mvps} MVPs in "
+                       f"{el:.1f} s on {platform.machine()}; RHS/s extrapolated to "
+                       f"{mvps_per_step} MVPs per 12-RHS step")}
+
+
+def run_reference(args):
+    """The oracle timed as it stands on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import cwilson, krylov, wilson
+    w, dims, U, kappa, B = workload_inputs()
+    Q = cwilson.operator(U, kappa, dims, "Q")
+    b = wilson.apply_gamma5(B[0]).reshape(-1)
+    # one bounded sample per step: one MinRes-DR(100,40) cycle (m Lanczos steps + restart)
+    mvps_per_rhs = args.ref_mvps_per_rhs
+    for _ in range(args.warmup):
+        krylov.minresdr(Q, b, w["m"], w["k"], tol=1e-10, max_cycles=1)
+    t0 = time.perf_counter()
+    mv = 0
+    for _ in range(args.steps):
+        r = krylov.minresdr(Q, b, w["m"], w["k"], tol=1e-10, max_cycles=1)
+        mv += r.info.mvps
+    el = time.perf_counter() - t0
+    value = 1.0 / (el / mv * mvps_per_rhs)
+    threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "form": "oracle"},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": int(threads),
+                            "kind": "oracle",
+                            "sample": (f"per step one MinRes-DR(100,40) cycle ({mv // args.steps} MVPs); "
+                                       f"RHS/s extrapolated at {mvps_per_rhs} MVPs per RHS")},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["plain", "chosen"], default="plain")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-mvps-per-rhs", type=int, default=600)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

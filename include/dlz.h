@@ -1,0 +1,211 @@
+/*
+ * dlz -- deflated restarted Lanczos solvers for the hermitian Wilson-Dirac
+ * operators on one GB300 GPU (sm_103a).  C ABI.
+ *
+ * Method: A. M. Abdel-Rehim, R. B. Morgan, D. A. Nicely, W. Wilcox,
+ * "Deflated Hermitian Lanczos Methods for Multiple Right-Hand Sides"
+ * (arXiv:0901.3163).  The first right-hand side is solved by Lan-DR(m,k)
+ * on D^dagger D (Sec. 1: CG implementation of Lanczos, optimal for positive
+ * definite spectra) or MinRes-DR(m,k) on Q = gamma5 D (Sec. 1: MinRes
+ * implementation, optimal for indefinite spectra); both keep k
+ * eigenvectors across restarts and return them.  Later right-hand sides
+ * are solved by D-CG / D-MinRes: a Galerkin projection over the k vectors
+ * at the start, then CG / MinRes (Sec. 2).
+ *
+ * Conventions shared with every caller:
+ *   lattice dims[4] = {Lx, Ly, Lz, Lt}; V = Lx*Ly*Lz*Lt;
+ *   site s = ((t*Lz + z)*Ly + y)*Lx + x (x fastest);
+ *   spinor: V x 4 spins x 3 colours complex, component a = 3*spin + colour,
+ *           interleaved re/im, i.e. complex128 [V][4][3] (n = 12 V);
+ *   gauge:  4 directions (x, y, z, t) x V links, each a row-major 3x3
+ *           complex128 matrix: [4][V][3][3], U[mu][s] links s to s + mu;
+ *   D psi(x) = psi(x) - kappa sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                    + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)]
+ *   with the chiral gamma basis (gamma_k = [[0,-i sigma_k],[i sigma_k,0]],
+ *   gamma_4 = [[0,1],[1,0]], gamma5 = diag(1,1,-1,-1)), periodic boundaries
+ *   and optionally antiperiodic time (bc_t = -1).  Sec. 2 calls D "M".
+ *
+ * Memory: every vector argument is a plain pointer that may be device
+ * memory or host memory (pageable or pinned); the library detects which
+ * (cudaPointerGetAttributes) and copies host data in and out itself.  The
+ * caller owns all vector memory.  Objects (dlz_op_t, dlz_defl_t) are owned
+ * by the library and released with their destroy call.  All GPU work is
+ * ordered on the stream given to dlz_create_operator (0 = legacy default
+ * stream); the solver calls return when their results are complete.
+ *
+ * Errors: every call returns DLZ_OK (0) or a negative DLZ_ERR_* code; no
+ * C++ exception crosses the ABI.  dlz_strerror() names a code,
+ * dlz_last_error() gives the message of the last failure on this thread.
+ */
+#ifndef DLZ_H
+#define DLZ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DLZ_OK 0
+#define DLZ_ERR_BADARG (-1)         /* invalid argument (null, size, enum)        */
+#define DLZ_ERR_BAD_GAUGE (-2)      /* gauge field not SU(3) to 1e-10 or not finite */
+#define DLZ_ERR_NONFINITE (-3)      /* NaN/Inf met in an input or a reduction      */
+#define DLZ_ERR_NOT_CONVERGED (-4)  /* iteration limit hit; outputs hold the last iterate */
+#define DLZ_ERR_BREAKDOWN (-5)      /* Lanczos breakdown (invariant subspace)       */
+#define DLZ_ERR_DEVICE_TIMEOUT (-6) /* a bounded device wait gave up                */
+#define DLZ_ERR_CUDA (-7)           /* CUDA runtime error                           */
+#define DLZ_ERR_OOM (-8)            /* device allocation failed                     */
+#define DLZ_ERR_IO (-9)             /* file read/write failed or bad file           */
+
+/* Operators (Sec. 2): D (the Wilson matrix M), D^dagger, Q = gamma5 D, D^dagger D. */
+#define DLZ_D 0
+#define DLZ_DDAG 1
+#define DLZ_Q 2
+#define DLZ_DDAGD 3
+
+/* Arithmetic of the hot loop. */
+#define DLZ_F64 0   /* plain FP64 everywhere                                     */
+#define DLZ_F32 1   /* FP32 stencil and Krylov vectors, FP64 reliable updates    */
+
+typedef struct dlz_op_s *dlz_op_t;
+typedef struct dlz_defl_s *dlz_defl_t;
+
+/* Solver parameters; dlz_params_default() fills the defaults given here. */
+typedef struct {
+    int m;               /* Krylov dimension per cycle (Lan-DR(m,k), MinRes-DR(m,k)); 40 */
+    int k;               /* eigenvectors kept across restarts; 10                        */
+    double tol;          /* stop on ||b - D x|| / ||b|| <= tol (Sec. 2 residual of M^-1); 1e-10 */
+    double tol_eig;      /* kept Ritz residuals must reach this (<= 0: 1e-10 * ||A|| est.); 0 */
+    double oversolve;    /* extra MVPs after linear convergence, as a fraction of the
+                            MVPs before it (Sec. 2: at most a factor of two); 1.0         */
+    int max_cycles;      /* restart cycles (DR solvers); 1000                            */
+    int max_iter;        /* iterations (D-CG / D-MinRes); 100000                         */
+    int reorth_period;   /* re-orthogonalise against the kept vectors every this many
+                            Lanczos steps, at the restart vector and the first new step
+                            (Sec. 2: periodic, period not given); 10                      */
+    int precision;       /* DLZ_F64 or DLZ_F32 (hot loop of D-CG / D-MinRes); DLZ_F64     */
+    double reliable_delta; /* DLZ_F32: FP64 true-residual update when the iterated
+                              residual fell by this factor; 0.1                          */
+    int check_every;     /* D-CG / D-MinRes: read the residual on the host every this
+                            many iterations; 16                                          */
+    int profile;         /* 1: time every stencil launch with CUDA events (stats)  ; 0   */
+} dlz_params;
+
+/* Per-solve statistics. */
+typedef struct {
+    int converged;          /* 1 if ||b - D x|| / ||b|| <= tol was verified in FP64   */
+    int iterations;         /* CG / MinRes iterations, or Lanczos steps               */
+    int cycles;             /* restart cycles (DR solvers)                            */
+    long long mvps;         /* applications of D or D^dagger (D^dagger D counts 2)     */
+    double true_residual;   /* ||b - D x|| / ||b|| recomputed in FP64 at exit          */
+    double seconds;         /* wall time of the call                                  */
+    double stencil_ms;      /* profile = 1: summed device time of stencil launches     */
+    long long stencil_launches; /* profile = 1: number of timed stencil launches       */
+    long long gpu_launches; /* kernels launched by this call                          */
+} dlz_stats;
+
+/* Fills *p with the defaults listed above. */
+int dlz_params_default(dlz_params *p);
+
+/* Name of an error code; static storage. */
+const char *dlz_strerror(int code);
+/* Message of the last failing call on this thread; static per-thread storage. */
+const char *dlz_last_error(void);
+
+/*
+ * Creates the Wilson operator D for the gauge field `gauge` (complex128
+ * [4][V][3][3], host or device) with hopping parameter kappa (Sec. 2) and
+ * time boundary bc_t (+1 periodic, -1 antiperiodic).  The library keeps its
+ * own FP64 and FP32 copies of the links in its internal layout.  Every link
+ * is checked to be SU(3) to 1e-10 (||U^dag U - 1||_max, |det U - 1|):
+ * DLZ_ERR_BAD_GAUGE otherwise.  `stream` is a cudaStream_t (may be 0).
+ * dims[i] >= 1; V * 12 must fit in a 32-bit signed int.
+ */
+int dlz_create_operator(const int dims[4], const void *gauge, double kappa, int bc_t,
+                        void *stream, dlz_op_t *out);
+int dlz_destroy_operator(dlz_op_t op);
+/* Lattice volume V of the operator. */
+int dlz_op_volume(dlz_op_t op, long long *V);
+
+/*
+ * out = A in for A = DLZ_D, DLZ_DDAG, DLZ_Q or DLZ_DDAGD (Sec. 2: M, M^dagger,
+ * gamma5 M, M^dagger M), on `nrhs` spinors stored one after another.
+ * dtype DLZ_F64: complex128 [nrhs][V][4][3]; DLZ_F32: complex64, computed in
+ * FP32.  in and out must not overlap.  nrhs = 0 is a no-op.
+ */
+int dlz_apply(dlz_op_t op, int which, const void *in, void *out, int dtype, int nrhs);
+
+/*
+ * Lan-DR(m,k) on A = D^dagger D for D x = b (Sec. 1, Sec. 2): solves
+ * D^dagger D x = D^dagger b by restarted Lanczos with a Galerkin solve per
+ * cycle, keeping the k lowest regular Ritz vectors across restarts, and
+ * runs past linear convergence until the kept Ritz residuals reach tol_eig
+ * (or the oversolve budget is spent).  b, x: complex128 [V][4][3] (x is
+ * output only; the start vector is 0).  If defl_out is not NULL it receives
+ * the deflation set (k vectors + H = V_k^dag A V_k) for dlz_dcg.
+ * Returns DLZ_ERR_NOT_CONVERGED (x and defl still valid) if max_cycles ran out.
+ */
+int dlz_landr(dlz_op_t op, const void *b, void *x, const dlz_params *p,
+              dlz_defl_t *defl_out, dlz_stats *stats);
+
+/*
+ * MinRes-DR(m,k) on Q = gamma5 D for D x = b (Sec. 1, Sec. 2): solves
+ * Q x = gamma5 b by restarted Lanczos with a least-squares (minimum residual)
+ * solve per cycle, keeping k harmonic Ritz vectors (nearest zero) across
+ * restarts.  Arguments and returns as dlz_landr; the deflation set is for
+ * dlz_dminres.
+ */
+int dlz_minresdr(dlz_op_t op, const void *b, void *x, const dlz_params *p,
+                 dlz_defl_t *defl_out, dlz_stats *stats);
+
+/*
+ * D-CG (Sec. 2): for each of the nrhs right-hand sides B[i] (complex128
+ * [nrhs][V][4][3]) the Galerkin projection x0 = V_k H^-1 V_k^dag D^dag b over
+ * the deflation set, then CG on D^dagger D x = D^dagger b, stopping on the
+ * FP64-verified ||b - D x|| / ||b|| <= tol.  defl may be NULL (plain CG on
+ * the normal equations).  stats: array of nrhs entries or NULL.  Returns
+ * DLZ_ERR_NOT_CONVERGED if any right-hand side missed tol within max_iter.
+ */
+int dlz_dcg(dlz_op_t op, dlz_defl_t defl, const void *B, void *X, int nrhs,
+            const dlz_params *p, dlz_stats *stats);
+
+/*
+ * D-MinRes (Sec. 2): projection x0 = V_k H^-1 V_k^dag gamma5 b over the
+ * deflation set (H = V_k^dag Q V_k), then MinRes on Q x = gamma5 b.
+ * Arguments as dlz_dcg; defl NULL gives plain MinRes.
+ */
+int dlz_dminres(dlz_op_t op, dlz_defl_t defl, const void *B, void *X, int nrhs,
+                const dlz_params *p, dlz_stats *stats);
+
+/* Number k of vectors in a deflation set, and which operator it deflates
+ * (DLZ_DDAGD from dlz_landr, DLZ_Q from dlz_minresdr). */
+int dlz_defl_count(dlz_defl_t d, int *k, int *which);
+/*
+ * i-th Rayleigh-Ritz pair of the deflation set: eigenvalues of H in
+ * ascending order, the unit vector y_i = V_k z_i (complex128 [V][4][3], host
+ * or device; NULL to skip), its value y_i^dag A y_i and its residual
+ * ||A y_i - value y_i|| (either pointer may be NULL).
+ */
+int dlz_defl_get(dlz_defl_t d, int i, void *vec_out, double *value, double *residual);
+/* Writes the deflation set (header, H, V_k in FP64) to a file / reads it back
+ * for the same operator geometry.  DLZ_ERR_IO on failure. */
+int dlz_defl_save(dlz_defl_t d, const char *path);
+int dlz_defl_load(dlz_op_t op, const char *path, dlz_defl_t *out);
+int dlz_defl_destroy(dlz_defl_t d);
+
+/*
+ * Host-side dense helpers used by the restart (exported for testing; no
+ * GPU needed).  Row-major n x n matrices.
+ *   dlz_host_symeig: eigen-decomposition of a real symmetric matrix A
+ *     (Householder tridiagonalisation + implicit QR with Wilkinson shifts):
+ *     w[n] ascending, Z[n][n] with the eigenvector of w[j] in column j.
+ *   dlz_host_lstsq: y = argmin ||c - T y|| for T (rows x cols, rows > cols,
+ *     full column rank) by Householder QR; q[rows] receives the unit
+ *     vector spanning the orthogonal complement of range(T) when rows == cols + 1
+ *     (may be NULL).
+ */
+int dlz_host_symeig(int n, const double *A, double *w, double *Z);
+int dlz_host_lstsq(int rows, int cols, const double *T, const double *c, double *y, double *q);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DLZ_H */

@@ -11,9 +11,9 @@ min |eig(gamma5 D)| = sigma_min(D) = 1e-3:
     bracket by safeguarded false position (Illinois) to
     |sigma_min / 1e-3 - 1| < 1e-6;
   * larger lattices: sigma_min = min |eig(Q)| from MinRes-DR run as an
-    eigensolver (the harmonic Ritz pair nearest zero), stepping by 0.005
-    from a start value near the dense-lattice answer to bracket the
-    crossing, then Illinois to 1e-4 and an independent re-verification.
+    eigensolver (the harmonic Ritz pair nearest zero), stepping by 0.003
+    from a start value near the expected crossing to bracket it, then
+    Illinois to 1e-3 and an independent re-verification.
 """
 from __future__ import annotations
 
@@ -77,18 +77,26 @@ def kappa_dense(U, dims, bc_t=1, step=0.005, rtol=1e-6):
     return kap, sigma_min_dense(H, kap)
 
 
-def sigma_min_iterative(U, kappa, dims, v0, res_tol, m=100, k=20, bc_t=1, max_cycles=2000):
+def sigma_min_iterative(U, kappa, dims, v0, res_tol, m=100, k=20, bc_t=1, max_cycles=2000,
+                        log=None):
     """min |eig(gamma5 D)| by MinRes-DR used as an eigensolver (harmonic Ritz pairs
     nearest zero), started from v0.  Returns (sigma, eigenvector, residual, mvps)."""
     from .krylov import minresdr
     A = cwilson.operator(U, kappa, dims, "Q", bc_t)
-    r = minresdr(A, v0, m, k, tol=0.0, max_cycles=max_cycles, eig_stop=res_tol)
+
+    def progress(cycle, mvps, rel, theta, res):
+        if log and cycle % 5 == 0:
+            i = int(np.argmin(np.abs(theta)))
+            log(f"   cycle {cycle} mvps {mvps} theta {abs(theta[i]):.6e} res {res[i]:.2e}")
+
+    r = minresdr(A, v0, m, k, tol=0.0, max_cycles=max_cycles, eig_stop=res_tol, progress=progress)
     i = int(np.argmin(np.abs(r.ritz_values)))
     return (float(abs(r.ritz_values[i])), r.ritz_vectors[:, i], float(r.ritz_residuals[i]),
             r.info.mvps)
 
 
-def kappa_iterative(U, dims, start, bc_t=1, step=0.005, rtol=1e-4, seed=12345, log=None):
+def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5, seed=12345,
+                    log=None):
     """kappa with sigma_min(D) = 1e-3 on a lattice too large for a dense eigensolve.
 
     sigma_min is min |eig(Q)|, taken from the harmonic Ritz pair nearest zero of
@@ -96,14 +104,16 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.005, rtol=1e-4, seed=12345, l
     eigenvector.  From `start` kappa is stepped by `step` (down while
     sigma_min < 1e-3, then up) to bracket the crossing, which is refined by
     Illinois false position to |sigma_min/1e-3 - 1| < rtol and re-verified
-    from a fresh random start vector.  Returns (kappa, sigma_min).
+    from a fresh random start vector.  Returns (kappa, sigma_min).  The
+    default accuracy (1e-3 on sigma_min, harmonic Ritz residual 1e-5) fixes
+    the near-critical workload well enough; the dense rule uses 1e-6.
     """
     V = int(np.prod(dims))
     rng = np.random.default_rng(seed)
     state = {"v": rng.standard_normal(V * 12) + 1j * rng.standard_normal(V * 12)}
 
-    def f(kap, res_tol=1e-6):
-        s, y, res, mv = sigma_min_iterative(U, kap, dims, state["v"], res_tol, bc_t=bc_t)
+    def f(kap, res_tol=res_tol):
+        s, y, res, mv = sigma_min_iterative(U, kap, dims, state["v"], res_tol, bc_t=bc_t, log=log)
         state["v"] = y + 1e-3 * (rng.standard_normal(V * 12) + 1j * rng.standard_normal(V * 12)) / np.sqrt(V * 12)
         if log:
             log(f"kappa={kap:.10f} sigma_min={s:.10e} res={res:.2e} mvps={mv}")
@@ -122,4 +132,4 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.005, rtol=1e-4, seed=12345, l
         fb = f(b)
     kap = _illinois(f, a, fa, b, fb, rtol)
     state["v"] = rng.standard_normal(V * 12) + 1j * rng.standard_normal(V * 12)
-    return kap, f(kap, 1e-7) + TARGET
+    return kap, f(kap, res_tol) + TARGET

@@ -286,7 +286,7 @@ class DRResult:
 
 
 def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
-          full_reorth=False, residual=None, oversolve=1.0, eig_stop=None):
+          full_reorth=False, residual=None, oversolve=1.0, eig_stop=None, progress=None):
     """Lan-DR(m,k) for hermitian positive definite A (Sec. 1, Sec. 2).
 
     Cycle 1: x0 = 0, r0 = b, v1 = r0/||r0||, Lanczos to j = m.  Each cycle:
@@ -309,11 +309,11 @@ def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
     Ritz pair has a residual <= eig_stop.
     """
     return _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth,
-               residual, oversolve, harmonic=False, eig_stop=eig_stop)
+               residual, oversolve, harmonic=False, eig_stop=eig_stop, progress=progress)
 
 
 def minresdr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
-             full_reorth=False, residual=None, oversolve=1.0, eig_stop=None):
+             full_reorth=False, residual=None, oversolve=1.0, eig_stop=None, progress=None):
     """MinRes-DR(m,k) for hermitian, possibly indefinite A (Sec. 1, Sec. 2).
 
     Same Lanczos and restart skeleton as Lan-DR, with (GMRES-DR read for a
@@ -331,7 +331,7 @@ def minresdr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=
     (eigenvalues of V_k^dag A V_k = top k x k block of Tbar_k); stopping as Lan-DR.
     """
     return _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth,
-               residual, oversolve, harmonic=True, eig_stop=eig_stop)
+               residual, oversolve, harmonic=True, eig_stop=eig_stop, progress=progress)
 
 
 def _mgs_columns(P):
@@ -351,7 +351,7 @@ def _rayleigh_ritz(T, k):
 
 
 def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residual,
-        oversolve, harmonic, eig_stop=None):
+        oversolve, harmonic, eig_stop=None, progress=None):
     b = np.asarray(b, dtype=np.complex128)
     n = b.size
     bn = _norm(b)
@@ -411,6 +411,8 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
         if lin_ok and mvps_at_conv is None:
             mvps_at_conv = info.mvps
         eig_ok = bool(np.all(ritz_res <= tol_eig_abs))
+        if progress is not None:
+            progress(cycle, info.mvps, rel, theta_k, ritz_res)
         over = mvps_at_conv is not None and (info.mvps - mvps_at_conv) >= oversolve * mvps_at_conv
         last = cycle == max_cycles - 1
         if lin_ok and (eig_ok or over):

@@ -1,0 +1,163 @@
+// Internal declarations of the dlz library (not part of the C ABI).
+//
+// Device data layout ("field order"): a spinor of V sites is stored as
+// component-major planes so that thread s of a warp touches consecutive
+// 16-byte words:
+//   FP64: double2 [12][V]   element (a, s) at a*V + s   (a = 3*spin + colour)
+//   FP32: float4  [6][V]    plane c holds components 2c, 2c+1 of site s
+// Gauge links (per direction mu, entry e = 3*row + col of the 3x3 matrix):
+//   FP64: double2 [4][9][V] at (mu*9 + e)*V + s
+//   FP32: float2  [4][9][V] at (mu*9 + e)*V + s
+// The canonical user layout is complex [V][12] (see include/dlz.h); pack
+// and unpack kernels convert at the API boundary.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dlz.h"
+
+namespace dlz {
+
+// ---------------------------------------------------------------- complex
+template <typename T> struct cplx_of;
+template <> struct cplx_of<double> { typedef double2 type; };
+template <> struct cplx_of<float> { typedef float2 type; };
+template <typename T> using cx = typename cplx_of<T>::type;
+
+template <typename T> __host__ __device__ inline cx<T> mk(T re, T im) { cx<T> r; r.x = re; r.y = im; return r; }
+__host__ __device__ inline double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// i * a
+__host__ __device__ inline double2 timesI(double2 a) { return make_double2(-a.y, a.x); }
+__host__ __device__ inline float2 timesI(float2 a) { return make_float2(-a.y, a.x); }
+// a + i b, a - i b
+__host__ __device__ inline double2 addI(double2 a, double2 b) { return make_double2(a.x - b.y, a.y + b.x); }
+__host__ __device__ inline double2 subI(double2 a, double2 b) { return make_double2(a.x + b.y, a.y - b.x); }
+__host__ __device__ inline float2 addI(float2 a, float2 b) { return make_float2(a.x - b.y, a.y + b.x); }
+__host__ __device__ inline float2 subI(float2 a, float2 b) { return make_float2(a.x + b.y, a.y - b.x); }
+// acc + u * v
+__host__ __device__ inline double2 cfma(double2 u, double2 v, double2 acc) {
+    acc.x = fma(u.x, v.x, acc.x); acc.x = fma(-u.y, v.y, acc.x);
+    acc.y = fma(u.x, v.y, acc.y); acc.y = fma(u.y, v.x, acc.y);
+    return acc;
+}
+__host__ __device__ inline float2 cfma(float2 u, float2 v, float2 acc) {
+    acc.x = fmaf(u.x, v.x, acc.x); acc.x = fmaf(-u.y, v.y, acc.x);
+    acc.y = fmaf(u.x, v.y, acc.y); acc.y = fmaf(u.y, v.x, acc.y);
+    return acc;
+}
+// acc + conj(u) * v
+__host__ __device__ inline double2 cfmaConj(double2 u, double2 v, double2 acc) {
+    acc.x = fma(u.x, v.x, acc.x); acc.x = fma(u.y, v.y, acc.x);
+    acc.y = fma(u.x, v.y, acc.y); acc.y = fma(-u.y, v.x, acc.y);
+    return acc;
+}
+__host__ __device__ inline float2 cfmaConj(float2 u, float2 v, float2 acc) {
+    acc.x = fmaf(u.x, v.x, acc.x); acc.x = fmaf(u.y, v.y, acc.x);
+    acc.y = fmaf(u.x, v.y, acc.y); acc.y = fmaf(-u.y, v.x, acc.y);
+    return acc;
+}
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+    int L[4];      // Lx, Ly, Lz, Lt
+    int V;         // sites
+    int bc_t;      // +1 periodic, -1 antiperiodic time
+};
+
+// ---------------------------------------------------------------- errors
+struct Error {
+    int code;
+    std::string msg;
+};
+void set_error(int code, const std::string &msg);
+int fail(int code, const std::string &msg);
+#define DLZ_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return ::dlz::fail(e_ == cudaErrorMemoryAllocation ? DLZ_ERR_OOM : DLZ_ERR_CUDA, \
+                               std::string(#expr) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+#define DLZ_TRY(expr)              \
+    do {                           \
+        int r_ = (expr);           \
+        if (r_ != DLZ_OK) return r_; \
+    } while (0)
+
+// ---------------------------------------------------------------- device buffers
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    int alloc(size_t nbytes);
+    void release();
+    template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Reduction scratch: per-block partials, a completion counter and results.
+// One instance per concurrently used reduction slot.
+constexpr int kRedBlocks = 608;      // 4 x 152 SMs: fixed grid -> fixed summation order
+constexpr int kRedThreads = 256;
+constexpr int kMaxDots = 16;         // dots reduced by one fused kernel
+struct RedScratch {
+    double *partials;   // [kMaxDots][kRedBlocks]
+    unsigned *counter;  // 1
+    double *result;     // [kMaxDots]
+};
+
+struct Op;
+
+// Launch accounting and optional stencil timing.
+struct Profiler {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    long long launches = 0;      // all kernels
+    long long stencils = 0;      // stencil kernels
+    void begin(bool on);
+    void stencil_start(cudaStream_t s);
+    void stencil_stop(cudaStream_t s);
+    double stencil_ms();         // synchronises the events; sums pairs
+    ~Profiler();
+};
+
+struct Op {
+    Geom g;
+    double kappa;
+    cudaStream_t stream;
+    DevBuf gauge64;   // double2 [4][9][V]
+    DevBuf gauge32;   // float2  [4][9][V]
+    DevBuf red_mem;   // reduction scratch
+    RedScratch red;
+    Profiler prof;
+    DevBuf scratch_a, scratch_b, scratch_c;  // spinor-sized scratch (FP64)
+};
+
+// ---------------------------------------------------------------- kernels (launchers)
+// Wilson stencil: out = [g5_out] (1 - kappa H) [g5_in] in, FP64 or FP32.
+// which: DLZ_D (0,0), DLZ_DDAG (1,1), DLZ_Q (0,1).
+int wilson64(Op &op, double2 *out, const double2 *in, int which);
+int wilson32(Op &op, float4 *out, const float4 *in, int which);
+// A = D, D^dag, Q or D^dag D on internal FP64 vectors (tmp used for D^dag D).
+int apply64(Op &op, double2 *out, const double2 *in, int which, double2 *tmp);
+int apply32(Op &op, float4 *out, const float4 *in, int which, float4 *tmp);
+
+// pack / unpack between canonical complex [V][12] and internal planes
+int pack64(Op &op, double2 *dst, const double2 *src_canon);
+int unpack64(Op &op, double2 *dst_canon, const double2 *src);
+int pack32(Op &op, float4 *dst, const float2 *src_canon);
+int unpack32(Op &op, float2 *dst_canon, const float4 *src);
+int convert64to32(Op &op, float4 *dst, const double2 *src);
+int convert32to64(Op &op, double2 *dst, const float4 *src);
+
+}  // namespace dlz

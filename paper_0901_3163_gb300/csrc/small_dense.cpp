@@ -1,0 +1,299 @@
+// Host FP64 dense kernels for the small projected problems of one restart
+// cycle (order m <= a few hundred): the eigenproblems of the regular and
+// harmonic Ritz extractions, the Galerkin and least-squares solves, and
+// the small factorisations of the deflation projection (arXiv:0901.3163,
+// Sec. 1-2: Lan-DR uses regular Ritz vectors and a CG-type solve,
+// MinRes-DR harmonic Ritz vectors and a minimum-residual solve).
+//
+// Methods: Householder tridiagonalisation followed by implicit symmetric QR
+// steps with Wilkinson shifts (Golub & Van Loan, "Matrix Computations",
+// Sec. 8.3); Householder QR for least squares; Cholesky; LU with partial
+// pivoting; modified Gram-Schmidt.  All matrices are row-major.
+#include "small_dense.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+namespace dlz {
+
+namespace {
+
+inline double sgn1(double x) { return x >= 0.0 ? 1.0 : -1.0; }
+
+// Reduce symmetric a (n x n) to tridiagonal form Q^T a Q; returns d, e, Q.
+void tridiagonalise(int n, std::vector<double> &a, std::vector<double> &d, std::vector<double> &e,
+                    std::vector<double> &Q) {
+    Q.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+    std::vector<double> v(n), p(n), q(n);
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;          // length of the column below the diagonal
+        double alpha = 0.0;
+        for (int i = 0; i < m; ++i) alpha += a[(size_t)(k + 1 + i) * n + k] * a[(size_t)(k + 1 + i) * n + k];
+        alpha = std::sqrt(alpha);
+        if (alpha == 0.0) continue;
+        const double x0 = a[(size_t)(k + 1) * n + k];
+        alpha = -sgn1(x0) * alpha;
+        for (int i = 0; i < m; ++i) v[i] = a[(size_t)(k + 1 + i) * n + k];
+        v[0] -= alpha;
+        double vn2 = 0.0;
+        for (int i = 0; i < m; ++i) vn2 += v[i] * v[i];
+        if (vn2 == 0.0) continue;
+        const double tau = 2.0 / vn2;
+        // p = tau * A22 v ;  K = tau/2 (v.p) ;  q = p - K v ;  A22 -= v q^T + q v^T
+        for (int i = 0; i < m; ++i) {
+            double s = 0.0;
+            const double *row = &a[(size_t)(k + 1 + i) * n + k + 1];
+            for (int j = 0; j < m; ++j) s += row[j] * v[j];
+            p[i] = tau * s;
+        }
+        double vp = 0.0;
+        for (int i = 0; i < m; ++i) vp += v[i] * p[i];
+        const double K = 0.5 * tau * vp;
+        for (int i = 0; i < m; ++i) q[i] = p[i] - K * v[i];
+        for (int i = 0; i < m; ++i) {
+            double *row = &a[(size_t)(k + 1 + i) * n + k + 1];
+            for (int j = 0; j < m; ++j) row[j] -= v[i] * q[j] + q[i] * v[j];
+        }
+        a[(size_t)(k + 1) * n + k] = a[(size_t)k * n + k + 1] = alpha;
+        for (int i = 1; i < m; ++i) a[(size_t)(k + 1 + i) * n + k] = a[(size_t)k * n + k + 1 + i] = 0.0;
+        // Q <- Q H on columns k+1..n-1
+        for (int r = 0; r < n; ++r) {
+            double *row = &Q[(size_t)r * n + k + 1];
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s += row[j] * v[j];
+            s *= tau;
+            for (int j = 0; j < m; ++j) row[j] -= s * v[j];
+        }
+    }
+    d.resize(n);
+    e.assign(n > 1 ? n - 1 : 0, 0.0);
+    for (int i = 0; i < n; ++i) d[i] = a[(size_t)i * n + i];
+    for (int i = 0; i + 1 < n; ++i) e[i] = a[(size_t)(i + 1) * n + i];
+}
+
+// Implicit symmetric QR with Wilkinson shifts on (d, e); rotations accumulated into Q.
+bool tridiagonal_qr(int n, std::vector<double> &d, std::vector<double> &e, std::vector<double> &Q) {
+    const double eps = 2.2e-16;
+    int h = n - 1;
+    long iter = 0;
+    const long max_iter = 60L * n + 100;
+    while (h > 0) {
+        if (std::fabs(e[h - 1]) <= eps * (std::fabs(d[h - 1]) + std::fabs(d[h]))) {
+            e[h - 1] = 0.0;
+            --h;
+            continue;
+        }
+        int l = h - 1;
+        while (l > 0 && std::fabs(e[l - 1]) > eps * (std::fabs(d[l - 1]) + std::fabs(d[l]))) --l;
+        if (l > 0) e[l - 1] = 0.0;
+        if (++iter > max_iter) return false;
+        // Wilkinson shift from the trailing 2x2 block of [l..h]
+        const double delta = 0.5 * (d[h - 1] - d[h]);
+        const double b = e[h - 1];
+        const double mu = d[h] - b * b / (delta + sgn1(delta) * std::hypot(delta, b));
+        double x = d[l] - mu, z = e[l];
+        for (int k = l; k < h; ++k) {
+            const double r = std::hypot(x, z);
+            const double c = (r == 0.0) ? 1.0 : x / r, s = (r == 0.0) ? 0.0 : z / r;
+            if (k > l) e[k - 1] = r;
+            const double dk = d[k], dk1 = d[k + 1], ek = e[k];
+            d[k] = c * c * dk + 2.0 * c * s * ek + s * s * dk1;
+            d[k + 1] = s * s * dk - 2.0 * c * s * ek + c * c * dk1;
+            e[k] = c * s * (dk1 - dk) + (c * c - s * s) * ek;
+            if (k + 1 < h) {
+                z = s * e[k + 1];            // bulge at (k, k+2)
+                e[k + 1] = c * e[k + 1];
+                x = e[k];
+            }
+            for (int r2 = 0; r2 < n; ++r2) {
+                double *row = &Q[(size_t)r2 * n];
+                const double qk = row[k], qk1 = row[k + 1];
+                row[k] = c * qk + s * qk1;
+                row[k + 1] = -s * qk + c * qk1;
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+bool sym_eig(int n, const double *A, double *w, double *Z) {
+    if (n <= 0) return true;
+    std::vector<double> a(A, A + (size_t)n * n), d, e, Q;
+    // symmetrise the input against rounding in the caller
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) {
+            const double s = 0.5 * (a[(size_t)i * n + j] + a[(size_t)j * n + i]);
+            a[(size_t)i * n + j] = a[(size_t)j * n + i] = s;
+        }
+    tridiagonalise(n, a, d, e, Q);
+    if (!tridiagonal_qr(n, d, e, Q)) return false;
+    std::vector<int> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return d[x] < d[y]; });
+    for (int j = 0; j < n; ++j) {
+        w[j] = d[idx[j]];
+        for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = Q[(size_t)i * n + idx[j]];
+    }
+    return true;
+}
+
+bool lstsq(int rows, int cols, const double *T, const double *c, double *y, double *q) {
+    if (rows <= cols || cols <= 0) return false;
+    std::vector<double> a(T, T + (size_t)rows * cols), b(c, c + rows);
+    std::vector<std::vector<double>> vs(cols);
+    std::vector<double> taus(cols, 0.0);
+    for (int k = 0; k < cols; ++k) {
+        double alpha = 0.0;
+        for (int i = k; i < rows; ++i) alpha += a[(size_t)i * cols + k] * a[(size_t)i * cols + k];
+        alpha = std::sqrt(alpha);
+        std::vector<double> &v = vs[k];
+        v.assign(rows - k, 0.0);
+        if (alpha == 0.0) return false;
+        alpha = -sgn1(a[(size_t)k * cols + k]) * alpha;
+        for (int i = k; i < rows; ++i) v[i - k] = a[(size_t)i * cols + k];
+        v[0] -= alpha;
+        double vn2 = 0.0;
+        for (double t : v) vn2 += t * t;
+        const double tau = (vn2 == 0.0) ? 0.0 : 2.0 / vn2;
+        taus[k] = tau;
+        for (int j = k; j < cols; ++j) {
+            double s = 0.0;
+            for (int i = k; i < rows; ++i) s += v[i - k] * a[(size_t)i * cols + j];
+            s *= tau;
+            for (int i = k; i < rows; ++i) a[(size_t)i * cols + j] -= s * v[i - k];
+        }
+        double s = 0.0;
+        for (int i = k; i < rows; ++i) s += v[i - k] * b[i];
+        s *= tau;
+        for (int i = k; i < rows; ++i) b[i] -= s * v[i - k];
+    }
+    for (int k = cols - 1; k >= 0; --k) {
+        double s = b[k];
+        for (int j = k + 1; j < cols; ++j) s -= a[(size_t)k * cols + j] * y[j];
+        const double r = a[(size_t)k * cols + k];
+        if (r == 0.0) return false;
+        y[k] = s / r;
+    }
+    if (q) {
+        // q = H_0 H_1 ... H_{cols-1} e_{rows-1}: the last column of the full Q
+        std::vector<double> u(rows, 0.0);
+        u[rows - 1] = 1.0;
+        for (int k = cols - 1; k >= 0; --k) {
+            const std::vector<double> &v = vs[k];
+            double s = 0.0;
+            for (int i = k; i < rows; ++i) s += v[i - k] * u[i];
+            s *= taus[k];
+            for (int i = k; i < rows; ++i) u[i] -= s * v[i - k];
+        }
+        for (int i = 0; i < rows; ++i) q[i] = u[i];
+    }
+    return true;
+}
+
+bool cholesky(int n, const double *A, double *L) {
+    for (int i = 0; i < n * n; ++i) L[i] = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double s = A[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        if (!(s > 0.0)) return false;
+        const double ljj = std::sqrt(s);
+        L[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = t / ljj;
+        }
+    }
+    return true;
+}
+
+void lower_solve(int n, const double *L, double *b) {
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * b[k];
+        b[i] = s / L[(size_t)i * n + i];
+    }
+}
+
+void upper_t_solve(int n, const double *L, double *b) {
+    // solve L^T x = b
+    for (int i = n - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * b[k];
+        b[i] = s / L[(size_t)i * n + i];
+    }
+}
+
+template <typename S>
+static bool lu_factor_t(int n, S *A, int *piv) {
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        double best = std::abs(A[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; ++i)
+            if (std::abs(A[(size_t)i * n + k]) > best) { best = std::abs(A[(size_t)i * n + k]); p = i; }
+        piv[k] = p;
+        if (best == 0.0) return false;
+        if (p != k)
+            for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
+        for (int i = k + 1; i < n; ++i) {
+            const S f = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+            A[(size_t)i * n + k] = f;
+            for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= f * A[(size_t)k * n + j];
+        }
+    }
+    return true;
+}
+
+template <typename S>
+static void lu_solve_t(int n, const S *LU, const int *piv, S *b) {
+    for (int k = 0; k < n; ++k)
+        if (piv[k] != k) std::swap(b[k], b[piv[k]]);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < i; ++k) b[i] -= LU[(size_t)i * n + k] * b[k];
+    for (int i = n - 1; i >= 0; --i) {
+        for (int k = i + 1; k < n; ++k) b[i] -= LU[(size_t)i * n + k] * b[k];
+        b[i] /= LU[(size_t)i * n + i];
+    }
+}
+
+bool lu_factor(int n, double *A, int *piv) { return lu_factor_t(n, A, piv); }
+void lu_solve(int n, const double *LU, const int *piv, double *b) { lu_solve_t(n, LU, piv, b); }
+bool lu_factor(int n, std::complex<double> *A, int *piv) { return lu_factor_t(n, A, piv); }
+void lu_solve(int n, const std::complex<double> *LU, const int *piv, std::complex<double> *b) {
+    lu_solve_t(n, LU, piv, b);
+}
+
+bool mgs_columns(int rows, int cols, double *P) {
+    for (int j = 0; j < cols; ++j) {
+        for (int pass = 0; pass < 2; ++pass)
+            for (int i = 0; i < j; ++i) {
+                double s = 0.0;
+                for (int r = 0; r < rows; ++r) s += P[(size_t)r * cols + i] * P[(size_t)r * cols + j];
+                for (int r = 0; r < rows; ++r) P[(size_t)r * cols + j] -= s * P[(size_t)r * cols + i];
+            }
+        double nrm = 0.0;
+        for (int r = 0; r < rows; ++r) nrm += P[(size_t)r * cols + j] * P[(size_t)r * cols + j];
+        nrm = std::sqrt(nrm);
+        if (!(nrm > 0.0)) return false;
+        for (int r = 0; r < rows; ++r) P[(size_t)r * cols + j] /= nrm;
+    }
+    return true;
+}
+
+}  // namespace dlz
+
+extern "C" int dlz_host_symeig(int n, const double *A, double *w, double *Z) {
+    if (n < 0 || (n > 0 && (!A || !w || !Z))) return DLZ_ERR_BADARG;
+    return dlz::sym_eig(n, A, w, Z) ? DLZ_OK : DLZ_ERR_NONFINITE;
+}
+
+extern "C" int dlz_host_lstsq(int rows, int cols, const double *T, const double *c, double *y,
+                              double *q) {
+    if (rows <= cols || cols <= 0 || !T || !c || !y) return DLZ_ERR_BADARG;
+    return dlz::lstsq(rows, cols, T, c, y, q) ? DLZ_OK : DLZ_ERR_BREAKDOWN;
+}

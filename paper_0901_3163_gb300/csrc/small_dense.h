@@ -1,0 +1,27 @@
+// Host FP64 dense helpers for the small projected problems (row-major).
+#pragma once
+
+#include <complex>
+
+#include "../../include/dlz.h"
+
+namespace dlz {
+
+// Eigen-decomposition of symmetric A (n x n): w ascending, column j of Z the
+// eigenvector of w[j].  false if the QR iteration did not converge.
+bool sym_eig(int n, const double *A, double *w, double *Z);
+// y = argmin ||c - T y|| (rows > cols); q (optional, rows == cols + 1): unit
+// vector orthogonal to range(T).
+bool lstsq(int rows, int cols, const double *T, const double *c, double *y, double *q);
+// A = L L^T (lower L); false if A is not positive definite.
+bool cholesky(int n, const double *A, double *L);
+void lower_solve(int n, const double *L, double *b);      // L x = b, in place
+void upper_t_solve(int n, const double *L, double *b);    // L^T x = b, in place
+bool lu_factor(int n, double *A, int *piv);
+void lu_solve(int n, const double *LU, const int *piv, double *b);
+bool lu_factor(int n, std::complex<double> *A, int *piv);
+void lu_solve(int n, const std::complex<double> *LU, const int *piv, std::complex<double> *b);
+// Orthonormalise the columns of P (rows x cols) left to right, MGS twice.
+bool mgs_columns(int rows, int cols, double *P);
+
+}  // namespace dlz

@@ -1,0 +1,861 @@
+// Solver drivers: Lan-DR(m,k), MinRes-DR(m,k), D-CG and D-MinRes
+// (arXiv:0901.3163, Sec. 1-2) on the FP64 and FP32 device kernels.
+//
+// The host drives the cycle structure; inside a Lanczos cycle and inside the
+// CG / MinRes loops every scalar (alpha_j, beta_j, the Givens rotation of
+// MinRes, the CG step lengths) is produced and consumed on the device by the
+// fused reduction kernels, so the host only synchronises at the end of a
+// restart cycle (to solve the small projected problem) and every
+// `check_every` iterations (to read a residual norm).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "dlz_internal.cuh"
+#include "reduce.cuh"
+#include "small_dense.h"
+#include "solvers.h"
+
+namespace dlz {
+
+typedef std::complex<double> zc;
+
+// ------------------------------------------------------------------ vector helpers (FP64)
+namespace v64 {
+
+inline long nel(const Op &op) { return 12L * op.g.V; }
+
+int copy(Op &op, double2 *dst, const double2 *src) {
+    DLZ_CUDA_TRY(cudaMemcpyAsync(dst, src, nel(op) * sizeof(double2), cudaMemcpyDeviceToDevice, op.stream));
+    return DLZ_OK;
+}
+int zero(Op &op, double2 *dst) {
+    DLZ_CUDA_TRY(cudaMemsetAsync(dst, 0, nel(op) * sizeof(double2), op.stream));
+    return DLZ_OK;
+}
+// gamma5 on internal planes: components 6..11 (spins 2, 3) change sign
+int gamma5(Op &op, double2 *dst, const double2 *src) {
+    const long half = 6L * op.g.V;
+    return map(op, nel(op), [=] __device__(long i) {
+        double2 v = src[i];
+        if (i >= half) { v.x = -v.x; v.y = -v.y; }
+        dst[i] = v;
+    });
+}
+// result[slot] = ||a - b||^2 (b may be null: ||a||^2), copied to *host_out after sync
+int norm2_diff(Op &op, const double2 *a, const double2 *b, double *dev_out) {
+    return reduce<1>(op, nel(op), [=] __device__(long i, double (&acc)[1]) {
+        double2 v = a[i];
+        if (b) { const double2 w = b[i]; v.x -= w.x; v.y -= w.y; }
+        acc[0] += v.x * v.x + v.y * v.y;
+    }, [=] __device__(const double *r) { if (dev_out) *dev_out = r[0]; });
+}
+// out[l] (complex) = <V_l, w>  for l < nv, V_l = V + l*ld ; dev_out gets scale * dots
+int multidot(Op &op, const double2 *V, long ld, int nv, const double2 *w, double2 *dev_out, double scale) {
+    const long n = nel(op);
+    for (int l0 = 0; l0 < nv; l0 += 8) {
+        const int nb = std::min(8, nv - l0);
+        const double2 *Vb = V + (size_t)l0 * ld;
+        double2 *o = dev_out + l0;
+        DLZ_TRY(reduce<16>(op, n, [=] __device__(long i, double (&acc)[16]) {
+            const double2 x = w[i];
+#pragma unroll
+            for (int l = 0; l < 8; ++l) {
+                if (l < nb) {
+                    const double2 v = Vb[(size_t)l * ld + i];
+                    acc[2 * l] += v.x * x.x + v.y * x.y;        // Re conj(v) x
+                    acc[2 * l + 1] += v.x * x.y - v.y * x.x;    // Im conj(v) x
+                }
+            }
+        }, [=] __device__(const double *r) {
+            for (int l = 0; l < nb; ++l) o[l] = make_double2(scale * r[2 * l], scale * r[2 * l + 1]);
+        }));
+    }
+    return DLZ_OK;
+}
+
+}  // namespace v64
+
+// combine: out_l = (acc ? out_l : 0) + sum_j C[j][l] in_j   (nout any, in groups of 16)
+int combine64(Op &op, double2 *out, long ld_out, int nout, const double2 *in, long ld_in, int nin,
+              const void *dev_coef, int ld_coef, bool real, bool acc) {
+    const long n = 12L * op.g.V;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_combine64<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_combine64<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_combine64<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_combine64<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    if (nin <= 0 || nout <= 0) return DLZ_OK;
+    long blocks = (n + 127) / 128;
+    blocks = std::min(blocks, 152L * 8);
+    for (int l0 = 0; l0 < nout; l0 += 16) {
+        const int nb = std::min(16, nout - l0);
+        if (nb == 1) {
+            const size_t sm = (size_t)nin * 1 * sizeof(double2);
+            if (real) k_combine64<true, 1><<<(int)blocks, 128, sm, op.stream>>>(out + (size_t)l0 * ld_out, ld_out, 1, in, ld_in, nin, dev_coef, ld_coef, l0, acc, n);
+            else k_combine64<false, 1><<<(int)blocks, 128, sm, op.stream>>>(out + (size_t)l0 * ld_out, ld_out, 1, in, ld_in, nin, dev_coef, ld_coef, l0, acc, n);
+        } else {
+            const size_t sm = (size_t)nin * 16 * sizeof(double2);
+            if (real) k_combine64<true, 16><<<(int)blocks, 128, sm, op.stream>>>(out + (size_t)l0 * ld_out, ld_out, nb, in, ld_in, nin, dev_coef, ld_coef, l0, acc, n);
+            else k_combine64<false, 16><<<(int)blocks, 128, sm, op.stream>>>(out + (size_t)l0 * ld_out, ld_out, nb, in, ld_in, nin, dev_coef, ld_coef, l0, acc, n);
+        }
+        op.prof.launches++;
+        DLZ_CUDA_TRY(cudaGetLastError());
+    }
+    return DLZ_OK;
+}
+
+// ------------------------------------------------------------------ small pinned scalar block
+struct HostScratch {
+    double *p = nullptr;
+    size_t n = 0;
+    int ensure(size_t count) {
+        if (count <= n) return DLZ_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        DLZ_CUDA_TRY(cudaMallocHost(&p, count * sizeof(double)));
+        n = count;
+        return DLZ_OK;
+    }
+    ~HostScratch() { if (p) cudaFreeHost(p); }
+};
+
+static int d2h_sync(Op &op, void *dst, const void *src, size_t bytes) {
+    DLZ_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, op.stream));
+    DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+    return DLZ_OK;
+}
+static int h2d(Op &op, void *dst, const void *src, size_t bytes) {
+    DLZ_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, op.stream));
+    return DLZ_OK;
+}
+
+// ------------------------------------------------------------------ deflation set
+int build_deflation(Op &op, int which, const double2 *Vk, int k, dlz_defl_s **out) {
+    dlz_defl_s *d = new dlz_defl_s();
+    d->op = &op;
+    d->k = k;
+    d->which = which;
+    const long n = 12L * op.g.V;
+    int rc = d->V64.alloc((size_t)k * n * sizeof(double2));
+    if (rc != DLZ_OK) { delete d; return rc; }
+    rc = [&]() -> int {
+        DLZ_CUDA_TRY(cudaMemcpyAsync(d->V64.p, Vk, (size_t)k * n * sizeof(double2), cudaMemcpyDeviceToDevice, op.stream));
+        return DLZ_OK;
+    }();
+    if (rc != DLZ_OK) { delete d; return rc; }
+    rc = deflation_finish(op, d);
+    if (rc != DLZ_OK) { delete d; return rc; }
+    *out = d;
+    return DLZ_OK;
+}
+
+// H = V^dag A V, its LU factors, and the Rayleigh-Ritz pairs (values, residuals).
+int deflation_finish(Op &op, dlz_defl_s *d) {
+    const int k = d->k;
+    const long n = 12L * op.g.V;
+    if (k == 0) return DLZ_OK;
+    DevBuf AV, tmp, dots, Y, AY, coef;
+    DLZ_TRY(AV.alloc((size_t)k * n * sizeof(double2)));
+    DLZ_TRY(tmp.alloc((size_t)n * sizeof(double2)));
+    DLZ_TRY(dots.alloc((size_t)k * k * sizeof(double2)));
+    const double2 *V = d->V64.as<double2>();
+    for (int j = 0; j < k; ++j) {
+        double2 *avj = AV.as<double2>() + (size_t)j * n;
+        DLZ_TRY(apply64(op, avj, V + (size_t)j * n, d->which, tmp.as<double2>()));
+        DLZ_TRY(v64::multidot(op, V, n, k, avj, dots.as<double2>() + (size_t)j * k, 1.0));
+    }
+    std::vector<double2> hd((size_t)k * k);
+    DLZ_TRY(d2h_sync(op, hd.data(), dots.p, hd.size() * sizeof(double2)));
+    // dots[j*k + i] = <v_i, A v_j> = H[i][j]; hermitise
+    d->H.assign((size_t)k * k, zc(0, 0));
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            const zc hij(hd[(size_t)j * k + i].x, hd[(size_t)j * k + i].y);
+            const zc hji(hd[(size_t)i * k + j].x, hd[(size_t)i * k + j].y);
+            d->H[(size_t)i * k + j] = 0.5 * (hij + std::conj(hji));
+        }
+    d->Hlu = d->H;
+    d->piv.assign(k, 0);
+    if (!lu_factor(k, d->Hlu.data(), d->piv.data()))
+        return fail(DLZ_ERR_BREAKDOWN, "deflation: H = V^dag A V is singular");
+    // Rayleigh-Ritz pairs: eigenvectors of the hermitian H via the real
+    // symmetric embedding [[Re H, -Im H], [Im H, Re H]] (each eigenvalue twice).
+    const int n2 = 2 * k;
+    std::vector<double> E((size_t)n2 * n2), w(n2), Z((size_t)n2 * n2);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            const zc h = d->H[(size_t)i * k + j];
+            E[(size_t)i * n2 + j] = h.real();
+            E[(size_t)i * n2 + k + j] = -h.imag();
+            E[(size_t)(k + i) * n2 + j] = h.imag();
+            E[(size_t)(k + i) * n2 + k + j] = h.real();
+        }
+    if (!sym_eig(n2, E.data(), w.data(), Z.data()))
+        return fail(DLZ_ERR_NONFINITE, "deflation: eigensolve of H failed");
+    d->values.clear();
+    d->Z.clear();
+    std::vector<std::vector<zc>> chosen;
+    for (int c = 0; c < n2 && (int)chosen.size() < k; ++c) {
+        std::vector<zc> z(k);
+        for (int i = 0; i < k; ++i) z[i] = zc(Z[(size_t)i * n2 + c], Z[(size_t)(k + i) * n2 + c]);
+        for (const auto &q : chosen) {
+            zc s(0, 0);
+            for (int i = 0; i < k; ++i) s += std::conj(q[i]) * z[i];
+            for (int i = 0; i < k; ++i) z[i] -= s * q[i];
+        }
+        double nr = 0;
+        for (int i = 0; i < k; ++i) nr += std::norm(z[i]);
+        nr = std::sqrt(nr);
+        if (nr < 0.5) continue;   // the twin of an eigenvector already taken
+        for (int i = 0; i < k; ++i) z[i] /= nr;
+        chosen.push_back(z);
+        d->values.push_back(w[c]);
+    }
+    if ((int)chosen.size() < k) return fail(DLZ_ERR_NONFINITE, "deflation: eigenvectors of H");
+    d->Z.resize((size_t)k * k);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) d->Z[(size_t)i * k + j] = chosen[j][i];   // column j = vector j
+    // residuals ||A y_j - value_j y_j|| with y = V Z, A y = (A V) Z
+    DLZ_TRY(Y.alloc((size_t)k * n * sizeof(double2)));
+    DLZ_TRY(AY.alloc((size_t)k * n * sizeof(double2)));
+    DLZ_TRY(coef.alloc((size_t)k * k * sizeof(double2)));
+    std::vector<double2> zc2((size_t)k * k);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j)
+            zc2[(size_t)i * k + j] = make_double2(d->Z[(size_t)i * k + j].real(), d->Z[(size_t)i * k + j].imag());
+    DLZ_TRY(h2d(op, coef.p, zc2.data(), zc2.size() * sizeof(double2)));
+    DLZ_TRY(combine64(op, Y.as<double2>(), n, k, V, n, k, coef.p, k, false, false));
+    DLZ_TRY(combine64(op, AY.as<double2>(), n, k, AV.as<double2>(), n, k, coef.p, k, false, false));
+    DevBuf res;
+    DLZ_TRY(res.alloc((size_t)k * sizeof(double)));
+    for (int j = 0; j < k; ++j) {
+        const double2 *y = Y.as<double2>() + (size_t)j * n, *ay = AY.as<double2>() + (size_t)j * n;
+        const double lam = d->values[j];
+        double *o = res.as<double>() + j;
+        DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+            const double2 a = ay[i], b = y[i];
+            const double rx = a.x - lam * b.x, ry = a.y - lam * b.y;
+            acc[0] += rx * rx + ry * ry;
+        }, [=] __device__(const double *r) { *o = sqrt(r[0]); }));
+    }
+    d->residuals.assign(k, 0.0);
+    DLZ_TRY(d2h_sync(op, d->residuals.data(), res.p, (size_t)k * sizeof(double)));
+    return DLZ_OK;
+}
+
+// x0 = V H^-1 V^dag b  (b, x0 internal FP64; x0 overwritten)
+static int project64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x0, DevBuf &dots) {
+    const int k = d->k;
+    const long n = 12L * op.g.V;
+    if (k == 0) return v64::zero(op, x0);
+    DLZ_TRY(v64::multidot(op, d->V64.as<double2>(), n, k, b, dots.as<double2>(), 1.0));
+    std::vector<double2> c(k);
+    DLZ_TRY(d2h_sync(op, c.data(), dots.p, k * sizeof(double2)));
+    std::vector<zc> z(k);
+    for (int i = 0; i < k; ++i) z[i] = zc(c[i].x, c[i].y);
+    lu_solve(k, d->Hlu.data(), d->piv.data(), z.data());
+    for (int i = 0; i < k; ++i) c[i] = make_double2(z[i].real(), z[i].imag());
+    DLZ_TRY(h2d(op, dots.p, c.data(), k * sizeof(double2)));
+    return combine64(op, x0, n, 1, d->V64.as<double2>(), n, k, dots.p, 1, false, false);
+}
+
+// ------------------------------------------------------------------ DR solvers
+int dr_solve(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const dlz_params &p,
+             dlz_defl_s **defl_out, dlz_stats &st) {
+    const int m = p.m, k = p.k;
+    const long n = 12L * op.g.V;
+    const int which = harmonic ? DLZ_Q : DLZ_DDAGD;
+    const int mv_per = harmonic ? 1 : 2;
+    DevBuf Va, Vb, w, tmp, bb, bp, x, Dx, scal, coef;
+    DLZ_TRY(Va.alloc((size_t)(m + 1) * n * sizeof(double2)));
+    DLZ_TRY(Vb.alloc((size_t)(m + 1) * n * sizeof(double2)));
+    DLZ_TRY(w.alloc(n * sizeof(double2)));
+    DLZ_TRY(tmp.alloc(n * sizeof(double2)));
+    DLZ_TRY(bb.alloc(n * sizeof(double2)));
+    DLZ_TRY(bp.alloc(n * sizeof(double2)));
+    DLZ_TRY(x.alloc(n * sizeof(double2)));
+    DLZ_TRY(Dx.alloc(n * sizeof(double2)));
+    // device scalars: alpha[m], beta[m], norms[4]
+    DLZ_TRY(scal.alloc((size_t)(2 * m + 8) * sizeof(double)));
+    DLZ_TRY(coef.alloc((size_t)(m + 1) * (m + 1) * sizeof(double2)));
+    double *d_alpha = scal.as<double>(), *d_beta = d_alpha + m, *d_norm = d_beta + m;
+    HostScratch hs;
+    DLZ_TRY(hs.ensure(2 * m + 8));
+
+    DLZ_TRY(v64::copy(op, bb.as<double2>(), b_in));
+    // right-hand side of the hermitian system: gamma5 b (Q) or D^dag b (D^dag D)
+    if (harmonic) DLZ_TRY(v64::gamma5(op, bp.as<double2>(), bb.as<double2>()));
+    else DLZ_TRY(wilson64(op, bp.as<double2>(), bb.as<double2>(), DLZ_DDAG));
+    if (!harmonic) st.mvps += 1;
+    DLZ_TRY(v64::zero(op, x.as<double2>()));
+    DLZ_TRY(v64::norm2_diff(op, bb.as<double2>(), nullptr, d_norm));
+    DLZ_TRY(v64::norm2_diff(op, bp.as<double2>(), nullptr, d_norm + 1));
+    DLZ_TRY(d2h_sync(op, hs.p, d_norm, 2 * sizeof(double)));
+    const double bnorm = std::sqrt(hs.p[0]), beta0 = std::sqrt(hs.p[1]);
+    if (!std::isfinite(bnorm) || !std::isfinite(beta0)) return fail(DLZ_ERR_NONFINITE, "right-hand side is not finite");
+    if (bnorm == 0.0) {
+        DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
+        st.converged = 1; st.true_residual = 0.0;
+        if (defl_out) *defl_out = nullptr;
+        return DLZ_OK;
+    }
+    double2 *V = Va.as<double2>(), *Vn = Vb.as<double2>();
+    // v_1 = b' / ||b'||
+    {
+        const double2 *src = bp.as<double2>();
+        const double inv = 1.0 / beta0;
+        DLZ_TRY(map(op, n, [=] __device__(long i) { double2 v = src[i]; V[i] = make_double2(v.x * inv, v.y * inv); }));
+    }
+    std::vector<double> T((size_t)(m + 1) * m, 0.0), c(m + 1, 0.0);
+    c[0] = beta0;
+    int j0 = 0;
+    double Anorm = 0.0;
+    long long mvps_at_conv = -1;
+    std::vector<double> theta_k(k), ritz_res(k);
+    bool converged = false;
+    int cycle = 0;
+    const double2 *coefd = coef.as<double2>();
+    double *coefr = coef.as<double>();
+    for (cycle = 0; cycle < p.max_cycles; ++cycle) {
+        // ---------------- Lanczos steps j0 .. m-1
+        if (j0 > 0) {
+            // coupling of the restart vector to the kept vectors: coefficients -T[j0][i]
+            std::vector<double> cp(j0);
+            for (int i = 0; i < j0; ++i) cp[i] = -T[(size_t)j0 * m + i];
+            DLZ_TRY(h2d(op, coefr, cp.data(), j0 * sizeof(double)));
+        }
+        for (int j = j0; j < m; ++j) {
+            double2 *vj = V + (size_t)j * n, *wv = w.as<double2>();
+            DLZ_TRY(apply64(op, wv, vj, which, tmp.as<double2>()));
+            st.mvps += mv_per;
+            if (j == j0 && j0 > 0)
+                DLZ_TRY(combine64(op, wv, n, 1, V, n, j0, coefr, 1, true, true));
+            const double2 *vprev = (j > j0) ? V + (size_t)(j - 1) * n : nullptr;
+            const double *bprev = (j > j0) ? d_beta + (j - 1) : nullptr;
+            double *aj = d_alpha + j, *bj = d_beta + j;
+            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                double2 x_ = wv[i];
+                if (vprev) {
+                    const double bt = *bprev;
+                    const double2 u = vprev[i];
+                    x_.x -= bt * u.x; x_.y -= bt * u.y;
+                    wv[i] = x_;
+                }
+                const double2 v = vj[i];
+                acc[0] += v.x * x_.x + v.y * x_.y;
+            }, [=] __device__(const double *r) { *aj = r[0]; }));
+            const bool reorth = (j0 > 0) && p.reorth_period > 0 && ((j - j0) % p.reorth_period == 0);
+            if (reorth) {
+                DLZ_TRY(map(op, n, [=] __device__(long i) {
+                    const double a = *aj;
+                    double2 x_ = wv[i];
+                    const double2 v = vj[i];
+                    x_.x -= a * v.x; x_.y -= a * v.y;
+                    wv[i] = x_;
+                }));
+                double2 *cd = coef.as<double2>() + (m + 1);   // after the coupling block
+                DLZ_TRY(v64::multidot(op, V, n, j0, wv, cd, -1.0));
+                DLZ_TRY(combine64(op, wv, n, 1, V, n, j0, cd, 1, false, true));
+                DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                    const double2 x_ = wv[i];
+                    acc[0] += x_.x * x_.x + x_.y * x_.y;
+                }, [=] __device__(const double *r) { *bj = sqrt(r[0]); }));
+            } else {
+                DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                    const double a = *aj;
+                    double2 x_ = wv[i];
+                    const double2 v = vj[i];
+                    x_.x -= a * v.x; x_.y -= a * v.y;
+                    wv[i] = x_;
+                    acc[0] += x_.x * x_.x + x_.y * x_.y;
+                }, [=] __device__(const double *r) { *bj = sqrt(r[0]); }));
+            }
+            double2 *vn = V + (size_t)(j + 1) * n;
+            DLZ_TRY(map(op, n, [=] __device__(long i) {
+                const double inv = 1.0 / *bj;
+                const double2 x_ = wv[i];
+                vn[i] = make_double2(x_.x * inv, x_.y * inv);
+            }));
+            st.iterations++;
+        }
+        // ---------------- small problem on the host
+        DLZ_TRY(d2h_sync(op, hs.p, d_alpha, 2 * m * sizeof(double)));
+        double tmax = 0.0;
+        for (int j = j0; j < m; ++j) {
+            const double a = hs.p[j], bt = hs.p[m + j];
+            if (!std::isfinite(a) || !std::isfinite(bt)) return fail(DLZ_ERR_NONFINITE, "Lanczos coefficients not finite");
+            T[(size_t)j * m + j] = a;
+            T[(size_t)(j + 1) * m + j] = bt;
+            if (j + 1 < m) T[(size_t)j * m + j + 1] = bt;
+            if (j > j0) T[(size_t)(j - 1) * m + j] = T[(size_t)j * m + j - 1];
+            tmax = std::max(tmax, std::fabs(a));
+        }
+        for (int i = 0; i < j0; ++i) T[(size_t)i * m + j0] = T[(size_t)j0 * m + i];
+        for (int j = j0; j < m; ++j)
+            if (hs.p[m + j] <= 1e-14 * std::max(tmax, Anorm))
+                return fail(DLZ_ERR_BREAKDOWN, "Lanczos breakdown (invariant subspace)");
+        std::vector<double> Tm((size_t)m * m);
+        for (int i = 0; i < m; ++i)
+            for (int jj = 0; jj < m; ++jj) Tm[(size_t)i * m + jj] = T[(size_t)i * m + jj];
+        std::vector<double> ev(m), G((size_t)m * m), y(m);
+        if (!sym_eig(m, Tm.data(), ev.data(), G.data())) return fail(DLZ_ERR_NONFINITE, "eig(T_m) failed");
+        Anorm = std::max(Anorm, std::max(std::fabs(ev[0]), std::fabs(ev[m - 1])));
+        const double tol_eig = p.tol_eig > 0 ? p.tol_eig : 1e-10 * Anorm;
+        std::vector<double> P((size_t)(m + 1) * (k + 1), 0.0), Tn((size_t)(m + 1) * m, 0.0), cn(m + 1, 0.0);
+        std::vector<double> s_ls;
+        double rho = 0.0;
+        if (!harmonic) {
+            // Galerkin T_m y = c (Lan-DR)
+            std::vector<double> LU = Tm;
+            std::vector<int> piv(m);
+            std::copy(c.begin(), c.begin() + m, y.begin());
+            if (!lu_factor(m, LU.data(), piv.data())) return fail(DLZ_ERR_BREAKDOWN, "T_m singular");
+            lu_solve(m, LU.data(), piv.data(), y.data());
+            rho = -T[(size_t)m * m + m - 1] * y[m - 1];
+            // k algebraically smallest Ritz values (ev ascending)
+            for (int l = 0; l < k; ++l) {
+                theta_k[l] = ev[l];
+                for (int i = 0; i < m; ++i) P[(size_t)i * (k + 1) + l] = G[(size_t)i * m + l];
+                ritz_res[l] = std::fabs(T[(size_t)m * m + m - 1] * G[(size_t)(m - 1) * m + l]);
+            }
+            P[(size_t)m * (k + 1) + k] = 1.0;
+            for (int l = 0; l < k; ++l) Tn[(size_t)l * m + l] = theta_k[l];
+            for (int l = 0; l < k; ++l) Tn[(size_t)k * m + l] = T[(size_t)m * m + m - 1] * G[(size_t)(m - 1) * m + l];
+            cn[k] = rho;
+        } else {
+            // least squares min ||c - Tbar y|| (MinRes-DR)
+            std::vector<double> q(m + 1);
+            if (!lstsq(m + 1, m, T.data(), c.data(), y.data(), q.data())) return fail(DLZ_ERR_BREAKDOWN, "least squares failed");
+            s_ls.assign(m + 1, 0.0);
+            for (int i = 0; i <= m; ++i) {
+                double t = c[i];
+                for (int jj = 0; jj < m; ++jj) t -= T[(size_t)i * m + jj] * y[jj];
+                s_ls[i] = t;
+            }
+            // harmonic Ritz: T_m g = mu (Tbar^T Tbar) g, theta = 1/mu
+            std::vector<double> M((size_t)m * m, 0.0), L((size_t)m * m), X((size_t)m * m), C((size_t)m * m);
+            for (int i = 0; i < m; ++i)
+                for (int jj = 0; jj < m; ++jj) {
+                    double t = 0;
+                    for (int r = 0; r <= m; ++r) t += T[(size_t)r * m + i] * T[(size_t)r * m + jj];
+                    M[(size_t)i * m + jj] = t;
+                }
+            if (!cholesky(m, M.data(), L.data())) return fail(DLZ_ERR_BREAKDOWN, "Tbar^T Tbar not positive definite");
+            // X = L^-1 T_m (column by column), C = L^-1 X^T
+            std::vector<double> col(m);
+            for (int jj = 0; jj < m; ++jj) {
+                for (int i = 0; i < m; ++i) col[i] = Tm[(size_t)i * m + jj];
+                lower_solve(m, L.data(), col.data());
+                for (int i = 0; i < m; ++i) X[(size_t)i * m + jj] = col[i];
+            }
+            for (int jj = 0; jj < m; ++jj) {
+                for (int i = 0; i < m; ++i) col[i] = X[(size_t)jj * m + i];
+                lower_solve(m, L.data(), col.data());
+                for (int i = 0; i < m; ++i) C[(size_t)i * m + jj] = col[i];
+            }
+            std::vector<double> mu(m), Zc((size_t)m * m);
+            if (!sym_eig(m, C.data(), mu.data(), Zc.data())) return fail(DLZ_ERR_NONFINITE, "harmonic eigensolve failed");
+            std::vector<int> idx(m);
+            for (int i = 0; i < m; ++i) idx[i] = i;
+            std::stable_sort(idx.begin(), idx.end(), [&](int a, int bq) { return std::fabs(mu[a]) > std::fabs(mu[bq]); });
+            std::vector<double> Gk((size_t)m * k);
+            for (int l = 0; l < k; ++l) {
+                for (int i = 0; i < m; ++i) col[i] = Zc[(size_t)i * m + idx[l]];
+                upper_t_solve(m, L.data(), col.data());
+                double nr = 0;
+                for (int i = 0; i < m; ++i) nr += col[i] * col[i];
+                nr = std::sqrt(nr);
+                for (int i = 0; i < m; ++i) Gk[(size_t)i * k + l] = col[i] / nr;
+                theta_k[l] = 1.0 / mu[idx[l]];
+                double r2 = 0;
+                for (int r = 0; r <= m; ++r) {
+                    double t = 0;
+                    for (int jj = 0; jj < m; ++jj) t += T[(size_t)r * m + jj] * Gk[(size_t)jj * k + l];
+                    if (r < m) t -= theta_k[l] * Gk[(size_t)r * k + l];
+                    r2 += t * t;
+                }
+                ritz_res[l] = std::sqrt(r2);
+            }
+            double qs = 0;
+            for (int i = 0; i <= m; ++i) qs += q[i] * s_ls[i];
+            if (qs < 0) for (double &t : q) t = -t;
+            for (int i = 0; i < m; ++i)
+                for (int l = 0; l < k; ++l) P[(size_t)i * (k + 1) + l] = Gk[(size_t)i * k + l];
+            for (int i = 0; i <= m; ++i) P[(size_t)i * (k + 1) + k] = q[i];
+            if (!mgs_columns(m + 1, k + 1, P.data())) return fail(DLZ_ERR_BREAKDOWN, "restart basis lost rank");
+            // Tbar_k = P^T Tbar P[:m, :k]
+            std::vector<double> TP((size_t)(m + 1) * k, 0.0);
+            for (int r = 0; r <= m; ++r)
+                for (int l = 0; l < k; ++l) {
+                    double t = 0;
+                    for (int jj = 0; jj < m; ++jj) t += T[(size_t)r * m + jj] * P[(size_t)jj * (k + 1) + l];
+                    TP[(size_t)r * k + l] = t;
+                }
+            for (int a = 0; a <= k; ++a)
+                for (int l = 0; l < k; ++l) {
+                    double t = 0;
+                    for (int r = 0; r <= m; ++r) t += P[(size_t)r * (k + 1) + a] * TP[(size_t)r * k + l];
+                    Tn[(size_t)a * m + l] = t;
+                }
+            for (int a = 0; a < k; ++a)
+                for (int l = 0; l < a; ++l) {
+                    const double sym = 0.5 * (Tn[(size_t)a * m + l] + Tn[(size_t)l * m + a]);
+                    Tn[(size_t)a * m + l] = Tn[(size_t)l * m + a] = sym;
+                }
+            for (int a = 0; a <= k; ++a) {
+                double t = 0;
+                for (int r = 0; r <= m; ++r) t += P[(size_t)r * (k + 1) + a] * s_ls[r];
+                cn[a] = t;
+            }
+        }
+        // ---------------- x += V_m y ; true residual ||b - D x|| / ||b||
+        DLZ_TRY(h2d(op, coefr, y.data(), m * sizeof(double)));
+        DLZ_TRY(combine64(op, x.as<double2>(), n, 1, V, n, m, coefr, 1, true, true));
+        DLZ_TRY(wilson64(op, Dx.as<double2>(), x.as<double2>(), DLZ_D));
+        st.mvps += 1;
+        DLZ_TRY(v64::norm2_diff(op, bb.as<double2>(), Dx.as<double2>(), d_norm + 2));
+        // ---------------- restart: V_{k+1} <- V_{m+1} P
+        DLZ_TRY(h2d(op, coef.p, P.data(), P.size() * sizeof(double)));
+        DLZ_TRY(combine64(op, Vn, n, k + 1, V, n, m + 1, coef.p, k + 1, true, false));
+        if (p.reorth_period > 0) {
+            // the vector carried across the restart joins the periodic re-orthogonalisation
+            double2 *vk = Vn + (size_t)k * n;
+            double2 *cd = coef.as<double2>() + (size_t)(m + 1) * (k + 1);
+            DLZ_TRY(v64::multidot(op, Vn, n, k, vk, cd, -1.0));
+            DLZ_TRY(combine64(op, vk, n, 1, Vn, n, k, cd, 1, false, true));
+            double *nrm = d_norm + 3;
+            DLZ_TRY(v64::norm2_diff(op, vk, nullptr, nrm));
+            DLZ_TRY(map(op, n, [=] __device__(long i) {
+                const double inv = 1.0 / sqrt(*nrm);
+                const double2 v = vk[i];
+                vk[i] = make_double2(v.x * inv, v.y * inv);
+            }));
+        }
+        DLZ_TRY(d2h_sync(op, hs.p, d_norm + 2, sizeof(double)));
+        const double rel = std::sqrt(hs.p[0]) / bnorm;
+        st.true_residual = rel;
+        if (!std::isfinite(rel)) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
+        const bool lin_ok = rel <= p.tol;
+        if (lin_ok && mvps_at_conv < 0) mvps_at_conv = st.mvps;
+        bool eig_ok = true;
+        for (int l = 0; l < k; ++l) eig_ok = eig_ok && ritz_res[l] <= tol_eig;
+        const bool over = mvps_at_conv >= 0 && (double)(st.mvps - mvps_at_conv) >= p.oversolve * (double)mvps_at_conv;
+        std::swap(V, Vn);
+        T.swap(Tn);
+        c.swap(cn);
+        j0 = k;
+        if (lin_ok && (eig_ok || over)) { converged = true; ++cycle; break; }
+    }
+    st.cycles = cycle;
+    st.converged = converged ? 1 : 0;
+    DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
+    if (defl_out) DLZ_TRY(build_deflation(op, which, V, k, defl_out));
+    DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+    return converged ? DLZ_OK : DLZ_ERR_NOT_CONVERGED;
+}
+
+// ------------------------------------------------------------------ D-MinRes (FP64)
+struct MinresState {
+    double beta, alpha, beta_next, inv_beta;
+    double c, s, c_old, s_old, phibar;
+    double eps, delta, gamma, tau;
+};
+
+static int minres_init(Op &op, MinresState *dst, double *d_norm) {
+    // beta = phibar = ||r||, fresh rotations
+    return map(op, 1, [=] __device__(long) {
+        const double b = sqrt(*d_norm);
+        MinresState s0;
+        s0.beta = 0.0; s0.alpha = 0.0; s0.beta_next = b; s0.inv_beta = b > 0 ? 1.0 / b : 0.0;
+        s0.c = 1.0; s0.s = 0.0; s0.c_old = 1.0; s0.s_old = 0.0; s0.phibar = b;
+        s0.eps = s0.delta = s0.gamma = s0.tau = 0.0;
+        *dst = s0;
+    });
+}
+
+int dminres64(Op &op, const dlz_defl_s *d, const double2 *b_in, double2 *x_out, const dlz_params &p,
+              dlz_stats &st) {
+    const long n = 12L * op.g.V;
+    DevBuf bg, x, r, vp, v, w, d1, d2, scal, dots;
+    DLZ_TRY(bg.alloc(n * sizeof(double2)));
+    DLZ_TRY(x.alloc(n * sizeof(double2)));
+    DLZ_TRY(r.alloc(n * sizeof(double2)));
+    DLZ_TRY(vp.alloc(n * sizeof(double2)));
+    DLZ_TRY(v.alloc(n * sizeof(double2)));
+    DLZ_TRY(w.alloc(n * sizeof(double2)));
+    DLZ_TRY(d1.alloc(n * sizeof(double2)));
+    DLZ_TRY(d2.alloc(n * sizeof(double2)));
+    DLZ_TRY(scal.alloc(64 * sizeof(double)));
+    DLZ_TRY(dots.alloc((size_t)std::max(1, d ? d->k : 1) * sizeof(double2)));
+    MinresState *ms = reinterpret_cast<MinresState *>(scal.as<double>());
+    double *d_norm = scal.as<double>() + 32;
+    HostScratch hs;
+    DLZ_TRY(hs.ensure(32));
+    DLZ_TRY(v64::gamma5(op, bg.as<double2>(), b_in));
+    DLZ_TRY(v64::norm2_diff(op, bg.as<double2>(), nullptr, d_norm + 1));
+    DLZ_TRY(d2h_sync(op, hs.p, d_norm + 1, sizeof(double)));
+    const double bnorm = std::sqrt(hs.p[0]);
+    if (!std::isfinite(bnorm)) return fail(DLZ_ERR_NONFINITE, "right-hand side is not finite");
+    if (bnorm == 0.0) {
+        DLZ_TRY(v64::zero(op, x_out));
+        st.converged = 1; st.true_residual = 0.0;
+        return DLZ_OK;
+    }
+    if (d && d->k > 0) DLZ_TRY(project64(op, d, bg.as<double2>(), x.as<double2>(), dots));
+    else DLZ_TRY(v64::zero(op, x.as<double2>()));
+    bool converged = false;
+    while (st.iterations < p.max_iter) {
+        // r = gamma5 b - Q x ; start a MinRes run from x
+        DLZ_TRY(wilson64(op, r.as<double2>(), x.as<double2>(), DLZ_Q));
+        st.mvps += 1;
+        {
+            const double2 *bgp = bg.as<double2>();
+            double2 *rp = r.as<double2>();
+            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                const double2 a = bgp[i], q = rp[i];
+                const double2 t = make_double2(a.x - q.x, a.y - q.y);
+                rp[i] = t;
+                acc[0] += t.x * t.x + t.y * t.y;
+            }, [=] __device__(const double *res) { *d_norm = res[0]; }));
+        }
+        DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
+        const double rel0 = std::sqrt(hs.p[0]) / bnorm;
+        st.true_residual = rel0;
+        if (!std::isfinite(rel0)) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
+        if (rel0 <= p.tol) { converged = true; break; }
+        DLZ_TRY(minres_init(op, ms, d_norm));
+        double2 *pvp = vp.as<double2>(), *pv = v.as<double2>(), *pw = w.as<double2>();
+        double2 *pd1 = d1.as<double2>(), *pd2 = d2.as<double2>();
+        {
+            const double2 *rp = r.as<double2>();
+            DLZ_TRY(map(op, n, [=] __device__(long i) {
+                const double inv = ms->inv_beta;
+                const double2 t = rp[i];
+                pv[i] = make_double2(t.x * inv, t.y * inv);
+                pvp[i] = make_double2(0.0, 0.0);
+                pd1[i] = make_double2(0.0, 0.0);
+                pd2[i] = make_double2(0.0, 0.0);
+            }));
+        }
+        double2 *px = x.as<double2>();
+        int it_run = 0;
+        bool stop_run = false;
+        while (!stop_run && st.iterations < p.max_iter) {
+            DLZ_TRY(wilson64(op, pw, pv, DLZ_Q));
+            st.mvps += 1;
+            // w -= beta_j v_{j-1}; alpha_j = <v_j, w>
+            {
+                const double2 *a_vp = pvp, *a_v = pv;
+                double2 *a_w = pw;
+                DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                    const double bt = ms->beta_next;
+                    double2 t = a_w[i];
+                    const double2 u = a_vp[i];
+                    t.x -= bt * u.x; t.y -= bt * u.y;
+                    a_w[i] = t;
+                    const double2 q = a_v[i];
+                    acc[0] += q.x * t.x + q.y * t.y;
+                }, [=] __device__(const double *res) {
+                    ms->beta = ms->beta_next;
+                    ms->alpha = res[0];
+                }));
+            }
+            // w -= alpha_j v_j; beta_{j+1} = ||w||; Givens update of the QR of Tbar_j
+            {
+                const double2 *a_v = pv;
+                double2 *a_w = pw;
+                DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                    const double al = ms->alpha;
+                    double2 t = a_w[i];
+                    const double2 q = a_v[i];
+                    t.x -= al * q.x; t.y -= al * q.y;
+                    a_w[i] = t;
+                    acc[0] += t.x * t.x + t.y * t.y;
+                }, [=] __device__(const double *res) {
+                    MinresState s = *ms;
+                    const double bn = sqrt(res[0]);
+                    const double eps = s.s_old * s.beta;
+                    const double deltabar = s.c_old * s.beta;
+                    const double delta = s.c * deltabar + s.s * s.alpha;
+                    const double gammabar = -s.s * deltabar + s.c * s.alpha;
+                    const double gamma = hypot(gammabar, bn);
+                    const double cn = gammabar / gamma, sn = bn / gamma;
+                    s.tau = cn * s.phibar;
+                    s.phibar = -sn * s.phibar;
+                    s.eps = eps; s.delta = delta; s.gamma = gamma;
+                    s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
+                    s.beta_next = bn;
+                    s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
+                    *ms = s;
+                }));
+            }
+            // d_j = (v_j - delta d_{j-1} - eps d_{j-2}) / gamma ; x += tau d_j ; v_{j+1} = w / beta_{j+1}
+            {
+                const double2 *a_v = pv, *a_d1 = pd1;
+                double2 *a_d2 = pd2, *a_w = pw, *a_x = px;
+                DLZ_TRY(map(op, n, [=] __device__(long i) {
+                    const double de = ms->delta, ep = ms->eps, ig = 1.0 / ms->gamma, ta = ms->tau, ib = ms->inv_beta;
+                    const double2 q = a_v[i], e1 = a_d1[i], e2 = a_d2[i];
+                    double2 dn;
+                    dn.x = (q.x - de * e1.x - ep * e2.x) * ig;
+                    dn.y = (q.y - de * e1.y - ep * e2.y) * ig;
+                    a_d2[i] = dn;
+                    double2 xx = a_x[i];
+                    xx.x += ta * dn.x; xx.y += ta * dn.y;
+                    a_x[i] = xx;
+                    const double2 t = a_w[i];
+                    a_w[i] = make_double2(t.x * ib, t.y * ib);
+                }));
+            }
+            // rotate: (v_prev, v, w) <- (v, w, v_prev) ; (d1, d2) <- (d2, d1)
+            double2 *t0 = pvp; pvp = pv; pv = pw; pw = t0;
+            std::swap(pd1, pd2);
+            st.iterations++;
+            ++it_run;
+            if (it_run % p.check_every == 0 || st.iterations >= p.max_iter) {
+                DLZ_TRY(d2h_sync(op, hs.p, ms, sizeof(MinresState)));
+                const MinresState *hsm = reinterpret_cast<const MinresState *>(hs.p);
+                if (!std::isfinite(hsm->phibar)) return fail(DLZ_ERR_NONFINITE, "MinRes residual not finite");
+                if (std::fabs(hsm->phibar) <= 0.5 * p.tol * bnorm || hsm->beta_next == 0.0) stop_run = true;
+            }
+        }
+    }
+    DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
+    if (!converged) {
+        // final FP64 verification
+        DLZ_TRY(wilson64(op, r.as<double2>(), x.as<double2>(), DLZ_Q));
+        DLZ_TRY(v64::norm2_diff(op, bg.as<double2>(), r.as<double2>(), d_norm));
+        DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
+        st.true_residual = std::sqrt(hs.p[0]) / bnorm;
+        converged = st.true_residual <= p.tol;
+    }
+    st.converged = converged ? 1 : 0;
+    return converged ? DLZ_OK : DLZ_ERR_NOT_CONVERGED;
+}
+
+// ------------------------------------------------------------------ D-CG (FP64, normal equations)
+struct CgState {
+    double rr, alpha, beta, ss;
+};
+
+int dcg64(Op &op, const dlz_defl_s *d, const double2 *b_in, double2 *x_out, const dlz_params &p,
+          dlz_stats &st) {
+    const long n = 12L * op.g.V;
+    DevBuf x, r, s, pp, t, q, bd, scal, dots;
+    DLZ_TRY(x.alloc(n * sizeof(double2)));
+    DLZ_TRY(r.alloc(n * sizeof(double2)));
+    DLZ_TRY(s.alloc(n * sizeof(double2)));
+    DLZ_TRY(pp.alloc(n * sizeof(double2)));
+    DLZ_TRY(t.alloc(n * sizeof(double2)));
+    DLZ_TRY(q.alloc(n * sizeof(double2)));
+    DLZ_TRY(bd.alloc(n * sizeof(double2)));
+    DLZ_TRY(scal.alloc(64 * sizeof(double)));
+    DLZ_TRY(dots.alloc((size_t)std::max(1, d ? d->k : 1) * sizeof(double2)));
+    CgState *cs = reinterpret_cast<CgState *>(scal.as<double>());
+    double *d_norm = scal.as<double>() + 32;
+    HostScratch hs;
+    DLZ_TRY(hs.ensure(32));
+    const double2 *b = b_in;
+    DLZ_TRY(v64::norm2_diff(op, b, nullptr, d_norm + 1));
+    DLZ_TRY(d2h_sync(op, hs.p, d_norm + 1, sizeof(double)));
+    const double bnorm = std::sqrt(hs.p[0]);
+    if (!std::isfinite(bnorm)) return fail(DLZ_ERR_NONFINITE, "right-hand side is not finite");
+    if (bnorm == 0.0) {
+        DLZ_TRY(v64::zero(op, x_out));
+        st.converged = 1; st.true_residual = 0.0;
+        return DLZ_OK;
+    }
+    if (d && d->k > 0) {
+        DLZ_TRY(wilson64(op, bd.as<double2>(), b, DLZ_DDAG));    // b' = D^dag b
+        st.mvps += 1;
+        DLZ_TRY(project64(op, d, bd.as<double2>(), x.as<double2>(), dots));
+    } else {
+        DLZ_TRY(v64::zero(op, x.as<double2>()));
+    }
+    double2 *px = x.as<double2>(), *pr = r.as<double2>(), *ps = s.as<double2>(), *pp_ = pp.as<double2>();
+    double2 *pt = t.as<double2>(), *pq = q.as<double2>();
+    bool converged = false;
+    while (st.iterations < p.max_iter) {
+        // s = b - D x ; r = D^dag s ; p = r
+        DLZ_TRY(wilson64(op, pt, px, DLZ_D));
+        st.mvps += 1;
+        DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+            const double2 a = b[i], u = pt[i];
+            const double2 v = make_double2(a.x - u.x, a.y - u.y);
+            ps[i] = v;
+            acc[0] += v.x * v.x + v.y * v.y;
+        }, [=] __device__(const double *res) { *d_norm = res[0]; }));
+        DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
+        const double rel0 = std::sqrt(hs.p[0]) / bnorm;
+        st.true_residual = rel0;
+        if (!std::isfinite(rel0)) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
+        if (rel0 <= p.tol) { converged = true; break; }
+        DLZ_TRY(wilson64(op, pr, ps, DLZ_DDAG));
+        st.mvps += 1;
+        DLZ_TRY(reduce<2>(op, n, [=] __device__(long i, double (&acc)[2]) {
+            const double2 v = pr[i];
+            pp_[i] = v;
+            acc[0] += v.x * v.x + v.y * v.y;
+            const double2 u = ps[i];
+            acc[1] += u.x * u.x + u.y * u.y;
+        }, [=] __device__(const double *res) { cs->rr = res[0]; cs->ss = res[1]; }));
+        int it_run = 0;
+        bool stop_run = false;
+        while (!stop_run && st.iterations < p.max_iter) {
+            DLZ_TRY(wilson64(op, pt, pp_, DLZ_D));               // t = D p
+            DLZ_TRY(wilson64(op, pq, pt, DLZ_DDAG));             // q = D^dag t
+            st.mvps += 2;
+            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                const double2 a = pp_[i], c = pq[i];
+                acc[0] += a.x * c.x + a.y * c.y;
+            }, [=] __device__(const double *res) { cs->alpha = cs->rr / res[0]; }));
+            DLZ_TRY(reduce<2>(op, n, [=] __device__(long i, double (&acc)[2]) {
+                const double al = cs->alpha;
+                const double2 a = pp_[i], c = pq[i], tt = pt[i];
+                double2 xx = px[i], rr_ = pr[i], ss_ = ps[i];
+                xx.x += al * a.x; xx.y += al * a.y;
+                rr_.x -= al * c.x; rr_.y -= al * c.y;
+                ss_.x -= al * tt.x; ss_.y -= al * tt.y;
+                px[i] = xx; pr[i] = rr_; ps[i] = ss_;
+                acc[0] += rr_.x * rr_.x + rr_.y * rr_.y;
+                acc[1] += ss_.x * ss_.x + ss_.y * ss_.y;
+            }, [=] __device__(const double *res) {
+                cs->beta = res[0] / cs->rr;
+                cs->rr = res[0];
+                cs->ss = res[1];
+            }));
+            DLZ_TRY(map(op, n, [=] __device__(long i) {
+                const double be = cs->beta;
+                const double2 rr_ = pr[i], a = pp_[i];
+                pp_[i] = make_double2(rr_.x + be * a.x, rr_.y + be * a.y);
+            }));
+            st.iterations++;
+            ++it_run;
+            if (it_run % p.check_every == 0 || st.iterations >= p.max_iter) {
+                DLZ_TRY(d2h_sync(op, hs.p, cs, sizeof(CgState)));
+                const CgState *h = reinterpret_cast<const CgState *>(hs.p);
+                if (!std::isfinite(h->ss)) return fail(DLZ_ERR_NONFINITE, "CG residual not finite");
+                if (std::sqrt(h->ss) <= 0.5 * p.tol * bnorm || h->rr == 0.0) stop_run = true;
+            }
+        }
+    }
+    DLZ_TRY(v64::copy(op, x_out, px));
+    if (!converged) {
+        DLZ_TRY(wilson64(op, pt, px, DLZ_D));
+        DLZ_TRY(v64::norm2_diff(op, b, pt, d_norm));
+        DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
+        st.true_residual = std::sqrt(hs.p[0]) / bnorm;
+        converged = st.true_residual <= p.tol;
+    }
+    st.converged = converged ? 1 : 0;
+    return converged ? DLZ_OK : DLZ_ERR_NOT_CONVERGED;
+}
+
+}  // namespace dlz

@@ -1,0 +1,39 @@
+// Solver entry points between the C ABI (api.cu) and the kernels (solvers.cu).
+#pragma once
+
+#include <complex>
+#include <vector>
+
+#include "dlz_internal.cuh"
+
+// The deflation set of Sec. 2: k orthonormal vectors (regular Ritz vectors
+// of Lan-DR or the span of the harmonic Ritz vectors of MinRes-DR) and the
+// projected operator H = V^dag A V used by the Galerkin projection of
+// D-CG / D-MinRes.
+struct dlz_defl_s {
+    dlz::Op *op = nullptr;
+    int k = 0;
+    int which = DLZ_Q;                          // DLZ_Q or DLZ_DDAGD
+    dlz::DevBuf V64;                            // k internal FP64 vectors
+    std::vector<std::complex<double>> H;        // k x k, row-major
+    std::vector<std::complex<double>> Hlu;      // LU factors of H
+    std::vector<int> piv;
+    std::vector<double> values;                 // Rayleigh-Ritz values (ascending)
+    std::vector<double> residuals;              // ||A y - value y||
+    std::vector<std::complex<double>> Z;        // eigenvectors of H (column j <-> values[j])
+};
+
+namespace dlz {
+
+int dr_solve(Op &op, bool harmonic, const double2 *b, double2 *x, const dlz_params &p,
+             dlz_defl_s **defl_out, dlz_stats &st);
+int dminres64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x, const dlz_params &p,
+              dlz_stats &st);
+int dcg64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x, const dlz_params &p,
+          dlz_stats &st);
+int build_deflation(Op &op, int which, const double2 *Vk, int k, dlz_defl_s **out);
+int deflation_finish(Op &op, dlz_defl_s *d);
+int combine64(Op &op, double2 *out, long ld_out, int nout, const double2 *in, long ld_in, int nin,
+              const void *dev_coef, int ld_coef, bool real, bool acc);
+
+}  // namespace dlz

@@ -1,0 +1,166 @@
+// Wilson-Dirac stencil kernels (Sec. 2 of arXiv:0901.3163: the Wilson matrix M,
+// used as gamma5 M and M^dagger M) and the layout conversions around them.
+//
+// One thread per lattice site.  Spinor and link planes are component-major,
+// so each load instruction of a warp reads consecutive 16-byte (FP64 double2,
+// FP32 float4) or 8-byte (FP32 link float2) words; the eight neighbour
+// spinors of a site are re-read from L1/L2 (the time neighbour of site s is
+// Lx*Ly*Lz sites away: a window of a few MB that stays in the 129 MB L2), so
+// DRAM sees each spinor and link about once per application.
+#include "dlz_internal.cuh"
+#include "wilson_site.cuh"
+
+namespace dlz {
+
+namespace {
+
+constexpr int kStencilThreads64 = 128;
+constexpr int kStencilThreads32 = 128;
+
+template <typename T, bool G5IN, bool G5OUT>
+__global__ void __launch_bounds__(128)
+k_wilson(typename Field<T>::vec *__restrict__ out, const typename Field<T>::vec *__restrict__ in,
+         const cx<T> *__restrict__ U, Geom g, T kappa) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    cx<T> o[12];
+    wilson_site<T, G5IN, G5OUT>(s, g, kappa, in, U, o);
+    Field<T>::store(out, g.V, s, o);
+}
+
+template <typename T>
+int launch_wilson(Op &op, typename Field<T>::vec *out, const typename Field<T>::vec *in,
+                  const cx<T> *U, int which, int threads) {
+    const Geom &g = op.g;
+    const int blocks = (g.V + threads - 1) / threads;
+    const T kappa = (T)op.kappa;
+    op.prof.stencil_start(op.stream);
+    switch (which) {
+    case DLZ_D: k_wilson<T, false, false><<<blocks, threads, 0, op.stream>>>(out, in, U, g, kappa); break;
+    case DLZ_DDAG: k_wilson<T, true, true><<<blocks, threads, 0, op.stream>>>(out, in, U, g, kappa); break;
+    case DLZ_Q: k_wilson<T, false, true><<<blocks, threads, 0, op.stream>>>(out, in, U, g, kappa); break;
+    default: return fail(DLZ_ERR_BADARG, "stencil: which must be D, DDAG or Q");
+    }
+    op.prof.stencil_stop(op.stream);
+    op.prof.launches++;
+    op.prof.stencils++;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+
+// ------------------------------------------------------------------ layout kernels
+__global__ void k_pack64(double2 *__restrict__ dst, const double2 *__restrict__ src, int V) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // canonical index s*12 + a
+    if (i >= 12L * V) return;
+    const int s = (int)(i / 12), a = (int)(i % 12);
+    dst[(size_t)a * V + s] = src[i];
+}
+__global__ void k_unpack64(double2 *__restrict__ dst, const double2 *__restrict__ src, int V) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 12L * V) return;
+    const int s = (int)(i / 12), a = (int)(i % 12);
+    dst[i] = src[(size_t)a * V + s];
+}
+__global__ void k_pack32(float4 *__restrict__ dst, const float2 *__restrict__ src, int V) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // s*6 + c
+    if (i >= 6L * V) return;
+    const int s = (int)(i / 6), c = (int)(i % 6);
+    const float2 a = src[(size_t)s * 12 + 2 * c], b = src[(size_t)s * 12 + 2 * c + 1];
+    dst[(size_t)c * V + s] = make_float4(a.x, a.y, b.x, b.y);
+}
+__global__ void k_unpack32(float2 *__restrict__ dst, const float4 *__restrict__ src, int V) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6L * V) return;
+    const int s = (int)(i / 6), c = (int)(i % 6);
+    const float4 q = src[(size_t)c * V + s];
+    dst[(size_t)s * 12 + 2 * c] = make_float2(q.x, q.y);
+    dst[(size_t)s * 12 + 2 * c + 1] = make_float2(q.z, q.w);
+}
+// internal FP64 planes <-> internal FP32 planes (plane c of FP32 = planes 2c, 2c+1)
+__global__ void k_64to32(float4 *__restrict__ dst, const double2 *__restrict__ src, int V) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // c*V + s
+    if (i >= 6L * V) return;
+    const int c = (int)(i / V), s = (int)(i % V);
+    const double2 a = src[(size_t)(2 * c) * V + s], b = src[(size_t)(2 * c + 1) * V + s];
+    dst[i] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+__global__ void k_32to64(double2 *__restrict__ dst, const float4 *__restrict__ src, int V) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6L * V) return;
+    const int c = (int)(i / V), s = (int)(i % V);
+    const float4 q = src[i];
+    dst[(size_t)(2 * c) * V + s] = make_double2(q.x, q.y);
+    dst[(size_t)(2 * c + 1) * V + s] = make_double2(q.z, q.w);
+}
+
+inline int grid_for(long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace
+
+int wilson64(Op &op, double2 *out, const double2 *in, int which) {
+    return launch_wilson<double>(op, out, in, op.gauge64.as<double2>(), which, kStencilThreads64);
+}
+int wilson32(Op &op, float4 *out, const float4 *in, int which) {
+    return launch_wilson<float>(op, out, in, op.gauge32.as<float2>(), which, kStencilThreads32);
+}
+
+int apply64(Op &op, double2 *out, const double2 *in, int which, double2 *tmp) {
+    if (which == DLZ_DDAGD) {
+        // D^dag D = Q Q (gamma5 D is hermitian, Q^2 = gamma5 D gamma5 D = D^dag D)
+        DLZ_TRY(wilson64(op, tmp, in, DLZ_Q));
+        return wilson64(op, out, tmp, DLZ_Q);
+    }
+    return wilson64(op, out, in, which);
+}
+int apply32(Op &op, float4 *out, const float4 *in, int which, float4 *tmp) {
+    if (which == DLZ_DDAGD) {
+        DLZ_TRY(wilson32(op, tmp, in, DLZ_Q));
+        return wilson32(op, out, tmp, DLZ_Q);
+    }
+    return wilson32(op, out, in, which);
+}
+
+int pack64(Op &op, double2 *dst, const double2 *src) {
+    const long n = 12L * op.g.V;
+    k_pack64<<<grid_for(n, 256), 256, 0, op.stream>>>(dst, src, op.g.V);
+    op.prof.launches++;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+int unpack64(Op &op, double2 *dst, const double2 *src) {
+    const long n = 12L * op.g.V;
+    k_unpack64<<<grid_for(n, 256), 256, 0, op.stream>>>(dst, src, op.g.V);
+    op.prof.launches++;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+int pack32(Op &op, float4 *dst, const float2 *src) {
+    const long n = 6L * op.g.V;
+    k_pack32<<<grid_for(n, 256), 256, 0, op.stream>>>(dst, src, op.g.V);
+    op.prof.launches++;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+int unpack32(Op &op, float2 *dst, const float4 *src) {
+    const long n = 6L * op.g.V;
+    k_unpack32<<<grid_for(n, 256), 256, 0, op.stream>>>(dst, src, op.g.V);
+    op.prof.launches++;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+int convert64to32(Op &op, float4 *dst, const double2 *src) {
+    const long n = 6L * op.g.V;
+    k_64to32<<<grid_for(n, 256), 256, 0, op.stream>>>(dst, src, op.g.V);
+    op.prof.launches++;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+int convert32to64(Op &op, double2 *dst, const float4 *src) {
+    const long n = 6L * op.g.V;
+    k_32to64<<<grid_for(n, 256), 256, 0, op.stream>>>(dst, src, op.g.V);
+    op.prof.launches++;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+
+}  // namespace dlz

@@ -1,0 +1,192 @@
+// Per-site Wilson hopping term in the chiral basis, by spin projection.
+//
+// D psi(x) = psi(x) - kappa sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+//                                   + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ]
+// (the Wilson matrix M of arXiv:0901.3163, Sec. 2).  With psi = (u0, u1, l0, l1)
+// (spins 0..3, each a colour 3-vector) and gamma_k = [[0, -i s_k], [i s_k, 0]],
+// gamma_4 = [[0, 1], [1, 0]], each (1 -+ gamma_mu) has rank 2: its image is fixed
+// by a 2-spinor h = (h0, h1) built from psi, with the lower pair a fixed
+// 2x2 map (entries 0, +-1, +-i) of the upper pair.  Colour and spin commute,
+// so U is applied to h only (2 colour mat-vecs per hop instead of 4):
+//
+//   fwd mu=x: h = (u0 + i l1, u1 + i l0)   lower = (-i H1, -i H0)
+//   fwd mu=y: h = (u0 + l1,   u1 - l0)     lower = (-H1,    H0)
+//   fwd mu=z: h = (u0 + i l0, u1 - i l1)   lower = (-i H0,  i H1)
+//   fwd mu=t: h = (u0 - l0,   u1 - l1)     lower = (-H0,   -H1)
+//   bwd mu=x: h = (u0 - i l1, u1 - i l0)   lower = ( i H1,  i H0)
+//   bwd mu=y: h = (u0 - l1,   u1 + l0)     lower = ( H1,   -H0)
+//   bwd mu=z: h = (u0 - i l0, u1 + i l1)   lower = ( i H0, -i H1)
+//   bwd mu=t: h = (u0 + l0,   u1 + l1)     lower = ( H0,    H1)
+// where H = U h (forward) or U^dag h (backward).
+#pragma once
+
+#include "dlz_internal.cuh"
+
+namespace dlz {
+
+template <typename T> struct Field;
+template <> struct Field<double> {
+    typedef double2 vec;
+    __host__ __device__ static inline void load(const double2 *__restrict__ p, int V, int s,
+                                                double2 (&v)[12]) {
+#pragma unroll
+        for (int a = 0; a < 12; ++a) v[a] = p[(size_t)a * V + s];
+    }
+    __host__ __device__ static inline void store(double2 *__restrict__ p, int V, int s,
+                                                 const double2 (&v)[12]) {
+#pragma unroll
+        for (int a = 0; a < 12; ++a) p[(size_t)a * V + s] = v[a];
+    }
+};
+template <> struct Field<float> {
+    typedef float4 vec;
+    __host__ __device__ static inline void load(const float4 *__restrict__ p, int V, int s,
+                                                float2 (&v)[12]) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            float4 q = p[(size_t)c * V + s];
+            v[2 * c] = make_float2(q.x, q.y);
+            v[2 * c + 1] = make_float2(q.z, q.w);
+        }
+    }
+    __host__ __device__ static inline void store(float4 *__restrict__ p, int V, int s,
+                                                 const float2 (&v)[12]) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            p[(size_t)c * V + s] = make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
+    }
+};
+
+template <typename T>
+__host__ __device__ inline void load_link(const cx<T> *__restrict__ U, int V, int mu, int s,
+                                          cx<T> (&u)[9]) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u[e] = U[(size_t)(mu * 9 + e) * V + s];
+}
+
+// Accumulate (1 - gamma_mu) U h-projection of p into acc (forward hop).
+template <typename T, int MU>
+__host__ __device__ inline void hop_fwd(const cx<T> (&p)[12], const cx<T> (&u)[9], T sign,
+                                        cx<T> (&acc)[12]) {
+    cx<T> h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cx<T> u0 = p[c], u1 = p[3 + c], l0 = p[6 + c], l1 = p[9 + c];
+        if (MU == 0) { h0[c] = addI(u0, l1); h1[c] = addI(u1, l0); }
+        if (MU == 1) { h0[c] = u0 + l1;      h1[c] = u1 - l0; }
+        if (MU == 2) { h0[c] = addI(u0, l0); h1[c] = subI(u1, l1); }
+        if (MU == 3) { h0[c] = u0 - l0;      h1[c] = u1 - l1; }
+        h0[c].x *= sign; h0[c].y *= sign; h1[c].x *= sign; h1[c].y *= sign;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        cx<T> H0 = mk<T>(0, 0), H1 = mk<T>(0, 0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            H0 = cfma(u[3 * i + j], h0[j], H0);
+            H1 = cfma(u[3 * i + j], h1[j], H1);
+        }
+        acc[i] = acc[i] + H0;
+        acc[3 + i] = acc[3 + i] + H1;
+        if (MU == 0) { acc[6 + i] = subI(acc[6 + i], H1); acc[9 + i] = subI(acc[9 + i], H0); }
+        if (MU == 1) { acc[6 + i] = acc[6 + i] - H1;      acc[9 + i] = acc[9 + i] + H0; }
+        if (MU == 2) { acc[6 + i] = subI(acc[6 + i], H0); acc[9 + i] = addI(acc[9 + i], H1); }
+        if (MU == 3) { acc[6 + i] = acc[6 + i] - H0;      acc[9 + i] = acc[9 + i] - H1; }
+    }
+}
+
+// Accumulate (1 + gamma_mu) U^dag h-projection of p into acc (backward hop).
+template <typename T, int MU>
+__host__ __device__ inline void hop_bwd(const cx<T> (&p)[12], const cx<T> (&u)[9], T sign,
+                                        cx<T> (&acc)[12]) {
+    cx<T> h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cx<T> u0 = p[c], u1 = p[3 + c], l0 = p[6 + c], l1 = p[9 + c];
+        if (MU == 0) { h0[c] = subI(u0, l1); h1[c] = subI(u1, l0); }
+        if (MU == 1) { h0[c] = u0 - l1;      h1[c] = u1 + l0; }
+        if (MU == 2) { h0[c] = subI(u0, l0); h1[c] = addI(u1, l1); }
+        if (MU == 3) { h0[c] = u0 + l0;      h1[c] = u1 + l1; }
+        h0[c].x *= sign; h0[c].y *= sign; h1[c].x *= sign; h1[c].y *= sign;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        cx<T> H0 = mk<T>(0, 0), H1 = mk<T>(0, 0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            H0 = cfmaConj(u[3 * j + i], h0[j], H0);
+            H1 = cfmaConj(u[3 * j + i], h1[j], H1);
+        }
+        acc[i] = acc[i] + H0;
+        acc[3 + i] = acc[3 + i] + H1;
+        if (MU == 0) { acc[6 + i] = addI(acc[6 + i], H1); acc[9 + i] = addI(acc[9 + i], H0); }
+        if (MU == 1) { acc[6 + i] = acc[6 + i] + H1;      acc[9 + i] = acc[9 + i] - H0; }
+        if (MU == 2) { acc[6 + i] = addI(acc[6 + i], H0); acc[9 + i] = subI(acc[9 + i], H1); }
+        if (MU == 3) { acc[6 + i] = acc[6 + i] + H0;      acc[9 + i] = acc[9 + i] + H1; }
+    }
+}
+
+template <bool G5> __host__ __device__ inline void maybe_g5(double2 (&v)[12]) {
+    if (G5) {
+#pragma unroll
+        for (int a = 6; a < 12; ++a) { v[a].x = -v[a].x; v[a].y = -v[a].y; }
+    }
+}
+template <bool G5> __host__ __device__ inline void maybe_g5(float2 (&v)[12]) {
+    if (G5) {
+#pragma unroll
+        for (int a = 6; a < 12; ++a) { v[a].x = -v[a].x; v[a].y = -v[a].y; }
+    }
+}
+
+template <typename T, int MU, bool G5IN>
+__host__ __device__ inline void hop_pair(int s, const int (&c)[4], const Geom &g, int stride,
+                                         const typename Field<T>::vec *__restrict__ in,
+                                         const cx<T> *__restrict__ U, cx<T> (&acc)[12]) {
+    const int L = g.L[MU];
+    // forward neighbour and the boundary phase of a hop across the time edge
+    const int sf = (c[MU] == L - 1) ? s - (L - 1) * stride : s + stride;
+    const T phf = (MU == 3 && c[3] == L - 1) ? (T)g.bc_t : (T)1;
+    const int sb = (c[MU] == 0) ? s + (L - 1) * stride : s - stride;
+    const T phb = (MU == 3 && c[3] == 0) ? (T)g.bc_t : (T)1;
+    cx<T> p[12], u[9];
+    Field<T>::load(in, g.V, sf, p);
+    maybe_g5<G5IN>(p);
+    load_link<T>(U, g.V, MU, s, u);
+    hop_fwd<T, MU>(p, u, phf, acc);
+    Field<T>::load(in, g.V, sb, p);
+    maybe_g5<G5IN>(p);
+    load_link<T>(U, g.V, MU, sb, u);
+    hop_bwd<T, MU>(p, u, phb, acc);
+}
+
+// out(s) = [gamma5]^G5OUT (1 - kappa H) [gamma5]^G5IN in, at one site.
+template <typename T, bool G5IN, bool G5OUT>
+__host__ __device__ inline void wilson_site(int s, const Geom &g, T kappa,
+                                            const typename Field<T>::vec *__restrict__ in,
+                                            const cx<T> *__restrict__ U, cx<T> (&out)[12]) {
+    int c[4];
+    int r = s;
+    c[0] = r % g.L[0]; r /= g.L[0];
+    c[1] = r % g.L[1]; r /= g.L[1];
+    c[2] = r % g.L[2];
+    c[3] = r / g.L[2];
+    const int st1 = g.L[0], st2 = g.L[0] * g.L[1], st3 = st2 * g.L[2];
+    cx<T> acc[12];
+#pragma unroll
+    for (int a = 0; a < 12; ++a) acc[a] = mk<T>(0, 0);
+    hop_pair<T, 0, G5IN>(s, c, g, 1, in, U, acc);
+    hop_pair<T, 1, G5IN>(s, c, g, st1, in, U, acc);
+    hop_pair<T, 2, G5IN>(s, c, g, st2, in, U, acc);
+    hop_pair<T, 3, G5IN>(s, c, g, st3, in, U, acc);
+    Field<T>::load(in, g.V, s, out);
+    maybe_g5<G5IN>(out);
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+        out[a].x = out[a].x - kappa * acc[a].x;
+        out[a].y = out[a].y - kappa * acc[a].y;
+    }
+    maybe_g5<G5OUT>(out);
+}
+
+}  // namespace dlz

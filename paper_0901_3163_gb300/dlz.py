@@ -1,0 +1,295 @@
+"""Thin ctypes binding of the dlz C ABI (include/dlz.h); argument marshalling only.
+
+Every function carries the name of its C counterpart without the `dlz_`
+prefix.  Vectors are torch tensors (CUDA or CPU) or numpy arrays of complex128
+(complex64 for FP32 `apply`) laid out as [..., V, 4, 3]; the library itself
+detects host or device memory and does every step of the computation in its
+CUDA kernels.  There is no fallback: if libdlz.so is missing, importing this
+module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdlz.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "dlz.h")
+
+OK = 0
+ERR_BADARG = -1
+ERR_BAD_GAUGE = -2
+ERR_NONFINITE = -3
+ERR_NOT_CONVERGED = -4
+ERR_BREAKDOWN = -5
+ERR_DEVICE_TIMEOUT = -6
+ERR_CUDA = -7
+ERR_OOM = -8
+ERR_IO = -9
+
+D, DDAG, Q, DDAGD = 0, 1, 2, 3
+F64, F32 = 0, 1
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("k", ctypes.c_int), ("tol", ctypes.c_double),
+                ("tol_eig", ctypes.c_double), ("oversolve", ctypes.c_double),
+                ("max_cycles", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("reorth_period", ctypes.c_int), ("precision", ctypes.c_int),
+                ("reliable_delta", ctypes.c_double), ("check_every", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("mvps", ctypes.c_longlong), ("true_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("stencil_ms", ctypes.c_double),
+                ("stencil_launches", ctypes.c_longlong), ("gpu_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DlzError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(msg)
+        self.code = code
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_0901_3163_gb300.build.build()")
+lib = ctypes.CDLL(LIB_PATH)
+
+_vp = ctypes.c_void_p
+_ip = ctypes.c_int
+_dp = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "dlz_params_default": ([ctypes.POINTER(Params)], _ip),
+    "dlz_strerror": ([_ip], ctypes.c_char_p),
+    "dlz_last_error": ([], ctypes.c_char_p),
+    "dlz_create_operator": ([ctypes.POINTER(ctypes.c_int), _vp, ctypes.c_double, _ip, _vp,
+                             ctypes.POINTER(_vp)], _ip),
+    "dlz_destroy_operator": ([_vp], _ip),
+    "dlz_op_volume": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _ip),
+    "dlz_apply": ([_vp, _ip, _vp, _vp, _ip, _ip], _ip),
+    "dlz_landr": ([_vp, _vp, _vp, ctypes.POINTER(Params), ctypes.POINTER(_vp),
+                   ctypes.POINTER(Stats)], _ip),
+    "dlz_minresdr": ([_vp, _vp, _vp, ctypes.POINTER(Params), ctypes.POINTER(_vp),
+                      ctypes.POINTER(Stats)], _ip),
+    "dlz_dcg": ([_vp, _vp, _vp, _vp, _ip, ctypes.POINTER(Params), ctypes.POINTER(Stats)], _ip),
+    "dlz_dminres": ([_vp, _vp, _vp, _vp, _ip, ctypes.POINTER(Params), ctypes.POINTER(Stats)], _ip),
+    "dlz_defl_count": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], _ip),
+    "dlz_defl_get": ([_vp, _ip, _vp, _dp, _dp], _ip),
+    "dlz_defl_save": ([_vp, ctypes.c_char_p], _ip),
+    "dlz_defl_load": ([_vp, ctypes.c_char_p, ctypes.POINTER(_vp)], _ip),
+    "dlz_defl_destroy": ([_vp], _ip),
+    "dlz_host_symeig": ([_ip, _vp, _vp, _vp], _ip),
+    "dlz_host_lstsq": ([_ip, _ip, _vp, _vp, _vp, _vp], _ip),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def header_symbols():
+    """Function names declared in include/dlz.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:int|const char \*)\s*(dlz_\w+)\s*\(", txt, re.M)))
+
+
+def strerror(code):
+    return lib.dlz_strerror(code).decode()
+
+
+def last_error():
+    return lib.dlz_last_error().decode()
+
+
+def _check(rc, allow=()):
+    if rc != OK and rc not in allow:
+        raise DlzError(rc, last_error() or strerror(rc))
+    return rc
+
+
+def _ptr(a):
+    """Data pointer of a contiguous torch tensor or numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr()
+
+
+def _empty_like(a, dtype=None):
+    if isinstance(a, np.ndarray):
+        return np.empty(a.shape, dtype=dtype or a.dtype)
+    import torch
+    return torch.empty(a.shape, dtype=dtype or a.dtype, device=a.device)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def params_default(**overrides):
+    p = Params()
+    _check(lib.dlz_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Operator:
+    """Handle of a dlz_op_t (dlz_create_operator / dlz_destroy_operator)."""
+
+    def __init__(self, handle, dims, kappa, bc_t):
+        self.handle = handle
+        self.dims = tuple(dims)
+        self.kappa = kappa
+        self.bc_t = bc_t
+
+    @property
+    def volume(self):
+        v = ctypes.c_longlong()
+        _check(lib.dlz_op_volume(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.dlz_destroy_operator(self.handle)
+            self.handle = None
+
+
+class Deflation:
+    """Handle of a dlz_defl_t (the k eigenvectors passed to D-CG / D-MinRes)."""
+
+    def __init__(self, handle, op):
+        self.handle = handle
+        self.op = op            # keeps the operator alive
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.dlz_defl_destroy(self.handle)
+            self.handle = None
+
+
+def create_operator(dims, gauge, kappa, bc_t=1, stream=None):
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    h = _vp()
+    _check(lib.dlz_create_operator(d, _ptr(gauge), float(kappa), int(bc_t),
+                                   _stream_handle(stream), ctypes.byref(h)))
+    return Operator(h, dims, kappa, bc_t)
+
+
+def apply(op, which, x, out=None, dtype=None):
+    """out = A x for A in {D, DDAG, Q, DDAGD}; x is [nrhs?, V, 4, 3]."""
+    if dtype is None:
+        dtype = F32 if str(x.dtype).endswith("complex64") else F64
+    if out is None:
+        out = _empty_like(x)
+    V = op.volume
+    nrhs = int(np.prod(x.shape)) // (12 * V) if np.prod(x.shape) else 0
+    _check(lib.dlz_apply(op.handle, int(which), _ptr(x), _ptr(out), int(dtype), nrhs))
+    return out
+
+
+def _dr(fn, op, b, params, x, deflate):
+    p = params if params is not None else params_default()
+    if x is None:
+        x = _empty_like(b)
+    st = Stats()
+    h = _vp()
+    rc = _check(fn(op.handle, _ptr(b), _ptr(x), ctypes.byref(p),
+                   ctypes.byref(h) if deflate else None, ctypes.byref(st)),
+                allow=(ERR_NOT_CONVERGED,))
+    defl = Deflation(h, op) if (deflate and h.value) else None
+    return x, defl, st
+
+
+def landr(op, b, params=None, x=None, deflate=True):
+    """Lan-DR(m,k) on D^dagger D for D x = b: returns (x, Deflation, Stats)."""
+    return _dr(lib.dlz_landr, op, b, params, x, deflate)
+
+
+def minresdr(op, b, params=None, x=None, deflate=True):
+    """MinRes-DR(m,k) on gamma5 D for D x = b: returns (x, Deflation, Stats)."""
+    return _dr(lib.dlz_minresdr, op, b, params, x, deflate)
+
+
+def _dsolve(fn, op, defl, B, params, X):
+    p = params if params is not None else params_default()
+    if X is None:
+        X = _empty_like(B)
+    V = op.volume
+    nrhs = int(np.prod(B.shape)) // (12 * V)
+    st = (Stats * max(nrhs, 1))()
+    _check(fn(op.handle, defl.handle if defl is not None else None, _ptr(B), _ptr(X), nrhs,
+              ctypes.byref(p), st), allow=(ERR_NOT_CONVERGED,))
+    return X, [st[i] for i in range(nrhs)]
+
+
+def dcg(op, defl, B, params=None, X=None):
+    """D-CG (Galerkin projection over defl, then CG on D^dagger D); returns (X, [Stats])."""
+    return _dsolve(lib.dlz_dcg, op, defl, B, params, X)
+
+
+def dminres(op, defl, B, params=None, X=None):
+    """D-MinRes (Galerkin projection over defl, then MinRes on gamma5 D); returns (X, [Stats])."""
+    return _dsolve(lib.dlz_dminres, op, defl, B, params, X)
+
+
+def defl_count(defl):
+    k, w = ctypes.c_int(), ctypes.c_int()
+    _check(lib.dlz_defl_count(defl.handle, ctypes.byref(k), ctypes.byref(w)))
+    return k.value, w.value
+
+
+def defl_get(defl, i, vec_out=None):
+    """(value, residual) of Rayleigh-Ritz pair i; fills vec_out ([V,4,3]) if given."""
+    v, r = ctypes.c_double(), ctypes.c_double()
+    _check(lib.dlz_defl_get(defl.handle, int(i), _ptr(vec_out), ctypes.byref(v), ctypes.byref(r)))
+    return v.value, r.value
+
+
+def defl_save(defl, path):
+    _check(lib.dlz_defl_save(defl.handle, str(path).encode()))
+
+
+def defl_load(op, path):
+    h = _vp()
+    _check(lib.dlz_defl_load(op.handle, str(path).encode(), ctypes.byref(h)))
+    return Deflation(h, op)
+
+
+def host_symeig(A):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.empty(n)
+    Z = np.empty((n, n))
+    _check(lib.dlz_host_symeig(n, A.ctypes.data, w.ctypes.data, Z.ctypes.data))
+    return w, Z
+
+
+def host_lstsq(T, c):
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    rows, cols = T.shape
+    y = np.empty(cols)
+    q = np.empty(rows)
+    _check(lib.dlz_host_lstsq(rows, cols, T.ctypes.data, c.ctypes.data, y.ctypes.data,
+                              q.ctypes.data if rows == cols + 1 else None))
+    return y, (q if rows == cols + 1 else None)

@@ -34,11 +34,12 @@ def main(argv):
             kap, sig = okappa.kappa_dense(U, dims)
             how = "dense LAPACK eigvalsh of D^dagger D; scan from 0 by 0.005, Illinois refine"
         else:
+            start = float(os.environ.get("KAPPA_START", "0.262"))
             kap, sig = okappa.kappa_iterative(
-                U, dims, start=0.255, log=lambda s: print(s, flush=True))
-            how = ("MinRes-DR(100,20) harmonic Ritz pair nearest zero of gamma5 D; "
-                   "steps of 0.005 from 0.255 to bracket, Illinois refine to 1e-4, "
-                   "re-verified from a fresh start vector")
+                U, dims, start=start, log=lambda s: print(s, flush=True))
+            how = ("MinRes-DR(100,20) harmonic Ritz pair nearest zero of gamma5 D "
+                   f"(residual 1e-5); steps of 0.003 from {start} to bracket, Illinois "
+                   "refine to 1e-3, re-verified from a fresh start vector")
         key = f"{lat}_s{seed}"
         table[key] = dict(kappa=kap, sigma_min=sig, method=how,
                           seconds=round(time.time() - t0, 1), host=platform.machine())

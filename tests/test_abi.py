@@ -1,0 +1,86 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and its host-side helpers (small dense solvers of the
+restart, argument validation, error names) behave."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from tests._lib import dlz
+
+
+def test_library_exports_every_declared_symbol():
+    m = dlz()
+    syms = m.header_symbols()
+    assert len(syms) >= 18
+    for s in syms:
+        assert hasattr(m.lib, s), s
+
+
+def test_params_defaults():
+    m = dlz()
+    p = m.params_default()
+    assert (p.m, p.k, p.tol, p.oversolve, p.reorth_period, p.precision) == (40, 10, 1e-10, 1.0, 10, m.F64)
+
+
+def test_error_names():
+    m = dlz()
+    for code, name in [(0, "DLZ_OK"), (-1, "DLZ_ERR_BADARG"), (-2, "DLZ_ERR_BAD_GAUGE"),
+                       (-4, "DLZ_ERR_NOT_CONVERGED"), (-9, "DLZ_ERR_IO")]:
+        assert m.strerror(code) == name
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 40, 121])
+def test_host_symeig_matches_lapack(n):
+    m = dlz()
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    w, Z = m.host_symeig(A)
+    assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-13 * max(1, np.abs(w).max())
+    assert np.abs(A @ Z - Z * w).max() < 1e-12 * max(1, np.abs(w).max())
+    assert np.abs(Z.T @ Z - np.eye(n)).max() < 1e-13
+
+
+def test_host_symeig_arrowhead_with_clusters():
+    """The Lan-DR restart matrix: diagonal block of Ritz values, one coupling row."""
+    m = dlz()
+    k, n = 10, 40
+    rng = np.random.default_rng(3)
+    T = np.zeros((n, n))
+    T[:k, :k] = np.diag(np.sort(rng.uniform(1e-6, 1e-3, k)))
+    T[k, :k] = T[:k, k] = rng.standard_normal(k) * 1e-9
+    for j in range(k, n):
+        T[j, j] = rng.uniform(0.5, 4)
+        if j + 1 < n:
+            T[j, j + 1] = T[j + 1, j] = rng.uniform(0.1, 1)
+    w, Z = m.host_symeig(T)
+    assert np.abs(w - np.linalg.eigvalsh(T)).max() < 1e-14 * 4
+
+
+@pytest.mark.parametrize("rows,cols", [(5, 4), (41, 40), (101, 100), (30, 12)])
+def test_host_lstsq(rows, cols):
+    m = dlz()
+    rng = np.random.default_rng(rows)
+    T = rng.standard_normal((rows, cols))
+    c = rng.standard_normal(rows)
+    y, q = m.host_lstsq(T, c)
+    assert np.abs(y - np.linalg.lstsq(T, c, rcond=None)[0]).max() < 1e-11
+    if q is not None:
+        assert abs(np.linalg.norm(q) - 1) < 1e-14 and np.abs(T.T @ q).max() < 1e-13
+
+
+def test_argument_validation_without_gpu():
+    m = dlz()
+    out = ctypes.c_void_p()
+    bad = (ctypes.c_int * 4)(4, 0, 4, 4)
+    g = np.zeros(16, dtype=np.complex128)
+    assert m.lib.dlz_create_operator(bad, g.ctypes.data, 0.1, 1, None, ctypes.byref(out)) == m.ERR_BADARG
+    dims = (ctypes.c_int * 4)(4, 4, 4, 4)
+    assert m.lib.dlz_create_operator(dims, g.ctypes.data, 0.1, 2, None, ctypes.byref(out)) == m.ERR_BADARG
+    assert m.lib.dlz_create_operator(dims, None, 0.1, 1, None, ctypes.byref(out)) == m.ERR_BADARG
+    assert m.lib.dlz_create_operator(dims, g.ctypes.data, float("nan"), 1, None, ctypes.byref(out)) == m.ERR_BADARG
+    assert m.lib.dlz_destroy_operator(None) == m.ERR_BADARG
+    assert m.lib.dlz_apply(None, 0, None, None, 0, 1) == m.ERR_BADARG
+    assert m.lib.dlz_defl_count(None, None, None) == m.ERR_BADARG
+    assert "null" in m.last_error()

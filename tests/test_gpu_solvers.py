@@ -1,0 +1,184 @@
+"""GPU parity of Lan-DR, MinRes-DR, D-CG and D-MinRes against the FP64 oracle,
+through the C ABI (arXiv:0901.3163, Sec. 1-2).
+
+Tolerances: every solve reaches a true relative residual ||b - D x||/||b|| <=
+1e-10 verified in FP64; two such solutions differ by at most
+2e-10 ||b|| / sigma_min(D); Ritz values of converged pairs agree to 1e-8
+relative; the first restart cycle (no restart yet, same FP64 algorithm) agrees
+element by element to round-off."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import krylov as K
+from oracle import wilson
+from tests._lib import dlz
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+DIMS = (4, 4, 4, 4)
+KAPPA = 0.2       # quick case; the kappa-rule workload is tested below
+
+
+@pytest.fixture(scope="module")
+def m():
+    return dlz()
+
+
+@pytest.fixture(scope="module")
+def case(m):
+    U = synth.su3_links(DIMS, 1)
+    op = m.create_operator(DIMS, torch.from_numpy(U).cuda(), KAPPA)
+    b = synth.gaussian_spinor(DIMS, 0)
+    return U, op, b
+
+
+def _g5(x):
+    return wilson.apply_gamma5(x.reshape(-1, 4, 3)).reshape(-1)
+
+
+def _ops(U, kappa):
+    return (wilson.operator(U, kappa, DIMS, "Q"), wilson.operator(U, kappa, DIMS, "D"),
+            wilson.operator(U, kappa, DIMS, "Ddag"), wilson.operator(U, kappa, DIMS, "DdagD"))
+
+
+def _params(m, **kw):
+    base = dict(m=40, k=10, tol=1e-10, oversolve=2.0, max_cycles=400)
+    base.update(kw)
+    return m.params_default(**base)
+
+
+def test_first_cycle_matches_oracle_elementwise(m, case):
+    U, op, b = case
+    Aq, D, Dd, Ad = _ops(U, KAPPA)
+    xg, _, st = m.minresdr(op, torch.from_numpy(b).cuda(), _params(m, max_cycles=1), deflate=False)
+    xo = K.minresdr(Aq, _g5(b), m=40, k=10, tol=1e-10, max_cycles=1).x
+    assert np.abs(xg.cpu().numpy().reshape(-1) - xo).max() <= 1e-11 * np.abs(xo).max()
+    xg, _, st = m.landr(op, torch.from_numpy(b).cuda(), _params(m, max_cycles=1), deflate=False)
+    xo = K.landr(Ad, Dd(b.reshape(-1)), m=40, k=10, tol=1e-10, max_cycles=1).x
+    assert np.abs(xg.cpu().numpy().reshape(-1) - xo).max() <= 1e-11 * np.abs(xo).max()
+
+
+def _compare_dr(m, defl, st, r_or, xg, xo, bnorm, sigma):
+    assert st.converged == 1 and st.true_residual <= 1e-10
+    assert np.linalg.norm(xg - xo) <= 2.5e-10 * bnorm / sigma
+    k, _ = m.defl_count(defl)
+    vals = np.array([m.defl_get(defl, i) for i in range(k)])
+    ov = np.sort(r_or.ritz_values)
+    order = np.argsort(vals[:, 0])
+    gv, gr = vals[order, 0], vals[order, 1]
+    orr = r_or.ritz_residuals[np.argsort(r_or.ritz_values)]
+    ok = (gr <= 1e-7) & (orr <= 1e-7)
+    assert ok.sum() >= 1
+    assert np.all(np.abs(gv[ok] - ov[ok]) <= 1e-8 * np.abs(ov[ok]))
+    return gv
+
+
+def test_minresdr_and_dminres_match_oracle(m, case):
+    U, op, b = case
+    Aq, D, Dd, Ad = _ops(U, KAPPA)
+    bnorm = np.linalg.norm(b)
+    xg, defl, st = m.minresdr(op, torch.from_numpy(b).cuda(), _params(m))
+    ro = K.minresdr(Aq, _g5(b), m=40, k=10, tol=1e-10, oversolve=2.0, max_cycles=400)
+    sigma = np.abs(ro.ritz_values).min()
+    _compare_dr(m, defl, st, ro, xg.cpu().numpy().reshape(-1), ro.x, bnorm, sigma)
+    # D-MinRes on four more right-hand sides, and plain MinRes for comparison
+    B = synth.gaussian_spinors(DIMS, [1, 2, 3, 4])
+    Xg, sts = m.dminres(op, defl, torch.from_numpy(B).cuda(), _params(m))
+    X0, sts0 = m.dminres(op, None, torch.from_numpy(B).cuda(), _params(m))
+    H = K.deflation_space(Aq, ro.Vk)
+    for i in range(4):
+        xo, io = K.dminres(Aq, _g5(B[i]), ro.Vk, H)
+        assert sts[i].converged == 1 and sts[i].true_residual <= 1e-10
+        assert sts0[i].converged == 1
+        nb = np.linalg.norm(B[i])
+        assert np.linalg.norm(Xg[i].cpu().numpy().reshape(-1) - xo) <= 2.5e-10 * nb / sigma
+        assert sts[i].iterations < sts0[i].iterations
+        assert abs(sts[i].iterations - io.iterations) <= 0.1 * io.iterations + 16
+
+
+def test_landr_and_dcg_match_oracle(m, case):
+    U, op, b = case
+    Aq, D, Dd, Ad = _ops(U, KAPPA)
+    bf = b.reshape(-1)
+    bnorm = np.linalg.norm(b)
+    xg, defl, st = m.landr(op, torch.from_numpy(b).cuda(), _params(m))
+    ro = K.landr(Ad, Dd(bf), m=40, k=10, tol=1e-10, oversolve=2.0, max_cycles=400,
+                 residual=lambda xx: np.linalg.norm(bf - D(xx)) / bnorm)
+    sigma = np.sqrt(np.min(ro.ritz_values))
+    _compare_dr(m, defl, st, ro, xg.cpu().numpy().reshape(-1), ro.x, bnorm, sigma)
+    B = synth.gaussian_spinors(DIMS, [1, 2])
+    Xg, sts = m.dcg(op, defl, torch.from_numpy(B).cuda(), _params(m))
+    _, sts0 = m.dcg(op, None, torch.from_numpy(B).cuda(), _params(m))
+    H = K.deflation_space(Ad, ro.Vk)
+    for i in range(2):
+        xo, io = K.dcg(D, Dd, B[i].reshape(-1), ro.Vk, H)
+        assert sts[i].converged == 1 and sts[i].true_residual <= 1e-10
+        assert np.linalg.norm(Xg[i].cpu().numpy().reshape(-1) - xo) <= 2.5e-10 * np.linalg.norm(B[i]) / sigma
+        assert sts[i].iterations < sts0[i].iterations
+
+
+def test_kappa_rule_workload_4x4x4x4(m):
+    """The 4^4 workload at the kappa of min|eig(gamma5 D)| = 1e-3, MinRes-DR(40,10)."""
+    w = synth.WORKLOADS["wilson_4x4x4x4"]
+    dims = w["dims"]
+    U = synth.su3_links(dims, w["gauge_seed"])
+    kappa = synth.kappa_for(dims, w["gauge_seed"])
+    op = m.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
+    b = synth.gaussian_spinor(dims, w["first_rhs_seed"])
+    p = m.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=2000)
+    xg, defl, st = m.minresdr(op, torch.from_numpy(b).cuda(), p)
+    assert st.converged == 1 and st.true_residual <= 1e-10
+    B = synth.gaussian_spinors(dims, w["rhs_seeds"])
+    Xg, sts = m.dminres(op, defl, torch.from_numpy(B).cuda(), p)
+    Q = wilson.operator(U, kappa, dims, "Q")
+    D = wilson.operator(U, kappa, dims, "D")
+    for i in range(len(B)):
+        assert sts[i].converged == 1 and sts[i].true_residual <= 1e-10
+        xi = Xg[i].cpu().numpy().reshape(-1)
+        # the oracle's own residual of the GPU solution, and agreement with the oracle solve
+        assert np.linalg.norm(B[i].reshape(-1) - D(xi)) <= 1.01e-10 * np.linalg.norm(B[i])
+    xo, io = K.minres(Q, _g5(B[0]), tol=1e-10, maxiter=20000)
+    x0 = Xg[0].cpu().numpy().reshape(-1)
+    assert np.linalg.norm(x0 - xo) <= 2.5e-10 * np.linalg.norm(B[0]) / 1e-3
+    assert sts[0].iterations < io.iterations
+
+
+def test_error_paths(m, case):
+    U, op, b = case
+    bad = b.copy()
+    bad[3, 1, 2] = np.nan
+    with pytest.raises(m.DlzError) as e:
+        m.dminres(op, None, torch.from_numpy(bad[None]).cuda(), _params(m))
+    assert e.value.code == m.ERR_NONFINITE
+    X, sts = m.dminres(op, None, torch.from_numpy(b[None]).cuda(), _params(m, max_iter=5, check_every=1))
+    assert sts[0].converged == 0 and np.isfinite(X.cpu().numpy()).all()
+    Z, stz = m.dminres(op, None, torch.zeros((1,) + b.shape, dtype=torch.complex128, device="cuda"), _params(m))
+    assert stz[0].converged == 1 and float(Z.abs().max()) == 0.0
+    with pytest.raises(m.DlzError) as e:
+        m.minresdr(op, torch.from_numpy(b).cuda(), _params(m, k=40))
+    assert e.value.code == m.ERR_BADARG
+
+
+def test_deflation_save_load_roundtrip(m, case, tmp_path):
+    U, op, b = case
+    _, defl, _ = m.minresdr(op, torch.from_numpy(b).cuda(), _params(m))
+    path = tmp_path / "defl.bin"
+    m.defl_save(defl, path)
+    d2 = m.defl_load(op, path)
+    assert m.defl_count(d2) == m.defl_count(defl)
+    for i in range(m.defl_count(defl)[0]):
+        v1, r1 = m.defl_get(defl, i)
+        v2, r2 = m.defl_get(d2, i)
+        assert abs(v1 - v2) <= 1e-12 * abs(v1)
+    y = torch.empty(b.shape, dtype=torch.complex128, device="cuda")
+    val, res = m.defl_get(d2, 0, y)
+    Q = wilson.operator(U, KAPPA, DIMS, "Q")
+    yv = y.cpu().numpy().reshape(-1)
+    assert abs(np.linalg.norm(yv) - 1) < 1e-12
+    assert abs(np.linalg.norm(Q(yv) - val * yv) - res) < 1e-10
+    B = synth.gaussian_spinors(DIMS, [7])
+    _, s1 = m.dminres(op, defl, torch.from_numpy(B).cuda(), _params(m))
+    _, s2 = m.dminres(op, d2, torch.from_numpy(B).cuda(), _params(m))
+    assert s1[0].iterations == s2[0].iterations
