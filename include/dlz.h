@@ -63,7 +63,8 @@ extern "C" {
 
 /* Arithmetic of the hot loop. */
 #define DLZ_F64 0   /* plain FP64 everywhere                                     */
-#define DLZ_F32 1   /* FP32 stencil and Krylov vectors, FP64 reliable updates    */
+#define DLZ_F32 1   /* FP32 stencil and Krylov vectors inside an FP64 defect-correction
+                       loop (FP64 x, residual and deflation projection)           */
 
 typedef struct dlz_op_s *dlz_op_t;
 typedef struct dlz_defl_s *dlz_defl_t;
@@ -82,8 +83,9 @@ typedef struct {
                             Lanczos steps, at the restart vector and the first new step
                             (Sec. 2: periodic, period not given); 10                      */
     int precision;       /* DLZ_F64 or DLZ_F32 (hot loop of D-CG / D-MinRes); DLZ_F64     */
-    double reliable_delta; /* DLZ_F32: FP64 true-residual update when the iterated
-                              residual fell by this factor; 0.1                          */
+    double reliable_delta; /* DLZ_F32: each FP32 inner solve reduces the residual by
+                              this factor, then x is updated and the residual recomputed
+                              in FP64 (defect correction); 1e-5                          */
     int check_every;     /* D-CG / D-MinRes: read the residual on the host every this
                             many iterations; 16                                          */
     int profile;         /* 1: time every stencil launch with CUDA events (stats)  ; 0   */
@@ -99,6 +101,8 @@ typedef struct {
     double seconds;         /* wall time of the call                                  */
     double stencil_ms;      /* profile = 1: summed device time of stencil launches     */
     long long stencil_launches; /* profile = 1: number of timed stencil launches       */
+    long long stencil_sites;    /* profile = 1: sites x right-hand sides those launches
+                                   processed (a batched launch counts every RHS)         */
     long long gpu_launches; /* kernels launched by this call                          */
 } dlz_stats;
 

@@ -113,7 +113,12 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5,
     state = {"v": rng.standard_normal(V * 12) + 1j * rng.standard_normal(V * 12)}
 
     def f(kap, res_tol=res_tol):
-        s, y, res, mv = sigma_min_iterative(U, kap, dims, state["v"], res_tol, bc_t=bc_t, log=log)
+        # Far from the target only the sign and a rough size of sigma_min - 1e-3
+        # are needed: stop once the residual is below 5% of that distance.
+        def stop(theta, res):
+            return res <= max(res_tol, 0.05 * abs(abs(theta) - TARGET))
+
+        s, y, res, mv = sigma_min_iterative(U, kap, dims, state["v"], stop, bc_t=bc_t, log=log)
         state["v"] = y + 1e-3 * (rng.standard_normal(V * 12) + 1j * rng.standard_normal(V * 12)) / np.sqrt(V * 12)
         if log:
             log(f"kappa={kap:.10f} sigma_min={s:.10e} res={res:.2e} mvps={mv}")

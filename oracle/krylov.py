@@ -306,7 +306,8 @@ def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
     `residual(x)` gives the relative residual used for the linear test
     (default ||b - A x|| / ||b||, evaluated once per cycle).  `eig_stop`
     turns the routine into an eigensolver: it stops as soon as the lowest
-    Ritz pair has a residual <= eig_stop.
+    Ritz pair has a residual <= eig_stop (or, for a callable,
+    eig_stop(value, residual) is true).
     """
     return _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth,
                residual, oversolve, harmonic=False, eig_stop=eig_stop, progress=progress)
@@ -379,9 +380,10 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             tol_eig_abs = 1e-10 * Anorm_est
         else:
             tol_eig_abs = tol_eig
+        Vs = np.stack(V)            # (m+1) x n: the basis as rows, for the products below
         if not harmonic:
             y = sla.solve(Tm, c[:m], assume_a="sym")
-            x = x + _combine(V, y)
+            x = x + y @ Vs[:m]
             rho = -T[m, m - 1] * y[m - 1]
             theta, G = np.linalg.eigh(Tm)
             order = np.argsort(theta, kind="stable")[:k]
@@ -390,7 +392,7 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             rnorm = abs(rho)
         else:
             y, *_ = np.linalg.lstsq(T, c, rcond=None)
-            x = x + _combine(V, y)
+            x = x + y @ Vs[:m]
             s = c - T @ y
             rnorm = float(np.linalg.norm(s))
             L = np.linalg.cholesky(T.T @ T)
@@ -421,14 +423,16 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             # eigenvalue-only use: stop once the pair nearest zero (harmonic) or the
             # lowest pair (regular) has a residual <= eig_stop, whatever the linear residual
             i0 = int(np.argmin(np.abs(theta_k))) if harmonic else 0
-            if ritz_res[i0] <= eig_stop:
+            done = (eig_stop(theta_k[i0], ritz_res[i0]) if callable(eig_stop)
+                    else ritz_res[i0] <= eig_stop)
+            if done:
                 info.converged = True
         # restart (always performed so that V[:k] is the kept space on exit)
         if not harmonic:
             P = np.zeros((m + 1, k + 1))
             P[:m, :k] = G_k
             P[m, k] = 1.0
-            Vnew = [_combine(V, P[:, i]) for i in range(k + 1)]
+            Vnew = list(P.T @ Vs)
             Tn = np.zeros((m + 1, m))
             Tn[:k, :k] = np.diag(theta_k)
             Tn[k, :k] = T[m, m - 1] * G_k[m - 1, :]
@@ -441,7 +445,7 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             if q @ s < 0:
                 q = -q
             P = _mgs_columns(np.hstack([np.vstack([G_k, np.zeros((1, k))]), q[:, None]]))
-            Vnew = [_combine(V, P[:, i]) for i in range(k + 1)]
+            Vnew = list(P.T @ Vs)
             Tk = P.T @ T @ P[:m, :k]
             Tn = np.zeros((m + 1, m))
             Tn[: k + 1, :k] = Tk
@@ -455,6 +459,7 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             for i in range(k):
                 Vnew[k] = Vnew[k] - _dot(Vnew[i], Vnew[k]) * Vnew[i]
             Vnew[k] = Vnew[k] / _norm(Vnew[k])
+        del Vs
         V, T, c, j0 = Vnew, Tn, cn, k
         if info.converged or last:
             break

@@ -1,5 +1,6 @@
 // C ABI of the dlz library (include/dlz.h): operator objects, host/device
 // staging of user vectors, the solver and deflation-set entry points.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -53,6 +54,7 @@ void Profiler::begin(bool on) {
     used = 0;
     launches = 0;
     stencils = 0;
+    stencil_sites = 0;
 }
 void Profiler::stencil_start(cudaStream_t s) {
     if (!enabled) return;
@@ -192,6 +194,7 @@ int check_params(const dlz_params *p) {
     if (p->max_cycles < 1 || p->max_iter < 1 || p->check_every < 1)
         return fail(DLZ_ERR_BADARG, "max_cycles, max_iter, check_every must be >= 1");
     if (p->precision != DLZ_F64 && p->precision != DLZ_F32) return fail(DLZ_ERR_BADARG, "precision");
+    if (!(p->reliable_delta > 0.0 && p->reliable_delta < 1.0)) return fail(DLZ_ERR_BADARG, "reliable_delta must be in (0, 1)");
     return DLZ_OK;
 }
 
@@ -208,6 +211,7 @@ struct CallStats {
         if (op.prof.enabled) {
             st.stencil_ms = op.prof.stencil_ms();
             st.stencil_launches = op.prof.stencils;
+            st.stencil_sites = op.prof.stencil_sites;
         }
     }
 };
@@ -230,7 +234,7 @@ int dlz_params_default(dlz_params *p) {
     p->max_iter = 100000;
     p->reorth_period = 10;
     p->precision = DLZ_F64;
-    p->reliable_delta = 0.1;
+    p->reliable_delta = 1e-5;
     p->check_every = 16;
     p->profile = 0;
     return DLZ_OK;
@@ -414,22 +418,59 @@ static int dsolve_entry(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nr
             return fail(DLZ_ERR_BADARG, minres ? "D-MinRes needs a MinRes-DR (Q) deflation set"
                                                : "D-CG needs a Lan-DR (D^dag D) deflation set");
     }
-    if (p->precision != DLZ_F64) return fail(DLZ_ERR_BADARG, "only DLZ_F64 is available for D-CG / D-MinRes");
     const long n = 12L * op.g.V;
     Staged sb, sx;
     DLZ_TRY(sb.in(op, B, (size_t)n * nrhs * sizeof(double2)));
     DLZ_TRY(sx.out(op, X, (size_t)n * nrhs * sizeof(double2)));
+    int worst = DLZ_OK;
+    if (p->precision == DLZ_F32 && minres) {
+        // batched mixed-precision D-MinRes, up to 16 right-hand sides per pass
+        const int chunk = std::min(nrhs, 16);
+        DevBuf bi, xi;
+        DLZ_TRY(bi.alloc((size_t)chunk * n * sizeof(double2)));
+        DLZ_TRY(xi.alloc((size_t)chunk * n * sizeof(double2)));
+        std::vector<dlz_stats> sts(chunk);
+        for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+            const int nb = std::min(chunk, nrhs - r0);
+            CallStats cs(op, nullptr, p->profile != 0);
+            for (int q = 0; q < nb; ++q)
+                DLZ_TRY(pack64(op, bi.as<double2>() + (size_t)q * n, (const double2 *)sb.dev + (size_t)(r0 + q) * n));
+            const int rc = dsolve_mixed_batch(op, d, true, bi.as<double2>(), xi.as<double2>(), nb, *p, sts.data());
+            if (rc != DLZ_OK && rc != DLZ_ERR_NOT_CONVERGED) return rc;
+            if (rc != DLZ_OK) worst = rc;
+            for (int q = 0; q < nb; ++q)
+                DLZ_TRY(unpack64(op, (double2 *)sx.dev + (size_t)(r0 + q) * n, xi.as<double2>() + (size_t)q * n));
+            DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+            dlz_stats shared;
+            std::memset(&shared, 0, sizeof(shared));
+            cs.finish(shared);
+            for (int q = 0; q < nb; ++q) {
+                sts[q].seconds = shared.seconds / nb;
+                sts[q].gpu_launches = shared.gpu_launches / nb;
+                sts[q].stencil_ms = shared.stencil_ms / nb;
+                sts[q].stencil_launches = shared.stencil_launches / nb;
+                sts[q].stencil_sites = shared.stencil_sites / nb;
+                if (stats) stats[r0 + q] = sts[q];
+            }
+        }
+        DLZ_TRY(sx.flush(op));
+        if (worst != DLZ_OK) set_error(worst, "max_iter reached for at least one right-hand side");
+        return worst;
+    }
     DevBuf bi, xi;
     DLZ_TRY(bi.alloc(n * sizeof(double2)));
     DLZ_TRY(xi.alloc(n * sizeof(double2)));
-    int worst = DLZ_OK;
     for (int r = 0; r < nrhs; ++r) {
         dlz_stats st;
         std::memset(&st, 0, sizeof(st));
         CallStats cs(op, nullptr, p->profile != 0);
         DLZ_TRY(pack64(op, bi.as<double2>(), (const double2 *)sb.dev + (size_t)r * n));
-        const int rc = minres ? dminres64(op, d, bi.as<double2>(), xi.as<double2>(), *p, st)
-                              : dcg64(op, d, bi.as<double2>(), xi.as<double2>(), *p, st);
+        int rc;
+        if (p->precision == DLZ_F32)
+            rc = dsolve_mixed(op, d, minres, bi.as<double2>(), xi.as<double2>(), *p, st);
+        else
+            rc = minres ? dminres64(op, d, bi.as<double2>(), xi.as<double2>(), *p, st)
+                        : dcg64(op, d, bi.as<double2>(), xi.as<double2>(), *p, st);
         if (rc != DLZ_OK && rc != DLZ_ERR_NOT_CONVERGED) return rc;
         if (rc != DLZ_OK) worst = rc;
         DLZ_TRY(unpack64(op, (double2 *)sx.dev + (size_t)r * n, xi.as<double2>()));

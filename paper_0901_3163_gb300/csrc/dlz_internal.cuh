@@ -124,6 +124,7 @@ struct Profiler {
     size_t used = 0;
     long long launches = 0;      // all kernels
     long long stencils = 0;      // stencil kernels
+    long long stencil_sites = 0; // lattice sites (x right-hand sides) they processed
     void begin(bool on);
     void stencil_start(cudaStream_t s);
     void stencil_stop(cudaStream_t s);
@@ -148,6 +149,9 @@ struct Op {
 // which: DLZ_D (0,0), DLZ_DDAG (1,1), DLZ_Q (0,1).
 int wilson64(Op &op, double2 *out, const double2 *in, int which);
 int wilson32(Op &op, float4 *out, const float4 *in, int which);
+// nrhs spinors stored one after another (FP32: 6V float4 each, FP64: 12V double2 each)
+int wilson32_batch(Op &op, float4 *out, const float4 *in, int which, int nrhs);
+int wilson64_batch(Op &op, double2 *out, const double2 *in, int which, int nrhs);
 // A = D, D^dag, Q or D^dag D on internal FP64 vectors (tmp used for D^dag D).
 int apply64(Op &op, double2 *out, const double2 *in, int which, double2 *tmp);
 int apply32(Op &op, float4 *out, const float4 *in, int which, float4 *tmp);

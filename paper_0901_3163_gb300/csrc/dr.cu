@@ -1,0 +1,436 @@
+// Lan-DR(m,k) and MinRes-DR(m,k) (arXiv:0901.3163, Sec. 1-2), one code path
+// for the FP64 basis (plain form) and the FP32 basis (mixed form).
+//
+// Per cycle:
+//   Lanczos steps j0..m-1 on the device: w = A v_j, the coupling of the
+//   restart vector to the kept vectors (first step only), three-term
+//   subtraction fused with the alpha_j reduction, alpha subtraction fused with
+//   the beta_j reduction, periodic re-orthogonalisation against the kept
+//   vectors, v_{j+1} = w / beta_j -- all scalars stay on the device;
+//   the small projected problem on the host (FP64): Galerkin solve + regular
+//   Ritz vectors (Lan-DR) or least squares + harmonic Ritz vectors
+//   (MinRes-DR), and the restart coefficients P;
+//   x += V_m y (accumulated in FP64), the true residual ||b - D x|| with the
+//   FP64 stencil, and the restart V_{k+1} <- V_{m+1} P.
+// The mixed form keeps the basis, the stencil and the element updates in
+// FP32 and stops the DR phase once its residual stagnates at the FP32 level
+// or meets tol; the caller then finishes the solve by FP64 defect correction
+// over the deflation set it produced.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "dlz_internal.cuh"
+#include "krylov_util.cuh"
+#include "prec.cuh"
+#include "reduce.cuh"
+#include "small_dense.h"
+#include "solvers.h"
+
+namespace dlz {
+
+namespace {
+
+struct RestartPlan {
+    std::vector<double> y;       // m     : x += V_m y
+    std::vector<double> P;       // (m+1) x (k+1): V_{k+1} <- V_{m+1} P
+    std::vector<double> Tn, cn;  // new Tbar ((m+1) x m, rows/cols < k+1 filled) and c
+    std::vector<double> theta, res;   // kept (harmonic) Ritz values and residuals
+};
+
+// The small FP64 problem of one cycle (host).  T: (m+1) x m row-major Tbar_m.
+int plan_restart(bool harmonic, int m, int k, const std::vector<double> &T, const std::vector<double> &c,
+                 double &Anorm, RestartPlan &o) {
+    std::vector<double> Tm((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) Tm[(size_t)i * m + j] = T[(size_t)i * m + j];
+    std::vector<double> ev(m), G((size_t)m * m);
+    if (!sym_eig(m, Tm.data(), ev.data(), G.data())) return fail(DLZ_ERR_NONFINITE, "eig(T_m) failed");
+    Anorm = std::max(Anorm, std::max(std::fabs(ev[0]), std::fabs(ev[m - 1])));
+    o.y.assign(m, 0.0);
+    o.P.assign((size_t)(m + 1) * (k + 1), 0.0);
+    o.Tn.assign((size_t)(m + 1) * m, 0.0);
+    o.cn.assign(m + 1, 0.0);
+    o.theta.assign(k, 0.0);
+    o.res.assign(k, 0.0);
+    const double bm = T[(size_t)m * m + m - 1];
+    if (!harmonic) {
+        // Galerkin T_m y = c; residual rho v_{m+1}, rho = -beta_m y_m
+        std::vector<double> LU = Tm;
+        std::vector<int> piv(m);
+        std::copy(c.begin(), c.begin() + m, o.y.begin());
+        if (!lu_factor(m, LU.data(), piv.data())) return fail(DLZ_ERR_BREAKDOWN, "T_m singular");
+        lu_solve(m, LU.data(), piv.data(), o.y.data());
+        const double rho = -bm * o.y[m - 1];
+        for (int l = 0; l < k; ++l) {           // k algebraically smallest Ritz values
+            o.theta[l] = ev[l];
+            for (int i = 0; i < m; ++i) o.P[(size_t)i * (k + 1) + l] = G[(size_t)i * m + l];
+            o.res[l] = std::fabs(bm * G[(size_t)(m - 1) * m + l]);
+        }
+        o.P[(size_t)m * (k + 1) + k] = 1.0;
+        for (int l = 0; l < k; ++l) o.Tn[(size_t)l * m + l] = o.theta[l];
+        for (int l = 0; l < k; ++l) o.Tn[(size_t)k * m + l] = bm * G[(size_t)(m - 1) * m + l];
+        o.cn[k] = rho;
+        return DLZ_OK;
+    }
+    // least squares min ||c - Tbar y||; s = c - Tbar y; q spans range(Tbar)^perp
+    std::vector<double> q(m + 1), s(m + 1);
+    if (!lstsq(m + 1, m, T.data(), c.data(), o.y.data(), q.data())) return fail(DLZ_ERR_BREAKDOWN, "least squares failed");
+    for (int i = 0; i <= m; ++i) {
+        double t = c[i];
+        for (int j = 0; j < m; ++j) t -= T[(size_t)i * m + j] * o.y[j];
+        s[i] = t;
+    }
+    // harmonic Ritz pairs: T_m g = mu (Tbar^T Tbar) g, theta = 1/mu, via the Cholesky
+    // factor L of Tbar^T Tbar: C = L^-1 T_m L^-T, g = L^-T z
+    std::vector<double> M((size_t)m * m, 0.0), L((size_t)m * m), X((size_t)m * m), C((size_t)m * m), col(m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            double t = 0;
+            for (int r = 0; r <= m; ++r) t += T[(size_t)r * m + i] * T[(size_t)r * m + j];
+            M[(size_t)i * m + j] = t;
+        }
+    if (!cholesky(m, M.data(), L.data())) return fail(DLZ_ERR_BREAKDOWN, "Tbar^T Tbar not positive definite");
+    for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < m; ++i) col[i] = Tm[(size_t)i * m + j];
+        lower_solve(m, L.data(), col.data());
+        for (int i = 0; i < m; ++i) X[(size_t)i * m + j] = col[i];
+    }
+    for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < m; ++i) col[i] = X[(size_t)j * m + i];
+        lower_solve(m, L.data(), col.data());
+        for (int i = 0; i < m; ++i) C[(size_t)i * m + j] = col[i];
+    }
+    std::vector<double> mu(m), Zc((size_t)m * m);
+    if (!sym_eig(m, C.data(), mu.data(), Zc.data())) return fail(DLZ_ERR_NONFINITE, "harmonic eigensolve failed");
+    std::vector<int> idx(m);
+    for (int i = 0; i < m; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return std::fabs(mu[a]) > std::fabs(mu[b]); });
+    std::vector<double> Gk((size_t)m * k);
+    for (int l = 0; l < k; ++l) {
+        for (int i = 0; i < m; ++i) col[i] = Zc[(size_t)i * m + idx[l]];
+        upper_t_solve(m, L.data(), col.data());
+        double nr = 0;
+        for (int i = 0; i < m; ++i) nr += col[i] * col[i];
+        nr = std::sqrt(nr);
+        for (int i = 0; i < m; ++i) Gk[(size_t)i * k + l] = col[i] / nr;
+        o.theta[l] = 1.0 / mu[idx[l]];
+        double r2 = 0;
+        for (int r = 0; r <= m; ++r) {
+            double t = 0;
+            for (int j = 0; j < m; ++j) t += T[(size_t)r * m + j] * Gk[(size_t)j * k + l];
+            if (r < m) t -= o.theta[l] * Gk[(size_t)r * k + l];
+            r2 += t * t;
+        }
+        o.res[l] = std::sqrt(r2);
+    }
+    double qs = 0;
+    for (int i = 0; i <= m; ++i) qs += q[i] * s[i];
+    if (qs < 0)
+        for (double &t : q) t = -t;
+    for (int i = 0; i < m; ++i)
+        for (int l = 0; l < k; ++l) o.P[(size_t)i * (k + 1) + l] = Gk[(size_t)i * k + l];
+    for (int i = 0; i <= m; ++i) o.P[(size_t)i * (k + 1) + k] = q[i];
+    if (!mgs_columns(m + 1, k + 1, o.P.data())) return fail(DLZ_ERR_BREAKDOWN, "restart basis lost rank");
+    // Tbar_k = P^T Tbar P[:m, :k] (k x k block symmetric, not diagonal); c <- P^T s
+    std::vector<double> TP((size_t)(m + 1) * k, 0.0);
+    for (int r = 0; r <= m; ++r)
+        for (int l = 0; l < k; ++l) {
+            double t = 0;
+            for (int j = 0; j < m; ++j) t += T[(size_t)r * m + j] * o.P[(size_t)j * (k + 1) + l];
+            TP[(size_t)r * k + l] = t;
+        }
+    for (int a = 0; a <= k; ++a)
+        for (int l = 0; l < k; ++l) {
+            double t = 0;
+            for (int r = 0; r <= m; ++r) t += o.P[(size_t)r * (k + 1) + a] * TP[(size_t)r * k + l];
+            o.Tn[(size_t)a * m + l] = t;
+        }
+    for (int a = 0; a < k; ++a)
+        for (int l = 0; l < a; ++l) {
+            const double sym = 0.5 * (o.Tn[(size_t)a * m + l] + o.Tn[(size_t)l * m + a]);
+            o.Tn[(size_t)a * m + l] = o.Tn[(size_t)l * m + a] = sym;
+        }
+    for (int a = 0; a <= k; ++a) {
+        double t = 0;
+        for (int r = 0; r <= m; ++r) t += o.P[(size_t)r * (k + 1) + a] * s[r];
+        o.cn[a] = t;
+    }
+    return DLZ_OK;
+}
+
+// x64 += sum_j y_j V_j for an FP32 basis (accumulated in FP64)
+__global__ void __launch_bounds__(128)
+k_accum_x32(double2 *__restrict__ x, const float4 *__restrict__ Vb, long ld, int nin,
+            const double *__restrict__ y, int V) {
+    extern __shared__ double ysm[];
+    for (int t = threadIdx.x; t < nin; t += blockDim.x) ysm[t] = y[t];
+    __syncthreads();
+    const long n = 6L * V;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int j = 0; j < nin; ++j) {
+            const float4 v = Vb[(size_t)j * ld + i];
+            const double c = ysm[j];
+            a0 = fma(c, (double)v.x, a0); a1 = fma(c, (double)v.y, a1);
+            a2 = fma(c, (double)v.z, a2); a3 = fma(c, (double)v.w, a3);
+        }
+        const int cpl = (int)(i / V), s = (int)(i % V);
+        double2 &p = x[(size_t)(2 * cpl) * V + s];
+        double2 &q = x[(size_t)(2 * cpl + 1) * V + s];
+        p.x += a0; p.y += a1; q.x += a2; q.y += a3;
+    }
+}
+
+template <class P> int accum_x(Op &op, double2 *x, const typename P::E *Vb, long ld, int nin, const double *dev_y);
+template <> int accum_x<P64>(Op &op, double2 *x, const double2 *Vb, long ld, int nin, const double *dev_y) {
+    return combine<P64>(op, x, ld, 1, Vb, ld, nin, dev_y, 1, true, true);
+}
+template <> int accum_x<P32>(Op &op, double2 *x, const float4 *Vb, long ld, int nin, const double *dev_y) {
+    const long n = 6L * op.g.V;
+    long blocks = std::min((n + 127) / 128, 152L * 8);
+    k_accum_x32<<<(int)blocks, 128, nin * sizeof(double), op.stream>>>(x, Vb, ld, nin, dev_y, op.g.V);
+    op.prof.launches++;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+
+// v (precision P) = scale * src (FP64 internal planes)
+template <class P> int from64(Op &op, typename P::E *dst, const double2 *src, double scale);
+template <> int from64<P64>(Op &op, double2 *dst, const double2 *src, double scale) {
+    return map(op, 12L * op.g.V, [=] __device__(long i) {
+        const double2 v = src[i];
+        dst[i] = make_double2(v.x * scale, v.y * scale);
+    });
+}
+template <> int from64<P32>(Op &op, float4 *dst, const double2 *src, double scale) {
+    const int V = op.g.V;
+    return map(op, 6L * V, [=] __device__(long i) {
+        const int c = (int)(i / V), s = (int)(i % V);
+        const double2 a = src[(size_t)(2 * c) * V + s], b = src[(size_t)(2 * c + 1) * V + s];
+        dst[i] = make_float4((float)(scale * a.x), (float)(scale * a.y), (float)(scale * b.x), (float)(scale * b.y));
+    });
+}
+
+// FP64 copy of k basis vectors (for the deflation set)
+template <class P> int basis_to64(Op &op, double2 *dst, const typename P::E *src, int k);
+template <> int basis_to64<P64>(Op &op, double2 *dst, const double2 *src, int k) {
+    DLZ_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)k * 12 * op.g.V * sizeof(double2), cudaMemcpyDeviceToDevice, op.stream));
+    return DLZ_OK;
+}
+template <> int basis_to64<P32>(Op &op, double2 *dst, const float4 *src, int k) {
+    const long n64 = 12L * op.g.V, n32 = 6L * op.g.V;
+    for (int j = 0; j < k; ++j) DLZ_TRY(convert32to64(op, dst + (size_t)j * n64, src + (size_t)j * n32));
+    return DLZ_OK;
+}
+
+}  // namespace
+
+template <class P>
+int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const dlz_params &p,
+               dlz_defl_s **defl_out, dlz_stats &st) {
+    typedef typename P::E E;
+    const int m = p.m, k = p.k;
+    const long n = P::nel(op);
+    const long n64 = 12L * op.g.V;
+    const int which = harmonic ? DLZ_Q : DLZ_DDAGD;
+    const int mv_per = harmonic ? 1 : 2;
+    DevBuf Va, Vb, w, tmp, bb, bp, x, Dx, scal, coef;
+    DLZ_TRY(Va.alloc((size_t)(m + 1) * n * sizeof(E)));
+    DLZ_TRY(Vb.alloc((size_t)(m + 1) * n * sizeof(E)));
+    DLZ_TRY(w.alloc(n * sizeof(E)));
+    DLZ_TRY(tmp.alloc(n * sizeof(E)));
+    DLZ_TRY(bb.alloc(n64 * sizeof(double2)));
+    DLZ_TRY(bp.alloc(n64 * sizeof(double2)));
+    DLZ_TRY(x.alloc(n64 * sizeof(double2)));
+    DLZ_TRY(Dx.alloc(n64 * sizeof(double2)));
+    DLZ_TRY(scal.alloc((size_t)(2 * m + 8) * sizeof(double)));
+    DLZ_TRY(coef.alloc((size_t)(m + 1) * (m + 1) * sizeof(double2)));
+    double *d_alpha = scal.as<double>(), *d_beta = d_alpha + m, *d_norm = d_beta + m;
+    HostScratch hs;
+    DLZ_TRY(hs.ensure(2 * m + 8));
+
+    DLZ_TRY(v64::copy(op, bb.as<double2>(), b_in));
+    // right-hand side of the hermitian system: gamma5 b (Q) or D^dag b (D^dag D), in FP64
+    if (harmonic) DLZ_TRY(v64::gamma5(op, bp.as<double2>(), bb.as<double2>()));
+    else DLZ_TRY(wilson64(op, bp.as<double2>(), bb.as<double2>(), DLZ_DDAG));
+    if (!harmonic) st.mvps += 1;
+    DLZ_TRY(v64::zero(op, x.as<double2>()));
+    DLZ_TRY(v64::norm2_diff(op, bb.as<double2>(), nullptr, d_norm));
+    DLZ_TRY(v64::norm2_diff(op, bp.as<double2>(), nullptr, d_norm + 1));
+    DLZ_TRY(d2h_sync(op, hs.p, d_norm, 2 * sizeof(double)));
+    const double bnorm = std::sqrt(hs.p[0]), beta0 = std::sqrt(hs.p[1]);
+    if (!std::isfinite(bnorm) || !std::isfinite(beta0)) return fail(DLZ_ERR_NONFINITE, "right-hand side is not finite");
+    if (bnorm == 0.0) {
+        DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
+        st.converged = 1;
+        st.true_residual = 0.0;
+        if (defl_out) *defl_out = nullptr;
+        return DLZ_OK;
+    }
+    E *V = Va.as<E>(), *Vn = Vb.as<E>();
+    DLZ_TRY(from64<P>(op, V, bp.as<double2>(), 1.0 / beta0));   // v_1 = b' / ||b'||
+    std::vector<double> T((size_t)(m + 1) * m, 0.0), c(m + 1, 0.0);
+    c[0] = beta0;
+    int j0 = 0;
+    double Anorm = 0.0;
+    long long mvps_at_conv = -1;
+    bool converged = false;
+    int cycle = 0;
+    double *coefr = coef.as<double>();
+    std::vector<double> hist;
+    for (cycle = 0; cycle < p.max_cycles; ++cycle) {
+        // ---------------- Lanczos steps j0 .. m-1
+        if (j0 > 0) {
+            std::vector<double> cp(j0);                 // coupling of v_{k+1} to the kept vectors
+            for (int i = 0; i < j0; ++i) cp[i] = -T[(size_t)j0 * m + i];
+            DLZ_TRY(h2d(op, coefr, cp.data(), j0 * sizeof(double)));
+        }
+        for (int j = j0; j < m; ++j) {
+            E *vj = V + (size_t)j * n, *wv = w.as<E>();
+            DLZ_TRY(P::apply(op, wv, vj, which, tmp.as<E>()));
+            st.mvps += mv_per;
+            if (j == j0 && j0 > 0) DLZ_TRY(combine<P>(op, wv, n, 1, V, n, j0, coefr, 1, true, true));
+            const E *vprev = (j > j0) ? V + (size_t)(j - 1) * n : nullptr;
+            const double *bprev = (j > j0) ? d_beta + (j - 1) : nullptr;
+            double *aj = d_alpha + j, *bj = d_beta + j;
+            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                E x_ = wv[i];
+                if (vprev) {
+                    x_ = P::axpy(-*bprev, vprev[i], x_);
+                    wv[i] = x_;
+                }
+                acc[0] += P::rdot(vj[i], x_);
+            }, [=] __device__(const double *r) { *aj = r[0]; }));
+            const bool reorth = (j0 > 0) && p.reorth_period > 0 && ((j - j0) % p.reorth_period == 0);
+            if (reorth) {
+                DLZ_TRY(map(op, n, [=] __device__(long i) { wv[i] = P::axpy(-*aj, vj[i], wv[i]); }));
+                double2 *cd = coef.as<double2>() + (m + 1);   // after the coupling block
+                DLZ_TRY(multidot<P>(op, V, n, j0, wv, cd, -1.0));
+                DLZ_TRY(combine<P>(op, wv, n, 1, V, n, j0, cd, 1, false, true));
+                DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) { acc[0] += P::nrm(wv[i]); },
+                                  [=] __device__(const double *r) { *bj = sqrt(r[0]); }));
+            } else {
+                DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                    const E x_ = P::axpy(-*aj, vj[i], wv[i]);
+                    wv[i] = x_;
+                    acc[0] += P::nrm(x_);
+                }, [=] __device__(const double *r) { *bj = sqrt(r[0]); }));
+            }
+            E *vn = V + (size_t)(j + 1) * n;
+            DLZ_TRY(map(op, n, [=] __device__(long i) { vn[i] = P::scal(1.0 / *bj, wv[i]); }));
+            st.iterations++;
+        }
+        // ---------------- small problem on the host
+        DLZ_TRY(d2h_sync(op, hs.p, d_alpha, 2 * m * sizeof(double)));
+        double tmax = 0.0;
+        for (int j = j0; j < m; ++j) {
+            const double a = hs.p[j], bt = hs.p[m + j];
+            if (!std::isfinite(a) || !std::isfinite(bt)) return fail(DLZ_ERR_NONFINITE, "Lanczos coefficients not finite");
+            T[(size_t)j * m + j] = a;
+            T[(size_t)(j + 1) * m + j] = bt;
+            if (j + 1 < m) T[(size_t)j * m + j + 1] = bt;
+            if (j > j0) T[(size_t)(j - 1) * m + j] = T[(size_t)j * m + j - 1];
+            tmax = std::max(tmax, std::fabs(a));
+        }
+        for (int i = 0; i < j0; ++i) T[(size_t)i * m + j0] = T[(size_t)j0 * m + i];
+        for (int j = j0; j < m; ++j)
+            if (hs.p[m + j] <= 1e-14 * std::max(tmax, Anorm))
+                return fail(DLZ_ERR_BREAKDOWN, "Lanczos breakdown (invariant subspace)");
+        RestartPlan pl;
+        DLZ_TRY(plan_restart(harmonic, m, k, T, c, Anorm, pl));
+        // FP32 basis: Ritz residuals below ~1e-5 ||A|| are under its rounding level
+        const double tol_eig = p.tol_eig > 0 ? p.tol_eig : (P::kF32 ? 1e-5 : 1e-10) * Anorm;
+        // ---------------- x += V_m y ; true residual ||b - D x|| / ||b|| in FP64
+        DLZ_TRY(h2d(op, coefr, pl.y.data(), m * sizeof(double)));
+        DLZ_TRY(accum_x<P>(op, x.as<double2>(), V, n, m, coefr));
+        DLZ_TRY(wilson64(op, Dx.as<double2>(), x.as<double2>(), DLZ_D));
+        st.mvps += 1;
+        DLZ_TRY(v64::norm2_diff(op, bb.as<double2>(), Dx.as<double2>(), d_norm + 2));
+        // ---------------- restart: V_{k+1} <- V_{m+1} P
+        DLZ_TRY(h2d(op, coef.p, pl.P.data(), pl.P.size() * sizeof(double)));
+        DLZ_TRY(combine<P>(op, Vn, n, k + 1, V, n, m + 1, coef.p, k + 1, true, false));
+        if (p.reorth_period > 0) {
+            // the vector carried across the restart joins the periodic re-orthogonalisation
+            E *vk = Vn + (size_t)k * n;
+            double2 *cd = coef.as<double2>() + (size_t)(m + 1) * (k + 1);
+            DLZ_TRY(multidot<P>(op, Vn, n, k, vk, cd, -1.0));
+            DLZ_TRY(combine<P>(op, vk, n, 1, Vn, n, k, cd, 1, false, true));
+            double *nrm = d_norm + 3;
+            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) { acc[0] += P::nrm(vk[i]); },
+                              [=] __device__(const double *r) { *nrm = 1.0 / sqrt(r[0]); }));
+            DLZ_TRY(map(op, n, [=] __device__(long i) { vk[i] = P::scal(*nrm, vk[i]); }));
+        }
+        DLZ_TRY(d2h_sync(op, hs.p, d_norm + 2, sizeof(double)));
+        const double rel = std::sqrt(hs.p[0]) / bnorm;
+        st.true_residual = rel;
+        if (!std::isfinite(rel)) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
+        hist.push_back(rel);
+        bool lin_ok = rel <= p.tol;
+        if (P::kF32 && !lin_ok && hist.size() >= 4) {
+            // FP32 basis: the residual stalls near eps_32 * cond; stop the DR phase there
+            const double prev = hist[hist.size() - 4];
+            lin_ok = rel > 0.5 * prev && rel < 1e-3;
+        }
+        if (lin_ok && mvps_at_conv < 0) mvps_at_conv = st.mvps;
+        bool eig_ok = true;
+        for (int l = 0; l < k; ++l) eig_ok = eig_ok && pl.res[l] <= tol_eig;
+        const bool over = mvps_at_conv >= 0 && (double)(st.mvps - mvps_at_conv) >= p.oversolve * (double)mvps_at_conv;
+        std::swap(V, Vn);
+        T.swap(pl.Tn);
+        c.swap(pl.cn);
+        j0 = k;
+        if (lin_ok && (eig_ok || over)) {
+            converged = true;
+            ++cycle;
+            break;
+        }
+    }
+    st.cycles = cycle;
+    st.converged = (converged && st.true_residual <= p.tol) ? 1 : 0;
+    DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
+    if (defl_out) {
+        DevBuf V64;
+        double2 *vk64;
+        if (P::kF32) {
+            DLZ_TRY(V64.alloc((size_t)k * n64 * sizeof(double2)));
+            DLZ_TRY(basis_to64<P>(op, V64.as<double2>(), V, k));
+            vk64 = V64.as<double2>();
+        } else {
+            vk64 = reinterpret_cast<double2 *>(V);
+        }
+        DLZ_TRY(build_deflation(op, which, vk64, k, defl_out));
+    }
+    DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+    return converged ? DLZ_OK : DLZ_ERR_NOT_CONVERGED;
+}
+
+int dr_solve(Op &op, bool harmonic, const double2 *b, double2 *x, const dlz_params &p,
+             dlz_defl_s **defl_out, dlz_stats &st) {
+    if (p.precision == DLZ_F64) return dr_solve_t<P64>(op, harmonic, b, x, p, defl_out, st);
+    // mixed form: FP32 DR phase, then FP64 defect correction over its deflation set
+    dlz_defl_s *d = nullptr;
+    int rc = dr_solve_t<P32>(op, harmonic, b, x, p, &d, st);
+    if (rc != DLZ_OK && rc != DLZ_ERR_NOT_CONVERGED) {
+        delete d;
+        return rc;
+    }
+    if (st.true_residual > p.tol) {
+        dlz_stats s2 = st;
+        rc = dsolve_mixed(op, d, harmonic, b, x, p, s2, x);
+        st.iterations = s2.iterations;
+        st.mvps = s2.mvps;
+        st.true_residual = s2.true_residual;
+        st.converged = s2.converged;
+    } else {
+        st.converged = 1;
+        rc = DLZ_OK;
+    }
+    if (defl_out) *defl_out = d;
+    else delete d;
+    return rc;
+}
+
+}  // namespace dlz

@@ -18,123 +18,11 @@
 #include "reduce.cuh"
 #include "small_dense.h"
 #include "solvers.h"
+#include "krylov_util.cuh"
 
 namespace dlz {
 
 typedef std::complex<double> zc;
-
-// ------------------------------------------------------------------ vector helpers (FP64)
-namespace v64 {
-
-inline long nel(const Op &op) { return 12L * op.g.V; }
-
-int copy(Op &op, double2 *dst, const double2 *src) {
-    DLZ_CUDA_TRY(cudaMemcpyAsync(dst, src, nel(op) * sizeof(double2), cudaMemcpyDeviceToDevice, op.stream));
-    return DLZ_OK;
-}
-int zero(Op &op, double2 *dst) {
-    DLZ_CUDA_TRY(cudaMemsetAsync(dst, 0, nel(op) * sizeof(double2), op.stream));
-    return DLZ_OK;
-}
-// gamma5 on internal planes: components 6..11 (spins 2, 3) change sign
-int gamma5(Op &op, double2 *dst, const double2 *src) {
-    const long half = 6L * op.g.V;
-    return map(op, nel(op), [=] __device__(long i) {
-        double2 v = src[i];
-        if (i >= half) { v.x = -v.x; v.y = -v.y; }
-        dst[i] = v;
-    });
-}
-// result[slot] = ||a - b||^2 (b may be null: ||a||^2), copied to *host_out after sync
-int norm2_diff(Op &op, const double2 *a, const double2 *b, double *dev_out) {
-    return reduce<1>(op, nel(op), [=] __device__(long i, double (&acc)[1]) {
-        double2 v = a[i];
-        if (b) { const double2 w = b[i]; v.x -= w.x; v.y -= w.y; }
-        acc[0] += v.x * v.x + v.y * v.y;
-    }, [=] __device__(const double *r) { if (dev_out) *dev_out = r[0]; });
-}
-// out[l] (complex) = <V_l, w>  for l < nv, V_l = V + l*ld ; dev_out gets scale * dots
-int multidot(Op &op, const double2 *V, long ld, int nv, const double2 *w, double2 *dev_out, double scale) {
-    const long n = nel(op);
-    for (int l0 = 0; l0 < nv; l0 += 8) {
-        const int nb = std::min(8, nv - l0);
-        const double2 *Vb = V + (size_t)l0 * ld;
-        double2 *o = dev_out + l0;
-        DLZ_TRY(reduce<16>(op, n, [=] __device__(long i, double (&acc)[16]) {
-            const double2 x = w[i];
-#pragma unroll
-            for (int l = 0; l < 8; ++l) {
-                if (l < nb) {
-                    const double2 v = Vb[(size_t)l * ld + i];
-                    acc[2 * l] += v.x * x.x + v.y * x.y;        // Re conj(v) x
-                    acc[2 * l + 1] += v.x * x.y - v.y * x.x;    // Im conj(v) x
-                }
-            }
-        }, [=] __device__(const double *r) {
-            for (int l = 0; l < nb; ++l) o[l] = make_double2(scale * r[2 * l], scale * r[2 * l + 1]);
-        }));
-    }
-    return DLZ_OK;
-}
-
-}  // namespace v64
-
-// combine: out_l = (acc ? out_l : 0) + sum_j C[j][l] in_j   (nout any, in groups of 16)
-int combine64(Op &op, double2 *out, long ld_out, int nout, const double2 *in, long ld_in, int nin,
-              const void *dev_coef, int ld_coef, bool real, bool acc) {
-    const long n = 12L * op.g.V;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_combine64<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_combine64<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_combine64<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_combine64<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
-    if (nin <= 0 || nout <= 0) return DLZ_OK;
-    long blocks = (n + 127) / 128;
-    blocks = std::min(blocks, 152L * 8);
-    for (int l0 = 0; l0 < nout; l0 += 16) {
-        const int nb = std::min(16, nout - l0);
-        if (nb == 1) {
-            const size_t sm = (size_t)nin * 1 * sizeof(double2);
-            if (real) k_combine64<true, 1><<<(int)blocks, 128, sm, op.stream>>>(out + (size_t)l0 * ld_out, ld_out, 1, in, ld_in, nin, dev_coef, ld_coef, l0, acc, n);
-            else k_combine64<false, 1><<<(int)blocks, 128, sm, op.stream>>>(out + (size_t)l0 * ld_out, ld_out, 1, in, ld_in, nin, dev_coef, ld_coef, l0, acc, n);
-        } else {
-            const size_t sm = (size_t)nin * 16 * sizeof(double2);
-            if (real) k_combine64<true, 16><<<(int)blocks, 128, sm, op.stream>>>(out + (size_t)l0 * ld_out, ld_out, nb, in, ld_in, nin, dev_coef, ld_coef, l0, acc, n);
-            else k_combine64<false, 16><<<(int)blocks, 128, sm, op.stream>>>(out + (size_t)l0 * ld_out, ld_out, nb, in, ld_in, nin, dev_coef, ld_coef, l0, acc, n);
-        }
-        op.prof.launches++;
-        DLZ_CUDA_TRY(cudaGetLastError());
-    }
-    return DLZ_OK;
-}
-
-// ------------------------------------------------------------------ small pinned scalar block
-struct HostScratch {
-    double *p = nullptr;
-    size_t n = 0;
-    int ensure(size_t count) {
-        if (count <= n) return DLZ_OK;
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        DLZ_CUDA_TRY(cudaMallocHost(&p, count * sizeof(double)));
-        n = count;
-        return DLZ_OK;
-    }
-    ~HostScratch() { if (p) cudaFreeHost(p); }
-};
-
-static int d2h_sync(Op &op, void *dst, const void *src, size_t bytes) {
-    DLZ_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, op.stream));
-    DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
-    return DLZ_OK;
-}
-static int h2d(Op &op, void *dst, const void *src, size_t bytes) {
-    DLZ_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, op.stream));
-    return DLZ_OK;
-}
 
 // ------------------------------------------------------------------ deflation set
 int build_deflation(Op &op, int which, const double2 *Vk, int k, dlz_defl_s **out) {
@@ -251,7 +139,7 @@ int deflation_finish(Op &op, dlz_defl_s *d) {
 }
 
 // x0 = V H^-1 V^dag b  (b, x0 internal FP64; x0 overwritten)
-static int project64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x0, DevBuf &dots) {
+int project64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x0, DevBuf &dots) {
     const int k = d->k;
     const long n = 12L * op.g.V;
     if (k == 0) return v64::zero(op, x0);
@@ -264,301 +152,6 @@ static int project64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x0,
     for (int i = 0; i < k; ++i) c[i] = make_double2(z[i].real(), z[i].imag());
     DLZ_TRY(h2d(op, dots.p, c.data(), k * sizeof(double2)));
     return combine64(op, x0, n, 1, d->V64.as<double2>(), n, k, dots.p, 1, false, false);
-}
-
-// ------------------------------------------------------------------ DR solvers
-int dr_solve(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const dlz_params &p,
-             dlz_defl_s **defl_out, dlz_stats &st) {
-    const int m = p.m, k = p.k;
-    const long n = 12L * op.g.V;
-    const int which = harmonic ? DLZ_Q : DLZ_DDAGD;
-    const int mv_per = harmonic ? 1 : 2;
-    DevBuf Va, Vb, w, tmp, bb, bp, x, Dx, scal, coef;
-    DLZ_TRY(Va.alloc((size_t)(m + 1) * n * sizeof(double2)));
-    DLZ_TRY(Vb.alloc((size_t)(m + 1) * n * sizeof(double2)));
-    DLZ_TRY(w.alloc(n * sizeof(double2)));
-    DLZ_TRY(tmp.alloc(n * sizeof(double2)));
-    DLZ_TRY(bb.alloc(n * sizeof(double2)));
-    DLZ_TRY(bp.alloc(n * sizeof(double2)));
-    DLZ_TRY(x.alloc(n * sizeof(double2)));
-    DLZ_TRY(Dx.alloc(n * sizeof(double2)));
-    // device scalars: alpha[m], beta[m], norms[4]
-    DLZ_TRY(scal.alloc((size_t)(2 * m + 8) * sizeof(double)));
-    DLZ_TRY(coef.alloc((size_t)(m + 1) * (m + 1) * sizeof(double2)));
-    double *d_alpha = scal.as<double>(), *d_beta = d_alpha + m, *d_norm = d_beta + m;
-    HostScratch hs;
-    DLZ_TRY(hs.ensure(2 * m + 8));
-
-    DLZ_TRY(v64::copy(op, bb.as<double2>(), b_in));
-    // right-hand side of the hermitian system: gamma5 b (Q) or D^dag b (D^dag D)
-    if (harmonic) DLZ_TRY(v64::gamma5(op, bp.as<double2>(), bb.as<double2>()));
-    else DLZ_TRY(wilson64(op, bp.as<double2>(), bb.as<double2>(), DLZ_DDAG));
-    if (!harmonic) st.mvps += 1;
-    DLZ_TRY(v64::zero(op, x.as<double2>()));
-    DLZ_TRY(v64::norm2_diff(op, bb.as<double2>(), nullptr, d_norm));
-    DLZ_TRY(v64::norm2_diff(op, bp.as<double2>(), nullptr, d_norm + 1));
-    DLZ_TRY(d2h_sync(op, hs.p, d_norm, 2 * sizeof(double)));
-    const double bnorm = std::sqrt(hs.p[0]), beta0 = std::sqrt(hs.p[1]);
-    if (!std::isfinite(bnorm) || !std::isfinite(beta0)) return fail(DLZ_ERR_NONFINITE, "right-hand side is not finite");
-    if (bnorm == 0.0) {
-        DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
-        st.converged = 1; st.true_residual = 0.0;
-        if (defl_out) *defl_out = nullptr;
-        return DLZ_OK;
-    }
-    double2 *V = Va.as<double2>(), *Vn = Vb.as<double2>();
-    // v_1 = b' / ||b'||
-    {
-        const double2 *src = bp.as<double2>();
-        const double inv = 1.0 / beta0;
-        DLZ_TRY(map(op, n, [=] __device__(long i) { double2 v = src[i]; V[i] = make_double2(v.x * inv, v.y * inv); }));
-    }
-    std::vector<double> T((size_t)(m + 1) * m, 0.0), c(m + 1, 0.0);
-    c[0] = beta0;
-    int j0 = 0;
-    double Anorm = 0.0;
-    long long mvps_at_conv = -1;
-    std::vector<double> theta_k(k), ritz_res(k);
-    bool converged = false;
-    int cycle = 0;
-    const double2 *coefd = coef.as<double2>();
-    double *coefr = coef.as<double>();
-    for (cycle = 0; cycle < p.max_cycles; ++cycle) {
-        // ---------------- Lanczos steps j0 .. m-1
-        if (j0 > 0) {
-            // coupling of the restart vector to the kept vectors: coefficients -T[j0][i]
-            std::vector<double> cp(j0);
-            for (int i = 0; i < j0; ++i) cp[i] = -T[(size_t)j0 * m + i];
-            DLZ_TRY(h2d(op, coefr, cp.data(), j0 * sizeof(double)));
-        }
-        for (int j = j0; j < m; ++j) {
-            double2 *vj = V + (size_t)j * n, *wv = w.as<double2>();
-            DLZ_TRY(apply64(op, wv, vj, which, tmp.as<double2>()));
-            st.mvps += mv_per;
-            if (j == j0 && j0 > 0)
-                DLZ_TRY(combine64(op, wv, n, 1, V, n, j0, coefr, 1, true, true));
-            const double2 *vprev = (j > j0) ? V + (size_t)(j - 1) * n : nullptr;
-            const double *bprev = (j > j0) ? d_beta + (j - 1) : nullptr;
-            double *aj = d_alpha + j, *bj = d_beta + j;
-            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
-                double2 x_ = wv[i];
-                if (vprev) {
-                    const double bt = *bprev;
-                    const double2 u = vprev[i];
-                    x_.x -= bt * u.x; x_.y -= bt * u.y;
-                    wv[i] = x_;
-                }
-                const double2 v = vj[i];
-                acc[0] += v.x * x_.x + v.y * x_.y;
-            }, [=] __device__(const double *r) { *aj = r[0]; }));
-            const bool reorth = (j0 > 0) && p.reorth_period > 0 && ((j - j0) % p.reorth_period == 0);
-            if (reorth) {
-                DLZ_TRY(map(op, n, [=] __device__(long i) {
-                    const double a = *aj;
-                    double2 x_ = wv[i];
-                    const double2 v = vj[i];
-                    x_.x -= a * v.x; x_.y -= a * v.y;
-                    wv[i] = x_;
-                }));
-                double2 *cd = coef.as<double2>() + (m + 1);   // after the coupling block
-                DLZ_TRY(v64::multidot(op, V, n, j0, wv, cd, -1.0));
-                DLZ_TRY(combine64(op, wv, n, 1, V, n, j0, cd, 1, false, true));
-                DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
-                    const double2 x_ = wv[i];
-                    acc[0] += x_.x * x_.x + x_.y * x_.y;
-                }, [=] __device__(const double *r) { *bj = sqrt(r[0]); }));
-            } else {
-                DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
-                    const double a = *aj;
-                    double2 x_ = wv[i];
-                    const double2 v = vj[i];
-                    x_.x -= a * v.x; x_.y -= a * v.y;
-                    wv[i] = x_;
-                    acc[0] += x_.x * x_.x + x_.y * x_.y;
-                }, [=] __device__(const double *r) { *bj = sqrt(r[0]); }));
-            }
-            double2 *vn = V + (size_t)(j + 1) * n;
-            DLZ_TRY(map(op, n, [=] __device__(long i) {
-                const double inv = 1.0 / *bj;
-                const double2 x_ = wv[i];
-                vn[i] = make_double2(x_.x * inv, x_.y * inv);
-            }));
-            st.iterations++;
-        }
-        // ---------------- small problem on the host
-        DLZ_TRY(d2h_sync(op, hs.p, d_alpha, 2 * m * sizeof(double)));
-        double tmax = 0.0;
-        for (int j = j0; j < m; ++j) {
-            const double a = hs.p[j], bt = hs.p[m + j];
-            if (!std::isfinite(a) || !std::isfinite(bt)) return fail(DLZ_ERR_NONFINITE, "Lanczos coefficients not finite");
-            T[(size_t)j * m + j] = a;
-            T[(size_t)(j + 1) * m + j] = bt;
-            if (j + 1 < m) T[(size_t)j * m + j + 1] = bt;
-            if (j > j0) T[(size_t)(j - 1) * m + j] = T[(size_t)j * m + j - 1];
-            tmax = std::max(tmax, std::fabs(a));
-        }
-        for (int i = 0; i < j0; ++i) T[(size_t)i * m + j0] = T[(size_t)j0 * m + i];
-        for (int j = j0; j < m; ++j)
-            if (hs.p[m + j] <= 1e-14 * std::max(tmax, Anorm))
-                return fail(DLZ_ERR_BREAKDOWN, "Lanczos breakdown (invariant subspace)");
-        std::vector<double> Tm((size_t)m * m);
-        for (int i = 0; i < m; ++i)
-            for (int jj = 0; jj < m; ++jj) Tm[(size_t)i * m + jj] = T[(size_t)i * m + jj];
-        std::vector<double> ev(m), G((size_t)m * m), y(m);
-        if (!sym_eig(m, Tm.data(), ev.data(), G.data())) return fail(DLZ_ERR_NONFINITE, "eig(T_m) failed");
-        Anorm = std::max(Anorm, std::max(std::fabs(ev[0]), std::fabs(ev[m - 1])));
-        const double tol_eig = p.tol_eig > 0 ? p.tol_eig : 1e-10 * Anorm;
-        std::vector<double> P((size_t)(m + 1) * (k + 1), 0.0), Tn((size_t)(m + 1) * m, 0.0), cn(m + 1, 0.0);
-        std::vector<double> s_ls;
-        double rho = 0.0;
-        if (!harmonic) {
-            // Galerkin T_m y = c (Lan-DR)
-            std::vector<double> LU = Tm;
-            std::vector<int> piv(m);
-            std::copy(c.begin(), c.begin() + m, y.begin());
-            if (!lu_factor(m, LU.data(), piv.data())) return fail(DLZ_ERR_BREAKDOWN, "T_m singular");
-            lu_solve(m, LU.data(), piv.data(), y.data());
-            rho = -T[(size_t)m * m + m - 1] * y[m - 1];
-            // k algebraically smallest Ritz values (ev ascending)
-            for (int l = 0; l < k; ++l) {
-                theta_k[l] = ev[l];
-                for (int i = 0; i < m; ++i) P[(size_t)i * (k + 1) + l] = G[(size_t)i * m + l];
-                ritz_res[l] = std::fabs(T[(size_t)m * m + m - 1] * G[(size_t)(m - 1) * m + l]);
-            }
-            P[(size_t)m * (k + 1) + k] = 1.0;
-            for (int l = 0; l < k; ++l) Tn[(size_t)l * m + l] = theta_k[l];
-            for (int l = 0; l < k; ++l) Tn[(size_t)k * m + l] = T[(size_t)m * m + m - 1] * G[(size_t)(m - 1) * m + l];
-            cn[k] = rho;
-        } else {
-            // least squares min ||c - Tbar y|| (MinRes-DR)
-            std::vector<double> q(m + 1);
-            if (!lstsq(m + 1, m, T.data(), c.data(), y.data(), q.data())) return fail(DLZ_ERR_BREAKDOWN, "least squares failed");
-            s_ls.assign(m + 1, 0.0);
-            for (int i = 0; i <= m; ++i) {
-                double t = c[i];
-                for (int jj = 0; jj < m; ++jj) t -= T[(size_t)i * m + jj] * y[jj];
-                s_ls[i] = t;
-            }
-            // harmonic Ritz: T_m g = mu (Tbar^T Tbar) g, theta = 1/mu
-            std::vector<double> M((size_t)m * m, 0.0), L((size_t)m * m), X((size_t)m * m), C((size_t)m * m);
-            for (int i = 0; i < m; ++i)
-                for (int jj = 0; jj < m; ++jj) {
-                    double t = 0;
-                    for (int r = 0; r <= m; ++r) t += T[(size_t)r * m + i] * T[(size_t)r * m + jj];
-                    M[(size_t)i * m + jj] = t;
-                }
-            if (!cholesky(m, M.data(), L.data())) return fail(DLZ_ERR_BREAKDOWN, "Tbar^T Tbar not positive definite");
-            // X = L^-1 T_m (column by column), C = L^-1 X^T
-            std::vector<double> col(m);
-            for (int jj = 0; jj < m; ++jj) {
-                for (int i = 0; i < m; ++i) col[i] = Tm[(size_t)i * m + jj];
-                lower_solve(m, L.data(), col.data());
-                for (int i = 0; i < m; ++i) X[(size_t)i * m + jj] = col[i];
-            }
-            for (int jj = 0; jj < m; ++jj) {
-                for (int i = 0; i < m; ++i) col[i] = X[(size_t)jj * m + i];
-                lower_solve(m, L.data(), col.data());
-                for (int i = 0; i < m; ++i) C[(size_t)i * m + jj] = col[i];
-            }
-            std::vector<double> mu(m), Zc((size_t)m * m);
-            if (!sym_eig(m, C.data(), mu.data(), Zc.data())) return fail(DLZ_ERR_NONFINITE, "harmonic eigensolve failed");
-            std::vector<int> idx(m);
-            for (int i = 0; i < m; ++i) idx[i] = i;
-            std::stable_sort(idx.begin(), idx.end(), [&](int a, int bq) { return std::fabs(mu[a]) > std::fabs(mu[bq]); });
-            std::vector<double> Gk((size_t)m * k);
-            for (int l = 0; l < k; ++l) {
-                for (int i = 0; i < m; ++i) col[i] = Zc[(size_t)i * m + idx[l]];
-                upper_t_solve(m, L.data(), col.data());
-                double nr = 0;
-                for (int i = 0; i < m; ++i) nr += col[i] * col[i];
-                nr = std::sqrt(nr);
-                for (int i = 0; i < m; ++i) Gk[(size_t)i * k + l] = col[i] / nr;
-                theta_k[l] = 1.0 / mu[idx[l]];
-                double r2 = 0;
-                for (int r = 0; r <= m; ++r) {
-                    double t = 0;
-                    for (int jj = 0; jj < m; ++jj) t += T[(size_t)r * m + jj] * Gk[(size_t)jj * k + l];
-                    if (r < m) t -= theta_k[l] * Gk[(size_t)r * k + l];
-                    r2 += t * t;
-                }
-                ritz_res[l] = std::sqrt(r2);
-            }
-            double qs = 0;
-            for (int i = 0; i <= m; ++i) qs += q[i] * s_ls[i];
-            if (qs < 0) for (double &t : q) t = -t;
-            for (int i = 0; i < m; ++i)
-                for (int l = 0; l < k; ++l) P[(size_t)i * (k + 1) + l] = Gk[(size_t)i * k + l];
-            for (int i = 0; i <= m; ++i) P[(size_t)i * (k + 1) + k] = q[i];
-            if (!mgs_columns(m + 1, k + 1, P.data())) return fail(DLZ_ERR_BREAKDOWN, "restart basis lost rank");
-            // Tbar_k = P^T Tbar P[:m, :k]
-            std::vector<double> TP((size_t)(m + 1) * k, 0.0);
-            for (int r = 0; r <= m; ++r)
-                for (int l = 0; l < k; ++l) {
-                    double t = 0;
-                    for (int jj = 0; jj < m; ++jj) t += T[(size_t)r * m + jj] * P[(size_t)jj * (k + 1) + l];
-                    TP[(size_t)r * k + l] = t;
-                }
-            for (int a = 0; a <= k; ++a)
-                for (int l = 0; l < k; ++l) {
-                    double t = 0;
-                    for (int r = 0; r <= m; ++r) t += P[(size_t)r * (k + 1) + a] * TP[(size_t)r * k + l];
-                    Tn[(size_t)a * m + l] = t;
-                }
-            for (int a = 0; a < k; ++a)
-                for (int l = 0; l < a; ++l) {
-                    const double sym = 0.5 * (Tn[(size_t)a * m + l] + Tn[(size_t)l * m + a]);
-                    Tn[(size_t)a * m + l] = Tn[(size_t)l * m + a] = sym;
-                }
-            for (int a = 0; a <= k; ++a) {
-                double t = 0;
-                for (int r = 0; r <= m; ++r) t += P[(size_t)r * (k + 1) + a] * s_ls[r];
-                cn[a] = t;
-            }
-        }
-        // ---------------- x += V_m y ; true residual ||b - D x|| / ||b||
-        DLZ_TRY(h2d(op, coefr, y.data(), m * sizeof(double)));
-        DLZ_TRY(combine64(op, x.as<double2>(), n, 1, V, n, m, coefr, 1, true, true));
-        DLZ_TRY(wilson64(op, Dx.as<double2>(), x.as<double2>(), DLZ_D));
-        st.mvps += 1;
-        DLZ_TRY(v64::norm2_diff(op, bb.as<double2>(), Dx.as<double2>(), d_norm + 2));
-        // ---------------- restart: V_{k+1} <- V_{m+1} P
-        DLZ_TRY(h2d(op, coef.p, P.data(), P.size() * sizeof(double)));
-        DLZ_TRY(combine64(op, Vn, n, k + 1, V, n, m + 1, coef.p, k + 1, true, false));
-        if (p.reorth_period > 0) {
-            // the vector carried across the restart joins the periodic re-orthogonalisation
-            double2 *vk = Vn + (size_t)k * n;
-            double2 *cd = coef.as<double2>() + (size_t)(m + 1) * (k + 1);
-            DLZ_TRY(v64::multidot(op, Vn, n, k, vk, cd, -1.0));
-            DLZ_TRY(combine64(op, vk, n, 1, Vn, n, k, cd, 1, false, true));
-            double *nrm = d_norm + 3;
-            DLZ_TRY(v64::norm2_diff(op, vk, nullptr, nrm));
-            DLZ_TRY(map(op, n, [=] __device__(long i) {
-                const double inv = 1.0 / sqrt(*nrm);
-                const double2 v = vk[i];
-                vk[i] = make_double2(v.x * inv, v.y * inv);
-            }));
-        }
-        DLZ_TRY(d2h_sync(op, hs.p, d_norm + 2, sizeof(double)));
-        const double rel = std::sqrt(hs.p[0]) / bnorm;
-        st.true_residual = rel;
-        if (!std::isfinite(rel)) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
-        const bool lin_ok = rel <= p.tol;
-        if (lin_ok && mvps_at_conv < 0) mvps_at_conv = st.mvps;
-        bool eig_ok = true;
-        for (int l = 0; l < k; ++l) eig_ok = eig_ok && ritz_res[l] <= tol_eig;
-        const bool over = mvps_at_conv >= 0 && (double)(st.mvps - mvps_at_conv) >= p.oversolve * (double)mvps_at_conv;
-        std::swap(V, Vn);
-        T.swap(Tn);
-        c.swap(cn);
-        j0 = k;
-        if (lin_ok && (eig_ok || over)) { converged = true; ++cycle; break; }
-    }
-    st.cycles = cycle;
-    st.converged = converged ? 1 : 0;
-    DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
-    if (defl_out) DLZ_TRY(build_deflation(op, which, V, k, defl_out));
-    DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
-    return converged ? DLZ_OK : DLZ_ERR_NOT_CONVERGED;
 }
 
 // ------------------------------------------------------------------ D-MinRes (FP64)

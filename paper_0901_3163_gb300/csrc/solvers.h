@@ -31,6 +31,14 @@ int dminres64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x, const d
               dlz_stats &st);
 int dcg64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x, const dlz_params &p,
           dlz_stats &st);
+// D-MinRes (minres) or D-CG in FP32 with FP64 defect correction (DLZ_F32).
+// x_init (may alias x, may be null) is the starting guess.
+int dsolve_mixed(Op &op, const dlz_defl_s *d, bool minres, const double2 *b, double2 *x,
+                 const dlz_params &p, dlz_stats &st, const double2 *x_init = nullptr);
+// D-MinRes in FP32 with FP64 defect correction on N <= 16 right-hand sides at once
+// (B, X: N internal FP64 vectors one after another; st: N entries).
+int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *B, double2 *X, int N,
+                       const dlz_params &p, dlz_stats *st);
 int build_deflation(Op &op, int which, const double2 *Vk, int k, dlz_defl_s **out);
 int deflation_finish(Op &op, dlz_defl_s *d);
 int combine64(Op &op, double2 *out, long ld_out, int nout, const double2 *in, long ld_in, int nin,

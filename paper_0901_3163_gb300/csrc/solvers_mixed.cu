@@ -1,0 +1,630 @@
+// Mixed-precision D-MinRes and D-CG (arXiv:0901.3163, Sec. 2 methods):
+// FP32 stencil and FP32 Krylov vectors inside, FP64 outside.
+//
+// Defect correction: the FP64 outer loop keeps x in FP64, recomputes the true
+// residual r = b' - A x with the FP64 stencil, re-applies the Galerkin
+// projection over the deflation set to it (which also removes the deflated
+// directions that rounding lets back in), and hands r / ||r|| to an FP32
+// MinRes (or CG on the normal equations) that reduces it by the factor
+// `reliable_delta`; the FP32 correction is added to x in FP64.  All scalars
+// of the inner iteration (alpha, beta, Givens rotations, step lengths) and all
+// reductions are FP64; only vectors and the stencil are FP32.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "dlz_internal.cuh"
+#include "krylov_util.cuh"
+#include "reduce.cuh"
+#include "small_dense.h"
+#include "solvers.h"
+
+namespace dlz {
+
+namespace {
+
+struct InnerState {
+    double beta, alpha, beta_next, inv_beta;
+    double c, s, c_old, s_old, phibar;
+    double eps, delta, gamma, tau;
+    double rr, ss, pq;   // CG
+};
+
+__device__ inline double re_dot(float4 a, float4 b) {
+    return (double)(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
+}
+__device__ inline double nrm2(float4 a) { return (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w); }
+__device__ inline float4 axpy4(float a, float4 x, float4 y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ inline float4 scale4(float a, float4 x) { return make_float4(a * x.x, a * x.y, a * x.z, a * x.w); }
+
+// r32 = scale * r64 (internal planes: FP32 plane c holds FP64 planes 2c, 2c+1)
+int to32_scaled(Op &op, float4 *dst, const double2 *src, const double *d_scale) {
+    const int V = op.g.V;
+    return map(op, 6L * V, [=] __device__(long i) {
+        const int c = (int)(i / V), s = (int)(i % V);
+        const double sc = *d_scale;
+        const double2 a = src[(size_t)(2 * c) * V + s], b = src[(size_t)(2 * c + 1) * V + s];
+        dst[i] = make_float4((float)(sc * a.x), (float)(sc * a.y), (float)(sc * b.x), (float)(sc * b.y));
+    });
+}
+// x64 += scale * e32
+int add_from32(Op &op, double2 *x, const float4 *e, const double *d_scale) {
+    const int V = op.g.V;
+    return map(op, 6L * V, [=] __device__(long i) {
+        const int c = (int)(i / V), s = (int)(i % V);
+        const double sc = *d_scale;
+        const float4 q = e[i];
+        double2 &a = x[(size_t)(2 * c) * V + s];
+        double2 &b = x[(size_t)(2 * c + 1) * V + s];
+        a.x += sc * q.x; a.y += sc * q.y; b.x += sc * q.z; b.y += sc * q.w;
+    });
+}
+
+// FP32 MinRes on Q e = r from e = 0, until |phibar| <= tol_rel * ||r||.
+int minres_inner32(Op &op, const float4 *r, float4 *e, float4 *vp, float4 *v, float4 *w, float4 *d1,
+                   float4 *d2, InnerState *ms, double tol_rel, const dlz_params &p, dlz_stats &st,
+                   HostScratch &hs) {
+    const long n = 6L * op.g.V;
+    DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) { acc[0] += nrm2(r[i]); },
+                      [=] __device__(const double *res) {
+                          const double b = sqrt(res[0]);
+                          InnerState s0 = {};
+                          s0.beta_next = b; s0.inv_beta = b > 0 ? 1.0 / b : 0.0;
+                          s0.c = 1.0; s0.c_old = 1.0; s0.phibar = b;
+                          *ms = s0;
+                      }));
+    DLZ_TRY(map(op, n, [=] __device__(long i) {
+        const float ib = (float)ms->inv_beta;
+        v[i] = scale4(ib, r[i]);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        vp[i] = z; d1[i] = z; d2[i] = z; e[i] = z;
+    }));
+    DLZ_TRY(d2h_sync(op, hs.p, ms, sizeof(InnerState)));
+    const double beta1 = reinterpret_cast<const InnerState *>(hs.p)->beta_next;
+    if (!(beta1 > 0.0)) return std::isfinite(beta1) ? DLZ_OK : fail(DLZ_ERR_NONFINITE, "inner residual");
+    int it = 0;
+    while (st.iterations < p.max_iter) {
+        DLZ_TRY(wilson32(op, w, v, DLZ_Q));
+        st.mvps += 1;
+        {
+            const float4 *a_vp = vp, *a_v = v;
+            float4 *a_w = w;
+            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                const float bt = (float)ms->beta_next;
+                const float4 t = axpy4(-bt, a_vp[i], a_w[i]);
+                a_w[i] = t;
+                acc[0] += re_dot(a_v[i], t);
+            }, [=] __device__(const double *res) {
+                ms->beta = ms->beta_next;
+                ms->alpha = res[0];
+            }));
+        }
+        {
+            const float4 *a_v = v;
+            float4 *a_w = w;
+            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+                const float al = (float)ms->alpha;
+                const float4 t = axpy4(-al, a_v[i], a_w[i]);
+                a_w[i] = t;
+                acc[0] += nrm2(t);
+            }, [=] __device__(const double *res) {
+                InnerState s = *ms;
+                const double bn = sqrt(res[0]);
+                const double eps = s.s_old * s.beta;
+                const double deltabar = s.c_old * s.beta;
+                const double delta = s.c * deltabar + s.s * s.alpha;
+                const double gammabar = -s.s * deltabar + s.c * s.alpha;
+                const double gamma = hypot(gammabar, bn);
+                const double cn = gammabar / gamma, sn = bn / gamma;
+                s.tau = cn * s.phibar;
+                s.phibar = -sn * s.phibar;
+                s.eps = eps; s.delta = delta; s.gamma = gamma;
+                s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
+                s.beta_next = bn;
+                s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
+                *ms = s;
+            }));
+        }
+        {
+            const float4 *a_v = v, *a_d1 = d1;
+            float4 *a_d2 = d2, *a_w = w, *a_e = e;
+            DLZ_TRY(map(op, n, [=] __device__(long i) {
+                const float de = (float)ms->delta, ep = (float)ms->eps, ig = (float)(1.0 / ms->gamma);
+                const float ta = (float)ms->tau, ib = (float)ms->inv_beta;
+                const float4 q = a_v[i], e1 = a_d1[i], e2 = a_d2[i];
+                float4 dn;
+                dn.x = (q.x - de * e1.x - ep * e2.x) * ig;
+                dn.y = (q.y - de * e1.y - ep * e2.y) * ig;
+                dn.z = (q.z - de * e1.z - ep * e2.z) * ig;
+                dn.w = (q.w - de * e1.w - ep * e2.w) * ig;
+                a_d2[i] = dn;
+                a_e[i] = axpy4(ta, dn, a_e[i]);
+                a_w[i] = scale4(ib, a_w[i]);
+            }));
+        }
+        float4 *t0 = vp; vp = v; v = w; w = t0;
+        std::swap(d1, d2);
+        st.iterations++;
+        ++it;
+        if (it % p.check_every == 0 || st.iterations >= p.max_iter) {
+            DLZ_TRY(d2h_sync(op, hs.p, ms, sizeof(InnerState)));
+            const InnerState *h = reinterpret_cast<const InnerState *>(hs.p);
+            if (!std::isfinite(h->phibar)) return fail(DLZ_ERR_NONFINITE, "MinRes residual not finite");
+            if (std::fabs(h->phibar) <= tol_rel * beta1 || h->beta_next == 0.0) break;
+        }
+    }
+    return DLZ_OK;
+}
+
+// FP32 CG on D^dag D e = D^dag s from e = 0, tracking s - D e, until that falls
+// by tol_rel.  r, pp, t, q: work vectors.
+int cgnr_inner32(Op &op, float4 *s, float4 *e, float4 *r, float4 *pp, float4 *t, float4 *q,
+                 InnerState *cs, double tol_rel, const dlz_params &p, dlz_stats &st, HostScratch &hs) {
+    const long n = 6L * op.g.V;
+    DLZ_TRY(wilson32(op, r, s, DLZ_DDAG));
+    st.mvps += 1;
+    DLZ_TRY(reduce<2>(op, n, [=] __device__(long i, double (&acc)[2]) {
+        const float4 v = r[i];
+        pp[i] = v;
+        e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        acc[0] += nrm2(v);
+        acc[1] += nrm2(s[i]);
+    }, [=] __device__(const double *res) { cs->rr = res[0]; cs->ss = res[1]; }));
+    DLZ_TRY(d2h_sync(op, hs.p, cs, sizeof(InnerState)));
+    const double s0 = std::sqrt(reinterpret_cast<const InnerState *>(hs.p)->ss);
+    int it = 0;
+    while (st.iterations < p.max_iter) {
+        DLZ_TRY(wilson32(op, t, pp, DLZ_D));
+        DLZ_TRY(wilson32(op, q, t, DLZ_DDAG));
+        st.mvps += 2;
+        DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) { acc[0] += re_dot(pp[i], q[i]); },
+                          [=] __device__(const double *res) { cs->pq = res[0]; }));
+        DLZ_TRY(reduce<2>(op, n, [=] __device__(long i, double (&acc)[2]) {
+            const float al = (float)(cs->rr / cs->pq);
+            const float4 pv = pp[i];
+            e[i] = axpy4(al, pv, e[i]);
+            const float4 rv = axpy4(-al, q[i], r[i]);
+            const float4 sv = axpy4(-al, t[i], s[i]);
+            r[i] = rv;
+            s[i] = sv;
+            acc[0] += nrm2(rv);
+            acc[1] += nrm2(sv);
+        }, [=] __device__(const double *res) {
+            cs->beta = res[0] / cs->rr;
+            cs->rr = res[0];
+            cs->ss = res[1];
+        }));
+        DLZ_TRY(map(op, n, [=] __device__(long i) {
+            const float be = (float)cs->beta;
+            pp[i] = axpy4(be, pp[i], r[i]);
+        }));
+        st.iterations++;
+        ++it;
+        if (it % p.check_every == 0 || st.iterations >= p.max_iter) {
+            DLZ_TRY(d2h_sync(op, hs.p, cs, sizeof(InnerState)));
+            const InnerState *h = reinterpret_cast<const InnerState *>(hs.p);
+            if (!std::isfinite(h->ss)) return fail(DLZ_ERR_NONFINITE, "CG residual not finite");
+            if (std::sqrt(h->ss) <= tol_rel * s0 || h->rr == 0.0) break;
+        }
+    }
+    return DLZ_OK;
+}
+
+}  // namespace
+
+int dsolve_mixed(Op &op, const dlz_defl_s *d, bool minres, const double2 *b, double2 *x_out,
+                 const dlz_params &p, dlz_stats &st, const double2 *x_init) {
+    const long n64 = 12L * op.g.V;
+    const long n32 = 6L * op.g.V;
+    DevBuf bp, x, r, tmp, dots, scal, f32;
+    DLZ_TRY(bp.alloc(n64 * sizeof(double2)));
+    DLZ_TRY(x.alloc(n64 * sizeof(double2)));
+    DLZ_TRY(r.alloc(n64 * sizeof(double2)));
+    DLZ_TRY(tmp.alloc(n64 * sizeof(double2)));
+    DLZ_TRY(dots.alloc((size_t)std::max(1, d ? d->k : 1) * sizeof(double2)));
+    DLZ_TRY(scal.alloc(64 * sizeof(double)));
+    DLZ_TRY(f32.alloc((size_t)7 * n32 * sizeof(float4)));
+    float4 *w32[7];
+    for (int i = 0; i < 7; ++i) w32[i] = f32.as<float4>() + (size_t)i * n32;
+    InnerState *ist = reinterpret_cast<InnerState *>(scal.as<double>());
+    double *d_norm = scal.as<double>() + 40;
+    HostScratch hs;
+    DLZ_TRY(hs.ensure(64));
+    // the FP64 system: Q x = gamma5 b (MinRes) or D x = b through D^dag D (CG)
+    if (minres) DLZ_TRY(v64::gamma5(op, bp.as<double2>(), b));
+    else DLZ_TRY(v64::copy(op, bp.as<double2>(), b));
+    DLZ_TRY(v64::norm2_diff(op, bp.as<double2>(), nullptr, d_norm + 1));
+    DLZ_TRY(d2h_sync(op, hs.p, d_norm + 1, sizeof(double)));
+    const double bnorm = std::sqrt(hs.p[0]);
+    if (!std::isfinite(bnorm)) return fail(DLZ_ERR_NONFINITE, "right-hand side is not finite");
+    if (bnorm == 0.0) {
+        DLZ_TRY(v64::zero(op, x_out));
+        st.converged = 1; st.true_residual = 0.0;
+        return DLZ_OK;
+    }
+    const int fwd = minres ? DLZ_Q : DLZ_D;
+    if (x_init) DLZ_TRY(v64::copy(op, x.as<double2>(), x_init));
+    else DLZ_TRY(v64::zero(op, x.as<double2>()));
+    bool converged = false;
+    int outer = 0;
+    while (true) {
+        // r = b' - A x in FP64
+        DLZ_TRY(wilson64(op, tmp.as<double2>(), x.as<double2>(), fwd));
+        st.mvps += 1;
+        {
+            const double2 *bq = bp.as<double2>(), *ax = tmp.as<double2>();
+            double2 *rr = r.as<double2>();
+            DLZ_TRY(reduce<1>(op, n64, [=] __device__(long i, double (&acc)[1]) {
+                const double2 a = bq[i], c = ax[i];
+                const double2 t = make_double2(a.x - c.x, a.y - c.y);
+                rr[i] = t;
+                acc[0] += t.x * t.x + t.y * t.y;
+            }, [=] __device__(const double *res) { *d_norm = sqrt(res[0]); }));
+        }
+        DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
+        const double rn = hs.p[0];
+        st.true_residual = rn / bnorm;
+        if (!std::isfinite(rn)) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
+        if (rn <= p.tol * bnorm) { converged = true; break; }
+        if (st.iterations >= p.max_iter) break;
+        if (d && d->k > 0) {
+            // Galerkin projection of the current residual over the deflation set
+            double2 *corr = tmp.as<double2>();
+            if (minres) {
+                DLZ_TRY(project64(op, d, r.as<double2>(), corr, dots));
+            } else {
+                DLZ_TRY(wilson64(op, x_out, r.as<double2>(), DLZ_DDAG));   // x_out as scratch
+                st.mvps += 1;
+                DLZ_TRY(project64(op, d, x_out, corr, dots));
+            }
+            double2 *xx = x.as<double2>();
+            const double2 *cc = corr;
+            DLZ_TRY(map(op, n64, [=] __device__(long i) {
+                double2 a = xx[i];
+                const double2 c = cc[i];
+                a.x += c.x; a.y += c.y;
+                xx[i] = a;
+            }));
+            // residual after the projection (the first outer pass is the D-solve's own start)
+            DLZ_TRY(wilson64(op, tmp.as<double2>(), x.as<double2>(), fwd));
+            st.mvps += 1;
+            const double2 *bq = bp.as<double2>(), *ax = tmp.as<double2>();
+            double2 *rr = r.as<double2>();
+            DLZ_TRY(reduce<1>(op, n64, [=] __device__(long i, double (&acc)[1]) {
+                const double2 a = bq[i], c = ax[i];
+                const double2 t = make_double2(a.x - c.x, a.y - c.y);
+                rr[i] = t;
+                acc[0] += t.x * t.x + t.y * t.y;
+            }, [=] __device__(const double *res) { *d_norm = sqrt(res[0]); }));
+            DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
+            if (hs.p[0] <= p.tol * bnorm) { st.true_residual = hs.p[0] / bnorm; converged = true; break; }
+        }
+        // FP32 correction of the normalised residual
+        double *inv = d_norm + 2, *scl = d_norm + 3;
+        DLZ_TRY(map(op, 1, [=] __device__(long) { *inv = 1.0 / *d_norm; *scl = *d_norm; }));
+        DLZ_TRY(to32_scaled(op, w32[0], r.as<double2>(), inv));
+        DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
+        const double rcur = hs.p[0];
+        const double inner_tol = std::max(0.5 * p.tol * bnorm / rcur, p.reliable_delta);
+        if (minres)
+            DLZ_TRY(minres_inner32(op, w32[0], w32[1], w32[2], w32[3], w32[4], w32[5], w32[6], ist,
+                                   inner_tol, p, st, hs));
+        else
+            DLZ_TRY(cgnr_inner32(op, w32[0], w32[1], w32[2], w32[3], w32[4], w32[5], ist, inner_tol, p,
+                                 st, hs));
+        DLZ_TRY(add_from32(op, x.as<double2>(), w32[1], scl));
+        ++outer;
+    }
+    DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
+    DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+    st.cycles = outer;
+    st.converged = converged ? 1 : 0;
+    return converged ? DLZ_OK : DLZ_ERR_NOT_CONVERGED;
+}
+
+}  // namespace dlz
+
+// ------------------------------------------------------------------ batched form
+// N <= kMaxBatch right-hand sides share every launch: the stencil processes all
+// of them (links read once per site), and each fused reduction carries one
+// accumulator per right-hand side.  Each right-hand side keeps its own FP64
+// scalar recurrence (MinRes Givens rotations or CG step lengths); a right-hand
+// side whose residual is already below tol enters with a zero vector and its
+// scalars are held at a no-op.
+namespace dlz {
+
+namespace {
+
+constexpr int kMaxBatch = 16;
+
+// FP32 MinRes on Q e_r = r_r for all r at once, from e = 0, until every
+// |phibar_r| <= tol_r * ||r_r||.
+int minres_inner32_batch(Op &op, int N, const float4 *r, float4 *e, float4 *vp, float4 *v, float4 *w,
+                         float4 *d1, float4 *d2, InnerState *ms, const double *d_tol,
+                         const dlz_params &p, int &iters, HostScratch &hs) {
+    const long n = 6L * op.g.V;
+    DLZ_TRY(reduce<kMaxBatch>(op, n, [=] __device__(long i, double (&acc)[kMaxBatch]) {
+#pragma unroll
+        for (int q = 0; q < kMaxBatch; ++q)
+            if (q < N) acc[q] += nrm2(r[(size_t)q * n + i]);
+    }, [=] __device__(const double *res) {
+        for (int q = 0; q < N; ++q) {
+            const double b = sqrt(res[q]);
+            InnerState s0 = {};
+            s0.beta_next = b; s0.inv_beta = b > 0 ? 1.0 / b : 0.0;
+            s0.c = 1.0; s0.c_old = 1.0; s0.phibar = b;
+            s0.rr = b;          // ||r_q||: reference for the stopping test
+            ms[q] = s0;
+        }
+    }));
+    DLZ_TRY(map(op, n * N, [=] __device__(long i) {
+        const int q = (int)(i / n);
+        const float ib = (float)ms[q].inv_beta;
+        v[i] = scale4(ib, r[i]);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        vp[i] = z; d1[i] = z; d2[i] = z; e[i] = z;
+    }));
+    int it = 0;
+    while (iters < p.max_iter) {
+        DLZ_TRY(wilson32_batch(op, w, v, DLZ_Q, N));
+        {
+            const float4 *a_vp = vp, *a_v = v;
+            float4 *a_w = w;
+            DLZ_TRY(reduce<kMaxBatch>(op, n, [=] __device__(long i, double (&acc)[kMaxBatch]) {
+#pragma unroll
+                for (int q = 0; q < kMaxBatch; ++q) {
+                    if (q < N) {
+                        const size_t o = (size_t)q * n + i;
+                        const float bt = (float)ms[q].beta_next;
+                        const float4 t = axpy4(-bt, a_vp[o], a_w[o]);
+                        a_w[o] = t;
+                        acc[q] += re_dot(a_v[o], t);
+                    }
+                }
+            }, [=] __device__(const double *res) {
+                for (int q = 0; q < N; ++q) {
+                    ms[q].beta = ms[q].beta_next;
+                    ms[q].alpha = res[q];
+                }
+            }));
+        }
+        {
+            const float4 *a_v = v;
+            float4 *a_w = w;
+            DLZ_TRY(reduce<kMaxBatch>(op, n, [=] __device__(long i, double (&acc)[kMaxBatch]) {
+#pragma unroll
+                for (int q = 0; q < kMaxBatch; ++q) {
+                    if (q < N) {
+                        const size_t o = (size_t)q * n + i;
+                        const float al = (float)ms[q].alpha;
+                        const float4 t = axpy4(-al, a_v[o], a_w[o]);
+                        a_w[o] = t;
+                        acc[q] += nrm2(t);
+                    }
+                }
+            }, [=] __device__(const double *res) {
+                for (int q = 0; q < N; ++q) {
+                    InnerState s = ms[q];
+                    const double bn = sqrt(res[q]);
+                    const double eps = s.s_old * s.beta;
+                    const double deltabar = s.c_old * s.beta;
+                    const double delta = s.c * deltabar + s.s * s.alpha;
+                    const double gammabar = -s.s * deltabar + s.c * s.alpha;
+                    double gamma = hypot(gammabar, bn);
+                    double cn = 1.0, sn = 0.0;
+                    if (gamma > 0.0) { cn = gammabar / gamma; sn = bn / gamma; }
+                    else gamma = 1.0;            // zero right-hand side: hold a no-op
+                    s.tau = cn * s.phibar;
+                    s.phibar = -sn * s.phibar;
+                    s.eps = eps; s.delta = delta; s.gamma = gamma;
+                    s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
+                    s.beta_next = bn;
+                    s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
+                    ms[q] = s;
+                }
+            }));
+        }
+        {
+            const float4 *a_v = v, *a_d1 = d1;
+            float4 *a_d2 = d2, *a_w = w, *a_e = e;
+            DLZ_TRY(map(op, n * N, [=] __device__(long i) {
+                const int q = (int)(i / n);
+                const InnerState &s = ms[q];
+                const float de = (float)s.delta, ep = (float)s.eps, ig = (float)(1.0 / s.gamma);
+                const float ta = (float)s.tau, ib = (float)s.inv_beta;
+                const float4 qv = a_v[i], e1 = a_d1[i], e2 = a_d2[i];
+                float4 dn;
+                dn.x = (qv.x - de * e1.x - ep * e2.x) * ig;
+                dn.y = (qv.y - de * e1.y - ep * e2.y) * ig;
+                dn.z = (qv.z - de * e1.z - ep * e2.z) * ig;
+                dn.w = (qv.w - de * e1.w - ep * e2.w) * ig;
+                a_d2[i] = dn;
+                a_e[i] = axpy4(ta, dn, a_e[i]);
+                a_w[i] = scale4(ib, a_w[i]);
+            }));
+        }
+        float4 *t0 = vp; vp = v; v = w; w = t0;
+        std::swap(d1, d2);
+        ++iters;
+        ++it;
+        if (it % p.check_every == 0 || iters >= p.max_iter) {
+            DLZ_TRY(d2h_sync(op, hs.p, ms, N * sizeof(InnerState)));
+            const InnerState *h = reinterpret_cast<const InnerState *>(hs.p);
+            bool done = true;
+            for (int q = 0; q < N; ++q)
+                if (!std::isfinite(h[q].phibar)) return fail(DLZ_ERR_NONFINITE, "MinRes residual not finite");
+            DLZ_TRY(d2h_sync(op, hs.p + 512, d_tol, N * sizeof(double)));
+            for (int q = 0; q < N; ++q) {
+                const InnerState *hq = reinterpret_cast<const InnerState *>(hs.p) + q;
+                if (!(std::fabs(hq->phibar) <= hs.p[512 + q] * hq->rr || hq->beta_next == 0.0)) done = false;
+            }
+            if (done) break;
+        }
+    }
+    return DLZ_OK;
+}
+
+}  // namespace
+
+int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *B, double2 *X, int N,
+                       const dlz_params &p, dlz_stats *st) {
+    if (N < 1 || N > kMaxBatch) return fail(DLZ_ERR_BADARG, "batch size");
+    if (!minres) {
+        // D-CG keeps the one-at-a-time form
+        for (int q = 0; q < N; ++q)
+            DLZ_TRY(dsolve_mixed(op, d, false, B + (size_t)q * 12 * op.g.V, X + (size_t)q * 12 * op.g.V, p, st[q]));
+        return DLZ_OK;
+    }
+    const long n64 = 12L * op.g.V;
+    const long n32 = 6L * op.g.V;
+    DevBuf bp, x, r, tmp, corr, dots, scal, f32;
+    DLZ_TRY(bp.alloc((size_t)N * n64 * sizeof(double2)));
+    DLZ_TRY(x.alloc((size_t)N * n64 * sizeof(double2)));
+    DLZ_TRY(r.alloc((size_t)N * n64 * sizeof(double2)));
+    DLZ_TRY(tmp.alloc((size_t)N * n64 * sizeof(double2)));
+    DLZ_TRY(corr.alloc(n64 * sizeof(double2)));
+    DLZ_TRY(dots.alloc((size_t)std::max(1, d ? d->k : 1) * sizeof(double2)));
+    DLZ_TRY(scal.alloc((size_t)(kMaxBatch * 24 + 4 * kMaxBatch) * sizeof(double)));
+    DLZ_TRY(f32.alloc((size_t)7 * N * n32 * sizeof(float4)));
+    float4 *w32[7];
+    for (int i = 0; i < 7; ++i) w32[i] = f32.as<float4>() + (size_t)i * N * n32;
+    InnerState *ist = reinterpret_cast<InnerState *>(scal.as<double>());
+    double *d_rn = scal.as<double>() + kMaxBatch * 24;        // ||r_q||
+    double *d_inv = d_rn + kMaxBatch, *d_tol = d_inv + kMaxBatch, *d_bn = d_tol + kMaxBatch;
+    HostScratch hs;
+    DLZ_TRY(hs.ensure(1024));
+    double2 *pbp = bp.as<double2>(), *px = x.as<double2>(), *pr = r.as<double2>(), *pt = tmp.as<double2>();
+    // b'_q = gamma5 b_q ; ||b_q||
+    {
+        const long half = 6L * op.g.V;
+        DLZ_TRY(map(op, n64 * N, [=] __device__(long i) {
+            double2 v = B[i];
+            if ((i % n64) >= half) { v.x = -v.x; v.y = -v.y; }
+            pbp[i] = v;
+        }));
+    }
+    DLZ_TRY(reduce<kMaxBatch>(op, n64, [=] __device__(long i, double (&acc)[kMaxBatch]) {
+#pragma unroll
+        for (int q = 0; q < kMaxBatch; ++q)
+            if (q < N) { const double2 v = pbp[(size_t)q * n64 + i]; acc[q] += v.x * v.x + v.y * v.y; }
+    }, [=] __device__(const double *res) { for (int q = 0; q < N; ++q) d_bn[q] = sqrt(res[q]); }));
+    std::vector<double> bn(N);
+    DLZ_TRY(d2h_sync(op, bn.data(), d_bn, N * sizeof(double)));
+    for (int q = 0; q < N; ++q) {
+        std::memset(&st[q], 0, sizeof(dlz_stats));
+        if (!std::isfinite(bn[q])) return fail(DLZ_ERR_NONFINITE, "right-hand side is not finite");
+    }
+    DLZ_CUDA_TRY(cudaMemsetAsync(px, 0, (size_t)N * n64 * sizeof(double2), op.stream));
+    std::vector<char> done(N, 0);
+    std::vector<double> rn(N);
+    int iters = 0, outer = 0;
+    long long mv_batch = 0;
+    auto residuals = [&]() -> int {
+        DLZ_TRY(wilson64_batch(op, pt, px, DLZ_Q, N));
+        mv_batch += 1;
+        DLZ_TRY(reduce<kMaxBatch>(op, n64, [=] __device__(long i, double (&acc)[kMaxBatch]) {
+#pragma unroll
+            for (int q = 0; q < kMaxBatch; ++q) {
+                if (q < N) {
+                    const size_t o = (size_t)q * n64 + i;
+                    const double2 a = pbp[o], c = pt[o];
+                    const double2 t = make_double2(a.x - c.x, a.y - c.y);
+                    pr[o] = t;
+                    acc[q] += t.x * t.x + t.y * t.y;
+                }
+            }
+        }, [=] __device__(const double *res) { for (int q = 0; q < N; ++q) d_rn[q] = sqrt(res[q]); }));
+        DLZ_TRY(d2h_sync(op, rn.data(), d_rn, N * sizeof(double)));
+        for (int q = 0; q < N; ++q)
+            if (!std::isfinite(rn[q])) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
+        return DLZ_OK;
+    };
+    while (true) {
+        DLZ_TRY(residuals());
+        bool all = true;
+        for (int q = 0; q < N; ++q) {
+            if (!done[q] && (bn[q] == 0.0 || rn[q] <= p.tol * bn[q])) {
+                done[q] = 1;
+                st[q].iterations = iters;
+                st[q].cycles = outer;
+            }
+            all = all && done[q];
+        }
+        if (all || iters >= p.max_iter) break;
+        if (d && d->k > 0) {
+            // Galerkin projection of each open residual over the deflation set
+            for (int q = 0; q < N; ++q) {
+                if (done[q]) continue;
+                double2 *xq = px + (size_t)q * n64;
+                DLZ_TRY(project64(op, d, pr + (size_t)q * n64, corr.as<double2>(), dots));
+                const double2 *cc = corr.as<double2>();
+                DLZ_TRY(map(op, n64, [=] __device__(long i) {
+                    double2 a = xq[i];
+                    const double2 c = cc[i];
+                    a.x += c.x; a.y += c.y;
+                    xq[i] = a;
+                }));
+            }
+            DLZ_TRY(residuals());
+        }
+        // normalised FP32 residuals (zero for finished right-hand sides) and inner tolerances
+        std::vector<double> inv(N), tl(N);
+        for (int q = 0; q < N; ++q) {
+            const bool open = !done[q] && rn[q] > p.tol * bn[q];
+            inv[q] = open ? 1.0 / rn[q] : 0.0;
+            tl[q] = open ? std::max(0.5 * p.tol * bn[q] / rn[q], p.reliable_delta) : 1.0;
+        }
+        DLZ_TRY(h2d(op, d_inv, inv.data(), N * sizeof(double)));
+        DLZ_TRY(h2d(op, d_tol, tl.data(), N * sizeof(double)));
+        {
+            const int V = op.g.V;
+            float4 *r32 = w32[0];
+            DLZ_TRY(map(op, n32 * N, [=] __device__(long i) {
+                const int q = (int)(i / n32);
+                const long j = i % n32;
+                const int c = (int)(j / V), s = (int)(j % V);
+                const double sc = d_inv[q];
+                const double2 *src = pr + (size_t)q * n64;
+                const double2 a = src[(size_t)(2 * c) * V + s], b = src[(size_t)(2 * c + 1) * V + s];
+                r32[i] = make_float4((float)(sc * a.x), (float)(sc * a.y), (float)(sc * b.x), (float)(sc * b.y));
+            }));
+        }
+        const int it0 = iters;
+        DLZ_TRY(minres_inner32_batch(op, N, w32[0], w32[1], w32[2], w32[3], w32[4], w32[5], w32[6], ist, d_tol,
+                                     p, iters, hs));
+        mv_batch += iters - it0;
+        // x_q += ||r_q|| e_q
+        {
+            const int V = op.g.V;
+            const float4 *e32 = w32[1];
+            DLZ_TRY(map(op, n32 * N, [=] __device__(long i) {
+                const int q = (int)(i / n32);
+                const double sc = d_inv[q] > 0.0 ? 1.0 / d_inv[q] : 0.0;
+                const long j = i % n32;
+                const int c = (int)(j / V), s = (int)(j % V);
+                const float4 qv = e32[i];
+                double2 *xq = px + (size_t)q * n64;
+                double2 &a = xq[(size_t)(2 * c) * V + s];
+                double2 &b = xq[(size_t)(2 * c + 1) * V + s];
+                a.x += sc * qv.x; a.y += sc * qv.y; b.x += sc * qv.z; b.y += sc * qv.w;
+            }));
+        }
+        ++outer;
+    }
+    DLZ_CUDA_TRY(cudaMemcpyAsync(X, px, (size_t)N * n64 * sizeof(double2), cudaMemcpyDeviceToDevice, op.stream));
+    DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+    int rc = DLZ_OK;
+    for (int q = 0; q < N; ++q) {
+        st[q].true_residual = bn[q] > 0 ? rn[q] / bn[q] : 0.0;
+        st[q].converged = done[q] ? 1 : 0;
+        if (!done[q]) { st[q].iterations = iters; st[q].cycles = outer; rc = DLZ_ERR_NOT_CONVERGED; }
+        st[q].mvps = mv_batch;
+    }
+    return rc;
+}
+
+}  // namespace dlz

@@ -28,6 +28,42 @@ k_wilson(typename Field<T>::vec *__restrict__ out, const typename Field<T>::vec 
     Field<T>::store(out, g.V, s, o);
 }
 
+// N right-hand sides stored one after another (each nel elements); consecutive
+// blocks take the same sites of different right-hand sides, so the links they
+// share are read from L2 (and DRAM) once.
+template <typename T, bool G5IN, bool G5OUT>
+__global__ void __launch_bounds__(128)
+k_wilson_batch(typename Field<T>::vec *__restrict__ out, const typename Field<T>::vec *__restrict__ in,
+               const cx<T> *__restrict__ U, Geom g, T kappa, int nrhs, long nel) {
+    const int r = blockIdx.x % nrhs;
+    const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    cx<T> o[12];
+    wilson_site<T, G5IN, G5OUT>(s, g, kappa, in + (size_t)r * nel, U, o);
+    Field<T>::store(out + (size_t)r * nel, g.V, s, o);
+}
+
+template <typename T>
+int launch_wilson_batch(Op &op, typename Field<T>::vec *out, const typename Field<T>::vec *in,
+                        const cx<T> *U, int which, int nrhs, long nel, int threads) {
+    const Geom &g = op.g;
+    const long blocks = (long)((g.V + threads - 1) / threads) * nrhs;
+    const T kappa = (T)op.kappa;
+    op.prof.stencil_start(op.stream);
+    switch (which) {
+    case DLZ_D: k_wilson_batch<T, false, false><<<(unsigned)blocks, threads, 0, op.stream>>>(out, in, U, g, kappa, nrhs, nel); break;
+    case DLZ_DDAG: k_wilson_batch<T, true, true><<<(unsigned)blocks, threads, 0, op.stream>>>(out, in, U, g, kappa, nrhs, nel); break;
+    case DLZ_Q: k_wilson_batch<T, false, true><<<(unsigned)blocks, threads, 0, op.stream>>>(out, in, U, g, kappa, nrhs, nel); break;
+    default: return fail(DLZ_ERR_BADARG, "stencil: which must be D, DDAG or Q");
+    }
+    op.prof.stencil_stop(op.stream);
+    op.prof.launches++;
+    op.prof.stencils++;
+    op.prof.stencil_sites += (long long)g.V * nrhs;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+
 template <typename T>
 int launch_wilson(Op &op, typename Field<T>::vec *out, const typename Field<T>::vec *in,
                   const cx<T> *U, int which, int threads) {
@@ -44,6 +80,7 @@ int launch_wilson(Op &op, typename Field<T>::vec *out, const typename Field<T>::
     op.prof.stencil_stop(op.stream);
     op.prof.launches++;
     op.prof.stencils++;
+    op.prof.stencil_sites += g.V;
     DLZ_CUDA_TRY(cudaGetLastError());
     return DLZ_OK;
 }
@@ -102,6 +139,15 @@ int wilson64(Op &op, double2 *out, const double2 *in, int which) {
 }
 int wilson32(Op &op, float4 *out, const float4 *in, int which) {
     return launch_wilson<float>(op, out, in, op.gauge32.as<float2>(), which, kStencilThreads32);
+}
+
+int wilson32_batch(Op &op, float4 *out, const float4 *in, int which, int nrhs) {
+    return launch_wilson_batch<float>(op, out, in, op.gauge32.as<float2>(), which, nrhs, 6L * op.g.V,
+                                      kStencilThreads32);
+}
+int wilson64_batch(Op &op, double2 *out, const double2 *in, int which, int nrhs) {
+    return launch_wilson_batch<double>(op, out, in, op.gauge64.as<double2>(), which, nrhs, 12L * op.g.V,
+                                       kStencilThreads64);
 }
 
 int apply64(Op &op, double2 *out, const double2 *in, int which, double2 *tmp) {

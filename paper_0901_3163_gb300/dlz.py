@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int), ("cycles", ctypes.c_int),
                 ("mvps", ctypes.c_longlong), ("true_residual", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("stencil_ms", ctypes.c_double),
-                ("stencil_launches", ctypes.c_longlong), ("gpu_launches", ctypes.c_longlong)]
+                ("stencil_launches", ctypes.c_longlong), ("stencil_sites", ctypes.c_longlong),
+                ("gpu_launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -182,3 +182,62 @@ def test_deflation_save_load_roundtrip(m, case, tmp_path):
     _, s1 = m.dminres(op, defl, torch.from_numpy(B).cuda(), _params(m))
     _, s2 = m.dminres(op, d2, torch.from_numpy(B).cuda(), _params(m))
     assert s1[0].iterations == s2[0].iterations
+
+
+@pytest.mark.parametrize("minres", [True, False])
+def test_mixed_precision_dsolves_reach_fp64_tolerance(m, case, minres):
+    """FP32 stencil and vectors inside FP64 defect correction: the FP64-verified
+    residual still reaches 1e-10 and x agrees with the FP64 oracle solve."""
+    U, op, b = case
+    Aq, D, Dd, Ad = _ops(U, KAPPA)
+    fn = m.minresdr if minres else m.landr
+    _, defl, _ = fn(op, torch.from_numpy(b).cuda(), _params(m))
+    B = synth.gaussian_spinors(DIMS, [5, 6, 7])
+    p32 = _params(m, precision=m.F32)
+    solve = m.dminres if minres else m.dcg
+    X32, s32 = solve(op, defl, torch.from_numpy(B).cuda(), p32)
+    X64, s64 = solve(op, defl, torch.from_numpy(B).cuda(), _params(m))
+    for i in range(len(B)):
+        bi = B[i].reshape(-1)
+        assert s32[i].converged == 1 and s32[i].true_residual <= 1e-10
+        x32 = X32[i].cpu().numpy().reshape(-1)
+        # the oracle's FP64 residual of the mixed-precision solution
+        assert np.linalg.norm(bi - D(x32)) <= 1.01e-10 * np.linalg.norm(bi)
+        x64 = X64[i].cpu().numpy().reshape(-1)
+        rel = np.linalg.norm(x32 - x64) / np.linalg.norm(x64)
+        assert rel <= 2.5e-10 * np.linalg.norm(bi) / (0.16 * np.linalg.norm(x64)), rel
+        assert s32[i].iterations <= 3 * s64[i].iterations + 64
+
+
+@pytest.mark.parametrize("method", ["minresdr", "landr"])
+def test_mixed_precision_dr_first_rhs(m, case, method):
+    """FP32 DR phase (FP32 basis and stencil, FP64 small problem, x and residual)
+    followed by FP64 defect correction: the first right-hand side still reaches
+    1e-10 and the Rayleigh-Ritz values of the FP32-built deflation set match the
+    FP64 oracle's converged ones to their residual level."""
+    U, op, b = case
+    Aq, D, Dd, Ad = _ops(U, KAPPA)
+    bf = b.reshape(-1)
+    x32, d32, st = getattr(m, method)(op, torch.from_numpy(b).cuda(), _params(m, precision=m.F32))
+    assert st.converged == 1 and st.true_residual <= 1e-10
+    xv = x32.cpu().numpy().reshape(-1)
+    assert np.linalg.norm(bf - D(xv)) <= 1.01e-10 * np.linalg.norm(bf)
+    k, _ = m.defl_count(d32)
+    vals = np.array([m.defl_get(d32, i) for i in range(k)])
+    if method == "minresdr":
+        ro = K.minresdr(Aq, _g5(b), m=40, k=10, tol=1e-10, oversolve=2.0, max_cycles=400)
+    else:
+        bn = np.linalg.norm(bf)
+        ro = K.landr(Ad, Dd(bf), m=40, k=10, tol=1e-10, oversolve=2.0, max_cycles=400,
+                     residual=lambda xx: np.linalg.norm(bf - D(xx)) / bn)
+    ok = (vals[:, 1] <= 1e-4)
+    assert ok.sum() >= 3
+    for v, r in vals[ok]:
+        # an oracle eigenvalue estimate lies within the pair's residual
+        assert np.min(np.abs(ro.ritz_values - v)) <= r + 1e-6 * abs(v)
+    # and the FP32-built set still deflates: D-MinRes / D-CG in F32 converge faster than without it
+    B = synth.gaussian_spinors(DIMS, [11])
+    solve = m.dminres if method == "minresdr" else m.dcg
+    _, s1 = solve(op, d32, torch.from_numpy(B).cuda(), _params(m, precision=m.F32))
+    _, s0 = solve(op, None, torch.from_numpy(B).cuda(), _params(m, precision=m.F32))
+    assert s1[0].converged == 1 and s1[0].iterations < s0[0].iterations
