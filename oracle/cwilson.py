@@ -103,8 +103,13 @@ def operator(U, kappa, dims, which="D", bc_t=1):
         return D
     if which == "Ddag":
         return Dd
+    def Q(x):
+        y = D(x)
+        y.reshape(-1, 4, 3)[:, 2:, :] *= -1.0     # gamma5 in place on the fresh output
+        return y
+
     if which == "Q":
-        return lambda x: _g5(D(x))
+        return Q
     if which == "DdagD":
         return lambda x: Dd(D(x))
     raise ValueError(which)

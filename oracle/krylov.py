@@ -209,7 +209,7 @@ class LanczosBreakdown(FloatingPointError):
 
 
 def lanczos_extend(A, V, T, j0, m, kept=0, reorth_period=10, full_reorth=False,
-                   breakdown_tol=1e-14):
+                   breakdown_tol=1e-14, store=None):
     """Extend A V_j = V_{j+1} Tbar_j from j = j0 to j = m (0-based columns).
 
     V is a list of orthonormal vectors with len(V) == j0 + 1; T is the
@@ -254,7 +254,11 @@ def lanczos_extend(A, V, T, j0, m, kept=0, reorth_period=10, full_reorth=False,
         scale = max(abs(alpha), float(np.abs(T[: j + 1, : j + 1]).max()))
         if beta <= breakdown_tol * scale:
             raise LanczosBreakdown(j)
-        V.append(w / beta)
+        if store is None:
+            V.append(w / beta)
+        else:                       # preallocated (m+1) x n basis rows
+            np.multiply(w, 1.0 / beta, out=store[j + 1])
+            V.append(store[j + 1])
     return mvps
 
 
@@ -361,7 +365,10 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             return _norm(b - A(xx)) / bn
     info = SolveInfo()
     x = np.zeros_like(b)
-    V = [b / bn]
+    stores = [np.empty((m + 1, n), dtype=np.complex128), np.empty((m + 1, n), dtype=np.complex128)]
+    cur = 0
+    np.multiply(b, 1.0 / bn, out=stores[cur][0])
+    V = [stores[cur][0]]
     T = np.zeros((m + 1, m))
     c = np.zeros(m + 1)
     c[0] = bn
@@ -373,14 +380,14 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
     for cycle in range(max_cycles):
         cycles += 1
         info.mvps += lanczos_extend(A, V, T, j0, m, kept=j0, reorth_period=reorth_period,
-                                    full_reorth=full_reorth)
+                                    full_reorth=full_reorth, store=stores[cur])
         Tm = T[:m, :m]
         Anorm_est = max(Anorm_est, float(np.abs(np.linalg.eigvalsh(Tm)).max()))
         if tol_eig is None:
             tol_eig_abs = 1e-10 * Anorm_est
         else:
             tol_eig_abs = tol_eig
-        Vs = np.stack(V)            # (m+1) x n: the basis as rows, for the products below
+        Vs = stores[cur]            # (m+1) x n: the basis as rows, for the products below
         if not harmonic:
             y = sla.solve(Tm, c[:m], assume_a="sym")
             x = x + y @ Vs[:m]
@@ -432,7 +439,9 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             P = np.zeros((m + 1, k + 1))
             P[:m, :k] = G_k
             P[m, k] = 1.0
-            Vnew = list(P.T @ Vs)
+            nxt = stores[1 - cur]
+            np.matmul(P.T.astype(np.complex128), Vs, out=nxt[: k + 1])
+            Vnew = [nxt[i] for i in range(k + 1)]
             Tn = np.zeros((m + 1, m))
             Tn[:k, :k] = np.diag(theta_k)
             Tn[k, :k] = T[m, m - 1] * G_k[m - 1, :]
@@ -445,7 +454,9 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             if q @ s < 0:
                 q = -q
             P = _mgs_columns(np.hstack([np.vstack([G_k, np.zeros((1, k))]), q[:, None]]))
-            Vnew = list(P.T @ Vs)
+            nxt = stores[1 - cur]
+            np.matmul(P.T.astype(np.complex128), Vs, out=nxt[: k + 1])
+            Vnew = [nxt[i] for i in range(k + 1)]
             Tk = P.T @ T @ P[:m, :k]
             Tn = np.zeros((m + 1, m))
             Tn[: k + 1, :k] = Tk
@@ -457,13 +468,14 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             # of the periodic re-orthogonalisation over the kept vectors (Sec. 2);
             # without it the rounding-level overlap grows from cycle to cycle.
             for i in range(k):
-                Vnew[k] = Vnew[k] - _dot(Vnew[i], Vnew[k]) * Vnew[i]
-            Vnew[k] = Vnew[k] / _norm(Vnew[k])
+                Vnew[k] -= _dot(Vnew[i], Vnew[k]) * Vnew[i]
+            Vnew[k] /= _norm(Vnew[k])
         del Vs
+        cur = 1 - cur
         V, T, c, j0 = Vnew, Tn, cn, k
         if info.converged or last:
             break
-    Vk = np.stack(V[:k], axis=1)
+    Vk = np.array(np.stack(V[:k], axis=1))
     # Rayleigh-Ritz over the kept space (values reported for comparison)
     vals, Z = _rayleigh_ritz(T, k)
     Y = Vk @ Z
