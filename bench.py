@@ -93,29 +93,20 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload_inputs():
+def workload_inputs(kappa=None):
     import numpy as np
 
     import synth
     w = synth.WORKLOADS[WORKLOAD]
     dims = w["dims"]
     U = synth.su3_links(dims, w["gauge_seed"])
-    kappa = synth.kappa_for(dims, w["gauge_seed"])
+    if kappa is None:
+        kappa = synth.kappa_for(dims, w["gauge_seed"])
     V = synth.volume(dims)
     B = np.zeros((12, V, 4, 3), dtype=np.complex128)
     for a in range(12):
         B[a] = synth.point_source(dims, a // 3, a % 3)
     return w, dims, U, kappa, B
-
-
-def algorithmic_stencil(dims, form):
-    """Bytes and flops one Wilson stencil application must move / do (per site:
-    read the spinor (24 reals) and 4 links (72 reals), write 24 reals; 1320 flops
-    of the hopping term + 48 for psi - kappa*H psi)."""
-    import synth
-    V = synth.volume(dims)
-    real = 8 if form == "plain" else 4
-    return 120 * real * V, 1368 * V
 
 
 def run_ours(args):
@@ -204,30 +195,35 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     e2e_value = e2e_solved / e2e_s * world
     # roofline of the dominant kernel (the Wilson stencil), timed with events inside the steps
-    st_ms = sum(s.stencil_ms for s in stats)
-    st_n = sum(s.stencil_launches for s in stats)
-    st_sites = sum(s.stencil_sites for s in stats)
+    # the dominant kernel is the stencil of the deflated phase (all 11 right-hand sides
+    # batched into each launch in the mixed form); the first-RHS phase is reported apart
+    dstats = [s for i, s in enumerate(stats) if i % 12]
+    st_ms = sum(s.stencil_ms for s in dstats)
+    st_n = sum(s.stencil_launches for s in dstats)
+    st_bytes = sum(s.stencil_bytes for s in dstats)
     avg_ms = st_ms / max(st_n, 1)
-    nbytes, nflops = algorithmic_stencil(dims, "plain" if prec == dlz.F64 else "chosen")
-    # per launch: the site-RHS pairs one launch processes, at the per-site figure
-    import synth
-    scale = (st_sites / max(st_n, 1)) / synth.volume(dims)
-    nbytes, nflops = nbytes * scale, nflops * scale
+    bytes_per_launch = st_bytes / max(st_n, 1)
+    # flops: 1368 per site and right-hand side (bytes / reals-per-site gives site-RHS pairs)
+    real = 8 if prec == dlz.F64 else 4
     peaks, src = _peaks()
     if prec == dlz.F64:
-        # FP64 stencil: 1.375 flop/byte is past the ridge of GB300's FP64 pipe
+        # FP64 stencil, one right-hand side per launch: 1368 flops per 960 bytes is past
+        # the ridge of GB300's FP64 pipe, so the roofline is the FP64 ALU rate
+        nflops = bytes_per_launch / (120 * real) * 1368
         peak = 1.25
         roof = {"bound": "alu", "achieved": round(nflops / (avg_ms * 1e-3) / 1e12, 4),
                 "peak": peak, "unit": "TFLOP/s FP64",
                 "frac": round(nflops / (avg_ms * 1e-3) / 1e12 / peak, 4),
                 "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); measured FMA probe 1.01 at 1987 MHz",
-                "hbm_gbs": round(nbytes / (avg_ms * 1e-3) / 1e9, 1),
-                "traffic": None, "kernel": "k_wilson<double>", "avg_launch_ms": round(avg_ms, 5)}
+                "hbm_gbs": round(bytes_per_launch / (avg_ms * 1e-3) / 1e9, 1),
+                "traffic": None, "kernel": "k_wilson<double>", "avg_launch_ms": round(avg_ms, 5),
+                "bytes_per_launch": int(bytes_per_launch)}
     else:
-        ach = nbytes / (avg_ms * 1e-3) / 1e9
+        ach = bytes_per_launch / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / peaks["hbm_gbs"], 4), "peak_source": src, "traffic": None,
-                "kernel": "k_wilson<float>", "avg_launch_ms": round(avg_ms, 5)}
+                "kernel": "k_wilson_batch<float> / k_wilson<float>", "avg_launch_ms": round(avg_ms, 5),
+                "bytes_per_launch": int(bytes_per_launch)}
     dr_s = sum(s.seconds for s in stats[0::12]) / max(args.steps, 1)
     d_s = sum(s.seconds for i, s in enumerate(stats) if i % 12) / max(args.steps, 1)
     launches = sum(s.gpu_launches for s in stats) // max(args.steps, 1)
@@ -325,6 +321,51 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_stencil_only(args):
+    """The Wilson stencil alone, as the solvers launch it: FP32 batched over `nrhs`
+    right-hand sides and FP64 single, on the benchmark lattice (or --lattice),
+    timed with CUDA events over back-to-back launches (inputs larger than L2
+    when nrhs * 12.6 MB + links exceed 129 MB).  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_0901_3163_gb300 import dlz
+    dims = tuple(int(v) for v in args.lattice.split("x")) if args.lattice else synth.WORKLOADS[WORKLOAD]["dims"]
+    V = synth.volume(dims)
+    U = synth.su3_links(dims, 2)
+    op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), 0.25)
+    out = {"mode": "stencil-only", "lattice": list(dims)}
+    peaks, src = _peaks()
+    for name, dt, nrhs in (("f32_batched", torch.complex64, args.nrhs), ("f64_single", torch.complex128, 1)):
+        x = torch.randn((nrhs, V, 4, 3), dtype=dt, device="cuda")
+        st = dlz.stencil_bench(op, x, args.stencil_iters)
+        ms = st["ms"]
+        real = 4 if dt == torch.complex64 else 8
+        nbytes = V * (48 * nrhs + (48 if real == 4 else 72)) * real
+        out[name] = {"nrhs": nrhs, "avg_launch_ms": round(ms, 5), "bytes_per_launch": nbytes,
+                     "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                     "frac_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                     "fp_tflops": round(1368 * V * nrhs / (ms * 1e-3) / 1e12, 3)}
+    print(json.dumps(out), flush=True)
+
+
+def run_first_rhs_only(args):
+    """One first-right-hand-side solve (MinRes-DR(100,40) on the point source) of
+    the benchmark workload, for profiling the restart cycles; prints its stats.
+    --kappa overrides the tabulated kappa (profiling runs only)."""
+    import torch
+
+    from paper_0901_3163_gb300 import dlz
+    w, dims, U, kappa, B = workload_inputs(args.kappa)
+    op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
+    prec = dlz.F32 if args.form == "chosen" else dlz.F64
+    p = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=args.max_cycles, precision=prec)
+    x, d, st = dlz.minresdr(op, torch.from_numpy(B[0]).cuda(), p, deflate=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "first-rhs-only", "form": args.form, "kappa": kappa, "stats": st.as_dict()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,8 +376,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-mvps-per-rhs", type=int, default=600)
+    ap.add_argument("--stencil-only", action="store_true")
+    ap.add_argument("--lattice", default=None)
+    ap.add_argument("--nrhs", type=int, default=11)
+    ap.add_argument("--stencil-iters", type=int, default=50)
+    ap.add_argument("--first-rhs-only", action="store_true")
+    ap.add_argument("--max-cycles", type=int, default=4000)
+    ap.add_argument("--kappa", type=float, default=None)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.stencil_only:
+        run_stencil_only(args)
+    elif args.first_rhs_only:
+        run_first_rhs_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

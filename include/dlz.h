@@ -99,10 +99,12 @@ typedef struct {
     long long mvps;         /* applications of D or D^dagger (D^dagger D counts 2)     */
     double true_residual;   /* ||b - D x|| / ||b|| recomputed in FP64 at exit          */
     double seconds;         /* wall time of the call                                  */
-    double stencil_ms;      /* profile = 1: summed device time of stencil launches     */
-    long long stencil_launches; /* profile = 1: number of timed stencil launches       */
-    long long stencil_sites;    /* profile = 1: sites x right-hand sides those launches
-                                   processed (a batched launch counts every RHS)         */
+    double stencil_ms;      /* profile = 1: summed device time (CUDA events) of the stencil
+                               launches in the hot-loop precision (FP32 for DLZ_F32)   */
+    long long stencil_launches; /* profile = 1: number of those launches                */
+    double stencil_bytes;   /* profile = 1: their algorithmic bytes: per site 48 reals per
+                               right-hand side (spinor in and out) + 4 links (72 reals
+                               in FP64; 48 in FP32, which stores two rows per link)    */
     long long gpu_launches; /* kernels launched by this call                          */
 } dlz_stats;
 
@@ -186,7 +188,8 @@ int dlz_defl_count(dlz_defl_t d, int *k, int *which);
  * i-th Rayleigh-Ritz pair of the deflation set: eigenvalues of H in
  * ascending order, the unit vector y_i = V_k z_i (complex128 [V][4][3], host
  * or device; NULL to skip), its value y_i^dag A y_i and its residual
- * ||A y_i - value y_i|| (either pointer may be NULL).
+ * ||A y_i - value y_i|| (either pointer may be NULL).  The residuals of all k
+ * pairs are computed in FP64 on the first request for one (k MVPs).
  */
 int dlz_defl_get(dlz_defl_t d, int i, void *vec_out, double *value, double *residual);
 /* Writes the deflation set (header, H, V_k in FP64) to a file / reads it back
@@ -194,6 +197,17 @@ int dlz_defl_get(dlz_defl_t d, int i, void *vec_out, double *value, double *resi
 int dlz_defl_save(dlz_defl_t d, const char *path);
 int dlz_defl_load(dlz_op_t op, const char *path, dlz_defl_t *out);
 int dlz_defl_destroy(dlz_defl_t d);
+
+/*
+ * Measurement entry point: packs `nrhs` spinors `in` (dtype DLZ_F64:
+ * complex128, DLZ_F32: complex64, [nrhs][V][4][3], host or device) into the
+ * internal layout and launches the stencil `which` (DLZ_D, DLZ_DDAG or DLZ_Q)
+ * the way the solvers do -- all nrhs right-hand sides in one launch -- `iters`
+ * times back to back on the operator's stream, after 3 untimed launches.
+ * *ms_per_launch receives the average device time per launch (CUDA events).
+ */
+int dlz_stencil_bench(dlz_op_t op, int dtype, int which, int nrhs, int iters, const void *in,
+                      double *ms_per_launch);
 
 /*
  * Host-side dense helpers used by the restart (exported for testing; no

@@ -96,17 +96,18 @@ def sigma_min_iterative(U, kappa, dims, v0, res_tol, m=100, k=20, bc_t=1, max_cy
 
 
 def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5, seed=12345,
-                    log=None):
+                    log=None, max_cycles=2000):
     """kappa with sigma_min(D) = 1e-3 on a lattice too large for a dense eigensolve.
 
     sigma_min is min |eig(Q)|, taken from the harmonic Ritz pair nearest zero of
     MinRes-DR(100, 20) run as an eigensolver and warm-started from the previous
     eigenvector.  From `start` kappa is stepped by `step` (down while
     sigma_min < 1e-3, then up) to bracket the crossing, which is refined by
-    Illinois false position to |sigma_min/1e-3 - 1| < rtol and re-verified
-    from a fresh random start vector.  Returns (kappa, sigma_min).  The
-    default accuracy (1e-3 on sigma_min, harmonic Ritz residual 1e-5) fixes
-    the near-critical workload well enough; the dense rule uses 1e-6.
+    Illinois false position to |sigma_min/1e-3 - 1| < rtol, and re-evaluated
+    there.  Each eigensolve stops at a harmonic Ritz residual below
+    max(res_tol, 5% of |sigma - 1e-3|) or after max_cycles restart cycles
+    (the nearest-zero harmonic Ritz value of a capped run is then the
+    estimate used).  Returns (kappa, sigma_min, residual of that estimate).
     """
     V = int(np.prod(dims))
     rng = np.random.default_rng(seed)
@@ -118,7 +119,9 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5,
         def stop(theta, res):
             return res <= max(res_tol, 0.05 * abs(abs(theta) - TARGET))
 
-        s, y, res, mv = sigma_min_iterative(U, kap, dims, state["v"], stop, bc_t=bc_t, log=log)
+        s, y, res, mv = sigma_min_iterative(U, kap, dims, state["v"], stop, bc_t=bc_t, log=log,
+                                            max_cycles=max_cycles)
+        state["res"] = res
         state["v"] = y + 1e-3 * (rng.standard_normal(V * 12) + 1j * rng.standard_normal(V * 12)) / np.sqrt(V * 12)
         if log:
             log(f"kappa={kap:.10f} sigma_min={s:.10e} res={res:.2e} mvps={mv}")
@@ -136,5 +139,4 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5,
         b = a + step
         fb = f(b)
     kap = _illinois(f, a, fa, b, fb, rtol)
-    state["v"] = rng.standard_normal(V * 12) + 1j * rng.standard_normal(V * 12)
-    return kap, f(kap, res_tol) + TARGET
+    return kap, f(kap, res_tol) + TARGET, state["res"]

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -14,6 +15,9 @@
 
 struct dlz_op_s {
     dlz::Op op;
+    ~dlz_op_s() {
+        if (op.cap_stream) cudaStreamDestroy(op.cap_stream);
+    }
 };
 
 namespace dlz {
@@ -49,15 +53,34 @@ void DevBuf::release() {
     bytes = 0;
 }
 
-void Profiler::begin(bool on) {
+void Profiler::begin(bool on, bool f32) {
     enabled = on;
+    hot_f32 = f32;
     used = 0;
     launches = 0;
     stencils = 0;
-    stencil_sites = 0;
+    stencil_bytes = 0.0;
+    armed = false;
+    capture = nullptr;
+    sampled_ms = sampled_bytes = 0.0;
+    sampled = 0;
 }
-void Profiler::stencil_start(cudaStream_t s) {
-    if (!enabled) return;
+void Profiler::stencil_start(cudaStream_t s, bool f32, long long sites, int nrhs, int reals_per_rhs) {
+    armed = enabled && f32 == hot_f32;
+    if (!armed) return;
+    const double nbytes = f32 ? (double)sites * ((double)reals_per_rhs * nrhs + 48.0) * 4.0
+                              : (double)sites * ((double)reals_per_rhs * nrhs + 72.0) * 8.0;
+    if (capture) {
+        // inside a graph capture: an external event node, owned by the graph
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        capture->ev.push_back(a);
+        capture->ev.push_back(b);
+        capture->bytes.push_back(nbytes);
+        cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+        return;
+    }
     if (used + 2 > pool.size()) {
         for (int i = 0; i < 256; ++i) {
             cudaEvent_t e;
@@ -66,11 +89,19 @@ void Profiler::stencil_start(cudaStream_t s) {
         }
     }
     cudaEventRecord(pool[used], s);
+    stencils++;
+    stencil_bytes += nbytes;
 }
 void Profiler::stencil_stop(cudaStream_t s) {
-    if (!enabled) return;
+    if (!armed) return;
+    if (capture) {
+        cudaEventRecordWithFlags(capture->ev.back(), s, cudaEventRecordExternal);
+        armed = false;
+        return;
+    }
     cudaEventRecord(pool[used + 1], s);
     used += 2;
+    armed = false;
 }
 double Profiler::stencil_ms() {
     double tot = 0.0;
@@ -131,17 +162,22 @@ struct Staged {
 };
 
 // canonical gauge [4][V][9] complex128 -> FP64 planes [4][9][V] and FP32 planes; flags non-SU(3) links
-__global__ void k_gauge_pack(double2 *__restrict__ g64, float2 *__restrict__ g32,
+// FP32 copy: first two rows only, float4 planes [4][3][V] (the stencil rebuilds row 3)
+__global__ void k_gauge_pack(double2 *__restrict__ g64, float4 *__restrict__ g32,
                              const double2 *__restrict__ src, int V) {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // mu*V + s
     if (i >= 4L * V) return;
     const int mu = (int)(i / V), s = (int)(i % V);
+    double2 u[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
-        const double2 u = src[i * 9 + e];
-        g64[(size_t)(mu * 9 + e) * V + s] = u;
-        g32[(size_t)(mu * 9 + e) * V + s] = make_float2((float)u.x, (float)u.y);
+        u[e] = src[i * 9 + e];
+        g64[(size_t)(mu * 9 + e) * V + s] = u[e];
     }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        g32[(size_t)(mu * 3 + q) * V + s] =
+            make_float4((float)u[2 * q].x, (float)u[2 * q].y, (float)u[2 * q + 1].x, (float)u[2 * q + 1].y);
 }
 
 struct CountBadLinks {
@@ -202,16 +238,16 @@ struct CallStats {
     Op &op;
     dlz_stats *out;
     std::chrono::steady_clock::time_point t0;
-    CallStats(Op &o, dlz_stats *s, bool profile) : op(o), out(s), t0(std::chrono::steady_clock::now()) {
-        op.prof.begin(profile);
+    CallStats(Op &o, dlz_stats *s, bool profile, bool f32) : op(o), out(s), t0(std::chrono::steady_clock::now()) {
+        op.prof.begin(profile, f32);
     }
     void finish(dlz_stats &st) {
         st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         st.gpu_launches = op.prof.launches;
         if (op.prof.enabled) {
-            st.stencil_ms = op.prof.stencil_ms();
-            st.stencil_launches = op.prof.stencils;
-            st.stencil_sites = op.prof.stencil_sites;
+            st.stencil_ms = op.prof.stencil_ms() + op.prof.sampled_ms;
+            st.stencil_launches = op.prof.stencils + op.prof.sampled;
+            st.stencil_bytes = op.prof.stencil_bytes + op.prof.sampled_bytes;
         }
     }
 };
@@ -280,7 +316,7 @@ int dlz_create_operator(const int dims[4], const void *gauge, double kappa, int 
     auto bail = [&](int rc) { delete h; return rc; };
     int rc = op.gauge64.alloc((size_t)36 * V * sizeof(double2));
     if (rc) return bail(rc);
-    rc = op.gauge32.alloc((size_t)36 * V * sizeof(float2));
+    rc = op.gauge32.alloc((size_t)12 * V * sizeof(float4));
     if (rc) return bail(rc);
     rc = op.red_mem.alloc((kMaxDots * kRedBlocks + kMaxDots + 8) * sizeof(double));
     if (rc) return bail(rc);
@@ -289,12 +325,20 @@ int dlz_create_operator(const int dims[4], const void *gauge, double kappa, int 
     op.red.counter = reinterpret_cast<unsigned *>(op.red.result + kMaxDots);
     if (cudaMemsetAsync(op.red.counter, 0, sizeof(unsigned) * 2, op.stream) != cudaSuccess)
         return bail(fail(DLZ_ERR_CUDA, "memset"));
+    if (cudaStreamCreateWithFlags(&op.cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(DLZ_ERR_CUDA, "stream create"));
+    {
+        const char *env = std::getenv("DLZ_NO_GRAPHS");
+        op.use_graphs = !(env && env[0] == '1');
+    }
+    rc = prepare_kernels(op);
+    if (rc) return bail(rc);
     Staged g;
     rc = g.in(op, gauge, (size_t)36 * V * sizeof(double2));
     if (rc) return bail(rc);
     const double2 *src = (const double2 *)g.dev;
     k_gauge_pack<<<(int)((4 * V + 255) / 256), 256, 0, op.stream>>>(op.gauge64.as<double2>(),
-                                                                      op.gauge32.as<float2>(), src, (int)V);
+                                                                      op.gauge32.as<float4>(), src, (int)V);
     if (cudaGetLastError() != cudaSuccess) return bail(fail(DLZ_ERR_CUDA, "gauge pack launch"));
     double *d_bad = op.red.result + kMaxDots - 1;
     rc = reduce<1>(op, 4L * V, CountBadLinks{src}, [=] __device__(const double *r) { *d_bad = r[0]; });
@@ -331,7 +375,7 @@ int dlz_apply(dlz_op_t h, int which, const void *in, void *out, int dtype, int n
     if (dtype != DLZ_F64 && dtype != DLZ_F32) return fail(DLZ_ERR_BADARG, "dtype");
     if (nrhs == 0) return DLZ_OK;
     if (!in || !out) return fail(DLZ_ERR_BADARG, "null vector");
-    op.prof.begin(false);
+    op.prof.begin(false, false);
     const long n = 12L * op.g.V;
     const size_t esz = dtype == DLZ_F64 ? sizeof(double2) : sizeof(float2);
     const size_t bytes = (size_t)n * esz * nrhs;
@@ -362,6 +406,45 @@ int dlz_apply(dlz_op_t h, int which, const void *in, void *out, int dtype, int n
     return so.flush(op);
 }
 
+int dlz_stencil_bench(dlz_op_t h, int dtype, int which, int nrhs, int iters, const void *in,
+                      double *ms_per_launch) {
+    DLZ_TRY(check_op(h));
+    Op &op = h->op;
+    if (!in || !ms_per_launch || nrhs < 1 || nrhs > 64 || iters < 1) return fail(DLZ_ERR_BADARG, "stencil_bench arguments");
+    if (which != DLZ_D && which != DLZ_DDAG && which != DLZ_Q) return fail(DLZ_ERR_BADARG, "which");
+    if (dtype != DLZ_F64 && dtype != DLZ_F32) return fail(DLZ_ERR_BADARG, "dtype");
+    op.prof.begin(false, false);
+    const long n = 12L * op.g.V;
+    const size_t esz = dtype == DLZ_F64 ? sizeof(double2) : sizeof(float2);
+    Staged si;
+    DLZ_TRY(si.in(op, in, (size_t)n * nrhs * esz));
+    DevBuf a, b;
+    DLZ_TRY(a.alloc((size_t)n * nrhs * esz));
+    DLZ_TRY(b.alloc((size_t)n * nrhs * esz));
+    for (int r = 0; r < nrhs; ++r) {
+        if (dtype == DLZ_F64) DLZ_TRY(pack64(op, a.as<double2>() + (size_t)r * n, (const double2 *)si.dev + (size_t)r * n));
+        else DLZ_TRY(pack32(op, a.as<float4>() + (size_t)r * n / 2, (const float2 *)si.dev + (size_t)r * n));
+    }
+    auto launch = [&]() -> int {
+        if (dtype == DLZ_F64) return wilson64_batch(op, b.as<double2>(), a.as<double2>(), which, nrhs);
+        return wilson32_batch(op, b.as<float4>(), a.as<float4>(), which, nrhs);
+    };
+    for (int i = 0; i < 3; ++i) DLZ_TRY(launch());
+    cudaEvent_t e0, e1;
+    DLZ_CUDA_TRY(cudaEventCreate(&e0));
+    DLZ_CUDA_TRY(cudaEventCreate(&e1));
+    cudaEventRecord(e0, op.stream);
+    for (int i = 0; i < iters; ++i) DLZ_TRY(launch());
+    cudaEventRecord(e1, op.stream);
+    DLZ_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_launch = ms / iters;
+    return DLZ_OK;
+}
+
 static int dr_entry(dlz_op_t h, bool harmonic, const void *b, void *x, const dlz_params *p,
                     dlz_defl_t *defl_out, dlz_stats *stats) {
     DLZ_TRY(check_op(h));
@@ -371,7 +454,7 @@ static int dr_entry(dlz_op_t h, bool harmonic, const void *b, void *x, const dlz
     if (defl_out) *defl_out = nullptr;
     dlz_stats st;
     std::memset(&st, 0, sizeof(st));
-    CallStats cs(op, stats, p->profile != 0);
+    CallStats cs(op, stats, p->profile != 0, p->precision == DLZ_F32);
     const long n = 12L * op.g.V;
     Staged sb, sx;
     DLZ_TRY(sb.in(op, b, n * sizeof(double2)));
@@ -432,7 +515,7 @@ static int dsolve_entry(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nr
         std::vector<dlz_stats> sts(chunk);
         for (int r0 = 0; r0 < nrhs; r0 += chunk) {
             const int nb = std::min(chunk, nrhs - r0);
-            CallStats cs(op, nullptr, p->profile != 0);
+            CallStats cs(op, nullptr, p->profile != 0, p->precision == DLZ_F32);
             for (int q = 0; q < nb; ++q)
                 DLZ_TRY(pack64(op, bi.as<double2>() + (size_t)q * n, (const double2 *)sb.dev + (size_t)(r0 + q) * n));
             const int rc = dsolve_mixed_batch(op, d, true, bi.as<double2>(), xi.as<double2>(), nb, *p, sts.data());
@@ -449,7 +532,7 @@ static int dsolve_entry(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nr
                 sts[q].gpu_launches = shared.gpu_launches / nb;
                 sts[q].stencil_ms = shared.stencil_ms / nb;
                 sts[q].stencil_launches = shared.stencil_launches / nb;
-                sts[q].stencil_sites = shared.stencil_sites / nb;
+                sts[q].stencil_bytes = shared.stencil_bytes / nb;
                 if (stats) stats[r0 + q] = sts[q];
             }
         }
@@ -463,7 +546,7 @@ static int dsolve_entry(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nr
     for (int r = 0; r < nrhs; ++r) {
         dlz_stats st;
         std::memset(&st, 0, sizeof(st));
-        CallStats cs(op, nullptr, p->profile != 0);
+        CallStats cs(op, nullptr, p->profile != 0, p->precision == DLZ_F32);
         DLZ_TRY(pack64(op, bi.as<double2>(), (const double2 *)sb.dev + (size_t)r * n));
         int rc;
         if (p->precision == DLZ_F32)
@@ -503,7 +586,10 @@ int dlz_defl_get(dlz_defl_t d, int i, void *vec_out, double *value, double *resi
     if (!d) return fail(DLZ_ERR_BADARG, "null deflation set");
     if (i < 0 || i >= d->k) return fail(DLZ_ERR_BADARG, "index out of range");
     if (value) *value = d->values[i];
-    if (residual) *residual = d->residuals[i];
+    if (residual) {
+        DLZ_TRY(deflation_residuals(*d->op, d));
+        *residual = d->residuals[i];
+    }
     if (!vec_out) return DLZ_OK;
     Op &op = *d->op;
     const long n = 12L * op.g.V;

@@ -117,18 +117,32 @@ struct RedScratch {
 
 struct Op;
 
-// Launch accounting and optional stencil timing.
+// Launch accounting and optional stencil timing.  Only stencil launches in the
+// precision of the solve's hot loop (`hot_f32`) are timed, so the reported
+// average describes one kernel; each timed launch adds its algorithmic bytes:
+// per site 24 reals read + 24 written per right-hand side, plus 4 links read
+// once per site: 18 reals (FP64, 8 bytes each) or 12 reals (FP32, 4 bytes).
+struct GraphExec;
 struct Profiler {
     bool enabled = false;
+    bool hot_f32 = false;
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
-    long long launches = 0;      // all kernels
-    long long stencils = 0;      // stencil kernels
-    long long stencil_sites = 0; // lattice sites (x right-hand sides) they processed
-    void begin(bool on);
-    void stencil_start(cudaStream_t s);
+    bool armed = false;             // the current launch is being timed
+    long long launches = 0;         // all kernels
+    long long stencils = 0;         // timed stencil launches (direct)
+    double stencil_bytes = 0.0;     // their algorithmic bytes
+    // stencils inside captured graphs: timed by external event nodes of the graph,
+    // read after a host synchronisation (one replay sampled per read)
+    GraphExec *capture = nullptr;
+    double sampled_ms = 0.0, sampled_bytes = 0.0;
+    long long sampled = 0;
+    void begin(bool on, bool f32);
+    // reals_per_rhs: spinor reals moved per site and right-hand side (48 for a plain
+    // stencil: read 24, write 24; more for a stencil with a fused epilogue)
+    void stencil_start(cudaStream_t s, bool f32, long long sites, int nrhs, int reals_per_rhs = 48);
     void stencil_stop(cudaStream_t s);
-    double stencil_ms();         // synchronises the events; sums pairs
+    double stencil_ms();            // synchronises the events; sums pairs
     ~Profiler();
 };
 
@@ -136,13 +150,79 @@ struct Op {
     Geom g;
     double kappa;
     cudaStream_t stream;
+    cudaStream_t cap_stream = nullptr;   // private stream used only to capture CUDA graphs
+    bool use_graphs = true;
     DevBuf gauge64;   // double2 [4][9][V]
-    DevBuf gauge32;   // float2  [4][9][V]
+    DevBuf gauge32;   // float4  [4][3][V] (two rows)
     DevBuf red_mem;   // reduction scratch
     RedScratch red;
     Profiler prof;
     DevBuf scratch_a, scratch_b, scratch_c;  // spinor-sized scratch (FP64)
 };
+
+// ---------------------------------------------------------------- CUDA graphs
+// A launch-bound sequence of kernels (a Lanczos cycle, a group of MinRes
+// iterations on one right-hand side) is captured once on the private stream
+// and replayed on op.stream.  Stencil timing is off while capturing; the
+// launch count of the captured body is added on every replay.
+struct GraphExec {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    std::vector<cudaEvent_t> ev;      // start/stop pairs of the timed stencils
+    std::vector<double> bytes;        // algorithmic bytes of each timed stencil
+    bool fresh = false;               // replayed since the last sample
+    GraphExec() = default;
+    GraphExec(const GraphExec &) = delete;
+    GraphExec &operator=(const GraphExec &) = delete;
+    ~GraphExec() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    // add the stencil times of the last completed replay (call after a host sync)
+    void sample(Profiler &pr) {
+        if (!fresh) return;
+        fresh = false;
+        for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) {
+                pr.sampled_ms += ms;
+                pr.sampled_bytes += bytes[i / 2];
+                pr.sampled++;
+            }
+        }
+    }
+};
+
+template <class F>
+int run_graph(Op &op, GraphExec &ge, F &&body) {
+    if (!op.use_graphs || !op.cap_stream) return body();
+    if (!ge.exec) {
+        cudaStream_t saved = op.stream;
+        const bool prof_saved = op.prof.enabled;
+        const long long l0 = op.prof.launches;
+        cudaError_t e = cudaStreamBeginCapture(op.cap_stream, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return fail(DLZ_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+        op.stream = op.cap_stream;
+        op.prof.capture = prof_saved ? &ge : nullptr;
+        const int rc = body();
+        op.stream = saved;
+        op.prof.capture = nullptr;
+        op.prof.enabled = prof_saved;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(op.cap_stream, &graph);
+        if (rc != DLZ_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (e != cudaSuccess) return fail(DLZ_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { ge.exec = nullptr; return fail(DLZ_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)); }
+        ge.launches = op.prof.launches - l0;
+        op.prof.launches = l0;
+    }
+    DLZ_CUDA_TRY(cudaGraphLaunch(ge.exec, op.stream));
+    op.prof.launches += ge.launches;
+    ge.fresh = true;
+    return DLZ_OK;
+}
 
 // ---------------------------------------------------------------- kernels (launchers)
 // Wilson stencil: out = [g5_out] (1 - kappa H) [g5_in] in, FP64 or FP32.

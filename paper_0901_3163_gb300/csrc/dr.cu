@@ -17,8 +17,12 @@
 // or meets tol; the caller then finishes the solve by FP64 defect correction
 // over the deflation set it produced.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <complex>
+#include <cstring>
 #include <vector>
 
 #include "dlz_internal.cuh"
@@ -45,8 +49,11 @@ int plan_restart(bool harmonic, int m, int k, const std::vector<double> &T, cons
     std::vector<double> Tm((size_t)m * m);
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < m; ++j) Tm[(size_t)i * m + j] = T[(size_t)i * m + j];
-    std::vector<double> ev(m), G((size_t)m * m);
-    if (!sym_eig(m, Tm.data(), ev.data(), G.data())) return fail(DLZ_ERR_NONFINITE, "eig(T_m) failed");
+    std::vector<double> ev(m), G;
+    // Lan-DR needs the Ritz vectors of T_m; MinRes-DR only its extreme eigenvalues (||A|| estimate)
+    if (!harmonic) G.resize((size_t)m * m);
+    if (!sym_eig(m, Tm.data(), ev.data(), harmonic ? nullptr : G.data()))
+        return fail(DLZ_ERR_NONFINITE, "eig(T_m) failed");
     Anorm = std::max(Anorm, std::max(std::fabs(ev[0]), std::fabs(ev[m - 1])));
     o.y.assign(m, 0.0);
     o.P.assign((size_t)(m + 1) * (k + 1), 0.0);
@@ -281,17 +288,27 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
     int cycle = 0;
     double *coefr = coef.as<double>();
     std::vector<double> hist;
+    GraphExec g_first, g_a, g_b;
+    // DLZ_TRACE=1: per-phase wall times on stderr (diagnostics)
+    const char *trace_env = std::getenv("DLZ_TRACE");
+    const bool trace = trace_env && trace_env[0] == '1';
+    double t_lanczos = 0, t_host = 0, t_restart = 0;
+    auto now = [] { return std::chrono::steady_clock::now(); };
+    auto secs = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+        return std::chrono::duration<double>(b - a).count();
+    };
     for (cycle = 0; cycle < p.max_cycles; ++cycle) {
+        const auto tc0 = now();
         // ---------------- Lanczos steps j0 .. m-1
         if (j0 > 0) {
             std::vector<double> cp(j0);                 // coupling of v_{k+1} to the kept vectors
             for (int i = 0; i < j0; ++i) cp[i] = -T[(size_t)j0 * m + i];
             DLZ_TRY(h2d(op, coefr, cp.data(), j0 * sizeof(double)));
         }
+        auto lanczos_steps = [&]() -> int {
         for (int j = j0; j < m; ++j) {
             E *vj = V + (size_t)j * n, *wv = w.as<E>();
             DLZ_TRY(P::apply(op, wv, vj, which, tmp.as<E>()));
-            st.mvps += mv_per;
             if (j == j0 && j0 > 0) DLZ_TRY(combine<P>(op, wv, n, 1, V, n, j0, coefr, 1, true, true));
             const E *vprev = (j > j0) ? V + (size_t)(j - 1) * n : nullptr;
             const double *bprev = (j > j0) ? d_beta + (j - 1) : nullptr;
@@ -321,10 +338,18 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
             }
             E *vn = V + (size_t)(j + 1) * n;
             DLZ_TRY(map(op, n, [=] __device__(long i) { vn[i] = P::scal(1.0 / *bj, wv[i]); }));
-            st.iterations++;
         }
+        return DLZ_OK;
+        };
+        // the steps of a cycle are the same kernels with the same arguments from one
+        // cycle to the next (per basis buffer): capture them once, replay them
+        GraphExec &ge = (j0 == 0) ? g_first : (V == Va.as<E>() ? g_a : g_b);
+        DLZ_TRY(run_graph(op, ge, lanczos_steps));
+        st.mvps += (long long)(m - j0) * mv_per;
+        st.iterations += m - j0;
         // ---------------- small problem on the host
         DLZ_TRY(d2h_sync(op, hs.p, d_alpha, 2 * m * sizeof(double)));
+        ge.sample(op.prof);
         double tmax = 0.0;
         for (int j = j0; j < m; ++j) {
             const double a = hs.p[j], bt = hs.p[m + j];
@@ -339,8 +364,10 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         for (int j = j0; j < m; ++j)
             if (hs.p[m + j] <= 1e-14 * std::max(tmax, Anorm))
                 return fail(DLZ_ERR_BREAKDOWN, "Lanczos breakdown (invariant subspace)");
+        const auto tc1 = now();
         RestartPlan pl;
         DLZ_TRY(plan_restart(harmonic, m, k, T, c, Anorm, pl));
+        const auto tc2 = now();
         // FP32 basis: Ritz residuals below ~1e-5 ||A|| are under its rounding level
         const double tol_eig = p.tol_eig > 0 ? p.tol_eig : (P::kF32 ? 1e-5 : 1e-10) * Anorm;
         // ---------------- x += V_m y ; true residual ||b - D x|| / ||b|| in FP64
@@ -364,6 +391,10 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
             DLZ_TRY(map(op, n, [=] __device__(long i) { vk[i] = P::scal(*nrm, vk[i]); }));
         }
         DLZ_TRY(d2h_sync(op, hs.p, d_norm + 2, sizeof(double)));
+        const auto tc3 = now();
+        t_lanczos += secs(tc0, tc1);
+        t_host += secs(tc1, tc2);
+        t_restart += secs(tc2, tc3);
         const double rel = std::sqrt(hs.p[0]) / bnorm;
         st.true_residual = rel;
         if (!std::isfinite(rel)) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
@@ -391,6 +422,7 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
     st.cycles = cycle;
     st.converged = (converged && st.true_residual <= p.tol) ? 1 : 0;
     DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
+    const auto td0 = now();
     if (defl_out) {
         DevBuf V64;
         double2 *vk64;
@@ -404,7 +436,19 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         DLZ_TRY(build_deflation(op, which, vk64, k, defl_out));
     }
     DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+    if (trace)
+        std::fprintf(stderr, "[dlz] DR(%s, %s) cycles %d steps %d: lanczos %.4f s, small problem %.4f s, "
+                     "restart+residual %.4f s, deflation set %.4f s\n", harmonic ? "MinRes" : "Lan",
+                     P::kF32 ? "f32" : "f64", cycle, st.iterations, t_lanczos, t_host, t_restart, secs(td0, now()));
     return converged ? DLZ_OK : DLZ_ERR_NOT_CONVERGED;
+}
+
+// Kernel attributes that must be set before any graph capture.
+int prepare_kernels(Op &op) {
+    DLZ_TRY(combine<P64>(op, nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, true, false));
+    DLZ_TRY(combine<P32>(op, nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, true, false));
+    DLZ_TRY(combine64(op, nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, true, false));
+    return DLZ_OK;
 }
 
 int dr_solve(Op &op, bool harmonic, const double2 *b, double2 *x, const dlz_params &p,
@@ -418,10 +462,11 @@ int dr_solve(Op &op, bool harmonic, const double2 *b, double2 *x, const dlz_para
         return rc;
     }
     if (st.true_residual > p.tol) {
-        dlz_stats s2 = st;
-        rc = dsolve_mixed(op, d, harmonic, b, x, p, s2, x);
-        st.iterations = s2.iterations;
-        st.mvps = s2.mvps;
+        dlz_stats s2;
+        std::memset(&s2, 0, sizeof(s2));
+        rc = dsolve_mixed_batch(op, d, harmonic, b, x, 1, p, &s2, x);
+        st.iterations += s2.iterations;
+        st.mvps += s2.mvps;
         st.true_residual = s2.true_residual;
         st.converged = s2.converged;
     } else {

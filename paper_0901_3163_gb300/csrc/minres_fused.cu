@@ -1,0 +1,241 @@
+// Fused FP32 MinRes iteration for a batch of right-hand sides (the inner
+// solve of the mixed-precision D-MinRes, arXiv:0901.3163 Sec. 2).
+//
+// Three launches per iteration (two of them full passes) instead of four:
+//   K1 (stencil + epilogue, one block = 128 sites of one right-hand side):
+//        v_j   = u_j / beta_j                      (u_j: unnormalised Lanczos vector)
+//        w     = Q v_j - beta_j v_{j-1}            (Q u_j / beta_j: Q is linear)
+//        alpha_j partial = Re <v_j, w>
+//        d_{j-1} = (v_{j-1} - delta d_{j-2} - eps d_{j-3}) / gamma,  e += tau d_{j-1}
+//        (the direction update of the previous step: its Givens rotation needed
+//         beta_j, known only now)
+//   K1b: alpha_j = sum of K1's block partials (one block per right-hand side);
+//   K2 (reduction): u_{j+1} = w - alpha_j v_j, beta_{j+1} = ||u_{j+1}||, and the
+//        Givens rotation of step j in the finisher.
+// The alpha partials of K1 (one per block, block b belongs to right-hand side
+// b mod N) are summed in a fixed order by a one-block-per-RHS kernel, so
+// results are deterministic.  Buffers rotate with period 2, so a group of 6 iterations is
+// captured once as a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dlz_internal.cuh"
+#include "krylov_util.cuh"
+#include "reduce.cuh"
+#include "solvers.h"
+#include "wilson_site.cuh"
+
+namespace dlz {
+
+struct FusedState {          // one per right-hand side (FP64 scalars)
+    double beta, alpha, beta_next, inv_beta;
+    double c, s, c_old, s_old, phibar;
+    double eps, delta, gamma, tau;
+    double r0, pad0, pad1;   // r0 = ||r|| at the start of the inner solve
+};
+
+namespace {
+
+constexpr int kThreads = 128;
+
+__device__ inline float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+
+__global__ void __launch_bounds__(kThreads)
+k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Vp, float4 *__restrict__ Vc,
+            float4 *__restrict__ W, const float4 *__restrict__ D2, float4 *__restrict__ D3,
+            float4 *__restrict__ E, const float4 *__restrict__ links, Geom g, float kappa, int N,
+            FusedState *__restrict__ st, double *__restrict__ partials) {
+    const int q = blockIdx.x % N;
+    const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
+    const long nel = 6L * g.V;
+    const size_t base = (size_t)q * nel;
+    double acc = 0.0;
+    if (s < g.V) {
+        const FusedState sc = st[q];
+        const float ib = (float)sc.inv_beta, bt = (float)sc.beta_next;
+        const float de = (float)sc.delta, ep = (float)sc.eps, ig = (float)(1.0 / sc.gamma), ta = (float)sc.tau;
+        float2 o[12];
+        wilson_site<float, false, true>(s, g, kappa, Ub + base, links, o);   // Q u_j
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const size_t i = base + (size_t)c * g.V + s;
+            const float4 u = Ub[i], vp = Vp[i], d2 = D2[i], d3 = D3[i];
+            const float4 vj = f4(u.x * ib, u.y * ib, u.z * ib, u.w * ib);
+            const float4 w = f4(o[2 * c].x * ib - bt * vp.x, o[2 * c].y * ib - bt * vp.y,
+                                o[2 * c + 1].x * ib - bt * vp.z, o[2 * c + 1].y * ib - bt * vp.w);
+            Vc[i] = vj;
+            W[i] = w;
+            acc += (double)(vj.x * w.x + vj.y * w.y) + (double)(vj.z * w.z + vj.w * w.w);
+            const float4 dn = f4((vp.x - de * d2.x - ep * d3.x) * ig, (vp.y - de * d2.y - ep * d3.y) * ig,
+                                 (vp.z - de * d2.z - ep * d3.z) * ig, (vp.w - de * d2.w - ep * d3.w) * ig);
+            D3[i] = dn;
+            float4 ev = E[i];
+            ev.x = fmaf(ta, dn.x, ev.x); ev.y = fmaf(ta, dn.y, ev.y);
+            ev.z = fmaf(ta, dn.z, ev.z); ev.w = fmaf(ta, dn.w, ev.w);
+            E[i] = ev;
+        }
+    }
+    // block partial of alpha_q, stored contiguously per right-hand side
+    __shared__ double sm[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) t += sm[w];
+        partials[(size_t)q * (gridDim.x / N) + blockIdx.x / N] = t;
+    }
+}
+
+// alpha_q = sum of the block partials of right-hand side q (block q of the grid),
+// in a fixed order
+__global__ void __launch_bounds__(256)
+k_minres_alpha(const double *__restrict__ partials, int nbq, FusedState *__restrict__ st) {
+    const int q = blockIdx.x;
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nbq; b += blockDim.x) t += partials[(size_t)q * nbq + b];
+    __shared__ double sm[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) a += sm[w];
+        st[q].beta = st[q].beta_next;
+        st[q].alpha = a;
+    }
+}
+
+}  // namespace
+
+int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const bufs[6],
+                       FusedState *ms, double *partials, const double *d_tol,
+                       const dlz_params &p, int &iters, HostScratch &hs) {
+    const long n = 6L * op.g.V;
+    // beta_1 = ||r_q||, rotations reset, a no-op direction update for step 0
+    DLZ_TRY(reduce<16>(op, n, [=] __device__(long i, double (&acc)[16]) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (q < N) { const float4 v = r[(size_t)q * n + i]; acc[q] += (double)(v.x * v.x + v.y * v.y) + (double)(v.z * v.z + v.w * v.w); }
+    }, [=] __device__(const double *res) {
+        for (int q = 0; q < N; ++q) {
+            const double b = sqrt(res[q]);
+            FusedState s0 = {};
+            s0.beta_next = b; s0.inv_beta = b > 0 ? 1.0 / b : 0.0;
+            s0.c = 1.0; s0.c_old = 1.0; s0.phibar = b; s0.gamma = 1.0; s0.r0 = b;
+            ms[q] = s0;
+        }
+    }));
+    float4 *U0 = bufs[0], *Vp0 = bufs[1], *Vc0 = bufs[2], *W0 = bufs[3], *D20 = bufs[4], *D30 = bufs[5];
+    DLZ_CUDA_TRY(cudaMemcpyAsync(U0, r, (size_t)N * n * sizeof(float4), cudaMemcpyDeviceToDevice, op.stream));
+    for (float4 *z : {Vp0, D20, D30, e})
+        DLZ_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)N * n * sizeof(float4), op.stream));
+    const Geom g = op.g;
+    const float kappa = (float)op.kappa;
+    const float4 *links = op.gauge32.as<float4>();
+    const unsigned blocks = (unsigned)(((g.V + kThreads - 1) / kThreads) * N);
+    auto iteration = [&](float4 *U, float4 *Vp, float4 *Vc, float4 *W, float4 *D2, float4 *D3) -> int {
+        // K1 moves 216 reals per site and right-hand side: u, v_{j-1}, d_{j-2}, d_{j-3}, e
+        // read; v_j, w, d_{j-1}, e written (24 each), plus the links once per site
+        op.prof.stencil_start(op.stream, true, g.V, N, 216);
+        k_minres_k1<<<blocks, kThreads, 0, op.stream>>>(U, Vp, Vc, W, D2, D3, e, links, g, kappa, N, ms,
+                                                         partials);
+        op.prof.stencil_stop(op.stream);
+        k_minres_alpha<<<N, 256, 0, op.stream>>>(partials, (int)(blocks / N), ms);
+        op.prof.launches += 2;
+        DLZ_CUDA_TRY(cudaGetLastError());
+        // u_{j+1} = w - alpha v_j ; beta_{j+1} ; Givens rotation of step j
+        const float4 *vc = Vc;
+        float4 *w = W;
+        return reduce<16>(op, n, [=] __device__(long i, double (&acc)[16]) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                if (q < N) {
+                    const size_t o = (size_t)q * n + i;
+                    const float al = (float)ms[q].alpha;
+                    const float4 a = w[o], v = vc[o];
+                    const float4 t = f4(fmaf(-al, v.x, a.x), fmaf(-al, v.y, a.y), fmaf(-al, v.z, a.z), fmaf(-al, v.w, a.w));
+                    w[o] = t;
+                    acc[q] += (double)(t.x * t.x + t.y * t.y) + (double)(t.z * t.z + t.w * t.w);
+                }
+            }
+        }, [=] __device__(const double *res) {
+            for (int q = 0; q < N; ++q) {
+                FusedState s = ms[q];
+                const double bn = sqrt(res[q]);
+                const double eps = s.s_old * s.beta;
+                const double deltabar = s.c_old * s.beta;
+                const double delta = s.c * deltabar + s.s * s.alpha;
+                const double gammabar = -s.s * deltabar + s.c * s.alpha;
+                double gamma = hypot(gammabar, bn);
+                double cn = 1.0, sn = 0.0;
+                if (gamma > 0.0) { cn = gammabar / gamma; sn = bn / gamma; }
+                else gamma = 1.0;            // zero right-hand side: hold a no-op
+                s.tau = cn * s.phibar;
+                s.phibar = -sn * s.phibar;
+                s.eps = eps; s.delta = delta; s.gamma = gamma;
+                s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
+                s.beta_next = bn;
+                s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
+                ms[q] = s;
+            }
+        });
+    };
+    GraphExec ge;
+    auto six = [&]() -> int {
+        float4 *U = U0, *Vp = Vp0, *Vc = Vc0, *W = W0, *D2 = D20, *D3 = D30;
+        for (int sub = 0; sub < 6; ++sub) {
+            DLZ_TRY(iteration(U, Vp, Vc, W, D2, D3));
+            float4 *tU = U, *tVp = Vp;
+            U = W; Vp = Vc; Vc = tVp; W = tU;     // (U, Vp, Vc, W) -> (W, Vc, Vp, U)
+            std::swap(D2, D3);
+        }
+        return DLZ_OK;
+    };
+    const int check = std::max(6, (p.check_every / 6) * 6);
+    int it = 0;
+    while (iters < p.max_iter) {
+        DLZ_TRY(run_graph(op, ge, six));
+        iters += 6;
+        it += 6;
+        if (it % check == 0 || iters >= p.max_iter) {
+            DLZ_TRY(d2h_sync(op, hs.p, ms, N * sizeof(FusedState)));
+            ge.sample(op.prof);
+            const FusedState *h = reinterpret_cast<const FusedState *>(hs.p);
+            bool done = true;
+            for (int q = 0; q < N; ++q)
+                if (!std::isfinite(h[q].phibar)) return fail(DLZ_ERR_NONFINITE, "MinRes residual not finite");
+            DLZ_TRY(d2h_sync(op, hs.p + 512, d_tol, N * sizeof(double)));
+            for (int q = 0; q < N; ++q) {
+                const FusedState *hq = reinterpret_cast<const FusedState *>(hs.p) + q;
+                if (!(std::fabs(hq->phibar) <= hs.p[512 + q] * hq->r0 || hq->beta_next == 0.0)) done = false;
+            }
+            if (done) break;
+        }
+    }
+    // the direction update of the last step (after 6k steps the buffers are back
+    // in their starting roles: v_J in Vp, d_{J-1} in D2, d_{J-2} in D3)
+    {
+        const float4 *vj = Vp0, *d2 = D20, *d3 = D30;
+        float4 *ee = e;
+        DLZ_TRY(map(op, n * N, [=] __device__(long i) {
+            const int q = (int)(i / n);
+            const FusedState &sc = ms[q];
+            const float de = (float)sc.delta, ep = (float)sc.eps, ig = (float)(1.0 / sc.gamma), ta = (float)sc.tau;
+            const float4 vp = vj[i], a = d2[i], b = d3[i];
+            const float4 dn = f4((vp.x - de * a.x - ep * b.x) * ig, (vp.y - de * a.y - ep * b.y) * ig,
+                                 (vp.z - de * a.z - ep * b.z) * ig, (vp.w - de * a.w - ep * b.w) * ig);
+            float4 ev = ee[i];
+            ev.x = fmaf(ta, dn.x, ev.x); ev.y = fmaf(ta, dn.y, ev.y);
+            ev.z = fmaf(ta, dn.z, ev.z); ev.w = fmaf(ta, dn.w, ev.w);
+            ee[i] = ev;
+        }));
+    }
+    return DLZ_OK;
+}
+
+}  // namespace dlz

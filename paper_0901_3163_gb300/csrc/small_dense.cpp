@@ -22,12 +22,16 @@ namespace {
 
 inline double sgn1(double x) { return x >= 0.0 ? 1.0 : -1.0; }
 
-// Reduce symmetric a (n x n) to tridiagonal form Q^T a Q; returns d, e, Q.
+// Reduce symmetric a (n x n) to tridiagonal form Q^T a Q; returns d, e and, if
+// want_q, Qt = Q^T (row i of Qt is column i of Q, so the later plane rotations
+// touch two contiguous rows).
 void tridiagonalise(int n, std::vector<double> &a, std::vector<double> &d, std::vector<double> &e,
-                    std::vector<double> &Q) {
-    Q.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
-    std::vector<double> v(n), p(n), q(n);
+                    std::vector<double> &Qt, bool want_q) {
+    if (want_q) {
+        Qt.assign((size_t)n * n, 0.0);
+        for (int i = 0; i < n; ++i) Qt[(size_t)i * n + i] = 1.0;
+    }
+    std::vector<double> v(n), p(n), q(n), sc(n);
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;          // length of the column below the diagonal
         double alpha = 0.0;
@@ -59,13 +63,18 @@ void tridiagonalise(int n, std::vector<double> &a, std::vector<double> &d, std::
         }
         a[(size_t)(k + 1) * n + k] = a[(size_t)k * n + k + 1] = alpha;
         for (int i = 1; i < m; ++i) a[(size_t)(k + 1 + i) * n + k] = a[(size_t)k * n + k + 1 + i] = 0.0;
-        // Q <- Q H on columns k+1..n-1
-        for (int r = 0; r < n; ++r) {
-            double *row = &Q[(size_t)r * n + k + 1];
-            double s = 0.0;
-            for (int j = 0; j < m; ++j) s += row[j] * v[j];
-            s *= tau;
-            for (int j = 0; j < m; ++j) row[j] -= s * v[j];
+        if (want_q) {
+            // Q <- Q H on columns k+1..n-1, i.e. Qt <- H Qt on rows k+1..n-1
+            for (int c = 0; c < n; ++c) sc[c] = 0.0;
+            for (int i = 0; i < m; ++i) {
+                const double *row = &Qt[(size_t)(k + 1 + i) * n];
+                for (int c = 0; c < n; ++c) sc[c] += v[i] * row[c];
+            }
+            for (int i = 0; i < m; ++i) {
+                double *row = &Qt[(size_t)(k + 1 + i) * n];
+                const double f = tau * v[i];
+                for (int c = 0; c < n; ++c) row[c] -= f * sc[c];
+            }
         }
     }
     d.resize(n);
@@ -75,7 +84,7 @@ void tridiagonalise(int n, std::vector<double> &a, std::vector<double> &d, std::
 }
 
 // Implicit symmetric QR with Wilkinson shifts on (d, e); rotations accumulated into Q.
-bool tridiagonal_qr(int n, std::vector<double> &d, std::vector<double> &e, std::vector<double> &Q) {
+bool tridiagonal_qr(int n, std::vector<double> &d, std::vector<double> &e, std::vector<double> &Qt, bool want_q) {
     const double eps = 2.2e-16;
     int h = n - 1;
     long iter = 0;
@@ -108,11 +117,14 @@ bool tridiagonal_qr(int n, std::vector<double> &d, std::vector<double> &e, std::
                 e[k + 1] = c * e[k + 1];
                 x = e[k];
             }
-            for (int r2 = 0; r2 < n; ++r2) {
-                double *row = &Q[(size_t)r2 * n];
-                const double qk = row[k], qk1 = row[k + 1];
-                row[k] = c * qk + s * qk1;
-                row[k + 1] = -s * qk + c * qk1;
+            if (want_q) {
+                // columns k, k+1 of Q = rows k, k+1 of Qt
+                double *rk = &Qt[(size_t)k * n], *rk1 = &Qt[(size_t)(k + 1) * n];
+                for (int r2 = 0; r2 < n; ++r2) {
+                    const double qk = rk[r2], qk1 = rk1[r2];
+                    rk[r2] = c * qk + s * qk1;
+                    rk1[r2] = -s * qk + c * qk1;
+                }
             }
         }
     }
@@ -130,14 +142,16 @@ bool sym_eig(int n, const double *A, double *w, double *Z) {
             const double s = 0.5 * (a[(size_t)i * n + j] + a[(size_t)j * n + i]);
             a[(size_t)i * n + j] = a[(size_t)j * n + i] = s;
         }
-    tridiagonalise(n, a, d, e, Q);
-    if (!tridiagonal_qr(n, d, e, Q)) return false;
+    const bool want_q = Z != nullptr;
+    tridiagonalise(n, a, d, e, Q, want_q);
+    if (!tridiagonal_qr(n, d, e, Q, want_q)) return false;
     std::vector<int> idx(n);
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return d[x] < d[y]; });
     for (int j = 0; j < n; ++j) {
         w[j] = d[idx[j]];
-        for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = Q[(size_t)i * n + idx[j]];
+        if (want_q)
+            for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = Q[(size_t)idx[j] * n + i];
     }
     return true;
 }

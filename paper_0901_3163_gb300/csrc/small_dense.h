@@ -8,7 +8,8 @@
 namespace dlz {
 
 // Eigen-decomposition of symmetric A (n x n): w ascending, column j of Z the
-// eigenvector of w[j].  false if the QR iteration did not converge.
+// eigenvector of w[j] (Z may be null: eigenvalues only).  false if the QR
+// iteration did not converge.
 bool sym_eig(int n, const double *A, double *w, double *Z);
 // y = argmin ||c - T y|| (rows > cols); q (optional, rows == cols + 1): unit
 // vector orthogonal to range(T).

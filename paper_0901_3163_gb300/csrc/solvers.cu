@@ -49,13 +49,13 @@ int deflation_finish(Op &op, dlz_defl_s *d) {
     const int k = d->k;
     const long n = 12L * op.g.V;
     if (k == 0) return DLZ_OK;
-    DevBuf AV, tmp, dots, Y, AY, coef;
-    DLZ_TRY(AV.alloc((size_t)k * n * sizeof(double2)));
+    DevBuf AV, tmp, dots;
+    DLZ_TRY(AV.alloc((size_t)n * sizeof(double2)));
     DLZ_TRY(tmp.alloc((size_t)n * sizeof(double2)));
     DLZ_TRY(dots.alloc((size_t)k * k * sizeof(double2)));
     const double2 *V = d->V64.as<double2>();
     for (int j = 0; j < k; ++j) {
-        double2 *avj = AV.as<double2>() + (size_t)j * n;
+        double2 *avj = AV.as<double2>();
         DLZ_TRY(apply64(op, avj, V + (size_t)j * n, d->which, tmp.as<double2>()));
         DLZ_TRY(v64::multidot(op, V, n, k, avj, dots.as<double2>() + (size_t)j * k, 1.0));
     }
@@ -110,7 +110,18 @@ int deflation_finish(Op &op, dlz_defl_s *d) {
     d->Z.resize((size_t)k * k);
     for (int i = 0; i < k; ++i)
         for (int j = 0; j < k; ++j) d->Z[(size_t)i * k + j] = chosen[j][i];   // column j = vector j
-    // residuals ||A y_j - value_j y_j|| with y = V Z, A y = (A V) Z
+    d->residuals.clear();   // computed on first request (deflation_residuals)
+    return DLZ_OK;
+}
+
+// ||A y_j - value_j y_j|| for the Rayleigh-Ritz pairs, y = V Z (k MVPs).
+int deflation_residuals(Op &op, dlz_defl_s *d) {
+    const int k = d->k;
+    const long n = 12L * op.g.V;
+    if (k == 0 || (int)d->residuals.size() == k) return DLZ_OK;
+    const double2 *V = d->V64.as<double2>();
+    DevBuf Y, AY, coef, tmp;
+    DLZ_TRY(tmp.alloc((size_t)n * sizeof(double2)));
     DLZ_TRY(Y.alloc((size_t)k * n * sizeof(double2)));
     DLZ_TRY(AY.alloc((size_t)k * n * sizeof(double2)));
     DLZ_TRY(coef.alloc((size_t)k * k * sizeof(double2)));
@@ -120,7 +131,9 @@ int deflation_finish(Op &op, dlz_defl_s *d) {
             zc2[(size_t)i * k + j] = make_double2(d->Z[(size_t)i * k + j].real(), d->Z[(size_t)i * k + j].imag());
     DLZ_TRY(h2d(op, coef.p, zc2.data(), zc2.size() * sizeof(double2)));
     DLZ_TRY(combine64(op, Y.as<double2>(), n, k, V, n, k, coef.p, k, false, false));
-    DLZ_TRY(combine64(op, AY.as<double2>(), n, k, AV.as<double2>(), n, k, coef.p, k, false, false));
+    for (int j = 0; j < k; ++j)
+        DLZ_TRY(apply64(op, AY.as<double2>() + (size_t)j * n, Y.as<double2>() + (size_t)j * n, d->which,
+                        tmp.as<double2>()));
     DevBuf res;
     DLZ_TRY(res.alloc((size_t)k * sizeof(double)));
     for (int j = 0; j < k; ++j) {

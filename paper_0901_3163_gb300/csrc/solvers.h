@@ -19,7 +19,7 @@ struct dlz_defl_s {
     std::vector<std::complex<double>> Hlu;      // LU factors of H
     std::vector<int> piv;
     std::vector<double> values;                 // Rayleigh-Ritz values (ascending)
-    std::vector<double> residuals;              // ||A y - value y||
+    std::vector<double> residuals;              // ||A y - value y|| (empty until requested)
     std::vector<std::complex<double>> Z;        // eigenvectors of H (column j <-> values[j])
 };
 
@@ -38,9 +38,18 @@ int dsolve_mixed(Op &op, const dlz_defl_s *d, bool minres, const double2 *b, dou
 // D-MinRes in FP32 with FP64 defect correction on N <= 16 right-hand sides at once
 // (B, X: N internal FP64 vectors one after another; st: N entries).
 int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *B, double2 *X, int N,
-                       const dlz_params &p, dlz_stats *st);
+                       const dlz_params &p, dlz_stats *st, const double2 *X_init = nullptr);
 int build_deflation(Op &op, int which, const double2 *Vk, int k, dlz_defl_s **out);
+int prepare_kernels(Op &op);
+struct FusedState;
+struct HostScratch;
+// Fused two-kernel FP32 MinRes on N right-hand sides (minres_fused.cu).
+int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const bufs[6],
+                       FusedState *ms, double *partials, const double *d_tol,
+                       const dlz_params &p, int &iters, HostScratch &hs);
 int deflation_finish(Op &op, dlz_defl_s *d);
+// Residuals of the Rayleigh-Ritz pairs (computed on first request: k MVPs).
+int deflation_residuals(Op &op, dlz_defl_s *d);
 int combine64(Op &op, double2 *out, long ld_out, int nout, const double2 *in, long ld_in, int nin,
               const void *dev_coef, int ld_coef, bool real, bool acc);
 

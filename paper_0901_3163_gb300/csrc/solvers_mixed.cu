@@ -369,7 +369,13 @@ int minres_inner32_batch(Op &op, int N, const float4 *r, float4 *e, float4 *vp, 
         vp[i] = z; d1[i] = z; d2[i] = z; e[i] = z;
     }));
     int it = 0;
-    while (iters < p.max_iter) {
+    // one graph = 6 iterations: the (v_prev, v, w) and (d1, d2) rotations return to
+    // their starting assignment after 6 steps, so the captured arguments repeat
+    GraphExec ge;
+    float4 *const vp0 = vp, *const v0 = v, *const w0 = w, *const d10 = d1, *const d20 = d2;
+    auto six = [&]() -> int {
+    float4 *vp = vp0, *v = v0, *w = w0, *d1 = d10, *d2 = d20;
+    for (int sub = 0; sub < 6; ++sub) {
         DLZ_TRY(wilson32_batch(op, w, v, DLZ_Q, N));
         {
             const float4 *a_vp = vp, *a_v = v;
@@ -449,10 +455,17 @@ int minres_inner32_batch(Op &op, int N, const float4 *r, float4 *e, float4 *vp, 
         }
         float4 *t0 = vp; vp = v; v = w; w = t0;
         std::swap(d1, d2);
-        ++iters;
-        ++it;
-        if (it % p.check_every == 0 || iters >= p.max_iter) {
+    }
+    return DLZ_OK;
+    };
+    const int check = std::max(6, (p.check_every / 6) * 6);
+    while (iters < p.max_iter) {
+        DLZ_TRY(run_graph(op, ge, six));
+        iters += 6;
+        it += 6;
+        if (it % check == 0 || iters >= p.max_iter) {
             DLZ_TRY(d2h_sync(op, hs.p, ms, N * sizeof(InnerState)));
+            ge.sample(op.prof);
             const InnerState *h = reinterpret_cast<const InnerState *>(hs.p);
             bool done = true;
             for (int q = 0; q < N; ++q)
@@ -471,12 +484,13 @@ int minres_inner32_batch(Op &op, int N, const float4 *r, float4 *e, float4 *vp, 
 }  // namespace
 
 int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *B, double2 *X, int N,
-                       const dlz_params &p, dlz_stats *st) {
+                       const dlz_params &p, dlz_stats *st, const double2 *X_init) {
     if (N < 1 || N > kMaxBatch) return fail(DLZ_ERR_BADARG, "batch size");
     if (!minres) {
         // D-CG keeps the one-at-a-time form
         for (int q = 0; q < N; ++q)
-            DLZ_TRY(dsolve_mixed(op, d, false, B + (size_t)q * 12 * op.g.V, X + (size_t)q * 12 * op.g.V, p, st[q]));
+            DLZ_TRY(dsolve_mixed(op, d, false, B + (size_t)q * 12 * op.g.V, X + (size_t)q * 12 * op.g.V, p, st[q],
+                                 X_init ? X_init + (size_t)q * 12 * op.g.V : nullptr));
         return DLZ_OK;
     }
     const long n64 = 12L * op.g.V;
@@ -489,9 +503,12 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
     DLZ_TRY(corr.alloc(n64 * sizeof(double2)));
     DLZ_TRY(dots.alloc((size_t)std::max(1, d ? d->k : 1) * sizeof(double2)));
     DLZ_TRY(scal.alloc((size_t)(kMaxBatch * 24 + 4 * kMaxBatch) * sizeof(double)));
-    DLZ_TRY(f32.alloc((size_t)7 * N * n32 * sizeof(float4)));
-    float4 *w32[7];
-    for (int i = 0; i < 7; ++i) w32[i] = f32.as<float4>() + (size_t)i * N * n32;
+    DLZ_TRY(f32.alloc((size_t)8 * N * n32 * sizeof(float4)));
+    float4 *w32[8];
+    for (int i = 0; i < 8; ++i) w32[i] = f32.as<float4>() + (size_t)i * N * n32;
+    DevBuf fpart;
+    const long k1_blocks = (long)((op.g.V + 127) / 128) * N;
+    DLZ_TRY(fpart.alloc((size_t)k1_blocks * sizeof(double)));
     InnerState *ist = reinterpret_cast<InnerState *>(scal.as<double>());
     double *d_rn = scal.as<double>() + kMaxBatch * 24;        // ||r_q||
     double *d_inv = d_rn + kMaxBatch, *d_tol = d_inv + kMaxBatch, *d_bn = d_tol + kMaxBatch;
@@ -518,7 +535,10 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
         std::memset(&st[q], 0, sizeof(dlz_stats));
         if (!std::isfinite(bn[q])) return fail(DLZ_ERR_NONFINITE, "right-hand side is not finite");
     }
-    DLZ_CUDA_TRY(cudaMemsetAsync(px, 0, (size_t)N * n64 * sizeof(double2), op.stream));
+    if (X_init)
+        DLZ_CUDA_TRY(cudaMemcpyAsync(px, X_init, (size_t)N * n64 * sizeof(double2), cudaMemcpyDeviceToDevice, op.stream));
+    else
+        DLZ_CUDA_TRY(cudaMemsetAsync(px, 0, (size_t)N * n64 * sizeof(double2), op.stream));
     std::vector<char> done(N, 0);
     std::vector<double> rn(N);
     int iters = 0, outer = 0;
@@ -594,8 +614,9 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
             }));
         }
         const int it0 = iters;
-        DLZ_TRY(minres_inner32_batch(op, N, w32[0], w32[1], w32[2], w32[3], w32[4], w32[5], w32[6], ist, d_tol,
-                                     p, iters, hs));
+        float4 *const bufs[6] = {w32[2], w32[3], w32[4], w32[5], w32[6], w32[7]};
+        DLZ_TRY(minres_fused_batch(op, N, w32[0], w32[1], bufs, reinterpret_cast<FusedState *>(ist),
+                                   fpart.as<double>(), d_tol, p, iters, hs));
         mv_batch += iters - it0;
         // x_q += ||r_q|| e_q
         {

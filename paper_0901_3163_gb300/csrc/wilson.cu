@@ -20,7 +20,7 @@ constexpr int kStencilThreads32 = 128;
 template <typename T, bool G5IN, bool G5OUT>
 __global__ void __launch_bounds__(128)
 k_wilson(typename Field<T>::vec *__restrict__ out, const typename Field<T>::vec *__restrict__ in,
-         const cx<T> *__restrict__ U, Geom g, T kappa) {
+         const typename Link<T>::vec *__restrict__ U, Geom g, T kappa) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.V) return;
     cx<T> o[12];
@@ -34,7 +34,7 @@ k_wilson(typename Field<T>::vec *__restrict__ out, const typename Field<T>::vec 
 template <typename T, bool G5IN, bool G5OUT>
 __global__ void __launch_bounds__(128)
 k_wilson_batch(typename Field<T>::vec *__restrict__ out, const typename Field<T>::vec *__restrict__ in,
-               const cx<T> *__restrict__ U, Geom g, T kappa, int nrhs, long nel) {
+               const typename Link<T>::vec *__restrict__ U, Geom g, T kappa, int nrhs, long nel) {
     const int r = blockIdx.x % nrhs;
     const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
     if (s >= g.V) return;
@@ -45,11 +45,11 @@ k_wilson_batch(typename Field<T>::vec *__restrict__ out, const typename Field<T>
 
 template <typename T>
 int launch_wilson_batch(Op &op, typename Field<T>::vec *out, const typename Field<T>::vec *in,
-                        const cx<T> *U, int which, int nrhs, long nel, int threads) {
+                        const typename Link<T>::vec *U, int which, int nrhs, long nel, int threads) {
     const Geom &g = op.g;
     const long blocks = (long)((g.V + threads - 1) / threads) * nrhs;
     const T kappa = (T)op.kappa;
-    op.prof.stencil_start(op.stream);
+    op.prof.stencil_start(op.stream, sizeof(T) == 4, g.V, nrhs);
     switch (which) {
     case DLZ_D: k_wilson_batch<T, false, false><<<(unsigned)blocks, threads, 0, op.stream>>>(out, in, U, g, kappa, nrhs, nel); break;
     case DLZ_DDAG: k_wilson_batch<T, true, true><<<(unsigned)blocks, threads, 0, op.stream>>>(out, in, U, g, kappa, nrhs, nel); break;
@@ -58,19 +58,17 @@ int launch_wilson_batch(Op &op, typename Field<T>::vec *out, const typename Fiel
     }
     op.prof.stencil_stop(op.stream);
     op.prof.launches++;
-    op.prof.stencils++;
-    op.prof.stencil_sites += (long long)g.V * nrhs;
     DLZ_CUDA_TRY(cudaGetLastError());
     return DLZ_OK;
 }
 
 template <typename T>
 int launch_wilson(Op &op, typename Field<T>::vec *out, const typename Field<T>::vec *in,
-                  const cx<T> *U, int which, int threads) {
+                  const typename Link<T>::vec *U, int which, int threads) {
     const Geom &g = op.g;
     const int blocks = (g.V + threads - 1) / threads;
     const T kappa = (T)op.kappa;
-    op.prof.stencil_start(op.stream);
+    op.prof.stencil_start(op.stream, sizeof(T) == 4, g.V, 1);
     switch (which) {
     case DLZ_D: k_wilson<T, false, false><<<blocks, threads, 0, op.stream>>>(out, in, U, g, kappa); break;
     case DLZ_DDAG: k_wilson<T, true, true><<<blocks, threads, 0, op.stream>>>(out, in, U, g, kappa); break;
@@ -79,8 +77,6 @@ int launch_wilson(Op &op, typename Field<T>::vec *out, const typename Field<T>::
     }
     op.prof.stencil_stop(op.stream);
     op.prof.launches++;
-    op.prof.stencils++;
-    op.prof.stencil_sites += g.V;
     DLZ_CUDA_TRY(cudaGetLastError());
     return DLZ_OK;
 }
@@ -138,11 +134,11 @@ int wilson64(Op &op, double2 *out, const double2 *in, int which) {
     return launch_wilson<double>(op, out, in, op.gauge64.as<double2>(), which, kStencilThreads64);
 }
 int wilson32(Op &op, float4 *out, const float4 *in, int which) {
-    return launch_wilson<float>(op, out, in, op.gauge32.as<float2>(), which, kStencilThreads32);
+    return launch_wilson<float>(op, out, in, op.gauge32.as<float4>(), which, kStencilThreads32);
 }
 
 int wilson32_batch(Op &op, float4 *out, const float4 *in, int which, int nrhs) {
-    return launch_wilson_batch<float>(op, out, in, op.gauge32.as<float2>(), which, nrhs, 6L * op.g.V,
+    return launch_wilson_batch<float>(op, out, in, op.gauge32.as<float4>(), which, nrhs, 6L * op.g.V,
                                       kStencilThreads32);
 }
 int wilson64_batch(Op &op, double2 *out, const double2 *in, int which, int nrhs) {

@@ -57,11 +57,52 @@ template <> struct Field<float> {
     }
 };
 
-template <typename T>
-__host__ __device__ inline void load_link(const cx<T> *__restrict__ U, int V, int mu, int s,
-                                          cx<T> (&u)[9]) {
+// Link storage.  FP64: all 9 complex entries, double2 planes [4][9][V].
+// FP32: the first two rows only ("12-real" form), float4 planes [4][3][V]
+// holding (u00,u01), (u02,u10), (u11,u12); the third row of an SU(3) matrix is
+// the complex conjugate of the cross product of the first two,
+//   u2j = conj(u0k u1l - u0l u1k)  for (j,k,l) cyclic,
+// so 48 instead of 72 bytes are read per link.
+template <typename T> struct Link;
+template <> struct Link<double> {
+    typedef double2 vec;
+    static constexpr int planes = 9;
+    __host__ __device__ static inline void load(const double2 *__restrict__ U, int V, int mu, int s,
+                                                double2 (&u)[9]) {
 #pragma unroll
-    for (int e = 0; e < 9; ++e) u[e] = U[(size_t)(mu * 9 + e) * V + s];
+        for (int e = 0; e < 9; ++e) u[e] = U[(size_t)(mu * 9 + e) * V + s];
+    }
+};
+template <> struct Link<float> {
+    typedef float4 vec;
+    static constexpr int planes = 3;
+    __host__ __device__ static inline float2 cmul_conj_diff(float2 a, float2 b, float2 c, float2 d) {
+        // conj(a b - c d)
+        const float re = (a.x * b.x - a.y * b.y) - (c.x * d.x - c.y * d.y);
+        const float im = (a.x * b.y + a.y * b.x) - (c.x * d.y + c.y * d.x);
+        return make_float2(re, -im);
+    }
+    __host__ __device__ static inline void load(const float4 *__restrict__ U, int V, int mu, int s,
+                                                float2 (&u)[9]) {
+        const float4 q0 = U[(size_t)(mu * 3 + 0) * V + s];
+        const float4 q1 = U[(size_t)(mu * 3 + 1) * V + s];
+        const float4 q2 = U[(size_t)(mu * 3 + 2) * V + s];
+        u[0] = make_float2(q0.x, q0.y);
+        u[1] = make_float2(q0.z, q0.w);
+        u[2] = make_float2(q1.x, q1.y);
+        u[3] = make_float2(q1.z, q1.w);
+        u[4] = make_float2(q2.x, q2.y);
+        u[5] = make_float2(q2.z, q2.w);
+        u[6] = cmul_conj_diff(u[1], u[5], u[2], u[4]);
+        u[7] = cmul_conj_diff(u[2], u[3], u[0], u[5]);
+        u[8] = cmul_conj_diff(u[0], u[4], u[1], u[3]);
+    }
+};
+
+template <typename T>
+__host__ __device__ inline void load_link(const typename Link<T>::vec *__restrict__ U, int V, int mu, int s,
+                                          cx<T> (&u)[9]) {
+    Link<T>::load(U, V, mu, s, u);
 }
 
 // Accumulate (1 - gamma_mu) U h-projection of p into acc (forward hop).
@@ -142,7 +183,7 @@ template <bool G5> __host__ __device__ inline void maybe_g5(float2 (&v)[12]) {
 template <typename T, int MU, bool G5IN>
 __host__ __device__ inline void hop_pair(int s, const int (&c)[4], const Geom &g, int stride,
                                          const typename Field<T>::vec *__restrict__ in,
-                                         const cx<T> *__restrict__ U, cx<T> (&acc)[12]) {
+                                         const typename Link<T>::vec *__restrict__ U, cx<T> (&acc)[12]) {
     const int L = g.L[MU];
     // forward neighbour and the boundary phase of a hop across the time edge
     const int sf = (c[MU] == L - 1) ? s - (L - 1) * stride : s + stride;
@@ -164,7 +205,7 @@ __host__ __device__ inline void hop_pair(int s, const int (&c)[4], const Geom &g
 template <typename T, bool G5IN, bool G5OUT>
 __host__ __device__ inline void wilson_site(int s, const Geom &g, T kappa,
                                             const typename Field<T>::vec *__restrict__ in,
-                                            const cx<T> *__restrict__ U, cx<T> (&out)[12]) {
+                                            const typename Link<T>::vec *__restrict__ U, cx<T> (&out)[12]) {
     int c[4];
     int r = s;
     c[0] = r % g.L[0]; r /= g.L[0];

@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int), ("cycles", ctypes.c_int),
                 ("mvps", ctypes.c_longlong), ("true_residual", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("stencil_ms", ctypes.c_double),
-                ("stencil_launches", ctypes.c_longlong), ("stencil_sites", ctypes.c_longlong),
+                ("stencil_launches", ctypes.c_longlong), ("stencil_bytes", ctypes.c_double),
                 ("gpu_launches", ctypes.c_longlong)]
 
     def as_dict(self):
@@ -87,6 +87,7 @@ _SIGS = {
     "dlz_defl_save": ([_vp, ctypes.c_char_p], _ip),
     "dlz_defl_load": ([_vp, ctypes.c_char_p, ctypes.POINTER(_vp)], _ip),
     "dlz_defl_destroy": ([_vp], _ip),
+    "dlz_stencil_bench": ([_vp, _ip, _ip, _ip, _ip, _vp, _dp], _ip),
     "dlz_host_symeig": ([_ip, _vp, _vp, _vp], _ip),
     "dlz_host_lstsq": ([_ip, _ip, _vp, _vp, _vp, _vp], _ip),
 }
@@ -274,6 +275,15 @@ def defl_load(op, path):
     h = _vp()
     _check(lib.dlz_defl_load(op.handle, str(path).encode(), ctypes.byref(h)))
     return Deflation(h, op)
+
+
+def stencil_bench(op, x, iters=50, which=D):
+    """Average device time of one stencil launch over x's right-hand sides ([nrhs, V, 4, 3])."""
+    dtype = F32 if str(x.dtype).endswith("complex64") else F64
+    nrhs = int(np.prod(x.shape)) // (12 * op.volume)
+    ms = ctypes.c_double()
+    _check(lib.dlz_stencil_bench(op.handle, dtype, int(which), nrhs, int(iters), _ptr(x), ctypes.byref(ms)))
+    return {"ms": ms.value, "nrhs": nrhs}
 
 
 def host_symeig(A):

@@ -35,11 +35,16 @@ def main(argv):
             how = "dense LAPACK eigvalsh of D^dagger D; scan from 0 by 0.005, Illinois refine"
         else:
             start = float(os.environ.get("KAPPA_START", "0.262"))
-            kap, sig = okappa.kappa_iterative(
-                U, dims, start=start, log=lambda s: print(s, flush=True))
-            how = ("MinRes-DR(100,20) harmonic Ritz pair nearest zero of gamma5 D "
-                   f"(residual 1e-5); steps of 0.003 from {start} to bracket, Illinois "
-                   "refine to 1e-3, re-verified from a fresh start vector")
+            step = float(os.environ.get("KAPPA_STEP", "0.003"))
+            rtol = float(os.environ.get("KAPPA_RTOL", "1e-3"))
+            cap = int(os.environ.get("KAPPA_MAX_CYCLES", "2000"))
+            kap, sig, res = okappa.kappa_iterative(
+                U, dims, start=start, step=step, rtol=rtol, max_cycles=cap,
+                log=lambda s: print(s, flush=True))
+            how = ("MinRes-DR(100,20) as an eigensolver: harmonic Ritz pair nearest zero of "
+                   f"gamma5 D (at most {cap} cycles per evaluation); steps of {step} from {start} "
+                   f"to bracket, Illinois refine to |sigma/1e-3 - 1| < {rtol}; harmonic Ritz "
+                   f"residual of the final estimate {res:.2e}")
         key = f"{lat}_s{seed}"
         table[key] = dict(kappa=kap, sigma_min=sig, method=how,
                           seconds=round(time.time() - t0, 1), host=platform.machine())

@@ -241,3 +241,35 @@ def test_mixed_precision_dr_first_rhs(m, case, method):
     _, s1 = solve(op, d32, torch.from_numpy(B).cuda(), _params(m, precision=m.F32))
     _, s0 = solve(op, None, torch.from_numpy(B).cuda(), _params(m, precision=m.F32))
     assert s1[0].converged == 1 and s1[0].iterations < s0[0].iterations
+
+
+def test_graph_replay_is_bit_identical_to_direct_launches(m, case, tmp_path):
+    """The CUDA-graph path (captured Lanczos cycles and MinRes iteration groups)
+    gives bit-identical results to plain launches: the reductions have a fixed
+    summation order, so only a wrong captured argument could change a bit."""
+    import os
+    import subprocess
+    import sys
+    U, op, b = case
+    p = _params(m, precision=m.F32)
+    x, d, st = m.minresdr(op, torch.from_numpy(b).cuda(), p)
+    B = synth.gaussian_spinors(DIMS, [21, 22])
+    X, sts = m.dminres(op, d, torch.from_numpy(B).cuda(), p)
+    np.save(tmp_path / "ref.npy", np.concatenate([x.cpu().numpy()[None], X.cpu().numpy()]))
+    code = f"""
+import sys, numpy as np, torch
+sys.path.insert(0, {os.path.dirname(os.path.dirname(os.path.abspath(__file__)))!r})
+import synth
+from paper_0901_3163_gb300 import dlz
+dims = {DIMS!r}
+op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, 1)).cuda(), {KAPPA!r})
+p = dlz.params_default(m=40, k=10, tol=1e-10, oversolve=2.0, max_cycles=400, precision=dlz.F32)
+x, d, st = dlz.minresdr(op, torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda(), p)
+X, sts = dlz.dminres(op, d, torch.from_numpy(synth.gaussian_spinors(dims, [21, 22])).cuda(), p)
+np.save(sys.argv[1], np.concatenate([x.cpu().numpy()[None], X.cpu().numpy()]))
+"""
+    env = dict(os.environ, DLZ_NO_GRAPHS="1")
+    subprocess.run([sys.executable, "-c", code, str(tmp_path / "plain.npy")], check=True, env=env)
+    ref = np.load(tmp_path / "ref.npy")
+    plain = np.load(tmp_path / "plain.npy")
+    assert np.array_equal(ref, plain)
