@@ -360,7 +360,7 @@ def run_first_rhs_only(args):
     w, dims, U, kappa, B = workload_inputs(args.kappa)
     op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
     prec = dlz.F32 if args.form == "chosen" else dlz.F64
-    p = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=args.max_cycles, precision=prec)
+    p = dlz.params_default(m=w["m"], k=w["k"], tol=args.tol, max_cycles=args.max_cycles, precision=prec)
     x, d, st = dlz.minresdr(op, torch.from_numpy(B[0]).cuda(), p, deflate=True)
     torch.cuda.synchronize()
     print(json.dumps({"mode": "first-rhs-only", "form": args.form, "kappa": kappa, "stats": st.as_dict()}))
@@ -383,6 +383,7 @@ def main():
     ap.add_argument("--first-rhs-only", action="store_true")
     ap.add_argument("--max-cycles", type=int, default=4000)
     ap.add_argument("--kappa", type=float, default=None)
+    ap.add_argument("--tol", type=float, default=1e-10)
     args = ap.parse_args()
     if args.stencil_only:
         run_stencil_only(args)

@@ -65,7 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared",
-                                                         "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+                                                         "-Xlinker", "-rpath=/usr/local/cuda/lib64",
+                                                         "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

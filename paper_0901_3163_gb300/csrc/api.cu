@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "dlz_internal.cuh"
+#include "krylov_util.cuh"
 #include "reduce.cuh"
 #include "solvers.h"
 

@@ -50,7 +50,5 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
 int deflation_finish(Op &op, dlz_defl_s *d);
 // Residuals of the Rayleigh-Ritz pairs (computed on first request: k MVPs).
 int deflation_residuals(Op &op, dlz_defl_s *d);
-int combine64(Op &op, double2 *out, long ld_out, int nout, const double2 *in, long ld_in, int nin,
-              const void *dev_coef, int ld_coef, bool real, bool acc);
 
 }  // namespace dlz
