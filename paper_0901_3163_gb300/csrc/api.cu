@@ -110,6 +110,7 @@ double Profiler::stencil_ms() {
         float ms = 0.f;
         cudaEventSynchronize(pool[i + 1]);
         if (cudaEventElapsedTime(&ms, pool[i], pool[i + 1]) == cudaSuccess) tot += ms;
+        else cudaGetLastError();
     }
     return tot;
 }

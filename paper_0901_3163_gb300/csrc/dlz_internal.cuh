@@ -85,9 +85,9 @@ int fail(int code, const std::string &msg);
             return ::dlz::fail(e_ == cudaErrorMemoryAllocation ? DLZ_ERR_OOM : DLZ_ERR_CUDA, \
                                std::string(#expr) + ": " + cudaGetErrorString(e_));    \
     } while (0)
-#define DLZ_TRY(expr)              \
-    do {                           \
-        int r_ = (expr);           \
+#define DLZ_TRY(...)                 \
+    do {                             \
+        int r_ = (__VA_ARGS__);      \
         if (r_ != DLZ_OK) return r_; \
     } while (0)
 
@@ -188,6 +188,8 @@ struct GraphExec {
                 pr.sampled_ms += ms;
                 pr.sampled_bytes += bytes[i / 2];
                 pr.sampled++;
+            } else {
+                cudaGetLastError();   // a sample that cannot be read must not poison later checks
             }
         }
     }

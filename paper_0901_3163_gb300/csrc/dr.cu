@@ -171,18 +171,19 @@ int plan_restart(bool harmonic, int m, int k, const std::vector<double> &T, cons
 __global__ void __launch_bounds__(128)
 k_accum_x32(double2 *__restrict__ x, const float4 *__restrict__ Vb, long ld, int nin,
             const double *__restrict__ y, int V) {
-    extern __shared__ double ysm[];
-    for (int t = threadIdx.x; t < nin; t += blockDim.x) ysm[t] = y[t];
+    extern __shared__ float ysm[];
+    for (int t = threadIdx.x; t < nin; t += blockDim.x) ysm[t] = (float)y[t];
     __syncthreads();
     const long n = 6L * V;
     const long stride = (long)gridDim.x * blockDim.x;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        // the correction V_m y of one cycle in FP32 (the basis precision); x itself in FP64
+        float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         for (int j = 0; j < nin; ++j) {
             const float4 v = Vb[(size_t)j * ld + i];
-            const double c = ysm[j];
-            a0 = fma(c, (double)v.x, a0); a1 = fma(c, (double)v.y, a1);
-            a2 = fma(c, (double)v.z, a2); a3 = fma(c, (double)v.w, a3);
+            const float c = ysm[j];
+            a0 = fmaf(c, v.x, a0); a1 = fmaf(c, v.y, a1);
+            a2 = fmaf(c, v.z, a2); a3 = fmaf(c, v.w, a3);
         }
         const int cpl = (int)(i / V), s = (int)(i % V);
         double2 &p = x[(size_t)(2 * cpl) * V + s];
@@ -198,7 +199,7 @@ template <> int accum_x<P64>(Op &op, double2 *x, const double2 *Vb, long ld, int
 template <> int accum_x<P32>(Op &op, double2 *x, const float4 *Vb, long ld, int nin, const double *dev_y) {
     const long n = 6L * op.g.V;
     long blocks = std::min((n + 127) / 128, 152L * 8);
-    k_accum_x32<<<(int)blocks, 128, nin * sizeof(double), op.stream>>>(x, Vb, ld, nin, dev_y, op.g.V);
+    k_accum_x32<<<(int)blocks, 128, nin * sizeof(float), op.stream>>>(x, Vb, ld, nin, dev_y, op.g.V);
     op.prof.launches++;
     DLZ_CUDA_TRY(cudaGetLastError());
     return DLZ_OK;
@@ -213,6 +214,7 @@ template <> int from64<P64>(Op &op, double2 *dst, const double2 *src, double sca
     });
 }
 template <> int from64<P32>(Op &op, float4 *dst, const double2 *src, double scale) {
+    // once per solve: the FP64 multiply keeps the scaled values exact before rounding
     const int V = op.g.V;
     return map(op, 6L * V, [=] __device__(long i) {
         const int c = (int)(i / V), s = (int)(i % V);
@@ -256,6 +258,11 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
     DLZ_TRY(scal.alloc((size_t)(2 * m + 8) * sizeof(double)));
     DLZ_TRY(coef.alloc((size_t)(m + 1) * (m + 1) * sizeof(double2)));
     double *d_alpha = scal.as<double>(), *d_beta = d_alpha + m, *d_norm = d_beta + m;
+    // the same scalars in the element-update precision (written by the finishers)
+    typedef typename P::S S;
+    DevBuf sscal;
+    DLZ_TRY(sscal.alloc((size_t)(3 * m + 4) * sizeof(S)));
+    S *s_alpha = sscal.as<S>(), *s_beta = s_alpha + m, *s_invbeta = s_beta + m, *s_nrm = s_invbeta + m;
     HostScratch hs;
     DLZ_TRY(hs.ensure(2 * m + 8));
 
@@ -311,33 +318,40 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
             DLZ_TRY(P::apply(op, wv, vj, which, tmp.as<E>()));
             if (j == j0 && j0 > 0) DLZ_TRY(combine<P>(op, wv, n, 1, V, n, j0, coefr, 1, true, true));
             const E *vprev = (j > j0) ? V + (size_t)(j - 1) * n : nullptr;
-            const double *bprev = (j > j0) ? d_beta + (j - 1) : nullptr;
+            const S *bprev = (j > j0) ? s_beta + (j - 1) : nullptr;
             double *aj = d_alpha + j, *bj = d_beta + j;
-            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
+            S *saj = s_alpha + j, *sbj = s_beta + j, *sib = s_invbeta + j;
+            DLZ_TRY(red<P, 1>(op, n, [=] __device__(long i, typename P::Acc (&acc)[1]) {
                 E x_ = wv[i];
                 if (vprev) {
                     x_ = P::axpy(-*bprev, vprev[i], x_);
                     wv[i] = x_;
                 }
                 acc[0] += P::rdot(vj[i], x_);
-            }, [=] __device__(const double *r) { *aj = r[0]; }));
+            }, [=] __device__(const double *r) { *aj = r[0]; *saj = (S)r[0]; }));
             const bool reorth = (j0 > 0) && p.reorth_period > 0 && ((j - j0) % p.reorth_period == 0);
             if (reorth) {
-                DLZ_TRY(map(op, n, [=] __device__(long i) { wv[i] = P::axpy(-*aj, vj[i], wv[i]); }));
+                DLZ_TRY(map(op, n, [=] __device__(long i) { wv[i] = P::axpy(-*saj, vj[i], wv[i]); }));
                 double2 *cd = coef.as<double2>() + (m + 1);   // after the coupling block
                 DLZ_TRY(multidot<P>(op, V, n, j0, wv, cd, -1.0));
                 DLZ_TRY(combine<P>(op, wv, n, 1, V, n, j0, cd, 1, false, true));
-                DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) { acc[0] += P::nrm(wv[i]); },
-                                  [=] __device__(const double *r) { *bj = sqrt(r[0]); }));
+                DLZ_TRY(red<P, 1>(op, n, [=] __device__(long i, typename P::Acc (&acc)[1]) { acc[0] += P::nrm(wv[i]); },
+                                  [=] __device__(const double *r) {
+                                      const double b = sqrt(r[0]);
+                                      *bj = b; *sbj = (S)b; *sib = (S)(1.0 / b);
+                                  }));
             } else {
-                DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
-                    const E x_ = P::axpy(-*aj, vj[i], wv[i]);
+                DLZ_TRY(red<P, 1>(op, n, [=] __device__(long i, typename P::Acc (&acc)[1]) {
+                    const E x_ = P::axpy(-*saj, vj[i], wv[i]);
                     wv[i] = x_;
                     acc[0] += P::nrm(x_);
-                }, [=] __device__(const double *r) { *bj = sqrt(r[0]); }));
+                }, [=] __device__(const double *r) {
+                    const double b = sqrt(r[0]);
+                    *bj = b; *sbj = (S)b; *sib = (S)(1.0 / b);
+                }));
             }
             E *vn = V + (size_t)(j + 1) * n;
-            DLZ_TRY(map(op, n, [=] __device__(long i) { vn[i] = P::scal(1.0 / *bj, wv[i]); }));
+            DLZ_TRY(map(op, n, [=] __device__(long i) { vn[i] = P::scal(*sib, wv[i]); }));
         }
         return DLZ_OK;
         };
@@ -385,9 +399,9 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
             double2 *cd = coef.as<double2>() + (size_t)(m + 1) * (k + 1);
             DLZ_TRY(multidot<P>(op, Vn, n, k, vk, cd, -1.0));
             DLZ_TRY(combine<P>(op, vk, n, 1, Vn, n, k, cd, 1, false, true));
-            double *nrm = d_norm + 3;
-            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) { acc[0] += P::nrm(vk[i]); },
-                              [=] __device__(const double *r) { *nrm = 1.0 / sqrt(r[0]); }));
+            S *nrm = s_nrm;
+            DLZ_TRY(red<P, 1>(op, n, [=] __device__(long i, typename P::Acc (&acc)[1]) { acc[0] += P::nrm(vk[i]); },
+                              [=] __device__(const double *r) { *nrm = (S)(1.0 / sqrt(r[0])); }));
             DLZ_TRY(map(op, n, [=] __device__(long i) { vk[i] = P::scal(*nrm, vk[i]); }));
         }
         DLZ_TRY(d2h_sync(op, hs.p, d_norm + 2, sizeof(double)));
@@ -433,7 +447,10 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         } else {
             vk64 = reinterpret_cast<double2 *>(V);
         }
-        DLZ_TRY(build_deflation(op, which, vk64, k, defl_out));
+        std::vector<double> Hk((size_t)k * k);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) Hk[(size_t)i * k + j] = T[(size_t)i * m + j];
+        DLZ_TRY(build_deflation(op, which, vk64, k, defl_out, Hk.data()));
     }
     DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
     if (trace)

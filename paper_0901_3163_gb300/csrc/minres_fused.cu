@@ -18,6 +18,8 @@
 // captured once as a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "dlz_internal.cuh"
@@ -32,7 +34,10 @@ struct FusedState {          // one per right-hand side (FP64 scalars)
     double beta, alpha, beta_next, inv_beta;
     double c, s, c_old, s_old, phibar;
     double eps, delta, gamma, tau;
-    double r0, pad0, pad1;   // r0 = ||r|| at the start of the inner solve
+    double r0;               // ||r|| at the start of the inner solve
+    // FP32 copies read by the element updates (no FP64 op or conversion per element):
+    // f[0] 1/beta_j, f[1] beta_j, f[2] delta, f[3] eps, f[4] 1/gamma, f[5] tau, f[6] alpha
+    float f[8];
 };
 
 namespace {
@@ -50,11 +55,10 @@ k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Vp, float4
     const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
     const long nel = 6L * g.V;
     const size_t base = (size_t)q * nel;
-    double acc = 0.0;
+    float facc = 0.f;
     if (s < g.V) {
-        const FusedState sc = st[q];
-        const float ib = (float)sc.inv_beta, bt = (float)sc.beta_next;
-        const float de = (float)sc.delta, ep = (float)sc.eps, ig = (float)(1.0 / sc.gamma), ta = (float)sc.tau;
+        const float ib = st[q].f[0], bt = st[q].f[1];
+        const float de = st[q].f[2], ep = st[q].f[3], ig = st[q].f[4], ta = st[q].f[5];
         float2 o[12];
         wilson_site<float, false, true>(s, g, kappa, Ub + base, links, o);   // Q u_j
 #pragma unroll
@@ -66,7 +70,7 @@ k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Vp, float4
                                 o[2 * c + 1].x * ib - bt * vp.z, o[2 * c + 1].y * ib - bt * vp.w);
             Vc[i] = vj;
             W[i] = w;
-            acc += (double)(vj.x * w.x + vj.y * w.y) + (double)(vj.z * w.z + vj.w * w.w);
+            facc += (vj.x * w.x + vj.y * w.y) + (vj.z * w.z + vj.w * w.w);
             const float4 dn = f4((vp.x - de * d2.x - ep * d3.x) * ig, (vp.y - de * d2.y - ep * d3.y) * ig,
                                  (vp.z - de * d2.z - ep * d3.z) * ig, (vp.w - de * d2.w - ep * d3.w) * ig);
             D3[i] = dn;
@@ -76,7 +80,8 @@ k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Vp, float4
             E[i] = ev;
         }
     }
-    // block partial of alpha_q, stored contiguously per right-hand side
+    // block partial of alpha_q (FP64 across threads), stored contiguously per right-hand side
+    double acc = (double)facc;
     __shared__ double sm[kThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -107,7 +112,17 @@ k_minres_alpha(const double *__restrict__ partials, int nbq, FusedState *__restr
         for (int w = 0; w < (int)(blockDim.x / 32); ++w) a += sm[w];
         st[q].beta = st[q].beta_next;
         st[q].alpha = a;
+        st[q].f[6] = (float)a;
     }
+}
+
+__device__ inline void set_floats(FusedState &s) {
+    s.f[0] = (float)s.inv_beta;
+    s.f[1] = (float)s.beta_next;
+    s.f[2] = (float)s.delta;
+    s.f[3] = (float)s.eps;
+    s.f[4] = (float)(1.0 / s.gamma);
+    s.f[5] = (float)s.tau;
 }
 
 }  // namespace
@@ -117,16 +132,17 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
                        const dlz_params &p, int &iters, HostScratch &hs) {
     const long n = 6L * op.g.V;
     // beta_1 = ||r_q||, rotations reset, a no-op direction update for step 0
-    DLZ_TRY(reduce<16>(op, n, [=] __device__(long i, double (&acc)[16]) {
+    DLZ_TRY(reduce32<16>(op, n, [=] __device__(long i, float (&acc)[16]) {
 #pragma unroll
         for (int q = 0; q < 16; ++q)
-            if (q < N) { const float4 v = r[(size_t)q * n + i]; acc[q] += (double)(v.x * v.x + v.y * v.y) + (double)(v.z * v.z + v.w * v.w); }
+            if (q < N) { const float4 v = r[(size_t)q * n + i]; acc[q] += (v.x * v.x + v.y * v.y) + (v.z * v.z + v.w * v.w); }
     }, [=] __device__(const double *res) {
         for (int q = 0; q < N; ++q) {
             const double b = sqrt(res[q]);
             FusedState s0 = {};
             s0.beta_next = b; s0.inv_beta = b > 0 ? 1.0 / b : 0.0;
             s0.c = 1.0; s0.c_old = 1.0; s0.phibar = b; s0.gamma = 1.0; s0.r0 = b;
+            set_floats(s0);
             ms[q] = s0;
         }
     }));
@@ -151,16 +167,16 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
         // u_{j+1} = w - alpha v_j ; beta_{j+1} ; Givens rotation of step j
         const float4 *vc = Vc;
         float4 *w = W;
-        return reduce<16>(op, n, [=] __device__(long i, double (&acc)[16]) {
+        return reduce32<16>(op, n, [=] __device__(long i, float (&acc)[16]) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 if (q < N) {
                     const size_t o = (size_t)q * n + i;
-                    const float al = (float)ms[q].alpha;
+                    const float al = ms[q].f[6];
                     const float4 a = w[o], v = vc[o];
                     const float4 t = f4(fmaf(-al, v.x, a.x), fmaf(-al, v.y, a.y), fmaf(-al, v.z, a.z), fmaf(-al, v.w, a.w));
                     w[o] = t;
-                    acc[q] += (double)(t.x * t.x + t.y * t.y) + (double)(t.z * t.z + t.w * t.w);
+                    acc[q] += (t.x * t.x + t.y * t.y) + (t.z * t.z + t.w * t.w);
                 }
             }
         }, [=] __device__(const double *res) {
@@ -181,6 +197,7 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
                 s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
                 s.beta_next = bn;
                 s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
+                set_floats(s);
                 ms[q] = s;
             }
         });
@@ -198,8 +215,24 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
     };
     const int check = std::max(6, (p.check_every / 6) * 6);
     int it = 0;
+    // DLZ_TRACE=1: time the replays of the 6-iteration group (diagnostics)
+    const char *trace_env = std::getenv("DLZ_TRACE");
+    const bool trace = trace_env && trace_env[0] == '1';
+    cudaEvent_t te0 = nullptr, te1 = nullptr;
+    double t_graph = 0.0;
+    int n_timed = 0;
+    if (trace) { cudaEventCreate(&te0); cudaEventCreate(&te1); }
     while (iters < p.max_iter) {
+        const bool timed = trace && ge.exec;      // not the replay that captures the graph
+        if (timed) cudaEventRecord(te0, op.stream);
         DLZ_TRY(run_graph(op, ge, six));
+        if (timed) {
+            cudaEventRecord(te1, op.stream);
+            cudaEventSynchronize(te1);
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, te0, te1) == cudaSuccess) { t_graph += ms; ++n_timed; }
+            else cudaGetLastError();
+        }
         iters += 6;
         it += 6;
         if (it % check == 0 || iters >= p.max_iter) {
@@ -217,6 +250,12 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
             if (done) break;
         }
     }
+    if (trace) {
+        std::fprintf(stderr, "[dlz] fused MinRes N=%d: %d iterations, graph replay %.4f ms per iteration (%d timed)\n",
+                     N, iters, n_timed ? t_graph / (6.0 * n_timed) : 0.0, n_timed);
+        cudaEventDestroy(te0);
+        cudaEventDestroy(te1);
+    }
     // the direction update of the last step (after 6k steps the buffers are back
     // in their starting roles: v_J in Vp, d_{J-1} in D2, d_{J-2} in D3)
     {
@@ -224,8 +263,7 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
         float4 *ee = e;
         DLZ_TRY(map(op, n * N, [=] __device__(long i) {
             const int q = (int)(i / n);
-            const FusedState &sc = ms[q];
-            const float de = (float)sc.delta, ep = (float)sc.eps, ig = (float)(1.0 / sc.gamma), ta = (float)sc.tau;
+            const float de = ms[q].f[2], ep = ms[q].f[3], ig = ms[q].f[4], ta = ms[q].f[5];
             const float4 vp = vj[i], a = d2[i], b = d3[i];
             const float4 dn = f4((vp.x - de * a.x - ep * b.x) * ig, (vp.y - de * a.y - ep * b.y) * ig,
                                  (vp.z - de * a.z - ep * b.z) * ig, (vp.w - de * a.w - ep * b.w) * ig);

@@ -1,6 +1,7 @@
 // Precision traits of the Krylov vectors: FP64 (double2 elements, 12 per site)
-// and FP32 (float4 elements, 6 per site).  Reductions always accumulate in
-// FP64; element updates run in the vector precision.
+// and FP32 (float4 elements, 6 per site).  Reductions sum across threads and
+// blocks in FP64 (FP32 vectors accumulate each thread's few elements in float
+// first); element updates run in the vector precision.
 #pragma once
 
 #include "dlz_internal.cuh"
@@ -11,6 +12,8 @@ namespace dlz {
 struct P64 {
     typedef double2 E;
     typedef double2 C;   // coefficient of a complex combination
+    typedef double Acc;  // per-thread reduction accumulator
+    typedef double S;    // scalar type of element updates
     static constexpr bool kF32 = false;
     static long nel(const Op &op) { return 12L * op.g.V; }
     static int apply(Op &op, E *out, const E *in, int which, E *tmp) { return apply64(op, out, in, which, tmp); }
@@ -32,23 +35,21 @@ struct P64 {
 struct P32 {
     typedef float4 E;
     typedef float2 C;
+    typedef float Acc;
+    typedef float S;     // FP32 updates take FP32 scalars (no FP64 op per element)
     static constexpr bool kF32 = true;
     static long nel(const Op &op) { return 6L * op.g.V; }
     static int apply(Op &op, E *out, const E *in, int which, E *tmp) { return apply32(op, out, in, which, tmp); }
-    __device__ static double rdot(E a, E b) { return (double)(a.x * b.x + a.y * b.y) + (double)(a.z * b.z + a.w * b.w); }
-    __device__ static void cdot(E a, E b, double &re, double &im) {
-        re += (double)(a.x * b.x + a.y * b.y) + (double)(a.z * b.z + a.w * b.w);
-        im += (double)(a.x * b.y - a.y * b.x) + (double)(a.z * b.w - a.w * b.z);
+    __device__ static float rdot(E a, E b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
+    __device__ static void cdot(E a, E b, float &re, float &im) {
+        re += (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w);
+        im += (a.x * b.y - a.y * b.x) + (a.z * b.w - a.w * b.z);
     }
-    __device__ static double nrm(E a) { return (double)(a.x * a.x + a.y * a.y) + (double)(a.z * a.z + a.w * a.w); }
-    __device__ static E axpy(double s, E x, E y) {
-        const float f = (float)s;
+    __device__ static float nrm(E a) { return (a.x * a.x + a.y * a.y) + (a.z * a.z + a.w * a.w); }
+    __device__ static E axpy(float f, E x, E y) {
         return make_float4(fmaf(f, x.x, y.x), fmaf(f, x.y, y.y), fmaf(f, x.z, y.z), fmaf(f, x.w, y.w));
     }
-    __device__ static E scal(double s, E x) {
-        const float f = (float)s;
-        return make_float4(f * x.x, f * x.y, f * x.z, f * x.w);
-    }
+    __device__ static E scal(float f, E x) { return make_float4(f * x.x, f * x.y, f * x.z, f * x.w); }
     __device__ static E zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ static void racc(float c, E x, E &y) {
         y.x = fmaf(c, x.x, y.x); y.y = fmaf(c, x.y, y.y); y.z = fmaf(c, x.z, y.z); y.w = fmaf(c, x.w, y.w);
@@ -61,6 +62,13 @@ struct P32 {
     }
     __device__ static E add(E a, E b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 };
+
+// reduce with the per-thread accumulator type of precision P
+template <class P, int ND, class Body, class Fin>
+inline int red(Op &op, long n, Body body, Fin fin) {
+    if constexpr (P::kF32) return reduce32<ND>(op, n, body, fin);
+    else return reduce<ND>(op, n, body, fin);
+}
 
 // out_l = (acc ? out_l : 0) + sum_j coef[j][col0 + l] in_j, l < nout <= NOUT.
 // Coefficients are given in FP64 (double or double2) and rounded to the
@@ -155,7 +163,7 @@ inline int multidot(Op &op, const typename P::E *V, long ld, int nv, const typen
         const int nb = (nv - l0) < 8 ? (nv - l0) : 8;
         const E *Vb = V + (size_t)l0 * ld;
         double2 *o = dev_out + l0;
-        DLZ_TRY(reduce<16>(op, n, [=] __device__(long i, double (&acc)[16]) {
+        DLZ_TRY(red<P, 16>(op, n, [=] __device__(long i, typename P::Acc (&acc)[16]) {
             const E x = w[i];
 #pragma unroll
             for (int l = 0; l < 8; ++l)

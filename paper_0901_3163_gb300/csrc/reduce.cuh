@@ -36,15 +36,24 @@ __device__ inline void block_sum(double (&acc)[ND], double (*sm)[kRedThreads / 3
 
 // body(i, acc): element update and contributions for element i.
 // fin(res): run once by one thread with the ND reduced values.
-template <int ND, class Body, class Fin>
+// A: the per-thread accumulator type.  FP32 vectors accumulate their few
+// elements per thread in float (GB300's FP64 pipe runs at 1/64 of the FP32
+// rate, so a double add per element would bound the kernel); every sum
+// across threads and blocks is FP64.
+template <int ND, typename A, class Body, class Fin>
 __global__ void __launch_bounds__(kRedThreads) k_reduce(Body body, Fin fin, long n, RedScratch red) {
     __shared__ double sm[ND > 0 ? ND : 1][kRedThreads / 32];
     __shared__ bool last;
     double acc[ND > 0 ? ND : 1];
+    {
+        A local[ND > 0 ? ND : 1];
 #pragma unroll
-    for (int j = 0; j < ND; ++j) acc[j] = 0.0;
-    const long stride = (long)gridDim.x * blockDim.x;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) body(i, acc);
+        for (int j = 0; j < ND; ++j) local[j] = A(0);
+        const long stride = (long)gridDim.x * blockDim.x;
+        for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) body(i, local);
+#pragma unroll
+        for (int j = 0; j < ND; ++j) acc[j] = (double)local[j];
+    }
     block_sum<ND>(acc, sm);
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -78,7 +87,16 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(Body body, Fin fin, long
 template <int ND, class Body, class Fin>
 inline int reduce(Op &op, long n, Body body, Fin fin) {
     static_assert(ND <= kMaxDots, "too many accumulators");
-    k_reduce<ND><<<kRedBlocks, kRedThreads, 0, op.stream>>>(body, fin, n, op.red);
+    k_reduce<ND, double><<<kRedBlocks, kRedThreads, 0, op.stream>>>(body, fin, n, op.red);
+    op.prof.launches++;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+// Same, with float per-thread accumulators (body gets float (&)[ND]).
+template <int ND, class Body, class Fin>
+inline int reduce32(Op &op, long n, Body body, Fin fin) {
+    static_assert(ND <= kMaxDots, "too many accumulators");
+    k_reduce<ND, float><<<kRedBlocks, kRedThreads, 0, op.stream>>>(body, fin, n, op.red);
     op.prof.launches++;
     DLZ_CUDA_TRY(cudaGetLastError());
     return DLZ_OK;

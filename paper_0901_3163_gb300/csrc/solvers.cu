@@ -25,7 +25,7 @@ namespace dlz {
 typedef std::complex<double> zc;
 
 // ------------------------------------------------------------------ deflation set
-int build_deflation(Op &op, int which, const double2 *Vk, int k, dlz_defl_s **out) {
+int build_deflation(Op &op, int which, const double2 *Vk, int k, dlz_defl_s **out, const double *Hk) {
     dlz_defl_s *d = new dlz_defl_s();
     d->op = &op;
     d->k = k;
@@ -38,7 +38,16 @@ int build_deflation(Op &op, int which, const double2 *Vk, int k, dlz_defl_s **ou
         return DLZ_OK;
     }();
     if (rc != DLZ_OK) { delete d; return rc; }
-    rc = deflation_finish(op, d);
+    if (Hk) {
+        // H = V_k^dag A V_k is the k x k block of the restarted projected matrix
+        // (the Lanczos relation A V_k = V_{k+1} Tbar_k holds to the basis rounding)
+        d->H.assign((size_t)k * k, zc(0, 0));
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) d->H[(size_t)i * k + j] = zc(0.5 * (Hk[(size_t)i * k + j] + Hk[(size_t)j * k + i]), 0.0);
+        rc = deflation_factor(op, d);
+    } else {
+        rc = deflation_finish(op, d);
+    }
     if (rc != DLZ_OK) { delete d; return rc; }
     *out = d;
     return DLZ_OK;
@@ -69,6 +78,13 @@ int deflation_finish(Op &op, dlz_defl_s *d) {
             const zc hji(hd[(size_t)i * k + j].x, hd[(size_t)i * k + j].y);
             d->H[(size_t)i * k + j] = 0.5 * (hij + std::conj(hji));
         }
+    return deflation_factor(op, d);
+}
+
+// LU factors of H and its eigen-decomposition (the Rayleigh-Ritz pairs).
+int deflation_factor(Op &op, dlz_defl_s *d) {
+    const int k = d->k;
+    if (k == 0) return DLZ_OK;
     d->Hlu = d->H;
     d->piv.assign(k, 0);
     if (!lu_factor(k, d->Hlu.data(), d->piv.data()))

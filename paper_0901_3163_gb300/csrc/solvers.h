@@ -39,7 +39,9 @@ int dsolve_mixed(Op &op, const dlz_defl_s *d, bool minres, const double2 *b, dou
 // (B, X: N internal FP64 vectors one after another; st: N entries).
 int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *B, double2 *X, int N,
                        const dlz_params &p, dlz_stats *st, const double2 *X_init = nullptr);
-int build_deflation(Op &op, int which, const double2 *Vk, int k, dlz_defl_s **out);
+// Hk (k x k, may be null): V_k^dag A V_k known from the restart; else computed (k MVPs).
+int build_deflation(Op &op, int which, const double2 *Vk, int k, dlz_defl_s **out, const double *Hk = nullptr);
+int deflation_factor(Op &op, dlz_defl_s *d);
 int prepare_kernels(Op &op);
 struct FusedState;
 struct HostScratch;

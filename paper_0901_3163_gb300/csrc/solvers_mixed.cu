@@ -30,12 +30,11 @@ struct InnerState {
     double c, s, c_old, s_old, phibar;
     double eps, delta, gamma, tau;
     double rr, ss, pq;   // CG
+    float fa, fb;        // CG step lengths in FP32 for the element updates
 };
 
-__device__ inline double re_dot(float4 a, float4 b) {
-    return (double)(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
-}
-__device__ inline double nrm2(float4 a) { return (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w); }
+__device__ inline float re_dot(float4 a, float4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
+__device__ inline float nrm2(float4 a) { return (a.x * a.x + a.y * a.y) + (a.z * a.z + a.w * a.w); }
 __device__ inline float4 axpy4(float a, float4 x, float4 y) {
     return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
 }
@@ -64,102 +63,6 @@ int add_from32(Op &op, double2 *x, const float4 *e, const double *d_scale) {
     });
 }
 
-// FP32 MinRes on Q e = r from e = 0, until |phibar| <= tol_rel * ||r||.
-int minres_inner32(Op &op, const float4 *r, float4 *e, float4 *vp, float4 *v, float4 *w, float4 *d1,
-                   float4 *d2, InnerState *ms, double tol_rel, const dlz_params &p, dlz_stats &st,
-                   HostScratch &hs) {
-    const long n = 6L * op.g.V;
-    DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) { acc[0] += nrm2(r[i]); },
-                      [=] __device__(const double *res) {
-                          const double b = sqrt(res[0]);
-                          InnerState s0 = {};
-                          s0.beta_next = b; s0.inv_beta = b > 0 ? 1.0 / b : 0.0;
-                          s0.c = 1.0; s0.c_old = 1.0; s0.phibar = b;
-                          *ms = s0;
-                      }));
-    DLZ_TRY(map(op, n, [=] __device__(long i) {
-        const float ib = (float)ms->inv_beta;
-        v[i] = scale4(ib, r[i]);
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        vp[i] = z; d1[i] = z; d2[i] = z; e[i] = z;
-    }));
-    DLZ_TRY(d2h_sync(op, hs.p, ms, sizeof(InnerState)));
-    const double beta1 = reinterpret_cast<const InnerState *>(hs.p)->beta_next;
-    if (!(beta1 > 0.0)) return std::isfinite(beta1) ? DLZ_OK : fail(DLZ_ERR_NONFINITE, "inner residual");
-    int it = 0;
-    while (st.iterations < p.max_iter) {
-        DLZ_TRY(wilson32(op, w, v, DLZ_Q));
-        st.mvps += 1;
-        {
-            const float4 *a_vp = vp, *a_v = v;
-            float4 *a_w = w;
-            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
-                const float bt = (float)ms->beta_next;
-                const float4 t = axpy4(-bt, a_vp[i], a_w[i]);
-                a_w[i] = t;
-                acc[0] += re_dot(a_v[i], t);
-            }, [=] __device__(const double *res) {
-                ms->beta = ms->beta_next;
-                ms->alpha = res[0];
-            }));
-        }
-        {
-            const float4 *a_v = v;
-            float4 *a_w = w;
-            DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) {
-                const float al = (float)ms->alpha;
-                const float4 t = axpy4(-al, a_v[i], a_w[i]);
-                a_w[i] = t;
-                acc[0] += nrm2(t);
-            }, [=] __device__(const double *res) {
-                InnerState s = *ms;
-                const double bn = sqrt(res[0]);
-                const double eps = s.s_old * s.beta;
-                const double deltabar = s.c_old * s.beta;
-                const double delta = s.c * deltabar + s.s * s.alpha;
-                const double gammabar = -s.s * deltabar + s.c * s.alpha;
-                const double gamma = hypot(gammabar, bn);
-                const double cn = gammabar / gamma, sn = bn / gamma;
-                s.tau = cn * s.phibar;
-                s.phibar = -sn * s.phibar;
-                s.eps = eps; s.delta = delta; s.gamma = gamma;
-                s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
-                s.beta_next = bn;
-                s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
-                *ms = s;
-            }));
-        }
-        {
-            const float4 *a_v = v, *a_d1 = d1;
-            float4 *a_d2 = d2, *a_w = w, *a_e = e;
-            DLZ_TRY(map(op, n, [=] __device__(long i) {
-                const float de = (float)ms->delta, ep = (float)ms->eps, ig = (float)(1.0 / ms->gamma);
-                const float ta = (float)ms->tau, ib = (float)ms->inv_beta;
-                const float4 q = a_v[i], e1 = a_d1[i], e2 = a_d2[i];
-                float4 dn;
-                dn.x = (q.x - de * e1.x - ep * e2.x) * ig;
-                dn.y = (q.y - de * e1.y - ep * e2.y) * ig;
-                dn.z = (q.z - de * e1.z - ep * e2.z) * ig;
-                dn.w = (q.w - de * e1.w - ep * e2.w) * ig;
-                a_d2[i] = dn;
-                a_e[i] = axpy4(ta, dn, a_e[i]);
-                a_w[i] = scale4(ib, a_w[i]);
-            }));
-        }
-        float4 *t0 = vp; vp = v; v = w; w = t0;
-        std::swap(d1, d2);
-        st.iterations++;
-        ++it;
-        if (it % p.check_every == 0 || st.iterations >= p.max_iter) {
-            DLZ_TRY(d2h_sync(op, hs.p, ms, sizeof(InnerState)));
-            const InnerState *h = reinterpret_cast<const InnerState *>(hs.p);
-            if (!std::isfinite(h->phibar)) return fail(DLZ_ERR_NONFINITE, "MinRes residual not finite");
-            if (std::fabs(h->phibar) <= tol_rel * beta1 || h->beta_next == 0.0) break;
-        }
-    }
-    return DLZ_OK;
-}
-
 // FP32 CG on D^dag D e = D^dag s from e = 0, tracking s - D e, until that falls
 // by tol_rel.  r, pp, t, q: work vectors.
 int cgnr_inner32(Op &op, float4 *s, float4 *e, float4 *r, float4 *pp, float4 *t, float4 *q,
@@ -167,7 +70,7 @@ int cgnr_inner32(Op &op, float4 *s, float4 *e, float4 *r, float4 *pp, float4 *t,
     const long n = 6L * op.g.V;
     DLZ_TRY(wilson32(op, r, s, DLZ_DDAG));
     st.mvps += 1;
-    DLZ_TRY(reduce<2>(op, n, [=] __device__(long i, double (&acc)[2]) {
+    DLZ_TRY(reduce32<2>(op, n, [=] __device__(long i, float (&acc)[2]) {
         const float4 v = r[i];
         pp[i] = v;
         e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -181,10 +84,10 @@ int cgnr_inner32(Op &op, float4 *s, float4 *e, float4 *r, float4 *pp, float4 *t,
         DLZ_TRY(wilson32(op, t, pp, DLZ_D));
         DLZ_TRY(wilson32(op, q, t, DLZ_DDAG));
         st.mvps += 2;
-        DLZ_TRY(reduce<1>(op, n, [=] __device__(long i, double (&acc)[1]) { acc[0] += re_dot(pp[i], q[i]); },
-                          [=] __device__(const double *res) { cs->pq = res[0]; }));
-        DLZ_TRY(reduce<2>(op, n, [=] __device__(long i, double (&acc)[2]) {
-            const float al = (float)(cs->rr / cs->pq);
+        DLZ_TRY(reduce32<1>(op, n, [=] __device__(long i, float (&acc)[1]) { acc[0] += re_dot(pp[i], q[i]); },
+                          [=] __device__(const double *res) { cs->pq = res[0]; cs->fa = (float)(cs->rr / res[0]); }));
+        DLZ_TRY(reduce32<2>(op, n, [=] __device__(long i, float (&acc)[2]) {
+            const float al = cs->fa;
             const float4 pv = pp[i];
             e[i] = axpy4(al, pv, e[i]);
             const float4 rv = axpy4(-al, q[i], r[i]);
@@ -195,11 +98,12 @@ int cgnr_inner32(Op &op, float4 *s, float4 *e, float4 *r, float4 *pp, float4 *t,
             acc[1] += nrm2(sv);
         }, [=] __device__(const double *res) {
             cs->beta = res[0] / cs->rr;
+            cs->fb = (float)cs->beta;
             cs->rr = res[0];
             cs->ss = res[1];
         }));
         DLZ_TRY(map(op, n, [=] __device__(long i) {
-            const float be = (float)cs->beta;
+            const float be = cs->fb;
             pp[i] = axpy4(be, pp[i], r[i]);
         }));
         st.iterations++;
@@ -218,6 +122,7 @@ int cgnr_inner32(Op &op, float4 *s, float4 *e, float4 *r, float4 *pp, float4 *t,
 
 int dsolve_mixed(Op &op, const dlz_defl_s *d, bool minres, const double2 *b, double2 *x_out,
                  const dlz_params &p, dlz_stats &st, const double2 *x_init) {
+    if (minres) return dsolve_mixed_batch(op, d, true, b, x_out, 1, p, &st, x_init);
     const long n64 = 12L * op.g.V;
     const long n32 = 6L * op.g.V;
     DevBuf bp, x, r, tmp, dots, scal, f32;
@@ -310,12 +215,7 @@ int dsolve_mixed(Op &op, const dlz_defl_s *d, bool minres, const double2 *b, dou
         DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
         const double rcur = hs.p[0];
         const double inner_tol = std::max(0.5 * p.tol * bnorm / rcur, p.reliable_delta);
-        if (minres)
-            DLZ_TRY(minres_inner32(op, w32[0], w32[1], w32[2], w32[3], w32[4], w32[5], w32[6], ist,
-                                   inner_tol, p, st, hs));
-        else
-            DLZ_TRY(cgnr_inner32(op, w32[0], w32[1], w32[2], w32[3], w32[4], w32[5], ist, inner_tol, p,
-                                 st, hs));
+        DLZ_TRY(cgnr_inner32(op, w32[0], w32[1], w32[2], w32[3], w32[4], w32[5], ist, inner_tol, p, st, hs));
         DLZ_TRY(add_from32(op, x.as<double2>(), w32[1], scl));
         ++outer;
     }
@@ -340,146 +240,6 @@ namespace dlz {
 namespace {
 
 constexpr int kMaxBatch = 16;
-
-// FP32 MinRes on Q e_r = r_r for all r at once, from e = 0, until every
-// |phibar_r| <= tol_r * ||r_r||.
-int minres_inner32_batch(Op &op, int N, const float4 *r, float4 *e, float4 *vp, float4 *v, float4 *w,
-                         float4 *d1, float4 *d2, InnerState *ms, const double *d_tol,
-                         const dlz_params &p, int &iters, HostScratch &hs) {
-    const long n = 6L * op.g.V;
-    DLZ_TRY(reduce<kMaxBatch>(op, n, [=] __device__(long i, double (&acc)[kMaxBatch]) {
-#pragma unroll
-        for (int q = 0; q < kMaxBatch; ++q)
-            if (q < N) acc[q] += nrm2(r[(size_t)q * n + i]);
-    }, [=] __device__(const double *res) {
-        for (int q = 0; q < N; ++q) {
-            const double b = sqrt(res[q]);
-            InnerState s0 = {};
-            s0.beta_next = b; s0.inv_beta = b > 0 ? 1.0 / b : 0.0;
-            s0.c = 1.0; s0.c_old = 1.0; s0.phibar = b;
-            s0.rr = b;          // ||r_q||: reference for the stopping test
-            ms[q] = s0;
-        }
-    }));
-    DLZ_TRY(map(op, n * N, [=] __device__(long i) {
-        const int q = (int)(i / n);
-        const float ib = (float)ms[q].inv_beta;
-        v[i] = scale4(ib, r[i]);
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        vp[i] = z; d1[i] = z; d2[i] = z; e[i] = z;
-    }));
-    int it = 0;
-    // one graph = 6 iterations: the (v_prev, v, w) and (d1, d2) rotations return to
-    // their starting assignment after 6 steps, so the captured arguments repeat
-    GraphExec ge;
-    float4 *const vp0 = vp, *const v0 = v, *const w0 = w, *const d10 = d1, *const d20 = d2;
-    auto six = [&]() -> int {
-    float4 *vp = vp0, *v = v0, *w = w0, *d1 = d10, *d2 = d20;
-    for (int sub = 0; sub < 6; ++sub) {
-        DLZ_TRY(wilson32_batch(op, w, v, DLZ_Q, N));
-        {
-            const float4 *a_vp = vp, *a_v = v;
-            float4 *a_w = w;
-            DLZ_TRY(reduce<kMaxBatch>(op, n, [=] __device__(long i, double (&acc)[kMaxBatch]) {
-#pragma unroll
-                for (int q = 0; q < kMaxBatch; ++q) {
-                    if (q < N) {
-                        const size_t o = (size_t)q * n + i;
-                        const float bt = (float)ms[q].beta_next;
-                        const float4 t = axpy4(-bt, a_vp[o], a_w[o]);
-                        a_w[o] = t;
-                        acc[q] += re_dot(a_v[o], t);
-                    }
-                }
-            }, [=] __device__(const double *res) {
-                for (int q = 0; q < N; ++q) {
-                    ms[q].beta = ms[q].beta_next;
-                    ms[q].alpha = res[q];
-                }
-            }));
-        }
-        {
-            const float4 *a_v = v;
-            float4 *a_w = w;
-            DLZ_TRY(reduce<kMaxBatch>(op, n, [=] __device__(long i, double (&acc)[kMaxBatch]) {
-#pragma unroll
-                for (int q = 0; q < kMaxBatch; ++q) {
-                    if (q < N) {
-                        const size_t o = (size_t)q * n + i;
-                        const float al = (float)ms[q].alpha;
-                        const float4 t = axpy4(-al, a_v[o], a_w[o]);
-                        a_w[o] = t;
-                        acc[q] += nrm2(t);
-                    }
-                }
-            }, [=] __device__(const double *res) {
-                for (int q = 0; q < N; ++q) {
-                    InnerState s = ms[q];
-                    const double bn = sqrt(res[q]);
-                    const double eps = s.s_old * s.beta;
-                    const double deltabar = s.c_old * s.beta;
-                    const double delta = s.c * deltabar + s.s * s.alpha;
-                    const double gammabar = -s.s * deltabar + s.c * s.alpha;
-                    double gamma = hypot(gammabar, bn);
-                    double cn = 1.0, sn = 0.0;
-                    if (gamma > 0.0) { cn = gammabar / gamma; sn = bn / gamma; }
-                    else gamma = 1.0;            // zero right-hand side: hold a no-op
-                    s.tau = cn * s.phibar;
-                    s.phibar = -sn * s.phibar;
-                    s.eps = eps; s.delta = delta; s.gamma = gamma;
-                    s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
-                    s.beta_next = bn;
-                    s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
-                    ms[q] = s;
-                }
-            }));
-        }
-        {
-            const float4 *a_v = v, *a_d1 = d1;
-            float4 *a_d2 = d2, *a_w = w, *a_e = e;
-            DLZ_TRY(map(op, n * N, [=] __device__(long i) {
-                const int q = (int)(i / n);
-                const InnerState &s = ms[q];
-                const float de = (float)s.delta, ep = (float)s.eps, ig = (float)(1.0 / s.gamma);
-                const float ta = (float)s.tau, ib = (float)s.inv_beta;
-                const float4 qv = a_v[i], e1 = a_d1[i], e2 = a_d2[i];
-                float4 dn;
-                dn.x = (qv.x - de * e1.x - ep * e2.x) * ig;
-                dn.y = (qv.y - de * e1.y - ep * e2.y) * ig;
-                dn.z = (qv.z - de * e1.z - ep * e2.z) * ig;
-                dn.w = (qv.w - de * e1.w - ep * e2.w) * ig;
-                a_d2[i] = dn;
-                a_e[i] = axpy4(ta, dn, a_e[i]);
-                a_w[i] = scale4(ib, a_w[i]);
-            }));
-        }
-        float4 *t0 = vp; vp = v; v = w; w = t0;
-        std::swap(d1, d2);
-    }
-    return DLZ_OK;
-    };
-    const int check = std::max(6, (p.check_every / 6) * 6);
-    while (iters < p.max_iter) {
-        DLZ_TRY(run_graph(op, ge, six));
-        iters += 6;
-        it += 6;
-        if (it % check == 0 || iters >= p.max_iter) {
-            DLZ_TRY(d2h_sync(op, hs.p, ms, N * sizeof(InnerState)));
-            ge.sample(op.prof);
-            const InnerState *h = reinterpret_cast<const InnerState *>(hs.p);
-            bool done = true;
-            for (int q = 0; q < N; ++q)
-                if (!std::isfinite(h[q].phibar)) return fail(DLZ_ERR_NONFINITE, "MinRes residual not finite");
-            DLZ_TRY(d2h_sync(op, hs.p + 512, d_tol, N * sizeof(double)));
-            for (int q = 0; q < N; ++q) {
-                const InnerState *hq = reinterpret_cast<const InnerState *>(hs.p) + q;
-                if (!(std::fabs(hq->phibar) <= hs.p[512 + q] * hq->rr || hq->beta_next == 0.0)) done = false;
-            }
-            if (done) break;
-        }
-    }
-    return DLZ_OK;
-}
 
 }  // namespace
 
