@@ -157,7 +157,7 @@ struct Op {
     DevBuf red_mem;   // reduction scratch
     RedScratch red;
     Profiler prof;
-    DevBuf scratch_a, scratch_b, scratch_c;  // spinor-sized scratch (FP64)
+    DevBuf md_scratch;   // block partials of the FP32 multi-dot (grown on demand, outside graphs)
 };
 
 // ---------------------------------------------------------------- CUDA graphs

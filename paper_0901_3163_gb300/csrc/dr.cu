@@ -31,6 +31,7 @@
 #include "reduce.cuh"
 #include "small_dense.h"
 #include "solvers.h"
+#include "wilson_site.cuh"
 
 namespace dlz {
 
@@ -92,21 +93,27 @@ int plan_restart(bool harmonic, int m, int k, const std::vector<double> &T, cons
     // harmonic Ritz pairs: T_m g = mu (Tbar^T Tbar) g, theta = 1/mu, via the Cholesky
     // factor L of Tbar^T Tbar: C = L^-1 T_m L^-T, g = L^-T z
     std::vector<double> M((size_t)m * m, 0.0), L((size_t)m * m), X((size_t)m * m), C((size_t)m * m), col(m);
-    for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) {
-            double t = 0;
-            for (int r = 0; r <= m; ++r) t += T[(size_t)r * m + i] * T[(size_t)r * m + j];
-            M[(size_t)i * m + j] = t;
-        }
+    // M = Tbar^T Tbar from the nonzeros of each row of Tbar (dense (k+1) block + band)
+    for (int r = 0; r <= m; ++r) {
+        const double *row = &T[(size_t)r * m];
+        int nz[1024];
+        int cnt = 0;
+        for (int j = 0; j < m; ++j)
+            if (row[j] != 0.0) nz[cnt++] = j;
+        for (int a = 0; a < cnt; ++a)
+            for (int b = 0; b < cnt; ++b) M[(size_t)nz[a] * m + nz[b]] += row[nz[a]] * row[nz[b]];
+    }
     if (!cholesky(m, M.data(), L.data())) return fail(DLZ_ERR_BREAKDOWN, "Tbar^T Tbar not positive definite");
+    std::vector<int> env;
+    envelope(m, L.data(), env);
     for (int j = 0; j < m; ++j) {
         for (int i = 0; i < m; ++i) col[i] = Tm[(size_t)i * m + j];
-        lower_solve(m, L.data(), col.data());
+        lower_solve(m, L.data(), col.data(), env.data());
         for (int i = 0; i < m; ++i) X[(size_t)i * m + j] = col[i];
     }
     for (int j = 0; j < m; ++j) {
         for (int i = 0; i < m; ++i) col[i] = X[(size_t)j * m + i];
-        lower_solve(m, L.data(), col.data());
+        lower_solve(m, L.data(), col.data(), env.data());
         for (int i = 0; i < m; ++i) C[(size_t)i * m + j] = col[i];
     }
     std::vector<double> mu(m), Zc((size_t)m * m);
@@ -117,7 +124,7 @@ int plan_restart(bool harmonic, int m, int k, const std::vector<double> &T, cons
     std::vector<double> Gk((size_t)m * k);
     for (int l = 0; l < k; ++l) {
         for (int i = 0; i < m; ++i) col[i] = Zc[(size_t)i * m + idx[l]];
-        upper_t_solve(m, L.data(), col.data());
+        upper_t_solve(m, L.data(), col.data(), env.data());
         double nr = 0;
         for (int i = 0; i < m; ++i) nr += col[i] * col[i];
         nr = std::sqrt(nr);
@@ -235,6 +242,137 @@ template <> int basis_to64<P32>(Op &op, double2 *dst, const float4 *src, int k) 
     return DLZ_OK;
 }
 
+// ---------------------------------------------------------------- fused FP32 Lanczos step
+// K1L: v_j = u_j / beta_{j-1} (written to the basis), w = A v_j - beta_{j-1} v_{j-1},
+//      block partial of alpha_j = Re <v_j, w>;  A v_j = Q(in) * sin where in = u_j (A = Q)
+//      or Q u_j (A = D^dag D = Q Q), so the normalisation of the previous step is folded
+//      into this one instead of costing a pass of its own.
+// K2aL: u_{j+1} = w - alpha_j v_j and the block partial of ||u_{j+1}||^2.
+// K1b/K2b: the partials summed in a fixed order, scalars written (FP64 and FP32).
+constexpr int kLz = 128;
+
+__global__ void __launch_bounds__(kLz)
+k_lanczos_k1(const float4 *__restrict__ in, const float *__restrict__ sin_, const float4 *__restrict__ U,
+             const float4 *__restrict__ Vp, const float *__restrict__ bprev, float4 *__restrict__ Vj,
+             float4 *__restrict__ W, const float4 *__restrict__ links, Geom g, float kappa,
+             double *__restrict__ partials) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    float facc = 0.f;
+    if (s < g.V) {
+        const float ib = *sin_, bt = *bprev;
+        float2 o[12];
+        wilson_site<float, false, true>(s, g, kappa, in, links, o);
+        float4 u[6], vp[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            u[c] = U[(size_t)c * g.V + s];
+            vp[c] = Vp[(size_t)c * g.V + s];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float4 vj = make_float4(u[c].x * ib, u[c].y * ib, u[c].z * ib, u[c].w * ib);
+            const float4 w = make_float4(o[2 * c].x * ib - bt * vp[c].x, o[2 * c].y * ib - bt * vp[c].y,
+                                         o[2 * c + 1].x * ib - bt * vp[c].z, o[2 * c + 1].y * ib - bt * vp[c].w);
+            Vj[(size_t)c * g.V + s] = vj;
+            W[(size_t)c * g.V + s] = w;
+            facc += (vj.x * w.x + vj.y * w.y) + (vj.z * w.z + vj.w * w.w);
+        }
+    }
+    double acc = (double)facc;
+    __shared__ double sm[kLz / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kLz / 32; ++w) t += sm[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kLz)
+k_lanczos_k2a(float4 *__restrict__ W, const float4 *__restrict__ Vj, const float *__restrict__ salpha, Geom g,
+              double *__restrict__ partials) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    float facc = 0.f;
+    if (s < g.V) {
+        const float al = *salpha;
+        float4 w[6], v[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            w[c] = W[(size_t)c * g.V + s];
+            v[c] = Vj[(size_t)c * g.V + s];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float4 t = make_float4(fmaf(-al, v[c].x, w[c].x), fmaf(-al, v[c].y, w[c].y),
+                                         fmaf(-al, v[c].z, w[c].z), fmaf(-al, v[c].w, w[c].w));
+            W[(size_t)c * g.V + s] = t;
+            facc += (t.x * t.x + t.y * t.y) + (t.z * t.z + t.w * t.w);
+        }
+    }
+    double acc = (double)facc;
+    __shared__ double sm[kLz / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kLz / 32; ++w) t += sm[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+// sum of nb partials (fixed order); kind 0: alpha_j, kind 1: beta_j = sqrt(sum)
+__global__ void __launch_bounds__(256)
+k_lanczos_fin(const double *__restrict__ partials, int nb, int kind, double *__restrict__ d_out,
+              float *__restrict__ s_out, float *__restrict__ s_inv) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += partials[b];
+    __shared__ double sm[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) a += sm[w];
+        if (kind == 1) {
+            a = sqrt(a);
+            *s_inv = (float)(1.0 / a);
+        }
+        *d_out = a;
+        *s_out = (float)a;
+    }
+}
+
+// one fused FP32 Lanczos step (see above)
+int lanczos_fused_step(Op &op, bool ddagd, const float4 *u, const float *s_ib_prev, const float4 *vp,
+                       const float *s_b_prev, float4 *vj, float4 *w_out, float4 *tmp, double *partials,
+                       double *d_a, float *s_a, double *d_b, float *s_b, float *s_ib) {
+    const Geom g = op.g;
+    const unsigned blocks = (unsigned)((g.V + kLz - 1) / kLz);
+    const float4 *in = u;
+    if (ddagd) {
+        DLZ_TRY(wilson32(op, tmp, u, DLZ_Q));      // first factor of Q Q
+        in = tmp;
+    }
+    op.prof.stencil_start(op.stream, true, g.V, 1, 96);
+    k_lanczos_k1<<<blocks, kLz, 0, op.stream>>>(in, s_ib_prev, u, vp, s_b_prev, vj, w_out, op.gauge32.as<float4>(),
+                                                g, (float)op.kappa, partials);
+    op.prof.stencil_stop(op.stream);
+    k_lanczos_fin<<<1, 256, 0, op.stream>>>(partials, (int)blocks, 0, d_a, s_a, nullptr);
+    k_lanczos_k2a<<<blocks, kLz, 0, op.stream>>>(w_out, vj, s_a, g, partials + blocks);
+    k_lanczos_fin<<<1, 256, 0, op.stream>>>(partials + blocks, (int)blocks, 1, d_b, s_b, s_ib);
+    op.prof.launches += 4;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+
 }  // namespace
 
 template <class P>
@@ -251,6 +389,12 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
     DLZ_TRY(Vb.alloc((size_t)(m + 1) * n * sizeof(E)));
     DLZ_TRY(w.alloc(n * sizeof(E)));
     DLZ_TRY(tmp.alloc(n * sizeof(E)));
+    DevBuf w2, fpart;                          // fused FP32 steps: second work vector, partials
+    if (P::kF32) {
+        DLZ_TRY(reserve_multidot(op, k));
+        DLZ_TRY(w2.alloc(n * sizeof(E)));
+        DLZ_TRY(fpart.alloc((size_t)2 * ((op.g.V + 127) / 128 + 1) * sizeof(double)));
+    }
     DLZ_TRY(bb.alloc(n64 * sizeof(double2)));
     DLZ_TRY(bp.alloc(n64 * sizeof(double2)));
     DLZ_TRY(x.alloc(n64 * sizeof(double2)));
@@ -313,8 +457,32 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
             DLZ_TRY(h2d(op, coefr, cp.data(), j0 * sizeof(double)));
         }
         auto lanczos_steps = [&]() -> int {
+        // FP32: steps other than the first of a cycle and the re-orthogonalisation steps
+        // run fused (lanczos_fused_step); `ucur` holds the unnormalised u_j, and V[j] is
+        // written lazily (by the next fused step, or by a scaling pass before an unfused one)
+        E *ucur = w.as<E>(), *uoth = P::kF32 ? w2.as<E>() : nullptr;
+        bool vmat = true;
         for (int j = j0; j < m; ++j) {
-            E *vj = V + (size_t)j * n, *wv = w.as<E>();
+            const bool reorth_j = (j0 > 0) && p.reorth_period > 0 && ((j - j0) % p.reorth_period == 0);
+            if constexpr (P::kF32) {
+                if (j > j0 && !reorth_j) {
+                    DLZ_TRY(lanczos_fused_step(op, !harmonic, ucur, s_invbeta + (j - 1), V + (size_t)(j - 1) * n,
+                                               s_beta + (j - 1), V + (size_t)j * n, uoth, tmp.as<E>(),
+                                               fpart.as<double>(), d_alpha + j, s_alpha + j, d_beta + j,
+                                               s_beta + j, s_invbeta + j));
+                    std::swap(ucur, uoth);
+                    vmat = false;
+                    continue;
+                }
+                if (!vmat) {
+                    E *vjm = V + (size_t)j * n;
+                    const E *uc = ucur;
+                    const S *ibp = s_invbeta + (j - 1);
+                    DLZ_TRY(map(op, n, [=] __device__(long i) { vjm[i] = P::scal(*ibp, uc[i]); }));
+                    vmat = true;
+                }
+            }
+            E *vj = V + (size_t)j * n, *wv = ucur;
             DLZ_TRY(P::apply(op, wv, vj, which, tmp.as<E>()));
             if (j == j0 && j0 > 0) DLZ_TRY(combine<P>(op, wv, n, 1, V, n, j0, coefr, 1, true, true));
             const E *vprev = (j > j0) ? V + (size_t)(j - 1) * n : nullptr;
@@ -329,7 +497,7 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
                 }
                 acc[0] += P::rdot(vj[i], x_);
             }, [=] __device__(const double *r) { *aj = r[0]; *saj = (S)r[0]; }));
-            const bool reorth = (j0 > 0) && p.reorth_period > 0 && ((j - j0) % p.reorth_period == 0);
+            const bool reorth = reorth_j;
             if (reorth) {
                 DLZ_TRY(map(op, n, [=] __device__(long i) { wv[i] = P::axpy(-*saj, vj[i], wv[i]); }));
                 double2 *cd = coef.as<double2>() + (m + 1);   // after the coupling block
@@ -352,6 +520,13 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
             }
             E *vn = V + (size_t)(j + 1) * n;
             DLZ_TRY(map(op, n, [=] __device__(long i) { vn[i] = P::scal(*sib, wv[i]); }));
+            vmat = true;
+        }
+        if (!vmat) {                           // v_{m+1} after a fused last step
+            E *vm = V + (size_t)m * n;
+            const E *uc = ucur;
+            const S *ibp = s_invbeta + (m - 1);
+            DLZ_TRY(map(op, n, [=] __device__(long i) { vm[i] = P::scal(*ibp, uc[i]); }));
         }
         return DLZ_OK;
         };

@@ -1,7 +1,7 @@
 // Fused FP32 MinRes iteration for a batch of right-hand sides (the inner
 // solve of the mixed-precision D-MinRes, arXiv:0901.3163 Sec. 2).
 //
-// Three launches per iteration (two of them full passes) instead of four:
+// Four launches per iteration, two of them full passes over the vectors:
 //   K1 (stencil + epilogue, one block = 128 sites of one right-hand side):
 //        v_j   = u_j / beta_j                      (u_j: unnormalised Lanczos vector)
 //        w     = Q v_j - beta_j v_{j-1}            (Q u_j / beta_j: Q is linear)
@@ -10,11 +10,11 @@
 //        (the direction update of the previous step: its Givens rotation needed
 //         beta_j, known only now)
 //   K1b: alpha_j = sum of K1's block partials (one block per right-hand side);
-//   K2 (reduction): u_{j+1} = w - alpha_j v_j, beta_{j+1} = ||u_{j+1}||, and the
-//        Givens rotation of step j in the finisher.
-// The alpha partials of K1 (one per block, block b belongs to right-hand side
-// b mod N) are summed in a fixed order by a one-block-per-RHS kernel, so
-// results are deterministic.  Buffers rotate with period 2, so a group of 6 iterations is
+//   K2a: u_{j+1} = w - alpha_j v_j and the block partials of ||u_{j+1}||^2;
+//   K2b: beta_{j+1}, and the Givens rotation of step j (one block per right-hand side).
+// The block partials of K1 and K2a (block b belongs to right-hand side b mod N)
+// are summed in a fixed order by one-block-per-RHS kernels, so results are
+// deterministic.  Buffers rotate with period 2, so a group of 6 iterations is
 // captured once as a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
@@ -116,6 +116,84 @@ k_minres_alpha(const double *__restrict__ partials, int nbq, FusedState *__restr
     }
 }
 
+// K2a: u_{j+1} = w - alpha_j v_j (written over w) and the block partial of ||u_{j+1}||^2;
+// one block = 128 sites of one right-hand side, all 6 planes of a site loaded before
+// any store so the loads overlap.
+__global__ void __launch_bounds__(kThreads)
+k_minres_k2a(float4 *__restrict__ W, const float4 *__restrict__ Vc, Geom g, int N,
+             const FusedState *__restrict__ st, double *__restrict__ partials) {
+    const int q = blockIdx.x % N;
+    const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
+    const size_t base = (size_t)q * 6 * g.V;
+    float facc = 0.f;
+    if (s < g.V) {
+        const float al = st[q].f[6];
+        float4 w[6], v[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            w[c] = W[base + (size_t)c * g.V + s];
+            v[c] = Vc[base + (size_t)c * g.V + s];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float4 t = f4(fmaf(-al, v[c].x, w[c].x), fmaf(-al, v[c].y, w[c].y),
+                                fmaf(-al, v[c].z, w[c].z), fmaf(-al, v[c].w, w[c].w));
+            W[base + (size_t)c * g.V + s] = t;
+            facc += (t.x * t.x + t.y * t.y) + (t.z * t.z + t.w * t.w);
+        }
+    }
+    double acc = (double)facc;
+    __shared__ double sm[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) t += sm[w];
+        partials[(size_t)q * (gridDim.x / N) + blockIdx.x / N] = t;
+    }
+}
+
+__device__ inline void set_floats(FusedState &s);
+
+// K2b: beta_{j+1} = sqrt(sum of K2a's partials) and the Givens rotation of step j,
+// one block per right-hand side
+__global__ void __launch_bounds__(256)
+k_minres_k2b(const double *__restrict__ partials, int nbq, FusedState *__restrict__ st) {
+    const int q = blockIdx.x;
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nbq; b += blockDim.x) t += partials[(size_t)q * nbq + b];
+    __shared__ double sm[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) r2 += sm[w];
+        FusedState s = st[q];
+        const double bn = sqrt(r2);
+        const double eps = s.s_old * s.beta;
+        const double deltabar = s.c_old * s.beta;
+        const double delta = s.c * deltabar + s.s * s.alpha;
+        const double gammabar = -s.s * deltabar + s.c * s.alpha;
+        double gamma = hypot(gammabar, bn);
+        double cn = 1.0, sn = 0.0;
+        if (gamma > 0.0) { cn = gammabar / gamma; sn = bn / gamma; }
+        else gamma = 1.0;            // zero right-hand side: hold a no-op
+        s.tau = cn * s.phibar;
+        s.phibar = -sn * s.phibar;
+        s.eps = eps; s.delta = delta; s.gamma = gamma;
+        s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
+        s.beta_next = bn;
+        s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
+        set_floats(s);
+        st[q] = s;
+    }
+}
+
 __device__ inline void set_floats(FusedState &s) {
     s.f[0] = (float)s.inv_beta;
     s.f[1] = (float)s.beta_next;
@@ -154,6 +232,7 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
     const float kappa = (float)op.kappa;
     const float4 *links = op.gauge32.as<float4>();
     const unsigned blocks = (unsigned)(((g.V + kThreads - 1) / kThreads) * N);
+    double *partials2 = partials + blocks;    // K2a's partials after K1's
     auto iteration = [&](float4 *U, float4 *Vp, float4 *Vc, float4 *W, float4 *D2, float4 *D3) -> int {
         // K1 moves 216 reals per site and right-hand side: u, v_{j-1}, d_{j-2}, d_{j-3}, e
         // read; v_j, w, d_{j-1}, e written (24 each), plus the links once per site
@@ -165,42 +244,11 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
         op.prof.launches += 2;
         DLZ_CUDA_TRY(cudaGetLastError());
         // u_{j+1} = w - alpha v_j ; beta_{j+1} ; Givens rotation of step j
-        const float4 *vc = Vc;
-        float4 *w = W;
-        return reduce32<16>(op, n, [=] __device__(long i, float (&acc)[16]) {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                if (q < N) {
-                    const size_t o = (size_t)q * n + i;
-                    const float al = ms[q].f[6];
-                    const float4 a = w[o], v = vc[o];
-                    const float4 t = f4(fmaf(-al, v.x, a.x), fmaf(-al, v.y, a.y), fmaf(-al, v.z, a.z), fmaf(-al, v.w, a.w));
-                    w[o] = t;
-                    acc[q] += (t.x * t.x + t.y * t.y) + (t.z * t.z + t.w * t.w);
-                }
-            }
-        }, [=] __device__(const double *res) {
-            for (int q = 0; q < N; ++q) {
-                FusedState s = ms[q];
-                const double bn = sqrt(res[q]);
-                const double eps = s.s_old * s.beta;
-                const double deltabar = s.c_old * s.beta;
-                const double delta = s.c * deltabar + s.s * s.alpha;
-                const double gammabar = -s.s * deltabar + s.c * s.alpha;
-                double gamma = hypot(gammabar, bn);
-                double cn = 1.0, sn = 0.0;
-                if (gamma > 0.0) { cn = gammabar / gamma; sn = bn / gamma; }
-                else gamma = 1.0;            // zero right-hand side: hold a no-op
-                s.tau = cn * s.phibar;
-                s.phibar = -sn * s.phibar;
-                s.eps = eps; s.delta = delta; s.gamma = gamma;
-                s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
-                s.beta_next = bn;
-                s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
-                set_floats(s);
-                ms[q] = s;
-            }
-        });
+        k_minres_k2a<<<blocks, kThreads, 0, op.stream>>>(W, Vc, g, N, ms, partials2);
+        k_minres_k2b<<<N, 256, 0, op.stream>>>(partials2, (int)(blocks / N), ms);
+        op.prof.launches += 2;
+        DLZ_CUDA_TRY(cudaGetLastError());
+        return DLZ_OK;
     };
     GraphExec ge;
     auto six = [&]() -> int {

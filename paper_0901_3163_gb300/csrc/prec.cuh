@@ -153,10 +153,112 @@ inline int combine(Op &op, typename P::E *out, long ld_out, int nout, const type
     return DLZ_OK;
 }
 
+// ---------------------------------------------------------------- FP32 multi-dot
+// <V_l, w> for l < nv in one pass over the V_l: block (site chunk, group of 8
+// vectors); each thread loads w at its site once and accumulates 8 complex dots
+// over the 6 planes in float; warps and blocks are summed in FP64 (fixed order).
+constexpr int kMdThreads = 128;
+__global__ void __launch_bounds__(kMdThreads)
+k_multidot32(const float4 *__restrict__ V, long ld, int nv, const float4 *__restrict__ w, int sites,
+             double *__restrict__ partials) {
+    const int grp = blockIdx.y;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    float re[8], im[8];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) { re[l] = 0.f; im[l] = 0.f; }
+    if (s < sites) {
+        float4 x[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) x[c] = w[(size_t)c * sites + s];
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+            const int vi = grp * 8 + l;
+            if (vi < nv) {
+                const float4 *v = V + (size_t)vi * ld;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    const float4 a = v[(size_t)c * sites + s];
+                    re[l] += (a.x * x[c].x + a.y * x[c].y) + (a.z * x[c].z + a.w * x[c].w);
+                    im[l] += (a.x * x[c].y - a.y * x[c].x) + (a.z * x[c].w - a.w * x[c].z);
+                }
+            }
+        }
+    }
+    __shared__ double sm[16][kMdThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+        double a = (double)re[l], b = (double)im[l];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) { sm[2 * l][warp] = a; sm[2 * l + 1][warp] = b; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < kMdThreads / 32; ++k) t += sm[threadIdx.x][k];
+        // partials[(grp*16 + j) * gridDim.x + blockIdx.x]
+        partials[((size_t)grp * 16 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// out[l] = scale * (sum over blocks of the partials of vector l), one block per vector
+__global__ void __launch_bounds__(256)
+k_multidot_fin(const double *__restrict__ partials, int nblk, int nv, double scale, double2 *__restrict__ out) {
+    const int l = blockIdx.x;
+    const int grp = l / 8, j = l % 8;
+    const double *pre = partials + ((size_t)grp * 16 + 2 * j) * nblk;
+    const double *pim = pre + nblk;
+    double a = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < nblk; t += blockDim.x) { a += pre[t]; b += pim[t]; }
+    __shared__ double sa[8], sb[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) { sa[threadIdx.x >> 5] = a; sb[threadIdx.x >> 5] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int k = 0; k < (int)(blockDim.x / 32); ++k) { x += sa[k]; y += sb[k]; }
+        out[l] = make_double2(scale * x, scale * y);
+    }
+}
+
+// Grow the FP32 multi-dot scratch for up to nv vectors (call outside graph capture).
+inline int reserve_multidot(Op &op, int nv) {
+    const int nblk = (op.g.V + kMdThreads - 1) / kMdThreads;
+    const size_t need = (size_t)((nv + 7) / 8) * 16 * nblk * sizeof(double);
+    if (op.md_scratch.bytes < need) {
+        DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+        DLZ_TRY(op.md_scratch.alloc(need));
+    }
+    return DLZ_OK;
+}
+
 // dev_out[l] = scale * <V_l, w> (complex), l < nv, V_l = V + l*ld
 template <class P>
 inline int multidot(Op &op, const typename P::E *V, long ld, int nv, const typename P::E *w, double2 *dev_out,
                     double scale) {
+    if constexpr (P::kF32) {
+        if (nv <= 0) return DLZ_OK;
+        const int sites = op.g.V;
+        const int nblk = (sites + kMdThreads - 1) / kMdThreads;
+        const int ngrp = (nv + 7) / 8;
+        const size_t need = (size_t)ngrp * 16 * nblk;
+        if (op.md_scratch.bytes < need * sizeof(double))
+            return fail(DLZ_ERR_BADARG, "multidot scratch not reserved (reserve_multidot)");
+        k_multidot32<<<dim3(nblk, ngrp), kMdThreads, 0, op.stream>>>(V, ld, nv, w, sites, op.md_scratch.as<double>());
+        k_multidot_fin<<<nv, 256, 0, op.stream>>>(op.md_scratch.as<double>(), nblk, nv, scale, dev_out);
+        op.prof.launches += 2;
+        DLZ_CUDA_TRY(cudaGetLastError());
+        return DLZ_OK;
+    }
     typedef typename P::E E;
     const long n = P::nel(op);
     for (int l0 = 0; l0 < nv; l0 += 8) {

@@ -34,8 +34,12 @@ void tridiagonalise(int n, std::vector<double> &a, std::vector<double> &d, std::
     std::vector<double> v(n), p(n), q(n), sc(n);
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;          // length of the column below the diagonal
-        double alpha = 0.0;
-        for (int i = 0; i < m; ++i) alpha += a[(size_t)(k + 1 + i) * n + k] * a[(size_t)(k + 1 + i) * n + k];
+        // a column with nothing below its subdiagonal is already reduced (the tridiagonal
+        // tail of a restarted Lanczos matrix): no reflection needed
+        double tail = 0.0;
+        for (int i = 1; i < m; ++i) tail += a[(size_t)(k + 1 + i) * n + k] * a[(size_t)(k + 1 + i) * n + k];
+        if (tail == 0.0) continue;
+        double alpha = tail + a[(size_t)(k + 1) * n + k] * a[(size_t)(k + 1) * n + k];
         alpha = std::sqrt(alpha);
         if (alpha == 0.0) continue;
         const double x0 = a[(size_t)(k + 1) * n + k];
@@ -161,30 +165,36 @@ bool lstsq(int rows, int cols, const double *T, const double *c, double *y, doub
     std::vector<double> a(T, T + (size_t)rows * cols), b(c, c + rows);
     std::vector<std::vector<double>> vs(cols);
     std::vector<double> taus(cols, 0.0);
+    std::vector<int> ends(cols);
     for (int k = 0; k < cols; ++k) {
+        // rows k..end-1 hold the nonzeros of column k (banded below the dense block)
+        int end = rows;
+        while (end > k + 1 && a[(size_t)(end - 1) * cols + k] == 0.0) --end;
+        ends[k] = end;
         double alpha = 0.0;
-        for (int i = k; i < rows; ++i) alpha += a[(size_t)i * cols + k] * a[(size_t)i * cols + k];
+        for (int i = k; i < end; ++i) alpha += a[(size_t)i * cols + k] * a[(size_t)i * cols + k];
         alpha = std::sqrt(alpha);
         std::vector<double> &v = vs[k];
         v.assign(rows - k, 0.0);
         if (alpha == 0.0) return false;
         alpha = -sgn1(a[(size_t)k * cols + k]) * alpha;
-        for (int i = k; i < rows; ++i) v[i - k] = a[(size_t)i * cols + k];
+        for (int i = k; i < end; ++i) v[i - k] = a[(size_t)i * cols + k];
         v[0] -= alpha;
         double vn2 = 0.0;
-        for (double t : v) vn2 += t * t;
+        for (int i = k; i < end; ++i) vn2 += v[i - k] * v[i - k];
         const double tau = (vn2 == 0.0) ? 0.0 : 2.0 / vn2;
         taus[k] = tau;
         for (int j = k; j < cols; ++j) {
             double s = 0.0;
-            for (int i = k; i < rows; ++i) s += v[i - k] * a[(size_t)i * cols + j];
+            for (int i = k; i < end; ++i) s += v[i - k] * a[(size_t)i * cols + j];
+            if (s == 0.0) continue;
             s *= tau;
-            for (int i = k; i < rows; ++i) a[(size_t)i * cols + j] -= s * v[i - k];
+            for (int i = k; i < end; ++i) a[(size_t)i * cols + j] -= s * v[i - k];
         }
         double s = 0.0;
-        for (int i = k; i < rows; ++i) s += v[i - k] * b[i];
+        for (int i = k; i < end; ++i) s += v[i - k] * b[i];
         s *= tau;
-        for (int i = k; i < rows; ++i) b[i] -= s * v[i - k];
+        for (int i = k; i < end; ++i) b[i] -= s * v[i - k];
     }
     for (int k = cols - 1; k >= 0; --k) {
         double s = b[k];
@@ -200,9 +210,9 @@ bool lstsq(int rows, int cols, const double *T, const double *c, double *y, doub
         for (int k = cols - 1; k >= 0; --k) {
             const std::vector<double> &v = vs[k];
             double s = 0.0;
-            for (int i = k; i < rows; ++i) s += v[i - k] * u[i];
+            for (int i = k; i < ends[k]; ++i) s += v[i - k] * u[i];
             s *= taus[k];
-            for (int i = k; i < rows; ++i) u[i] -= s * v[i - k];
+            for (int i = k; i < ends[k]; ++i) u[i] -= s * v[i - k];
         }
         for (int i = 0; i < rows; ++i) q[i] = u[i];
     }
@@ -210,35 +220,60 @@ bool lstsq(int rows, int cols, const double *T, const double *c, double *y, doub
 }
 
 bool cholesky(int n, const double *A, double *L) {
+    // the factor keeps the envelope of A (first nonzero column per row), so loops start there
+    std::vector<int> first(n);
+    for (int i = 0; i < n; ++i) {
+        int f = 0;
+        while (f < i && A[(size_t)i * n + f] == 0.0) ++f;
+        first[i] = f;
+    }
     for (int i = 0; i < n * n; ++i) L[i] = 0.0;
     for (int j = 0; j < n; ++j) {
         double s = A[(size_t)j * n + j];
-        for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        for (int k = first[j]; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
         if (!(s > 0.0)) return false;
         const double ljj = std::sqrt(s);
         L[(size_t)j * n + j] = ljj;
         for (int i = j + 1; i < n; ++i) {
+            if (first[i] > j) continue;
             double t = A[(size_t)i * n + j];
-            for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            for (int k = std::max(first[i], first[j]); k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
             L[(size_t)i * n + j] = t / ljj;
         }
     }
     return true;
 }
 
-void lower_solve(int n, const double *L, double *b) {
+// first nonzero column of each row of a lower-triangular L (its envelope)
+void envelope(int n, const double *L, std::vector<int> &first) {
+    first.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        int f = 0;
+        while (f < i && L[(size_t)i * n + f] == 0.0) ++f;
+        first[i] = f;
+    }
+}
+
+void lower_solve(int n, const double *L, double *b, const int *first_in) {
+    std::vector<int> own;
+    const int *first = first_in;
+    if (!first) { envelope(n, L, own); first = own.data(); }
     for (int i = 0; i < n; ++i) {
         double s = b[i];
-        for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * b[k];
+        for (int k = first[i]; k < i; ++k) s -= L[(size_t)i * n + k] * b[k];
         b[i] = s / L[(size_t)i * n + i];
     }
 }
 
-void upper_t_solve(int n, const double *L, double *b) {
+void upper_t_solve(int n, const double *L, double *b, const int *first_in) {
     // solve L^T x = b
+    std::vector<int> own;
+    const int *first = first_in;
+    if (!first) { envelope(n, L, own); first = own.data(); }
     for (int i = n - 1; i >= 0; --i) {
         double s = b[i];
-        for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * b[k];
+        for (int k = i + 1; k < n; ++k)
+            if (first[k] <= i) s -= L[(size_t)k * n + i] * b[k];
         b[i] = s / L[(size_t)i * n + i];
     }
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <complex>
+#include <vector>
 
 #include "../../include/dlz.h"
 
@@ -16,8 +17,10 @@ bool sym_eig(int n, const double *A, double *w, double *Z);
 bool lstsq(int rows, int cols, const double *T, const double *c, double *y, double *q);
 // A = L L^T (lower L); false if A is not positive definite.
 bool cholesky(int n, const double *A, double *L);
-void lower_solve(int n, const double *L, double *b);      // L x = b, in place
-void upper_t_solve(int n, const double *L, double *b);    // L^T x = b, in place
+// L x = b / L^T x = b in place; `first` (optional): the envelope of L from envelope()
+void lower_solve(int n, const double *L, double *b, const int *first = nullptr);
+void upper_t_solve(int n, const double *L, double *b, const int *first = nullptr);
+void envelope(int n, const double *L, std::vector<int> &first);
 bool lu_factor(int n, double *A, int *piv);
 void lu_solve(int n, const double *LU, const int *piv, double *b);
 bool lu_factor(int n, std::complex<double> *A, int *piv);

@@ -268,7 +268,7 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
     for (int i = 0; i < 8; ++i) w32[i] = f32.as<float4>() + (size_t)i * N * n32;
     DevBuf fpart;
     const long k1_blocks = (long)((op.g.V + 127) / 128) * N;
-    DLZ_TRY(fpart.alloc((size_t)k1_blocks * sizeof(double)));
+    DLZ_TRY(fpart.alloc((size_t)2 * k1_blocks * sizeof(double)));   // K1 and K2a partials
     InnerState *ist = reinterpret_cast<InnerState *>(scal.as<double>());
     double *d_rn = scal.as<double>() + kMaxBatch * 24;        // ||r_q||
     double *d_inv = d_rn + kMaxBatch, *d_tol = d_inv + kMaxBatch, *d_bn = d_tol + kMaxBatch;
