@@ -207,7 +207,7 @@ __device__ inline void set_floats(FusedState &s) {
 
 int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const bufs[6],
                        FusedState *ms, double *partials, const double *d_tol,
-                       const dlz_params &p, int &iters, HostScratch &hs) {
+                       const dlz_params &p, int &iters, HostScratch &hs, bool e_init) {
     const long n = 6L * op.g.V;
     // beta_1 = ||r_q||, rotations reset, a no-op direction update for step 0
     DLZ_TRY(reduce32<16>(op, n, [=] __device__(long i, float (&acc)[16]) {
@@ -219,15 +219,17 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
             const double b = sqrt(res[q]);
             FusedState s0 = {};
             s0.beta_next = b; s0.inv_beta = b > 0 ? 1.0 / b : 0.0;
-            s0.c = 1.0; s0.c_old = 1.0; s0.phibar = b; s0.gamma = 1.0; s0.r0 = b;
+            // tolerances are relative to the normalised outer residual (norm 1)
+            s0.c = 1.0; s0.c_old = 1.0; s0.phibar = b; s0.gamma = 1.0; s0.r0 = 1.0;
             set_floats(s0);
             ms[q] = s0;
         }
     }));
     float4 *U0 = bufs[0], *Vp0 = bufs[1], *Vc0 = bufs[2], *W0 = bufs[3], *D20 = bufs[4], *D30 = bufs[5];
     DLZ_CUDA_TRY(cudaMemcpyAsync(U0, r, (size_t)N * n * sizeof(float4), cudaMemcpyDeviceToDevice, op.stream));
-    for (float4 *z : {Vp0, D20, D30, e})
+    for (float4 *z : {Vp0, D20, D30})
         DLZ_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)N * n * sizeof(float4), op.stream));
+    if (!e_init) DLZ_CUDA_TRY(cudaMemsetAsync(e, 0, (size_t)N * n * sizeof(float4), op.stream));
     const Geom g = op.g;
     const float kappa = (float)op.kappa;
     const float4 *links = op.gauge32.as<float4>();

@@ -158,7 +158,7 @@ inline int combine(Op &op, typename P::E *out, long ld_out, int nout, const type
 // vectors); each thread loads w at its site once and accumulates 8 complex dots
 // over the 6 planes in float; warps and blocks are summed in FP64 (fixed order).
 constexpr int kMdThreads = 128;
-__global__ void __launch_bounds__(kMdThreads)
+static __global__ void __launch_bounds__(kMdThreads)
 k_multidot32(const float4 *__restrict__ V, long ld, int nv, const float4 *__restrict__ w, int sites,
              double *__restrict__ partials) {
     const int grp = blockIdx.y;
@@ -207,7 +207,7 @@ k_multidot32(const float4 *__restrict__ V, long ld, int nv, const float4 *__rest
 }
 
 // out[l] = scale * (sum over blocks of the partials of vector l), one block per vector
-__global__ void __launch_bounds__(256)
+static __global__ void __launch_bounds__(256)
 k_multidot_fin(const double *__restrict__ partials, int nblk, int nv, double scale, double2 *__restrict__ out) {
     const int l = blockIdx.x;
     const int grp = l / 8, j = l % 8;

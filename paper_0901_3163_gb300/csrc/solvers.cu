@@ -167,6 +167,15 @@ int deflation_residuals(Op &op, dlz_defl_s *d) {
     return DLZ_OK;
 }
 
+int deflation_v32(Op &op, dlz_defl_s *d) {
+    if (d->k == 0 || d->V32.p) return DLZ_OK;
+    const long n64 = 12L * op.g.V, n32 = 6L * op.g.V;
+    DLZ_TRY(d->V32.alloc((size_t)d->k * n32 * sizeof(float4)));
+    for (int j = 0; j < d->k; ++j)
+        DLZ_TRY(convert64to32(op, d->V32.as<float4>() + (size_t)j * n32, d->V64.as<double2>() + (size_t)j * n64));
+    return DLZ_OK;
+}
+
 // x0 = V H^-1 V^dag b  (b, x0 internal FP64; x0 overwritten)
 int project64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x0, DevBuf &dots) {
     const int k = d->k;

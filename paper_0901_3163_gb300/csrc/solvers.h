@@ -15,6 +15,7 @@ struct dlz_defl_s {
     int k = 0;
     int which = DLZ_Q;                          // DLZ_Q or DLZ_DDAGD
     dlz::DevBuf V64;                            // k internal FP64 vectors
+    dlz::DevBuf V32;                            // FP32 copy for the mixed-precision solvers
     std::vector<std::complex<double>> H;        // k x k, row-major
     std::vector<std::complex<double>> Hlu;      // LU factors of H
     std::vector<int> piv;
@@ -46,9 +47,12 @@ int prepare_kernels(Op &op);
 struct FusedState;
 struct HostScratch;
 // Fused two-kernel FP32 MinRes on N right-hand sides (minres_fused.cu).
+// e_init: e holds a starting guess (r is then the residual of that guess).
 int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const bufs[6],
                        FusedState *ms, double *partials, const double *d_tol,
-                       const dlz_params &p, int &iters, HostScratch &hs);
+                       const dlz_params &p, int &iters, HostScratch &hs, bool e_init = false);
+// FP32 copy of the deflation basis (made on first use).
+int deflation_v32(Op &op, dlz_defl_s *d);
 int deflation_finish(Op &op, dlz_defl_s *d);
 // Residuals of the Rayleigh-Ritz pairs (computed on first request: k MVPs).
 int deflation_residuals(Op &op, dlz_defl_s *d);

@@ -17,6 +17,7 @@
 
 #include "dlz_internal.cuh"
 #include "krylov_util.cuh"
+#include "prec.cuh"
 #include "reduce.cuh"
 #include "small_dense.h"
 #include "solvers.h"
@@ -266,7 +267,11 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
     DLZ_TRY(f32.alloc((size_t)8 * N * n32 * sizeof(float4)));
     float4 *w32[8];
     for (int i = 0; i < 8; ++i) w32[i] = f32.as<float4>() + (size_t)i * N * n32;
-    DevBuf fpart;
+    DevBuf fpart, pdot;
+    if (d && d->k > 0) {
+        DLZ_TRY(pdot.alloc((size_t)N * d->k * sizeof(double2)));
+        DLZ_TRY(reserve_multidot(op, d->k));
+    }
     const long k1_blocks = (long)((op.g.V + 127) / 128) * N;
     DLZ_TRY(fpart.alloc((size_t)2 * k1_blocks * sizeof(double)));   // K1 and K2a partials
     InnerState *ist = reinterpret_cast<InnerState *>(scal.as<double>());
@@ -335,22 +340,6 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
             all = all && done[q];
         }
         if (all || iters >= p.max_iter) break;
-        if (d && d->k > 0) {
-            // Galerkin projection of each open residual over the deflation set
-            for (int q = 0; q < N; ++q) {
-                if (done[q]) continue;
-                double2 *xq = px + (size_t)q * n64;
-                DLZ_TRY(project64(op, d, pr + (size_t)q * n64, corr.as<double2>(), dots));
-                const double2 *cc = corr.as<double2>();
-                DLZ_TRY(map(op, n64, [=] __device__(long i) {
-                    double2 a = xq[i];
-                    const double2 c = cc[i];
-                    a.x += c.x; a.y += c.y;
-                    xq[i] = a;
-                }));
-            }
-            DLZ_TRY(residuals());
-        }
         // normalised FP32 residuals (zero for finished right-hand sides) and inner tolerances
         std::vector<double> inv(N), tl(N);
         for (int q = 0; q < N; ++q) {
@@ -373,10 +362,40 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
                 r32[i] = make_float4((float)(sc * a.x), (float)(sc * a.y), (float)(sc * b.x), (float)(sc * b.y));
             }));
         }
+        // Galerkin projection of each open residual over the deflation set, in FP32
+        // (Sec. 2: D-MinRes starts with it; repeated at every defect-correction restart):
+        // e0 = V_k H^-1 V_k^dag r, u = r - Q e0; the inner MinRes then starts from e0.
+        const bool proj = d && d->k > 0;
+        if (proj) {
+            const int k = d->k;
+            DLZ_TRY(deflation_v32(op, const_cast<dlz_defl_s *>(d)));
+            const float4 *V32 = d->V32.as<float4>();
+            double2 *pdots = pdot.as<double2>();
+            for (int q = 0; q < N; ++q)
+                DLZ_TRY(multidot<P32>(op, V32, n32, k, w32[0] + (size_t)q * n32, pdots + (size_t)q * k, 1.0));
+            std::vector<double2> hc((size_t)N * k);
+            DLZ_TRY(d2h_sync(op, hc.data(), pdots, hc.size() * sizeof(double2)));
+            std::vector<std::complex<double>> z(k);
+            for (int q = 0; q < N; ++q) {
+                for (int i = 0; i < k; ++i) z[i] = std::complex<double>(hc[(size_t)q * k + i].x, hc[(size_t)q * k + i].y);
+                lu_solve(k, d->Hlu.data(), d->piv.data(), z.data());
+                for (int i = 0; i < k; ++i) hc[(size_t)q * k + i] = make_double2(z[i].real(), z[i].imag());
+            }
+            DLZ_TRY(h2d(op, pdots, hc.data(), hc.size() * sizeof(double2)));
+            for (int q = 0; q < N; ++q)
+                DLZ_TRY(combine<P32>(op, w32[1] + (size_t)q * n32, n32, 1, V32, n32, k, pdots + (size_t)q * k, 1, false,
+                                     false));
+            float4 *qe = w32[2], *r32 = w32[0];
+            DLZ_TRY(wilson32_batch(op, qe, w32[1], DLZ_Q, N));
+            DLZ_TRY(map(op, n32 * N, [=] __device__(long i) {
+                const float4 a = r32[i], b = qe[i];
+                r32[i] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+            }));
+        }
         const int it0 = iters;
         float4 *const bufs[6] = {w32[2], w32[3], w32[4], w32[5], w32[6], w32[7]};
         DLZ_TRY(minres_fused_batch(op, N, w32[0], w32[1], bufs, reinterpret_cast<FusedState *>(ist),
-                                   fpart.as<double>(), d_tol, p, iters, hs));
+                                   fpart.as<double>(), d_tol, p, iters, hs, proj));
         mv_batch += iters - it0;
         // x_q += ||r_q|| e_q
         {
