@@ -3,7 +3,8 @@
 //
 // Four launches per iteration, two of them full passes over the vectors:
 //   K1 (stencil + epilogue, one block = 128 sites of one right-hand side):
-//        v_j   = u_j / beta_j                      (u_j: unnormalised Lanczos vector)
+//        v_j   = u_j / beta_j                      (u_j: unnormalised Lanczos vector; the
+//                                                   v's are never stored, only the u's)
 //        w     = Q v_j - beta_j v_{j-1}            (Q u_j / beta_j: Q is linear)
 //        alpha_j partial = Re <v_j, w>
 //        d_{j-1} = (v_{j-1} - delta d_{j-2} - eps d_{j-3}) / gamma,  e += tau d_{j-1}
@@ -14,7 +15,7 @@
 //   K2b: beta_{j+1}, and the Givens rotation of step j (one block per right-hand side).
 // The block partials of K1 and K2a (block b belongs to right-hand side b mod N)
 // are summed in a fixed order by one-block-per-RHS kernels, so results are
-// deterministic.  Buffers rotate with period 2, so a group of 6 iterations is
+// deterministic.  Buffers rotate with periods 3 and 2, so a group of 6 iterations is
 // captured once as a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
@@ -36,7 +37,8 @@ struct FusedState {          // one per right-hand side (FP64 scalars)
     double eps, delta, gamma, tau;
     double r0;               // ||r|| at the start of the inner solve
     // FP32 copies read by the element updates (no FP64 op or conversion per element):
-    // f[0] 1/beta_j, f[1] beta_j, f[2] delta, f[3] eps, f[4] 1/gamma, f[5] tau, f[6] alpha
+    // f[0] 1/beta_j, f[1] beta_j, f[2] delta, f[3] eps, f[4] 1/gamma, f[5] tau, f[6] alpha,
+    // f[7] 1/beta_{j-1}
     float f[8];
 };
 
@@ -47,9 +49,9 @@ constexpr int kThreads = 128;
 __device__ inline float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 
 __global__ void __launch_bounds__(kThreads)
-k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Vp, float4 *__restrict__ Vc,
-            float4 *__restrict__ W, const float4 *__restrict__ D2, float4 *__restrict__ D3,
-            float4 *__restrict__ E, const float4 *__restrict__ links, Geom g, float kappa, int N,
+k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Up, float4 *__restrict__ W,
+            const float4 *__restrict__ D2, float4 *__restrict__ D3, float4 *__restrict__ E,
+            const float4 *__restrict__ links, Geom g, float kappa, int N,
             FusedState *__restrict__ st, double *__restrict__ partials) {
     const int q = blockIdx.x % N;
     const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
@@ -57,18 +59,18 @@ k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Vp, float4
     const size_t base = (size_t)q * nel;
     float facc = 0.f;
     if (s < g.V) {
-        const float ib = st[q].f[0], bt = st[q].f[1];
+        const float ib = st[q].f[0], bt = st[q].f[1], ibp = st[q].f[7];
         const float de = st[q].f[2], ep = st[q].f[3], ig = st[q].f[4], ta = st[q].f[5];
         float2 o[12];
         wilson_site<float, false, true>(s, g, kappa, Ub + base, links, o);   // Q u_j
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const size_t i = base + (size_t)c * g.V + s;
-            const float4 u = Ub[i], vp = Vp[i], d2 = D2[i], d3 = D3[i];
+            const float4 u = Ub[i], up = Up[i], d2 = D2[i], d3 = D3[i];
             const float4 vj = f4(u.x * ib, u.y * ib, u.z * ib, u.w * ib);
+            const float4 vp = f4(up.x * ibp, up.y * ibp, up.z * ibp, up.w * ibp);
             const float4 w = f4(o[2 * c].x * ib - bt * vp.x, o[2 * c].y * ib - bt * vp.y,
                                 o[2 * c + 1].x * ib - bt * vp.z, o[2 * c + 1].y * ib - bt * vp.w);
-            Vc[i] = vj;
             W[i] = w;
             facc += (vj.x * w.x + vj.y * w.y) + (vj.z * w.z + vj.w * w.w);
             const float4 dn = f4((vp.x - de * d2.x - ep * d3.x) * ig, (vp.y - de * d2.y - ep * d3.y) * ig,
@@ -122,12 +124,13 @@ k_minres_alpha(const double *__restrict__ partials, int nbq, FusedState *__restr
 __global__ void __launch_bounds__(kThreads)
 k_minres_k2a(float4 *__restrict__ W, const float4 *__restrict__ Vc, Geom g, int N,
              const FusedState *__restrict__ st, double *__restrict__ partials) {
+    // Vc: the unnormalised u_j; alpha_j v_j = (alpha_j / beta_j) u_j
     const int q = blockIdx.x % N;
     const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
     const size_t base = (size_t)q * 6 * g.V;
     float facc = 0.f;
     if (s < g.V) {
-        const float al = st[q].f[6];
+        const float al = st[q].f[6] * st[q].f[0];
         float4 w[6], v[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -189,6 +192,7 @@ k_minres_k2b(const double *__restrict__ partials, int nbq, FusedState *__restric
         s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
         s.beta_next = bn;
         s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
+        s.f[7] = s.f[0];             // 1/beta_j, to scale u_j into v_j in the next step
         set_floats(s);
         st[q] = s;
     }
@@ -225,9 +229,10 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
             ms[q] = s0;
         }
     }));
-    float4 *U0 = bufs[0], *Vp0 = bufs[1], *Vc0 = bufs[2], *W0 = bufs[3], *D20 = bufs[4], *D30 = bufs[5];
+    // u_j, u_{j-1} (unnormalised Lanczos vectors), w, d_{j-2}, d_{j-3}
+    float4 *U0 = bufs[0], *Up0 = bufs[1], *W0 = bufs[2], *D20 = bufs[3], *D30 = bufs[4];
     DLZ_CUDA_TRY(cudaMemcpyAsync(U0, r, (size_t)N * n * sizeof(float4), cudaMemcpyDeviceToDevice, op.stream));
-    for (float4 *z : {Vp0, D20, D30})
+    for (float4 *z : {Up0, D20, D30})
         DLZ_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)N * n * sizeof(float4), op.stream));
     if (!e_init) DLZ_CUDA_TRY(cudaMemsetAsync(e, 0, (size_t)N * n * sizeof(float4), op.stream));
     const Geom g = op.g;
@@ -235,18 +240,17 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
     const float4 *links = op.gauge32.as<float4>();
     const unsigned blocks = (unsigned)(((g.V + kThreads - 1) / kThreads) * N);
     double *partials2 = partials + blocks;    // K2a's partials after K1's
-    auto iteration = [&](float4 *U, float4 *Vp, float4 *Vc, float4 *W, float4 *D2, float4 *D3) -> int {
-        // K1 moves 216 reals per site and right-hand side: u, v_{j-1}, d_{j-2}, d_{j-3}, e
-        // read; v_j, w, d_{j-1}, e written (24 each), plus the links once per site
-        op.prof.stencil_start(op.stream, true, g.V, N, 216);
-        k_minres_k1<<<blocks, kThreads, 0, op.stream>>>(U, Vp, Vc, W, D2, D3, e, links, g, kappa, N, ms,
-                                                         partials);
+    auto iteration = [&](float4 *U, float4 *Up, float4 *W, float4 *D2, float4 *D3) -> int {
+        // K1 moves 192 reals per site and right-hand side: u_j, u_{j-1}, d_{j-2}, d_{j-3}, e
+        // read; w, d_{j-1}, e written (24 each), plus the links once per site
+        op.prof.stencil_start(op.stream, true, g.V, N, 192);
+        k_minres_k1<<<blocks, kThreads, 0, op.stream>>>(U, Up, W, D2, D3, e, links, g, kappa, N, ms, partials);
         op.prof.stencil_stop(op.stream);
         k_minres_alpha<<<N, 256, 0, op.stream>>>(partials, (int)(blocks / N), ms);
         op.prof.launches += 2;
         DLZ_CUDA_TRY(cudaGetLastError());
         // u_{j+1} = w - alpha v_j ; beta_{j+1} ; Givens rotation of step j
-        k_minres_k2a<<<blocks, kThreads, 0, op.stream>>>(W, Vc, g, N, ms, partials2);
+        k_minres_k2a<<<blocks, kThreads, 0, op.stream>>>(W, U, g, N, ms, partials2);
         k_minres_k2b<<<N, 256, 0, op.stream>>>(partials2, (int)(blocks / N), ms);
         op.prof.launches += 2;
         DLZ_CUDA_TRY(cudaGetLastError());
@@ -254,12 +258,12 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
     };
     GraphExec ge;
     auto six = [&]() -> int {
-        float4 *U = U0, *Vp = Vp0, *Vc = Vc0, *W = W0, *D2 = D20, *D3 = D30;
+        float4 *U = U0, *Up = Up0, *W = W0, *D2 = D20, *D3 = D30;
         for (int sub = 0; sub < 6; ++sub) {
-            DLZ_TRY(iteration(U, Vp, Vc, W, D2, D3));
-            float4 *tU = U, *tVp = Vp;
-            U = W; Vp = Vc; Vc = tVp; W = tU;     // (U, Vp, Vc, W) -> (W, Vc, Vp, U)
-            std::swap(D2, D3);
+            DLZ_TRY(iteration(U, Up, W, D2, D3));
+            float4 *tUp = Up;
+            Up = U; U = W; W = tUp;               // (U, Up, W) -> (W, U, Up): period 3
+            std::swap(D2, D3);                     // period 2
         }
         return DLZ_OK;
     };
@@ -307,14 +311,16 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
         cudaEventDestroy(te1);
     }
     // the direction update of the last step (after 6k steps the buffers are back
-    // in their starting roles: v_J in Vp, d_{J-1} in D2, d_{J-2} in D3)
+    // in their starting roles: u_J in Up, d_{J-1} in D2, d_{J-2} in D3; v_J = u_J / beta_J)
     {
-        const float4 *vj = Vp0, *d2 = D20, *d3 = D30;
+        const float4 *vj = Up0, *d2 = D20, *d3 = D30;
         float4 *ee = e;
         DLZ_TRY(map(op, n * N, [=] __device__(long i) {
             const int q = (int)(i / n);
             const float de = ms[q].f[2], ep = ms[q].f[3], ig = ms[q].f[4], ta = ms[q].f[5];
-            const float4 vp = vj[i], a = d2[i], b = d3[i];
+            const float ibj = ms[q].f[7];
+            const float4 uj = vj[i], a = d2[i], b = d3[i];
+            const float4 vp = f4(uj.x * ibj, uj.y * ibj, uj.z * ibj, uj.w * ibj);
             const float4 dn = f4((vp.x - de * a.x - ep * b.x) * ig, (vp.y - de * a.y - ep * b.y) * ig,
                                  (vp.z - de * a.z - ep * b.z) * ig, (vp.w - de * a.w - ep * b.w) * ig);
             float4 ev = ee[i];
