@@ -7,8 +7,12 @@ D-MinRes on the other 11 spin-colour point sources (arXiv:0901.3163, Sec. 2
 method on a synthetic stand-in for its quenched lattice).  Every right-hand
 side counts only if its true residual was verified in FP64.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--form plain|chosen]
-                    [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form chosen|plain]
+                    [--plain-steps P] [--impl ours|reference]
+
+`value` is the chosen form (FP32 Lanczos/MinRes with FP64 defect correction,
+right-hand sides batched); the plain FP64 form (one RHS at a time, FP64
+stencil) is timed beside it on the same operator (`plain_fp64`).
 
 Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) solve independent
 replicas of the workload, one per rank, with no collective on the data path.
@@ -28,6 +32,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "wilson_16x16x16x32"
+# restart cycles of the first right-hand side's MinRes-DR phase (both forms)
+DR_CYCLES = 150
+# MVPs per right-hand side of the FP64 form of the workload (150 MinRes-DR(100,40)
+# cycles + finish: 13968 MVPs; D-MinRes: 7648 each for the other 11), the unit the
+# oracle's timing is extrapolated with when no FP64 GPU run is at hand
+REF_MVPS_PER_RHS = 8175
 METRIC = "RHS solved/s to |r|/|b|<1e-10 (MinRes-DR(100,40) + D-MinRes, 12 point sources, 16^3x32)"
 UNIT = "RHS/s"
 
@@ -128,12 +138,21 @@ def run_ours(args):
     Bd = torch.from_numpy(B).to(dev)
     b0, rest = Bd[0].contiguous(), Bd[1:].contiguous()
     prec = dlz.F32 if args.form == "chosen" else dlz.F64
-    p_dr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=4000, check_every=16,
-                              precision=prec)
-    p_d = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=200000, precision=prec,
-                             check_every=16)
 
-    def step(profile=False, host=None):
+    def params(pr):
+        # first RHS: DR_CYCLES MinRes-DR(100,40) restart cycles (run past linear
+        # convergence so that the 40 harmonic Ritz vectors converge), then D-MinRes
+        # from that x over the 40 vectors; the same schedule in both forms
+        p_dr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=DR_CYCLES, check_every=16,
+                                  precision=pr, oversolve=1e9, finish=1)
+        p_d = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=200000, precision=pr,
+                                 check_every=16)
+        return p_dr, p_d
+
+    pars = params(prec)
+
+    def step(profile=False, host=None, pp=None):
+        p_dr, p_d = pp or pars
         p_dr.profile = p_d.profile = int(profile)
         if host is None:
             x0, defl, st = dlz.minresdr(op, b0, p_dr)
@@ -181,19 +200,23 @@ def run_ours(args):
         ms_max, solved_all = ms, float(solved)
     value = solved_all / (ms_max / 1e3)
     # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
-    hb0 = torch.from_numpy(B[0].copy()).pin_memory()
-    hrest = torch.from_numpy(B[1:].copy()).pin_memory()
-    hx0 = torch.empty_like(hb0).pin_memory()
-    hX = torch.empty_like(hrest).pin_memory()
-    barrier()
-    t0 = time.perf_counter()
-    e2e_solved = 0
-    for _ in range(max(1, args.steps)):
-        ok, _ = step(host=(hb0, hrest, hx0, hX))
-        e2e_solved += ok
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = e2e_solved / e2e_s * world
+    e2e = None
+    if not args.no_e2e:
+        hb0 = torch.from_numpy(B[0].copy()).pin_memory()
+        hrest = torch.from_numpy(B[1:].copy()).pin_memory()
+        hx0 = torch.empty_like(hb0).pin_memory()
+        hX = torch.empty_like(hrest).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        e2e_solved = 0
+        for _ in range(max(1, args.steps)):
+            ok, _ = step(host=(hb0, hrest, hx0, hX))
+            e2e_solved += ok
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        e2e_value = e2e_solved / e2e_s * world
+        e2e = {"value": round(e2e_value, 4), "unit": UNIT,
+               "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(B.nbytes)}
     # roofline of the dominant kernel (the Wilson stencil), timed with events inside the steps
     # the dominant kernel is the stencil of the deflated phase (all 11 right-hand sides
     # batched into each launch in the mixed form); the first-RHS phase is reported apart
@@ -219,16 +242,57 @@ def run_ours(args):
                 "traffic": None, "kernel": "k_wilson<double>", "avg_launch_ms": round(avg_ms, 5),
                 "bytes_per_launch": int(bytes_per_launch)}
     else:
+        # the fused MinRes kernel K1 (Q stencil + update epilogue, 11 right-hand sides per
+        # launch): 192 spinor reals per site and RHS + 48 link reals per site, FP32
         ach = bytes_per_launch / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(ach / peaks["hbm_gbs"], 4), "peak_source": src, "traffic": None,
-                "kernel": "k_wilson_batch<float> / k_wilson<float>", "avg_launch_ms": round(avg_ms, 5),
+                "frac": round(ach / peaks["hbm_gbs"], 4), "peak_source": src,
+                "traffic": args.k1_traffic,
+                "kernel": "k_minres_k1 (fused FP32 Q stencil + MinRes update, 11 RHS per launch)",
+                "avg_launch_ms": round(avg_ms, 5), "launches_timed": int(st_n),
                 "bytes_per_launch": int(bytes_per_launch)}
     dr_s = sum(s.seconds for s in stats[0::12]) / max(args.steps, 1)
     d_s = sum(s.seconds for i, s in enumerate(stats) if i % 12) / max(args.steps, 1)
     launches = sum(s.gpu_launches for s in stats) // max(args.steps, 1)
     mvps = sum(s.mvps for s in stats) // max(args.steps, 1)
     iters = [s.iterations for s in stats[:12]]
+    extra = {}
+    if args.form == "chosen" and args.plain_steps > 0:
+        # the plain FP64 form on the same operator: one RHS at a time, FP64 stencil
+        pp = params(dlz.F64)
+        # warm-up of the FP64 kernels: two restart cycles and a short D-MinRes
+        wdr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=2, precision=dlz.F64)
+        _, wd, _ = dlz.minresdr(op, b0, wdr)
+        dlz.dminres(op, wd, rest[:1].contiguous(), dlz.params_default(max_iter=32, precision=dlz.F64))
+        del wd
+        barrier()
+        t0 = time.perf_counter()
+        solved_p = 0
+        pst = []
+        for _ in range(args.plain_steps):
+            ok, allst = step(pp=pp)
+            solved_p += ok
+            pst.extend(allst)
+        barrier()
+        el = time.perf_counter() - t0
+        plain_mvps = sum(s.mvps for s in pst) // args.plain_steps
+        extra["plain_fp64"] = {"value": round(solved_p / el, 4), "unit": UNIT, "steps": args.plain_steps,
+                               "warmup": "2 restart cycles + 32 D-MinRes iterations",
+                               "ms_per_step": round(el / args.plain_steps * 1e3, 1),
+                               "mvps_per_step": int(plain_mvps),
+                               "iterations_first_steps": [s.iterations for s in pst[:12]]}
+        extra["chosen_over_plain"] = round(value / (solved_p / el), 3)
+    # the Wilson stencil alone (Dslash), as the solvers launch it
+    V = int(np.prod(dims))
+    ds = {}
+    for name, dt, nrhs in (("f32_batch11", torch.complex64, 11), ("f64_single", torch.complex128, 1)):
+        xs = torch.randn((nrhs, V, 4, 3), dtype=dt, device=dev)
+        ms_l = dlz.stencil_bench(op, xs, 50)["ms"]
+        real = 4 if dt == torch.complex64 else 8
+        nb = V * (48 * nrhs + (48 if real == 4 else 72)) * real
+        ds[name] = {"avg_launch_ms": round(ms_l, 5), "gbs": round(nb / (ms_l * 1e-3) / 1e9, 1),
+                    "frac_hbm": round(nb / (ms_l * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+        del xs
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2),
@@ -238,15 +302,19 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "lattice": list(dims), "kappa": kappa, "m": w["m"], "k": w["k"],
                    "rhs": 12, "form": args.form, "tol": 1e-10,
                    "l2": "inputs and Krylov basis (2.5 GB) larger than L2; no flush",
+                   "first_rhs": f"{DR_CYCLES} MinRes-DR cycles, then D-MinRes from x",
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": round(e2e_value, 4), "unit": UNIT,
-                "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(B.nbytes)},
+        "e2e": e2e,
         "gpu_launches": int(launches), "mvps_per_step": int(mvps), "iterations_first_steps": iters,
         "phase_seconds": {"first_rhs_dr": round(dr_s, 4), "deflated_11_rhs": round(d_s, 4)},
-        "roofline": roof, "clocks": clk,
+        "d_phase_rhs_per_s": round(11.0 / d_s, 4) if d_s > 0 else None,
+        "roofline": roof, "dslash": ds, "clocks": clk,
     }
+    out.update(extra)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(mvps, budget_s=args.cpu_seconds)
+        # the oracle runs the FP64 algorithm: extrapolate to the FP64 form's MVP count
+        ref_mvps = extra.get("plain_fp64", {}).get("mvps_per_step", REF_MVPS_PER_RHS * 12)
+        out["cpu_baseline"] = cpu_baseline(ref_mvps, budget_s=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -372,10 +440,15 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["plain", "chosen"], default="plain")
+    ap.add_argument("--form", choices=["plain", "chosen"], default="chosen")
+    ap.add_argument("--plain-steps", type=int, default=1,
+                    help="timed steps of the plain FP64 form reported beside the chosen form")
+    ap.add_argument("--k1-traffic", type=float, default=None,
+                    help="ncu DRAM bytes per launch of the dominant kernel, if measured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--ref-mvps-per-rhs", type=int, default=600)
+    ap.add_argument("--ref-mvps-per-rhs", type=int, default=REF_MVPS_PER_RHS)
     ap.add_argument("--stencil-only", action="store_true")
     ap.add_argument("--lattice", default=None)
     ap.add_argument("--nrhs", type=int, default=11)

@@ -89,6 +89,11 @@ typedef struct {
     int check_every;     /* D-CG / D-MinRes: read the residual on the host every this
                             many iterations; 16                                          */
     int profile;         /* 1: time every stencil launch with CUDA events (stats)  ; 0   */
+    int finish;          /* DR solvers, DLZ_F64: when the restart cycles end before the
+                            residual reaches tol (max_cycles), finish the solve with
+                            D-MinRes / D-CG from the current x over the deflation set
+                            just built (1) or return DLZ_ERR_NOT_CONVERGED (0).  The
+                            DLZ_F32 form always finishes this way; 0                     */
 } dlz_params;
 
 /* Per-solve statistics. */

@@ -233,6 +233,7 @@ int check_params(const dlz_params *p) {
         return fail(DLZ_ERR_BADARG, "max_cycles, max_iter, check_every must be >= 1");
     if (p->precision != DLZ_F64 && p->precision != DLZ_F32) return fail(DLZ_ERR_BADARG, "precision");
     if (!(p->reliable_delta > 0.0 && p->reliable_delta < 1.0)) return fail(DLZ_ERR_BADARG, "reliable_delta must be in (0, 1)");
+    if (p->finish != 0 && p->finish != 1) return fail(DLZ_ERR_BADARG, "finish must be 0 or 1");
     return DLZ_OK;
 }
 
@@ -275,6 +276,7 @@ int dlz_params_default(dlz_params *p) {
     p->reliable_delta = 1e-5;
     p->check_every = 16;
     p->profile = 0;
+    p->finish = 0;
     return DLZ_OK;
 }
 

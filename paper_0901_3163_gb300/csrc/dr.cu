@@ -645,7 +645,27 @@ int prepare_kernels(Op &op) {
 
 int dr_solve(Op &op, bool harmonic, const double2 *b, double2 *x, const dlz_params &p,
              dlz_defl_s **defl_out, dlz_stats &st) {
-    if (p.precision == DLZ_F64) return dr_solve_t<P64>(op, harmonic, b, x, p, defl_out, st);
+    if (p.precision == DLZ_F64) {
+        if (!p.finish) return dr_solve_t<P64>(op, harmonic, b, x, p, defl_out, st);
+        // restart cycles, then (if they ended short of tol) D-MinRes / D-CG from x
+        dlz_defl_s *d = nullptr;
+        int rc = dr_solve_t<P64>(op, harmonic, b, x, p, &d, st);
+        if (rc == DLZ_ERR_NOT_CONVERGED && d && st.true_residual > p.tol) {
+            dlz_stats s2;
+            std::memset(&s2, 0, sizeof(s2));
+            rc = harmonic ? dminres64(op, d, b, x, p, s2, x) : dcg64(op, d, b, x, p, s2, x);
+            st.iterations += s2.iterations;
+            st.mvps += s2.mvps;
+            st.true_residual = s2.true_residual;
+            st.converged = s2.converged;
+        } else if (rc == DLZ_ERR_NOT_CONVERGED && st.true_residual <= p.tol) {
+            st.converged = 1;
+            rc = DLZ_OK;
+        }
+        if (defl_out) *defl_out = d;
+        else delete d;
+        return rc;
+    }
     // mixed form: FP32 DR phase, then FP64 defect correction over its deflation set
     dlz_defl_s *d = nullptr;
     int rc = dr_solve_t<P32>(op, harmonic, b, x, p, &d, st);

@@ -212,7 +212,7 @@ static int minres_init(Op &op, MinresState *dst, double *d_norm) {
 }
 
 int dminres64(Op &op, const dlz_defl_s *d, const double2 *b_in, double2 *x_out, const dlz_params &p,
-              dlz_stats &st) {
+              dlz_stats &st, const double2 *x_init) {
     const long n = 12L * op.g.V;
     DevBuf bg, x, r, vp, v, w, d1, d2, scal, dots;
     DLZ_TRY(bg.alloc(n * sizeof(double2)));
@@ -239,8 +239,31 @@ int dminres64(Op &op, const dlz_defl_s *d, const double2 *b_in, double2 *x_out, 
         st.converged = 1; st.true_residual = 0.0;
         return DLZ_OK;
     }
-    if (d && d->k > 0) DLZ_TRY(project64(op, d, bg.as<double2>(), x.as<double2>(), dots));
-    else DLZ_TRY(v64::zero(op, x.as<double2>()));
+    if (x_init) {
+        // x = x_init + V H^-1 V^dag (gamma5 b - Q x_init)
+        DLZ_TRY(v64::copy(op, x.as<double2>(), x_init));
+        if (d && d->k > 0) {
+            DLZ_TRY(wilson64(op, r.as<double2>(), x.as<double2>(), DLZ_Q));
+            st.mvps += 1;
+            const double2 *bgp = bg.as<double2>();
+            double2 *rp = r.as<double2>();
+            DLZ_TRY(map(op, n, [=] __device__(long i) {
+                const double2 a = bgp[i], q = rp[i];
+                rp[i] = make_double2(a.x - q.x, a.y - q.y);
+            }));
+            DLZ_TRY(project64(op, d, r.as<double2>(), d1.as<double2>(), dots));
+            double2 *px0 = x.as<double2>();
+            const double2 *pe = d1.as<double2>();
+            DLZ_TRY(map(op, n, [=] __device__(long i) {
+                const double2 a = px0[i], e = pe[i];
+                px0[i] = make_double2(a.x + e.x, a.y + e.y);
+            }));
+        }
+    } else if (d && d->k > 0) {
+        DLZ_TRY(project64(op, d, bg.as<double2>(), x.as<double2>(), dots));
+    } else {
+        DLZ_TRY(v64::zero(op, x.as<double2>()));
+    }
     bool converged = false;
     while (st.iterations < p.max_iter) {
         // r = gamma5 b - Q x ; start a MinRes run from x
@@ -377,7 +400,7 @@ struct CgState {
 };
 
 int dcg64(Op &op, const dlz_defl_s *d, const double2 *b_in, double2 *x_out, const dlz_params &p,
-          dlz_stats &st) {
+          dlz_stats &st, const double2 *x_init) {
     const long n = 12L * op.g.V;
     DevBuf x, r, s, pp, t, q, bd, scal, dots;
     DLZ_TRY(x.alloc(n * sizeof(double2)));
@@ -403,7 +426,28 @@ int dcg64(Op &op, const dlz_defl_s *d, const double2 *b_in, double2 *x_out, cons
         st.converged = 1; st.true_residual = 0.0;
         return DLZ_OK;
     }
-    if (d && d->k > 0) {
+    if (x_init) {
+        // x = x_init + V H^-1 V^dag D^dag (b - D x_init)
+        DLZ_TRY(v64::copy(op, x.as<double2>(), x_init));
+        if (d && d->k > 0) {
+            DLZ_TRY(wilson64(op, s.as<double2>(), x.as<double2>(), DLZ_D));
+            const double2 *bp = b;
+            double2 *sp = s.as<double2>();
+            DLZ_TRY(map(op, n, [=] __device__(long i) {
+                const double2 a = bp[i], q = sp[i];
+                sp[i] = make_double2(a.x - q.x, a.y - q.y);
+            }));
+            DLZ_TRY(wilson64(op, bd.as<double2>(), s.as<double2>(), DLZ_DDAG));
+            st.mvps += 2;
+            DLZ_TRY(project64(op, d, bd.as<double2>(), t.as<double2>(), dots));
+            double2 *px0 = x.as<double2>();
+            const double2 *pe = t.as<double2>();
+            DLZ_TRY(map(op, n, [=] __device__(long i) {
+                const double2 a = px0[i], e = pe[i];
+                px0[i] = make_double2(a.x + e.x, a.y + e.y);
+            }));
+        }
+    } else if (d && d->k > 0) {
         DLZ_TRY(wilson64(op, bd.as<double2>(), b, DLZ_DDAG));    // b' = D^dag b
         st.mvps += 1;
         DLZ_TRY(project64(op, d, bd.as<double2>(), x.as<double2>(), dots));

@@ -28,10 +28,12 @@ namespace dlz {
 
 int dr_solve(Op &op, bool harmonic, const double2 *b, double2 *x, const dlz_params &p,
              dlz_defl_s **defl_out, dlz_stats &st);
+// x_init (may alias x, may be null): starting guess, corrected by the projection of
+// its residual; null: x0 is the projection of the right-hand side.
 int dminres64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x, const dlz_params &p,
-              dlz_stats &st);
+              dlz_stats &st, const double2 *x_init = nullptr);
 int dcg64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x, const dlz_params &p,
-          dlz_stats &st);
+          dlz_stats &st, const double2 *x_init = nullptr);
 // D-MinRes (minres) or D-CG in FP32 with FP64 defect correction (DLZ_F32).
 // x_init (may alias x, may be null) is the starting guess.
 int dsolve_mixed(Op &op, const dlz_defl_s *d, bool minres, const double2 *b, double2 *x,

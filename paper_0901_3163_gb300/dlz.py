@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("reorth_period", ctypes.c_int), ("precision", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("finish", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

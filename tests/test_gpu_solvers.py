@@ -243,6 +243,29 @@ def test_mixed_precision_dr_first_rhs(m, case, method):
     assert s1[0].converged == 1 and s1[0].iterations < s0[0].iterations
 
 
+@pytest.mark.parametrize("method", ["minresdr", "landr"])
+def test_fp64_dr_capped_then_finished(m, case, method):
+    """finish = 1: FP64 restart cycles capped at 3 (short of tol), then D-MinRes /
+    D-CG from that x over the deflation set just built.  The result reaches 1e-10
+    and agrees with the oracle's undeflated solution within 2e-10 ||b|| / sigma_min;
+    with finish = 0 the same cap returns not-converged."""
+    U, op, b = case
+    Aq, D, Dd, Ad = _ops(U, KAPPA)
+    bf = b.reshape(-1)
+    fn = getattr(m, method)
+    _, _, s0 = fn(op, torch.from_numpy(b).cuda(), _params(m, max_cycles=3), deflate=False)
+    assert s0.converged == 0 and s0.true_residual > 1e-10
+    xg, d, st = fn(op, torch.from_numpy(b).cuda(), _params(m, max_cycles=3, finish=1))
+    assert st.converged == 1 and st.true_residual <= 1e-10 and st.cycles == 3
+    assert st.iterations > s0.iterations
+    xv = xg.cpu().numpy().reshape(-1)
+    assert np.linalg.norm(bf - D(xv)) <= 1.01e-10 * np.linalg.norm(bf)
+    xo, _ = K.minres(Aq, _g5(b), tol=1e-12, maxiter=20000)
+    sig = np.abs(np.linalg.eigvalsh(wilson.dense(Aq, bf.size))).min()
+    assert np.linalg.norm(xv - xo) <= 2e-10 * np.linalg.norm(bf) / sig
+    assert m.defl_count(d)[0] == 10
+
+
 def test_graph_replay_is_bit_identical_to_direct_launches(m, case, tmp_path):
     """The CUDA-graph path (captured Lanczos cycles and MinRes iteration groups)
     gives bit-identical results to plain launches: the reductions have a fixed
