@@ -38,6 +38,10 @@ DR_CYCLES = 150
 # cycles + finish: 13968 MVPs; D-MinRes: 7648 each for the other 11), the unit the
 # oracle's timing is extrapolated with when no FP64 GPU run is at hand
 REF_MVPS_PER_RHS = 8175
+# DRAM bytes (read + write) of one k_minres_k1 launch with 11 right-hand sides on the
+# 16^3x32 lattice, from one ncu capture of the current kernel
+# (ncu --set full -k regex:k_minres_k1 -s 24 -c 1 python bench.py --ncu-case)
+K1_TRAFFIC_BYTES = 751348992 + 376703488
 METRIC = "RHS solved/s to |r|/|b|<1e-10 (MinRes-DR(100,40) + D-MinRes, 12 point sources, 16^3x32)"
 UNIT = "RHS/s"
 
@@ -182,13 +186,15 @@ def run_ours(args):
     solved = 0
     stats = []
     for _ in range(args.steps):
-        ok, allst = step(profile=True)
+        ok, allst = step()
         solved += ok
         stats.extend(allst)
     e1.record()
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    # one more step with every stencil launch timed by CUDA events (roofline only)
+    _, pstats = step(profile=True)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms, float(solved)], device=dev)
@@ -220,7 +226,7 @@ def run_ours(args):
     # roofline of the dominant kernel (the Wilson stencil), timed with events inside the steps
     # the dominant kernel is the stencil of the deflated phase (all 11 right-hand sides
     # batched into each launch in the mixed form); the first-RHS phase is reported apart
-    dstats = [s for i, s in enumerate(stats) if i % 12]
+    dstats = pstats[1:]
     st_ms = sum(s.stencil_ms for s in dstats)
     st_n = sum(s.stencil_launches for s in dstats)
     st_bytes = sum(s.stencil_bytes for s in dstats)
@@ -434,6 +440,26 @@ def run_first_rhs_only(args):
     print(json.dumps({"mode": "first-rhs-only", "form": args.form, "kappa": kappa, "stats": st.as_dict()}))
 
 
+def run_ncu_case(args):
+    """A short run of the benchmark's kernels for ncu captures: the 16^3x32
+    operator, a deflation set from 2 FP32 MinRes-DR(100,40) cycles (their
+    finishing MinRes capped at 12 iterations), then 48 FP32 D-MinRes iterations
+    on the 11 point sources batched (fused kernels with 11 right-hand sides per
+    launch).  Prints the stats."""
+    import torch
+
+    from paper_0901_3163_gb300 import dlz
+    w, dims, U, kappa, B = workload_inputs()
+    op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
+    Bd = torch.from_numpy(B).cuda()
+    p = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=2, max_iter=12, precision=dlz.F32)
+    _, d, st = dlz.minresdr(op, Bd[0].contiguous(), p)
+    pd = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=48, precision=dlz.F32)
+    _, sts = dlz.dminres(op, d, Bd[1:].contiguous(), pd)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "ncu-case", "dr": st.as_dict(), "d_iterations": [s.iterations for s in sts]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,8 +469,8 @@ def main():
     ap.add_argument("--form", choices=["plain", "chosen"], default="chosen")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed steps of the plain FP64 form reported beside the chosen form")
-    ap.add_argument("--k1-traffic", type=float, default=None,
-                    help="ncu DRAM bytes per launch of the dominant kernel, if measured")
+    ap.add_argument("--k1-traffic", type=float, default=K1_TRAFFIC_BYTES,
+                    help="ncu DRAM bytes per launch of the dominant kernel (None if not measured)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -454,6 +480,7 @@ def main():
     ap.add_argument("--nrhs", type=int, default=11)
     ap.add_argument("--stencil-iters", type=int, default=50)
     ap.add_argument("--first-rhs-only", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true")
     ap.add_argument("--max-cycles", type=int, default=4000)
     ap.add_argument("--kappa", type=float, default=None)
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -462,6 +489,8 @@ def main():
         run_stencil_only(args)
     elif args.first_rhs_only:
         run_first_rhs_only(args)
+    elif args.ncu_case:
+        run_ncu_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
