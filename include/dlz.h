@@ -144,6 +144,38 @@ int dlz_op_volume(dlz_op_t op, long long *V);
  */
 int dlz_apply(dlz_op_t op, int which, const void *in, void *out, int dtype, int nrhs);
 
+/* Size of the library's static device scratch used by dlz_apply_noalloc. */
+#define DLZ_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/*
+ * dlz_apply without any device allocation (the paper has no counterpart: it
+ * is a library-interface variant of dlz_apply).  For callers that cannot
+ * allocate device memory at the point of the call: a caller whose memory pool
+ * already holds the device's free memory (cudaMalloc would fail), or one that
+ * keeps other streams busy and cannot afford the device-wide synchronisation
+ * of the cudaFree that dlz_apply's temporary buffers end with.
+ *
+ * Same operation, arguments and layout as dlz_apply, except: in and out must
+ * be device (or managed) pointers (host pointers: DLZ_ERR_BADARG, since
+ * staging them would allocate), and the packed work vectors live in one
+ * static device array of DLZ_NOALLOC_SCRATCH_BYTES per device: 2 vectors of
+ * 12 V complex values (3 for DLZ_DDAGD), 16 B per value for DLZ_F64 and 8 B
+ * for DLZ_F32.  Lattices that need more are rejected with DLZ_ERR_BADARG
+ * before any work is queued (16^3x32: every case fits except DLZ_F64 with
+ * DLZ_DDAGD).  Nothing in the scratch has to start at zero: every element is
+ * written before it is read.
+ *
+ * The array is shared by every operator and thread of the process on that
+ * device: two calls that overlap in time (different host threads, or
+ * operators on different streams) race on it and give wrong results; the
+ * caller must serialise them.  The call is synchronous (returns after the
+ * operator's stream has finished the work), like dlz_apply.  The first call
+ * on each device looks the array's address up (cudaGetSymbolAddress) and
+ * should come before any stream capture that the caller starts.  Returns
+ * DLZ_ERR_CUDA if that lookup fails.
+ */
+int dlz_apply_noalloc(dlz_op_t op, int which, const void *in, void *out, int dtype, int nrhs);
+
 /*
  * Lan-DR(m,k) on A = D^dagger D for D x = b (Sec. 1, Sec. 2): solves
  * D^dagger D x = D^dagger b by restarted Lanczos with a Galerkin solve per

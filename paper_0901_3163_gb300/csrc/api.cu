@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -260,6 +261,34 @@ struct CallStats {
 
 using namespace dlz;
 
+// Static scratch of dlz_apply_noalloc (one per device; shared by all callers on it).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DLZ_NOALLOC_SCRATCH_BYTES];
+
+namespace dlz {
+namespace {
+// Device address of g_noalloc_scratch, looked up once per device.
+int noalloc_scratch(void **out) {
+    static std::mutex mu;
+    static void *addr[128] = {};
+    int dev = 0;
+    DLZ_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return fail(DLZ_ERR_CUDA, "device index out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return fail(DLZ_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        }
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return DLZ_OK;
+}
+}  // namespace
+}  // namespace dlz
+
 extern "C" {
 
 int dlz_params_default(dlz_params *p) {
@@ -408,6 +437,49 @@ int dlz_apply(dlz_op_t h, int which, const void *in, void *out, int dtype, int n
         }
     }
     return so.flush(op);
+}
+
+int dlz_apply_noalloc(dlz_op_t h, int which, const void *in, void *out, int dtype, int nrhs) {
+    DLZ_TRY(check_op(h));
+    Op &op = h->op;
+    if (nrhs < 0) return fail(DLZ_ERR_BADARG, "nrhs < 0");
+    if (which < DLZ_D || which > DLZ_DDAGD) return fail(DLZ_ERR_BADARG, "which");
+    if (dtype != DLZ_F64 && dtype != DLZ_F32) return fail(DLZ_ERR_BADARG, "dtype");
+    const long n = 12L * op.g.V;
+    const size_t esz = dtype == DLZ_F64 ? sizeof(double2) : sizeof(float2);
+    const size_t vec = (size_t)n * esz;
+    const size_t need = (which == DLZ_DDAGD ? 3 : 2) * vec;
+    if (need > (size_t)DLZ_NOALLOC_SCRATCH_BYTES)
+        return fail(DLZ_ERR_BADARG, "lattice too large for the static scratch of dlz_apply_noalloc");
+    if (nrhs == 0) return DLZ_OK;
+    if (!in || !out) return fail(DLZ_ERR_BADARG, "null vector");
+    if (!on_device(in) || !on_device(out))
+        return fail(DLZ_ERR_BADARG, "dlz_apply_noalloc takes device pointers only");
+    const size_t bytes = vec * nrhs;
+    const char *ip = (const char *)in, *op_ = (const char *)out;
+    if (ip < op_ + bytes && op_ < ip + bytes) return fail(DLZ_ERR_BADARG, "in and out overlap");
+    void *scratch = nullptr;
+    DLZ_TRY(noalloc_scratch(&scratch));
+    op.prof.begin(false, false);
+    // packed input, packed output and (D^dag D only) the intermediate Q vector
+    unsigned char *sa = (unsigned char *)scratch, *sb = sa + vec, *st = sb + vec;
+    for (int r = 0; r < nrhs; ++r) {
+        if (dtype == DLZ_F64) {
+            const double2 *src = (const double2 *)in + (size_t)r * n;
+            double2 *dst = (double2 *)out + (size_t)r * n;
+            DLZ_TRY(pack64(op, (double2 *)sa, src));
+            DLZ_TRY(apply64(op, (double2 *)sb, (const double2 *)sa, which, (double2 *)st));
+            DLZ_TRY(unpack64(op, dst, (const double2 *)sb));
+        } else {
+            const float2 *src = (const float2 *)in + (size_t)r * n;
+            float2 *dst = (float2 *)out + (size_t)r * n;
+            DLZ_TRY(pack32(op, (float4 *)sa, src));
+            DLZ_TRY(apply32(op, (float4 *)sb, (const float4 *)sa, which, (float4 *)st));
+            DLZ_TRY(unpack32(op, dst, (const float4 *)sb));
+        }
+    }
+    DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+    return DLZ_OK;
 }
 
 int dlz_stencil_bench(dlz_op_t h, int dtype, int which, int nrhs, int iters, const void *in,

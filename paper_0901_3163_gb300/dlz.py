@@ -76,6 +76,7 @@ _SIGS = {
     "dlz_destroy_operator": ([_vp], _ip),
     "dlz_op_volume": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _ip),
     "dlz_apply": ([_vp, _ip, _vp, _vp, _ip, _ip], _ip),
+    "dlz_apply_noalloc": ([_vp, _ip, _vp, _vp, _ip, _ip], _ip),
     "dlz_landr": ([_vp, _vp, _vp, ctypes.POINTER(Params), ctypes.POINTER(_vp),
                    ctypes.POINTER(Stats)], _ip),
     "dlz_minresdr": ([_vp, _vp, _vp, ctypes.POINTER(Params), ctypes.POINTER(_vp),
@@ -275,6 +276,17 @@ def defl_load(op, path):
     h = _vp()
     _check(lib.dlz_defl_load(op.handle, str(path).encode(), ctypes.byref(h)))
     return Deflation(h, op)
+
+
+def apply_noalloc(op, which, x, out=None):
+    """dlz_apply_noalloc: out = A x like apply(), with device tensors only and the
+    library's static device scratch instead of temporary allocations."""
+    dtype = F32 if str(x.dtype).endswith("complex64") else F64
+    nrhs = int(np.prod(x.shape)) // (12 * op.volume)
+    if out is None:
+        out = _empty_like(x)
+    _check(lib.dlz_apply_noalloc(op.handle, int(which), _ptr(x), _ptr(out), dtype, nrhs))
+    return out
 
 
 def stencil_bench(op, x, iters=50, which=D):
