@@ -68,6 +68,7 @@ extern "C" {
 
 typedef struct dlz_op_s *dlz_op_t;
 typedef struct dlz_defl_s *dlz_defl_t;
+typedef struct dlz_net_s *dlz_net_t;
 
 /* Solver parameters; dlz_params_default() fills the defaults given here. */
 typedef struct {
@@ -245,6 +246,55 @@ int dlz_defl_destroy(dlz_defl_t d);
  */
 int dlz_stencil_bench(dlz_op_t op, int dtype, int which, int nrhs, int iters, const void *in,
                       double *ms_per_launch);
+
+/*
+ * Learned seed for the deflation space (no counterpart in the paper, which
+ * builds the deflation space with Lan-DR / MinRes-DR only): a gauge-covariant
+ * parallel-transport convolution (PTC) network on the operator's lattice and
+ * links.  Layer l maps widths[l] channels to widths[l+1] channels (each a
+ * spinor field):
+ *   out[c'](x) = sum_o sum_c W[o][c'][c] (T_o in[c])(x),
+ * o = 0, +mu (1 + 2 mu), -mu (2 + 2 mu) for mu = x, y, z, t; T_0 = 1,
+ * (T_+mu psi)(x) = U_mu(x) psi(x + mu), (T_-mu psi)(x) = U_mu(x - mu)^dag psi(x - mu),
+ * periodic in all directions whatever the operator's time boundary; each
+ * W[o][c'][c] is a complex 4x4 spin matrix (entry [4 s' + s]).  No
+ * activation: the network is linear in its input.  The kernels use the
+ * weights rounded to bfloat16 and compute in FP32; an FP32 master copy is
+ * what the optimiser updates.  Gradients are G(z) = dL/dRe z + i dL/dIm z.
+ *
+ * dlz_net_create: nlayers in [1, 8], widths[0] = widths[nlayers] = 1, every
+ *   width in [1, 16]; weights: complex64, the layers one after another, each
+ *   [9][widths[l+1]][widths[l]][16] (host or device; copied).
+ * dlz_net_forward: in, out: device complex64 [nvec][V][4][3]; keeps every
+ *   layer's input for the next dlz_net_backward.
+ * dlz_net_backward: grad_out = G(out) of the last forward (same nvec);
+ *   adds G(W) to the gradient buffer; grad_in (may be NULL) receives G(in).
+ * dlz_net_get: what = 0 master weights, 1 gradients, 2 the bfloat16 weights in
+ *   use (as complex64); host_out holds dlz_net_weight_count complex64 values.
+ * dlz_net_adam_step: Adam (bias-corrected) on every real and imaginary part
+ *   of the master weights, then refreshes the bfloat16 copy and clears the
+ *   gradients.
+ * dlz_subspace_loss: per vector f_i (device complex64 [nvec][V][4][3]),
+ *   loss[i] = ||(1 - V V^dag) f_i||^2 / ||f_i||^2 against the deflation set's
+ *   orthonormal vectors V (host double[nvec]); grad (device complex64, may be
+ *   NULL) receives G(f_i) = 2 ((1 - V V^dag) f_i - loss[i] f_i) / ||f_i||^2.
+ * dlz_seed_deflation: a deflation set from k device vectors (dtype DLZ_F64:
+ *   complex128, DLZ_F32: complex64, [k][V][4][3]): orthonormalised (modified
+ *   Gram-Schmidt twice, in FP64), then H = V^dag A V (k MVPs of A = Q or
+ *   D^dag D) and its Rayleigh-Ritz pairs, usable by dlz_dcg / dlz_dminres /
+ *   dlz_defl_get.  DLZ_ERR_BREAKDOWN if the vectors are linearly dependent.
+ */
+int dlz_net_create(dlz_op_t op, int nlayers, const int *widths, const void *weights, dlz_net_t *net);
+int dlz_net_destroy(dlz_net_t net);
+int dlz_net_weight_count(dlz_net_t net, long long *count);
+int dlz_net_forward(dlz_net_t net, const void *in, int nvec, void *out);
+int dlz_net_backward(dlz_net_t net, const void *grad_out, int nvec, void *grad_in);
+int dlz_net_get(dlz_net_t net, int what, void *host_out);
+int dlz_net_set_weights(dlz_net_t net, const void *weights);
+int dlz_net_zero_grad(dlz_net_t net);
+int dlz_net_adam_step(dlz_net_t net, double lr, double beta1, double beta2, double eps);
+int dlz_subspace_loss(dlz_defl_t defl, const void *f, int nvec, double *loss, void *grad);
+int dlz_seed_deflation(dlz_op_t op, int which, const void *vecs, int dtype, int k, dlz_defl_t *defl_out);
 
 /*
  * Host-side dense helpers used by the restart (exported for testing; no

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdlz.so")
 SOURCES = ["wilson.cu", "dr.cu", "solvers.cu", "solvers_mixed.cu", "minres_fused.cu", "api.cu",
-           "small_dense.cpp"]
+           "ptc.cu", "small_dense.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

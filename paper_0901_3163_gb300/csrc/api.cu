@@ -15,13 +15,6 @@
 #include "reduce.cuh"
 #include "solvers.h"
 
-struct dlz_op_s {
-    dlz::Op op;
-    ~dlz_op_s() {
-        if (op.cap_stream) cudaStreamDestroy(op.cap_stream);
-    }
-};
-
 namespace dlz {
 
 namespace {

@@ -24,6 +24,14 @@ struct dlz_defl_s {
     std::vector<std::complex<double>> Z;        // eigenvectors of H (column j <-> values[j])
 };
 
+// The operator object behind dlz_op_t.
+struct dlz_op_s {
+    dlz::Op op;
+    ~dlz_op_s() {
+        if (op.cap_stream) cudaStreamDestroy(op.cap_stream);
+    }
+};
+
 namespace dlz {
 
 int dr_solve(Op &op, bool harmonic, const double2 *b, double2 *x, const dlz_params &p,

@@ -89,6 +89,17 @@ _SIGS = {
     "dlz_defl_load": ([_vp, ctypes.c_char_p, ctypes.POINTER(_vp)], _ip),
     "dlz_defl_destroy": ([_vp], _ip),
     "dlz_stencil_bench": ([_vp, _ip, _ip, _ip, _ip, _vp, _dp], _ip),
+    "dlz_net_create": ([_vp, _ip, ctypes.POINTER(ctypes.c_int), _vp, ctypes.POINTER(_vp)], _ip),
+    "dlz_net_destroy": ([_vp], _ip),
+    "dlz_net_weight_count": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _ip),
+    "dlz_net_forward": ([_vp, _vp, _ip, _vp], _ip),
+    "dlz_net_backward": ([_vp, _vp, _ip, _vp], _ip),
+    "dlz_net_get": ([_vp, _ip, _vp], _ip),
+    "dlz_net_set_weights": ([_vp, _vp], _ip),
+    "dlz_net_zero_grad": ([_vp], _ip),
+    "dlz_net_adam_step": ([_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double], _ip),
+    "dlz_subspace_loss": ([_vp, _vp, _ip, _dp, _vp], _ip),
+    "dlz_seed_deflation": ([_vp, _ip, _vp, _ip, _ip, ctypes.POINTER(_vp)], _ip),
     "dlz_host_symeig": ([_ip, _vp, _vp, _vp], _ip),
     "dlz_host_lstsq": ([_ip, _ip, _vp, _vp, _vp, _vp], _ip),
 }
@@ -296,6 +307,108 @@ def stencil_bench(op, x, iters=50, which=D):
     ms = ctypes.c_double()
     _check(lib.dlz_stencil_bench(op.handle, dtype, int(which), nrhs, int(iters), _ptr(x), ctypes.byref(ms)))
     return {"ms": ms.value, "nrhs": nrhs}
+
+
+class Network:
+    """Handle of a dlz_net_t: the parallel-transport convolution network."""
+
+    def __init__(self, handle, op, widths):
+        self.handle = handle
+        self.op = op
+        self.widths = tuple(widths)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and lib is not None:
+            lib.dlz_net_destroy(self.handle)
+            self.handle = None
+
+
+def net_weight_shapes(widths):
+    """Shapes of the layers' weights: (9, w[l+1], w[l], 4, 4)."""
+    return [(9, widths[i + 1], widths[i], 4, 4) for i in range(len(widths) - 1)]
+
+
+def _flat_weights(Ws):
+    return np.ascontiguousarray(np.concatenate([np.asarray(w).reshape(-1) for w in Ws]).astype(np.complex64))
+
+
+def _split_weights(flat, widths):
+    out, o = [], 0
+    for shp in net_weight_shapes(widths):
+        n = int(np.prod(shp))
+        out.append(flat[o:o + n].reshape(shp))
+        o += n
+    return out
+
+
+def net_create(op, widths, Ws):
+    """dlz_net_create with per-layer complex weights Ws (shapes net_weight_shapes(widths))."""
+    w = (ctypes.c_int * len(widths))(*widths)
+    flat = _flat_weights(Ws)
+    h = _vp()
+    _check(lib.dlz_net_create(op.handle, len(widths) - 1, w, flat.ctypes.data, ctypes.byref(h)))
+    return Network(h, op, widths)
+
+
+def net_forward(net, x, out=None):
+    """f = N x for device complex64 x [nvec, V, 4, 3] (or [V, 4, 3])."""
+    nvec = int(np.prod(x.shape)) // (12 * net.op.volume)
+    if out is None:
+        out = _empty_like(x)
+    _check(lib.dlz_net_forward(net.handle, _ptr(x), nvec, _ptr(out)))
+    return out
+
+
+def net_backward(net, grad_out, want_input_grad=False):
+    """Adds G(W) of the last forward to the gradients; returns G(x) if asked."""
+    nvec = int(np.prod(grad_out.shape)) // (12 * net.op.volume)
+    gin = _empty_like(grad_out) if want_input_grad else None
+    _check(lib.dlz_net_backward(net.handle, _ptr(grad_out), nvec, _ptr(gin)))
+    return gin
+
+
+def _net_count(net):
+    c = ctypes.c_longlong()
+    _check(lib.dlz_net_weight_count(net.handle, ctypes.byref(c)))
+    return c.value
+
+
+def net_get(net, what=0):
+    """Per-layer arrays: what = 0 master weights, 1 gradients, 2 bfloat16 weights in use."""
+    flat = np.empty(_net_count(net), dtype=np.complex64)
+    _check(lib.dlz_net_get(net.handle, int(what), flat.ctypes.data))
+    return _split_weights(flat, net.widths)
+
+
+def net_set_weights(net, Ws):
+    flat = _flat_weights(Ws)
+    _check(lib.dlz_net_set_weights(net.handle, flat.ctypes.data))
+
+
+def net_zero_grad(net):
+    _check(lib.dlz_net_zero_grad(net.handle))
+
+
+def net_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(lib.dlz_net_adam_step(net.handle, float(lr), float(beta1), float(beta2), float(eps)))
+
+
+def subspace_loss(defl, f, want_grad=True):
+    """Per-vector ||(1 - V V^dag) f||^2 / ||f||^2 against defl, and G(f) (device complex64)."""
+    nvec = int(np.prod(f.shape)) // (12 * defl.op.volume)
+    loss = np.empty(nvec)
+    g = _empty_like(f) if want_grad else None
+    _check(lib.dlz_subspace_loss(defl.handle, _ptr(f), nvec, loss.ctypes.data_as(_dp), _ptr(g)))
+    return loss, g
+
+
+def seed_deflation(op, vecs, which=DDAGD):
+    """Deflation set from the span of k device vectors [k, V, 4, 3] (Rayleigh-Ritz with A)."""
+    dtype = F32 if str(vecs.dtype).endswith("complex64") else F64
+    k = int(np.prod(vecs.shape)) // (12 * op.volume)
+    h = _vp()
+    _check(lib.dlz_seed_deflation(op.handle, int(which), _ptr(vecs), dtype, k, ctypes.byref(h)))
+    return Deflation(h, op)
 
 
 def host_symeig(A):
