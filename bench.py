@@ -460,6 +460,88 @@ def run_ncu_case(args):
     print(json.dumps({"mode": "ncu-case", "dr": st.as_dict(), "d_iterations": [s.iterations for s in sts]}))
 
 
+def run_learned_seed(args):
+    """The learned deflation seed on the 16^4 lattice (kappa 0.25, the same link
+    recipe): Lan-DR(100,40) eigenvectors of `--ls-train` training fields (gauge
+    seeds 1000...), Adam training of the 1 -> 12 -> 16 -> 1 PTC network for
+    `--ls-steps` steps of 4 noise vectors, then on `--ls-test` held-out fields
+    (gauge seeds 2000...) the seeded Rayleigh-Ritz set (40 MVPs) against one
+    Lan-DR(100,40) cycle (100 MVPs) and the untrained network: median Ritz
+    residuals and D-CG iterations on 4 Gaussian right-hand sides.  Also times
+    the network's forward and backward launches.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_0901_3163_gb300 import dlz
+    from paper_0901_3163_gb300 import ptc_train as T
+    dims, kappa, m, k = (16, 16, 16, 16), 0.25, 100, 40
+    V = synth.volume(dims)
+    t0 = time.perf_counter()
+    train_ops, train_defl, lan_s = [], [], []
+    for i in range(args.ls_train):
+        op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, 1000 + i)).cuda(), kappa)
+        b = torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda()
+        ta = time.perf_counter()
+        _, d, st = dlz.landr(op, b, dlz.params_default(m=m, k=k, tol=1e-10, max_cycles=400))
+        torch.cuda.synchronize()
+        lan_s.append(time.perf_counter() - ta)
+        train_ops.append(op)
+        train_defl.append(d)
+    t_data = time.perf_counter() - t0
+    widths = T.default_widths()
+    W0 = T.init_weights(widths, 1)
+    net = dlz.net_create(train_ops[0], widths, W0)
+    net0 = dlz.net_create(train_ops[0], widths, W0)
+    # kernel timing: one forward and one backward of 4 vectors (CUDA events)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    x = T.noise(torch, train_ops[0], 4, gen)
+    f = dlz.net_forward(net, x)
+    dlz.net_backward(net, f)
+    dlz.net_zero_grad(net)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        dlz.net_forward(net, x, out=f)
+    e1.record()
+    for _ in range(5):
+        dlz.net_backward(net, f)
+    e2.record()
+    torch.cuda.synchronize()
+    dlz.net_zero_grad(net)
+    fw_ms, bw_ms = e0.elapsed_time(e1) / 5, e1.elapsed_time(e2) / 5
+    # algorithmic flops: per layer, site and vector 9 c_in c_out 48 complex FMAs (spin
+    # mixing) + 9 c_in 36 (transport), 8 real flops each; backward twice that
+    fl = sum(9 * widths[i] * (widths[i + 1] * 48 + 36) * 8 for i in range(len(widths) - 1)) * V * 4
+    t1 = time.perf_counter()
+    hist = T.train(torch, net, train_ops, train_defl, steps=args.ls_steps, nvec=4, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    evals = []
+    for j in range(args.ls_test):
+        op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, 2000 + j)).cuda(), kappa)
+        bl = [torch.from_numpy(synth.gaussian_spinor(dims, s)).cuda() for s in (0, 1, 2, 3, 4)]
+        evals.append(T.evaluate(torch, net, op, bl, m, k, seed=j, net_untrained=net0))
+    med = lambda key: float(np.median([e[key] for e in evals]))
+    mean_it = lambda key: float(np.mean([np.mean(e[key]) for e in evals]))
+    out = {"mode": "learned-seed", "workload": "16^4 kappa 0.25, PTC 1-12-16-1, Lan-DR(100,40)",
+           "train_fields": args.ls_train, "test_fields": args.ls_test, "steps": args.ls_steps,
+           "data_seconds": round(t_data, 2), "lanczos_seconds_per_field": round(float(np.mean(lan_s)), 3),
+           "train_seconds": round(t_train, 2), "loss_first20": round(float(np.mean(hist[:20])), 5),
+           "loss_last20": round(float(np.mean(hist[-20:])), 5),
+           "forward_ms_4vec": round(fw_ms, 3), "backward_ms_4vec": round(bw_ms, 3),
+           "forward_tflops": round(fl / (fw_ms * 1e-3) / 1e12, 2),
+           "backward_tflops": round(2 * fl / (bw_ms * 1e-3) / 1e12, 2),
+           "ritz_median": {"seed": med("ritz_median_seed"), "untrained": med("ritz_median_untrained"),
+                           "plain_one_cycle": med("ritz_median_plain")},
+           "dcg_iterations_mean": {"seed": mean_it("dcg_iters_seed"), "plain_one_cycle": mean_it("dcg_iters_plain_cycle"),
+                                   "undeflated": mean_it("cg_iters_undeflated")},
+           "chosen": [e["chosen"] for e in evals], "all_converged": all(e["converged"] for e in evals)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -481,6 +563,10 @@ def main():
     ap.add_argument("--stencil-iters", type=int, default=50)
     ap.add_argument("--first-rhs-only", action="store_true")
     ap.add_argument("--ncu-case", action="store_true")
+    ap.add_argument("--learned-seed", action="store_true")
+    ap.add_argument("--ls-train", type=int, default=32)
+    ap.add_argument("--ls-test", type=int, default=8)
+    ap.add_argument("--ls-steps", type=int, default=400)
     ap.add_argument("--max-cycles", type=int, default=4000)
     ap.add_argument("--kappa", type=float, default=None)
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -491,6 +577,8 @@ def main():
         run_first_rhs_only(args)
     elif args.ncu_case:
         run_ncu_case(args)
+    elif args.learned_seed:
+        run_learned_seed(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -80,9 +80,11 @@ typedef struct {
                             MVPs before it (Sec. 2: at most a factor of two); 1.0         */
     int max_cycles;      /* restart cycles (DR solvers); 1000                            */
     int max_iter;        /* iterations (D-CG / D-MinRes); 100000                         */
-    int reorth_period;   /* re-orthogonalise against the kept vectors every this many
-                            Lanczos steps, at the restart vector and the first new step
-                            (Sec. 2: periodic, period not given); 10                      */
+    int reorth_period;   /* MinRes-DR: re-orthogonalise against the kept vectors every
+                            this many Lanczos steps, at the restart vector and the first
+                            new step (Sec. 2: periodic, period not given); Lan-DR does it
+                            at every step when this is > 0 (its converged regular Ritz
+                            vectors need it); 0 turns it off; 10                          */
     int precision;       /* DLZ_F64 or DLZ_F32 (hot loop of D-CG / D-MinRes); DLZ_F64     */
     double reliable_delta; /* DLZ_F32: each FP32 inner solve reduces the residual by
                               this factor, then x is updated and the residual recomputed
@@ -265,6 +267,8 @@ int dlz_stencil_bench(dlz_op_t op, int dtype, int which, int nrhs, int iters, co
  * dlz_net_create: nlayers in [1, 8], widths[0] = widths[nlayers] = 1, every
  *   width in [1, 16]; weights: complex64, the layers one after another, each
  *   [9][widths[l+1]][widths[l]][16] (host or device; copied).
+ * dlz_net_bind: the links (and stream) of another operator on the same lattice
+ *   are used from now on (a network is trained over many gauge fields).
  * dlz_net_forward: in, out: device complex64 [nvec][V][4][3]; keeps every
  *   layer's input for the next dlz_net_backward.
  * dlz_net_backward: grad_out = G(out) of the last forward (same nvec);
@@ -286,6 +290,7 @@ int dlz_stencil_bench(dlz_op_t op, int dtype, int which, int nrhs, int iters, co
  */
 int dlz_net_create(dlz_op_t op, int nlayers, const int *widths, const void *weights, dlz_net_t *net);
 int dlz_net_destroy(dlz_net_t net);
+int dlz_net_bind(dlz_net_t net, dlz_op_t op);
 int dlz_net_weight_count(dlz_net_t net, long long *count);
 int dlz_net_forward(dlz_net_t net, const void *in, int nvec, void *out);
 int dlz_net_backward(dlz_net_t net, const void *grad_out, int nvec, void *grad_in);

@@ -244,8 +244,9 @@ def lanczos_extend(A, V, T, j0, m, kept=0, reorth_period=10, full_reorth=False,
                 for i in range(j + 1):
                     w -= _dot(V[i], w) * V[i]
         elif kept > 0 and reorth_period and (j - j0) % reorth_period == 0:
-            for i in range(kept):
-                w -= _dot(V[i], w) * V[i]
+            # w -= V_kept (V_kept^dag w)
+            Vk = store[:kept] if store is not None else np.array(V[:kept])
+            w -= Vk.T @ (Vk.conj() @ w)
         beta = _norm(w)
         T[j, j] = alpha
         T[j + 1, j] = beta
@@ -313,6 +314,11 @@ def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
     Ritz pair has a residual <= eig_stop (or, for a callable,
     eig_stop(value, residual) is true).
     """
+    # Converged kept Ritz vectors attract rounding errors in every new Lanczos
+    # vector (the loss of orthogonality grows like eps ||A|| / Ritz residual), so
+    # Lan-DR re-orthogonalises against the kept vectors at every step.
+    if reorth_period:
+        reorth_period = 1
     return _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth,
                residual, oversolve, harmonic=False, eig_stop=eig_stop, progress=progress)
 

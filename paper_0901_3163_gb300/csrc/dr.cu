@@ -443,6 +443,13 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
     // DLZ_TRACE=1: per-phase wall times on stderr (diagnostics)
     const char *trace_env = std::getenv("DLZ_TRACE");
     const bool trace = trace_env && trace_env[0] == '1';
+    // Lan-DR: once kept regular Ritz vectors converge (the over-solve), new Lanczos
+    // vectors lose orthogonality to them within a few steps (the loss grows like
+    // rounding * ||A|| / Ritz residual), and a period of 10 lets spurious Ritz values
+    // (negative ones, for the positive definite D^dag D) into the kept set: seen at
+    // 16^4 after 8 cycles in FP64 and after 3 in FP32.  Lan-DR therefore
+    // re-orthogonalises against the kept vectors at every step.
+    const int rperiod = (!harmonic && p.reorth_period > 0) ? 1 : p.reorth_period;
     double t_lanczos = 0, t_host = 0, t_restart = 0;
     auto now = [] { return std::chrono::steady_clock::now(); };
     auto secs = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
@@ -463,7 +470,7 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         E *ucur = w.as<E>(), *uoth = P::kF32 ? w2.as<E>() : nullptr;
         bool vmat = true;
         for (int j = j0; j < m; ++j) {
-            const bool reorth_j = (j0 > 0) && p.reorth_period > 0 && ((j - j0) % p.reorth_period == 0);
+            const bool reorth_j = (j0 > 0) && rperiod > 0 && ((j - j0) % rperiod == 0);
             if constexpr (P::kF32) {
                 if (j > j0 && !reorth_j) {
                     DLZ_TRY(lanczos_fused_step(op, !harmonic, ucur, s_invbeta + (j - 1), V + (size_t)(j - 1) * n,
@@ -568,7 +575,7 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         // ---------------- restart: V_{k+1} <- V_{m+1} P
         DLZ_TRY(h2d(op, coef.p, pl.P.data(), pl.P.size() * sizeof(double)));
         DLZ_TRY(combine<P>(op, Vn, n, k + 1, V, n, m + 1, coef.p, k + 1, true, false));
-        if (p.reorth_period > 0) {
+        if (rperiod > 0) {
             // the vector carried across the restart joins the periodic re-orthogonalisation
             E *vk = Vn + (size_t)k * n;
             double2 *cd = coef.as<double2>() + (size_t)(m + 1) * (k + 1);
@@ -588,6 +595,17 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         st.true_residual = rel;
         if (!std::isfinite(rel)) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
         hist.push_back(rel);
+        if (trace) {
+            double bmin = 1e300, tmin = 1e300, tmax = -1e300, rmax = 0.0;
+            for (int j = j0; j < m; ++j) bmin = std::min(bmin, T[(size_t)(j + 1) * m + j]);
+            for (int l = 0; l < k; ++l) {
+                tmin = std::min(tmin, pl.theta[l]);
+                tmax = std::max(tmax, pl.theta[l]);
+                rmax = std::max(rmax, pl.res[l]);
+            }
+            std::fprintf(stderr, "[dlz]   cycle %d rel %.3e beta_min %.3e theta [%.4e, %.4e] ritz_res_max %.3e\n",
+                         cycle, rel, bmin, tmin, tmax, rmax);
+        }
         bool lin_ok = rel <= p.tol;
         if (P::kF32 && !lin_ok && hist.size() >= 4) {
             // FP32 basis: the residual stalls near eps_32 * cond; stop the DR phase there

@@ -558,6 +558,16 @@ int dlz_net_adam_step(dlz_net_t net, double lr, double beta1, double beta2, doub
     return DLZ_OK;
 }
 
+int dlz_net_bind(dlz_net_t net, dlz_op_t h) {
+    if (!net || !h) return fail(DLZ_ERR_BADARG, "null argument");
+    const Geom &a = net->op->g, &b = h->op.g;
+    for (int d = 0; d < 4; ++d)
+        if (a.L[d] != b.L[d]) return fail(DLZ_ERR_BADARG, "net_bind needs an operator on the same lattice");
+    DLZ_CUDA_TRY(cudaStreamSynchronize(net->op->stream));
+    net->op = &h->op;
+    return DLZ_OK;
+}
+
 int dlz_net_weight_count(dlz_net_t net, long long *count) {
     if (!net || !count) return fail(DLZ_ERR_BADARG, "null argument");
     *count = (long long)net->nw;

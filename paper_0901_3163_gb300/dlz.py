@@ -92,6 +92,7 @@ _SIGS = {
     "dlz_net_create": ([_vp, _ip, ctypes.POINTER(ctypes.c_int), _vp, ctypes.POINTER(_vp)], _ip),
     "dlz_net_destroy": ([_vp], _ip),
     "dlz_net_weight_count": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _ip),
+    "dlz_net_bind": ([_vp, _vp], _ip),
     "dlz_net_forward": ([_vp, _vp, _ip, _vp], _ip),
     "dlz_net_backward": ([_vp, _vp, _ip, _vp], _ip),
     "dlz_net_get": ([_vp, _ip, _vp], _ip),
@@ -348,6 +349,12 @@ def net_create(op, widths, Ws):
     h = _vp()
     _check(lib.dlz_net_create(op.handle, len(widths) - 1, w, flat.ctypes.data, ctypes.byref(h)))
     return Network(h, op, widths)
+
+
+def net_bind(net, op):
+    """Use op's links from now on (same lattice)."""
+    _check(lib.dlz_net_bind(net.handle, op.handle))
+    net.op = op
 
 
 def net_forward(net, x, out=None):
