@@ -575,8 +575,8 @@ static int dsolve_entry(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nr
     DLZ_TRY(sb.in(op, B, (size_t)n * nrhs * sizeof(double2)));
     DLZ_TRY(sx.out(op, X, (size_t)n * nrhs * sizeof(double2)));
     int worst = DLZ_OK;
-    if (p->precision == DLZ_F32 && minres) {
-        // batched mixed-precision D-MinRes, up to 16 right-hand sides per pass
+    if (p->precision == DLZ_F32) {
+        // batched mixed-precision D-MinRes / D-CG, up to 16 right-hand sides per pass
         const int chunk = std::min(nrhs, 16);
         DevBuf bi, xi;
         DLZ_TRY(bi.alloc((size_t)chunk * n * sizeof(double2)));
@@ -587,7 +587,7 @@ static int dsolve_entry(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nr
             CallStats cs(op, nullptr, p->profile != 0, p->precision == DLZ_F32);
             for (int q = 0; q < nb; ++q)
                 DLZ_TRY(pack64(op, bi.as<double2>() + (size_t)q * n, (const double2 *)sb.dev + (size_t)(r0 + q) * n));
-            const int rc = dsolve_mixed_batch(op, d, true, bi.as<double2>(), xi.as<double2>(), nb, *p, sts.data());
+            const int rc = dsolve_mixed_batch(op, d, minres, bi.as<double2>(), xi.as<double2>(), nb, *p, sts.data());
             if (rc != DLZ_OK && rc != DLZ_ERR_NOT_CONVERGED) return rc;
             if (rc != DLZ_OK) worst = rc;
             for (int q = 0; q < nb; ++q)

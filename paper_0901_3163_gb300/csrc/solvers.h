@@ -61,6 +61,11 @@ struct HostScratch;
 int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const bufs[6],
                        FusedState *ms, double *partials, const double *d_tol,
                        const dlz_params &p, int &iters, HostScratch &hs, bool e_init = false);
+// Fused FP32 CG on the normal equations for D e = s0 on N right-hand sides
+// (cg_fused.cu); s0 is overwritten, e is updated in place (holds the start).
+struct CgFusedState;
+int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5], CgFusedState *ms,
+                     double *partials, const double *d_tol, const dlz_params &p, int &iters, HostScratch &hs);
 // FP32 copy of the deflation basis (made on first use).
 int deflation_v32(Op &op, dlz_defl_s *d);
 int deflation_finish(Op &op, dlz_defl_s *d);

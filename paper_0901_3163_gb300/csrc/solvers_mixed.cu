@@ -247,13 +247,6 @@ constexpr int kMaxBatch = 16;
 int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *B, double2 *X, int N,
                        const dlz_params &p, dlz_stats *st, const double2 *X_init) {
     if (N < 1 || N > kMaxBatch) return fail(DLZ_ERR_BADARG, "batch size");
-    if (!minres) {
-        // D-CG keeps the one-at-a-time form
-        for (int q = 0; q < N; ++q)
-            DLZ_TRY(dsolve_mixed(op, d, false, B + (size_t)q * 12 * op.g.V, X + (size_t)q * 12 * op.g.V, p, st[q],
-                                 X_init ? X_init + (size_t)q * 12 * op.g.V : nullptr));
-        return DLZ_OK;
-    }
     const long n64 = 12L * op.g.V;
     const long n32 = 6L * op.g.V;
     DevBuf bp, x, r, tmp, corr, dots, scal, f32;
@@ -280,15 +273,16 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
     HostScratch hs;
     DLZ_TRY(hs.ensure(1024));
     double2 *pbp = bp.as<double2>(), *px = x.as<double2>(), *pr = r.as<double2>(), *pt = tmp.as<double2>();
-    // b'_q = gamma5 b_q ; ||b_q||
+    // b'_q = gamma5 b_q (MinRes on Q) or b_q (CG on the normal equations, residual of D) ; ||b_q||
     {
-        const long half = 6L * op.g.V;
+        const long half = minres ? 6L * op.g.V : n64;
         DLZ_TRY(map(op, n64 * N, [=] __device__(long i) {
             double2 v = B[i];
             if ((i % n64) >= half) { v.x = -v.x; v.y = -v.y; }
             pbp[i] = v;
         }));
     }
+    const int which = minres ? DLZ_Q : DLZ_D;
     DLZ_TRY(reduce<kMaxBatch>(op, n64, [=] __device__(long i, double (&acc)[kMaxBatch]) {
 #pragma unroll
         for (int q = 0; q < kMaxBatch; ++q)
@@ -309,7 +303,7 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
     int iters = 0, outer = 0;
     long long mv_batch = 0;
     auto residuals = [&]() -> int {
-        DLZ_TRY(wilson64_batch(op, pt, px, DLZ_Q, N));
+        DLZ_TRY(wilson64_batch(op, pt, px, which, N));
         mv_batch += 1;
         DLZ_TRY(reduce<kMaxBatch>(op, n64, [=] __device__(long i, double (&acc)[kMaxBatch]) {
 #pragma unroll
@@ -365,14 +359,21 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
         // Galerkin projection of each open residual over the deflation set, in FP32
         // (Sec. 2: D-MinRes starts with it; repeated at every defect-correction restart):
         // e0 = V_k H^-1 V_k^dag r, u = r - Q e0; the inner MinRes then starts from e0.
+        // D-CG: the projection is that of the normal equations, e0 = V_k H^-1 V_k^dag D^dag r
+        // (H = V_k^dag D^dag D V_k), and the inner CG starts from s = r - D e0.
         const bool proj = d && d->k > 0;
         if (proj) {
             const int k = d->k;
             DLZ_TRY(deflation_v32(op, const_cast<dlz_defl_s *>(d)));
             const float4 *V32 = d->V32.as<float4>();
             double2 *pdots = pdot.as<double2>();
+            const float4 *rhs32 = w32[0];
+            if (!minres) {
+                DLZ_TRY(wilson32_batch(op, w32[2], w32[0], DLZ_DDAG, N));
+                rhs32 = w32[2];
+            }
             for (int q = 0; q < N; ++q)
-                DLZ_TRY(multidot<P32>(op, V32, n32, k, w32[0] + (size_t)q * n32, pdots + (size_t)q * k, 1.0));
+                DLZ_TRY(multidot<P32>(op, V32, n32, k, rhs32 + (size_t)q * n32, pdots + (size_t)q * k, 1.0));
             std::vector<double2> hc((size_t)N * k);
             DLZ_TRY(d2h_sync(op, hc.data(), pdots, hc.size() * sizeof(double2)));
             std::vector<std::complex<double>> z(k);
@@ -386,17 +387,25 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
                 DLZ_TRY(combine<P32>(op, w32[1] + (size_t)q * n32, n32, 1, V32, n32, k, pdots + (size_t)q * k, 1, false,
                                      false));
             float4 *qe = w32[2], *r32 = w32[0];
-            DLZ_TRY(wilson32_batch(op, qe, w32[1], DLZ_Q, N));
+            DLZ_TRY(wilson32_batch(op, qe, w32[1], which, N));
             DLZ_TRY(map(op, n32 * N, [=] __device__(long i) {
                 const float4 a = r32[i], b = qe[i];
                 r32[i] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
             }));
         }
         const int it0 = iters;
-        float4 *const bufs[6] = {w32[2], w32[3], w32[4], w32[5], w32[6], w32[7]};
-        DLZ_TRY(minres_fused_batch(op, N, w32[0], w32[1], bufs, reinterpret_cast<FusedState *>(ist),
-                                   fpart.as<double>(), d_tol, p, iters, hs, proj));
-        mv_batch += iters - it0;
+        if (minres) {
+            float4 *const bufs[6] = {w32[2], w32[3], w32[4], w32[5], w32[6], w32[7]};
+            DLZ_TRY(minres_fused_batch(op, N, w32[0], w32[1], bufs, reinterpret_cast<FusedState *>(ist),
+                                       fpart.as<double>(), d_tol, p, iters, hs, proj));
+            mv_batch += iters - it0;
+        } else {
+            if (!proj) DLZ_CUDA_TRY(cudaMemsetAsync(w32[1], 0, (size_t)N * n32 * sizeof(float4), op.stream));
+            float4 *const bufs[5] = {w32[2], w32[3], w32[4], w32[5], w32[6]};
+            DLZ_TRY(cgnr_fused_batch(op, N, w32[0], w32[1], bufs, reinterpret_cast<CgFusedState *>(ist),
+                                     fpart.as<double>(), d_tol, p, iters, hs));
+            mv_batch += 2L * (iters - it0);
+        }
         // x_q += ||r_q|| e_q
         {
             const int V = op.g.V;

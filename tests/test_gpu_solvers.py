@@ -296,3 +296,22 @@ np.save(sys.argv[1], np.concatenate([x.cpu().numpy()[None], X.cpu().numpy()]))
     ref = np.load(tmp_path / "ref.npy")
     plain = np.load(tmp_path / "plain.npy")
     assert np.array_equal(ref, plain)
+
+
+def test_mixed_dcg_many_rhs_in_chunks(m, case):
+    """18 right-hand sides through the batched FP32 D-CG (chunks of 16 and 2): every
+    solution's oracle FP64 residual is below 1e-10, and batching does not change the
+    per-RHS iteration count much versus solving one right-hand side alone."""
+    U, op, b = case
+    Aq, D, Dd, Ad = _ops(U, KAPPA)
+    _, defl, _ = m.landr(op, torch.from_numpy(b).cuda(), _params(m))
+    B = synth.gaussian_spinors(DIMS, list(range(30, 48)))
+    p32 = _params(m, precision=m.F32)
+    X, sts = m.dcg(op, defl, torch.from_numpy(B).cuda(), p32)
+    _, one = m.dcg(op, defl, torch.from_numpy(B[:1]).cuda(), p32)
+    Xn = X.cpu().numpy()
+    for i in range(len(B)):
+        bi = B[i].reshape(-1)
+        assert sts[i].converged == 1
+        assert np.linalg.norm(bi - D(Xn[i].reshape(-1))) <= 1.01e-10 * np.linalg.norm(bi)
+    assert sts[0].iterations <= one[0].iterations + 24
