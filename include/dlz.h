@@ -239,6 +239,25 @@ int dlz_defl_load(dlz_op_t op, const char *path, dlz_defl_t *out);
 int dlz_defl_destroy(dlz_defl_t d);
 
 /*
+ * D-MinRes on many lattices at once (Sec. 2's D-MinRes applied to each
+ * lattice; the batching across lattices of uneven size has no counterpart in
+ * the paper).  ops[l]: the operator of lattice l; defls[l]: its MinRes-DR
+ * deflation set or NULL (defls itself may be NULL); B[l], X[l]: nrhs[l] <= 16
+ * complex128 vectors [nrhs[l]][V_l][4][3] (host or device).  With
+ * p->precision == DLZ_F32 every (lattice, right-hand side) pair is a slot of one
+ * fused FP32 MinRes whose kernels cover all slots in one launch per stage
+ * (a block table maps each block to its slot; CUDA-graph groups of 6
+ * iterations), inside a lattice-by-lattice FP64 defect correction with the
+ * Galerkin projection at every restart; the kernels run on ops[0]'s stream and
+ * the per-lattice work on each operator's stream (synchronised between the two).
+ * DLZ_F64: the lattices are solved one after another by dlz_dminres.
+ * stats: one entry per slot, lattice-major.  Returns DLZ_ERR_NOT_CONVERGED if
+ * any slot did not reach p->tol within p->max_iter inner iterations.
+ */
+int dlz_batch_dminres(int nlat, dlz_op_t *ops, dlz_defl_t *defls, const void *const *B, void *const *X,
+                      const int *nrhs, const dlz_params *p, dlz_stats *stats);
+
+/*
  * Measurement entry point: packs `nrhs` spinors `in` (dtype DLZ_F64:
  * complex128, DLZ_F32: complex64, [nrhs][V][4][3], host or device) into the
  * internal layout and launches the stencil `which` (DLZ_D, DLZ_DDAG or DLZ_Q)

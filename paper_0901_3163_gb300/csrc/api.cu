@@ -475,6 +475,79 @@ int dlz_apply_noalloc(dlz_op_t h, int which, const void *in, void *out, int dtyp
     return DLZ_OK;
 }
 
+int dlz_batch_dminres(int nlat, dlz_op_t *ops, dlz_defl_t *defls, const void *const *B, void *const *X,
+                      const int *nrhs, const dlz_params *p, dlz_stats *stats) {
+    if (nlat < 1 || !ops || !B || !X || !nrhs) return fail(DLZ_ERR_BADARG, "batch_dminres arguments");
+    DLZ_TRY(check_params(p));
+    int total = 0;
+    for (int l = 0; l < nlat; ++l) {
+        if (!ops[l]) return fail(DLZ_ERR_BADARG, "null operator");
+        if (nrhs[l] < 0 || nrhs[l] > 16) return fail(DLZ_ERR_BADARG, "nrhs per lattice must be in [0, 16]");
+        if (nrhs[l] > 0 && (!B[l] || !X[l])) return fail(DLZ_ERR_BADARG, "null vector");
+        if (defls && defls[l]) {
+            if (defls[l]->op != &ops[l]->op) return fail(DLZ_ERR_BADARG, "deflation set of another operator");
+            if (defls[l]->which != DLZ_Q) return fail(DLZ_ERR_BADARG, "D-MinRes needs a MinRes-DR (Q) deflation set");
+        }
+        total += nrhs[l];
+    }
+    if (p->precision == DLZ_F64) {
+        // the plain form: one lattice after another
+        int worst = DLZ_OK, q = 0;
+        for (int l = 0; l < nlat; ++l) {
+            if (nrhs[l] == 0) continue;
+            const int rc = dlz_dminres(ops[l], defls ? defls[l] : nullptr, B[l], X[l], nrhs[l], p,
+                                       stats ? stats + q : nullptr);
+            if (rc != DLZ_OK && rc != DLZ_ERR_NOT_CONVERGED) return rc;
+            if (rc != DLZ_OK) worst = rc;
+            q += nrhs[l];
+        }
+        return worst;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<Op *> opv(nlat);
+    std::vector<const dlz_defl_s *> dv(nlat);
+    std::vector<Staged> sb(nlat), sx(nlat);
+    std::vector<DevBuf> bi(nlat), xi(nlat);
+    std::vector<const double2 *> bptr(nlat);
+    std::vector<double2 *> xptr(nlat);
+    for (int l = 0; l < nlat; ++l) {
+        Op &op = ops[l]->op;
+        op.prof.begin(false, true);
+        opv[l] = &op;
+        dv[l] = defls ? defls[l] : nullptr;
+        const long n = 12L * op.g.V;
+        const size_t bytes = (size_t)n * std::max(nrhs[l], 1) * sizeof(double2);
+        DLZ_TRY(bi[l].alloc(bytes));
+        DLZ_TRY(xi[l].alloc(bytes));
+        if (nrhs[l] > 0) {
+            DLZ_TRY(sb[l].in(op, B[l], (size_t)n * nrhs[l] * sizeof(double2)));
+            DLZ_TRY(sx[l].out(op, X[l], (size_t)n * nrhs[l] * sizeof(double2)));
+            for (int r = 0; r < nrhs[l]; ++r)
+                DLZ_TRY(pack64(op, bi[l].as<double2>() + (size_t)r * n, (const double2 *)sb[l].dev + (size_t)r * n));
+        }
+        DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+        bptr[l] = bi[l].as<double2>();
+        xptr[l] = xi[l].as<double2>();
+    }
+    std::vector<dlz_stats> st(std::max(total, 1));
+    const int rc = dminres_multi(nlat, opv.data(), dv.data(), bptr.data(), xptr.data(), nrhs, *p, st.data());
+    if (rc != DLZ_OK && rc != DLZ_ERR_NOT_CONVERGED) return rc;
+    for (int l = 0; l < nlat; ++l) {
+        Op &op = ops[l]->op;
+        const long n = 12L * op.g.V;
+        for (int r = 0; r < nrhs[l]; ++r)
+            DLZ_TRY(unpack64(op, (double2 *)sx[l].dev + (size_t)r * n, xi[l].as<double2>() + (size_t)r * n));
+        if (nrhs[l] > 0) DLZ_TRY(sx[l].flush(op));
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats)
+        for (int q = 0; q < total; ++q) {
+            stats[q] = st[q];
+            stats[q].seconds = secs / total;
+        }
+    return rc;
+}
+
 int dlz_stencil_bench(dlz_op_t h, int dtype, int which, int nrhs, int iters, const void *in,
                       double *ms_per_launch) {
     DLZ_TRY(check_op(h));

@@ -27,26 +27,17 @@
 #include "krylov_util.cuh"
 #include "reduce.cuh"
 #include "solvers.h"
+#include "minres_state.cuh"
 #include "wilson_site.cuh"
 
 namespace dlz {
 
-struct FusedState {          // one per right-hand side (FP64 scalars)
-    double beta, alpha, beta_next, inv_beta;
-    double c, s, c_old, s_old, phibar;
-    double eps, delta, gamma, tau;
-    double r0;               // ||r|| at the start of the inner solve
-    // FP32 copies read by the element updates (no FP64 op or conversion per element):
-    // f[0] 1/beta_j, f[1] beta_j, f[2] delta, f[3] eps, f[4] 1/gamma, f[5] tau, f[6] alpha,
-    // f[7] 1/beta_{j-1}
-    float f[8];
-};
+
 
 namespace {
 
 constexpr int kThreads = 128;
 
-__device__ inline float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 
 __global__ void __launch_bounds__(kThreads)
 k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Up, float4 *__restrict__ W,
@@ -59,28 +50,8 @@ k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Up, float4
     const size_t base = (size_t)q * nel;
     float facc = 0.f;
     if (s < g.V) {
-        const float ib = st[q].f[0], bt = st[q].f[1], ibp = st[q].f[7];
-        const float de = st[q].f[2], ep = st[q].f[3], ig = st[q].f[4], ta = st[q].f[5];
-        float2 o[12];
-        wilson_site<float, false, true>(s, g, kappa, Ub + base, links, o);   // Q u_j
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            const size_t i = base + (size_t)c * g.V + s;
-            const float4 u = Ub[i], up = Up[i], d2 = D2[i], d3 = D3[i];
-            const float4 vj = f4(u.x * ib, u.y * ib, u.z * ib, u.w * ib);
-            const float4 vp = f4(up.x * ibp, up.y * ibp, up.z * ibp, up.w * ibp);
-            const float4 w = f4(o[2 * c].x * ib - bt * vp.x, o[2 * c].y * ib - bt * vp.y,
-                                o[2 * c + 1].x * ib - bt * vp.z, o[2 * c + 1].y * ib - bt * vp.w);
-            W[i] = w;
-            facc += (vj.x * w.x + vj.y * w.y) + (vj.z * w.z + vj.w * w.w);
-            const float4 dn = f4((vp.x - de * d2.x - ep * d3.x) * ig, (vp.y - de * d2.y - ep * d3.y) * ig,
-                                 (vp.z - de * d2.z - ep * d3.z) * ig, (vp.w - de * d2.w - ep * d3.w) * ig);
-            D3[i] = dn;
-            float4 ev = E[i];
-            ev.x = fmaf(ta, dn.x, ev.x); ev.y = fmaf(ta, dn.y, ev.y);
-            ev.z = fmaf(ta, dn.z, ev.z); ev.w = fmaf(ta, dn.w, ev.w);
-            E[i] = ev;
-        }
+        facc = minres_k1_site(s, g, kappa, Ub + base, Up + base, W + base, D2 + base, D3 + base, E + base,
+                              links, st[q]);
     }
     // block partial of alpha_q (FP64 across threads), stored contiguously per right-hand side
     double acc = (double)facc;
@@ -112,9 +83,7 @@ k_minres_alpha(const double *__restrict__ partials, int nbq, FusedState *__restr
     if (threadIdx.x == 0) {
         double a = 0.0;
         for (int w = 0; w < (int)(blockDim.x / 32); ++w) a += sm[w];
-        st[q].beta = st[q].beta_next;
-        st[q].alpha = a;
-        st[q].f[6] = (float)a;
+        fused_alpha(st[q], a);
     }
 }
 
@@ -130,20 +99,7 @@ k_minres_k2a(float4 *__restrict__ W, const float4 *__restrict__ Vc, Geom g, int 
     const size_t base = (size_t)q * 6 * g.V;
     float facc = 0.f;
     if (s < g.V) {
-        const float al = st[q].f[6] * st[q].f[0];
-        float4 w[6], v[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            w[c] = W[base + (size_t)c * g.V + s];
-            v[c] = Vc[base + (size_t)c * g.V + s];
-        }
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            const float4 t = f4(fmaf(-al, v[c].x, w[c].x), fmaf(-al, v[c].y, w[c].y),
-                                fmaf(-al, v[c].z, w[c].z), fmaf(-al, v[c].w, w[c].w));
-            W[base + (size_t)c * g.V + s] = t;
-            facc += (t.x * t.x + t.y * t.y) + (t.z * t.z + t.w * t.w);
-        }
+        facc = minres_k2a_site(s, g.V, W + base, Vc + base, st[q]);
     }
     double acc = (double)facc;
     __shared__ double sm[kThreads / 32];
@@ -158,8 +114,6 @@ k_minres_k2a(float4 *__restrict__ W, const float4 *__restrict__ Vc, Geom g, int 
         partials[(size_t)q * (gridDim.x / N) + blockIdx.x / N] = t;
     }
 }
-
-__device__ inline void set_floats(FusedState &s);
 
 // K2b: beta_{j+1} = sqrt(sum of K2a's partials) and the Givens rotation of step j,
 // one block per right-hand side
@@ -177,35 +131,11 @@ k_minres_k2b(const double *__restrict__ partials, int nbq, FusedState *__restric
         double r2 = 0.0;
         for (int w = 0; w < (int)(blockDim.x / 32); ++w) r2 += sm[w];
         FusedState s = st[q];
-        const double bn = sqrt(r2);
-        const double eps = s.s_old * s.beta;
-        const double deltabar = s.c_old * s.beta;
-        const double delta = s.c * deltabar + s.s * s.alpha;
-        const double gammabar = -s.s * deltabar + s.c * s.alpha;
-        double gamma = hypot(gammabar, bn);
-        double cn = 1.0, sn = 0.0;
-        if (gamma > 0.0) { cn = gammabar / gamma; sn = bn / gamma; }
-        else gamma = 1.0;            // zero right-hand side: hold a no-op
-        s.tau = cn * s.phibar;
-        s.phibar = -sn * s.phibar;
-        s.eps = eps; s.delta = delta; s.gamma = gamma;
-        s.c_old = s.c; s.s_old = s.s; s.c = cn; s.s = sn;
-        s.beta_next = bn;
-        s.inv_beta = bn > 0 ? 1.0 / bn : 0.0;
-        s.f[7] = s.f[0];             // 1/beta_j, to scale u_j into v_j in the next step
-        set_floats(s);
+        fused_givens(s, r2);
         st[q] = s;
     }
 }
 
-__device__ inline void set_floats(FusedState &s) {
-    s.f[0] = (float)s.inv_beta;
-    s.f[1] = (float)s.beta_next;
-    s.f[2] = (float)s.delta;
-    s.f[3] = (float)s.eps;
-    s.f[4] = (float)(1.0 / s.gamma);
-    s.f[5] = (float)s.tau;
-}
 
 }  // namespace
 
@@ -220,13 +150,7 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
             if (q < N) { const float4 v = r[(size_t)q * n + i]; acc[q] += (v.x * v.x + v.y * v.y) + (v.z * v.z + v.w * v.w); }
     }, [=] __device__(const double *res) {
         for (int q = 0; q < N; ++q) {
-            const double b = sqrt(res[q]);
-            FusedState s0 = {};
-            s0.beta_next = b; s0.inv_beta = b > 0 ? 1.0 / b : 0.0;
-            // tolerances are relative to the normalised outer residual (norm 1)
-            s0.c = 1.0; s0.c_old = 1.0; s0.phibar = b; s0.gamma = 1.0; s0.r0 = 1.0;
-            set_floats(s0);
-            ms[q] = s0;
+            fused_init(ms[q], sqrt(res[q]));
         }
     }));
     // u_j, u_{j-1} (unnormalised Lanczos vectors), w, d_{j-2}, d_{j-3}
@@ -317,16 +241,7 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
         float4 *ee = e;
         DLZ_TRY(map(op, n * N, [=] __device__(long i) {
             const int q = (int)(i / n);
-            const float de = ms[q].f[2], ep = ms[q].f[3], ig = ms[q].f[4], ta = ms[q].f[5];
-            const float ibj = ms[q].f[7];
-            const float4 uj = vj[i], a = d2[i], b = d3[i];
-            const float4 vp = f4(uj.x * ibj, uj.y * ibj, uj.z * ibj, uj.w * ibj);
-            const float4 dn = f4((vp.x - de * a.x - ep * b.x) * ig, (vp.y - de * a.y - ep * b.y) * ig,
-                                 (vp.z - de * a.z - ep * b.z) * ig, (vp.w - de * a.w - ep * b.w) * ig);
-            float4 ev = ee[i];
-            ev.x = fmaf(ta, dn.x, ev.x); ev.y = fmaf(ta, dn.y, ev.y);
-            ev.z = fmaf(ta, dn.z, ev.z); ev.w = fmaf(ta, dn.w, ev.w);
-            ee[i] = ev;
+            minres_last_direction(vj[i], d2[i], d3[i], ee[i], ms[q]);
         }));
     }
     return DLZ_OK;

@@ -1,0 +1,449 @@
+// D-MinRes on many lattices of uneven size at once (arXiv:0901.3163, Sec. 2,
+// applied lattice by lattice): every (lattice, right-hand side) pair is a slot
+// with its own geometry, links, kappa and deflation set, and the fused FP32
+// MinRes kernels of minres_fused.cu run over all slots in one launch per stage.
+// Each launch walks a block table (block -> slot, first site), built on the host
+// with the slots' blocks contiguous, so the per-slot sums of block partials are
+// contiguous ranges read in a fixed order (deterministic).  The FP64 defect
+// correction around it (true residuals, Galerkin projection over each lattice's
+// deflation set, x updates) runs lattice by lattice with that lattice's operator.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "dlz_internal.cuh"
+#include "krylov_util.cuh"
+#include "minres_state.cuh"
+#include "prec.cuh"
+#include "reduce.cuh"
+#include "small_dense.h"
+#include "solvers.h"
+#include "wilson_site.cuh"
+
+namespace dlz {
+
+struct SlotDesc {
+    Geom g;
+    float kappa;
+    int blk0, nb;                 // first block and number of blocks in the table
+    const float4 *links;          // FP32 two-row links of the slot's lattice
+    size_t off;                   // float4 offset of the slot's vectors in the arenas
+};
+
+namespace {
+
+constexpr int kMT = 128;
+
+struct Scales16 {            // per-right-hand-side scale factors captured by value
+    double v[16];
+};
+
+__device__ inline void block_partial(float facc, double *__restrict__ out) {
+    double acc = (double)facc;
+    __shared__ double sm[kMT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kMT / 32; ++w) t += sm[w];
+        *out = t;
+    }
+}
+
+// sum of partials[blk0 .. blk0 + nb) in a fixed order (valid in thread 0)
+__device__ inline double slot_sum(const double *__restrict__ partials, int blk0, int nb) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += partials[blk0 + b];
+    __shared__ double sm[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
+    __syncthreads();
+    double a = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) a += sm[w];
+    return a;
+}
+
+__global__ void __launch_bounds__(kMT)
+k_mm_norm(const float4 *__restrict__ R, const SlotDesc *__restrict__ sd, const int2 *__restrict__ table,
+          double *__restrict__ partials) {
+    const int2 t = table[blockIdx.x];
+    const SlotDesc d = sd[t.x];
+    const int s = t.y + threadIdx.x;
+    float facc = 0.f;
+    if (s < d.g.V) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float4 v = R[d.off + (size_t)c * d.g.V + s];
+            facc += (v.x * v.x + v.y * v.y) + (v.z * v.z + v.w * v.w);
+        }
+    }
+    block_partial(facc, partials + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256)
+k_mm_init(const double *__restrict__ partials, const SlotDesc *__restrict__ sd, FusedState *__restrict__ st) {
+    const SlotDesc d = sd[blockIdx.x];
+    const double r2 = slot_sum(partials, d.blk0, d.nb);
+    if (threadIdx.x == 0) fused_init(st[blockIdx.x], sqrt(r2));
+}
+
+__global__ void __launch_bounds__(kMT)
+k_mm_k1(const float4 *__restrict__ U, const float4 *__restrict__ Up, float4 *__restrict__ W,
+        const float4 *__restrict__ D2, float4 *__restrict__ D3, float4 *__restrict__ E,
+        const SlotDesc *__restrict__ sd, const int2 *__restrict__ table, const FusedState *__restrict__ st,
+        double *__restrict__ partials) {
+    const int2 t = table[blockIdx.x];
+    const SlotDesc d = sd[t.x];
+    const int s = t.y + threadIdx.x;
+    float facc = 0.f;
+    if (s < d.g.V)
+        facc = minres_k1_site(s, d.g, d.kappa, U + d.off, Up + d.off, W + d.off, D2 + d.off, D3 + d.off,
+                              E + d.off, d.links, st[t.x]);
+    block_partial(facc, partials + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256)
+k_mm_alpha(const double *__restrict__ partials, const SlotDesc *__restrict__ sd, FusedState *__restrict__ st) {
+    const SlotDesc d = sd[blockIdx.x];
+    const double a = slot_sum(partials, d.blk0, d.nb);
+    if (threadIdx.x == 0) fused_alpha(st[blockIdx.x], a);
+}
+
+__global__ void __launch_bounds__(kMT)
+k_mm_k2a(float4 *__restrict__ W, const float4 *__restrict__ U, const SlotDesc *__restrict__ sd,
+         const int2 *__restrict__ table, const FusedState *__restrict__ st, double *__restrict__ partials) {
+    const int2 t = table[blockIdx.x];
+    const SlotDesc d = sd[t.x];
+    const int s = t.y + threadIdx.x;
+    float facc = 0.f;
+    if (s < d.g.V) facc = minres_k2a_site(s, d.g.V, W + d.off, U + d.off, st[t.x]);
+    block_partial(facc, partials + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256)
+k_mm_k2b(const double *__restrict__ partials, const SlotDesc *__restrict__ sd, FusedState *__restrict__ st) {
+    const SlotDesc d = sd[blockIdx.x];
+    const double r2 = slot_sum(partials, d.blk0, d.nb);
+    if (threadIdx.x == 0) {
+        FusedState s = st[blockIdx.x];
+        fused_givens(s, r2);
+        st[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kMT)
+k_mm_last(const float4 *__restrict__ Uj, const float4 *__restrict__ D2, const float4 *__restrict__ D3,
+          float4 *__restrict__ E, const SlotDesc *__restrict__ sd, const int2 *__restrict__ table,
+          const FusedState *__restrict__ st) {
+    const int2 t = table[blockIdx.x];
+    const SlotDesc d = sd[t.x];
+    const int s = t.y + threadIdx.x;
+    if (s >= d.g.V) return;
+    const FusedState q = st[t.x];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const size_t i = d.off + (size_t)c * d.g.V + s;
+        float4 ev = E[i];
+        minres_last_direction(Uj[i], D2[i], D3[i], ev, q);
+        E[i] = ev;
+    }
+}
+
+}  // namespace
+
+// The fused FP32 MinRes over all slots (r: normalised residuals in the arena; e:
+// corrections, holding the start if e_init).  bufs: 5 arena-sized work vectors.
+int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const int2 *table, int nblocks, size_t arena,
+                       const float4 *r, float4 *e, float4 *const bufs[5], FusedState *ms, double *partials,
+                       const double *d_tol, const dlz_params &p, int &iters, HostScratch &hs, bool e_init) {
+    double *partials2 = partials + nblocks;
+    k_mm_norm<<<nblocks, kMT, 0, op.stream>>>(r, sd, table, partials);
+    k_mm_init<<<NS, 256, 0, op.stream>>>(partials, sd, ms);
+    op.prof.launches += 2;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    float4 *U0 = bufs[0], *Up0 = bufs[1], *W0 = bufs[2], *D20 = bufs[3], *D30 = bufs[4];
+    DLZ_CUDA_TRY(cudaMemcpyAsync(U0, r, arena * sizeof(float4), cudaMemcpyDeviceToDevice, op.stream));
+    for (float4 *z : {Up0, D20, D30}) DLZ_CUDA_TRY(cudaMemsetAsync(z, 0, arena * sizeof(float4), op.stream));
+    if (!e_init) DLZ_CUDA_TRY(cudaMemsetAsync(e, 0, arena * sizeof(float4), op.stream));
+    auto iteration = [&](float4 *U, float4 *Up, float4 *W, float4 *D2, float4 *D3) -> int {
+        k_mm_k1<<<nblocks, kMT, 0, op.stream>>>(U, Up, W, D2, D3, e, sd, table, ms, partials);
+        k_mm_alpha<<<NS, 256, 0, op.stream>>>(partials, sd, ms);
+        k_mm_k2a<<<nblocks, kMT, 0, op.stream>>>(W, U, sd, table, ms, partials2);
+        k_mm_k2b<<<NS, 256, 0, op.stream>>>(partials2, sd, ms);
+        op.prof.launches += 4;
+        DLZ_CUDA_TRY(cudaGetLastError());
+        return DLZ_OK;
+    };
+    GraphExec ge;
+    auto six = [&]() -> int {
+        float4 *U = U0, *Up = Up0, *W = W0, *D2 = D20, *D3 = D30;
+        for (int sub = 0; sub < 6; ++sub) {
+            DLZ_TRY(iteration(U, Up, W, D2, D3));
+            float4 *tUp = Up;
+            Up = U; U = W; W = tUp;
+            std::swap(D2, D3);
+        }
+        return DLZ_OK;
+    };
+    const int check = std::max(6, (p.check_every / 6) * 6);
+    std::vector<FusedState> h(NS);
+    std::vector<double> tol(NS);
+    DLZ_TRY(d2h_sync(op, tol.data(), d_tol, NS * sizeof(double)));
+    int it = 0;
+    while (iters < p.max_iter) {
+        DLZ_TRY(run_graph(op, ge, six));
+        iters += 6;
+        it += 6;
+        if (it % check == 0 || iters >= p.max_iter) {
+            DLZ_TRY(d2h_sync(op, h.data(), ms, NS * sizeof(FusedState)));
+            bool done = true;
+            for (int q = 0; q < NS; ++q) {
+                if (!std::isfinite(h[q].phibar)) return fail(DLZ_ERR_NONFINITE, "MinRes residual not finite");
+                if (!(std::fabs(h[q].phibar) <= tol[q] * h[q].r0 || h[q].beta_next == 0.0)) done = false;
+            }
+            if (done) break;
+        }
+    }
+    k_mm_last<<<nblocks, kMT, 0, op.stream>>>(Up0, D20, D30, e, sd, table, ms);
+    op.prof.launches += 1;
+    DLZ_CUDA_TRY(cudaGetLastError());
+    return DLZ_OK;
+}
+
+// FP32 D-MinRes with FP64 defect correction on every lattice's right-hand sides
+// at once.  B[l], X[l]: nrhs[l] internal FP64 vectors of lattice l.
+int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, const double2 *const *B,
+                  double2 *const *X, const int *nrhs, const dlz_params &p, dlz_stats *st) {
+    // slots and the block table
+    std::vector<SlotDesc> hsd;
+    std::vector<int2> table;
+    std::vector<int> slot_lat, slot_rhs, lat_slot0(nlat);
+    size_t arena = 0;
+    for (int l = 0; l < nlat; ++l) {
+        lat_slot0[l] = (int)hsd.size();
+        const Op &o = *ops[l];
+        for (int r = 0; r < nrhs[l]; ++r) {
+            SlotDesc d;
+            d.g = o.g;
+            d.kappa = (float)o.kappa;
+            d.links = o.gauge32.as<float4>();
+            d.off = arena;
+            d.blk0 = (int)table.size();
+            d.nb = (o.g.V + kMT - 1) / kMT;
+            for (int b = 0; b < d.nb; ++b) table.push_back(make_int2((int)hsd.size(), b * kMT));
+            arena += 6L * o.g.V;
+            hsd.push_back(d);
+            slot_lat.push_back(l);
+            slot_rhs.push_back(r);
+        }
+    }
+    const int NS = (int)hsd.size();
+    const int nblocks = (int)table.size();
+    if (NS == 0) return DLZ_OK;
+    Op &op = *ops[0];
+    DevBuf dsd, dtab, f32, part, scal;
+    DLZ_TRY(dsd.alloc(NS * sizeof(SlotDesc)));
+    DLZ_TRY(dtab.alloc(nblocks * sizeof(int2)));
+    DLZ_TRY(f32.alloc(7 * arena * sizeof(float4)));
+    DLZ_TRY(part.alloc(2 * (size_t)nblocks * sizeof(double)));
+    DLZ_TRY(scal.alloc((size_t)NS * (sizeof(FusedState) + 2 * sizeof(double))));
+    DLZ_TRY(h2d(op, dsd.p, hsd.data(), NS * sizeof(SlotDesc)));
+    DLZ_TRY(h2d(op, dtab.p, table.data(), nblocks * sizeof(int2)));
+    float4 *r32 = f32.as<float4>(), *e32 = r32 + arena;
+    float4 *const bufs[5] = {r32 + 2 * arena, r32 + 3 * arena, r32 + 4 * arena, r32 + 5 * arena, r32 + 6 * arena};
+    FusedState *ms = reinterpret_cast<FusedState *>(scal.p);
+    double *d_tol = reinterpret_cast<double *>(ms + NS);
+    HostScratch hs;
+    DLZ_TRY(hs.ensure(64));
+    // per-lattice FP64 work: b' = gamma5 b, x, r, Q x
+    struct Lat {
+        DevBuf bp, x, r, t, dots, nrm;
+        std::vector<double> bn, rn;
+    };
+    std::vector<Lat> L(nlat);
+    for (int l = 0; l < nlat; ++l) {
+        Op &o = *ops[l];
+        const long n64 = 12L * o.g.V;
+        const int N = nrhs[l];
+        if (N > 16) return fail(DLZ_ERR_BADARG, "at most 16 right-hand sides per lattice");
+        Lat &a = L[l];
+        DLZ_TRY(a.bp.alloc((size_t)N * n64 * sizeof(double2)));
+        DLZ_TRY(a.x.alloc((size_t)N * n64 * sizeof(double2)));
+        DLZ_TRY(a.r.alloc((size_t)N * n64 * sizeof(double2)));
+        DLZ_TRY(a.t.alloc((size_t)N * n64 * sizeof(double2)));
+        DLZ_TRY(a.nrm.alloc(16 * sizeof(double)));
+        if (defls[l] && defls[l]->k > 0) {
+            DLZ_TRY(a.dots.alloc((size_t)N * defls[l]->k * sizeof(double2)));
+            DLZ_TRY(reserve_multidot(o, defls[l]->k));
+            DLZ_TRY(deflation_v32(o, const_cast<dlz_defl_s *>(defls[l])));
+        }
+        const long half = 6L * o.g.V;
+        double2 *pbp = a.bp.as<double2>();
+        const double2 *pb = B[l];
+        DLZ_TRY(map(o, n64 * N, [=] __device__(long i) {
+            double2 v = pb[i];
+            if ((i % n64) >= half) { v.x = -v.x; v.y = -v.y; }
+            pbp[i] = v;
+        }));
+        double *dn = a.nrm.as<double>();
+        DLZ_TRY(reduce<16>(o, n64, [=] __device__(long i, double (&acc)[16]) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q < N) { const double2 v = pbp[(size_t)q * n64 + i]; acc[q] += v.x * v.x + v.y * v.y; }
+        }, [=] __device__(const double *res) { for (int q = 0; q < N; ++q) dn[q] = sqrt(res[q]); }));
+        a.bn.resize(N);
+        a.rn.resize(N);
+        DLZ_TRY(d2h_sync(o, a.bn.data(), dn, N * sizeof(double)));
+        DLZ_CUDA_TRY(cudaMemsetAsync(a.x.p, 0, (size_t)N * n64 * sizeof(double2), o.stream));
+    }
+    for (int q = 0; q < NS; ++q) std::memset(&st[q], 0, sizeof(dlz_stats));
+    std::vector<char> done(NS, 0);
+    std::vector<double> inv(NS), tl(NS);
+    int iters = 0, outer = 0;
+    while (true) {
+        // FP64 residuals lattice by lattice
+        bool all = true;
+        for (int l = 0; l < nlat; ++l) {
+            Op &o = *ops[l];
+            Lat &a = L[l];
+            const int N = nrhs[l];
+            const long n64 = 12L * o.g.V;
+            DLZ_TRY(wilson64_batch(o, a.t.as<double2>(), a.x.as<double2>(), DLZ_Q, N));
+            const double2 *pbp = a.bp.as<double2>(), *pt = a.t.as<double2>();
+            double2 *pr = a.r.as<double2>();
+            double *dn = a.nrm.as<double>();
+            DLZ_TRY(reduce<16>(o, n64, [=] __device__(long i, double (&acc)[16]) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    if (q < N) {
+                        const size_t k = (size_t)q * n64 + i;
+                        const double2 u = pbp[k], v = pt[k];
+                        const double2 t = make_double2(u.x - v.x, u.y - v.y);
+                        pr[k] = t;
+                        acc[q] += t.x * t.x + t.y * t.y;
+                    }
+                }
+            }, [=] __device__(const double *res) { for (int q = 0; q < N; ++q) dn[q] = sqrt(res[q]); }));
+            DLZ_TRY(d2h_sync(o, a.rn.data(), dn, N * sizeof(double)));
+            for (int r = 0; r < N; ++r) {
+                const int q = lat_slot0[l] + r;
+                if (!std::isfinite(a.rn[r])) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
+                if (!done[q] && (a.bn[r] == 0.0 || a.rn[r] <= p.tol * a.bn[r])) {
+                    done[q] = 1;
+                    st[q].iterations = iters;
+                    st[q].cycles = outer;
+                }
+                all = all && done[q];
+                const bool open = !done[q];
+                inv[q] = open ? 1.0 / a.rn[r] : 0.0;
+                tl[q] = open ? std::max(0.5 * p.tol * a.bn[r] / a.rn[r], p.reliable_delta) : 1.0;
+            }
+        }
+        if (all || iters >= p.max_iter) break;
+        // normalised FP32 residuals into the arena; Galerkin projection per lattice
+        for (int l = 0; l < nlat; ++l) {
+            Op &o = *ops[l];
+            Lat &a = L[l];
+            const int N = nrhs[l];
+            const int V = o.g.V;
+            const long n64 = 12L * V, n32 = 6L * V;
+            float4 *rl = r32 + hsd[lat_slot0[l]].off, *el = e32 + hsd[lat_slot0[l]].off;
+            const double2 *pr = a.r.as<double2>();
+            Scales16 scv;
+            for (int r = 0; r < N; ++r) scv.v[r] = inv[lat_slot0[l] + r];
+            DLZ_TRY(map(o, n32 * N, [=] __device__(long i) {
+                const int q = (int)(i / n32);
+                const long j = i % n32;
+                const int c = (int)(j / V), s = (int)(j % V);
+                const double f = scv.v[q];
+                const double2 *src = pr + (size_t)q * n64;
+                const double2 u = src[(size_t)(2 * c) * V + s], w = src[(size_t)(2 * c + 1) * V + s];
+                rl[i] = make_float4((float)(f * u.x), (float)(f * u.y), (float)(f * w.x), (float)(f * w.y));
+            }));
+            const dlz_defl_s *d = defls[l];
+            if (d && d->k > 0) {
+                const int k = d->k;
+                const float4 *V32 = d->V32.as<float4>();
+                double2 *pd = a.dots.as<double2>();
+                for (int r = 0; r < N; ++r)
+                    DLZ_TRY(multidot<P32>(o, V32, n32, k, rl + (size_t)r * n32, pd + (size_t)r * k, 1.0));
+                std::vector<double2> hc((size_t)N * k);
+                DLZ_TRY(d2h_sync(o, hc.data(), pd, hc.size() * sizeof(double2)));
+                std::vector<std::complex<double>> z(k);
+                for (int r = 0; r < N; ++r) {
+                    for (int i = 0; i < k; ++i) z[i] = std::complex<double>(hc[(size_t)r * k + i].x, hc[(size_t)r * k + i].y);
+                    lu_solve(k, d->Hlu.data(), d->piv.data(), z.data());
+                    for (int i = 0; i < k; ++i) hc[(size_t)r * k + i] = make_double2(z[i].real(), z[i].imag());
+                }
+                DLZ_TRY(h2d(o, pd, hc.data(), hc.size() * sizeof(double2)));
+                for (int r = 0; r < N; ++r)
+                    DLZ_TRY(combine<P32>(o, el + (size_t)r * n32, n32, 1, V32, n32, k, pd + (size_t)r * k, 1, false, false));
+                float4 *qe = bufs[0] + hsd[lat_slot0[l]].off;      // scratch: Q e0
+                DLZ_TRY(wilson32_batch(o, qe, el, DLZ_Q, N));
+                DLZ_TRY(map(o, n32 * N, [=] __device__(long i) {
+                    const float4 u = rl[i], w = qe[i];
+                    rl[i] = make_float4(u.x - w.x, u.y - w.y, u.z - w.z, u.w - w.w);
+                }));
+            } else {
+                DLZ_CUDA_TRY(cudaMemsetAsync(el, 0, (size_t)N * n32 * sizeof(float4), o.stream));
+            }
+            DLZ_CUDA_TRY(cudaStreamSynchronize(o.stream));
+        }
+        DLZ_TRY(h2d(op, d_tol, tl.data(), NS * sizeof(double)));
+        DLZ_TRY(minres_multi_batch(op, NS, dsd.as<SlotDesc>(), dtab.as<int2>(), nblocks, arena, r32, e32, bufs, ms,
+                                   part.as<double>(), d_tol, p, iters, hs, true));
+        DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+        // x += ||r|| e, lattice by lattice
+        for (int l = 0; l < nlat; ++l) {
+            Op &o = *ops[l];
+            Lat &a = L[l];
+            const int N = nrhs[l];
+            const int V = o.g.V;
+            const long n64 = 12L * V, n32 = 6L * V;
+            const float4 *el = e32 + hsd[lat_slot0[l]].off;
+            Scales16 scv;
+            for (int r = 0; r < N; ++r) {
+                const double iv = inv[lat_slot0[l] + r];
+                scv.v[r] = iv > 0.0 ? 1.0 / iv : 0.0;
+            }
+            double2 *px = a.x.as<double2>();
+            DLZ_TRY(map(o, n32 * N, [=] __device__(long i) {
+                const int q = (int)(i / n32);
+                const double f = scv.v[q];
+                const long j = i % n32;
+                const int c = (int)(j / V), s = (int)(j % V);
+                const float4 qv = el[i];
+                double2 *xq = px + (size_t)q * n64;
+                double2 &u = xq[(size_t)(2 * c) * V + s];
+                double2 &w = xq[(size_t)(2 * c + 1) * V + s];
+                u.x += f * qv.x; u.y += f * qv.y; w.x += f * qv.z; w.y += f * qv.w;
+            }));
+        }
+        ++outer;
+    }
+    int rc = DLZ_OK;
+    for (int l = 0; l < nlat; ++l) {
+        Op &o = *ops[l];
+        const long n64 = 12L * o.g.V;
+        DLZ_CUDA_TRY(cudaMemcpyAsync(X[l], L[l].x.p, (size_t)nrhs[l] * n64 * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                     o.stream));
+        DLZ_CUDA_TRY(cudaStreamSynchronize(o.stream));
+        for (int r = 0; r < nrhs[l]; ++r) {
+            const int q = lat_slot0[l] + r;
+            st[q].true_residual = L[l].bn[r] > 0 ? L[l].rn[r] / L[l].bn[r] : 0.0;
+            st[q].converged = done[q] ? 1 : 0;
+            if (!done[q]) { st[q].iterations = iters; st[q].cycles = outer; rc = DLZ_ERR_NOT_CONVERGED; }
+            st[q].mvps = iters + outer;
+        }
+    }
+    return rc;
+}
+
+}  // namespace dlz

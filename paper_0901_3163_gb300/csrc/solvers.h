@@ -66,6 +66,11 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
 struct CgFusedState;
 int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5], CgFusedState *ms,
                      double *partials, const double *d_tol, const dlz_params &p, int &iters, HostScratch &hs);
+// FP32 D-MinRes with FP64 defect correction on many lattices at once
+// (minres_multi.cu); B[l], X[l]: nrhs[l] <= 16 internal FP64 vectors of lattice l,
+// st: one entry per (lattice, right-hand side) in order.
+int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, const double2 *const *B,
+                  double2 *const *X, const int *nrhs, const dlz_params &p, dlz_stats *st);
 // FP32 copy of the deflation basis (made on first use).
 int deflation_v32(Op &op, dlz_defl_s *d);
 int deflation_finish(Op &op, dlz_defl_s *d);

@@ -89,6 +89,9 @@ _SIGS = {
     "dlz_defl_load": ([_vp, ctypes.c_char_p, ctypes.POINTER(_vp)], _ip),
     "dlz_defl_destroy": ([_vp], _ip),
     "dlz_stencil_bench": ([_vp, _ip, _ip, _ip, _ip, _vp, _dp], _ip),
+    "dlz_batch_dminres": ([_ip, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                           ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Params),
+                           ctypes.POINTER(Stats)], _ip),
     "dlz_net_create": ([_vp, _ip, ctypes.POINTER(ctypes.c_int), _vp, ctypes.POINTER(_vp)], _ip),
     "dlz_net_destroy": ([_vp], _ip),
     "dlz_net_weight_count": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _ip),
@@ -265,6 +268,28 @@ def dcg(op, defl, B, params=None, X=None):
 def dminres(op, defl, B, params=None, X=None):
     """D-MinRes (Galerkin projection over defl, then MinRes on gamma5 D); returns (X, [Stats])."""
     return _dsolve(lib.dlz_dminres, op, defl, B, params, X)
+
+
+def batch_dminres(ops, defls, Bs, params=None, Xs=None):
+    """dlz_batch_dminres: D-MinRes on several lattices at once.  ops, defls (or None
+    entries), Bs: per lattice [nrhs, V, 4, 3] complex128.  Returns (Xs, [[Stats]])."""
+    nlat = len(ops)
+    p = params if params is not None else params_default()
+    if Xs is None:
+        Xs = [_empty_like(b) for b in Bs]
+    nr = [int(np.prod(b.shape)) // (12 * o.volume) for b, o in zip(Bs, ops)]
+    oa = (_vp * nlat)(*[o.handle for o in ops])
+    da = (_vp * nlat)(*[(d.handle if d is not None else None) for d in defls])
+    ba = (_vp * nlat)(*[_ptr(b) for b in Bs])
+    xa = (_vp * nlat)(*[_ptr(x) for x in Xs])
+    na = (ctypes.c_int * nlat)(*nr)
+    st = (Stats * max(sum(nr), 1))()
+    _check(lib.dlz_batch_dminres(nlat, oa, da, ba, xa, na, ctypes.byref(p), st), allow=(ERR_NOT_CONVERGED,))
+    out, q = [], 0
+    for r in nr:
+        out.append([st[q + i] for i in range(r)])
+        q += r
+    return Xs, out
 
 
 def defl_count(defl):

@@ -1,0 +1,53 @@
+"""D-MinRes on several lattices of uneven size at once (dlz_batch_dminres):
+every solution reaches ||b - D x|| / ||b|| <= 1e-10 (checked with the FP64 oracle's
+own operator) and agrees with that lattice's solve on its own."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import wilson
+from tests._lib import dlz
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+LATS = [((4, 4, 4, 4), 0.18, 11), ((4, 4, 4, 8), 0.2, 12), ((6, 4, 4, 4), 0.21, 13), ((8, 8, 8, 8), 0.19, 14)]
+
+
+@pytest.fixture(scope="module")
+def m():
+    return dlz()
+
+
+@pytest.mark.parametrize("with_defl", [True, False])
+def test_batch_dminres_uneven_lattices(m, with_defl):
+    ops, defls, Bs, Us = [], [], [], []
+    for i, (dims, kappa, seed) in enumerate(LATS):
+        U = synth.su3_links(dims, seed)
+        op = m.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
+        b0 = torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda()
+        d = None
+        if with_defl:
+            _, d, _ = m.minresdr(op, b0, m.params_default(m=30, k=8, tol=1e-10, max_cycles=200))
+        ops.append(op); defls.append(d); Us.append(U)
+        Bs.append(torch.from_numpy(synth.gaussian_spinors(dims, [1 + i, 2 + i, 3 + i][: 2 + (i % 2)])).cuda())
+    p = m.params_default(m=30, k=8, tol=1e-10, max_iter=20000, precision=m.F32)
+    Xs, sts = m.batch_dminres(ops, defls, Bs, p)
+    alone_max = 0
+    for l, (dims, kappa, seed) in enumerate(LATS):
+        D = wilson.operator(Us[l], kappa, dims, "D")
+        Xl = Xs[l].cpu().numpy()
+        Bl = Bs[l].cpu().numpy()
+        _, alone = m.dminres(ops[l], defls[l], Bs[l], p)
+        alone_max = max(alone_max, max(s.iterations for s in alone))
+        for r in range(Bl.shape[0]):
+            assert sts[l][r].converged == 1
+            b = Bl[r].reshape(-1)
+            assert np.linalg.norm(b - D(Xl[r].reshape(-1))) <= 1.01e-10 * np.linalg.norm(b)
+    # the slots iterate together until the slowest one is done: the batch takes about
+    # as many iterations as the hardest lattice alone
+    assert max(s.iterations for ss in sts for s in ss) <= alone_max + 96
+    # the plain FP64 form of the same entry point solves them one lattice at a time
+    p64 = m.params_default(m=30, k=8, tol=1e-10, max_iter=20000)
+    Xs64, sts64 = m.batch_dminres(ops, defls, Bs, p64)
+    assert all(s.converged == 1 for ss in sts64 for s in ss)
