@@ -542,6 +542,81 @@ def run_learned_seed(args):
     print(json.dumps(out), flush=True)
 
 
+def run_multi_lattice(args):
+    """Uneven multi-lattice batching: 64 lattices (i mod 3 -> 8^4, 12^4, 16^4), links
+    by the same recipe (gauge seed 3000 + i), per-lattice kappa drawn uniformly in
+    [0.21, 0.24] (numpy default_rng(4000)); MinRes-DR(40,10) (FP32 form) on one
+    Gaussian RHS per lattice, then D-MinRes on 8 Gaussian RHS per lattice (512 solves):
+    all lattices through one dlz_batch_dminres call (FP32, one launch per stage for
+    all slots) against the same solves lattice by lattice (dlz_dminres, FP32 batched per
+    lattice) and, on one lattice of each size, the plain FP64 form.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_0901_3163_gb300 import dlz
+    sizes = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16)]
+    nl = args.ml_lattices
+    kap = np.random.default_rng(4000).uniform(0.21, 0.24, nl)
+    t0 = time.perf_counter()
+    ops, defls, Bs = [], [], []
+    dr_s = 0.0
+    for i in range(nl):
+        dims = sizes[i % 3]
+        op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, 3000 + i)).cuda(), float(kap[i]))
+        b0 = torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda()
+        ta = time.perf_counter()
+        _, d, st = dlz.minresdr(op, b0, dlz.params_default(m=40, k=10, tol=1e-10, max_cycles=400, precision=dlz.F32))
+        torch.cuda.synchronize()
+        dr_s += time.perf_counter() - ta
+        ops.append(op)
+        defls.append(d)
+        Bs.append(torch.from_numpy(synth.gaussian_spinors(dims, list(range(1, 9)))).cuda())
+    t_setup = time.perf_counter() - t0
+    sites = sum(o.volume for o in ops)
+    p32 = dlz.params_default(m=40, k=10, tol=1e-10, max_iter=100000, precision=dlz.F32)
+    dlz.batch_dminres(ops, defls, Bs, p32)          # warm-up (graph capture, scratch)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ta = time.perf_counter()
+    Xs, sts = dlz.batch_dminres(ops, defls, Bs, p32)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - ta
+    clk = clocks.stop()
+    ok_batch = sum(1 for ss in sts for s in ss if s.converged == 1 and s.true_residual <= 1e-10)
+    ta = time.perf_counter()
+    ok_seq = 0
+    for o, d, B in zip(ops, defls, Bs):
+        _, ss = dlz.dminres(o, d, B, p32)
+        ok_seq += sum(1 for s in ss if s.converged == 1 and s.true_residual <= 1e-10)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - ta
+    p64 = dlz.params_default(m=40, k=10, tol=1e-10, max_iter=100000)
+    ta = time.perf_counter()
+    ok64, n64 = 0, 0
+    for j in range(min(3, nl)):            # one lattice of each size
+        _, ss = dlz.dminres(ops[j], defls[j], Bs[j], p64)
+        ok64 += sum(1 for s in ss if s.converged == 1 and s.true_residual <= 1e-10)
+        n64 += len(ss)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - ta
+    iters = [max(s.iterations for s in ss) for ss in sts]
+    out = {"mode": "multi-lattice", "workload": f"{nl} lattices 8^4/12^4/16^4, kappa U[0.21,0.24], "
+                                                f"MinRes-DR(40,10) + D-MinRes x 8 RHS each",
+           "lattices": nl, "sites_total": int(sites), "rhs_total": int(sum(len(ss) for ss in sts)),
+           "setup_seconds": round(t_setup, 2), "first_rhs_dr_seconds": round(dr_s, 3),
+           "batched": {"seconds": round(t_batch, 3), "rhs_per_s": round(ok_batch / t_batch, 2), "solved": ok_batch,
+                       "iterations_max": int(max(iters))},
+           "lattice_by_lattice_f32": {"seconds": round(t_seq, 3), "rhs_per_s": round(ok_seq / t_seq, 2),
+                                      "solved": ok_seq},
+           "plain_fp64_sample": {"lattices": 3, "rhs": n64, "seconds": round(t64, 3),
+                                 "rhs_per_s": round(ok64 / t64, 3) if t64 > 0 else None},
+           "batched_over_lattice_by_lattice": round((ok_batch / t_batch) / (ok_seq / t_seq), 3),
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -564,6 +639,8 @@ def main():
     ap.add_argument("--first-rhs-only", action="store_true")
     ap.add_argument("--ncu-case", action="store_true")
     ap.add_argument("--learned-seed", action="store_true")
+    ap.add_argument("--multi-lattice", action="store_true")
+    ap.add_argument("--ml-lattices", type=int, default=64)
     ap.add_argument("--ls-train", type=int, default=32)
     ap.add_argument("--ls-test", type=int, default=8)
     ap.add_argument("--ls-steps", type=int, default=400)
@@ -579,6 +656,8 @@ def main():
         run_ncu_case(args)
     elif args.learned_seed:
         run_learned_seed(args)
+    elif args.multi_lattice:
+        run_multi_lattice(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -98,8 +98,12 @@ __global__ void __launch_bounds__(kMT)
 k_mm_k1(const float4 *__restrict__ U, const float4 *__restrict__ Up, float4 *__restrict__ W,
         const float4 *__restrict__ D2, float4 *__restrict__ D3, float4 *__restrict__ E,
         const SlotDesc *__restrict__ sd, const int2 *__restrict__ table, const FusedState *__restrict__ st,
-        double *__restrict__ partials) {
+        const int *__restrict__ active, double *__restrict__ partials) {
     const int2 t = table[blockIdx.x];
+    if (!active[t.x]) {                 // a finished slot: its blocks do no work (uniform per block)
+        if (threadIdx.x == 0) partials[blockIdx.x] = 0.0;
+        return;
+    }
     const SlotDesc d = sd[t.x];
     const int s = t.y + threadIdx.x;
     float facc = 0.f;
@@ -110,7 +114,9 @@ k_mm_k1(const float4 *__restrict__ U, const float4 *__restrict__ Up, float4 *__r
 }
 
 __global__ void __launch_bounds__(256)
-k_mm_alpha(const double *__restrict__ partials, const SlotDesc *__restrict__ sd, FusedState *__restrict__ st) {
+k_mm_alpha(const double *__restrict__ partials, const SlotDesc *__restrict__ sd, FusedState *__restrict__ st,
+           const int *__restrict__ active) {
+    if (!active[blockIdx.x]) return;
     const SlotDesc d = sd[blockIdx.x];
     const double a = slot_sum(partials, d.blk0, d.nb);
     if (threadIdx.x == 0) fused_alpha(st[blockIdx.x], a);
@@ -118,8 +124,13 @@ k_mm_alpha(const double *__restrict__ partials, const SlotDesc *__restrict__ sd,
 
 __global__ void __launch_bounds__(kMT)
 k_mm_k2a(float4 *__restrict__ W, const float4 *__restrict__ U, const SlotDesc *__restrict__ sd,
-         const int2 *__restrict__ table, const FusedState *__restrict__ st, double *__restrict__ partials) {
+         const int2 *__restrict__ table, const FusedState *__restrict__ st, const int *__restrict__ active,
+         double *__restrict__ partials) {
     const int2 t = table[blockIdx.x];
+    if (!active[t.x]) {
+        if (threadIdx.x == 0) partials[blockIdx.x] = 0.0;
+        return;
+    }
     const SlotDesc d = sd[t.x];
     const int s = t.y + threadIdx.x;
     float facc = 0.f;
@@ -128,7 +139,9 @@ k_mm_k2a(float4 *__restrict__ W, const float4 *__restrict__ U, const SlotDesc *_
 }
 
 __global__ void __launch_bounds__(256)
-k_mm_k2b(const double *__restrict__ partials, const SlotDesc *__restrict__ sd, FusedState *__restrict__ st) {
+k_mm_k2b(const double *__restrict__ partials, const SlotDesc *__restrict__ sd, FusedState *__restrict__ st,
+         const int *__restrict__ active) {
+    if (!active[blockIdx.x]) return;
     const SlotDesc d = sd[blockIdx.x];
     const double r2 = slot_sum(partials, d.blk0, d.nb);
     if (threadIdx.x == 0) {
@@ -160,9 +173,14 @@ k_mm_last(const float4 *__restrict__ Uj, const float4 *__restrict__ D2, const fl
 
 // The fused FP32 MinRes over all slots (r: normalised residuals in the arena; e:
 // corrections, holding the start if e_init).  bufs: 5 arena-sized work vectors.
+// A slot whose inner residual has met its tolerance at a check is frozen: its blocks
+// return at once and its state stops changing (the buffer roles repeat every 6
+// iterations and checks fall on multiples of 6, so the frozen slot's pending
+// direction update is still found where k_mm_last looks for it).
 int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const int2 *table, int nblocks, size_t arena,
                        const float4 *r, float4 *e, float4 *const bufs[5], FusedState *ms, double *partials,
-                       const double *d_tol, const dlz_params &p, int &iters, HostScratch &hs, bool e_init) {
+                       int *active, const double *d_tol, const dlz_params &p, int &iters, HostScratch &hs,
+                       bool e_init) {
     double *partials2 = partials + nblocks;
     k_mm_norm<<<nblocks, kMT, 0, op.stream>>>(r, sd, table, partials);
     k_mm_init<<<NS, 256, 0, op.stream>>>(partials, sd, ms);
@@ -173,10 +191,10 @@ int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const int2 *table, in
     for (float4 *z : {Up0, D20, D30}) DLZ_CUDA_TRY(cudaMemsetAsync(z, 0, arena * sizeof(float4), op.stream));
     if (!e_init) DLZ_CUDA_TRY(cudaMemsetAsync(e, 0, arena * sizeof(float4), op.stream));
     auto iteration = [&](float4 *U, float4 *Up, float4 *W, float4 *D2, float4 *D3) -> int {
-        k_mm_k1<<<nblocks, kMT, 0, op.stream>>>(U, Up, W, D2, D3, e, sd, table, ms, partials);
-        k_mm_alpha<<<NS, 256, 0, op.stream>>>(partials, sd, ms);
-        k_mm_k2a<<<nblocks, kMT, 0, op.stream>>>(W, U, sd, table, ms, partials2);
-        k_mm_k2b<<<NS, 256, 0, op.stream>>>(partials2, sd, ms);
+        k_mm_k1<<<nblocks, kMT, 0, op.stream>>>(U, Up, W, D2, D3, e, sd, table, ms, active, partials);
+        k_mm_alpha<<<NS, 256, 0, op.stream>>>(partials, sd, ms, active);
+        k_mm_k2a<<<nblocks, kMT, 0, op.stream>>>(W, U, sd, table, ms, active, partials2);
+        k_mm_k2b<<<NS, 256, 0, op.stream>>>(partials2, sd, ms, active);
         op.prof.launches += 4;
         DLZ_CUDA_TRY(cudaGetLastError());
         return DLZ_OK;
@@ -196,6 +214,8 @@ int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const int2 *table, in
     std::vector<FusedState> h(NS);
     std::vector<double> tol(NS);
     DLZ_TRY(d2h_sync(op, tol.data(), d_tol, NS * sizeof(double)));
+    std::vector<int> act(NS, 1);
+    DLZ_TRY(h2d(op, active, act.data(), NS * sizeof(int)));
     int it = 0;
     while (iters < p.max_iter) {
         DLZ_TRY(run_graph(op, ge, six));
@@ -203,12 +223,15 @@ int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const int2 *table, in
         it += 6;
         if (it % check == 0 || iters >= p.max_iter) {
             DLZ_TRY(d2h_sync(op, h.data(), ms, NS * sizeof(FusedState)));
-            bool done = true;
+            bool done = true, changed = false;
             for (int q = 0; q < NS; ++q) {
                 if (!std::isfinite(h[q].phibar)) return fail(DLZ_ERR_NONFINITE, "MinRes residual not finite");
-                if (!(std::fabs(h[q].phibar) <= tol[q] * h[q].r0 || h[q].beta_next == 0.0)) done = false;
+                const bool ok = std::fabs(h[q].phibar) <= tol[q] * h[q].r0 || h[q].beta_next == 0.0;
+                if (!ok) done = false;
+                else if (act[q]) { act[q] = 0; changed = true; }
             }
             if (done) break;
+            if (changed) DLZ_TRY(h2d(op, active, act.data(), NS * sizeof(int)));
         }
     }
     k_mm_last<<<nblocks, kMT, 0, op.stream>>>(Up0, D20, D30, e, sd, table, ms);
@@ -253,13 +276,14 @@ int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, cons
     DLZ_TRY(dtab.alloc(nblocks * sizeof(int2)));
     DLZ_TRY(f32.alloc(7 * arena * sizeof(float4)));
     DLZ_TRY(part.alloc(2 * (size_t)nblocks * sizeof(double)));
-    DLZ_TRY(scal.alloc((size_t)NS * (sizeof(FusedState) + 2 * sizeof(double))));
+    DLZ_TRY(scal.alloc((size_t)NS * (sizeof(FusedState) + 2 * sizeof(double) + sizeof(int))));
     DLZ_TRY(h2d(op, dsd.p, hsd.data(), NS * sizeof(SlotDesc)));
     DLZ_TRY(h2d(op, dtab.p, table.data(), nblocks * sizeof(int2)));
     float4 *r32 = f32.as<float4>(), *e32 = r32 + arena;
     float4 *const bufs[5] = {r32 + 2 * arena, r32 + 3 * arena, r32 + 4 * arena, r32 + 5 * arena, r32 + 6 * arena};
     FusedState *ms = reinterpret_cast<FusedState *>(scal.p);
     double *d_tol = reinterpret_cast<double *>(ms + NS);
+    int *d_active = reinterpret_cast<int *>(d_tol + 2 * NS);
     HostScratch hs;
     DLZ_TRY(hs.ensure(64));
     // per-lattice FP64 work: b' = gamma5 b, x, r, Q x
@@ -398,7 +422,7 @@ int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, cons
         }
         DLZ_TRY(h2d(op, d_tol, tl.data(), NS * sizeof(double)));
         DLZ_TRY(minres_multi_batch(op, NS, dsd.as<SlotDesc>(), dtab.as<int2>(), nblocks, arena, r32, e32, bufs, ms,
-                                   part.as<double>(), d_tol, p, iters, hs, true));
+                                   part.as<double>(), d_active, d_tol, p, iters, hs, true));
         DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
         // x += ||r|| e, lattice by lattice
         for (int l = 0; l < nlat; ++l) {
