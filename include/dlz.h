@@ -65,6 +65,9 @@ extern "C" {
 #define DLZ_F64 0   /* plain FP64 everywhere                                     */
 #define DLZ_F32 1   /* FP32 stencil and Krylov vectors inside an FP64 defect-correction
                        loop (FP64 x, residual and deflation projection)           */
+#define DLZ_BF16 2  /* dlz_apply / dlz_stencil_bench only: complex64 user vectors
+                       stored as bfloat16 inside (rounded to nearest even), FP32
+                       arithmetic, result rounded to bfloat16 once               */
 
 typedef struct dlz_op_s *dlz_op_t;
 typedef struct dlz_defl_s *dlz_defl_t;
@@ -143,7 +146,9 @@ int dlz_op_volume(dlz_op_t op, long long *V);
  * out = A in for A = DLZ_D, DLZ_DDAG, DLZ_Q or DLZ_DDAGD (Sec. 2: M, M^dagger,
  * gamma5 M, M^dagger M), on `nrhs` spinors stored one after another.
  * dtype DLZ_F64: complex128 [nrhs][V][4][3]; DLZ_F32: complex64, computed in
- * FP32.  in and out must not overlap.  nrhs = 0 is a no-op.
+ * FP32; DLZ_BF16: complex64 in and out, stored as bfloat16 inside (in rounded
+ * once, FP32 arithmetic, out rounded once; D^dag D rounds its intermediate
+ * gamma5 D too).  in and out must not overlap.  nrhs = 0 is a no-op.
  */
 int dlz_apply(dlz_op_t op, int which, const void *in, void *out, int dtype, int nrhs);
 
@@ -158,7 +163,8 @@ int dlz_apply(dlz_op_t op, int which, const void *in, void *out, int dtype, int 
  * keeps other streams busy and cannot afford the device-wide synchronisation
  * of the cudaFree that dlz_apply's temporary buffers end with.
  *
- * Same operation, arguments and layout as dlz_apply, except: in and out must
+ * Same operation, arguments and layout as dlz_apply (dtype DLZ_F64 or DLZ_F32
+ * only), except: in and out must
  * be device (or managed) pointers (host pointers: DLZ_ERR_BADARG, since
  * staging them would allocate), and the packed work vectors live in one
  * static device array of DLZ_NOALLOC_SCRATCH_BYTES per device: 2 vectors of

@@ -17,8 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdlz.so")
-SOURCES = ["wilson.cu", "dr.cu", "solvers.cu", "solvers_mixed.cu", "minres_fused.cu", "cg_fused.cu", "minres_multi.cu", "api.cu",
-           "ptc.cu", "small_dense.cpp"]
+SOURCES = ["wilson.cu", "wilson_bf16.cu", "dr.cu", "solvers.cu", "solvers_mixed.cu", "minres_fused.cu",
+           "cg_fused.cu", "minres_multi.cu", "api.cu", "ptc.cu", "small_dense.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -398,7 +398,7 @@ int dlz_apply(dlz_op_t h, int which, const void *in, void *out, int dtype, int n
     Op &op = h->op;
     if (nrhs < 0) return fail(DLZ_ERR_BADARG, "nrhs < 0");
     if (which < DLZ_D || which > DLZ_DDAGD) return fail(DLZ_ERR_BADARG, "which");
-    if (dtype != DLZ_F64 && dtype != DLZ_F32) return fail(DLZ_ERR_BADARG, "dtype");
+    if (dtype != DLZ_F64 && dtype != DLZ_F32 && dtype != DLZ_BF16) return fail(DLZ_ERR_BADARG, "dtype");
     if (nrhs == 0) return DLZ_OK;
     if (!in || !out) return fail(DLZ_ERR_BADARG, "null vector");
     op.prof.begin(false, false);
@@ -421,12 +421,24 @@ int dlz_apply(dlz_op_t h, int which, const void *in, void *out, int dtype, int n
             DLZ_TRY(pack64(op, a.as<double2>(), src));
             DLZ_TRY(apply64(op, b.as<double2>(), a.as<double2>(), which, t.as<double2>()));
             DLZ_TRY(unpack64(op, dst, b.as<double2>()));
-        } else {
+        } else if (dtype == DLZ_F32) {
             const float2 *src = (const float2 *)si.dev + (size_t)r * n;
             float2 *dst = (float2 *)so.dev + (size_t)r * n;
             DLZ_TRY(pack32(op, a.as<float4>(), src));
             DLZ_TRY(apply32(op, b.as<float4>(), a.as<float4>(), which, t.as<float4>()));
             DLZ_TRY(unpack32(op, dst, b.as<float4>()));
+        } else {
+            // bfloat16 storage: D^dag D is Q applied twice, rounded to bfloat16 in between
+            const float2 *src = (const float2 *)si.dev + (size_t)r * n;
+            float2 *dst = (float2 *)so.dev + (size_t)r * n;
+            DLZ_TRY(pack_bf16(op, a.as<uint2>(), src));
+            if (which == DLZ_DDAGD) {
+                DLZ_TRY(wilson_bf16_batch(op, t.as<uint2>(), a.as<uint2>(), DLZ_Q, 1));
+                DLZ_TRY(wilson_bf16_batch(op, b.as<uint2>(), t.as<uint2>(), DLZ_Q, 1));
+            } else {
+                DLZ_TRY(wilson_bf16_batch(op, b.as<uint2>(), a.as<uint2>(), which, 1));
+            }
+            DLZ_TRY(unpack_bf16(op, dst, b.as<uint2>()));
         }
     }
     return so.flush(op);
@@ -554,7 +566,7 @@ int dlz_stencil_bench(dlz_op_t h, int dtype, int which, int nrhs, int iters, con
     Op &op = h->op;
     if (!in || !ms_per_launch || nrhs < 1 || nrhs > 64 || iters < 1) return fail(DLZ_ERR_BADARG, "stencil_bench arguments");
     if (which != DLZ_D && which != DLZ_DDAG && which != DLZ_Q) return fail(DLZ_ERR_BADARG, "which");
-    if (dtype != DLZ_F64 && dtype != DLZ_F32) return fail(DLZ_ERR_BADARG, "dtype");
+    if (dtype != DLZ_F64 && dtype != DLZ_F32 && dtype != DLZ_BF16) return fail(DLZ_ERR_BADARG, "dtype");
     op.prof.begin(false, false);
     const long n = 12L * op.g.V;
     const size_t esz = dtype == DLZ_F64 ? sizeof(double2) : sizeof(float2);
@@ -565,10 +577,12 @@ int dlz_stencil_bench(dlz_op_t h, int dtype, int which, int nrhs, int iters, con
     DLZ_TRY(b.alloc((size_t)n * nrhs * esz));
     for (int r = 0; r < nrhs; ++r) {
         if (dtype == DLZ_F64) DLZ_TRY(pack64(op, a.as<double2>() + (size_t)r * n, (const double2 *)si.dev + (size_t)r * n));
-        else DLZ_TRY(pack32(op, a.as<float4>() + (size_t)r * n / 2, (const float2 *)si.dev + (size_t)r * n));
+        else if (dtype == DLZ_F32) DLZ_TRY(pack32(op, a.as<float4>() + (size_t)r * n / 2, (const float2 *)si.dev + (size_t)r * n));
+        else DLZ_TRY(pack_bf16(op, a.as<uint2>() + (size_t)r * n / 2, (const float2 *)si.dev + (size_t)r * n));
     }
     auto launch = [&]() -> int {
         if (dtype == DLZ_F64) return wilson64_batch(op, b.as<double2>(), a.as<double2>(), which, nrhs);
+        if (dtype == DLZ_BF16) return wilson_bf16_batch(op, b.as<uint2>(), a.as<uint2>(), which, nrhs);
         return wilson32_batch(op, b.as<float4>(), a.as<float4>(), which, nrhs);
     };
     for (int i = 0; i < 3; ++i) DLZ_TRY(launch());

@@ -243,6 +243,10 @@ int pack64(Op &op, double2 *dst, const double2 *src_canon);
 int unpack64(Op &op, double2 *dst_canon, const double2 *src);
 int pack32(Op &op, float4 *dst, const float2 *src_canon);
 int unpack32(Op &op, float2 *dst_canon, const float4 *src);
+// bfloat16 spinors (uint2 planes [6][V]) with FP32 arithmetic (wilson_bf16.cu)
+int wilson_bf16_batch(Op &op, uint2 *out, const uint2 *in, int which, int nrhs);
+int pack_bf16(Op &op, uint2 *dst, const float2 *src_canon);
+int unpack_bf16(Op &op, float2 *dst_canon, const uint2 *src);
 int convert64to32(Op &op, float4 *dst, const double2 *src);
 int convert32to64(Op &op, double2 *dst, const float4 *src);
 

@@ -31,7 +31,7 @@ ERR_OOM = -8
 ERR_IO = -9
 
 D, DDAG, Q, DDAGD = 0, 1, 2, 3
-F64, F32 = 0, 1
+F64, F32, BF16 = 0, 1, 2
 
 
 class Params(ctypes.Structure):
@@ -326,9 +326,11 @@ def apply_noalloc(op, which, x, out=None):
     return out
 
 
-def stencil_bench(op, x, iters=50, which=D):
-    """Average device time of one stencil launch over x's right-hand sides ([nrhs, V, 4, 3])."""
-    dtype = F32 if str(x.dtype).endswith("complex64") else F64
+def stencil_bench(op, x, iters=50, which=D, dtype=None):
+    """Average device time of one stencil launch over x's right-hand sides ([nrhs, V, 4, 3]);
+    dtype BF16 stores the complex64 x as bfloat16."""
+    if dtype is None:
+        dtype = F32 if str(x.dtype).endswith("complex64") else F64
     nrhs = int(np.prod(x.shape)) // (12 * op.volume)
     ms = ctypes.c_double()
     _check(lib.dlz_stencil_bench(op.handle, dtype, int(which), nrhs, int(iters), _ptr(x), ctypes.byref(ms)))

@@ -83,3 +83,24 @@ def test_bad_gauge_is_rejected(m):
     with pytest.raises(m.DlzError) as e:
         m.create_operator(dims, U, 0.1)
     assert e.value.code == m.ERR_BAD_GAUGE
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (3, 5, 4, 6)])
+@pytest.mark.parametrize("bc_t", [1, -1])
+def test_stencil_bf16_storage(m, dims, bc_t):
+    """bfloat16 storage, FP32 arithmetic: against the FP64 oracle applied to the input
+    rounded to bfloat16 on the host, within one bfloat16 rounding of the output (2^-8
+    of the largest entry; D^dag D within two); every output value is a bfloat16."""
+    from oracle import ptc
+    U = synth.su3_links(dims, 3)
+    kappa = 0.137
+    op = m.create_operator(dims, torch.from_numpy(U).cuda(), kappa, bc_t)
+    psi = synth.gaussian_spinors(dims, [1, 2])
+    xr = ptc.round_bf16(psi.astype(np.complex64))
+    x = torch.from_numpy(psi.astype(np.complex64)).cuda()
+    for name, ref in REFS.items():
+        want = ref(U, xr, kappa, dims, bc_t)
+        got = m.apply(op, getattr(m, name), x, dtype=m.BF16).cpu().numpy()
+        assert np.array_equal(ptc.round_bf16(got), got.astype(np.complex128))
+        tol = 2.0 ** -8 * (2 if name == "DDAGD" else 1)
+        assert _rel(got, want) < tol, (name, _rel(got, want))
