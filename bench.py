@@ -617,6 +617,75 @@ def run_multi_lattice(args):
     print(json.dumps(out), flush=True)
 
 
+def run_c3(args):
+    """Precision and batching on the 24^3x48 lattice (gauge seed 3, kappa by the
+    sigma_min = 1e-3 rule from synth/kappa_table.json, or --kappa): FP32 Lan-DR(120,60)
+    on D^dag D for the first Gaussian RHS (seed 0), then FP32 D-CG with FP64 defect
+    correction on 48 Gaussian RHS (seeds 1..48) in batches of 16 per launch; the
+    plain FP64 D-CG timed on 2 of them; the bare stencil in FP32 and bfloat16 with
+    16 RHS per launch.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_0901_3163_gb300 import dlz
+    dims = (24, 24, 24, 48)
+    V = synth.volume(dims)
+    if args.kappa is not None:
+        kappa, ksrc = args.kappa, "given on the command line (not the sigma_min rule)"
+    else:
+        try:
+            kappa, ksrc = synth.kappa_for(dims, 3), "sigma_min(D) = 1e-3 rule (oracle)"
+        except KeyError:
+            print(json.dumps({"mode": "c3", "unavailable": "kappa of the 24^3x48 seed-3 lattice not in the table"}))
+            return
+    t0 = time.perf_counter()
+    op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, 3)).cuda(), kappa)
+    t_links = time.perf_counter() - t0
+    peaks, src = _peaks()
+    ds = {}
+    for name, dt, real in (("f32", dlz.F32, 4), ("bf16", dlz.BF16, 2)):
+        xs = torch.randn((16, V, 4, 3), dtype=torch.complex64, device="cuda")
+        ms = dlz.stencil_bench(op, xs, 20, dtype=dt)["ms"]
+        nb = V * (48 * 16 * real + 48 * 4)
+        ds[name] = {"avg_launch_ms": round(ms, 4), "gbs": round(nb / ms / 1e6, 1),
+                    "frac_hbm": round(nb / ms / 1e6 / peaks["hbm_gbs"], 4)}
+        del xs
+    b0 = torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, d, st = dlz.landr(op, b0, dlz.params_default(m=120, k=60, tol=1e-10, max_cycles=args.max_cycles,
+                                                     precision=dlz.F32))
+    torch.cuda.synchronize()
+    t_dr = time.perf_counter() - t0
+    B = torch.from_numpy(synth.gaussian_spinors(dims, list(range(1, 49)))).cuda()
+    pd = dlz.params_default(m=120, k=60, tol=1e-10, max_iter=200000, precision=dlz.F32, profile=1)
+    t0 = time.perf_counter()
+    _, sts = dlz.dcg(op, d, B, pd)
+    torch.cuda.synchronize()
+    t_d = time.perf_counter() - t0
+    ok = sum(1 for s in sts if s.converged == 1 and s.true_residual <= 1e-10)
+    st_ms = sum(s.stencil_ms for s in sts)
+    st_b = sum(s.stencil_bytes for s in sts)
+    p64 = dlz.params_default(m=120, k=60, tol=1e-10, max_iter=200000)
+    t0 = time.perf_counter()
+    _, s64 = dlz.dcg(op, d, B[:2].contiguous(), p64)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    ok64 = sum(1 for s in s64 if s.converged == 1 and s.true_residual <= 1e-10)
+    out = {"mode": "c3", "workload": "24^3x48 Lan-DR(120,60) + D-CG on 48 Gaussian RHS",
+           "kappa": kappa, "kappa_source": ksrc, "links_seconds": round(t_links, 1),
+           "first_rhs": {"seconds": round(t_dr, 3), "cycles": st.cycles, "iterations": st.iterations,
+                         "converged": st.converged},
+           "dcg_f32_batched": {"seconds": round(t_d, 3), "rhs_per_s": round(ok / t_d, 4), "solved": ok,
+                               "iterations": [s.iterations for s in sts[:3]],
+                               "fused_kernel_gbs": round(st_b / max(st_ms, 1e-9) / 1e6, 1)},
+           "dcg_plain_fp64_2rhs": {"seconds": round(t64, 3), "rhs_per_s": round(ok64 / t64, 4), "solved": ok64,
+                                   "iterations": [s.iterations for s in s64]},
+           "dslash_16rhs": ds, "peak_source": src}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -640,6 +709,7 @@ def main():
     ap.add_argument("--ncu-case", action="store_true")
     ap.add_argument("--learned-seed", action="store_true")
     ap.add_argument("--multi-lattice", action="store_true")
+    ap.add_argument("--c3", action="store_true")
     ap.add_argument("--ml-lattices", type=int, default=64)
     ap.add_argument("--ls-train", type=int, default=32)
     ap.add_argument("--ls-test", type=int, default=8)
@@ -658,6 +728,8 @@ def main():
         run_learned_seed(args)
     elif args.multi_lattice:
         run_multi_lattice(args)
+    elif args.c3:
+        run_c3(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
