@@ -441,17 +441,43 @@ def run_first_rhs_only(args):
 
 
 def run_ncu_case(args):
-    """A short run of the benchmark's kernels for ncu captures: the 16^3x32
+    """A short run of the benchmark's kernels for ncu captures.  minres: the 16^3x32
     operator, a deflation set from 2 FP32 MinRes-DR(100,40) cycles (their
     finishing MinRes capped at 12 iterations), then 48 FP32 D-MinRes iterations
     on the 11 point sources batched (fused kernels with 11 right-hand sides per
-    launch).  Prints the stats."""
+    launch).  cg: the same with Lan-DR and D-CG on 11 Gaussian RHS.  ptc: one
+    forward and backward of the learned-seed network on 16^4.  Prints the stats."""
     import torch
 
+    import synth
     from paper_0901_3163_gb300 import dlz
     w, dims, U, kappa, B = workload_inputs()
     op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
     Bd = torch.from_numpy(B).cuda()
+    if args.ncu_case == "ptc":
+        # the learned-seed network on a 16^4 lattice: one forward and one backward of 4 vectors
+        from paper_0901_3163_gb300 import ptc_train as T
+        dims4 = (16, 16, 16, 16)
+        op4 = dlz.create_operator(dims4, torch.from_numpy(synth.su3_links(dims4, 1000)).cuda(), 0.25)
+        net = dlz.net_create(op4, T.default_widths(), T.init_weights(T.default_widths(), 1))
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(0)
+        x = T.noise(torch, op4, 4, gen)
+        f = dlz.net_forward(net, x)
+        dlz.net_backward(net, f)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "ncu-case", "case": "ptc"}))
+        return
+    if args.ncu_case == "cg":
+        # FP32 Lan-DR(100,40) for 2 cycles, then 48 fused CGNR iterations on 11 Gaussian RHS
+        p = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=2, max_iter=12, precision=dlz.F32)
+        _, d, st = dlz.landr(op, Bd[0].contiguous(), p)
+        G = torch.from_numpy(synth.gaussian_spinors(dims, list(range(1, 12)))).cuda()
+        pd = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=48, precision=dlz.F32)
+        _, sts = dlz.dcg(op, d, G, pd)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "ncu-case", "case": "cg", "d_iterations": [s.iterations for s in sts]}))
+        return
     p = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=2, max_iter=12, precision=dlz.F32)
     _, d, st = dlz.minresdr(op, Bd[0].contiguous(), p)
     pd = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=48, precision=dlz.F32)
@@ -706,7 +732,7 @@ def main():
     ap.add_argument("--nrhs", type=int, default=11)
     ap.add_argument("--stencil-iters", type=int, default=50)
     ap.add_argument("--first-rhs-only", action="store_true")
-    ap.add_argument("--ncu-case", action="store_true")
+    ap.add_argument("--ncu-case", nargs="?", const="minres", default=None, choices=["minres", "cg", "ptc"])
     ap.add_argument("--learned-seed", action="store_true")
     ap.add_argument("--multi-lattice", action="store_true")
     ap.add_argument("--c3", action="store_true")
@@ -722,7 +748,7 @@ def main():
         run_stencil_only(args)
     elif args.first_rhs_only:
         run_first_rhs_only(args)
-    elif args.ncu_case:
+    elif args.ncu_case is not None:
         run_ncu_case(args)
     elif args.learned_seed:
         run_learned_seed(args)
