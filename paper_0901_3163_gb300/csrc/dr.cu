@@ -401,6 +401,8 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
     DLZ_TRY(Dx.alloc(n64 * sizeof(double2)));
     DLZ_TRY(scal.alloc((size_t)(2 * m + 8) * sizeof(double)));
     DLZ_TRY(coef.alloc((size_t)(m + 1) * (m + 1) * sizeof(double2)));
+    DevBuf gcoef;                               // the restart GEMM's coefficient matrix
+    DLZ_TRY(gcoef.alloc((size_t)(m + 1) * (k + 1) * sizeof(double)));
     double *d_alpha = scal.as<double>(), *d_beta = d_alpha + m, *d_norm = d_beta + m;
     // the same scalars in the element-update precision (written by the finishers)
     typedef typename P::S S;
@@ -573,8 +575,8 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         st.mvps += 1;
         DLZ_TRY(v64::norm2_diff(op, bb.as<double2>(), Dx.as<double2>(), d_norm + 2));
         // ---------------- restart: V_{k+1} <- V_{m+1} P
-        DLZ_TRY(h2d(op, coef.p, pl.P.data(), pl.P.size() * sizeof(double)));
-        DLZ_TRY(combine<P>(op, Vn, n, k + 1, V, n, m + 1, coef.p, k + 1, true, false));
+        if constexpr (P::kF32) DLZ_TRY(restart_gemm32(op, Vn, V, n, m + 1, k + 1, pl.P.data(), gcoef.p));
+        else DLZ_TRY(restart_gemm64(op, Vn, V, n, m + 1, k + 1, pl.P.data(), gcoef.p));
         if (rperiod > 0) {
             // the vector carried across the restart joins the periodic re-orthogonalisation
             E *vk = Vn + (size_t)k * n;

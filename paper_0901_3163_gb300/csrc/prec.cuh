@@ -120,63 +120,9 @@ k_combine(typename P::E *__restrict__ out, long ld_out, int nout, const typename
     }
 }
 
-// FP32 restart combine with real coefficients in one pass: out_l = sum_j coef[j][l] in_j
-// for nout <= TPE * NH outputs.  TPE neighbouring threads share an element (float4)
-// and split the outputs, so each input vector is read from DRAM once per element
-// (the other threads' reads hit L1) instead of once per group of 16 outputs.
-template <int NH, int TPE>
-__global__ void __launch_bounds__(256)
-k_combine32_wide(float4 *__restrict__ out, long ld_out, int nout, const float4 *__restrict__ in, long ld_in,
-                 int nin, const double *__restrict__ coef, int ld_coef, long n) {
-    extern __shared__ float wcs[];   // [nin][nout]
-    for (int t = threadIdx.x; t < nin * nout; t += blockDim.x)
-        wcs[t] = (float)coef[(size_t)(t / nout) * ld_coef + (t % nout)];
-    __syncthreads();
-    const int part = threadIdx.x % TPE;
-    const int l0 = part * NH;
-    const long stride = (long)gridDim.x * (blockDim.x / TPE);
-    for (long e = (long)blockIdx.x * (blockDim.x / TPE) + threadIdx.x / TPE; e < n; e += stride) {
-        float4 a[NH];
-#pragma unroll
-        for (int l = 0; l < NH; ++l) a[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int j = 0; j < nin; ++j) {
-            const float4 v = in[(size_t)j * ld_in + e];
-            const float *c = wcs + j * nout + l0;
-#pragma unroll
-            for (int l = 0; l < NH; ++l) {
-                if (l0 + l < nout) {
-                    const float f = c[l];
-                    a[l].x = fmaf(f, v.x, a[l].x); a[l].y = fmaf(f, v.y, a[l].y);
-                    a[l].z = fmaf(f, v.z, a[l].z); a[l].w = fmaf(f, v.w, a[l].w);
-                }
-            }
-        }
-#pragma unroll
-        for (int l = 0; l < NH; ++l)
-            if (l0 + l < nout) out[(size_t)(l0 + l) * ld_out + e] = a[l];
-    }
-}
-
 template <class P>
 inline int combine(Op &op, typename P::E *out, long ld_out, int nout, const typename P::E *in, long ld_in,
                    int nin, const void *dev_coef, int ld_coef, bool real, bool acc) {
-    if constexpr (P::kF32) {
-        if (real && !acc && nout > 16 && nout <= 48 && nin <= 160) {
-            static bool wide_attr = false;
-            if (!wide_attr) {
-                cudaFuncSetAttribute(k_combine32_wide<12, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 48 * 4);
-                wide_attr = true;
-            }
-            const long n = P::nel(op);
-            long blocks = (n + 63) / 64;
-            blocks = blocks < 152L * 12 ? blocks : 152L * 12;
-            k_combine32_wide<12, 4><<<(int)blocks, 256, (size_t)nin * nout * sizeof(float), op.stream>>>(
-                out, ld_out, nout, in, ld_in, nin, (const double *)dev_coef, ld_coef, n);
-            op.prof.launches++;
-            DLZ_CUDA_TRY(cudaGetLastError());
-            return DLZ_OK;
-        }
-    }
     const long n = P::nel(op);
     static bool attr_set = false;
     if (!attr_set) {
