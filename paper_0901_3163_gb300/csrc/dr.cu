@@ -39,14 +39,45 @@ namespace {
 
 struct RestartPlan {
     std::vector<double> y;       // m     : x += V_m y
+    std::vector<double> s, q;    // MinRes-DR: LS residual c - Tbar y, unit vector spanning range(Tbar)^perp
+    double rho = 0.0;            // Lan-DR: the residual is rho v_{m+1}
     std::vector<double> P;       // (m+1) x (k+1): V_{k+1} <- V_{m+1} P
     std::vector<double> Tn, cn;  // new Tbar ((m+1) x m, rows/cols < k+1 filled) and c
     std::vector<double> theta, res;   // kept (harmonic) Ritz values and residuals
 };
 
-// The small FP64 problem of one cycle (host).  T: (m+1) x m row-major Tbar_m.
-int plan_restart(bool harmonic, int m, int k, const std::vector<double> &T, const std::vector<double> &c,
-                 double &Anorm, RestartPlan &o) {
+// The small FP64 problem of one cycle (host), in two parts so that the GPU can
+// update x and compute the true residual while the host does the eigenproblem.
+// T: (m+1) x m row-major Tbar_m.
+// Part 1: the linear-system coefficients y (Lan-DR: Galerkin T_m y = c; MinRes-DR:
+// least squares min ||c - Tbar y||, with s = c - Tbar y and q spanning range(Tbar)^perp).
+int plan_solve(bool harmonic, int m, const std::vector<double> &T, const std::vector<double> &c, RestartPlan &o) {
+    o.y.assign(m, 0.0);
+    const double bm = T[(size_t)m * m + m - 1];
+    if (!harmonic) {
+        std::vector<double> LU((size_t)m * m);
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) LU[(size_t)i * m + j] = T[(size_t)i * m + j];
+        std::vector<int> piv(m);
+        std::copy(c.begin(), c.begin() + m, o.y.begin());
+        if (!lu_factor(m, LU.data(), piv.data())) return fail(DLZ_ERR_BREAKDOWN, "T_m singular");
+        lu_solve(m, LU.data(), piv.data(), o.y.data());
+        o.rho = -bm * o.y[m - 1];
+        return DLZ_OK;
+    }
+    o.q.assign(m + 1, 0.0);
+    o.s.assign(m + 1, 0.0);
+    if (!lstsq(m + 1, m, T.data(), c.data(), o.y.data(), o.q.data())) return fail(DLZ_ERR_BREAKDOWN, "least squares failed");
+    for (int i = 0; i <= m; ++i) {
+        double t = c[i];
+        for (int j = 0; j < m; ++j) t -= T[(size_t)i * m + j] * o.y[j];
+        o.s[i] = t;
+    }
+    return DLZ_OK;
+}
+
+// Part 2: (harmonic) Ritz pairs, the restart matrix P and the new Tbar and c.
+int plan_finish(bool harmonic, int m, int k, const std::vector<double> &T, double &Anorm, RestartPlan &o) {
     std::vector<double> Tm((size_t)m * m);
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < m; ++j) Tm[(size_t)i * m + j] = T[(size_t)i * m + j];
@@ -56,7 +87,6 @@ int plan_restart(bool harmonic, int m, int k, const std::vector<double> &T, cons
     if (!sym_eig(m, Tm.data(), ev.data(), harmonic ? nullptr : G.data()))
         return fail(DLZ_ERR_NONFINITE, "eig(T_m) failed");
     Anorm = std::max(Anorm, std::max(std::fabs(ev[0]), std::fabs(ev[m - 1])));
-    o.y.assign(m, 0.0);
     o.P.assign((size_t)(m + 1) * (k + 1), 0.0);
     o.Tn.assign((size_t)(m + 1) * m, 0.0);
     o.cn.assign(m + 1, 0.0);
@@ -64,13 +94,6 @@ int plan_restart(bool harmonic, int m, int k, const std::vector<double> &T, cons
     o.res.assign(k, 0.0);
     const double bm = T[(size_t)m * m + m - 1];
     if (!harmonic) {
-        // Galerkin T_m y = c; residual rho v_{m+1}, rho = -beta_m y_m
-        std::vector<double> LU = Tm;
-        std::vector<int> piv(m);
-        std::copy(c.begin(), c.begin() + m, o.y.begin());
-        if (!lu_factor(m, LU.data(), piv.data())) return fail(DLZ_ERR_BREAKDOWN, "T_m singular");
-        lu_solve(m, LU.data(), piv.data(), o.y.data());
-        const double rho = -bm * o.y[m - 1];
         for (int l = 0; l < k; ++l) {           // k algebraically smallest Ritz values
             o.theta[l] = ev[l];
             for (int i = 0; i < m; ++i) o.P[(size_t)i * (k + 1) + l] = G[(size_t)i * m + l];
@@ -79,17 +102,10 @@ int plan_restart(bool harmonic, int m, int k, const std::vector<double> &T, cons
         o.P[(size_t)m * (k + 1) + k] = 1.0;
         for (int l = 0; l < k; ++l) o.Tn[(size_t)l * m + l] = o.theta[l];
         for (int l = 0; l < k; ++l) o.Tn[(size_t)k * m + l] = bm * G[(size_t)(m - 1) * m + l];
-        o.cn[k] = rho;
+        o.cn[k] = o.rho;
         return DLZ_OK;
     }
-    // least squares min ||c - Tbar y||; s = c - Tbar y; q spans range(Tbar)^perp
-    std::vector<double> q(m + 1), s(m + 1);
-    if (!lstsq(m + 1, m, T.data(), c.data(), o.y.data(), q.data())) return fail(DLZ_ERR_BREAKDOWN, "least squares failed");
-    for (int i = 0; i <= m; ++i) {
-        double t = c[i];
-        for (int j = 0; j < m; ++j) t -= T[(size_t)i * m + j] * o.y[j];
-        s[i] = t;
-    }
+    std::vector<double> &q = o.q, &s = o.s;
     // harmonic Ritz pairs: T_m g = mu (Tbar^T Tbar) g, theta = 1/mu, via the Cholesky
     // factor L of Tbar^T Tbar: C = L^-1 T_m L^-T, g = L^-T z
     std::vector<double> M((size_t)m * m, 0.0), L((size_t)m * m), X((size_t)m * m), C((size_t)m * m), col(m);
@@ -410,7 +426,7 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
     DLZ_TRY(sscal.alloc((size_t)(3 * m + 4) * sizeof(S)));
     S *s_alpha = sscal.as<S>(), *s_beta = s_alpha + m, *s_invbeta = s_beta + m, *s_nrm = s_invbeta + m;
     HostScratch hs;
-    DLZ_TRY(hs.ensure(2 * m + 8));
+    DLZ_TRY(hs.ensure(3 * m + 8));
 
     DLZ_TRY(v64::copy(op, bb.as<double2>(), b_in));
     // right-hand side of the hermitian system: gamma5 b (Q) or D^dag b (D^dag D), in FP64
@@ -564,16 +580,19 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
                 return fail(DLZ_ERR_BREAKDOWN, "Lanczos breakdown (invariant subspace)");
         const auto tc1 = now();
         RestartPlan pl;
-        DLZ_TRY(plan_restart(harmonic, m, k, T, c, Anorm, pl));
-        const auto tc2 = now();
-        // FP32 basis: Ritz residuals below ~1e-5 ||A|| are under its rounding level
-        const double tol_eig = p.tol_eig > 0 ? p.tol_eig : (P::kF32 ? 1e-5 : 1e-10) * Anorm;
-        // ---------------- x += V_m y ; true residual ||b - D x|| / ||b|| in FP64
-        DLZ_TRY(h2d(op, coefr, pl.y.data(), m * sizeof(double)));
+        DLZ_TRY(plan_solve(harmonic, m, T, c, pl));
+        // ---------------- x += V_m y ; true residual ||b - D x|| / ||b|| in FP64 (on the
+        // GPU while the host solves the eigenproblem)
+        std::memcpy(hs.p + 2 * m, pl.y.data(), m * sizeof(double));     // pinned staging
+        DLZ_TRY(h2d(op, coefr, hs.p + 2 * m, m * sizeof(double)));
         DLZ_TRY(accum_x<P>(op, x.as<double2>(), V, n, m, coefr));
         DLZ_TRY(wilson64(op, Dx.as<double2>(), x.as<double2>(), DLZ_D));
         st.mvps += 1;
         DLZ_TRY(v64::norm2_diff(op, bb.as<double2>(), Dx.as<double2>(), d_norm + 2));
+        DLZ_TRY(plan_finish(harmonic, m, k, T, Anorm, pl));
+        const auto tc2 = now();
+        // FP32 basis: Ritz residuals below ~1e-5 ||A|| are under its rounding level
+        const double tol_eig = p.tol_eig > 0 ? p.tol_eig : (P::kF32 ? 1e-5 : 1e-10) * Anorm;
         // ---------------- restart: V_{k+1} <- V_{m+1} P
         if constexpr (P::kF32) DLZ_TRY(restart_gemm32(op, Vn, V, n, m + 1, k + 1, pl.P.data(), gcoef.p));
         else DLZ_TRY(restart_gemm64(op, Vn, V, n, m + 1, k + 1, pl.P.data(), gcoef.p));
