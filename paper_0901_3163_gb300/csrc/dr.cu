@@ -31,6 +31,7 @@
 #include "reduce.cuh"
 #include "small_dense.h"
 #include "solvers.h"
+#include "minres_state.cuh"
 #include "wilson_site.cuh"
 
 namespace dlz {
@@ -264,14 +265,16 @@ template <> int basis_to64<P32>(Op &op, double2 *dst, const float4 *src, int k) 
 //      or Q u_j (A = D^dag D = Q Q), so the normalisation of the previous step is folded
 //      into this one instead of costing a pass of its own.
 // K2aL: u_{j+1} = w - alpha_j v_j and the block partial of ||u_{j+1}||^2.
-// K1b/K2b: the partials summed in a fixed order, scalars written (FP64 and FP32).
+// The last block of each kernel to finish sums the partials in a fixed order and writes
+// the scalar (FP64 and FP32); the block counter sits after the partials and resets itself.
 constexpr int kLz = 128;
 
 __global__ void __launch_bounds__(kLz)
 k_lanczos_k1(const float4 *__restrict__ in, const float *__restrict__ sin_, const float4 *__restrict__ U,
              const float4 *__restrict__ Vp, const float *__restrict__ bprev, float4 *__restrict__ Vj,
              float4 *__restrict__ W, const float4 *__restrict__ links, Geom g, float kappa,
-             double *__restrict__ partials) {
+             double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ d_a,
+             float *__restrict__ s_a) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     float facc = 0.f;
     if (s < g.V) {
@@ -294,23 +297,18 @@ k_lanczos_k1(const float4 *__restrict__ in, const float *__restrict__ sin_, cons
             facc += (vj.x * w.x + vj.y * w.y) + (vj.z * w.z + vj.w * w.w);
         }
     }
-    double acc = (double)facc;
-    __shared__ double sm[kLz / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < kLz / 32; ++w) t += sm[w];
-        partials[blockIdx.x] = t;
+    // the last block to finish forms alpha_j (FP64 and FP32 copies)
+    double a;
+    if (partial_then_last_sum<kLz>(facc, partials, blockIdx.x, gridDim.x, counter, &a) && threadIdx.x == 0) {
+        *d_a = a;
+        *s_a = (float)a;
     }
 }
 
 __global__ void __launch_bounds__(kLz)
 k_lanczos_k2a(float4 *__restrict__ W, const float4 *__restrict__ Vj, const float *__restrict__ salpha, Geom g,
-              double *__restrict__ partials) {
+              double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ d_b,
+              float *__restrict__ s_b, float *__restrict__ s_ib) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     float facc = 0.f;
     if (s < g.V) {
@@ -329,40 +327,13 @@ k_lanczos_k2a(float4 *__restrict__ W, const float4 *__restrict__ Vj, const float
             facc += (t.x * t.x + t.y * t.y) + (t.z * t.z + t.w * t.w);
         }
     }
-    double acc = (double)facc;
-    __shared__ double sm[kLz / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < kLz / 32; ++w) t += sm[w];
-        partials[blockIdx.x] = t;
-    }
-}
-
-// sum of nb partials (fixed order); kind 0: alpha_j, kind 1: beta_j = sqrt(sum)
-__global__ void __launch_bounds__(256)
-k_lanczos_fin(const double *__restrict__ partials, int nb, int kind, double *__restrict__ d_out,
-              float *__restrict__ s_out, float *__restrict__ s_inv) {
-    double t = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += partials[b];
-    __shared__ double sm[8];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0;
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) a += sm[w];
-        if (kind == 1) {
-            a = sqrt(a);
-            *s_inv = (float)(1.0 / a);
-        }
-        *d_out = a;
-        *s_out = (float)a;
+    // the last block to finish forms beta_{j+1} = ||u_{j+1}|| (and 1/beta in FP32)
+    double r2;
+    if (partial_then_last_sum<kLz>(facc, partials, blockIdx.x, gridDim.x, counter, &r2) && threadIdx.x == 0) {
+        const double b = sqrt(r2);
+        *d_b = b;
+        *s_b = (float)b;
+        *s_ib = (float)(1.0 / b);
     }
 }
 
@@ -378,13 +349,12 @@ int lanczos_fused_step(Op &op, bool ddagd, const float4 *u, const float *s_ib_pr
         in = tmp;
     }
     op.prof.stencil_start(op.stream, true, g.V, 1, 96);
+    unsigned *counter = reinterpret_cast<unsigned *>(partials + 2 * blocks);
     k_lanczos_k1<<<blocks, kLz, 0, op.stream>>>(in, s_ib_prev, u, vp, s_b_prev, vj, w_out, op.gauge32.as<float4>(),
-                                                g, (float)op.kappa, partials);
+                                                g, (float)op.kappa, partials, counter, d_a, s_a);
     op.prof.stencil_stop(op.stream);
-    k_lanczos_fin<<<1, 256, 0, op.stream>>>(partials, (int)blocks, 0, d_a, s_a, nullptr);
-    k_lanczos_k2a<<<blocks, kLz, 0, op.stream>>>(w_out, vj, s_a, g, partials + blocks);
-    k_lanczos_fin<<<1, 256, 0, op.stream>>>(partials + blocks, (int)blocks, 1, d_b, s_b, s_ib);
-    op.prof.launches += 4;
+    k_lanczos_k2a<<<blocks, kLz, 0, op.stream>>>(w_out, vj, s_a, g, partials + blocks, counter, d_b, s_b, s_ib);
+    op.prof.launches += 2;
     DLZ_CUDA_TRY(cudaGetLastError());
     return DLZ_OK;
 }
@@ -409,7 +379,8 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
     if (P::kF32) {
         DLZ_TRY(reserve_multidot(op, k));
         DLZ_TRY(w2.alloc(n * sizeof(E)));
-        DLZ_TRY(fpart.alloc((size_t)2 * ((op.g.V + 127) / 128 + 1) * sizeof(double)));
+        DLZ_TRY(fpart.alloc((size_t)2 * ((op.g.V + 127) / 128 + 1) * sizeof(double) + 64));
+        DLZ_CUDA_TRY(cudaMemsetAsync(fpart.p, 0, fpart.bytes, op.stream));
     }
     DLZ_TRY(bb.alloc(n64 * sizeof(double2)));
     DLZ_TRY(bp.alloc(n64 * sizeof(double2)));

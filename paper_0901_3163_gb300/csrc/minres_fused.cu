@@ -1,7 +1,7 @@
 // Fused FP32 MinRes iteration for a batch of right-hand sides (the inner
 // solve of the mixed-precision D-MinRes, arXiv:0901.3163 Sec. 2).
 //
-// Four launches per iteration, two of them full passes over the vectors:
+// Two full passes over the vectors per iteration:
 //   K1 (stencil + epilogue, one block = 128 sites of one right-hand side):
 //        v_j   = u_j / beta_j                      (u_j: unnormalised Lanczos vector; the
 //                                                   v's are never stored, only the u's)
@@ -10,12 +10,12 @@
 //        d_{j-1} = (v_{j-1} - delta d_{j-2} - eps d_{j-3}) / gamma,  e += tau d_{j-1}
 //        (the direction update of the previous step: its Givens rotation needed
 //         beta_j, known only now)
-//   K1b: alpha_j = sum of K1's block partials (one block per right-hand side);
 //   K2a: u_{j+1} = w - alpha_j v_j and the block partials of ||u_{j+1}||^2;
-//   K2b: beta_{j+1}, and the Givens rotation of step j (one block per right-hand side).
-// The block partials of K1 and K2a (block b belongs to right-hand side b mod N)
-// are summed in a fixed order by one-block-per-RHS kernels, so results are
-// deterministic.  Buffers rotate with periods 3 and 2, so a group of 6 iterations is
+//   K1b: alpha_j = sum of K1's block partials (one block per right-hand side);
+//   K2b: beta_{j+1}, and the Givens rotation of step j (one block per right-hand side);
+// for a single right-hand side K1b and K2b are folded into the last block of K1 and
+// K2a to finish.  The partials (block b belongs to right-hand side b mod N) are summed
+// in a fixed order, so results are deterministic.  Buffers rotate with periods 3 and 2, so a group of 6 iterations is
 // captured once as a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kThreads)
 k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Up, float4 *__restrict__ W,
             const float4 *__restrict__ D2, float4 *__restrict__ D3, float4 *__restrict__ E,
             const float4 *__restrict__ links, Geom g, float kappa, int N,
-            FusedState *__restrict__ st, double *__restrict__ partials) {
+            FusedState *__restrict__ st, double *__restrict__ partials, unsigned *__restrict__ counters) {
     const int q = blockIdx.x % N;
     const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
     const long nel = 6L * g.V;
@@ -53,18 +53,43 @@ k_minres_k1(const float4 *__restrict__ Ub, const float4 *__restrict__ Up, float4
         facc = minres_k1_site(s, g, kappa, Ub + base, Up + base, W + base, D2 + base, D3 + base, E + base,
                               links, st[q]);
     }
-    // block partial of alpha_q (FP64 across threads), stored contiguously per right-hand side
-    double acc = (double)facc;
-    __shared__ double sm[kThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) t += sm[w];
-        partials[(size_t)q * (gridDim.x / N) + blockIdx.x / N] = t;
+    // block partials of alpha_q; with counters, the last block of q to finish forms
+    // alpha_q (one right-hand side: saves a launch); without, k_minres_alpha does
+    const int nbq = gridDim.x / N;
+    if (!counters) {
+        block_partial_store<kThreads>(facc, partials + (size_t)q * nbq + blockIdx.x / N);
+        return;
+    }
+    double a;
+    if (partial_then_last_sum<kThreads>(facc, partials + (size_t)q * nbq, blockIdx.x / N, nbq, counters + q, &a) &&
+        threadIdx.x == 0)
+        fused_alpha(st[q], a);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_minres_k2a(float4 *__restrict__ W, const float4 *__restrict__ Vc, Geom g, int N,
+             FusedState *__restrict__ st, double *__restrict__ partials, unsigned *__restrict__ counters) {
+    // Vc: the unnormalised u_j; alpha_j v_j = (alpha_j / beta_j) u_j
+    const int q = blockIdx.x % N;
+    const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
+    const size_t base = (size_t)q * 6 * g.V;
+    float facc = 0.f;
+    if (s < g.V) {
+        facc = minres_k2a_site(s, g.V, W + base, Vc + base, st[q]);
+    }
+    // the last block of q to finish: beta_{j+1} and the Givens rotation of step j
+    // (with counters; without, k_minres_k2b does it)
+    const int nbq = gridDim.x / N;
+    if (!counters) {
+        block_partial_store<kThreads>(facc, partials + (size_t)q * nbq + blockIdx.x / N);
+        return;
+    }
+    double r2;
+    if (partial_then_last_sum<kThreads>(facc, partials + (size_t)q * nbq, blockIdx.x / N, nbq, counters + q, &r2) &&
+        threadIdx.x == 0) {
+        FusedState t = st[q];
+        fused_givens(t, r2);
+        st[q] = t;
     }
 }
 
@@ -84,34 +109,6 @@ k_minres_alpha(const double *__restrict__ partials, int nbq, FusedState *__restr
         double a = 0.0;
         for (int w = 0; w < (int)(blockDim.x / 32); ++w) a += sm[w];
         fused_alpha(st[q], a);
-    }
-}
-
-// K2a: u_{j+1} = w - alpha_j v_j (written over w) and the block partial of ||u_{j+1}||^2;
-// one block = 128 sites of one right-hand side, all 6 planes of a site loaded before
-// any store so the loads overlap.
-__global__ void __launch_bounds__(kThreads)
-k_minres_k2a(float4 *__restrict__ W, const float4 *__restrict__ Vc, Geom g, int N,
-             const FusedState *__restrict__ st, double *__restrict__ partials) {
-    // Vc: the unnormalised u_j; alpha_j v_j = (alpha_j / beta_j) u_j
-    const int q = blockIdx.x % N;
-    const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
-    const size_t base = (size_t)q * 6 * g.V;
-    float facc = 0.f;
-    if (s < g.V) {
-        facc = minres_k2a_site(s, g.V, W + base, Vc + base, st[q]);
-    }
-    double acc = (double)facc;
-    __shared__ double sm[kThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) t += sm[w];
-        partials[(size_t)q * (gridDim.x / N) + blockIdx.x / N] = t;
     }
 }
 
@@ -164,19 +161,26 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
     const float4 *links = op.gauge32.as<float4>();
     const unsigned blocks = (unsigned)(((g.V + kThreads - 1) / kThreads) * N);
     double *partials2 = partials + blocks;    // K2a's partials after K1's
+    DevBuf cnt;                               // per-RHS block counters (reset by their last block)
+    DLZ_TRY(cnt.alloc((size_t)N * sizeof(unsigned)));
+    DLZ_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, (size_t)N * sizeof(unsigned), op.stream));
+    unsigned *counters = cnt.as<unsigned>();
     auto iteration = [&](float4 *U, float4 *Up, float4 *W, float4 *D2, float4 *D3) -> int {
         // K1 moves 192 reals per site and right-hand side: u_j, u_{j-1}, d_{j-2}, d_{j-3}, e
         // read; w, d_{j-1}, e written (24 each), plus the links once per site
         op.prof.stencil_start(op.stream, true, g.V, N, 192);
-        k_minres_k1<<<blocks, kThreads, 0, op.stream>>>(U, Up, W, D2, D3, e, links, g, kappa, N, ms, partials);
+        // one right-hand side: the sums are taken by the kernels' last blocks (latency);
+        // several: by one-block-per-RHS kernels (cheaper than a tail in every block)
+        unsigned *cn = N == 1 ? counters : nullptr;
+        k_minres_k1<<<blocks, kThreads, 0, op.stream>>>(U, Up, W, D2, D3, e, links, g, kappa, N, ms, partials, cn);
         op.prof.stencil_stop(op.stream);
-        k_minres_alpha<<<N, 256, 0, op.stream>>>(partials, (int)(blocks / N), ms);
-        op.prof.launches += 2;
+        if (!cn) k_minres_alpha<<<N, 256, 0, op.stream>>>(partials, (int)(blocks / N), ms);
+        op.prof.launches += cn ? 1 : 2;
         DLZ_CUDA_TRY(cudaGetLastError());
         // u_{j+1} = w - alpha v_j ; beta_{j+1} ; Givens rotation of step j
-        k_minres_k2a<<<blocks, kThreads, 0, op.stream>>>(W, U, g, N, ms, partials2);
-        k_minres_k2b<<<N, 256, 0, op.stream>>>(partials2, (int)(blocks / N), ms);
-        op.prof.launches += 2;
+        k_minres_k2a<<<blocks, kThreads, 0, op.stream>>>(W, U, g, N, ms, partials2, cn);
+        if (!cn) k_minres_k2b<<<N, 256, 0, op.stream>>>(partials2, (int)(blocks / N), ms);
+        op.prof.launches += cn ? 1 : 2;
         DLZ_CUDA_TRY(cudaGetLastError());
         return DLZ_OK;
     };

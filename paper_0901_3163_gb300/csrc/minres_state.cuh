@@ -136,4 +136,65 @@ __device__ inline void minres_last_direction(float4 uj, float4 a, float4 b, floa
     ev.z = fmaf(ta, dn.z, ev.z); ev.w = fmaf(ta, dn.w, ev.w);
 }
 
+// Block sum (FP64 over the threads) of facc stored at *out by thread 0.
+template <int BT>
+__device__ inline void block_partial_store(float facc, double *__restrict__ out) {
+    __shared__ double sm[BT / 32];
+    double acc = (double)facc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < BT / 32; ++w) t += sm[w];
+        *out = t;
+    }
+}
+
+// Block partials with the sum taken by the last block to finish.  Each block of
+// right-hand side q stores its partial (FP64 over its threads) at slot[b], then
+// counts itself in counter[q]; the block that brings the count to nbq adds all nbq
+// partials of q in a fixed order and resets the counter (so the sum is deterministic
+// and needs no second launch).  Returns true, with the sum in *total (thread 0), in
+// that block only.  BT: threads per block.
+template <int BT>
+__device__ inline bool partial_then_last_sum(float facc, double *__restrict__ slot0, int b, int nbq,
+                                             unsigned *__restrict__ counter, double *total) {
+    __shared__ double sm[BT / 32];
+    __shared__ bool last;
+    double acc = (double)facc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < BT / 32; ++w) t += sm[w];
+        slot0[b] = t;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == (unsigned)nbq - 1u);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nbq; i += BT) t += __ldcg(&slot0[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+#pragma unroll
+        for (int w = 0; w < BT / 32; ++w) a += sm[w];
+        *total = a;
+        *counter = 0u;
+    }
+    return true;
+}
+
 }  // namespace dlz
