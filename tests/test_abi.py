@@ -85,3 +85,29 @@ def test_argument_validation_without_gpu():
     assert m.lib.dlz_apply(None, 0, None, None, 0, 1) == m.ERR_BADARG
     assert m.lib.dlz_defl_count(None, None, None) == m.ERR_BADARG
     assert "null" in m.last_error()
+
+
+def test_argument_validation_of_batch_network_and_noalloc_entries_without_gpu():
+    """The multi-lattice, network, seed and no-allocation entry points reject null or
+    out-of-range arguments before touching a GPU."""
+    m = dlz()
+    out = ctypes.c_void_p()
+    p = m.params_default()
+    z = (ctypes.c_int * 1)(0)
+    assert m.lib.dlz_batch_dminres(0, None, None, None, None, z, ctypes.byref(p), None) == m.ERR_BADARG
+    ops = (ctypes.c_void_p * 1)(None)
+    ptrs = (ctypes.c_void_p * 1)(None)
+    one = (ctypes.c_int * 1)(1)
+    assert m.lib.dlz_batch_dminres(1, ops, None, ptrs, ptrs, one, ctypes.byref(p), None) == m.ERR_BADARG
+    widths = (ctypes.c_int * 4)(1, 12, 16, 1)
+    assert m.lib.dlz_net_create(None, 3, widths, None, ctypes.byref(out)) == m.ERR_BADARG
+    assert m.lib.dlz_net_forward(None, None, 1, None) == m.ERR_BADARG
+    assert m.lib.dlz_net_backward(None, None, 1, None) == m.ERR_BADARG
+    assert m.lib.dlz_net_adam_step(None, 1e-3, 0.9, 0.999, 1e-8) == m.ERR_BADARG
+    assert m.lib.dlz_net_bind(None, None) == m.ERR_BADARG
+    assert m.lib.dlz_subspace_loss(None, None, 1, None, None) == m.ERR_BADARG
+    assert m.lib.dlz_seed_deflation(None, m.DDAGD, None, m.F64, 4, ctypes.byref(out)) == m.ERR_BADARG
+    assert m.lib.dlz_apply_noalloc(None, 0, None, None, m.F64, 1) == m.ERR_BADARG
+    bad_params = m.params_default()
+    bad_params.finish = 2
+    assert m.lib.dlz_batch_dminres(1, ops, None, ptrs, ptrs, one, ctypes.byref(bad_params), None) == m.ERR_BADARG
