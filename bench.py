@@ -41,7 +41,7 @@ REF_MVPS_PER_RHS = 8175
 # DRAM bytes (read + write) of one k_minres_k1 launch with 11 right-hand sides on the
 # 16^3x32 lattice, from one ncu capture of the current kernel
 # (ncu --set full -k regex:k_minres_k1 -s 24 -c 1 python bench.py --ncu-case)
-K1_TRAFFIC_BYTES = 747729664 + 376182784
+K1_TRAFFIC_BYTES = 745467648 + 376429824
 METRIC = "RHS solved/s to |r|/|b|<1e-10 (MinRes-DR(100,40) + D-MinRes, 12 point sources, 16^3x32)"
 UNIT = "RHS/s"
 

@@ -161,13 +161,11 @@ struct Op {
     void *blas = nullptr;   // cuBLAS handle for the restart GEMM (created on first use, outside graphs)
 };
 
-// V_new = V P for the Rayleigh-Ritz restart as one cuBLAS GEMM (a plain dense
-// product: (reals per vector) x (m+1) times (m+1) x (k+1), real coefficients P
-// row-major on the host).  FP32 (SGEMM, no TF32) or FP64 (DGEMM).
+// V_new = V P for the Rayleigh-Ritz restart of an FP32 basis as one cuBLAS SGEMM
+// (a plain dense product: (reals per vector) x (m+1) times (m+1) x (k+1), real
+// coefficients P row-major on the host; FP32 arithmetic, no TF32).
 // dev_scratch: >= nin * nout doubles on the device, alive until the GEMM has run.
 int restart_gemm32(Op &op, float4 *out, const float4 *in, long n, int nin, int nout, const double *P_host,
-                   void *dev_scratch);
-int restart_gemm64(Op &op, double2 *out, const double2 *in, long n, int nin, int nout, const double *P_host,
                    void *dev_scratch);
 void blas_destroy(Op &op);
 

@@ -565,8 +565,16 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         // FP32 basis: Ritz residuals below ~1e-5 ||A|| are under its rounding level
         const double tol_eig = p.tol_eig > 0 ? p.tol_eig : (P::kF32 ? 1e-5 : 1e-10) * Anorm;
         // ---------------- restart: V_{k+1} <- V_{m+1} P
-        if constexpr (P::kF32) DLZ_TRY(restart_gemm32(op, Vn, V, n, m + 1, k + 1, pl.P.data(), gcoef.p));
-        else DLZ_TRY(restart_gemm64(op, Vn, V, n, m + 1, k + 1, pl.P.data(), gcoef.p));
+        // FP32: one cuBLAS SGEMM (HBM-bound; on 16^3x32 the restart-and-residual time of
+        // 150 cycles fell from 0.45 s with three 16-output combine passes to 0.24 s);
+        // FP64: the combine kernel (FP64-ALU-bound either way; the plain-form step took
+        // 39.1 s with DGEMM against 36.8 s with it)
+        if constexpr (P::kF32) {
+            DLZ_TRY(restart_gemm32(op, Vn, V, n, m + 1, k + 1, pl.P.data(), gcoef.p));
+        } else {
+            DLZ_TRY(h2d(op, gcoef.p, pl.P.data(), pl.P.size() * sizeof(double)));
+            DLZ_TRY(combine<P>(op, Vn, n, k + 1, V, n, m + 1, gcoef.p, k + 1, true, false));
+        }
         if (rperiod > 0) {
             // the vector carried across the restart joins the periodic re-orthogonalisation
             E *vk = Vn + (size_t)k * n;

@@ -1,4 +1,4 @@
-// Restart GEMM through cuBLAS (a plain dense product, V_new = V P).
+// Restart GEMM through cuBLAS (a plain dense product, V_new = V P), FP32 basis.
 #include <cublas_v2.h>
 
 #include <vector>
@@ -39,21 +39,6 @@ int restart_gemm32(Op &op, float4 *out, const float4 *in, long n, int nin, int n
     if (cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, rows, nout, nin, &one, (const float *)in, rows, d, nout,
                     &zero, (float *)out, rows) != CUBLAS_STATUS_SUCCESS)
         return fail(DLZ_ERR_CUDA, "cublasSgemm failed");
-    op.prof.launches++;
-    return DLZ_OK;
-}
-
-int restart_gemm64(Op &op, double2 *out, const double2 *in, long n, int nin, int nout, const double *P_host,
-                   void *dev_scratch) {
-    cublasHandle_t h;
-    DLZ_TRY(handle(op, h));
-    double *d = (double *)dev_scratch;
-    DLZ_CUDA_TRY(cudaMemcpyAsync(d, P_host, (size_t)nin * nout * sizeof(double), cudaMemcpyHostToDevice, op.stream));
-    const int rows = (int)(2 * n);
-    const double one = 1.0, zero = 0.0;
-    if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, rows, nout, nin, &one, (const double *)in, rows, d, nout,
-                    &zero, (double *)out, rows) != CUBLAS_STATUS_SUCCESS)
-        return fail(DLZ_ERR_CUDA, "cublasDgemm failed");
     op.prof.launches++;
     return DLZ_OK;
 }
