@@ -385,7 +385,11 @@ def run_reference(args):
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "form": "oracle"},
+           "data": "synthetic (seeded SU(3) links exp(0.3iH), point sources)",
+           "config": {"workload": WORKLOAD, "lattice": list(dims), "kappa": kappa, "m": w["m"], "k": w["k"],
+                      "rhs": 12, "form": "oracle (FP64 CPU)", "tol": 1e-10,
+                      "first_rhs": f"{DR_CYCLES} MinRes-DR cycles, then D-MinRes from x",
+                      "parallelism": "rank 0 only"},
            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": int(threads),
                             "kind": "oracle",
                             "sample": (f"per step one MinRes-DR(100,40) cycle ({mv // args.steps} MVPs); "
