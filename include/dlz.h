@@ -90,8 +90,11 @@ typedef struct {
                             vectors need it); 0 turns it off; 10                          */
     int precision;       /* DLZ_F64 or DLZ_F32 (hot loop of D-CG / D-MinRes); DLZ_F64     */
     double reliable_delta; /* DLZ_F32: each FP32 inner solve reduces the residual by
-                              this factor, then x is updated and the residual recomputed
-                              in FP64 (defect correction); 1e-5                          */
+                              this factor, then x is updated, the residual recomputed
+                              in FP64 and projected over the deflation set again (defect
+                              correction); 1e-2 (on the 16^3x32 workload 6444 D-MinRes
+                              iterations against 9540 with 1e-5: the re-projection
+                              removes the deflated directions FP32 lets back in)        */
     int check_every;     /* D-CG / D-MinRes: read the residual on the host every this
                             many iterations; 16                                          */
     int profile;         /* 1: time every stencil launch with CUDA events (stats)  ; 0   */

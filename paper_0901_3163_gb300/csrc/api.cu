@@ -295,7 +295,7 @@ int dlz_params_default(dlz_params *p) {
     p->max_iter = 100000;
     p->reorth_period = 10;
     p->precision = DLZ_F64;
-    p->reliable_delta = 1e-5;
+    p->reliable_delta = 1e-2;
     p->check_every = 16;
     p->profile = 0;
     p->finish = 0;

@@ -21,7 +21,7 @@ def test_params_defaults():
     m = dlz()
     p = m.params_default()
     assert (p.m, p.k, p.tol, p.oversolve, p.reorth_period, p.precision) == (40, 10, 1e-10, 1.0, 10, m.F64)
-    assert p.reliable_delta == 1e-5
+    assert p.reliable_delta == 1e-2 and p.finish == 0
 
 
 def test_error_names():
