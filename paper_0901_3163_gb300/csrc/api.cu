@@ -704,12 +704,9 @@ static int dsolve_entry(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nr
         std::memset(&st, 0, sizeof(st));
         CallStats cs(op, nullptr, p->profile != 0, p->precision == DLZ_F32);
         DLZ_TRY(pack64(op, bi.as<double2>(), (const double2 *)sb.dev + (size_t)r * n));
-        int rc;
-        if (p->precision == DLZ_F32)
-            rc = dsolve_mixed(op, d, minres, bi.as<double2>(), xi.as<double2>(), *p, st);
-        else
-            rc = minres ? dminres64(op, d, bi.as<double2>(), xi.as<double2>(), *p, st)
-                        : dcg64(op, d, bi.as<double2>(), xi.as<double2>(), *p, st);
+        // the plain FP64 form, one right-hand side at a time
+        const int rc = minres ? dminres64(op, d, bi.as<double2>(), xi.as<double2>(), *p, st)
+                              : dcg64(op, d, bi.as<double2>(), xi.as<double2>(), *p, st);
         if (rc != DLZ_OK && rc != DLZ_ERR_NOT_CONVERGED) return rc;
         if (rc != DLZ_OK) worst = rc;
         DLZ_TRY(unpack64(op, (double2 *)sx.dev + (size_t)r * n, xi.as<double2>()));

@@ -43,12 +43,9 @@ int dminres64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x, const d
               dlz_stats &st, const double2 *x_init = nullptr);
 int dcg64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x, const dlz_params &p,
           dlz_stats &st, const double2 *x_init = nullptr);
-// D-MinRes (minres) or D-CG in FP32 with FP64 defect correction (DLZ_F32).
-// x_init (may alias x, may be null) is the starting guess.
-int dsolve_mixed(Op &op, const dlz_defl_s *d, bool minres, const double2 *b, double2 *x,
-                 const dlz_params &p, dlz_stats &st, const double2 *x_init = nullptr);
-// D-MinRes in FP32 with FP64 defect correction on N <= 16 right-hand sides at once
-// (B, X: N internal FP64 vectors one after another; st: N entries).
+// D-MinRes (minres) or D-CG in FP32 with FP64 defect correction on N <= 16
+// right-hand sides at once (B, X: N internal FP64 vectors one after another; st: N
+// entries); X_init (may alias X, may be null) is the starting guess.
 int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *B, double2 *X, int N,
                        const dlz_params &p, dlz_stats *st, const double2 *X_init = nullptr);
 // Hk (k x k, may be null): V_k^dag A V_k known from the restart; else computed (k MVPs).

@@ -26,206 +26,17 @@ namespace dlz {
 
 namespace {
 
+// scalar scratch of the inner solvers (sized for either state: FusedState of the
+// fused MinRes or CgFusedState of the fused CGNR)
 struct InnerState {
     double beta, alpha, beta_next, inv_beta;
     double c, s, c_old, s_old, phibar;
     double eps, delta, gamma, tau;
-    double rr, ss, pq;   // CG
-    float fa, fb;        // CG step lengths in FP32 for the element updates
+    double rr, ss, pq;
+    float fa, fb;
 };
 
-__device__ inline float re_dot(float4 a, float4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
-__device__ inline float nrm2(float4 a) { return (a.x * a.x + a.y * a.y) + (a.z * a.z + a.w * a.w); }
-__device__ inline float4 axpy4(float a, float4 x, float4 y) {
-    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
-}
-__device__ inline float4 scale4(float a, float4 x) { return make_float4(a * x.x, a * x.y, a * x.z, a * x.w); }
-
-// r32 = scale * r64 (internal planes: FP32 plane c holds FP64 planes 2c, 2c+1)
-int to32_scaled(Op &op, float4 *dst, const double2 *src, const double *d_scale) {
-    const int V = op.g.V;
-    return map(op, 6L * V, [=] __device__(long i) {
-        const int c = (int)(i / V), s = (int)(i % V);
-        const double sc = *d_scale;
-        const double2 a = src[(size_t)(2 * c) * V + s], b = src[(size_t)(2 * c + 1) * V + s];
-        dst[i] = make_float4((float)(sc * a.x), (float)(sc * a.y), (float)(sc * b.x), (float)(sc * b.y));
-    });
-}
-// x64 += scale * e32
-int add_from32(Op &op, double2 *x, const float4 *e, const double *d_scale) {
-    const int V = op.g.V;
-    return map(op, 6L * V, [=] __device__(long i) {
-        const int c = (int)(i / V), s = (int)(i % V);
-        const double sc = *d_scale;
-        const float4 q = e[i];
-        double2 &a = x[(size_t)(2 * c) * V + s];
-        double2 &b = x[(size_t)(2 * c + 1) * V + s];
-        a.x += sc * q.x; a.y += sc * q.y; b.x += sc * q.z; b.y += sc * q.w;
-    });
-}
-
-// FP32 CG on D^dag D e = D^dag s from e = 0, tracking s - D e, until that falls
-// by tol_rel.  r, pp, t, q: work vectors.
-int cgnr_inner32(Op &op, float4 *s, float4 *e, float4 *r, float4 *pp, float4 *t, float4 *q,
-                 InnerState *cs, double tol_rel, const dlz_params &p, dlz_stats &st, HostScratch &hs) {
-    const long n = 6L * op.g.V;
-    DLZ_TRY(wilson32(op, r, s, DLZ_DDAG));
-    st.mvps += 1;
-    DLZ_TRY(reduce32<2>(op, n, [=] __device__(long i, float (&acc)[2]) {
-        const float4 v = r[i];
-        pp[i] = v;
-        e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        acc[0] += nrm2(v);
-        acc[1] += nrm2(s[i]);
-    }, [=] __device__(const double *res) { cs->rr = res[0]; cs->ss = res[1]; }));
-    DLZ_TRY(d2h_sync(op, hs.p, cs, sizeof(InnerState)));
-    const double s0 = std::sqrt(reinterpret_cast<const InnerState *>(hs.p)->ss);
-    int it = 0;
-    while (st.iterations < p.max_iter) {
-        DLZ_TRY(wilson32(op, t, pp, DLZ_D));
-        DLZ_TRY(wilson32(op, q, t, DLZ_DDAG));
-        st.mvps += 2;
-        DLZ_TRY(reduce32<1>(op, n, [=] __device__(long i, float (&acc)[1]) { acc[0] += re_dot(pp[i], q[i]); },
-                          [=] __device__(const double *res) { cs->pq = res[0]; cs->fa = (float)(cs->rr / res[0]); }));
-        DLZ_TRY(reduce32<2>(op, n, [=] __device__(long i, float (&acc)[2]) {
-            const float al = cs->fa;
-            const float4 pv = pp[i];
-            e[i] = axpy4(al, pv, e[i]);
-            const float4 rv = axpy4(-al, q[i], r[i]);
-            const float4 sv = axpy4(-al, t[i], s[i]);
-            r[i] = rv;
-            s[i] = sv;
-            acc[0] += nrm2(rv);
-            acc[1] += nrm2(sv);
-        }, [=] __device__(const double *res) {
-            cs->beta = res[0] / cs->rr;
-            cs->fb = (float)cs->beta;
-            cs->rr = res[0];
-            cs->ss = res[1];
-        }));
-        DLZ_TRY(map(op, n, [=] __device__(long i) {
-            const float be = cs->fb;
-            pp[i] = axpy4(be, pp[i], r[i]);
-        }));
-        st.iterations++;
-        ++it;
-        if (it % p.check_every == 0 || st.iterations >= p.max_iter) {
-            DLZ_TRY(d2h_sync(op, hs.p, cs, sizeof(InnerState)));
-            const InnerState *h = reinterpret_cast<const InnerState *>(hs.p);
-            if (!std::isfinite(h->ss)) return fail(DLZ_ERR_NONFINITE, "CG residual not finite");
-            if (std::sqrt(h->ss) <= tol_rel * s0 || h->rr == 0.0) break;
-        }
-    }
-    return DLZ_OK;
-}
-
 }  // namespace
-
-int dsolve_mixed(Op &op, const dlz_defl_s *d, bool minres, const double2 *b, double2 *x_out,
-                 const dlz_params &p, dlz_stats &st, const double2 *x_init) {
-    if (minres) return dsolve_mixed_batch(op, d, true, b, x_out, 1, p, &st, x_init);
-    const long n64 = 12L * op.g.V;
-    const long n32 = 6L * op.g.V;
-    DevBuf bp, x, r, tmp, dots, scal, f32;
-    DLZ_TRY(bp.alloc(n64 * sizeof(double2)));
-    DLZ_TRY(x.alloc(n64 * sizeof(double2)));
-    DLZ_TRY(r.alloc(n64 * sizeof(double2)));
-    DLZ_TRY(tmp.alloc(n64 * sizeof(double2)));
-    DLZ_TRY(dots.alloc((size_t)std::max(1, d ? d->k : 1) * sizeof(double2)));
-    DLZ_TRY(scal.alloc(64 * sizeof(double)));
-    DLZ_TRY(f32.alloc((size_t)7 * n32 * sizeof(float4)));
-    float4 *w32[7];
-    for (int i = 0; i < 7; ++i) w32[i] = f32.as<float4>() + (size_t)i * n32;
-    InnerState *ist = reinterpret_cast<InnerState *>(scal.as<double>());
-    double *d_norm = scal.as<double>() + 40;
-    HostScratch hs;
-    DLZ_TRY(hs.ensure(64));
-    // the FP64 system: Q x = gamma5 b (MinRes) or D x = b through D^dag D (CG)
-    if (minres) DLZ_TRY(v64::gamma5(op, bp.as<double2>(), b));
-    else DLZ_TRY(v64::copy(op, bp.as<double2>(), b));
-    DLZ_TRY(v64::norm2_diff(op, bp.as<double2>(), nullptr, d_norm + 1));
-    DLZ_TRY(d2h_sync(op, hs.p, d_norm + 1, sizeof(double)));
-    const double bnorm = std::sqrt(hs.p[0]);
-    if (!std::isfinite(bnorm)) return fail(DLZ_ERR_NONFINITE, "right-hand side is not finite");
-    if (bnorm == 0.0) {
-        DLZ_TRY(v64::zero(op, x_out));
-        st.converged = 1; st.true_residual = 0.0;
-        return DLZ_OK;
-    }
-    const int fwd = minres ? DLZ_Q : DLZ_D;
-    if (x_init) DLZ_TRY(v64::copy(op, x.as<double2>(), x_init));
-    else DLZ_TRY(v64::zero(op, x.as<double2>()));
-    bool converged = false;
-    int outer = 0;
-    while (true) {
-        // r = b' - A x in FP64
-        DLZ_TRY(wilson64(op, tmp.as<double2>(), x.as<double2>(), fwd));
-        st.mvps += 1;
-        {
-            const double2 *bq = bp.as<double2>(), *ax = tmp.as<double2>();
-            double2 *rr = r.as<double2>();
-            DLZ_TRY(reduce<1>(op, n64, [=] __device__(long i, double (&acc)[1]) {
-                const double2 a = bq[i], c = ax[i];
-                const double2 t = make_double2(a.x - c.x, a.y - c.y);
-                rr[i] = t;
-                acc[0] += t.x * t.x + t.y * t.y;
-            }, [=] __device__(const double *res) { *d_norm = sqrt(res[0]); }));
-        }
-        DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
-        const double rn = hs.p[0];
-        st.true_residual = rn / bnorm;
-        if (!std::isfinite(rn)) return fail(DLZ_ERR_NONFINITE, "residual is not finite");
-        if (rn <= p.tol * bnorm) { converged = true; break; }
-        if (st.iterations >= p.max_iter) break;
-        if (d && d->k > 0) {
-            // Galerkin projection of the current residual over the deflation set
-            double2 *corr = tmp.as<double2>();
-            if (minres) {
-                DLZ_TRY(project64(op, d, r.as<double2>(), corr, dots));
-            } else {
-                DLZ_TRY(wilson64(op, x_out, r.as<double2>(), DLZ_DDAG));   // x_out as scratch
-                st.mvps += 1;
-                DLZ_TRY(project64(op, d, x_out, corr, dots));
-            }
-            double2 *xx = x.as<double2>();
-            const double2 *cc = corr;
-            DLZ_TRY(map(op, n64, [=] __device__(long i) {
-                double2 a = xx[i];
-                const double2 c = cc[i];
-                a.x += c.x; a.y += c.y;
-                xx[i] = a;
-            }));
-            // residual after the projection (the first outer pass is the D-solve's own start)
-            DLZ_TRY(wilson64(op, tmp.as<double2>(), x.as<double2>(), fwd));
-            st.mvps += 1;
-            const double2 *bq = bp.as<double2>(), *ax = tmp.as<double2>();
-            double2 *rr = r.as<double2>();
-            DLZ_TRY(reduce<1>(op, n64, [=] __device__(long i, double (&acc)[1]) {
-                const double2 a = bq[i], c = ax[i];
-                const double2 t = make_double2(a.x - c.x, a.y - c.y);
-                rr[i] = t;
-                acc[0] += t.x * t.x + t.y * t.y;
-            }, [=] __device__(const double *res) { *d_norm = sqrt(res[0]); }));
-            DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
-            if (hs.p[0] <= p.tol * bnorm) { st.true_residual = hs.p[0] / bnorm; converged = true; break; }
-        }
-        // FP32 correction of the normalised residual
-        double *inv = d_norm + 2, *scl = d_norm + 3;
-        DLZ_TRY(map(op, 1, [=] __device__(long) { *inv = 1.0 / *d_norm; *scl = *d_norm; }));
-        DLZ_TRY(to32_scaled(op, w32[0], r.as<double2>(), inv));
-        DLZ_TRY(d2h_sync(op, hs.p, d_norm, sizeof(double)));
-        const double rcur = hs.p[0];
-        const double inner_tol = std::max(0.5 * p.tol * bnorm / rcur, p.reliable_delta);
-        DLZ_TRY(cgnr_inner32(op, w32[0], w32[1], w32[2], w32[3], w32[4], w32[5], ist, inner_tol, p, st, hs));
-        DLZ_TRY(add_from32(op, x.as<double2>(), w32[1], scl));
-        ++outer;
-    }
-    DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
-    DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
-    st.cycles = outer;
-    st.converged = converged ? 1 : 0;
-    return converged ? DLZ_OK : DLZ_ERR_NOT_CONVERGED;
-}
 
 }  // namespace dlz
 
