@@ -107,6 +107,21 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(ms, solved, world, device):
+    """Replicas on N ranks: the job's time is the slowest rank's, its work the sum of
+    every rank's solved right-hand sides (host-side reduction of two numbers; the data
+    path has no collective)."""
+    if world <= 1:
+        return float(ms), float(solved)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms), float(solved)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(t[1])
+
+
 def workload_inputs(kappa=None):
     import numpy as np
 
@@ -195,15 +210,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     # one more step with every stencil launch timed by CUDA events (roofline only)
     _, pstats = step(profile=True)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, float(solved)], device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max, solved_all = float(mx[0]), float(t[1])
-    else:
-        ms_max, solved_all = ms, float(solved)
+    ms_max, solved_all = aggregate_ranks(ms, solved, world, dev)
     value = solved_all / (ms_max / 1e3)
     # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
     e2e = None
