@@ -2,14 +2,16 @@
 // applied lattice by lattice): every (lattice, right-hand side) pair is a slot
 // with its own geometry, links, kappa and deflation set, and the fused FP32
 // MinRes kernels of minres_fused.cu run over all slots in one launch per stage.
-// Each launch walks a block table (block -> slot, first site), built on the host
-// with the slots' blocks contiguous, so the per-slot sums of block partials are
-// contiguous ranges read in a fixed order (deterministic).  The FP64 defect
+// Each launch walks a block table (block -> slot, first 128-site chunk), built on
+// the host with each slot's chunks contiguous, so the per-slot sums of chunk
+// partials are contiguous ranges read in a fixed order (deterministic, and the same
+// for every block size).  The FP64 defect
 // correction around it (true residuals, Galerkin projection over each lattice's
 // deflation set, x updates) runs lattice by lattice with that lattice's operator.
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -27,7 +29,7 @@ namespace dlz {
 struct SlotDesc {
     Geom g;
     float kappa;
-    int blk0, nb;                 // first block and number of blocks in the table
+    int blk0, nb;                 // first chunk partial and number of 128-site chunks
     const float4 *links;          // FP32 two-row links of the slot's lattice
     size_t off;                   // float4 offset of the slot's vectors in the arenas
 };
@@ -40,18 +42,25 @@ struct Scales16 {            // per-right-hand-side scale factors captured by va
     double v[16];
 };
 
-__device__ inline void block_partial(float facc, double *__restrict__ out) {
+// Per-chunk partials: a block of TB = B * kMT threads covers B chunks of kMT sites of
+// one slot; each chunk's partial (FP64 over its threads) goes to its own slot in the
+// partials array, so the sums -- and the results -- do not depend on B.
+template <int B>
+__device__ inline void chunk_partials(float facc, double *__restrict__ out, int nvalid) {
     double acc = (double)facc;
-    __shared__ double sm[kMT / 32];
+    __shared__ double sm[B * kMT / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
+    if ((threadIdx.x % kMT) == 0) {
+        const int ch = threadIdx.x / kMT;
+        if (ch < nvalid) {
+            double t = 0.0;
 #pragma unroll
-        for (int w = 0; w < kMT / 32; ++w) t += sm[w];
-        *out = t;
+            for (int w = 0; w < kMT / 32; ++w) t += sm[ch * (kMT / 32) + w];
+            out[ch] = t;
+        }
     }
 }
 
@@ -70,12 +79,14 @@ __device__ inline double slot_sum(const double *__restrict__ partials, int blk0,
     return a;
 }
 
-__global__ void __launch_bounds__(kMT)
+// table entry of a block: (slot, first chunk of the block within the slot)
+template <int B>
+__global__ void __launch_bounds__(B * kMT)
 k_mm_norm(const float4 *__restrict__ R, const SlotDesc *__restrict__ sd, const int2 *__restrict__ table,
           double *__restrict__ partials) {
     const int2 t = table[blockIdx.x];
     const SlotDesc d = sd[t.x];
-    const int s = t.y + threadIdx.x;
+    const int s = t.y * kMT + threadIdx.x;
     float facc = 0.f;
     if (s < d.g.V) {
 #pragma unroll
@@ -84,7 +95,7 @@ k_mm_norm(const float4 *__restrict__ R, const SlotDesc *__restrict__ sd, const i
             facc += (v.x * v.x + v.y * v.y) + (v.z * v.z + v.w * v.w);
         }
     }
-    block_partial(facc, partials + blockIdx.x);
+    chunk_partials<B>(facc, partials + d.blk0 + t.y, d.nb - t.y);
 }
 
 __global__ void __launch_bounds__(256)
@@ -94,23 +105,25 @@ k_mm_init(const double *__restrict__ partials, const SlotDesc *__restrict__ sd, 
     if (threadIdx.x == 0) fused_init(st[blockIdx.x], sqrt(r2));
 }
 
-__global__ void __launch_bounds__(kMT)
+template <int B>
+__global__ void __launch_bounds__(B * kMT)
 k_mm_k1(const float4 *__restrict__ U, const float4 *__restrict__ Up, float4 *__restrict__ W,
         const float4 *__restrict__ D2, float4 *__restrict__ D3, float4 *__restrict__ E,
         const SlotDesc *__restrict__ sd, const int2 *__restrict__ table, const FusedState *__restrict__ st,
         const int *__restrict__ active, double *__restrict__ partials) {
     const int2 t = table[blockIdx.x];
+    const SlotDesc d = sd[t.x];
     if (!active[t.x]) {                 // a finished slot: its blocks do no work (uniform per block)
-        if (threadIdx.x == 0) partials[blockIdx.x] = 0.0;
+        if (threadIdx.x % kMT == 0 && t.y + (int)(threadIdx.x / kMT) < d.nb)
+            partials[d.blk0 + t.y + threadIdx.x / kMT] = 0.0;
         return;
     }
-    const SlotDesc d = sd[t.x];
-    const int s = t.y + threadIdx.x;
+    const int s = t.y * kMT + threadIdx.x;
     float facc = 0.f;
     if (s < d.g.V)
         facc = minres_k1_site(s, d.g, d.kappa, U + d.off, Up + d.off, W + d.off, D2 + d.off, D3 + d.off,
                               E + d.off, d.links, st[t.x]);
-    block_partial(facc, partials + blockIdx.x);
+    chunk_partials<B>(facc, partials + d.blk0 + t.y, d.nb - t.y);
 }
 
 __global__ void __launch_bounds__(256)
@@ -122,20 +135,22 @@ k_mm_alpha(const double *__restrict__ partials, const SlotDesc *__restrict__ sd,
     if (threadIdx.x == 0) fused_alpha(st[blockIdx.x], a);
 }
 
-__global__ void __launch_bounds__(kMT)
+template <int B>
+__global__ void __launch_bounds__(B * kMT)
 k_mm_k2a(float4 *__restrict__ W, const float4 *__restrict__ U, const SlotDesc *__restrict__ sd,
          const int2 *__restrict__ table, const FusedState *__restrict__ st, const int *__restrict__ active,
          double *__restrict__ partials) {
     const int2 t = table[blockIdx.x];
+    const SlotDesc d = sd[t.x];
     if (!active[t.x]) {
-        if (threadIdx.x == 0) partials[blockIdx.x] = 0.0;
+        if (threadIdx.x % kMT == 0 && t.y + (int)(threadIdx.x / kMT) < d.nb)
+            partials[d.blk0 + t.y + threadIdx.x / kMT] = 0.0;
         return;
     }
-    const SlotDesc d = sd[t.x];
-    const int s = t.y + threadIdx.x;
+    const int s = t.y * kMT + threadIdx.x;
     float facc = 0.f;
     if (s < d.g.V) facc = minres_k2a_site(s, d.g.V, W + d.off, U + d.off, st[t.x]);
-    block_partial(facc, partials + blockIdx.x);
+    chunk_partials<B>(facc, partials + d.blk0 + t.y, d.nb - t.y);
 }
 
 __global__ void __launch_bounds__(256)
@@ -151,13 +166,14 @@ k_mm_k2b(const double *__restrict__ partials, const SlotDesc *__restrict__ sd, F
     }
 }
 
-__global__ void __launch_bounds__(kMT)
+template <int B>
+__global__ void __launch_bounds__(B * kMT)
 k_mm_last(const float4 *__restrict__ Uj, const float4 *__restrict__ D2, const float4 *__restrict__ D3,
           float4 *__restrict__ E, const SlotDesc *__restrict__ sd, const int2 *__restrict__ table,
           const FusedState *__restrict__ st) {
     const int2 t = table[blockIdx.x];
     const SlotDesc d = sd[t.x];
-    const int s = t.y + threadIdx.x;
+    const int s = t.y * kMT + threadIdx.x;
     if (s >= d.g.V) return;
     const FusedState q = st[t.x];
 #pragma unroll
@@ -171,18 +187,29 @@ k_mm_last(const float4 *__restrict__ Uj, const float4 *__restrict__ D2, const fl
 
 }  // namespace
 
+// One block-table layout: blocks of B chunks (B * 128 sites) of one slot.
+struct Tile {
+    int B;
+    const int2 *table;
+    int nblocks;
+};
+
 // The fused FP32 MinRes over all slots (r: normalised residuals in the arena; e:
 // corrections, holding the start if e_init).  bufs: 5 arena-sized work vectors.
 // A slot whose inner residual has met its tolerance at a check is frozen: its blocks
 // return at once and its state stops changing (the buffer roles repeat every 6
 // iterations and checks fall on multiples of 6, so the frozen slot's pending
 // direction update is still found where k_mm_last looks for it).
-int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const int2 *table, int nblocks, size_t arena,
+// Tiles: the first three 6-iteration groups capture a graph per tile (128, 256 and
+// 512 threads per block), the next three time one replay each (CUDA events), and the
+// fastest serves the rest (DLZ_MULTI_TILE=1|2|4 forces one).  The partials are per
+// 128-site chunk whatever the tile, so every tile gives bit-identical results.
+int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const Tile *tiles, int nchunks, size_t arena,
                        const float4 *r, float4 *e, float4 *const bufs[5], FusedState *ms, double *partials,
                        int *active, const double *d_tol, const dlz_params &p, int &iters, HostScratch &hs,
                        bool e_init) {
-    double *partials2 = partials + nblocks;
-    k_mm_norm<<<nblocks, kMT, 0, op.stream>>>(r, sd, table, partials);
+    double *partials2 = partials + nchunks;
+    k_mm_norm<1><<<tiles[0].nblocks, kMT, 0, op.stream>>>(r, sd, tiles[0].table, partials);
     k_mm_init<<<NS, 256, 0, op.stream>>>(partials, sd, ms);
     op.prof.launches += 2;
     DLZ_CUDA_TRY(cudaGetLastError());
@@ -190,35 +217,70 @@ int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const int2 *table, in
     DLZ_CUDA_TRY(cudaMemcpyAsync(U0, r, arena * sizeof(float4), cudaMemcpyDeviceToDevice, op.stream));
     for (float4 *z : {Up0, D20, D30}) DLZ_CUDA_TRY(cudaMemsetAsync(z, 0, arena * sizeof(float4), op.stream));
     if (!e_init) DLZ_CUDA_TRY(cudaMemsetAsync(e, 0, arena * sizeof(float4), op.stream));
-    auto iteration = [&](float4 *U, float4 *Up, float4 *W, float4 *D2, float4 *D3) -> int {
-        k_mm_k1<<<nblocks, kMT, 0, op.stream>>>(U, Up, W, D2, D3, e, sd, table, ms, active, partials);
+    auto iteration = [&](const Tile &t, float4 *U, float4 *Up, float4 *W, float4 *D2, float4 *D3) -> int {
+        switch (t.B) {
+        case 1: k_mm_k1<1><<<t.nblocks, kMT, 0, op.stream>>>(U, Up, W, D2, D3, e, sd, t.table, ms, active, partials); break;
+        case 2: k_mm_k1<2><<<t.nblocks, 2 * kMT, 0, op.stream>>>(U, Up, W, D2, D3, e, sd, t.table, ms, active, partials); break;
+        default: k_mm_k1<4><<<t.nblocks, 4 * kMT, 0, op.stream>>>(U, Up, W, D2, D3, e, sd, t.table, ms, active, partials);
+        }
         k_mm_alpha<<<NS, 256, 0, op.stream>>>(partials, sd, ms, active);
-        k_mm_k2a<<<nblocks, kMT, 0, op.stream>>>(W, U, sd, table, ms, active, partials2);
+        switch (t.B) {
+        case 1: k_mm_k2a<1><<<t.nblocks, kMT, 0, op.stream>>>(W, U, sd, t.table, ms, active, partials2); break;
+        case 2: k_mm_k2a<2><<<t.nblocks, 2 * kMT, 0, op.stream>>>(W, U, sd, t.table, ms, active, partials2); break;
+        default: k_mm_k2a<4><<<t.nblocks, 4 * kMT, 0, op.stream>>>(W, U, sd, t.table, ms, active, partials2);
+        }
         k_mm_k2b<<<NS, 256, 0, op.stream>>>(partials2, sd, ms, active);
         op.prof.launches += 4;
         DLZ_CUDA_TRY(cudaGetLastError());
         return DLZ_OK;
     };
-    GraphExec ge;
+    GraphExec ge[3];
+    int cur = 0;
     auto six = [&]() -> int {
         float4 *U = U0, *Up = Up0, *W = W0, *D2 = D20, *D3 = D30;
         for (int sub = 0; sub < 6; ++sub) {
-            DLZ_TRY(iteration(U, Up, W, D2, D3));
+            DLZ_TRY(iteration(tiles[cur], U, Up, W, D2, D3));
             float4 *tUp = Up;
             Up = U; U = W; W = tUp;
             std::swap(D2, D3);
         }
         return DLZ_OK;
     };
+    int forced = -1;
+    if (const char *env = std::getenv("DLZ_MULTI_TILE")) {
+        const int b = std::atoi(env);
+        forced = b == 1 ? 0 : b == 2 ? 1 : b == 4 ? 2 : -1;
+    }
+    float tms[3] = {0.f, 0.f, 0.f};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (forced < 0) {
+        DLZ_CUDA_TRY(cudaEventCreate(&ev0));
+        DLZ_CUDA_TRY(cudaEventCreate(&ev1));
+    }
     const int check = std::max(6, (p.check_every / 6) * 6);
     std::vector<FusedState> h(NS);
     std::vector<double> tol(NS);
     DLZ_TRY(d2h_sync(op, tol.data(), d_tol, NS * sizeof(double)));
     std::vector<int> act(NS, 1);
     DLZ_TRY(h2d(op, active, act.data(), NS * sizeof(int)));
-    int it = 0;
+    int it = 0, group = 0, best = forced >= 0 ? forced : 0;
     while (iters < p.max_iter) {
-        DLZ_TRY(run_graph(op, ge, six));
+        const bool timed = forced < 0 && group >= 3 && group < 6;
+        cur = forced >= 0 ? forced : (group < 6 ? group % 3 : best);
+        if (timed) cudaEventRecord(ev0, op.stream);
+        DLZ_TRY(run_graph(op, ge[cur], six));
+        if (timed) {
+            cudaEventRecord(ev1, op.stream);
+            cudaEventSynchronize(ev1);
+            if (cudaEventElapsedTime(&tms[cur], ev0, ev1) != cudaSuccess) {
+                cudaGetLastError();
+                tms[cur] = 1e30f;
+            }
+            if (group == 5)
+                for (int v = 1; v < 3; ++v)
+                    if (tms[v] < tms[best]) best = v;
+        }
+        ++group;
         iters += 6;
         it += 6;
         if (it % check == 0 || iters >= p.max_iter) {
@@ -234,7 +296,9 @@ int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const int2 *table, in
             if (changed) DLZ_TRY(h2d(op, active, act.data(), NS * sizeof(int)));
         }
     }
-    k_mm_last<<<nblocks, kMT, 0, op.stream>>>(Up0, D20, D30, e, sd, table, ms);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    k_mm_last<1><<<tiles[0].nblocks, kMT, 0, op.stream>>>(Up0, D20, D30, e, sd, tiles[0].table, ms);
     op.prof.launches += 1;
     DLZ_CUDA_TRY(cudaGetLastError());
     return DLZ_OK;
@@ -244,11 +308,13 @@ int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const int2 *table, in
 // at once.  B[l], X[l]: nrhs[l] internal FP64 vectors of lattice l.
 int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, const double2 *const *B,
                   double2 *const *X, const int *nrhs, const dlz_params &p, dlz_stats *st) {
-    // slots and the block table
+    // slots (their 128-site chunks contiguous in the partials) and the block tables of
+    // the three tiles (1, 2 or 4 chunks per block)
     std::vector<SlotDesc> hsd;
-    std::vector<int2> table;
+    std::vector<int2> tab[3];
     std::vector<int> slot_lat, slot_rhs, lat_slot0(nlat);
     size_t arena = 0;
+    int nchunks = 0;
     for (int l = 0; l < nlat; ++l) {
         lat_slot0[l] = (int)hsd.size();
         const Op &o = *ops[l];
@@ -258,9 +324,11 @@ int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, cons
             d.kappa = (float)o.kappa;
             d.links = o.gauge32.as<float4>();
             d.off = arena;
-            d.blk0 = (int)table.size();
+            d.blk0 = nchunks;
             d.nb = (o.g.V + kMT - 1) / kMT;
-            for (int b = 0; b < d.nb; ++b) table.push_back(make_int2((int)hsd.size(), b * kMT));
+            for (int v = 0; v < 3; ++v)
+                for (int c0 = 0; c0 < d.nb; c0 += (1 << v)) tab[v].push_back(make_int2((int)hsd.size(), c0));
+            nchunks += d.nb;
             arena += 6L * o.g.V;
             hsd.push_back(d);
             slot_lat.push_back(l);
@@ -268,17 +336,20 @@ int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, cons
         }
     }
     const int NS = (int)hsd.size();
-    const int nblocks = (int)table.size();
     if (NS == 0) return DLZ_OK;
     Op &op = *ops[0];
-    DevBuf dsd, dtab, f32, part, scal;
+    DevBuf dsd, dtab[3], f32, part, scal;
     DLZ_TRY(dsd.alloc(NS * sizeof(SlotDesc)));
-    DLZ_TRY(dtab.alloc(nblocks * sizeof(int2)));
+    Tile tiles[3];
+    for (int v = 0; v < 3; ++v) {
+        DLZ_TRY(dtab[v].alloc(tab[v].size() * sizeof(int2)));
+        DLZ_TRY(h2d(op, dtab[v].p, tab[v].data(), tab[v].size() * sizeof(int2)));
+        tiles[v] = Tile{1 << v, dtab[v].as<int2>(), (int)tab[v].size()};
+    }
     DLZ_TRY(f32.alloc(7 * arena * sizeof(float4)));
-    DLZ_TRY(part.alloc(2 * (size_t)nblocks * sizeof(double)));
+    DLZ_TRY(part.alloc(2 * (size_t)nchunks * sizeof(double)));
     DLZ_TRY(scal.alloc((size_t)NS * (sizeof(FusedState) + 2 * sizeof(double) + sizeof(int))));
     DLZ_TRY(h2d(op, dsd.p, hsd.data(), NS * sizeof(SlotDesc)));
-    DLZ_TRY(h2d(op, dtab.p, table.data(), nblocks * sizeof(int2)));
     float4 *r32 = f32.as<float4>(), *e32 = r32 + arena;
     float4 *const bufs[5] = {r32 + 2 * arena, r32 + 3 * arena, r32 + 4 * arena, r32 + 5 * arena, r32 + 6 * arena};
     FusedState *ms = reinterpret_cast<FusedState *>(scal.p);
@@ -421,7 +492,7 @@ int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, cons
             DLZ_CUDA_TRY(cudaStreamSynchronize(o.stream));
         }
         DLZ_TRY(h2d(op, d_tol, tl.data(), NS * sizeof(double)));
-        DLZ_TRY(minres_multi_batch(op, NS, dsd.as<SlotDesc>(), dtab.as<int2>(), nblocks, arena, r32, e32, bufs, ms,
+        DLZ_TRY(minres_multi_batch(op, NS, dsd.as<SlotDesc>(), tiles, nchunks, arena, r32, e32, bufs, ms,
                                    part.as<double>(), d_active, d_tol, p, iters, hs, true));
         DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
         // x += ||r|| e, lattice by lattice

@@ -51,3 +51,29 @@ def test_batch_dminres_uneven_lattices(m, with_defl):
     p64 = m.params_default(m=30, k=8, tol=1e-10, max_iter=20000)
     Xs64, sts64 = m.batch_dminres(ops, defls, Bs, p64)
     assert all(s.converged == 1 for ss in sts64 for s in ss)
+
+
+def test_batch_dminres_tiles_bit_identical(m, monkeypatch):
+    """The batched kernels run with 1, 2 or 4 chunks of 128 sites per block (chosen by
+    timing, or forced with DLZ_MULTI_TILE); the sums are taken per chunk in a fixed
+    order, so every tile gives the same bits."""
+    ops, Bs = [], []
+    for i, (dims, kappa, seed) in enumerate(LATS):
+        U = synth.su3_links(dims, seed)
+        ops.append(m.create_operator(dims, torch.from_numpy(U).cuda(), kappa))
+        Bs.append(torch.from_numpy(synth.gaussian_spinors(dims, [5 + i, 6 + i])).cuda())
+    p = m.params_default(m=30, k=8, tol=1e-10, max_iter=20000, precision=m.F32)
+    runs = {}
+    for tile in ["1", "2", "4", None]:
+        if tile is None:
+            monkeypatch.delenv("DLZ_MULTI_TILE", raising=False)
+        else:
+            monkeypatch.setenv("DLZ_MULTI_TILE", tile)
+        Xs, sts = m.batch_dminres(ops, [None] * len(ops), Bs, p)
+        assert all(s.converged == 1 for ss in sts for s in ss)
+        runs[tile] = ([x.cpu().numpy() for x in Xs], [[s.iterations for s in ss] for ss in sts])
+    ref_x, ref_it = runs["1"]
+    for tile, (xs, its) in runs.items():
+        assert its == ref_it, tile
+        for a, b in zip(xs, ref_x):
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), tile
