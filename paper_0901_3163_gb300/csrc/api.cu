@@ -141,7 +141,7 @@ struct Staged {
         DLZ_CUDA_TRY(cudaMemcpyAsync(dev, p, nbytes, cudaMemcpyHostToDevice, op.stream));
         return DLZ_OK;
     }
-    int out(Op &op, void *p, size_t nbytes) {
+    int out(Op &, void *p, size_t nbytes) {
         user = p;
         bytes = nbytes;
         host = !on_device(p);
@@ -586,17 +586,15 @@ int dlz_stencil_bench(dlz_op_t h, int dtype, int which, int nrhs, int iters, con
         return wilson32_batch(op, b.as<float4>(), a.as<float4>(), which, nrhs);
     };
     for (int i = 0; i < 3; ++i) DLZ_TRY(launch());
-    cudaEvent_t e0, e1;
-    DLZ_CUDA_TRY(cudaEventCreate(&e0));
-    DLZ_CUDA_TRY(cudaEventCreate(&e1));
-    cudaEventRecord(e0, op.stream);
+    Event e0, e1;
+    DLZ_CUDA_TRY(e0.create());
+    DLZ_CUDA_TRY(e1.create());
+    DLZ_CUDA_TRY(cudaEventRecord(e0.e, op.stream));
     for (int i = 0; i < iters; ++i) DLZ_TRY(launch());
-    cudaEventRecord(e1, op.stream);
-    DLZ_CUDA_TRY(cudaEventSynchronize(e1));
+    DLZ_CUDA_TRY(cudaEventRecord(e1.e, op.stream));
+    DLZ_CUDA_TRY(cudaEventSynchronize(e1.e));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    DLZ_CUDA_TRY(cudaEventElapsedTime(&ms, e0.e, e1.e));
     *ms_per_launch = ms / iters;
     return DLZ_OK;
 }

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) k_cg_beta(const double *__restrict__ part
 }  // namespace
 
 int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5], CgFusedState *ms,
-                     double *partials, const double *d_tol, const dlz_params &p, int &iters, HostScratch &hs) {
+                     double *partials, const double *d_tol, const dlz_params &p, int &iters) {
     const long n = 6L * op.g.V;
     const Geom g = op.g;
     const float kappa = (float)op.kappa;

@@ -169,6 +169,18 @@ int restart_gemm32(Op &op, float4 *out, const float4 *in, long n, int nin, int n
                    void *dev_scratch);
 void blas_destroy(Op &op);
 
+// A CUDA event destroyed on every return path.
+struct Event {
+    cudaEvent_t e = nullptr;
+    Event() = default;
+    Event(const Event &) = delete;
+    Event &operator=(const Event &) = delete;
+    ~Event() {
+        if (e) cudaEventDestroy(e);
+    }
+    cudaError_t create() { return e ? cudaSuccess : cudaEventCreate(&e); }
+};
+
 // ---------------------------------------------------------------- CUDA graphs
 // A launch-bound sequence of kernels (a Lanczos cycle, a group of MinRes
 // iterations on one right-hand side) is captured once on the private stream

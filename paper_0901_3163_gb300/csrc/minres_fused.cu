@@ -200,19 +200,22 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
     // DLZ_TRACE=1: time the replays of the 6-iteration group (diagnostics)
     const char *trace_env = std::getenv("DLZ_TRACE");
     const bool trace = trace_env && trace_env[0] == '1';
-    cudaEvent_t te0 = nullptr, te1 = nullptr;
+    Event te0, te1;
     double t_graph = 0.0;
     int n_timed = 0;
-    if (trace) { cudaEventCreate(&te0); cudaEventCreate(&te1); }
+    if (trace) {
+        DLZ_CUDA_TRY(te0.create());
+        DLZ_CUDA_TRY(te1.create());
+    }
     while (iters < p.max_iter) {
         const bool timed = trace && ge.exec;      // not the replay that captures the graph
-        if (timed) cudaEventRecord(te0, op.stream);
+        if (timed) DLZ_CUDA_TRY(cudaEventRecord(te0.e, op.stream));
         DLZ_TRY(run_graph(op, ge, six));
         if (timed) {
-            cudaEventRecord(te1, op.stream);
-            cudaEventSynchronize(te1);
+            DLZ_CUDA_TRY(cudaEventRecord(te1.e, op.stream));
+            DLZ_CUDA_TRY(cudaEventSynchronize(te1.e));
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, te0, te1) == cudaSuccess) { t_graph += ms; ++n_timed; }
+            if (cudaEventElapsedTime(&ms, te0.e, te1.e) == cudaSuccess) { t_graph += ms; ++n_timed; }
             else cudaGetLastError();
         }
         iters += 6;
@@ -235,8 +238,6 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
     if (trace) {
         std::fprintf(stderr, "[dlz] fused MinRes N=%d: %d iterations, graph replay %.4f ms per iteration (%d timed)\n",
                      N, iters, n_timed ? t_graph / (6.0 * n_timed) : 0.0, n_timed);
-        cudaEventDestroy(te0);
-        cudaEventDestroy(te1);
     }
     // the direction update of the last step (after 6k steps the buffers are back
     // in their starting roles: u_J in Up, d_{J-1} in D2, d_{J-2} in D3; v_J = u_J / beta_J)

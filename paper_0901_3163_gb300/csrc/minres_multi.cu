@@ -206,8 +206,7 @@ struct Tile {
 // 128-site chunk whatever the tile, so every tile gives bit-identical results.
 int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const Tile *tiles, int nchunks, size_t arena,
                        const float4 *r, float4 *e, float4 *const bufs[5], FusedState *ms, double *partials,
-                       int *active, const double *d_tol, const dlz_params &p, int &iters, HostScratch &hs,
-                       bool e_init) {
+                       int *active, const double *d_tol, const dlz_params &p, int &iters, bool e_init) {
     double *partials2 = partials + nchunks;
     k_mm_norm<1><<<tiles[0].nblocks, kMT, 0, op.stream>>>(r, sd, tiles[0].table, partials);
     k_mm_init<<<NS, 256, 0, op.stream>>>(partials, sd, ms);
@@ -252,10 +251,10 @@ int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const Tile *tiles, in
         forced = b == 1 ? 0 : b == 2 ? 1 : b == 4 ? 2 : -1;
     }
     float tms[3] = {0.f, 0.f, 0.f};
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    Event ev0, ev1;
     if (forced < 0) {
-        DLZ_CUDA_TRY(cudaEventCreate(&ev0));
-        DLZ_CUDA_TRY(cudaEventCreate(&ev1));
+        DLZ_CUDA_TRY(ev0.create());
+        DLZ_CUDA_TRY(ev1.create());
     }
     const int check = std::max(6, (p.check_every / 6) * 6);
     std::vector<FusedState> h(NS);
@@ -267,12 +266,12 @@ int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const Tile *tiles, in
     while (iters < p.max_iter) {
         const bool timed = forced < 0 && group >= 3 && group < 6;
         cur = forced >= 0 ? forced : (group < 6 ? group % 3 : best);
-        if (timed) cudaEventRecord(ev0, op.stream);
+        if (timed) DLZ_CUDA_TRY(cudaEventRecord(ev0.e, op.stream));
         DLZ_TRY(run_graph(op, ge[cur], six));
         if (timed) {
-            cudaEventRecord(ev1, op.stream);
-            cudaEventSynchronize(ev1);
-            if (cudaEventElapsedTime(&tms[cur], ev0, ev1) != cudaSuccess) {
+            DLZ_CUDA_TRY(cudaEventRecord(ev1.e, op.stream));
+            DLZ_CUDA_TRY(cudaEventSynchronize(ev1.e));
+            if (cudaEventElapsedTime(&tms[cur], ev0.e, ev1.e) != cudaSuccess) {
                 cudaGetLastError();
                 tms[cur] = 1e30f;
             }
@@ -296,8 +295,6 @@ int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const Tile *tiles, in
             if (changed) DLZ_TRY(h2d(op, active, act.data(), NS * sizeof(int)));
         }
     }
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
     k_mm_last<1><<<tiles[0].nblocks, kMT, 0, op.stream>>>(Up0, D20, D30, e, sd, tiles[0].table, ms);
     op.prof.launches += 1;
     DLZ_CUDA_TRY(cudaGetLastError());
@@ -355,8 +352,6 @@ int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, cons
     FusedState *ms = reinterpret_cast<FusedState *>(scal.p);
     double *d_tol = reinterpret_cast<double *>(ms + NS);
     int *d_active = reinterpret_cast<int *>(d_tol + 2 * NS);
-    HostScratch hs;
-    DLZ_TRY(hs.ensure(64));
     // per-lattice FP64 work: b' = gamma5 b, x, r, Q x
     struct Lat {
         DevBuf bp, x, r, t, dots, nrm;
@@ -493,7 +488,7 @@ int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, cons
         }
         DLZ_TRY(h2d(op, d_tol, tl.data(), NS * sizeof(double)));
         DLZ_TRY(minres_multi_batch(op, NS, dsd.as<SlotDesc>(), tiles, nchunks, arena, r32, e32, bufs, ms,
-                                   part.as<double>(), d_active, d_tol, p, iters, hs, true));
+                                   part.as<double>(), d_active, d_tol, p, iters, true));
         DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
         // x += ||r|| e, lattice by lattice
         for (int l = 0; l < nlat; ++l) {

@@ -82,7 +82,7 @@ int deflation_finish(Op &op, dlz_defl_s *d) {
 }
 
 // LU factors of H and its eigen-decomposition (the Rayleigh-Ritz pairs).
-int deflation_factor(Op &op, dlz_defl_s *d) {
+int deflation_factor(Op &, dlz_defl_s *d) {
     const int k = d->k;
     if (k == 0) return DLZ_OK;
     d->Hlu = d->H;

@@ -63,7 +63,7 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
 // (cg_fused.cu); s0 is overwritten, e is updated in place (holds the start).
 struct CgFusedState;
 int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5], CgFusedState *ms,
-                     double *partials, const double *d_tol, const dlz_params &p, int &iters, HostScratch &hs);
+                     double *partials, const double *d_tol, const dlz_params &p, int &iters);
 // FP32 D-MinRes with FP64 defect correction on many lattices at once
 // (minres_multi.cu); B[l], X[l]: nrhs[l] <= 16 internal FP64 vectors of lattice l,
 // st: one entry per (lattice, right-hand side) in order.

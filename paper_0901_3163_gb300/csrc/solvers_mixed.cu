@@ -214,7 +214,7 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
             if (!proj) DLZ_CUDA_TRY(cudaMemsetAsync(w32[1], 0, (size_t)N * n32 * sizeof(float4), op.stream));
             float4 *const bufs[5] = {w32[2], w32[3], w32[4], w32[5], w32[6]};
             DLZ_TRY(cgnr_fused_batch(op, N, w32[0], w32[1], bufs, reinterpret_cast<CgFusedState *>(ist),
-                                     fpart.as<double>(), d_tol, p, iters, hs));
+                                     fpart.as<double>(), d_tol, p, iters));
             mv_batch += 2L * (iters - it0);
         }
         // x_q += ||r_q|| e_q
