@@ -138,6 +138,17 @@ int plan_finish(bool harmonic, int m, int k, const std::vector<double> &T, doubl
     std::vector<int> idx(m);
     for (int i = 0; i < m; ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return std::fabs(mu[a]) > std::fabs(mu[b]); });
+    // nonzero column range [j0, j1) of each row of Tbar (a dense leading block, then the
+    // band): the products with Tbar below skip only exact zeros
+    std::vector<int> j0(m + 1), j1(m + 1);
+    for (int r = 0; r <= m; ++r) {
+        const double *row = &T[(size_t)r * m];
+        int a = 0, b = m;
+        while (a < m && row[a] == 0.0) ++a;
+        while (b > a && row[b - 1] == 0.0) --b;
+        j0[r] = a;
+        j1[r] = b;
+    }
     std::vector<double> Gk((size_t)m * k);
     for (int l = 0; l < k; ++l) {
         for (int i = 0; i < m; ++i) col[i] = Zc[(size_t)i * m + idx[l]];
@@ -150,7 +161,7 @@ int plan_finish(bool harmonic, int m, int k, const std::vector<double> &T, doubl
         double r2 = 0;
         for (int r = 0; r <= m; ++r) {
             double t = 0;
-            for (int j = 0; j < m; ++j) t += T[(size_t)r * m + j] * Gk[(size_t)j * k + l];
+            for (int j = j0[r]; j < j1[r]; ++j) t += T[(size_t)r * m + j] * Gk[(size_t)j * k + l];
             if (r < m) t -= o.theta[l] * Gk[(size_t)r * k + l];
             r2 += t * t;
         }
@@ -169,7 +180,7 @@ int plan_finish(bool harmonic, int m, int k, const std::vector<double> &T, doubl
     for (int r = 0; r <= m; ++r)
         for (int l = 0; l < k; ++l) {
             double t = 0;
-            for (int j = 0; j < m; ++j) t += T[(size_t)r * m + j] * o.P[(size_t)j * (k + 1) + l];
+            for (int j = j0[r]; j < j1[r]; ++j) t += T[(size_t)r * m + j] * o.P[(size_t)j * (k + 1) + l];
             TP[(size_t)r * k + l] = t;
         }
     for (int a = 0; a <= k; ++a)

@@ -35,9 +35,17 @@ void tridiagonalise(int n, std::vector<double> &a, std::vector<double> &d, std::
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;          // length of the column below the diagonal
         // a column with nothing below its subdiagonal is already reduced (the tridiagonal
-        // tail of a restarted Lanczos matrix): no reflection needed
+        // tail of a restarted Lanczos matrix): no reflection needed.  vl: the Householder
+        // vector's nonzero length (the dense block of an arrowhead matrix ends early);
+        // every loop below skips only terms that are exact zeros, so the result is the
+        // same as with full-length loops
         double tail = 0.0;
-        for (int i = 1; i < m; ++i) tail += a[(size_t)(k + 1 + i) * n + k] * a[(size_t)(k + 1 + i) * n + k];
+        int vl = 1;
+        for (int i = 1; i < m; ++i) {
+            const double t = a[(size_t)(k + 1 + i) * n + k];
+            tail += t * t;
+            if (t != 0.0) vl = i + 1;
+        }
         if (tail == 0.0) continue;
         double alpha = tail + a[(size_t)(k + 1) * n + k] * a[(size_t)(k + 1) * n + k];
         alpha = std::sqrt(alpha);
@@ -47,34 +55,38 @@ void tridiagonalise(int n, std::vector<double> &a, std::vector<double> &d, std::
         for (int i = 0; i < m; ++i) v[i] = a[(size_t)(k + 1 + i) * n + k];
         v[0] -= alpha;
         double vn2 = 0.0;
-        for (int i = 0; i < m; ++i) vn2 += v[i] * v[i];
+        for (int i = 0; i < vl; ++i) vn2 += v[i] * v[i];
         if (vn2 == 0.0) continue;
         const double tau = 2.0 / vn2;
         // p = tau * A22 v ;  K = tau/2 (v.p) ;  q = p - K v ;  A22 -= v q^T + q v^T
         for (int i = 0; i < m; ++i) {
             double s = 0.0;
             const double *row = &a[(size_t)(k + 1 + i) * n + k + 1];
-            for (int j = 0; j < m; ++j) s += row[j] * v[j];
+            for (int j = 0; j < vl; ++j) s += row[j] * v[j];
             p[i] = tau * s;
         }
         double vp = 0.0;
-        for (int i = 0; i < m; ++i) vp += v[i] * p[i];
+        for (int i = 0; i < vl; ++i) vp += v[i] * p[i];
         const double K = 0.5 * tau * vp;
         for (int i = 0; i < m; ++i) q[i] = p[i] - K * v[i];
-        for (int i = 0; i < m; ++i) {
+        for (int i = 0; i < vl; ++i) {
             double *row = &a[(size_t)(k + 1 + i) * n + k + 1];
             for (int j = 0; j < m; ++j) row[j] -= v[i] * q[j] + q[i] * v[j];
         }
+        for (int i = vl; i < m; ++i) {      // v[i] = 0: only the columns j < vl change
+            double *row = &a[(size_t)(k + 1 + i) * n + k + 1];
+            for (int j = 0; j < vl; ++j) row[j] -= q[i] * v[j];
+        }
         a[(size_t)(k + 1) * n + k] = a[(size_t)k * n + k + 1] = alpha;
-        for (int i = 1; i < m; ++i) a[(size_t)(k + 1 + i) * n + k] = a[(size_t)k * n + k + 1 + i] = 0.0;
+        for (int i = 1; i < vl; ++i) a[(size_t)(k + 1 + i) * n + k] = a[(size_t)k * n + k + 1 + i] = 0.0;
         if (want_q) {
-            // Q <- Q H on columns k+1..n-1, i.e. Qt <- H Qt on rows k+1..n-1
+            // Q <- Q H on columns k+1..n-1, i.e. Qt <- H Qt on rows k+1..k+vl
             for (int c = 0; c < n; ++c) sc[c] = 0.0;
-            for (int i = 0; i < m; ++i) {
+            for (int i = 0; i < vl; ++i) {
                 const double *row = &Qt[(size_t)(k + 1 + i) * n];
                 for (int c = 0; c < n; ++c) sc[c] += v[i] * row[c];
             }
-            for (int i = 0; i < m; ++i) {
+            for (int i = 0; i < vl; ++i) {
                 double *row = &Qt[(size_t)(k + 1 + i) * n];
                 const double f = tau * v[i];
                 for (int c = 0; c < n; ++c) row[c] -= f * sc[c];
