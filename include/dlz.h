@@ -335,12 +335,16 @@ int dlz_seed_deflation(dlz_op_t op, int which, const void *vecs, int dtype, int 
  *   dlz_host_symeig: eigen-decomposition of a real symmetric matrix A
  *     (Householder tridiagonalisation + implicit QR with Wilkinson shifts):
  *     w[n] ascending, Z[n][n] with the eigenvector of w[j] in column j.
+ *   dlz_host_sym_extremes: the smallest (lo) and largest (hi) eigenvalue of a
+ *     real symmetric A (Householder tridiagonalisation + Sturm-sequence
+ *     bisection to the spacing of doubles); DLZ_ERR_NONFINITE on non-finite A.
  *   dlz_host_lstsq: y = argmin ||c - T y|| for T (rows x cols, rows > cols,
  *     full column rank) by Householder QR; q[rows] receives the unit
  *     vector spanning the orthogonal complement of range(T) when rows == cols + 1
  *     (may be NULL).
  */
 int dlz_host_symeig(int n, const double *A, double *w, double *Z);
+int dlz_host_sym_extremes(int n, const double *A, double *lo, double *hi);
 int dlz_host_lstsq(int rows, int cols, const double *T, const double *c, double *y, double *q);
 
 #ifdef __cplusplus

@@ -84,9 +84,12 @@ int plan_finish(bool harmonic, int m, int k, const std::vector<double> &T, doubl
         for (int j = 0; j < m; ++j) Tm[(size_t)i * m + j] = T[(size_t)i * m + j];
     std::vector<double> ev(m), G;
     // Lan-DR needs the Ritz vectors of T_m; MinRes-DR only its extreme eigenvalues (||A|| estimate)
-    if (!harmonic) G.resize((size_t)m * m);
-    if (!sym_eig(m, Tm.data(), ev.data(), harmonic ? nullptr : G.data()))
-        return fail(DLZ_ERR_NONFINITE, "eig(T_m) failed");
+    if (harmonic) {
+        if (!sym_extremes(m, Tm.data(), &ev[0], &ev[m - 1])) return fail(DLZ_ERR_NONFINITE, "eig(T_m) failed");
+    } else {
+        G.resize((size_t)m * m);
+        if (!sym_eig(m, Tm.data(), ev.data(), G.data())) return fail(DLZ_ERR_NONFINITE, "eig(T_m) failed");
+    }
     Anorm = std::max(Anorm, std::max(std::fabs(ev[0]), std::fabs(ev[m - 1])));
     o.P.assign((size_t)(m + 1) * (k + 1), 0.0);
     o.Tn.assign((size_t)(m + 1) * m, 0.0);

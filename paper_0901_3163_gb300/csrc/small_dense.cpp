@@ -121,8 +121,11 @@ bool tridiagonal_qr(int n, std::vector<double> &d, std::vector<double> &e, std::
         const double mu = d[h] - b * b / (delta + sgn1(delta) * std::hypot(delta, b));
         double x = d[l] - mu, z = e[l];
         for (int k = l; k < h; ++k) {
-            const double r = std::hypot(x, z);
-            const double c = (r == 0.0) ? 1.0 : x / r, s = (r == 0.0) ? 0.0 : z / r;
+            // plain square root unless x^2 + z^2 could over- or underflow
+            const double r2 = x * x + z * z;
+            const double r = (r2 > 1e-280 && r2 < 1e280) ? std::sqrt(r2) : std::hypot(x, z);
+            const double ir = (r == 0.0) ? 0.0 : 1.0 / r;
+            const double c = (r == 0.0) ? 1.0 : x * ir, s = z * ir;
             if (k > l) e[k - 1] = r;
             const double dk = d[k], dk1 = d[k + 1], ek = e[k];
             d[k] = c * c * dk + 2.0 * c * s * ek + s * s * dk1;
@@ -147,17 +150,85 @@ bool tridiagonal_qr(int n, std::vector<double> &d, std::vector<double> &e, std::
     return true;
 }
 
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x: the negative
+// pivots of the LDL^T factorisation of T - x I (Sturm sequence; Golub & Van Loan,
+// Sec. 8.4), a zero pivot replaced by a tiny one.
+int sturm_count(int n, const std::vector<double> &d, const std::vector<double> &e, double x, double tiny) {
+    int cnt = 0;
+    double q = 1.0;
+    for (int i = 0; i < n; ++i) {
+        q = d[i] - x - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
+        if (q == 0.0) q = -tiny;
+        if (q < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// The j-th smallest eigenvalue (j = 0..n-1) of (d, e) by bisection inside [lo, hi]
+// down to the spacing of doubles.
+double bisect_eigenvalue(int n, const std::vector<double> &d, const std::vector<double> &e, int j, double lo,
+                         double hi, double tiny) {
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi || hi - lo <= 2.2e-16 * std::max(std::fabs(lo), std::fabs(hi))) break;
+        if (sturm_count(n, d, e, mid, tiny) > j) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Symmetrise a copy of A (against rounding in the caller) and scale it by a power of
+// two so that its largest entry is near 1 (the sums of squares in the reduction then
+// neither overflow nor underflow); returns the factor to multiply eigenvalues by, or
+// 0 for non-finite input.
+double symmetrised_scaled(int n, const double *A, std::vector<double> &a) {
+    a.assign(A, A + (size_t)n * n);
+    double amax = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            const double s = 0.5 * (a[(size_t)i * n + j] + a[(size_t)j * n + i]);
+            a[(size_t)i * n + j] = a[(size_t)j * n + i] = s;
+            amax = std::max(amax, std::fabs(s));
+        }
+    if (!std::isfinite(amax)) return 0.0;
+    if (amax == 0.0 || (amax > 1e-100 && amax < 1e100)) return 1.0;
+    int ex = 0;
+    std::frexp(amax, &ex);
+    for (double &v : a) v = std::ldexp(v, -ex);
+    return std::ldexp(1.0, ex);
+}
+
 }  // namespace
+
+bool sym_extremes(int n, const double *A, double *lo, double *hi) {
+    if (n <= 0) return false;
+    std::vector<double> a, d, e, Q;
+    const double f = symmetrised_scaled(n, A, a);
+    if (f == 0.0) return false;
+    tridiagonalise(n, a, d, e, Q, false);
+    // Gershgorin interval of the tridiagonal matrix
+    double glo = 0.0, ghi = 0.0, scale = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(e[i]) : 0.0);
+        glo = (i == 0) ? d[i] - r : std::min(glo, d[i] - r);
+        ghi = (i == 0) ? d[i] + r : std::max(ghi, d[i] + r);
+        scale = std::max(scale, std::fabs(d[i]) + r);
+    }
+    if (!std::isfinite(scale)) return false;
+    const double pad = 1e-14 * scale + 1e-300;
+    glo -= pad;
+    ghi += pad;
+    const double tiny = 1e-300 + 1e-30 * scale;
+    *lo = f * bisect_eigenvalue(n, d, e, 0, glo, ghi, tiny);
+    *hi = f * bisect_eigenvalue(n, d, e, n - 1, glo, ghi, tiny);
+    return true;
+}
 
 bool sym_eig(int n, const double *A, double *w, double *Z) {
     if (n <= 0) return true;
-    std::vector<double> a(A, A + (size_t)n * n), d, e, Q;
-    // symmetrise the input against rounding in the caller
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < i; ++j) {
-            const double s = 0.5 * (a[(size_t)i * n + j] + a[(size_t)j * n + i]);
-            a[(size_t)i * n + j] = a[(size_t)j * n + i] = s;
-        }
+    std::vector<double> a, d, e, Q;
+    const double f = symmetrised_scaled(n, A, a);
+    if (f == 0.0) return false;
     const bool want_q = Z != nullptr;
     tridiagonalise(n, a, d, e, Q, want_q);
     if (!tridiagonal_qr(n, d, e, Q, want_q)) return false;
@@ -165,7 +236,7 @@ bool sym_eig(int n, const double *A, double *w, double *Z) {
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return d[x] < d[y]; });
     for (int j = 0; j < n; ++j) {
-        w[j] = d[idx[j]];
+        w[j] = f * d[idx[j]];
         if (want_q)
             for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = Q[(size_t)idx[j] * n + i];
     }
@@ -351,6 +422,11 @@ bool mgs_columns(int rows, int cols, double *P) {
 extern "C" int dlz_host_symeig(int n, const double *A, double *w, double *Z) {
     if (n < 0 || (n > 0 && (!A || !w || !Z))) return DLZ_ERR_BADARG;
     return dlz::sym_eig(n, A, w, Z) ? DLZ_OK : DLZ_ERR_NONFINITE;
+}
+
+extern "C" int dlz_host_sym_extremes(int n, const double *A, double *lo, double *hi) {
+    if (n <= 0 || !A || !lo || !hi) return DLZ_ERR_BADARG;
+    return dlz::sym_extremes(n, A, lo, hi) ? DLZ_OK : DLZ_ERR_NONFINITE;
 }
 
 extern "C" int dlz_host_lstsq(int rows, int cols, const double *T, const double *c, double *y,

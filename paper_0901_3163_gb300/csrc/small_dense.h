@@ -12,6 +12,9 @@ namespace dlz {
 // eigenvector of w[j] (Z may be null: eigenvalues only).  false if the QR
 // iteration did not converge.
 bool sym_eig(int n, const double *A, double *w, double *Z);
+// Smallest and largest eigenvalue of symmetric A (n x n) by Householder reduction and
+// Sturm bisection; false on non-finite input.
+bool sym_extremes(int n, const double *A, double *lo, double *hi);
 // y = argmin ||c - T y|| (rows > cols); q (optional, rows == cols + 1): unit
 // vector orthogonal to range(T).
 bool lstsq(int rows, int cols, const double *T, const double *c, double *y, double *q);

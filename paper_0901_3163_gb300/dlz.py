@@ -105,6 +105,7 @@ _SIGS = {
     "dlz_subspace_loss": ([_vp, _vp, _ip, _dp, _vp], _ip),
     "dlz_seed_deflation": ([_vp, _ip, _vp, _ip, _ip, ctypes.POINTER(_vp)], _ip),
     "dlz_host_symeig": ([_ip, _vp, _vp, _vp], _ip),
+    "dlz_host_sym_extremes": ([_ip, _vp, _vp, _vp], _ip),
     "dlz_host_lstsq": ([_ip, _ip, _vp, _vp, _vp, _vp], _ip),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -452,6 +453,13 @@ def host_symeig(A):
     Z = np.empty((n, n))
     _check(lib.dlz_host_symeig(n, A.ctypes.data, w.ctypes.data, Z.ctypes.data))
     return w, Z
+
+
+def host_sym_extremes(A):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib.dlz_host_sym_extremes(A.shape[0], A.ctypes.data, ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
 
 
 def host_lstsq(T, c):

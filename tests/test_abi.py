@@ -43,6 +43,19 @@ def test_host_symeig_matches_lapack(n):
     assert np.abs(Z.T @ Z - np.eye(n)).max() < 1e-13
 
 
+@pytest.mark.parametrize("scale", [1e-200, 1e200])
+def test_host_symeig_extreme_scales(scale):
+    """Entries near the ends of the double range: the reduction scales them first."""
+    m = dlz()
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((30, 30))
+    A = (B + B.T) * scale
+    w, Z = m.host_symeig(A)
+    w0 = np.linalg.eigvalsh(B + B.T) * scale
+    assert np.abs(w - w0).max() <= 1e-13 * np.abs(w0).max()
+    assert np.abs(Z.T @ Z - np.eye(30)).max() < 1e-13
+
+
 def test_host_symeig_arrowhead_with_clusters():
     """The Lan-DR restart matrix: diagonal block of Ritz values, one coupling row."""
     m = dlz()
@@ -57,6 +70,34 @@ def test_host_symeig_arrowhead_with_clusters():
             T[j, j + 1] = T[j + 1, j] = rng.uniform(0.1, 1)
     w, Z = m.host_symeig(T)
     assert np.abs(w - np.linalg.eigvalsh(T)).max() < 1e-14 * 4
+
+
+@pytest.mark.parametrize("case", ["dense", "arrowhead", "indefinite", "one", "huge", "tiny"])
+def test_host_sym_extremes(case):
+    """Smallest and largest eigenvalue by Sturm bisection, against LAPACK."""
+    m = dlz()
+    rng = np.random.default_rng(11)
+    if case == "one":
+        A = np.array([[2.5]])
+    elif case == "arrowhead":             # the MinRes-DR restart matrix: dense block, then a band
+        n, k = 100, 40
+        A = np.zeros((n, n))
+        B = rng.standard_normal((k + 1, k + 1)) * 1e-3
+        A[:k + 1, :k + 1] = B + B.T
+        for j in range(k + 1, n):
+            A[j, j] = rng.uniform(-2, 2)
+            A[j, j - 1] = A[j - 1, j] = rng.uniform(0.1, 1)
+    else:
+        n = 60
+        A = rng.standard_normal((n, n))
+        A = A + A.T
+        if case == "indefinite":
+            A += np.diag(np.linspace(-50, 50, n))
+        A *= {"huge": 1e200, "tiny": 1e-200}.get(case, 1.0)
+    lo, hi = m.host_sym_extremes(A)
+    w = np.linalg.eigvalsh(A)
+    scale = np.abs(w).max()
+    assert abs(lo - w[0]) <= 1e-13 * scale and abs(hi - w[-1]) <= 1e-13 * scale
 
 
 @pytest.mark.parametrize("rows,cols", [(5, 4), (41, 40), (101, 100), (30, 12)])
