@@ -22,23 +22,22 @@ namespace {
 
 inline double sgn1(double x) { return x >= 0.0 ? 1.0 : -1.0; }
 
-// Reduce symmetric a (n x n) to tridiagonal form Q^T a Q; returns d, e and, if
-// want_q, Qt = Q^T (row i of Qt is column i of Q, so the later plane rotations
-// touch two contiguous rows).
+// Reduce symmetric a (n x n) to tridiagonal form Q^T a Q (Golub & Van Loan, Sec. 8.3.1),
+// reading and updating the lower triangle only; returns d, e and, if want_q, Qt = Q^T
+// (row i of Qt is column i of Q, so the later plane rotations touch two contiguous
+// rows).  Q = H_0 H_1 ... is accumulated backwards (Qt = H_{n-3} ... H_0 as right
+// products on the identity), so each reflector touches only the trailing block it
+// acts on.  vl: the nonzero length of a Householder vector (the dense block of an
+// arrowhead matrix ends early); loops stop there.
 void tridiagonalise(int n, std::vector<double> &a, std::vector<double> &d, std::vector<double> &e,
                     std::vector<double> &Qt, bool want_q) {
-    if (want_q) {
-        Qt.assign((size_t)n * n, 0.0);
-        for (int i = 0; i < n; ++i) Qt[(size_t)i * n + i] = 1.0;
-    }
-    std::vector<double> v(n), p(n), q(n), sc(n);
+    std::vector<double> v(n), p(n), q(n);
+    std::vector<double> vs(want_q ? (size_t)n * n : 0), taus(n, 0.0);
+    std::vector<int> vls(n, 0);
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;          // length of the column below the diagonal
         // a column with nothing below its subdiagonal is already reduced (the tridiagonal
-        // tail of a restarted Lanczos matrix): no reflection needed.  vl: the Householder
-        // vector's nonzero length (the dense block of an arrowhead matrix ends early);
-        // every loop below skips only terms that are exact zeros, so the result is the
-        // same as with full-length loops
+        // tail of a restarted Lanczos matrix): no reflection needed
         double tail = 0.0;
         int vl = 1;
         for (int i = 1; i < m; ++i) {
@@ -47,49 +46,78 @@ void tridiagonalise(int n, std::vector<double> &a, std::vector<double> &d, std::
             if (t != 0.0) vl = i + 1;
         }
         if (tail == 0.0) continue;
-        double alpha = tail + a[(size_t)(k + 1) * n + k] * a[(size_t)(k + 1) * n + k];
-        alpha = std::sqrt(alpha);
-        if (alpha == 0.0) continue;
         const double x0 = a[(size_t)(k + 1) * n + k];
-        alpha = -sgn1(x0) * alpha;
-        for (int i = 0; i < m; ++i) v[i] = a[(size_t)(k + 1 + i) * n + k];
+        const double alpha = -sgn1(x0) * std::sqrt(tail + x0 * x0);
+        for (int i = 0; i < vl; ++i) v[i] = a[(size_t)(k + 1 + i) * n + k];
         v[0] -= alpha;
         double vn2 = 0.0;
         for (int i = 0; i < vl; ++i) vn2 += v[i] * v[i];
         if (vn2 == 0.0) continue;
         const double tau = 2.0 / vn2;
-        // p = tau * A22 v ;  K = tau/2 (v.p) ;  q = p - K v ;  A22 -= v q^T + q v^T
-        for (int i = 0; i < m; ++i) {
-            double s = 0.0;
+        // p = tau * A22 v from the lower triangle: rows i < vl give a dot over j < i and
+        // an axpy into p[j < i]; rows i >= vl only a dot over j < vl
+        for (int i = 0; i < m; ++i) p[i] = 0.0;
+        for (int i = 0; i < vl; ++i) {
             const double *row = &a[(size_t)(k + 1 + i) * n + k + 1];
+            const double vi = v[i];
+            double s = 0.0;
+            for (int j = 0; j < i; ++j) {
+                s += row[j] * v[j];
+                p[j] += row[j] * vi;
+            }
+            p[i] += s + row[i] * vi;
+        }
+        for (int i = vl; i < m; ++i) {
+            const double *row = &a[(size_t)(k + 1 + i) * n + k + 1];
+            double s = 0.0;
             for (int j = 0; j < vl; ++j) s += row[j] * v[j];
-            p[i] = tau * s;
+            p[i] = s;
         }
         double vp = 0.0;
+        for (int i = 0; i < m; ++i) p[i] *= tau;
         for (int i = 0; i < vl; ++i) vp += v[i] * p[i];
         const double K = 0.5 * tau * vp;
-        for (int i = 0; i < m; ++i) q[i] = p[i] - K * v[i];
+        for (int i = 0; i < m; ++i) q[i] = p[i] - (i < vl ? K * v[i] : 0.0);
+        // A22 -= v q^T + q v^T on the lower triangle (rows i >= vl: v[i] = 0, and only
+        // the columns j < vl change)
         for (int i = 0; i < vl; ++i) {
             double *row = &a[(size_t)(k + 1 + i) * n + k + 1];
-            for (int j = 0; j < m; ++j) row[j] -= v[i] * q[j] + q[i] * v[j];
+            const double vi = v[i], qi = q[i];
+            for (int j = 0; j <= i; ++j) row[j] -= vi * q[j] + qi * v[j];
         }
-        for (int i = vl; i < m; ++i) {      // v[i] = 0: only the columns j < vl change
+        for (int i = vl; i < m; ++i) {
             double *row = &a[(size_t)(k + 1 + i) * n + k + 1];
-            for (int j = 0; j < vl; ++j) row[j] -= q[i] * v[j];
+            const double qi = q[i];
+            for (int j = 0; j < vl; ++j) row[j] -= qi * v[j];
         }
-        a[(size_t)(k + 1) * n + k] = a[(size_t)k * n + k + 1] = alpha;
-        for (int i = 1; i < vl; ++i) a[(size_t)(k + 1 + i) * n + k] = a[(size_t)k * n + k + 1 + i] = 0.0;
+        a[(size_t)(k + 1) * n + k] = alpha;
+        for (int i = 1; i < vl; ++i) a[(size_t)(k + 1 + i) * n + k] = 0.0;
         if (want_q) {
-            // Q <- Q H on columns k+1..n-1, i.e. Qt <- H Qt on rows k+1..k+vl
-            for (int c = 0; c < n; ++c) sc[c] = 0.0;
-            for (int i = 0; i < vl; ++i) {
-                const double *row = &Qt[(size_t)(k + 1 + i) * n];
-                for (int c = 0; c < n; ++c) sc[c] += v[i] * row[c];
+            taus[k] = tau;
+            vls[k] = vl;
+            for (int i = 0; i < vl; ++i) vs[(size_t)k * n + i] = v[i];
+        }
+    }
+    if (want_q) {
+        Qt.assign((size_t)n * n, 0.0);
+        for (int i = 0; i < n; ++i) Qt[(size_t)i * n + i] = 1.0;
+        std::vector<double> w(n);
+        for (int k = n - 3; k >= 0; --k) {
+            if (taus[k] == 0.0) continue;
+            // Qt <- Qt H_k: rows k+1..n-1, columns k+1..k+vl (the other columns of H_k
+            // are those of the identity): Qt -= tau (Qt v) v^T
+            const int m = n - k - 1, vl = vls[k];
+            const double *vk = &vs[(size_t)k * n];
+            for (int i = 0; i < m; ++i) {
+                const double *row = &Qt[(size_t)(k + 1 + i) * n + k + 1];
+                double s = 0.0;
+                for (int j = 0; j < vl; ++j) s += row[j] * vk[j];
+                w[i] = taus[k] * s;
             }
-            for (int i = 0; i < vl; ++i) {
-                double *row = &Qt[(size_t)(k + 1 + i) * n];
-                const double f = tau * v[i];
-                for (int c = 0; c < n; ++c) row[c] -= f * sc[c];
+            for (int i = 0; i < m; ++i) {
+                double *row = &Qt[(size_t)(k + 1 + i) * n + k + 1];
+                const double wi = w[i];
+                for (int j = 0; j < vl; ++j) row[j] -= wi * vk[j];
             }
         }
     }
