@@ -112,7 +112,7 @@ int plan_finish(bool harmonic, int m, int k, const std::vector<double> &T, doubl
     std::vector<double> &q = o.q, &s = o.s;
     // harmonic Ritz pairs: T_m g = mu (Tbar^T Tbar) g, theta = 1/mu, via the Cholesky
     // factor L of Tbar^T Tbar: C = L^-1 T_m L^-T, g = L^-T z
-    std::vector<double> M((size_t)m * m, 0.0), L((size_t)m * m), X((size_t)m * m), C((size_t)m * m), col(m);
+    std::vector<double> M((size_t)m * m, 0.0), L((size_t)m * m), X, C((size_t)m * m);
     // M = Tbar^T Tbar from the nonzeros of each row of Tbar (dense (k+1) block + band)
     for (int r = 0; r <= m; ++r) {
         const double *row = &T[(size_t)r * m];
@@ -126,16 +126,12 @@ int plan_finish(bool harmonic, int m, int k, const std::vector<double> &T, doubl
     if (!cholesky(m, M.data(), L.data())) return fail(DLZ_ERR_BREAKDOWN, "Tbar^T Tbar not positive definite");
     std::vector<int> env;
     envelope(m, L.data(), env);
-    for (int j = 0; j < m; ++j) {
-        for (int i = 0; i < m; ++i) col[i] = Tm[(size_t)i * m + j];
-        lower_solve(m, L.data(), col.data(), env.data());
-        for (int i = 0; i < m; ++i) X[(size_t)i * m + j] = col[i];
-    }
-    for (int j = 0; j < m; ++j) {
-        for (int i = 0; i < m; ++i) col[i] = X[(size_t)j * m + i];
-        lower_solve(m, L.data(), col.data(), env.data());
-        for (int i = 0; i < m; ++i) C[(size_t)i * m + j] = col[i];
-    }
+    // X = L^-1 T_m, then C = L^-1 X^T (all columns at once)
+    X = Tm;
+    lower_solve_rows(m, L.data(), X.data(), m, env.data());
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) C[(size_t)i * m + j] = X[(size_t)j * m + i];
+    lower_solve_rows(m, L.data(), C.data(), m, env.data());
     std::vector<double> mu(m), Zc((size_t)m * m);
     if (!sym_eig(m, C.data(), mu.data(), Zc.data())) return fail(DLZ_ERR_NONFINITE, "harmonic eigensolve failed");
     std::vector<int> idx(m);
@@ -152,14 +148,17 @@ int plan_finish(bool harmonic, int m, int k, const std::vector<double> &T, doubl
         j0[r] = a;
         j1[r] = b;
     }
-    std::vector<double> Gk((size_t)m * k);
+    // g = L^-T z for the k selected z (all at once), each normalised
+    std::vector<double> Gk((size_t)m * k), nr(k, 0.0);
+    for (int i = 0; i < m; ++i)
+        for (int l = 0; l < k; ++l) Gk[(size_t)i * k + l] = Zc[(size_t)i * m + idx[l]];
+    upper_t_solve_rows(m, L.data(), Gk.data(), k, env.data());
+    for (int i = 0; i < m; ++i)
+        for (int l = 0; l < k; ++l) nr[l] += Gk[(size_t)i * k + l] * Gk[(size_t)i * k + l];
+    for (int l = 0; l < k; ++l) nr[l] = std::sqrt(nr[l]);
+    for (int i = 0; i < m; ++i)
+        for (int l = 0; l < k; ++l) Gk[(size_t)i * k + l] /= nr[l];
     for (int l = 0; l < k; ++l) {
-        for (int i = 0; i < m; ++i) col[i] = Zc[(size_t)i * m + idx[l]];
-        upper_t_solve(m, L.data(), col.data(), env.data());
-        double nr = 0;
-        for (int i = 0; i < m; ++i) nr += col[i] * col[i];
-        nr = std::sqrt(nr);
-        for (int i = 0; i < m; ++i) Gk[(size_t)i * k + l] = col[i] / nr;
         o.theta[l] = 1.0 / mu[idx[l]];
         double r2 = 0;
         for (int r = 0; r <= m; ++r) {

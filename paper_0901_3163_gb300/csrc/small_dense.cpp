@@ -389,6 +389,35 @@ void upper_t_solve(int n, const double *L, double *b, const int *first_in) {
     }
 }
 
+void lower_solve_rows(int n, const double *L, double *B, int nrhs, const int *first) {
+    // row i of X = (row i of B - sum_k L[i][k] row k of X) / L[i][i]: per column the
+    // same operations, in the same order, as lower_solve
+    for (int i = 0; i < n; ++i) {
+        double *bi = B + (size_t)i * nrhs;
+        for (int k = first[i]; k < i; ++k) {
+            const double l = L[(size_t)i * n + k];
+            const double *bk = B + (size_t)k * nrhs;
+            for (int j = 0; j < nrhs; ++j) bi[j] -= l * bk[j];
+        }
+        const double d = L[(size_t)i * n + i];
+        for (int j = 0; j < nrhs; ++j) bi[j] /= d;
+    }
+}
+
+void upper_t_solve_rows(int n, const double *L, double *B, int nrhs, const int *first) {
+    for (int i = n - 1; i >= 0; --i) {
+        double *bi = B + (size_t)i * nrhs;
+        for (int k = i + 1; k < n; ++k) {
+            if (first[k] > i) continue;
+            const double l = L[(size_t)k * n + i];
+            const double *bk = B + (size_t)k * nrhs;
+            for (int j = 0; j < nrhs; ++j) bi[j] -= l * bk[j];
+        }
+        const double d = L[(size_t)i * n + i];
+        for (int j = 0; j < nrhs; ++j) bi[j] /= d;
+    }
+}
+
 template <typename S>
 static bool lu_factor_t(int n, S *A, int *piv) {
     for (int k = 0; k < n; ++k) {
@@ -429,19 +458,27 @@ void lu_solve(int n, const std::complex<double> *LU, const int *piv, std::comple
 }
 
 bool mgs_columns(int rows, int cols, double *P) {
+    // on a column-major copy, so that every column is contiguous
+    std::vector<double> Q((size_t)rows * cols);
+    for (int r = 0; r < rows; ++r)
+        for (int j = 0; j < cols; ++j) Q[(size_t)j * rows + r] = P[(size_t)r * cols + j];
     for (int j = 0; j < cols; ++j) {
+        double *pj = &Q[(size_t)j * rows];
         for (int pass = 0; pass < 2; ++pass)
             for (int i = 0; i < j; ++i) {
+                const double *pi = &Q[(size_t)i * rows];
                 double s = 0.0;
-                for (int r = 0; r < rows; ++r) s += P[(size_t)r * cols + i] * P[(size_t)r * cols + j];
-                for (int r = 0; r < rows; ++r) P[(size_t)r * cols + j] -= s * P[(size_t)r * cols + i];
+                for (int r = 0; r < rows; ++r) s += pi[r] * pj[r];
+                for (int r = 0; r < rows; ++r) pj[r] -= s * pi[r];
             }
         double nrm = 0.0;
-        for (int r = 0; r < rows; ++r) nrm += P[(size_t)r * cols + j] * P[(size_t)r * cols + j];
+        for (int r = 0; r < rows; ++r) nrm += pj[r] * pj[r];
         nrm = std::sqrt(nrm);
         if (!(nrm > 0.0)) return false;
-        for (int r = 0; r < rows; ++r) P[(size_t)r * cols + j] /= nrm;
+        for (int r = 0; r < rows; ++r) pj[r] /= nrm;
     }
+    for (int r = 0; r < rows; ++r)
+        for (int j = 0; j < cols; ++j) P[(size_t)r * cols + j] = Q[(size_t)j * rows + r];
     return true;
 }
 

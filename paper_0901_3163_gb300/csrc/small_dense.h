@@ -24,6 +24,10 @@ bool cholesky(int n, const double *A, double *L);
 void lower_solve(int n, const double *L, double *b, const int *first = nullptr);
 void upper_t_solve(int n, const double *L, double *b, const int *first = nullptr);
 void envelope(int n, const double *L, std::vector<int> &first);
+// The same solves for nrhs right-hand sides at once: B (n x nrhs, row-major) is
+// overwritten by L^-1 B / L^-T B (first: the envelope of L, required).
+void lower_solve_rows(int n, const double *L, double *B, int nrhs, const int *first);
+void upper_t_solve_rows(int n, const double *L, double *B, int nrhs, const int *first);
 bool lu_factor(int n, double *A, int *piv);
 void lu_solve(int n, const double *LU, const int *piv, double *b);
 bool lu_factor(int n, std::complex<double> *A, int *piv);
