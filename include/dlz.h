@@ -36,6 +36,14 @@
  * Errors: every call returns DLZ_OK (0) or a negative DLZ_ERR_* code; no
  * C++ exception crosses the ABI.  dlz_strerror() names a code,
  * dlz_last_error() gives the message of the last failure on this thread.
+ *
+ * Environment (read at the call; none changes a result):
+ *   DLZ_NO_GRAPHS=1   launch kernels one by one instead of replaying CUDA graphs
+ *                     (read when an operator is created);
+ *   DLZ_TRACE=1       per-cycle and per-phase timing lines on stderr;
+ *   DLZ_MULTI_TILE=1|2|4  fix the block tile of dlz_batch_dminres (chunks of 128
+ *                     sites per block) instead of choosing it by timed graph
+ *                     replays; every tile gives the same bits.
  */
 #ifndef DLZ_H
 #define DLZ_H
