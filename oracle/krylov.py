@@ -291,7 +291,8 @@ class DRResult:
 
 
 def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
-          full_reorth=False, residual=None, oversolve=1.0, eig_stop=None, progress=None):
+          full_reorth=False, residual=None, oversolve=1.0, eig_stop=None, progress=None,
+          plan_hook=None):
     """Lan-DR(m,k) for hermitian positive definite A (Sec. 1, Sec. 2).
 
     Cycle 1: x0 = 0, r0 = b, v1 = r0/||r0||, Lanczos to j = m.  Each cycle:
@@ -320,11 +321,13 @@ def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
     if reorth_period:
         reorth_period = 1
     return _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth,
-               residual, oversolve, harmonic=False, eig_stop=eig_stop, progress=progress)
+               residual, oversolve, harmonic=False, eig_stop=eig_stop, progress=progress,
+               plan_hook=plan_hook)
 
 
 def minresdr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
-             full_reorth=False, residual=None, oversolve=1.0, eig_stop=None, progress=None):
+             full_reorth=False, residual=None, oversolve=1.0, eig_stop=None, progress=None,
+             plan_hook=None):
     """MinRes-DR(m,k) for hermitian, possibly indefinite A (Sec. 1, Sec. 2).
 
     Same Lanczos and restart skeleton as Lan-DR, with (GMRES-DR read for a
@@ -342,7 +345,8 @@ def minresdr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=
     (eigenvalues of V_k^dag A V_k = top k x k block of Tbar_k); stopping as Lan-DR.
     """
     return _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth,
-               residual, oversolve, harmonic=True, eig_stop=eig_stop, progress=progress)
+               residual, oversolve, harmonic=True, eig_stop=eig_stop, progress=progress,
+               plan_hook=plan_hook)
 
 
 def _mgs_columns(P):
@@ -356,13 +360,76 @@ def _mgs_columns(P):
     return Q
 
 
+@dataclass
+class RestartPlan:
+    """The small FP64 problem at the end of one DR cycle (Sec. 1-2; readings in
+    the landr / minresdr docstrings), given Tbar_m ((m+1) x m) and c (m+1)."""
+    y: np.ndarray            # m: x += V_m y
+    theta: np.ndarray        # k kept (harmonic) Ritz values
+    G: np.ndarray            # m x k, their unit vectors in the V_m basis
+    ritz_res: np.ndarray     # k (harmonic) Ritz residuals
+    P: np.ndarray            # (m+1) x (k+1): V_{k+1} <- V_{m+1} P
+    Tn: np.ndarray           # (m+1) x m: the new Tbar (rows / columns < k+1 filled)
+    cn: np.ndarray           # m+1: the new c
+    rho: float = 0.0         # Lan-DR: the residual is rho v_{m+1}
+    s: np.ndarray | None = None   # MinRes-DR: c - Tbar_m y (the residual is V_{m+1} s)
+
+
+def restart_plan(T, c, m, k, harmonic):
+    """Galerkin solve and regular Ritz pairs (Lan-DR) or least squares and harmonic
+    Ritz pairs (MinRes-DR) of one cycle, and the restart matrices P, Tbar_k, c."""
+    Tm = T[:m, :m]
+    if not harmonic:
+        y = sla.solve(Tm, c[:m], assume_a="sym")
+        rho = -T[m, m - 1] * y[m - 1]
+        theta, G = np.linalg.eigh(Tm)
+        order = np.argsort(theta, kind="stable")[:k]
+        theta_k, G_k = theta[order], G[:, order]
+        ritz_res = np.abs(T[m, m - 1] * G_k[m - 1, :])
+        P = np.zeros((m + 1, k + 1))
+        P[:m, :k] = G_k
+        P[m, k] = 1.0
+        Tn = np.zeros((m + 1, m))
+        Tn[:k, :k] = np.diag(theta_k)
+        Tn[k, :k] = T[m, m - 1] * G_k[m - 1, :]
+        cn = np.zeros(m + 1)
+        cn[k] = rho
+        return RestartPlan(y=y, theta=theta_k, G=G_k, ritz_res=ritz_res, P=P, Tn=Tn, cn=cn, rho=rho)
+    y, *_ = np.linalg.lstsq(T, c, rcond=None)
+    s = c - T @ y
+    L = np.linalg.cholesky(T.T @ T)
+    Cm = sla.solve_triangular(L, sla.solve_triangular(L, Tm, lower=True).T, lower=True)
+    Cm = 0.5 * (Cm + Cm.T)
+    mu, Z = np.linalg.eigh(Cm)
+    g = sla.solve_triangular(L.T, Z, lower=False)
+    order = np.argsort(-np.abs(mu), kind="stable")[:k]
+    theta_k = 1.0 / mu[order]
+    G_k = g[:, order]
+    G_k = G_k / np.linalg.norm(G_k, axis=0)
+    Gpad = np.vstack([G_k, np.zeros((1, k))])
+    ritz_res = np.linalg.norm(T @ G_k - theta_k * Gpad, axis=0)
+    # s is orthogonal to range(Tbar_m); its direction is taken from the
+    # complete QR of Tbar_m so that it stays exact when ||s|| is tiny.
+    q = np.linalg.qr(T, mode="complete")[0][:, m]
+    if q @ s < 0:
+        q = -q
+    P = _mgs_columns(np.hstack([np.vstack([G_k, np.zeros((1, k))]), q[:, None]]))
+    Tk = P.T @ T @ P[:m, :k]
+    Tn = np.zeros((m + 1, m))
+    Tn[: k + 1, :k] = Tk
+    Tn[:k, :k] = 0.5 * (Tn[:k, :k] + Tn[:k, :k].T)
+    cn = np.zeros(m + 1)
+    cn[: k + 1] = P.T @ s
+    return RestartPlan(y=y, theta=theta_k, G=G_k, ritz_res=ritz_res, P=P, Tn=Tn, cn=cn, s=s)
+
+
 def _rayleigh_ritz(T, k):
     """Eigen-decomposition of the k x k block, for the reported values/residuals."""
     return np.linalg.eigh(T[:k, :k])
 
 
 def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residual,
-        oversolve, harmonic, eig_stop=None, progress=None):
+        oversolve, harmonic, eig_stop=None, progress=None, plan_hook=None):
     b = np.asarray(b, dtype=np.complex128)
     n = b.size
     bn = _norm(b)
@@ -394,31 +461,11 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
         else:
             tol_eig_abs = tol_eig
         Vs = stores[cur]            # (m+1) x n: the basis as rows, for the products below
-        if not harmonic:
-            y = sla.solve(Tm, c[:m], assume_a="sym")
-            x = x + y @ Vs[:m]
-            rho = -T[m, m - 1] * y[m - 1]
-            theta, G = np.linalg.eigh(Tm)
-            order = np.argsort(theta, kind="stable")[:k]
-            theta_k, G_k = theta[order], G[:, order]
-            ritz_res = np.abs(T[m, m - 1] * G_k[m - 1, :])
-            rnorm = abs(rho)
-        else:
-            y, *_ = np.linalg.lstsq(T, c, rcond=None)
-            x = x + y @ Vs[:m]
-            s = c - T @ y
-            rnorm = float(np.linalg.norm(s))
-            L = np.linalg.cholesky(T.T @ T)
-            Cm = sla.solve_triangular(L, sla.solve_triangular(L, Tm, lower=True).T, lower=True)
-            Cm = 0.5 * (Cm + Cm.T)
-            mu, Z = np.linalg.eigh(Cm)
-            g = sla.solve_triangular(L.T, Z, lower=False)
-            order = np.argsort(-np.abs(mu), kind="stable")[:k]
-            theta_k = 1.0 / mu[order]
-            G_k = g[:, order]
-            G_k = G_k / np.linalg.norm(G_k, axis=0)
-            Gpad = np.vstack([G_k, np.zeros((1, k))])
-            ritz_res = np.linalg.norm(T @ G_k - theta_k * Gpad, axis=0)
+        pl = restart_plan(T, c, m, k, harmonic)
+        if plan_hook is not None:
+            plan_hook(T, c, pl)
+        x = x + pl.y @ Vs[:m]
+        theta_k, G_k, ritz_res = pl.theta, pl.G, pl.ritz_res
         info.iterations = info.mvps
         rel = residual(x)
         info.residuals.append(rel)
@@ -441,34 +488,10 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             if done:
                 info.converged = True
         # restart (always performed so that V[:k] is the kept space on exit)
-        if not harmonic:
-            P = np.zeros((m + 1, k + 1))
-            P[:m, :k] = G_k
-            P[m, k] = 1.0
-            nxt = stores[1 - cur]
-            np.matmul(P.T.astype(np.complex128), Vs, out=nxt[: k + 1])
-            Vnew = [nxt[i] for i in range(k + 1)]
-            Tn = np.zeros((m + 1, m))
-            Tn[:k, :k] = np.diag(theta_k)
-            Tn[k, :k] = T[m, m - 1] * G_k[m - 1, :]
-            cn = np.zeros(m + 1)
-            cn[k] = rho
-        else:
-            # s is orthogonal to range(Tbar_m); its direction is taken from the
-            # complete QR of Tbar_m so that it stays exact when ||s|| is tiny.
-            q = np.linalg.qr(T, mode="complete")[0][:, m]
-            if q @ s < 0:
-                q = -q
-            P = _mgs_columns(np.hstack([np.vstack([G_k, np.zeros((1, k))]), q[:, None]]))
-            nxt = stores[1 - cur]
-            np.matmul(P.T.astype(np.complex128), Vs, out=nxt[: k + 1])
-            Vnew = [nxt[i] for i in range(k + 1)]
-            Tk = P.T @ T @ P[:m, :k]
-            Tn = np.zeros((m + 1, m))
-            Tn[: k + 1, :k] = Tk
-            Tn[:k, :k] = 0.5 * (Tn[:k, :k] + Tn[:k, :k].T)
-            cn = np.zeros(m + 1)
-            cn[: k + 1] = P.T @ s
+        nxt = stores[1 - cur]
+        np.matmul(pl.P.T.astype(np.complex128), Vs, out=nxt[: k + 1])
+        Vnew = [nxt[i] for i in range(k + 1)]
+        Tn, cn = pl.Tn, pl.cn
         if not full_reorth and reorth_period:
             # The vector carried across the restart (v_{m+1} -> v_{k+1}) is part
             # of the periodic re-orthogonalisation over the kept vectors (Sec. 2);
