@@ -346,6 +346,15 @@ int dlz_seed_deflation(dlz_op_t op, int which, const void *vecs, int dtype, int 
  *   dlz_host_sym_extremes: the smallest (lo) and largest (hi) eigenvalue of a
  *     real symmetric A (Householder tridiagonalisation + Sturm-sequence
  *     bisection to the spacing of doubles); DLZ_ERR_NONFINITE on non-finite A.
+ *   dlz_host_restart_plan: the small problem at the end of one Lan-DR
+ *     (harmonic = 0) or MinRes-DR (harmonic = 1) cycle, as the solvers run it
+ *     (Sec. 1-2).  In: Tbar ((m+1) x m, the Lanczos matrix of the cycle: after a
+ *     restart a dense leading (k+1) x k block, then the band) and c (m+1, the
+ *     residual's coefficients in the basis V_{m+1}).  Out: y[m] (x += V_m y),
+ *     P[(m+1) x (k+1)] (V_{k+1} <- V_{m+1} P), Tn[(m+1) x m] and cn[m+1] (Tbar
+ *     and c of the next cycle), theta[k] and ritz_res[k] (the kept regular or
+ *     harmonic Ritz values and residuals); *anorm becomes
+ *     max(*anorm, max |eig T_m|).  Needs 2 <= m, 1 <= k < m.
  *   dlz_host_lstsq: y = argmin ||c - T y|| for T (rows x cols, rows > cols,
  *     full column rank) by Householder QR; q[rows] receives the unit
  *     vector spanning the orthogonal complement of range(T) when rows == cols + 1
@@ -354,6 +363,8 @@ int dlz_seed_deflation(dlz_op_t op, int which, const void *vecs, int dtype, int 
 int dlz_host_symeig(int n, const double *A, double *w, double *Z);
 int dlz_host_sym_extremes(int n, const double *A, double *lo, double *hi);
 int dlz_host_lstsq(int rows, int cols, const double *T, const double *c, double *y, double *q);
+int dlz_host_restart_plan(int harmonic, int m, int k, const double *Tbar, const double *c, double *y, double *P,
+                          double *Tn, double *cn, double *theta, double *ritz_res, double *anorm);
 
 #ifdef __cplusplus
 }

@@ -107,6 +107,7 @@ _SIGS = {
     "dlz_host_symeig": ([_ip, _vp, _vp, _vp], _ip),
     "dlz_host_sym_extremes": ([_ip, _vp, _vp, _vp], _ip),
     "dlz_host_lstsq": ([_ip, _ip, _vp, _vp, _vp, _vp], _ip),
+    "dlz_host_restart_plan": ([_ip, _ip, _ip, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _ip),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -460,6 +461,22 @@ def host_sym_extremes(A):
     lo, hi = ctypes.c_double(), ctypes.c_double()
     _check(lib.dlz_host_sym_extremes(A.shape[0], A.ctypes.data, ctypes.byref(lo), ctypes.byref(hi)))
     return lo.value, hi.value
+
+
+def host_restart_plan(T, c, k, harmonic, anorm=0.0):
+    """dlz_host_restart_plan on Tbar ((m+1) x m) and c; returns a dict of y, P, Tn,
+    cn, theta, ritz_res, anorm."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    m = T.shape[1]
+    out = dict(y=np.empty(m), P=np.empty((m + 1, k + 1)), Tn=np.empty((m + 1, m)), cn=np.empty(m + 1),
+               theta=np.empty(k), ritz_res=np.empty(k))
+    an = ctypes.c_double(anorm)
+    _check(lib.dlz_host_restart_plan(int(bool(harmonic)), m, k, T.ctypes.data, c.ctypes.data,
+                                     *(out[key].ctypes.data for key in ("y", "P", "Tn", "cn", "theta", "ritz_res")),
+                                     ctypes.byref(an)))
+    out["anorm"] = an.value
+    return out
 
 
 def host_lstsq(T, c):
