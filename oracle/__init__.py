@@ -11,7 +11,9 @@ Nicely, Wilcox) where the paper fixes the method:
   cwilson -- the same Wilson matrix as plain C loops (speed for big lattices);
   krylov  -- CG and MinRes (Sec. 1), the Lanczos recurrence, Lan-DR(m,k) and
              MinRes-DR(m,k) (Sec. 1, Sec. 2), D-CG and D-MinRes (Sec. 2);
-  kappa   -- the kappa rule of the synthetic workloads (min|eig(gamma5 M)|).
+  kappa   -- the kappa rule of the synthetic workloads (min|eig(gamma5 M)|);
+  evenodd -- the even-odd (Schur complement) form of M on the even sites (not
+             in the paper; the standard reduction the deflated methods apply to).
 
 The paper defers the definition of the four deflated algorithms to its
 ref. [3]; what is written here is the standard thick-restart reading
