@@ -138,6 +138,21 @@ def workload_inputs(kappa=None):
     return w, dims, U, kappa, B
 
 
+def workload_params(dlz, w, pr):
+    """Solver parameters of one benchmark step (first RHS, then the other 11).
+
+    First RHS: DR_CYCLES MinRes-DR(100,40) restart cycles (run past linear convergence
+    so that the 40 harmonic Ritz vectors converge), then D-MinRes from that x over the
+    40 vectors; the same schedule in both forms.  Re-orthogonalisation against the kept
+    vectors every 30 Lanczos steps (the paper gives no period): 5% faster per step than
+    every 10, same D-MinRes iterations."""
+    p_dr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=DR_CYCLES, check_every=16,
+                              precision=pr, oversolve=1e9, finish=1, reorth_period=30)
+    p_d = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=200000, precision=pr,
+                             check_every=16)
+    return p_dr, p_d
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -159,16 +174,7 @@ def run_ours(args):
     prec = dlz.F32 if args.form == "chosen" else dlz.F64
 
     def params(pr):
-        # first RHS: DR_CYCLES MinRes-DR(100,40) restart cycles (run past linear
-        # convergence so that the 40 harmonic Ritz vectors converge), then D-MinRes
-        # from that x over the 40 vectors; the same schedule in both forms
-        # re-orthogonalisation against the kept vectors every 30 Lanczos steps (the paper
-        # gives no period): 5% faster per step than every 10, same D-MinRes iterations
-        p_dr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=DR_CYCLES, check_every=16,
-                                  precision=pr, oversolve=1e9, finish=1, reorth_period=30)
-        p_d = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=200000, precision=pr,
-                                 check_every=16)
-        return p_dr, p_d
+        return workload_params(dlz, w, pr)
 
     pars = params(prec)
 
