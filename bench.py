@@ -1,18 +1,25 @@
 """Benchmark: right-hand sides solved per second to ||b - D x|| / ||b|| < 1e-10.
 
-Workload (one step): the 16^3x32 Wilson lattice with SU(3) links
-U = exp(0.3 i H) (gauge seed 2) at the kappa where min|eig(gamma5 D)| = 1e-3;
-MinRes-DR(100,40) on the point source at the origin (spin 0, colour 0), then
-D-MinRes on the other 11 spin-colour point sources (arXiv:0901.3163, Sec. 2
-method on a synthetic stand-in for its quenched lattice).  Every right-hand
-side counts only if its true residual was verified in FP64.
+Workload of one step (the default line): the 24^3x48 Wilson lattice with SU(3)
+links U = exp(0.3 i H) (gauge seed 3) at the kappa where min|eig(gamma5 D)| = 1e-3;
+Lan-DR(120,60) on D^dagger D for the first Gaussian right-hand side (seed 0), then
+D-CG on 48 Gaussian right-hand sides (seeds 1..48) (arXiv:0901.3163, Sec. 2 method
+on a synthetic stand-in for its quenched lattice): 49 right-hand sides per step.
+A right-hand side counts only if its true residual was verified in FP64.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--form chosen|plain]
-                    [--plain-steps P] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-`value` is the chosen form (FP32 Lanczos/MinRes with FP64 defect correction,
-right-hand sides batched); the plain FP64 form (one RHS at a time, FP64
-stencil) is timed beside it on the same operator (`plain_fp64`).
+`value` is the chosen form: FP32 Lanczos and FP32 CG on the normal equations
+(fused stencil kernels, 16 right-hand sides per launch) inside FP64 defect
+correction, FP64 for x, the true residual, the deflation projection and the small
+eigenproblem.  Beside it on the same operator:
+  plain_fp64  the plain FP64 form (FP64 Lan-DR, then D-CG one right-hand side at a
+              time, FP64 stencil), the first right-hand side in full and D-CG on a
+              sample of right-hand sides, extrapolated to 48;
+  c4          64 lattices of uneven size (8^4, 12^4, 16^4), D-MinRes on 8 RHS each,
+              all lattices in one batched call, against lattice by lattice and FP64;
+  c2          the 16^3x32 workload (MinRes-DR(100,40) + D-MinRes on 12 point sources);
+  dslash      the Wilson stencil alone (FP32 and bfloat16, 16 RHS per launch).
 
 Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) solve independent
 replicas of the workload, one per rank, with no collective on the data path.
@@ -31,18 +38,24 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "wilson_16x16x16x32"
-# restart cycles of the first right-hand side's MinRes-DR phase (both forms)
-DR_CYCLES = 150
-# MVPs per right-hand side of the FP64 form of the workload (150 MinRes-DR(100,40)
-# cycles + finish: 13968 MVPs; D-MinRes: 7648 each for the other 11), the unit the
-# oracle's timing is extrapolated with when no FP64 GPU run is at hand
-REF_MVPS_PER_RHS = 8175
-# DRAM bytes (read + write) of one k_minres_k1 launch with 11 right-hand sides on the
-# 16^3x32 lattice, from one ncu capture of the current kernel
-# (ncu --set full -k regex:k_minres_k1 -s 24 -c 1 python bench.py --ncu-case)
-K1_TRAFFIC_BYTES = 745467648 + 376429824
-METRIC = "RHS solved/s to |r|/|b|<1e-10 (MinRes-DR(100,40) + D-MinRes, 12 point sources, 16^3x32)"
+WORKLOAD = "wilson_24x24x24x48"
+C2 = "wilson_16x16x16x32"
+C4 = "uneven_64"
+# restart cycles of the 16^3x32 first right-hand side's MinRes-DR phase (both forms)
+C2_DR_CYCLES = 150
+# D-CG iterations per right-hand side of the FP64 form on the 24^3x48 workload, and
+# the MVPs of its first right-hand side (FP64 Lan-DR(120,60) with its D-CG finish):
+# the oracle runs the same FP64 algorithm but cannot finish this lattice in a bounded
+# sample, so the reference arm extrapolates its seconds per iteration with these counts
+# (taken from an FP64 run of the library on this workload; bench.py reports the counts
+# of its own FP64 run in plain_fp64)
+REF_ITERS_PER_RHS = 4400
+REF_FIRST_RHS_MVPS = 10000
+# DRAM bytes (read + write) of one k_cg_k23 launch (16 RHS, 24^3x48) from the ncu
+# capture summarised in profiles/k_cg_k23_wilson_24x24x24x48_n16.md; None until taken
+# for the current kernel
+K23_TRAFFIC_BYTES = None
+METRIC = "RHS solved/s to |r|/|b|<1e-10 (Lan-DR(120,60) + D-CG, 49 Gaussian RHS, 24^3x48)"
 UNIT = "RHS/s"
 
 
@@ -88,23 +101,28 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax = float(f[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        sm.sort()
-        med = sm[len(sm) // 2] if sm else None
-        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+        return parse_clock_lines(self.lines)
+
+
+def parse_clock_lines(lines):
+    """Median SM clock, max clock and the throttle reasons seen in nvidia-smi CSV lines."""
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax = float(f[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    sm.sort()
+    med = sm[len(sm) // 2] if sm else None
+    return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def aggregate_ranks(ms, solved, world, device):
@@ -122,35 +140,83 @@ def aggregate_ranks(ms, solved, world, device):
     return float(mx[0]), float(t[1])
 
 
-def workload_inputs(kappa=None):
+def workload_inputs(kappa=None, name=WORKLOAD):
+    """Links, kappa and right-hand sides of a named workload (synth.WORKLOADS).
+    24^3x48: B[0] is the first RHS (seed 0), B[1:] the 48 D-CG RHS.
+    16^3x32: the 12 spin-colour point sources at the origin."""
     import numpy as np
 
     import synth
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[name]
     dims = w["dims"]
     U = synth.su3_links(dims, w["gauge_seed"])
     if kappa is None:
         kappa = synth.kappa_for(dims, w["gauge_seed"])
     V = synth.volume(dims)
-    B = np.zeros((12, V, 4, 3), dtype=np.complex128)
-    for a in range(12):
-        B[a] = synth.point_source(dims, a // 3, a % 3)
+    if "point_sources" in w:
+        B = np.zeros((12, V, 4, 3), dtype=np.complex128)
+        for a in range(12):
+            B[a] = synth.point_source(dims, a // 3, a % 3)
+    else:
+        B = synth.gaussian_spinors(dims, (w["first_rhs_seed"],) + tuple(w["rhs_seeds"]))
     return w, dims, U, kappa, B
 
 
-def workload_params(dlz, w, pr):
-    """Solver parameters of one benchmark step (first RHS, then the other 11).
+def workload_params(dlz, w, pr, name=WORKLOAD):
+    """Solver parameters of one benchmark step (first RHS, then the others).
 
-    First RHS: DR_CYCLES MinRes-DR(100,40) restart cycles (run past linear convergence
-    so that the 40 harmonic Ritz vectors converge), then D-MinRes from that x over the
-    40 vectors; the same schedule in both forms.  Re-orthogonalisation against the kept
-    vectors every 30 Lanczos steps (the paper gives no period): 5% faster per step than
-    every 10, same D-MinRes iterations."""
-    p_dr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=DR_CYCLES, check_every=16,
-                              precision=pr, oversolve=1e9, finish=1, reorth_period=30)
+    24^3x48: Lan-DR(120,60) until the linear residual and the kept Ritz residuals
+    converge (FP32 form: then D-CG from x over the 60 vectors), D-CG with FP64
+    defect correction (inner reduction 1e-2).
+    16^3x32: C2_DR_CYCLES MinRes-DR(100,40) restart cycles (run past linear
+    convergence so that the 40 harmonic Ritz vectors converge), then D-MinRes from
+    that x over the 40 vectors; re-orthogonalisation against the kept vectors every 30
+    Lanczos steps (the paper gives no period)."""
+    if name == C2:
+        p_dr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=C2_DR_CYCLES, check_every=16,
+                                  precision=pr, oversolve=1e9, finish=1, reorth_period=30)
+    else:
+        p_dr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=400, check_every=16,
+                                  precision=pr, finish=1)
     p_d = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=200000, precision=pr,
                              check_every=16)
     return p_dr, p_d
+
+
+def solve_step(dlz, op, b0, rest, pars, minres, host=None, profile=False):
+    """One step: the first right-hand side by Lan-DR (MinRes-DR), the others by D-CG
+    (D-MinRes) over its deflation set.  Returns (verified solves, stats of every RHS)."""
+    p_dr, p_d = pars
+    p_dr.profile = p_d.profile = int(profile)
+    dr = dlz.minresdr if minres else dlz.landr
+    ds = dlz.dminres if minres else dlz.dcg
+    if host is None:
+        x0, defl, st = dr(op, b0, p_dr)
+        X, sts = ds(op, defl, rest, p_d)
+    else:
+        hb0, hrest, hx0, hX = host
+        x0, defl, st = dr(op, hb0, p_dr, x=hx0)
+        X, sts = ds(op, defl, hrest, p_d, X=hX)
+    allst = [st] + list(sts)
+    ok = sum(1 for s in allst if s.converged == 1 and s.true_residual <= 1e-10)
+    return ok, allst
+
+
+def kernel_roofline(stats, tag, peaks, src, name, traffic=None, traffic_src=None):
+    """Roofline of one fused kernel kind from the profiled stats (CUDA events on the
+    launching stream): algorithmic bytes per launch / average launch time."""
+    ms = sum(s.kernel_ms[tag] for s in stats)
+    nb = sum(s.kernel_bytes[tag] for s in stats)
+    n = sum(s.kernel_launches[tag] for s in stats)
+    if n == 0 or ms <= 0:
+        return None
+    avg = ms / n
+    bpl = nb / n
+    ach = bpl / (avg * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(ach / peaks["hbm_gbs"], 4), "peak_source": src, "kernel": name,
+            "avg_launch_ms": round(avg, 5), "launches_timed": int(n), "bytes_per_launch": int(bpl),
+            "traffic": traffic, "traffic_source": traffic_src}
 
 
 def run_ours(args):
@@ -167,30 +233,12 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w, dims, U, kappa, B = workload_inputs()
+    w, dims, U, kappa, B = workload_inputs(args.kappa)
+    nrhs = B.shape[0]
     op = dlz.create_operator(dims, torch.from_numpy(U).to(dev), kappa)
     Bd = torch.from_numpy(B).to(dev)
     b0, rest = Bd[0].contiguous(), Bd[1:].contiguous()
-    prec = dlz.F32 if args.form == "chosen" else dlz.F64
-
-    def params(pr):
-        return workload_params(dlz, w, pr)
-
-    pars = params(prec)
-
-    def step(profile=False, host=None, pp=None):
-        p_dr, p_d = pp or pars
-        p_dr.profile = p_d.profile = int(profile)
-        if host is None:
-            x0, defl, st = dlz.minresdr(op, b0, p_dr)
-            X, sts = dlz.dminres(op, defl, rest, p_d)
-        else:
-            hb0, hrest, hx0, hX = host
-            x0, defl, st = dlz.minresdr(op, hb0, p_dr, x=hx0)
-            X, sts = dlz.dminres(op, defl, hrest, p_d, X=hX)
-        allst = [st] + list(sts)
-        ok = sum(1 for s in allst if s.converged == 1 and s.true_residual <= 1e-10)
-        return ok, allst
+    pars = workload_params(dlz, w, dlz.F32)
 
     def barrier():
         if world > 1:
@@ -199,7 +247,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        step()
+        solve_step(dlz, op, b0, rest, pars, False)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -209,17 +257,32 @@ def run_ours(args):
     solved = 0
     stats = []
     for _ in range(args.steps):
-        ok, allst = step()
+        ok, allst = solve_step(dlz, op, b0, rest, pars, False)
         solved += ok
         stats.extend(allst)
     e1.record()
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    # one more step with every stencil launch timed by CUDA events (roofline only)
-    _, pstats = step(profile=True)
     ms_max, solved_all = aggregate_ranks(ms, solved, world, dev)
     value = solved_all / (ms_max / 1e3)
+    peaks, src = _peaks()
+    # roofline: one more pass of the D-CG phase (16 RHS, one launch group) with every
+    # fused stencil launch bracketed by CUDA events; the timed steps carry no events
+    p_dr, p_d = pars
+    _, defl, _ = dlz.landr(op, b0, p_dr)
+    p_d.profile = 1
+    _, pst = dlz.dcg(op, defl, rest[:16].contiguous(), p_d)
+    p_d.profile = 0
+    del defl
+    roof = kernel_roofline(pst, 2, peaks, src,
+                           "k_cg_k23 (fused FP32 CGNR: s - alpha t gathered, D^dag stencil, e += alpha p; 16 RHS per launch)",
+                           args.k23_traffic,
+                           "ncu capture of the current kernel (profiles/)" if args.k23_traffic else
+                           "not captured for the current kernel")
+    roof_k1 = kernel_roofline(pst, 1, peaks, src, "k_cg_k1 (fused FP32 CGNR: r + beta p gathered, D stencil; 16 RHS)")
+    it_ms = sum(s.kernel_ms[1] + s.kernel_ms[2] for s in pst)
+    it_b = sum(s.kernel_bytes[1] + s.kernel_bytes[2] for s in pst)
     # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -230,114 +293,60 @@ def run_ours(args):
         barrier()
         t0 = time.perf_counter()
         e2e_solved = 0
-        for _ in range(max(1, args.steps)):
-            ok, _ = step(host=(hb0, hrest, hx0, hX))
+        for _ in range(max(1, args.e2e_steps)):
+            ok, _ = solve_step(dlz, op, b0, rest, pars, False, host=(hb0, hrest, hx0, hX))
             e2e_solved += ok
         barrier()
         e2e_s = time.perf_counter() - t0
-        e2e_value = e2e_solved / e2e_s * world
-        e2e = {"value": round(e2e_value, 4), "unit": UNIT,
-               "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(B.nbytes)}
-    # roofline of the dominant kernel (the Wilson stencil), timed with events inside the steps
-    # the dominant kernel is the stencil of the deflated phase (all 11 right-hand sides
-    # batched into each launch in the mixed form); the first-RHS phase is reported apart
-    dstats = pstats[1:]
-    st_ms = sum(s.stencil_ms for s in dstats)
-    st_n = sum(s.stencil_launches for s in dstats)
-    st_bytes = sum(s.stencil_bytes for s in dstats)
-    avg_ms = st_ms / max(st_n, 1)
-    bytes_per_launch = st_bytes / max(st_n, 1)
-    # flops: 1368 per site and right-hand side (bytes / reals-per-site gives site-RHS pairs)
-    real = 8 if prec == dlz.F64 else 4
-    peaks, src = _peaks()
-    if prec == dlz.F64:
-        # FP64 stencil, one right-hand side per launch: 1368 flops per 960 bytes is past
-        # the ridge of GB300's FP64 pipe, so the roofline is the FP64 ALU rate
-        nflops = bytes_per_launch / (120 * real) * 1368
-        peak = 1.25
-        roof = {"bound": "alu", "achieved": round(nflops / (avg_ms * 1e-3) / 1e12, 4),
-                "peak": peak, "unit": "TFLOP/s FP64",
-                "frac": round(nflops / (avg_ms * 1e-3) / 1e12 / peak, 4),
-                "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); measured FMA probe 1.01 at 1987 MHz",
-                "hbm_gbs": round(bytes_per_launch / (avg_ms * 1e-3) / 1e9, 1),
-                "traffic": None, "kernel": "k_wilson<double>", "avg_launch_ms": round(avg_ms, 5),
-                "bytes_per_launch": int(bytes_per_launch)}
-    else:
-        # the fused MinRes kernel K1 (Q stencil + update epilogue, 11 right-hand sides per
-        # launch): 192 spinor reals per site and RHS + 48 link reals per site, FP32
-        ach = bytes_per_launch / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(ach / peaks["hbm_gbs"], 4), "peak_source": src,
-                "traffic": args.k1_traffic,
-                "kernel": "k_minres_k1 (fused FP32 Q stencil + MinRes update, 11 RHS per launch)",
-                "avg_launch_ms": round(avg_ms, 5), "launches_timed": int(st_n),
-                "bytes_per_launch": int(bytes_per_launch)}
-    dr_s = sum(s.seconds for s in stats[0::12]) / max(args.steps, 1)
-    d_s = sum(s.seconds for i, s in enumerate(stats) if i % 12) / max(args.steps, 1)
-    launches = sum(s.gpu_launches for s in stats)      # all timed steps (this library's kernels)
+        e2e = {"value": round(e2e_solved / e2e_s * world, 4), "unit": UNIT,
+               "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(B.nbytes),
+               "steps": max(1, args.e2e_steps)}
+        del hb0, hrest, hx0, hX
+    dr_s = sum(s.seconds for s in stats[0::nrhs]) / max(args.steps, 1)
+    d_s = sum(s.seconds for i, s in enumerate(stats) if i % nrhs) / max(args.steps, 1)
+    launches = sum(s.gpu_launches for s in stats)
     mvps = sum(s.mvps for s in stats) // max(args.steps, 1)
-    iters = [s.iterations for s in stats[:12]]
-    extra = {}
-    if args.form == "chosen" and args.plain_steps > 0:
-        # the plain FP64 form on the same operator: one RHS at a time, FP64 stencil
-        pp = params(dlz.F64)
-        # warm-up of the FP64 kernels: two restart cycles and a short D-MinRes
-        wdr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=2, precision=dlz.F64)
-        _, wd, _ = dlz.minresdr(op, b0, wdr)
-        dlz.dminres(op, wd, rest[:1].contiguous(), dlz.params_default(max_iter=32, precision=dlz.F64))
-        del wd
-        barrier()
-        t0 = time.perf_counter()
-        solved_p = 0
-        pst = []
-        for _ in range(args.plain_steps):
-            ok, allst = step(pp=pp)
-            solved_p += ok
-            pst.extend(allst)
-        barrier()
-        el = time.perf_counter() - t0
-        plain_mvps = sum(s.mvps for s in pst) // args.plain_steps
-        extra["plain_fp64"] = {"value": round(solved_p / el, 4), "unit": UNIT, "steps": args.plain_steps,
-                               "warmup": "2 restart cycles + 32 D-MinRes iterations",
-                               "ms_per_step": round(el / args.plain_steps * 1e3, 1),
-                               "mvps_per_step": int(plain_mvps),
-                               "iterations_first_steps": [s.iterations for s in pst[:12]]}
-        extra["chosen_over_plain"] = round(value / (solved_p / el), 3)
-    # the Wilson stencil alone (Dslash), as the solvers launch it
-    V = int(np.prod(dims))
-    ds = {}
-    for name, dt, nrhs in (("f32_batch11", torch.complex64, 11), ("f64_single", torch.complex128, 1)):
-        xs = torch.randn((nrhs, V, 4, 3), dtype=dt, device=dev)
-        ms_l = dlz.stencil_bench(op, xs, 50)["ms"]
-        real = 4 if dt == torch.complex64 else 8
-        nb = V * (48 * nrhs + (48 if real == 4 else 72)) * real
-        ds[name] = {"avg_launch_ms": round(ms_l, 5), "gbs": round(nb / (ms_l * 1e-3) / 1e9, 1),
-                    "frac_hbm": round(nb / (ms_l * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
-        del xs
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == dlz.F64 else "f32+f64",
-        "data": "synthetic (seeded SU(3) links exp(0.3iH), point sources)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded SU(3) links exp(0.3iH), seeded complex Gaussian RHS)",
         "config": {"workload": WORKLOAD, "lattice": list(dims), "kappa": kappa, "m": w["m"], "k": w["k"],
-                   "rhs": 12, "form": args.form, "tol": 1e-10,
-                   "l2": "inputs and Krylov basis (2.5 GB) larger than L2; no flush",
-                   "first_rhs": f"{DR_CYCLES} MinRes-DR cycles, then D-MinRes from x",
+                   "rhs": nrhs, "form": "chosen (FP32 inner, FP64 outer)", "tol": 1e-10,
+                   "l2": "inputs and Krylov basis (121 x 63.7 MB FP32) larger than L2; no flush",
+                   "first_rhs": "Lan-DR(120,60) on D^dag D to convergence, then D-CG from x",
+                   "d_phase": "D-CG on 48 RHS, 16 per launch, FP64 defect correction",
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e,
         "gpu_launches": int(launches), "gpu_launches_per_step": int(launches // max(args.steps, 1)),
         "library_kernels": "cuBLAS SGEMM for the restart V P (3 kernels per restart, not counted above)",
-        "mvps_per_step": int(mvps), "iterations_first_steps": iters,
-        "phase_seconds": {"first_rhs_dr": round(dr_s, 4), "deflated_11_rhs": round(d_s, 4)},
-        "d_phase_rhs_per_s": round(11.0 / d_s, 4) if d_s > 0 else None,
-        "roofline": roof, "dslash": ds, "clocks": clk,
+        "mvps_per_step": int(mvps), "iterations_first_steps": [s.iterations for s in stats[:4]],
+        "phase_seconds": {"first_rhs_dr": round(dr_s, 4), "deflated_48_rhs": round(d_s, 4)},
+        "d_phase_rhs_per_s": round((nrhs - 1) / d_s, 4) if d_s > 0 else None,
+        "roofline": roof, "roofline_k_cg_k1": roof_k1,
+        "cg_iteration_hbm_gbs": round(it_b / (it_ms * 1e-3) / 1e9, 1) if it_ms > 0 else None,
+        "clocks": clk,
     }
-    out.update(extra)
+    if args.plain_rhs > 0:
+        out["plain_fp64"] = plain_fp64(dlz, op, b0, rest, w, args.plain_rhs, nrhs, value)
+        out["chosen_over_plain"] = out["plain_fp64"].pop("_ratio")
+    out["dslash"] = dslash_lines(dlz, torch, op, dims, peaks)
+    del op
+    torch.cuda.empty_cache()
+    if not args.no_evenodd:
+        out["evenodd"] = run_evenodd(dlz, torch, w, dims, U, kappa, Bd, peaks, src, pars)
+    del Bd, b0, rest
+    torch.cuda.empty_cache()
+    if not args.no_c4:
+        out["c4"] = run_c4(dlz, torch, args.c4_lattices)
+    if not args.no_c2:
+        out["c2"] = run_c2(dlz, torch, peaks, src)
     if rank == 0 and not args.no_cpu_baseline:
-        # the oracle runs the FP64 algorithm: extrapolate to the FP64 form's MVP count
-        ref_mvps = extra.get("plain_fp64", {}).get("mvps_per_step", REF_MVPS_PER_RHS * 12)
-        out["cpu_baseline"] = cpu_baseline(ref_mvps, budget_s=args.cpu_seconds)
+        pf = out.get("plain_fp64", {})
+        out["cpu_baseline"] = cpu_baseline(pf.get("dcg_iterations_mean", REF_ITERS_PER_RHS),
+                                           pf.get("first_rhs_mvps", REF_FIRST_RHS_MVPS),
+                                           nrhs, budget_s=args.cpu_seconds,
+                                           source="this run's FP64 form" if pf else "constants in bench.py")
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -345,83 +354,313 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(mvps_per_step, budget_s=20.0):
-    """The FP64 oracle as it stands, on a bounded sample of the same workload:
-    MinRes-DR(100,40) cycles on the 16^3x32 lattice for about `budget_s` seconds;
-    the RHS/s figure extrapolates its seconds per MVP (Lanczos steps, restarts and
-    residual checks included) to the MVPs one step of the workload needs."""
+def run_evenodd(dlz, torch, w, dims, U, kappa, Bd, peaks, src, pars):
+    """The same step through the even-odd operator (not in the paper; the standard Schur
+    reduction the deflated methods apply to unchanged): b_e' = b_e + kappa H_eo b_o for
+    all 49 RHS, Lan-DR(120,60) on Dhat^dag Dhat for the first, D-CG on Dhat^dag Dhat for
+    the 48 others over its deflation set (FP32 inner, FP64 outer, as the chosen form),
+    then x_o = b_o + kappa H_oe x_e.  The even-site system stops at 0.5e-10 relative
+    residual: the odd rows of D x = b hold exactly, so ||b - D x|| = ||b_e' - Dhat x_e||,
+    and ||b_e'|| / ||b|| (reported) stays below 2, which keeps the full relative
+    residual below 1e-10.  One warm-up step, one timed step (CUDA events on the
+    operator's stream, prepare and reconstruct included)."""
+    op = dlz.create_operator_eo(dims, torch.from_numpy(U).cuda(), kappa)
+    p_dr, p_d = pars
+    p_dr = dlz.params_default(**{f: getattr(p_dr, f) for f, _ in p_dr._fields_})
+    p_d = dlz.params_default(**{f: getattr(p_d, f) for f, _ in p_d._fields_})
+    p_dr.tol = p_d.tol = 0.5e-10
+    nrhs = Bd.shape[0]
+
+    def step(profile=False):
+        p_dr.profile = p_d.profile = int(profile)
+        Be = dlz.eo_prepare(op, Bd)
+        xe0, defl, st = dlz.landr(op, Be[0].contiguous(), p_dr)
+        Xe, sts = dlz.dcg(op, defl, Be[1:].contiguous(), p_d)
+        X = dlz.eo_reconstruct(op, torch.cat([xe0[None], Xe]).contiguous(), Bd)
+        allst = [st] + list(sts)
+        ok = sum(1 for s in allst if s.converged == 1 and s.true_residual <= 0.5e-10)
+        return ok, allst, X, Be
+
+    ok, _, X, Be = step()
+    bn = torch.linalg.vector_norm(Bd.reshape(nrhs, -1), dim=1)
+    ben = torch.linalg.vector_norm(Be.reshape(nrhs, -1), dim=1)
+    ratio = float((ben / bn).max())
+    del X, Be
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ok, allst, X, Be = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    del X, Be
+    _, pst, X, Be = step(profile=True)
+    del X, Be
+    roof = kernel_roofline(pst[1:], 2, peaks, src, "k_eo_hop<float> + k_cg_eo_k23b (even-odd fused CGNR, 16 RHS)")
+    roof1 = kernel_roofline(pst[1:], 1, peaks, src, "k_eo_hop<float> + k_cg_eo_k1b (even-odd fused CGNR, 16 RHS)")
+    out = {"workload": WORKLOAD + " (even-odd)", "value": round(ok / (ms / 1e3), 4), "unit": UNIT,
+           "ms_per_step": round(ms, 1), "solved": ok, "even_rhs_norm_ratio_max": round(ratio, 4),
+           "tol_even_system": 0.5e-10,
+           "phase_seconds": {"first_rhs_dr": round(allst[0].seconds, 4),
+                             "deflated_48_rhs": round(sum(s.seconds for s in allst[1:]), 4)},
+           "iterations_first_steps": [s.iterations for s in allst[:4]],
+           "roofline_k23_pair": roof, "roofline_k1_pair": roof1}
+    del op
+    return out
+
+
+def plain_fp64(dlz, op, b0, rest, w, nsample, nrhs, chosen_value):
+    """The plain FP64 form on the same operator: FP64 Lan-DR(120,60) on the first
+    right-hand side (with its D-CG finish), then FP64 D-CG one right-hand side at a
+    time on `nsample` of the 48, whose mean time is extrapolated to all 48."""
+    import torch
+    p_dr, p_d = workload_params(dlz, w, dlz.F64)
+    # warm-up of the FP64 kernels: two restart cycles and a short D-CG
+    wdr = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=2, precision=dlz.F64)
+    _, wd, _ = dlz.landr(op, b0, wdr)
+    dlz.dcg(op, wd, rest[:1].contiguous(), dlz.params_default(max_iter=32, precision=dlz.F64))
+    del wd
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x0, defl, st = dlz.landr(op, b0, p_dr)
+    torch.cuda.synchronize()
+    t_dr = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, sts = dlz.dcg(op, defl, rest[:nsample].contiguous(), p_d)
+    torch.cuda.synchronize()
+    t_d = time.perf_counter() - t0
+    ok = [s.converged == 1 and s.true_residual <= 1e-10 for s in [st] + list(sts)]
+    per_rhs = t_d / nsample
+    step_s = t_dr + per_rhs * (nrhs - 1)
+    value = nrhs / step_s if all(ok) else None
+    return {"value": round(value, 5) if value else None, "unit": UNIT,
+            "sample": f"first RHS in full + D-CG on {nsample} of {nrhs - 1} RHS, per-RHS time extrapolated",
+            "first_rhs_seconds": round(t_dr, 3), "first_rhs_mvps": int(st.mvps), "first_rhs_cycles": st.cycles,
+            "dcg_seconds_per_rhs": round(per_rhs, 3),
+            "dcg_iterations_mean": float(sum(s.iterations for s in sts) / len(sts)),
+            "all_verified": bool(all(ok)), "_ratio": round(chosen_value / value, 3) if value else None}
+
+
+def dslash_lines(dlz, torch, op, dims, peaks):
+    """The Wilson stencil alone as the solvers launch it, 16 RHS per launch."""
+    import numpy as np
+    V = int(np.prod(dims))
+    ds = {}
+    for name, dt, real in (("f32_batch16", dlz.F32, 4), ("bf16_batch16", dlz.BF16, 2)):
+        xs = torch.randn((16, V, 4, 3), dtype=torch.complex64, device="cuda")
+        ms = dlz.stencil_bench(op, xs, 30, dtype=dt)["ms"]
+        nb = V * (48 * 16 * real + 48 * 4)
+        ds[name] = {"avg_launch_ms": round(ms, 5), "gbs": round(nb / ms / 1e6, 1),
+                    "frac_hbm": round(nb / ms / 1e6 / peaks["hbm_gbs"], 4), "bytes_per_launch": int(nb)}
+        del xs
+    xs = torch.randn((1, V, 4, 3), dtype=torch.complex128, device="cuda")
+    ms = dlz.stencil_bench(op, xs, 20)["ms"]
+    ds["f64_single"] = {"avg_launch_ms": round(ms, 5), "fp64_tflops": round(1368 * V / (ms * 1e-3) / 1e12, 3)}
+    return ds
+
+
+def c4_kappas(w):
+    """kappa per lattice of the uneven batch: the sigma_min = 1e-3 rule computed by the
+    oracle for the first lattice of each size (gauge seeds 3000, 3001, 3002) and used
+    for every lattice of that size (the links of all lattices follow one recipe)."""
+    import synth
+    ks = []
+    for i in range(w["lattices"]):
+        dims = w["sizes"][i % 3]
+        ks.append(synth.kappa_for(dims, w["gauge_seed0"] + i % 3))
+    return ks
+
+
+def run_c4(dlz, torch, nl=64):
+    """64 lattices (i mod 3 -> 8^4, 12^4, 16^4) at the kappa of c4_kappas: FP32
+    MinRes-DR(40,10) on one Gaussian RHS per lattice, then D-MinRes on 8 Gaussian RHS
+    per lattice (512 solves) through one dlz_batch_dminres call (FP32, one launch per
+    stage for all slots), against the same solves lattice by lattice (FP32 batched per
+    lattice) and the plain FP64 form on one lattice of each size."""
     import numpy as np
 
-    from oracle import cwilson, krylov, wilson
+    import synth
+    w = synth.WORKLOADS[C4]
+    try:
+        kap = c4_kappas(w)[:nl]
+        ksrc = "sigma_min = 1e-3 rule per size class (oracle, first lattice of each size)"
+    except KeyError as e:
+        return {"unavailable": str(e)}
+    ops, defls, Bs = [], [], []
+    dr_s = 0.0
+    for i in range(nl):
+        dims = w["sizes"][i % 3]
+        op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, w["gauge_seed0"] + i)).cuda(),
+                                 float(kap[i]))
+        b0 = torch.from_numpy(synth.gaussian_spinor(dims, w["first_rhs_seed"])).cuda()
+        ta = time.perf_counter()
+        _, d, st = dlz.minresdr(op, b0, dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=400,
+                                                           precision=dlz.F32))
+        torch.cuda.synchronize()
+        dr_s += time.perf_counter() - ta
+        ops.append(op)
+        defls.append(d)
+        Bs.append(torch.from_numpy(synth.gaussian_spinors(dims, w["rhs_seeds"])).cuda())
+    sites = sum(o.volume for o in ops)
+    p32 = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=100000, precision=dlz.F32,
+                             reliable_delta=1e-5)
+    dlz.batch_dminres(ops, defls, Bs, p32)          # warm-up (graph capture, scratch)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ta = time.perf_counter()
+    Xs, sts = dlz.batch_dminres(ops, defls, Bs, p32)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - ta
+    clk = clocks.stop()
+    ok_batch = sum(1 for ss in sts for s in ss if s.converged == 1 and s.true_residual <= 1e-10)
+    ta = time.perf_counter()
+    ok_seq = 0
+    for o, d, B in zip(ops, defls, Bs):
+        _, ss = dlz.dminres(o, d, B, p32)
+        ok_seq += sum(1 for s in ss if s.converged == 1 and s.true_residual <= 1e-10)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - ta
+    p64 = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=100000)
+    ta = time.perf_counter()
+    ok64, n64, sites64 = 0, 0, 0
+    for j in range(min(3, nl)):            # one lattice of each size
+        _, ss = dlz.dminres(ops[j], defls[j], Bs[j], p64)
+        ok64 += sum(1 for s in ss if s.converged == 1 and s.true_residual <= 1e-10)
+        n64 += len(ss)
+        sites64 += ops[j].volume * len(ss)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - ta
+    iters = [max(s.iterations for s in ss) for ss in sts]
+    # the FP64 sample covers one lattice of each size; its rate in site-RHS per second
+    # gives the FP64 time of the whole batch (sites x RHS of all 64 lattices)
+    rhs_sites = sum(o.volume * len(ss) for o, ss in zip(ops, sts))
+    t64_all = t64 / max(sites64, 1) * rhs_sites
+    rate64 = (ok64 / n64) * sum(len(ss) for ss in sts) / t64_all if n64 else None
+    out = {"workload": f"{nl} lattices 8^4/12^4/16^4, MinRes-DR(40,10) + D-MinRes x 8 RHS each",
+           "kappa": sorted(set(round(k, 10) for k in kap)), "kappa_source": ksrc,
+           "lattices": nl, "sites_total": int(sites), "rhs_total": int(sum(len(ss) for ss in sts)),
+           "first_rhs_dr_seconds": round(dr_s, 3),
+           "batched": {"seconds": round(t_batch, 3), "rhs_per_s": round(ok_batch / t_batch, 2), "solved": ok_batch,
+                       "iterations_max": int(max(iters))},
+           "lattice_by_lattice_f32": {"seconds": round(t_seq, 3), "rhs_per_s": round(ok_seq / t_seq, 2),
+                                      "solved": ok_seq},
+           "plain_fp64": {"sample": "one lattice of each size, 8 RHS each, one RHS at a time; extrapolated "
+                                    "to all 64 lattices by site-RHS",
+                          "seconds_sample": round(t64, 3), "rhs_per_s": round(rate64, 3) if rate64 else None},
+           "batched_over_lattice_by_lattice": round((ok_batch / t_batch) / (ok_seq / t_seq), 3),
+           "chosen_over_plain": round((ok_batch / t_batch) / rate64, 3) if rate64 else None,
+           "clocks": clk}
+    return out
+
+
+def run_c2(dlz, torch, peaks, src):
+    """The 16^3x32 workload (MinRes-DR(100,40) on the point source at the origin, spin 0
+    colour 0, then D-MinRes on the other 11 spin-colour point sources), chosen form:
+    one warm-up step and one timed step (CUDA events), then a profiled step for the
+    roofline of the fused MinRes kernel (k_minres_k1)."""
+    w, dims, U, kappa, B = workload_inputs(name=C2)
+    op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
+    Bd = torch.from_numpy(B).cuda()
+    b0, rest = Bd[0].contiguous(), Bd[1:].contiguous()
+    pars = workload_params(dlz, w, dlz.F32, name=C2)
+    solve_step(dlz, op, b0, rest, pars, True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ok, allst = solve_step(dlz, op, b0, rest, pars, True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, pst = solve_step(dlz, op, b0, rest, pars, True, profile=True)
+    roof = kernel_roofline(pst[1:], 1, peaks, src, "k_minres_k1 (fused FP32 Q stencil + MinRes update, 11 RHS)")
+    return {"workload": C2, "kappa": kappa, "value": round(ok / (ms / 1e3), 4), "unit": UNIT,
+            "ms_per_step": round(ms, 1), "solved": ok,
+            "phase_seconds": {"first_rhs_dr": round(allst[0].seconds, 4),
+                              "deflated_11_rhs": round(sum(s.seconds for s in allst[1:]), 4)},
+            "roofline_k_minres_k1": roof}
+
+
+def cpu_baseline(iters_per_rhs, first_rhs_mvps, nrhs, budget_s=20.0, source=""):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload: CG on
+    the normal equations (oracle.krylov.cgnr with the plain-C Wilson operator) on the
+    24^3x48 lattice for about `budget_s` seconds.  RHS/s extrapolates its seconds per
+    MVP to one step of the FP64 algorithm: the first right-hand side's MVPs plus
+    2 MVPs per D-CG iteration for each of the other right-hand sides."""
+    import numpy as np
+
+    from oracle import cwilson, krylov
     w, dims, U, kappa, B = workload_inputs()
-    Q = cwilson.operator(U, kappa, dims, "Q")
-    b = wilson.apply_gamma5(B[0]).reshape(-1)
-    t0 = time.perf_counter()
-    cycles = 1
+    D = cwilson.operator(U, kappa, dims, "D")
+    Dd = cwilson.operator(U, kappa, dims, "Ddag")
+    b = B[1].reshape(-1)
+    it = 2
     while True:
-        r = krylov.minresdr(Q, b, w["m"], w["k"], tol=1e-10, max_cycles=cycles)
+        t0 = time.perf_counter()
+        x, info = krylov.cgnr(D, Dd, b, tol=1e-30, maxiter=it)
         el = time.perf_counter() - t0
-        if el >= budget_s or cycles >= 8:
+        if el >= budget_s / 3 or it >= 4096:
             break
-        cycles += 1
-    # time the last run only
-    t1 = time.perf_counter()
-    r = krylov.minresdr(Q, b, w["m"], w["k"], tol=1e-10, max_cycles=max(1, cycles - 1))
-    el = time.perf_counter() - t1
-    s_per_mvp = el / max(r.info.mvps, 1)
-    rhs_per_s = 12.0 / (s_per_mvp * max(mvps_per_step, 1))
+        it *= 2
+    mv = 2 * it + 2
+    s_per_mvp = el / mv
+    step_mvps = first_rhs_mvps + (nrhs - 1) * (2 * iters_per_rhs + 2)
     threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
-    return {"value": round(rhs_per_s, 6), "unit": UNIT, "cores": int(threads), "kind": "oracle",
-            "sample": (f"oracle MinRes-DR(100,40), {r.cycles} cycle(s) = {r.info.mvps} MVPs in "
-                       f"{el:.1f} s on {platform.machine()}; RHS/s extrapolated to "
-                       f"{mvps_per_step} MVPs per 12-RHS step")}
+    return {"value": round(nrhs / (s_per_mvp * step_mvps), 8), "unit": UNIT, "cores": int(threads),
+            "kind": "oracle",
+            "sample": (f"oracle CGNR, {it} iterations ({mv} MVPs) on 24^3x48 in {el:.1f} s on "
+                       f"{platform.machine()}; RHS/s extrapolated to {step_mvps} MVPs per 49-RHS step "
+                       f"(MVP counts of the FP64 algorithm from {source})")}
 
 
 def run_reference(args):
-    """The oracle timed as it stands on the host cores (rank 0 only)."""
+    """The oracle timed as it stands on the host cores (rank 0 only): each step is a
+    bounded sample of the workload (oracle CG on the normal equations, 24^3x48, a fixed
+    number of iterations); RHS/s is extrapolated to the FP64 algorithm's MVPs per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import cwilson, krylov, wilson
-    w, dims, U, kappa, B = workload_inputs()
-    Q = cwilson.operator(U, kappa, dims, "Q")
-    b = wilson.apply_gamma5(B[0]).reshape(-1)
-    # one bounded sample per step: one MinRes-DR(100,40) cycle (m Lanczos steps + restart)
-    mvps_per_rhs = args.ref_mvps_per_rhs
+    from oracle import cwilson, krylov
+    w, dims, U, kappa, B = workload_inputs(args.kappa)
+    D = cwilson.operator(U, kappa, dims, "D")
+    Dd = cwilson.operator(U, kappa, dims, "Ddag")
+    b = B[1].reshape(-1)
+    it = args.ref_iters
     for _ in range(args.warmup):
-        krylov.minresdr(Q, b, w["m"], w["k"], tol=1e-10, max_cycles=1)
+        krylov.cgnr(D, Dd, b, tol=1e-30, maxiter=2)
     t0 = time.perf_counter()
-    mv = 0
     for _ in range(args.steps):
-        r = krylov.minresdr(Q, b, w["m"], w["k"], tol=1e-10, max_cycles=1)
-        mv += r.info.mvps
+        krylov.cgnr(D, Dd, b, tol=1e-30, maxiter=it)
     el = time.perf_counter() - t0
-    value = 1.0 / (el / mv * mvps_per_rhs)
+    mv = args.steps * (2 * it + 2)
+    nrhs = B.shape[0]
+    step_mvps = REF_FIRST_RHS_MVPS + (nrhs - 1) * (2 * REF_ITERS_PER_RHS + 2)
+    value = nrhs / (el / mv * step_mvps)
     threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
-    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": UNIT,
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded SU(3) links exp(0.3iH), point sources)",
+           "data": "synthetic (seeded SU(3) links exp(0.3iH), seeded complex Gaussian RHS)",
            "config": {"workload": WORKLOAD, "lattice": list(dims), "kappa": kappa, "m": w["m"], "k": w["k"],
-                      "rhs": 12, "form": "oracle (FP64 CPU)", "tol": 1e-10,
-                      "first_rhs": f"{DR_CYCLES} MinRes-DR cycles, then D-MinRes from x",
+                      "rhs": nrhs, "form": "oracle (FP64 CPU)", "tol": 1e-10,
+                      "timed": f"per step {it} oracle CG iterations on the normal equations (one RHS)",
                       "parallelism": "rank 0 only"},
-           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": int(threads),
-                            "kind": "oracle",
-                            "sample": (f"per step one MinRes-DR(100,40) cycle ({mv // args.steps} MVPs); "
-                                       f"RHS/s extrapolated at {mvps_per_rhs} MVPs per RHS")},
-           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
-                   "d2h_bytes_per_step": 0}}
+           "cpu_baseline": {"value": round(value, 8), "unit": UNIT, "cores": int(threads), "kind": "oracle",
+                            "sample": (f"{args.steps} x {it} oracle CGNR iterations ({mv} MVPs) in {el:.1f} s; "
+                                       f"RHS/s extrapolated to {step_mvps} MVPs per 49-RHS step (first RHS "
+                                       f"{REF_FIRST_RHS_MVPS} MVPs + 48 x {REF_ITERS_PER_RHS} D-CG iterations, "
+                                       f"counts of the FP64 algorithm taken from an FP64 run of the library)")},
+           "e2e": {"value": round(value, 8), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
 def run_stencil_only(args):
     """The Wilson stencil alone, as the solvers launch it: FP32 batched over `nrhs`
     right-hand sides and FP64 single, on the benchmark lattice (or --lattice),
-    timed with CUDA events over back-to-back launches (inputs larger than L2
-    when nrhs * 12.6 MB + links exceed 129 MB).  Prints one JSON line."""
-    import numpy as np
+    timed with CUDA events over back-to-back launches.  Prints one JSON line."""
     import torch
 
     import synth
@@ -445,38 +684,17 @@ def run_stencil_only(args):
     print(json.dumps(out), flush=True)
 
 
-def run_first_rhs_only(args):
-    """One first-right-hand-side solve (MinRes-DR(100,40) on the point source) of
-    the benchmark workload, for profiling the restart cycles; prints its stats.
-    --kappa overrides the tabulated kappa (profiling runs only)."""
-    import torch
-
-    from paper_0901_3163_gb300 import dlz
-    w, dims, U, kappa, B = workload_inputs(args.kappa)
-    op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
-    prec = dlz.F32 if args.form == "chosen" else dlz.F64
-    p = dlz.params_default(m=w["m"], k=w["k"], tol=args.tol, max_cycles=args.max_cycles, precision=prec)
-    x, d, st = dlz.minresdr(op, torch.from_numpy(B[0]).cuda(), p, deflate=True)
-    torch.cuda.synchronize()
-    print(json.dumps({"mode": "first-rhs-only", "form": args.form, "kappa": kappa, "stats": st.as_dict()}))
-
-
 def run_ncu_case(args):
-    """A short run of the benchmark's kernels for ncu captures.  minres: the 16^3x32
-    operator, a deflation set from 2 FP32 MinRes-DR(100,40) cycles (their
-    finishing MinRes capped at 12 iterations), then 48 FP32 D-MinRes iterations
-    on the 11 point sources batched (fused kernels with 11 right-hand sides per
-    launch).  cg: the same with Lan-DR and D-CG on 11 Gaussian RHS.  ptc: one
-    forward and backward of the learned-seed network on 16^4.  Prints the stats."""
+    """A short run of the benchmark's kernels for ncu captures.  cg (cg-eo): 48 fused
+    FP32 CGNR iterations (full or even-odd operator) on 16 Gaussian RHS of the 16^3x32
+    lattice, the launch shape of the 24^3x48 step on ~3 GB of device memory.  minres: the 16^3x32 operator, MinRes-DR(100,40) for 2 cycles, then
+    48 FP32 D-MinRes iterations on the 11 point sources.  ptc: one forward and
+    backward of the learned-seed network on 16^4.  Prints the stats."""
     import torch
 
     import synth
     from paper_0901_3163_gb300 import dlz
-    w, dims, U, kappa, B = workload_inputs()
-    op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
-    Bd = torch.from_numpy(B).cuda()
     if args.ncu_case == "ptc":
-        # the learned-seed network on a 16^4 lattice: one forward and one backward of 4 vectors
         from paper_0901_3163_gb300 import ptc_train as T
         dims4 = (16, 16, 16, 16)
         op4 = dlz.create_operator(dims4, torch.from_numpy(synth.su3_links(dims4, 1000)).cuda(), 0.25)
@@ -489,16 +707,24 @@ def run_ncu_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"mode": "ncu-case", "case": "ptc"}))
         return
-    if args.ncu_case == "cg":
-        # FP32 Lan-DR(100,40) for 2 cycles, then 48 fused CGNR iterations on 11 Gaussian RHS
-        p = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=2, max_iter=12, precision=dlz.F32)
-        _, d, st = dlz.landr(op, Bd[0].contiguous(), p)
-        G = torch.from_numpy(synth.gaussian_spinors(dims, list(range(1, 12)))).cuda()
-        pd = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=48, precision=dlz.F32)
-        _, sts = dlz.dcg(op, d, G, pd)
+    if args.ncu_case in ("cg", "cg-eo"):
+        # the fused CGNR kernels as the 24^3x48 step launches them (16 RHS per launch), on
+        # the 16^3x32 lattice so that the device holds ~3 GB: FP32 CG on the normal
+        # equations without deflation, 48 iterations (inputs larger than L2)
+        w2, dims, U, kappa, _ = workload_inputs(name=C2)
+        mk = dlz.create_operator_eo if args.ncu_case == "cg-eo" else dlz.create_operator
+        op = mk(dims, torch.from_numpy(U).cuda(), kappa)
+        B = synth.gaussian_spinors(dims, list(range(1, 17)))
+        if args.ncu_case == "cg-eo":
+            B = B[:, ::2].copy()
+        pd = dlz.params_default(m=100, k=40, tol=1e-10, max_iter=48, precision=dlz.F32)
+        _, sts = dlz.dcg(op, None, torch.from_numpy(B).cuda(), pd)
         torch.cuda.synchronize()
-        print(json.dumps({"mode": "ncu-case", "case": "cg", "d_iterations": [s.iterations for s in sts]}))
+        print(json.dumps({"mode": "ncu-case", "case": args.ncu_case, "d_iterations": [s.iterations for s in sts]}))
         return
+    w, dims, U, kappa, B = workload_inputs(name=C2)
+    op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
+    Bd = torch.from_numpy(B).cuda()
     p = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_cycles=2, max_iter=12, precision=dlz.F32)
     _, d, st = dlz.minresdr(op, Bd[0].contiguous(), p)
     pd = dlz.params_default(m=w["m"], k=w["k"], tol=1e-10, max_iter=48, precision=dlz.F32)
@@ -512,10 +738,10 @@ def run_learned_seed(args):
     recipe): Lan-DR(100,40) eigenvectors of `--ls-train` training fields (gauge
     seeds 1000...), Adam training of the 1 -> 12 -> 16 -> 1 PTC network for
     `--ls-steps` steps of 4 noise vectors, then on `--ls-test` held-out fields
-    (gauge seeds 2000...) the seeded Rayleigh-Ritz set (40 MVPs) against one
-    Lan-DR(100,40) cycle (100 MVPs) and the untrained network: median Ritz
-    residuals and D-CG iterations on 4 Gaussian right-hand sides.  Also times
-    the network's forward and backward launches.  Prints one JSON line."""
+    (gauge seeds 2000...) the seeded Rayleigh-Ritz set against plain Lan-DR at an
+    equal MVP budget and the untrained network: median Ritz residuals and D-CG
+    iterations on 4 Gaussian right-hand sides.  Also times the network's forward
+    and backward launches.  Prints one JSON line."""
     import numpy as np
     import torch
 
@@ -540,7 +766,6 @@ def run_learned_seed(args):
     W0 = T.init_weights(widths, 1)
     net = dlz.net_create(train_ops[0], widths, W0)
     net0 = dlz.net_create(train_ops[0], widths, W0)
-    # kernel timing: one forward and one backward of 4 vectors (CUDA events)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(3)
     x = T.noise(torch, train_ops[0], 4, gen)
@@ -559,8 +784,6 @@ def run_learned_seed(args):
     torch.cuda.synchronize()
     dlz.net_zero_grad(net)
     fw_ms, bw_ms = e0.elapsed_time(e1) / 5, e1.elapsed_time(e2) / 5
-    # algorithmic flops: per layer, site and vector 9 c_in c_out 48 complex FMAs (spin
-    # mixing) + 9 c_in 36 (transport), 8 real flops each; backward twice that
     fl = sum(9 * widths[i] * (widths[i + 1] * 48 + 36) * 8 for i in range(len(widths) - 1)) * V * 4
     t1 = time.perf_counter()
     hist = T.train(torch, net, train_ops, train_defl, steps=args.ls_steps, nvec=4, lr=3e-3)
@@ -571,8 +794,8 @@ def run_learned_seed(args):
         op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, 2000 + j)).cuda(), kappa)
         bl = [torch.from_numpy(synth.gaussian_spinor(dims, s)).cuda() for s in (0, 1, 2, 3, 4)]
         evals.append(T.evaluate(torch, net, op, bl, m, k, seed=j, net_untrained=net0))
-    med = lambda key: float(np.median([e[key] for e in evals]))
-    mean_it = lambda key: float(np.mean([np.mean(e[key]) for e in evals]))
+    med = lambda key: float(np.median([e[key] for e in evals]))  # noqa: E731
+    mean_it = lambda key: float(np.mean([np.mean(e[key]) for e in evals]))  # noqa: E731
     out = {"mode": "learned-seed", "workload": "16^4 kappa 0.25, PTC 1-12-16-1, Lan-DR(100,40)",
            "train_fields": args.ls_train, "test_fields": args.ls_test, "steps": args.ls_steps,
            "data_seconds": round(t_data, 2), "lanczos_seconds_per_field": round(float(np.mean(lan_s)), 3),
@@ -581,204 +804,128 @@ def run_learned_seed(args):
            "forward_ms_4vec": round(fw_ms, 3), "backward_ms_4vec": round(bw_ms, 3),
            "forward_tflops": round(fl / (fw_ms * 1e-3) / 1e12, 2),
            "backward_tflops": round(2 * fl / (bw_ms * 1e-3) / 1e12, 2),
+           "per_field": evals,
            "ritz_median": {"seed": med("ritz_median_seed"), "untrained": med("ritz_median_untrained"),
-                           "plain_one_cycle": med("ritz_median_plain")},
-           "dcg_iterations_mean": {"seed": mean_it("dcg_iters_seed"), "plain_one_cycle": mean_it("dcg_iters_plain_cycle"),
+                           "plain_equal_mvps": med("ritz_median_plain"),
+                           "plain_one_m_cycle": med("ritz_median_plain_m_cycle")},
+           "dcg_iterations_mean": {"seed": mean_it("dcg_iters_seed"), "plain_equal_mvps": mean_it("dcg_iters_plain_equal"),
+                                   "plain_one_m_cycle": mean_it("dcg_iters_plain_cycle"),
                                    "undeflated": mean_it("cg_iters_undeflated")},
            "chosen": [e["chosen"] for e in evals], "all_converged": all(e["converged"] for e in evals)}
     print(json.dumps(out), flush=True)
 
 
-def run_multi_lattice(args):
-    """Uneven multi-lattice batching: 64 lattices (i mod 3 -> 8^4, 12^4, 16^4), links
-    by the same recipe (gauge seed 3000 + i), per-lattice kappa drawn uniformly in
-    [0.21, 0.24] (numpy default_rng(4000)); MinRes-DR(40,10) (FP32 form) on one
-    Gaussian RHS per lattice, then D-MinRes on 8 Gaussian RHS per lattice (512 solves):
-    all lattices through one dlz_batch_dminres call (FP32, one launch per stage for
-    all slots) against the same solves lattice by lattice (dlz_dminres, FP32 batched per
-    lattice) and, on one lattice of each size, the plain FP64 form.  Prints one JSON line."""
-    import numpy as np
+def run_saturation(args):
+    """Lan-DR(200, k) for k = 20, 60, 100, 150 (Sec. 2 runs m = 200 with k = 20, 60, 150)
+    on the 16^3x32 lattice at its kappa, first Gaussian RHS (seed 0), FP64: the first
+    right-hand side's MVPs, then D-CG on 4 Gaussian RHS (seeds 1..4) over each
+    deflation set, and plain CG (no deflation) on the same RHS.  Saturation (Sec. 2):
+    the D-CG iteration count stops falling once the deflated rate matches the rate CG
+    reaches after its deflation knee.  Also Lan-DR(200,150) as a pure eigensolver
+    (eig_only): cycles, MVPs and seconds until all 150 kept Ritz residuals converge.
+    Prints one JSON line."""
     import torch
 
     import synth
     from paper_0901_3163_gb300 import dlz
-    sizes = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16)]
-    nl = args.ml_lattices
-    kap = np.random.default_rng(4000).uniform(0.21, 0.24, nl)
+    w, dims, U, kappa, _ = workload_inputs(name=C2)
+    op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
+    b0 = torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda()
+    B = torch.from_numpy(synth.gaussian_spinors(dims, (1, 2, 3, 4))).cuda()
+    # FP64 throughout (the paper's study): an FP32 Lan-DR on D^dag D stalls with its lowest
+    # Ritz residuals near 1e-5, above the smallest eigenvalues at this kappa, so the
+    # deflation sets it hands on would not show what k alone does
+    pd = dlz.params_default(m=200, k=20, tol=1e-10, max_iter=200000, precision=dlz.F64)
+    rows = []
     t0 = time.perf_counter()
-    ops, defls, Bs = [], [], []
-    dr_s = 0.0
-    for i in range(nl):
-        dims = sizes[i % 3]
-        op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, 3000 + i)).cuda(), float(kap[i]))
-        b0 = torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda()
-        ta = time.perf_counter()
-        _, d, st = dlz.minresdr(op, b0, dlz.params_default(m=40, k=10, tol=1e-10, max_cycles=400, precision=dlz.F32))
+    _, sts = dlz.dcg(op, None, B, pd)
+    torch.cuda.synchronize()
+    rows.append({"k": 0, "dcg_iterations": [s.iterations for s in sts], "dcg_seconds": round(time.perf_counter() - t0, 3),
+                 "verified": all(s.converged == 1 and s.true_residual <= 1e-10 for s in sts)})
+    for k in args.sat_k:
+        p = dlz.params_default(m=200, k=k, tol=1e-10, max_cycles=2000, precision=dlz.F64, finish=1)
+        t0 = time.perf_counter()
+        _, d, st = dlz.landr(op, b0, p)
         torch.cuda.synchronize()
-        dr_s += time.perf_counter() - ta
-        ops.append(op)
-        defls.append(d)
-        Bs.append(torch.from_numpy(synth.gaussian_spinors(dims, list(range(1, 9)))).cuda())
-    t_setup = time.perf_counter() - t0
-    sites = sum(o.volume for o in ops)
-    # inner tolerance 1e-5: on these small, well-conditioned lattices the FP64 restarts
-    # cost more than the re-projections save (278 against 309 RHS/s with 1e-2)
-    p32 = dlz.params_default(m=40, k=10, tol=1e-10, max_iter=100000, precision=dlz.F32, reliable_delta=1e-5)
-    dlz.batch_dminres(ops, defls, Bs, p32)          # warm-up (graph capture, scratch)
+        t_dr = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, sts = dlz.dcg(op, d, B, pd)
+        torch.cuda.synchronize()
+        rows.append({"k": k, "first_rhs_mvps": int(st.mvps), "first_rhs_cycles": st.cycles,
+                     "first_rhs_seconds": round(t_dr, 3), "first_rhs_verified": st.converged == 1,
+                     "dcg_iterations": [s.iterations for s in sts], "dcg_seconds": round(time.perf_counter() - t0, 3),
+                     "verified": all(s.converged == 1 and s.true_residual <= 1e-10 for s in sts)})
+        del d
+    p = dlz.params_default(m=200, k=150, tol=1e-10, max_cycles=4000, precision=dlz.F32, eig_only=1)
+    # (the eigensolver row: FP32 form, kept residuals to 1e-5 ||A||)
+    t0 = time.perf_counter()
+    _, d, st = dlz.landr(op, b0, p)
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
-    ta = time.perf_counter()
-    Xs, sts = dlz.batch_dminres(ops, defls, Bs, p32)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - ta
-    clk = clocks.stop()
-    ok_batch = sum(1 for ss in sts for s in ss if s.converged == 1 and s.true_residual <= 1e-10)
-    ta = time.perf_counter()
-    ok_seq = 0
-    for o, d, B in zip(ops, defls, Bs):
-        _, ss = dlz.dminres(o, d, B, p32)
-        ok_seq += sum(1 for s in ss if s.converged == 1 and s.true_residual <= 1e-10)
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - ta
-    p64 = dlz.params_default(m=40, k=10, tol=1e-10, max_iter=100000)
-    ta = time.perf_counter()
-    ok64, n64 = 0, 0
-    for j in range(min(3, nl)):            # one lattice of each size
-        _, ss = dlz.dminres(ops[j], defls[j], Bs[j], p64)
-        ok64 += sum(1 for s in ss if s.converged == 1 and s.true_residual <= 1e-10)
-        n64 += len(ss)
-    torch.cuda.synchronize()
-    t64 = time.perf_counter() - ta
-    iters = [max(s.iterations for s in ss) for ss in sts]
-    out = {"mode": "multi-lattice", "workload": f"{nl} lattices 8^4/12^4/16^4, kappa U[0.21,0.24], "
-                                                f"MinRes-DR(40,10) + D-MinRes x 8 RHS each",
-           "lattices": nl, "sites_total": int(sites), "rhs_total": int(sum(len(ss) for ss in sts)),
-           "setup_seconds": round(t_setup, 2), "first_rhs_dr_seconds": round(dr_s, 3),
-           "batched": {"seconds": round(t_batch, 3), "rhs_per_s": round(ok_batch / t_batch, 2), "solved": ok_batch,
-                       "iterations_max": int(max(iters))},
-           "lattice_by_lattice_f32": {"seconds": round(t_seq, 3), "rhs_per_s": round(ok_seq / t_seq, 2),
-                                      "solved": ok_seq},
-           "plain_fp64_sample": {"lattices": 3, "rhs": n64, "seconds": round(t64, 3),
-                                 "rhs_per_s": round(ok64 / t64, 3) if t64 > 0 else None},
-           "batched_over_lattice_by_lattice": round((ok_batch / t_batch) / (ok_seq / t_seq), 3),
-           "clocks": clk}
+    t_e = time.perf_counter() - t0
+    kk, _ = dlz.defl_count(d)
+    vals = [dlz.defl_get(d, i) for i in range(kk)]
+    out = {"mode": "saturation", "workload": f"{C2} kappa {kappa}, Lan-DR(200,k) FP64, D-CG on 4 Gaussian RHS",
+           "rows": rows,
+           "eigensolver_k150": {"converged": st.converged == 1, "cycles": st.cycles, "mvps": int(st.mvps),
+                                "seconds": round(t_e, 3), "lowest": vals[0][0], "highest_kept": vals[-1][0],
+                                "max_ritz_residual": max(v[1] for v in vals)}}
     print(json.dumps(out), flush=True)
 
 
-def run_c3(args):
-    """Precision and batching on the 24^3x48 lattice (gauge seed 3, kappa by the
-    sigma_min = 1e-3 rule from synth/kappa_table.json, or --kappa): FP32 Lan-DR(120,60)
-    on D^dag D for the first Gaussian RHS (seed 0), then FP32 D-CG with FP64 defect
-    correction on 48 Gaussian RHS (seeds 1..48) in batches of 16 per launch; the
-    plain FP64 D-CG timed on 2 of them; the bare stencil in FP32 and bfloat16 with
-    16 RHS per launch.  Prints one JSON line."""
-    import numpy as np
+def run_multi_lattice(args):
+    """The uneven multi-lattice batch alone (the c4 key of the default line)."""
     import torch
 
-    import synth
     from paper_0901_3163_gb300 import dlz
-    dims = (24, 24, 24, 48)
-    V = synth.volume(dims)
-    if args.kappa is not None:
-        kappa, ksrc = args.kappa, "given on the command line (not the sigma_min rule)"
-    else:
-        try:
-            kappa, ksrc = synth.kappa_for(dims, 3), "sigma_min(D) = 1e-3 rule (oracle)"
-        except KeyError:
-            print(json.dumps({"mode": "c3", "unavailable": "kappa of the 24^3x48 seed-3 lattice not in the table"}))
-            return
-    t0 = time.perf_counter()
-    op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, 3)).cuda(), kappa)
-    t_links = time.perf_counter() - t0
-    peaks, src = _peaks()
-    ds = {}
-    for name, dt, real in (("f32", dlz.F32, 4), ("bf16", dlz.BF16, 2)):
-        xs = torch.randn((16, V, 4, 3), dtype=torch.complex64, device="cuda")
-        ms = dlz.stencil_bench(op, xs, 20, dtype=dt)["ms"]
-        nb = V * (48 * 16 * real + 48 * 4)
-        ds[name] = {"avg_launch_ms": round(ms, 4), "gbs": round(nb / ms / 1e6, 1),
-                    "frac_hbm": round(nb / ms / 1e6 / peaks["hbm_gbs"], 4)}
-        del xs
-    b0 = torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, d, st = dlz.landr(op, b0, dlz.params_default(m=120, k=60, tol=1e-10, max_cycles=args.max_cycles,
-                                                     precision=dlz.F32))
-    torch.cuda.synchronize()
-    t_dr = time.perf_counter() - t0
-    B = torch.from_numpy(synth.gaussian_spinors(dims, list(range(1, 49)))).cuda()
-    pd = dlz.params_default(m=120, k=60, tol=1e-10, max_iter=200000, precision=dlz.F32, profile=1)
-    t0 = time.perf_counter()
-    _, sts = dlz.dcg(op, d, B, pd)
-    torch.cuda.synchronize()
-    t_d = time.perf_counter() - t0
-    ok = sum(1 for s in sts if s.converged == 1 and s.true_residual <= 1e-10)
-    st_ms = sum(s.stencil_ms for s in sts)
-    st_b = sum(s.stencil_bytes for s in sts)
-    p64 = dlz.params_default(m=120, k=60, tol=1e-10, max_iter=200000)
-    t0 = time.perf_counter()
-    _, s64 = dlz.dcg(op, d, B[:2].contiguous(), p64)
-    torch.cuda.synchronize()
-    t64 = time.perf_counter() - t0
-    ok64 = sum(1 for s in s64 if s.converged == 1 and s.true_residual <= 1e-10)
-    out = {"mode": "c3", "workload": "24^3x48 Lan-DR(120,60) + D-CG on 48 Gaussian RHS",
-           "kappa": kappa, "kappa_source": ksrc, "links_seconds": round(t_links, 1),
-           "first_rhs": {"seconds": round(t_dr, 3), "cycles": st.cycles, "iterations": st.iterations,
-                         "converged": st.converged},
-           "dcg_f32_batched": {"seconds": round(t_d, 3), "rhs_per_s": round(ok / t_d, 4), "solved": ok,
-                               "iterations": [s.iterations for s in sts[:3]],
-                               "fused_kernel_gbs": round(st_b / max(st_ms, 1e-9) / 1e6, 1)},
-           "dcg_plain_fp64_2rhs": {"seconds": round(t64, 3), "rhs_per_s": round(ok64 / t64, 4), "solved": ok64,
-                                   "iterations": [s.iterations for s in s64]},
-           "dslash_16rhs": ds, "peak_source": src}
+    out = {"mode": "multi-lattice"}
+    out.update(run_c4(dlz, torch, args.c4_lattices))
     print(json.dumps(out), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["plain", "chosen"], default="chosen")
-    ap.add_argument("--plain-steps", type=int, default=1,
-                    help="timed steps of the plain FP64 form reported beside the chosen form")
-    ap.add_argument("--k1-traffic", type=float, default=K1_TRAFFIC_BYTES,
+    ap.add_argument("--plain-rhs", type=int, default=2,
+                    help="D-CG right-hand sides of the plain FP64 form timed beside the chosen form")
+    ap.add_argument("--k23-traffic", type=float, default=K23_TRAFFIC_BYTES,
                     help="ncu DRAM bytes per launch of the dominant kernel (None if not measured)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-c4", action="store_true")
+    ap.add_argument("--no-c2", action="store_true")
+    ap.add_argument("--no-evenodd", action="store_true")
+    ap.add_argument("--c4-lattices", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--ref-mvps-per-rhs", type=int, default=REF_MVPS_PER_RHS)
+    ap.add_argument("--ref-iters", type=int, default=16, help="oracle CGNR iterations per reference step")
     ap.add_argument("--stencil-only", action="store_true")
     ap.add_argument("--lattice", default=None)
-    ap.add_argument("--nrhs", type=int, default=11)
+    ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--stencil-iters", type=int, default=50)
-    ap.add_argument("--first-rhs-only", action="store_true")
-    ap.add_argument("--ncu-case", nargs="?", const="minres", default=None, choices=["minres", "cg", "ptc"])
+    ap.add_argument("--ncu-case", nargs="?", const="minres", default=None, choices=["minres", "cg", "cg-eo", "ptc"])
     ap.add_argument("--learned-seed", action="store_true")
     ap.add_argument("--multi-lattice", action="store_true")
-    ap.add_argument("--c3", action="store_true")
-    ap.add_argument("--ml-lattices", type=int, default=64)
+    ap.add_argument("--saturation", action="store_true")
+    ap.add_argument("--sat-k", type=int, nargs="+", default=[20, 60, 100, 150])
     ap.add_argument("--ls-train", type=int, default=32)
     ap.add_argument("--ls-test", type=int, default=8)
     ap.add_argument("--ls-steps", type=int, default=400)
-    ap.add_argument("--max-cycles", type=int, default=4000)
-    ap.add_argument("--kappa", type=float, default=None)
-    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--kappa", type=float, default=None,
+                    help="override the tabulated kappa (profiling and trial runs only)")
     args = ap.parse_args()
     if args.stencil_only:
         run_stencil_only(args)
-    elif args.first_rhs_only:
-        run_first_rhs_only(args)
     elif args.ncu_case is not None:
         run_ncu_case(args)
     elif args.learned_seed:
         run_learned_seed(args)
     elif args.multi_lattice:
         run_multi_lattice(args)
-    elif args.c3:
-        run_c3(args)
+    elif args.saturation:
+        run_saturation(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

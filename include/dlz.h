@@ -37,13 +37,18 @@
  * C++ exception crosses the ABI.  dlz_strerror() names a code,
  * dlz_last_error() gives the message of the last failure on this thread.
  *
- * Environment (read at the call; none changes a result):
+ * Environment (read at the call; none changes a result, apart from DLZ_WAIT_LIMIT's
+ * error path):
  *   DLZ_NO_GRAPHS=1   launch kernels one by one instead of replaying CUDA graphs
  *                     (read when an operator is created);
  *   DLZ_TRACE=1       per-cycle and per-phase timing lines on stderr;
  *   DLZ_MULTI_TILE=1|2|4  fix the block tile of dlz_batch_dminres (chunks of 128
- *                     sites per block) instead of choosing it by timed graph
- *                     replays; every tile gives the same bits.
+ *                     sites per block or per work item) instead of choosing it by
+ *                     timing; every tile gives the same bits;
+ *   DLZ_MULTI_FORM=graph|persistent  fix the launch form of dlz_batch_dminres
+ *                     (see dlz_batch_last_choice); both forms give the same bits;
+ *   DLZ_WAIT_LIMIT=n  polls before a grid-barrier wait of the persistent form gives up
+ *                     (default 2^24, about a second); a test hook for the timeout path.
  */
 #ifndef DLZ_H
 #define DLZ_H
@@ -111,6 +116,15 @@ typedef struct {
                             D-MinRes / D-CG from the current x over the deflation set
                             just built (1) or return DLZ_ERR_NOT_CONVERGED (0).  The
                             DLZ_F32 form always finishes this way; 0                     */
+    int eig_only;        /* DR solvers: 1 runs Lan-DR / MinRes-DR as an eigensolver (the
+                            use Sec. 2 describes for the kept eigenvectors, and the paper's
+                            k = 150 study): the cycles stop as soon as every kept Ritz
+                            residual is <= tol_eig (<= 0: 1e-10 ||A|| est. in FP64,
+                            1e-5 ||A|| in FP32), whatever the linear residual; x is still
+                            the cycles' iterate and no finishing solve runs.
+                            stats.converged = 1 when the kept pairs converged, and the
+                            call returns DLZ_ERR_NOT_CONVERGED when max_cycles ran out
+                            first; 0                                                     */
 } dlz_params;
 
 /* Per-solve statistics. */
@@ -128,6 +142,13 @@ typedef struct {
                                right-hand side (spinor in and out) + 4 links (72 reals
                                in FP64; 48 in FP32, which stores two rows per link)    */
     long long gpu_launches; /* kernels launched by this call                          */
+    double kernel_ms[3];    /* profile = 1: the timed stencil launches split by kernel kind:
+                               [0] plain stencil launches, [1] the first fused stencil
+                               kernel of the inner solver (k_cg_k1, k_minres_k1,
+                               k_lanczos_k1), [2] the second (k_cg_k23); device ms      */
+    double kernel_bytes[3]; /* their algorithmic bytes (spinor reals of the fused kernel's
+                               reads and writes per site and right-hand side + links)  */
+    long long kernel_launches[3]; /* their launch counts                                 */
 } dlz_stats;
 
 /* Fills *p with the defaults listed above. */
@@ -152,6 +173,38 @@ int dlz_create_operator(const int dims[4], const void *gauge, double kappa, int 
 int dlz_destroy_operator(dlz_op_t op);
 /* Lattice volume V of the operator. */
 int dlz_op_volume(dlz_op_t op, long long *V);
+
+/*
+ * Even-odd (Schur complement) operator -- not in the paper: the standard reduction
+ * of D x = b to the even sites (x + y + z + t even), to which Lan-DR, MinRes-DR,
+ * D-CG and D-MinRes apply unchanged.  The hopping term of D = 1 - kappa H links
+ * only sites of opposite parity, so D x = b is
+ *   Dhat x_e = b_e + kappa H_eo b_o,  Dhat = 1 - kappa^2 H_eo H_oe,
+ *   x_o = b_o + kappa H_oe x_e,
+ * and Dhat^dag = gamma5 Dhat gamma5, so Qhat = gamma5 Dhat is hermitian.
+ * dlz_create_operator_eo: arguments as dlz_create_operator; every extent must be
+ *   even.  The operator's vectors are even-site spinors, complex128 [V/2][4][3]
+ *   holding the even sites in increasing site order; dlz_op_volume gives V/2.  On it
+ *   DLZ_D / DLZ_DDAG / DLZ_Q / DLZ_DDAGD mean Dhat, Dhat^dag, Qhat, Dhat^dag Dhat in
+ *   dlz_apply, dlz_apply_noalloc and dlz_stencil_bench (DLZ_F64, DLZ_F32), and
+ *   dlz_landr / dlz_minresdr / dlz_dcg / dlz_dminres solve Dhat x_e = b_e with the
+ *   same meaning of every parameter (the stopping residual is ||b_e - Dhat x_e|| /
+ *   ||b_e||).  Not built for it: bfloat16 storage, FP32 D-MinRes (DLZ_F64 D-MinRes
+ *   and FP32 / FP64 D-CG are), dlz_batch_dminres and the network (DLZ_ERR_BADARG).
+ *   Deflation files record the operator kind and load only into the same kind.
+ *   The operator holds two odd-site work fields of 16 right-hand sides (FP64 and
+ *   FP32), allocated at creation.
+ * dlz_eo_prepare: b (complex128 [nrhs][V][4][3], host or device) -> b_e =
+ *   even part of b + kappa H_eo (odd part of b), complex128 [nrhs][V/2][4][3].
+ * dlz_eo_reconstruct: x = (x_e, b_o + kappa H_oe x_e) in the full layout
+ *   [nrhs][V][4][3], from x_e [nrhs][V/2][4][3] and the same b.
+ * ||b - D x|| = ||b_e' - Dhat x_e|| for b_e' = dlz_eo_prepare(b): the odd rows of
+ * D x = b hold exactly, so the full residual is the even-site residual.
+ */
+int dlz_create_operator_eo(const int dims[4], const void *gauge, double kappa, int bc_t,
+                           void *stream, dlz_op_t *out);
+int dlz_eo_prepare(dlz_op_t op, const void *b, void *b_e, int nrhs);
+int dlz_eo_reconstruct(dlz_op_t op, const void *x_e, const void *b, void *x, int nrhs);
 
 /*
  * out = A in for A = DLZ_D, DLZ_DDAG, DLZ_Q or DLZ_DDAGD (Sec. 2: M, M^dagger,
@@ -275,6 +328,40 @@ int dlz_batch_dminres(int nlat, dlz_op_t *ops, dlz_defl_t *defls, const void *co
                       const int *nrhs, const dlz_params *p, dlz_stats *stats);
 
 /*
+ * Products of FP32 basis vectors on the tensor cores (tcgen05, FP32 data split into
+ * two TF32 parts, hi*hi + hi*lo + lo*hi accumulated in FP32): the kernels behind the
+ * Rayleigh-Ritz restart V_{k+1} = V_{m+1} P of the FP32 DR solvers and the batched
+ * Galerkin projection of the FP32 D-CG / D-MinRes (Sec. 1-2), exported for testing and
+ * measurement.  All vector pointers are device pointers to float data; work runs on the
+ * legacy default stream and the calls return when it is complete.
+ * dlz_basis_combine: out[j][t] = sum_i c_ij V[i][t] for t < len floats, j < nout <= 256;
+ *   V[i] at V + i * ldv, out[j] at out + j * ldo (len, ldv, ldo multiples of 4).
+ *   cplx = 0: coef real, host double [nin][nout]; cplx = 1: the vectors are complex
+ *   (interleaved re/im floats) and coef complex, host double [nin][nout][2].
+ * dlz_basis_dots: C[q][i] = <V_i, R_q> = sum_t conj(V_i[t]) R_q[t] over the len / 2
+ *   complex entries; nin <= 128, nq <= 16, len a multiple of 32; C: host complex
+ *   double [nq][nin][2].  Per block, 2048 floats are summed in FP32 by the tensor
+ *   cores, then in FP64.
+ * Both return DLZ_ERR_BADARG for shapes outside these limits and
+ * DLZ_ERR_DEVICE_TIMEOUT if a bounded wait in the kernel gave up.
+ */
+int dlz_basis_combine(const float *V, long long ldv, int nin, long long len, const double *coef, int nout,
+                      int cplx, float *out, long long ldo);
+int dlz_basis_dots(const float *V, long long ldv, int nin, const float *R, long long ldr, int nq,
+                   long long len, double *C);
+
+/*
+ * The launch form the autotuner of the last DLZ_F32 dlz_batch_dminres call chose (op:
+ * that call's ops[0]): form 0 = one launch per stage replayed from CUDA graphs, 1 = one
+ * persistent cooperative launch over all slots and iterations (grid barriers whose waits
+ * give up after a bounded number of polls, about a second, and then make the call return
+ * DLZ_ERR_DEVICE_TIMEOUT); chunks_per_block: 128-site chunks per block (or per work
+ * item); half_grid: 1 if the persistent grid was half the co-resident maximum.  Any
+ * pointer may be NULL.  All 0 before the first call.
+ */
+int dlz_batch_last_choice(dlz_op_t op, int *form, int *chunks_per_block, int *half_grid);
+
+/*
  * Measurement entry point: packs `nrhs` spinors `in` (dtype DLZ_F64:
  * complex128, DLZ_F32: complex64, [nrhs][V][4][3], host or device) into the
  * internal layout and launches the stencil `which` (DLZ_D, DLZ_DDAG or DLZ_Q)
@@ -317,7 +404,9 @@ int dlz_stencil_bench(dlz_op_t op, int dtype, int which, int nrhs, int iters, co
  * dlz_subspace_loss: per vector f_i (device complex64 [nvec][V][4][3]),
  *   loss[i] = ||(1 - V V^dag) f_i||^2 / ||f_i||^2 against the deflation set's
  *   orthonormal vectors V (host double[nvec]); grad (device complex64, may be
- *   NULL) receives G(f_i) = 2 ((1 - V V^dag) f_i - loss[i] f_i) / ||f_i||^2.
+ *   NULL) receives grad_scale * G(f_i) with
+ *   G(f_i) = 2 ((1 - V V^dag) f_i - loss[i] f_i) / ||f_i||^2 (grad_scale = 1/nvec
+ *   gives the gradient of the mean loss over the nvec vectors).
  * dlz_seed_deflation: a deflation set from k device vectors (dtype DLZ_F64:
  *   complex128, DLZ_F32: complex64, [k][V][4][3]): orthonormalised (modified
  *   Gram-Schmidt twice, in FP64), then H = V^dag A V (k MVPs of A = Q or
@@ -334,7 +423,7 @@ int dlz_net_get(dlz_net_t net, int what, void *host_out);
 int dlz_net_set_weights(dlz_net_t net, const void *weights);
 int dlz_net_zero_grad(dlz_net_t net);
 int dlz_net_adam_step(dlz_net_t net, double lr, double beta1, double beta2, double eps);
-int dlz_subspace_loss(dlz_defl_t defl, const void *f, int nvec, double *loss, void *grad);
+int dlz_subspace_loss(dlz_defl_t defl, const void *f, int nvec, double grad_scale, double *loss, void *grad);
 int dlz_seed_deflation(dlz_op_t op, int which, const void *vecs, int dtype, int k, dlz_defl_t *defl_out);
 
 /*

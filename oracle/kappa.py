@@ -140,3 +140,80 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5,
         fb = f(b)
     kap = _illinois(f, a, fa, b, fb, rtol)
     return kap, f(kap, res_tol) + TARGET, state["res"]
+
+
+def kappa_newton(U, dims, a, sa, b, sb, bc_t=1, rtol=1e-4, m=100, k=20, max_cycles=150,
+                 seed=12345, log=None, max_evals=6):
+    """Refine kappa with sigma_min(D) = 1e-3 inside a known bracket [a, b] with
+    sigma_min(a) = sa > 1e-3 > sigma_min(b) = sb (values of earlier oracle runs).
+
+    Each evaluation is MinRes-DR(m, k) on Q = gamma5 D run as an eigensolver,
+    warm-started from the previous evaluation's eigenvector.  It stops when the
+    harmonic Ritz pair nearest zero has a residual r with r^2 / gap below a tenth
+    of the tolerance rtol * 1e-3 (gap: the distance from that value to the next
+    kept harmonic Ritz value), or after max_cycles.  The reported value is the
+    Rayleigh quotient rho of the unit Ritz vector y, whose distance to an
+    eigenvalue of Q is at most |Q y - rho y|^2 / gap (Kato-Temple).
+
+    The step is Newton's on sigma(kappa) - 1e-3 with the Hellmann-Feynman slope:
+    Q(kappa) = gamma5 (1 - kappa H), so d rho / d kappa = <y, -gamma5 H y>
+    = (rho - <y, gamma5 y>) / kappa, and d sigma / d kappa = sign(rho) times that;
+    a step that leaves the bracket is replaced by false position.  Stops when
+    |sigma / 1e-3 - 1| < rtol.  Returns (kappa, sigma_min, residual, error bound,
+    list of evaluations)."""
+    from .krylov import minresdr
+    from .wilson import apply_gamma5
+    V = int(np.prod(dims))
+    n = V * 12
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    hist = []
+    tol_abs = rtol * TARGET
+
+    def evaluate(kap, v0):
+        A = cwilson.operator(U, kap, dims, "Q", bc_t)
+
+        def stop(theta, res):
+            return res * res / 3e-4 <= 0.1 * tol_abs
+
+        def progress(cycle, mvps, rel, theta, res):
+            if log and cycle % 5 == 0:
+                i = int(np.argmin(np.abs(theta)))
+                log(f"   cycle {cycle} mvps {mvps} theta {theta[i]:.9e} res {res[i]:.2e}")
+
+        r = minresdr(A, v0, m, k, tol=0.0, max_cycles=max_cycles, eig_stop=stop,
+                     progress=progress)
+        vals, res = r.ritz_values, r.ritz_residuals
+        i = int(np.argmin(np.abs(vals)))
+        others = np.delete(vals, i)
+        gap = float(np.min(np.abs(others - vals[i]))) if others.size else 1.0
+        y = r.ritz_vectors[:, i]
+        y = y / np.linalg.norm(y)
+        rho = float(vals[i])
+        g5 = float(np.vdot(y, apply_gamma5(y.reshape(V, 4, 3)).reshape(-1)).real)
+        dsig = np.sign(rho) * (rho - g5) / kap
+        bound = float(res[i]) ** 2 / gap
+        ev = dict(kappa=kap, sigma=abs(rho), residual=float(res[i]), gap=gap, bound=bound,
+                  dsigma_dkappa=float(dsig), mvps=r.info.mvps, cycles=r.cycles)
+        hist.append(ev)
+        if log:
+            log(f"kappa={kap:.12f} sigma={abs(rho):.12e} res={res[i]:.2e} gap={gap:.2e} "
+                f"bound={bound:.2e} dsigma/dkappa={dsig:.6f} mvps={r.info.mvps}")
+        return ev, y
+
+    kap = a + (sa - TARGET) * (b - a) / (sa - sb)
+    for _ in range(max_evals):
+        ev, y = evaluate(kap, v)
+        v = y + 1e-3 * (rng.standard_normal(n) + 1j * rng.standard_normal(n)) / np.sqrt(n)
+        f = ev["sigma"] - TARGET
+        if abs(f) < rtol * TARGET:
+            return kap, ev["sigma"], ev["residual"], ev["bound"], hist
+        if f > 0:
+            a, sa = kap, ev["sigma"]
+        else:
+            b, sb = kap, ev["sigma"]
+        nxt = kap - f / ev["dsigma_dkappa"] if ev["dsigma_dkappa"] != 0 else None
+        if nxt is None or not (a < nxt < b):
+            nxt = a + (sa - TARGET) * (b - a) / (sa - sb)
+        kap = nxt
+    raise RuntimeError("kappa_newton: no convergence within max_evals evaluations")

@@ -292,7 +292,7 @@ class DRResult:
 
 def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
           full_reorth=False, residual=None, oversolve=1.0, eig_stop=None, progress=None,
-          plan_hook=None):
+          plan_hook=None, eig_only=False):
     """Lan-DR(m,k) for hermitian positive definite A (Sec. 1, Sec. 2).
 
     Cycle 1: x0 = 0, r0 = b, v1 = r0/||r0||, Lanczos to j = m.  Each cycle:
@@ -313,7 +313,11 @@ def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
     (default ||b - A x|| / ||b||, evaluated once per cycle).  `eig_stop`
     turns the routine into an eigensolver: it stops as soon as the lowest
     Ritz pair has a residual <= eig_stop (or, for a callable,
-    eig_stop(value, residual) is true).
+    eig_stop(value, residual) is true).  `eig_only` is the eigensolver use
+    of all k kept pairs (Sec. 2: the eigenvectors are the product handed to
+    later right-hand sides): it stops as soon as every kept Ritz residual is
+    <= tol_eig, whatever the linear residual, and `info.converged` says
+    whether they did.
     """
     # Converged kept Ritz vectors attract rounding errors in every new Lanczos
     # vector (the loss of orthogonality grows like eps ||A|| / Ritz residual), so
@@ -322,12 +326,12 @@ def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
         reorth_period = 1
     return _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth,
                residual, oversolve, harmonic=False, eig_stop=eig_stop, progress=progress,
-               plan_hook=plan_hook)
+               plan_hook=plan_hook, eig_only=eig_only)
 
 
 def minresdr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
              full_reorth=False, residual=None, oversolve=1.0, eig_stop=None, progress=None,
-             plan_hook=None):
+             plan_hook=None, eig_only=False):
     """MinRes-DR(m,k) for hermitian, possibly indefinite A (Sec. 1, Sec. 2).
 
     Same Lanczos and restart skeleton as Lan-DR, with (GMRES-DR read for a
@@ -342,11 +346,12 @@ def minresdr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=
          unit direction is used so the step stays exact once ||s|| is tiny); V_{k+1} <- V_{m+1} P_{k+1}; Tbar_k <- P_{k+1}^T Tbar_m P_k
          (k x k block symmetric, not diagonal); c <- P_{k+1}^T s.
     The kept-space values reported are the Rayleigh quotients over span(V_k)
-    (eigenvalues of V_k^dag A V_k = top k x k block of Tbar_k); stopping as Lan-DR.
+    (eigenvalues of V_k^dag A V_k = top k x k block of Tbar_k); stopping as Lan-DR
+    (`eig_only`: every kept harmonic Ritz residual <= tol_eig).
     """
     return _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth,
                residual, oversolve, harmonic=True, eig_stop=eig_stop, progress=progress,
-               plan_hook=plan_hook)
+               plan_hook=plan_hook, eig_only=eig_only)
 
 
 def _mgs_columns(P):
@@ -429,7 +434,7 @@ def _rayleigh_ritz(T, k):
 
 
 def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residual,
-        oversolve, harmonic, eig_stop=None, progress=None, plan_hook=None):
+        oversolve, harmonic, eig_stop=None, progress=None, plan_hook=None, eig_only=False):
     b = np.asarray(b, dtype=np.complex128)
     n = b.size
     bn = _norm(b)
@@ -477,7 +482,9 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
             progress(cycle, info.mvps, rel, theta_k, ritz_res)
         over = mvps_at_conv is not None and (info.mvps - mvps_at_conv) >= oversolve * mvps_at_conv
         last = cycle == max_cycles - 1
-        if lin_ok and (eig_ok or over):
+        if eig_only:
+            info.converged = eig_ok
+        elif lin_ok and (eig_ok or over):
             info.converged = True
         if eig_stop is not None:
             # eigenvalue-only use: stop once the pair nearest zero (harmonic) or the

@@ -17,8 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdlz.so")
-SOURCES = ["wilson.cu", "wilson_bf16.cu", "dr.cu", "solvers.cu", "solvers_mixed.cu", "minres_fused.cu",
-           "cg_fused.cu", "minres_multi.cu", "api.cu", "ptc.cu", "restart_gemm.cu", "small_dense.cpp", "restart_plan.cpp"]
+SOURCES = ["wilson.cu", "wilson_eo.cu", "wilson_bf16.cu", "dr.cu", "solvers.cu", "solvers_mixed.cu", "minres_fused.cu",
+           "cg_fused.cu", "minres_multi.cu", "api.cu", "ptc.cu", "tc_gemm.cu", "small_dense.cpp", "restart_plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcublas", "-cudart", "shared",
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared",
                                                          "-Xlinker", "-rpath=/usr/local/cuda/lib64",
                                                          "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -59,12 +59,18 @@ void Profiler::begin(bool on, bool f32) {
     capture = nullptr;
     sampled_ms = sampled_bytes = 0.0;
     sampled = 0;
+    for (int t = 0; t < kTags; ++t) tag_ms[t] = tag_bytes[t] = 0.0, tag_n[t] = 0;
+    pair_tag.clear();
+    pair_bytes.clear();
 }
-void Profiler::stencil_start(cudaStream_t s, bool f32, long long sites, int nrhs, int reals_per_rhs) {
+void Profiler::stencil_start(cudaStream_t s, bool f32, long long sites, int nrhs, int reals_per_rhs,
+                             int tag, int link_reals) {
     armed = enabled && f32 == hot_f32;
     if (!armed) return;
-    const double nbytes = f32 ? (double)sites * ((double)reals_per_rhs * nrhs + 48.0) * 4.0
-                              : (double)sites * ((double)reals_per_rhs * nrhs + 72.0) * 8.0;
+    cur_tag = (tag >= 0 && tag < kTags) ? tag : 0;
+    const double lr = link_reals >= 0 ? (double)link_reals : (f32 ? 48.0 : 72.0);
+    const double nbytes = f32 ? (double)sites * ((double)reals_per_rhs * nrhs + lr) * 4.0
+                              : (double)sites * ((double)reals_per_rhs * nrhs + lr) * 8.0;
     if (capture) {
         // inside a graph capture: an external event node, owned by the graph
         cudaEvent_t a, b;
@@ -73,6 +79,7 @@ void Profiler::stencil_start(cudaStream_t s, bool f32, long long sites, int nrhs
         capture->ev.push_back(a);
         capture->ev.push_back(b);
         capture->bytes.push_back(nbytes);
+        capture->tags.push_back(cur_tag);
         cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
         return;
     }
@@ -86,6 +93,8 @@ void Profiler::stencil_start(cudaStream_t s, bool f32, long long sites, int nrhs
     cudaEventRecord(pool[used], s);
     stencils++;
     stencil_bytes += nbytes;
+    pair_tag.push_back(cur_tag);
+    pair_bytes.push_back(nbytes);
 }
 void Profiler::stencil_stop(cudaStream_t s) {
     if (!armed) return;
@@ -103,8 +112,15 @@ double Profiler::stencil_ms() {
     for (size_t i = 0; i + 1 < used; i += 2) {
         float ms = 0.f;
         cudaEventSynchronize(pool[i + 1]);
-        if (cudaEventElapsedTime(&ms, pool[i], pool[i + 1]) == cudaSuccess) tot += ms;
-        else cudaGetLastError();
+        if (cudaEventElapsedTime(&ms, pool[i], pool[i + 1]) == cudaSuccess) {
+            tot += ms;
+            const int t = pair_tag[i / 2];
+            tag_ms[t] += ms;
+            tag_bytes[t] += pair_bytes[i / 2];
+            tag_n[t]++;
+        } else {
+            cudaGetLastError();
+        }
     }
     return tot;
 }
@@ -228,6 +244,7 @@ int check_params(const dlz_params *p) {
     if (p->precision != DLZ_F64 && p->precision != DLZ_F32) return fail(DLZ_ERR_BADARG, "precision");
     if (!(p->reliable_delta > 0.0 && p->reliable_delta < 1.0)) return fail(DLZ_ERR_BADARG, "reliable_delta must be in (0, 1)");
     if (p->finish != 0 && p->finish != 1) return fail(DLZ_ERR_BADARG, "finish must be 0 or 1");
+    if (p->eig_only != 0 && p->eig_only != 1) return fail(DLZ_ERR_BADARG, "eig_only must be 0 or 1");
     return DLZ_OK;
 }
 
@@ -245,6 +262,11 @@ struct CallStats {
             st.stencil_ms = op.prof.stencil_ms() + op.prof.sampled_ms;
             st.stencil_launches = op.prof.stencils + op.prof.sampled;
             st.stencil_bytes = op.prof.stencil_bytes + op.prof.sampled_bytes;
+            for (int t = 0; t < Profiler::kTags; ++t) {
+                st.kernel_ms[t] = op.prof.tag_ms[t];
+                st.kernel_bytes[t] = op.prof.tag_bytes[t];
+                st.kernel_launches[t] = op.prof.tag_n[t];
+            }
         }
     }
 };
@@ -299,6 +321,7 @@ int dlz_params_default(dlz_params *p) {
     p->check_every = 16;
     p->profile = 0;
     p->finish = 0;
+    p->eig_only = 0;
     return DLZ_OK;
 }
 
@@ -393,12 +416,86 @@ int dlz_op_volume(dlz_op_t h, long long *V) {
     return DLZ_OK;
 }
 
+int dlz_create_operator_eo(const int dims[4], const void *gauge, double kappa, int bc_t, void *stream,
+                           dlz_op_t *out) {
+    if (!dims || !out) return fail(DLZ_ERR_BADARG, "null argument");
+    *out = nullptr;
+    for (int i = 0; i < 4; ++i)
+        if (dims[i] < 2 || dims[i] % 2) return fail(DLZ_ERR_BADARG, "even-odd operator needs every lattice extent even");
+    dlz_op_t h = nullptr;
+    DLZ_TRY(dlz_create_operator(dims, gauge, kappa, bc_t, stream, &h));
+    Op &op = h->op;
+    op.gf = op.g;
+    op.g.V = op.gf.V / 2;
+    op.eo = true;
+    const size_t vh = (size_t)op.g.V;
+    int rc = op.eo_tmp64.alloc((size_t)kEoBatch * 12 * vh * sizeof(double2));
+    if (rc == DLZ_OK) rc = op.eo_tmp32.alloc((size_t)kEoBatch * 6 * vh * sizeof(float4));
+    if (rc != DLZ_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return DLZ_OK;
+}
+
+static int check_eo(dlz_op_t h) {
+    DLZ_TRY(check_op(h));
+    if (!h->op.eo) return fail(DLZ_ERR_BADARG, "not an even-odd operator (dlz_create_operator_eo)");
+    return DLZ_OK;
+}
+
+int dlz_eo_prepare(dlz_op_t h, const void *b, void *b_e, int nrhs) {
+    DLZ_TRY(check_eo(h));
+    if (nrhs < 0) return fail(DLZ_ERR_BADARG, "nrhs < 0");
+    if (nrhs == 0) return DLZ_OK;
+    if (!b || !b_e) return fail(DLZ_ERR_BADARG, "null vector");
+    Op &op = h->op;
+    op.prof.begin(false, false);
+    const long nf = 12L * op.gf.V, nh = 12L * op.g.V;
+    Staged sb, so;
+    DLZ_TRY(sb.in(op, b, (size_t)nf * nrhs * sizeof(double2)));
+    DLZ_TRY(so.out(op, b_e, (size_t)nh * nrhs * sizeof(double2)));
+    DevBuf be, bo;
+    DLZ_TRY(be.alloc((size_t)nh * sizeof(double2)));
+    DLZ_TRY(bo.alloc((size_t)nh * sizeof(double2)));
+    for (int r = 0; r < nrhs; ++r) {
+        DLZ_TRY(eo_prepare64(op, be.as<double2>(), bo.as<double2>(), (const double2 *)sb.dev + (size_t)r * nf));
+        DLZ_TRY(unpack64(op, (double2 *)so.dev + (size_t)r * nh, be.as<double2>()));
+    }
+    return so.flush(op);
+}
+
+int dlz_eo_reconstruct(dlz_op_t h, const void *x_e, const void *b, void *x, int nrhs) {
+    DLZ_TRY(check_eo(h));
+    if (nrhs < 0) return fail(DLZ_ERR_BADARG, "nrhs < 0");
+    if (nrhs == 0) return DLZ_OK;
+    if (!x_e || !b || !x) return fail(DLZ_ERR_BADARG, "null vector");
+    Op &op = h->op;
+    op.prof.begin(false, false);
+    const long nf = 12L * op.gf.V, nh = 12L * op.g.V;
+    Staged sxe, sb, sx;
+    DLZ_TRY(sxe.in(op, x_e, (size_t)nh * nrhs * sizeof(double2)));
+    DLZ_TRY(sb.in(op, b, (size_t)nf * nrhs * sizeof(double2)));
+    DLZ_TRY(sx.out(op, x, (size_t)nf * nrhs * sizeof(double2)));
+    DevBuf xe, bo;
+    DLZ_TRY(xe.alloc((size_t)nh * sizeof(double2)));
+    DLZ_TRY(bo.alloc((size_t)nh * sizeof(double2)));
+    for (int r = 0; r < nrhs; ++r) {
+        DLZ_TRY(pack64(op, xe.as<double2>(), (const double2 *)sxe.dev + (size_t)r * nh));
+        DLZ_TRY(eo_reconstruct64(op, (double2 *)sx.dev + (size_t)r * nf, xe.as<double2>(), bo.as<double2>(),
+                                 (const double2 *)sb.dev + (size_t)r * nf));
+    }
+    return sx.flush(op);
+}
+
 int dlz_apply(dlz_op_t h, int which, const void *in, void *out, int dtype, int nrhs) {
     DLZ_TRY(check_op(h));
     Op &op = h->op;
     if (nrhs < 0) return fail(DLZ_ERR_BADARG, "nrhs < 0");
     if (which < DLZ_D || which > DLZ_DDAGD) return fail(DLZ_ERR_BADARG, "which");
     if (dtype != DLZ_F64 && dtype != DLZ_F32 && dtype != DLZ_BF16) return fail(DLZ_ERR_BADARG, "dtype");
+    if (dtype == DLZ_BF16 && op.eo) return fail(DLZ_ERR_BADARG, "bfloat16 storage is not built for even-odd operators");
     if (nrhs == 0) return DLZ_OK;
     if (!in || !out) return fail(DLZ_ERR_BADARG, "null vector");
     op.prof.begin(false, false);
@@ -494,6 +591,7 @@ int dlz_batch_dminres(int nlat, dlz_op_t *ops, dlz_defl_t *defls, const void *co
     int total = 0;
     for (int l = 0; l < nlat; ++l) {
         if (!ops[l]) return fail(DLZ_ERR_BADARG, "null operator");
+        if (ops[l]->op.eo) return fail(DLZ_ERR_BADARG, "dlz_batch_dminres takes full-lattice operators");
         if (nrhs[l] < 0 || nrhs[l] > 16) return fail(DLZ_ERR_BADARG, "nrhs per lattice must be in [0, 16]");
         if (nrhs[l] > 0 && (!B[l] || !X[l])) return fail(DLZ_ERR_BADARG, "null vector");
         if (defls && defls[l]) {
@@ -560,6 +658,15 @@ int dlz_batch_dminres(int nlat, dlz_op_t *ops, dlz_defl_t *defls, const void *co
     return rc;
 }
 
+int dlz_batch_last_choice(dlz_op_t h, int *form, int *chunks_per_block, int *half_grid) {
+    DLZ_TRY(check_op(h));
+    const int c = h->op.multi_choice;
+    if (form) *form = c / 100;
+    if (chunks_per_block) *chunks_per_block = (c / 10) % 10;
+    if (half_grid) *half_grid = c % 10;
+    return DLZ_OK;
+}
+
 int dlz_stencil_bench(dlz_op_t h, int dtype, int which, int nrhs, int iters, const void *in,
                       double *ms_per_launch) {
     DLZ_TRY(check_op(h));
@@ -567,6 +674,7 @@ int dlz_stencil_bench(dlz_op_t h, int dtype, int which, int nrhs, int iters, con
     if (!in || !ms_per_launch || nrhs < 1 || nrhs > 64 || iters < 1) return fail(DLZ_ERR_BADARG, "stencil_bench arguments");
     if (which != DLZ_D && which != DLZ_DDAG && which != DLZ_Q) return fail(DLZ_ERR_BADARG, "which");
     if (dtype != DLZ_F64 && dtype != DLZ_F32 && dtype != DLZ_BF16) return fail(DLZ_ERR_BADARG, "dtype");
+    if (dtype == DLZ_BF16 && op.eo) return fail(DLZ_ERR_BADARG, "bfloat16 storage is not built for even-odd operators");
     op.prof.begin(false, false);
     const long n = 12L * op.g.V;
     const size_t esz = dtype == DLZ_F64 ? sizeof(double2) : sizeof(float2);
@@ -687,6 +795,11 @@ static int dsolve_entry(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nr
                 sts[q].stencil_ms = shared.stencil_ms / nb;
                 sts[q].stencil_launches = shared.stencil_launches / nb;
                 sts[q].stencil_bytes = shared.stencil_bytes / nb;
+                for (int t = 0; t < 3; ++t) {
+                    sts[q].kernel_ms[t] = shared.kernel_ms[t] / nb;
+                    sts[q].kernel_bytes[t] = shared.kernel_bytes[t] / nb;
+                    sts[q].kernel_launches[t] = shared.kernel_launches[t] / nb;
+                }
                 if (stats) stats[r0 + q] = sts[q];
             }
         }
@@ -780,7 +893,7 @@ int dlz_defl_save(dlz_defl_t d, const char *path) {
     hd.bc_t = op.g.bc_t;
     hd.k = d->k;
     hd.which = d->which;
-    hd.reserved = 0;
+    hd.reserved = op.eo ? 1 : 0;        // 1: even-site vectors of an even-odd operator
     hd.kappa = op.kappa;
     std::vector<double2> host((size_t)n);
     DevBuf tmp;
@@ -810,6 +923,7 @@ int dlz_defl_load(dlz_op_t h, const char *path, dlz_defl_t *out) {
     bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, kMagic, 8) == 0;
     for (int i = 0; ok && i < 4; ++i) ok = hd.dims[i] == op.g.L[i];
     ok = ok && hd.bc_t == op.g.bc_t && hd.kappa == op.kappa && hd.k >= 0 && hd.k <= 1000 &&
+         hd.reserved == (op.eo ? 1 : 0) &&
          (hd.which == DLZ_Q || hd.which == DLZ_DDAGD);
     if (!ok) {
         std::fclose(f);

@@ -1,20 +1,21 @@
 // Fused FP32 CG on the normal equations (CGNR) for a batch of right-hand sides:
 // the inner solve of the mixed-precision D-CG (arXiv:0901.3163, Sec. 2: CG on
-// D^dag D).  For D e = s0 it iterates, per right-hand side,
+// D^dag D).  For D e = s0 it iterates, per right-hand side, CG on D^dag D e = D^dag s0
+// with the residual of D e = s0 carried alongside:
 //   p = r + beta p,  t = D p,  alpha = |r|^2 / |t|^2,
-//   e += alpha p,  s -= alpha t,  r = D^dag s,  beta = |r_new|^2 / |r|^2,
-// with s the residual of D e = s0 (so |s| is the quantity the outer FP64 loop
-// needs) and r = D^dag s the CG residual of D^dag D e = D^dag s0.
-//
-// Two full-vector kernels per iteration, each with its stencil:
-//   K1:  p_new = r + beta p (formed on the fly at every site the stencil reads),
-//        written once; t = D p_new; block partials of |t|^2.
-//   K23: s_new = s - alpha t (formed on the fly likewise), written once;
-//        e += alpha p_new; r = D^dag s_new; block partials of |r|^2 and |s_new|^2.
-// plus one-block-per-RHS kernels that sum the partials in a fixed order and
-// update the step lengths.  p and s alternate between two buffers (a stencil
-// must not read what its own launch writes), so six iterations form a CUDA
-// graph that is captured once and replayed.
+//   e += alpha p,  s -= alpha t,  r -= alpha D^dag t,  beta = |r_new|^2 / |r|^2,
+// s being the residual of D e = s0 (|s| is the quantity the outer FP64 loop needs)
+// and r = D^dag s the CG residual (r starts as D^dag s0 and is then updated by the
+// recurrence, as in CG on any hermitian matrix).  Since D p = D r + beta D p_old, the
+// image t is carried too, so that each kernel applies its stencil to ONE vector:
+//   K1:  t = D r + beta t (the stencil gathers r), p = r + beta p;
+//        block partials of |t|^2.
+//   K23: z = D^dag t (the stencil gathers t); r -= alpha z, s -= alpha t, e += alpha p;
+//        block partials of |r|^2 and |s|^2.
+// Each kernel writes only vectors it does not gather (and only at its own site), so
+// every vector is updated in place.  One-block-per-RHS kernels sum the partials in a
+// fixed order and update the step lengths; six iterations form a CUDA graph that is
+// captured once and replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -25,6 +26,7 @@
 #include "krylov_util.cuh"
 #include "reduce.cuh"
 #include "solvers.h"
+#include "wilson_eo_site.cuh"
 #include "wilson_site.cuh"
 
 namespace dlz {
@@ -39,67 +41,6 @@ struct CgFusedState {        // one per right-hand side
 namespace {
 
 constexpr int kT = 128;
-
-__device__ inline void load_ab(const float4 *__restrict__ A, const float4 *__restrict__ B, float cb, int V, int s,
-                               float2 (&p)[12]) {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        const float4 a = A[(size_t)c * V + s], b = B[(size_t)c * V + s];
-        p[2 * c] = make_float2(fmaf(cb, b.x, a.x), fmaf(cb, b.y, a.y));
-        p[2 * c + 1] = make_float2(fmaf(cb, b.z, a.z), fmaf(cb, b.w, a.w));
-    }
-}
-
-template <int MU, bool G5IN>
-__device__ inline void hop_pair_ab(int s, const int (&c)[4], const Geom &g, int stride, const float4 *__restrict__ A,
-                                   const float4 *__restrict__ B, float cb, const float4 *__restrict__ U,
-                                   float2 (&acc)[12]) {
-    const int L = g.L[MU];
-    const int sf = (c[MU] == L - 1) ? s - (L - 1) * stride : s + stride;
-    const float phf = (MU == 3 && c[3] == L - 1) ? (float)g.bc_t : 1.f;
-    const int sb = (c[MU] == 0) ? s + (L - 1) * stride : s - stride;
-    const float phb = (MU == 3 && c[3] == 0) ? (float)g.bc_t : 1.f;
-    float2 p[12], u[9];
-    load_ab(A, B, cb, g.V, sf, p);
-    maybe_g5<G5IN>(p);
-    load_link<float>(U, g.V, MU, s, u);
-    hop_fwd<float, MU>(p, u, phf, acc);
-    load_ab(A, B, cb, g.V, sb, p);
-    maybe_g5<G5IN>(p);
-    load_link<float>(U, g.V, MU, sb, u);
-    hop_bwd<float, MU>(p, u, phb, acc);
-}
-
-// out = [g5]^G5OUT (1 - kappa H) [g5]^G5IN (A + cb B) at site s; self = (A + cb B)(s)
-template <bool G5IN, bool G5OUT>
-__device__ inline void wilson_site_ab(int s, const Geom &g, float kappa, const float4 *__restrict__ A,
-                                      const float4 *__restrict__ B, float cb, const float4 *__restrict__ U,
-                                      float2 (&out)[12], float2 (&self)[12]) {
-    int c[4];
-    int r = s;
-    c[0] = r % g.L[0]; r /= g.L[0];
-    c[1] = r % g.L[1]; r /= g.L[1];
-    c[2] = r % g.L[2];
-    c[3] = r / g.L[2];
-    const int st1 = g.L[0], st2 = g.L[0] * g.L[1], st3 = st2 * g.L[2];
-    float2 acc[12];
-#pragma unroll
-    for (int a = 0; a < 12; ++a) acc[a] = make_float2(0.f, 0.f);
-    hop_pair_ab<0, G5IN>(s, c, g, 1, A, B, cb, U, acc);
-    hop_pair_ab<1, G5IN>(s, c, g, st1, A, B, cb, U, acc);
-    hop_pair_ab<2, G5IN>(s, c, g, st2, A, B, cb, U, acc);
-    hop_pair_ab<3, G5IN>(s, c, g, st3, A, B, cb, U, acc);
-    load_ab(A, B, cb, g.V, s, self);
-#pragma unroll
-    for (int a = 0; a < 12; ++a) out[a] = self[a];
-    maybe_g5<G5IN>(out);
-#pragma unroll
-    for (int a = 0; a < 12; ++a) {
-        out[a].x = out[a].x - kappa * acc[a].x;
-        out[a].y = out[a].y - kappa * acc[a].y;
-    }
-    maybe_g5<G5OUT>(out);
-}
 
 __device__ inline float nrm(const float2 (&v)[12]) {
     float a = 0.f;
@@ -131,52 +72,177 @@ __device__ inline void block_partials(float (&v)[NV], double *__restrict__ out, 
     }
 }
 
-__global__ void __launch_bounds__(kT)
-k_cg_k1(const float4 *__restrict__ R, const float4 *__restrict__ Pold, float4 *__restrict__ Pnew,
-        float4 *__restrict__ T, const float4 *__restrict__ links, Geom g, float kappa, int N,
-        const CgFusedState *__restrict__ st, double *__restrict__ partials) {
+__device__ inline void axpy_store(float4 *__restrict__ P, size_t base, int V, int s, float a,
+                                  const float2 (&x)[12], float2 (&y)[12]) {
+    // y = x + a y at site s (y read from and written back to P)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const size_t i = base + (size_t)c * V + s;
+        const float4 q = P[i];
+        const float2 x0 = x[2 * c], x1 = x[2 * c + 1];
+        const float4 r = make_float4(fmaf(a, q.x, x0.x), fmaf(a, q.y, x0.y), fmaf(a, q.z, x1.x), fmaf(a, q.w, x1.y));
+        P[i] = r;
+        y[2 * c] = make_float2(r.x, r.y);
+        y[2 * c + 1] = make_float2(r.z, r.w);
+    }
+}
+
+// K1: t = D r + beta t, p = r + beta p; partial |t|^2.  Gathers r only.
+__global__ void __launch_bounds__(kT, 6)
+k_cg_k1(const float4 *__restrict__ R, float4 *__restrict__ P, float4 *__restrict__ T,
+        const float4 *__restrict__ links, Geom g, float kappa, int N, const CgFusedState *__restrict__ st,
+        double *__restrict__ partials) {
     const int q = blockIdx.x % N;
     const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
     const size_t base = (size_t)q * 6 * g.V;
+    if (threadIdx.x == 0) {
+        const int s0 = (blockIdx.x / N) * blockDim.x, nb = min((int)blockDim.x, g.V - s0);
+        prefetch_planes_l2(R + base, 6, g.V, s0, nb);
+        prefetch_planes_l2(T + base, 6, g.V, s0, nb);
+        prefetch_planes_l2(P + base, 6, g.V, s0, nb);
+        if (q == 0) prefetch_planes_l2(links, 12, g.V, s0, nb);
+    }
     float v[1] = {0.f};
     if (s < g.V) {
         const float bt = st[q].f[1];
-        float2 o[12], self[12];
-        wilson_site_ab<false, false>(s, g, kappa, R + base, Pold + base, bt, links, o, self);
-        Field<float>::store(Pnew + base, g.V, s, self);
-        Field<float>::store(T + base, g.V, s, o);
-        v[0] = nrm(o);
+        float2 o[12], t[12];
+        wilson_site<float, false, false>(s, g, kappa, R + base, links, o);
+        axpy_store(T, base, g.V, s, bt, o, t);
+        v[0] = nrm(t);
+        float2 r[12], pn[12];
+        Field<float>::load(R + base, g.V, s, r);
+        axpy_store(P, base, g.V, s, bt, r, pn);
     }
     const int nbq = gridDim.x / N;
     block_partials<1>(v, partials + (size_t)q * nbq + blockIdx.x / N, 0);
 }
 
-__global__ void __launch_bounds__(kT)
-k_cg_k23(const float4 *__restrict__ S, const float4 *__restrict__ T, float4 *__restrict__ Snew,
-         const float4 *__restrict__ Pnew, float4 *__restrict__ E, float4 *__restrict__ R,
-         const float4 *__restrict__ links, Geom g, float kappa, int N, const CgFusedState *__restrict__ st,
-         double *__restrict__ partials) {
+// K23: r -= alpha D^dag t, s -= alpha t, e += alpha p; partials |r|^2, |s|^2.  Gathers t only.
+__global__ void __launch_bounds__(kT, 6)
+k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restrict__ S, const float4 *__restrict__ P,
+         float4 *__restrict__ E, const float4 *__restrict__ links, Geom g, float kappa, int N,
+         const CgFusedState *__restrict__ st, double *__restrict__ partials) {
     const int q = blockIdx.x % N;
     const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
     const size_t base = (size_t)q * 6 * g.V;
+    if (threadIdx.x == 0) {
+        const int s0 = (blockIdx.x / N) * blockDim.x, nb = min((int)blockDim.x, g.V - s0);
+        prefetch_planes_l2(T + base, 6, g.V, s0, nb);
+        prefetch_planes_l2(R + base, 6, g.V, s0, nb);
+        prefetch_planes_l2(S + base, 6, g.V, s0, nb);
+        prefetch_planes_l2(P + base, 6, g.V, s0, nb);
+        prefetch_planes_l2(E + base, 6, g.V, s0, nb);
+        if (q == 0) prefetch_planes_l2(links, 12, g.V, s0, nb);
+    }
     float v[2] = {0.f, 0.f};
     if (s < g.V) {
         const float al = st[q].f[0];
-        float2 o[12], self[12];
-        wilson_site_ab<true, true>(s, g, kappa, S + base, T + base, -al, links, o, self);
-        Field<float>::store(Snew + base, g.V, s, self);
-        Field<float>::store(R + base, g.V, s, o);
+        float2 z[12];
+        wilson_site<float, true, true>(s, g, kappa, T + base, links, z);
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const size_t i = base + (size_t)c * g.V + s;
-            const float4 p = Pnew[i];
+            const float2 z0 = z[2 * c], z1 = z[2 * c + 1];
+            float4 r = R[i];
+            r.x = fmaf(-al, z0.x, r.x); r.y = fmaf(-al, z0.y, r.y);
+            r.z = fmaf(-al, z1.x, r.z); r.w = fmaf(-al, z1.y, r.w);
+            R[i] = r;
+            v[0] += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+            const float4 t = T[i];
+            float4 sv = S[i];
+            sv.x = fmaf(-al, t.x, sv.x); sv.y = fmaf(-al, t.y, sv.y);
+            sv.z = fmaf(-al, t.z, sv.z); sv.w = fmaf(-al, t.w, sv.w);
+            S[i] = sv;
+            v[1] += sv.x * sv.x + sv.y * sv.y + sv.z * sv.z + sv.w * sv.w;
+            const float4 pv = P[i];
             float4 e = E[i];
-            e.x = fmaf(al, p.x, e.x); e.y = fmaf(al, p.y, e.y);
-            e.z = fmaf(al, p.z, e.z); e.w = fmaf(al, p.w, e.w);
+            e.x = fmaf(al, pv.x, e.x); e.y = fmaf(al, pv.y, e.y);
+            e.z = fmaf(al, pv.z, e.z); e.w = fmaf(al, pv.w, e.w);
             E[i] = e;
         }
-        v[0] = nrm(o);
-        v[1] = nrm(self);
+    }
+    const int nbq = gridDim.x / N;
+    block_partials<2>(v, partials + (size_t)q * nbq + blockIdx.x / N, (size_t)N * nbq);
+}
+
+// Even-odd operator (Dhat on the even sites): each stencil is two launches, the odd
+// hop (eo_hop32, gathering r or gamma5 t) and these Schur-step kernels at the even
+// sites, which gather the odd field and carry the same updates as K1 and K23.
+// K1b: t = Dhat r + beta t = (r - kappa^2 H_eo m) + beta t with m = H_oe r, p = r + beta p.
+__global__ void __launch_bounds__(kT, 6)
+k_cg_eo_k1b(const float4 *__restrict__ R, const float4 *__restrict__ M, float4 *__restrict__ P, float4 *__restrict__ T,
+            const float4 *__restrict__ links, Geom gf, float kappa2, int N, const CgFusedState *__restrict__ st,
+            double *__restrict__ partials) {
+    const int q = blockIdx.x % N;
+    const int cb = (blockIdx.x / N) * blockDim.x + threadIdx.x;
+    const int Vh = gf.V >> 1;
+    const size_t base = (size_t)q * 6 * Vh;
+    if (threadIdx.x == 0) {
+        const int c0 = (blockIdx.x / N) * blockDim.x, nb = min((int)blockDim.x, Vh - c0);
+        prefetch_planes_l2(R + base, 6, Vh, c0, nb);
+        prefetch_planes_l2(T + base, 6, Vh, c0, nb);
+        prefetch_planes_l2(P + base, 6, Vh, c0, nb);
+    }
+    float v[1] = {0.f};
+    if (cb < Vh) {
+        const float bt = st[q].f[1];
+        float2 o[12], t[12];
+        wilson_eo_schur_site<float, false, false>(cb, gf, kappa2, R + base, M + base, links, o);
+        axpy_store(T, base, Vh, cb, bt, o, t);
+        v[0] = nrm(t);
+        float2 r[12], pn[12];
+        Field<float>::load(R + base, Vh, cb, r);
+        axpy_store(P, base, Vh, cb, bt, r, pn);
+    }
+    const int nbq = gridDim.x / N;
+    block_partials<1>(v, partials + (size_t)q * nbq + blockIdx.x / N, 0);
+}
+
+// K23b: z = Dhat^dag t = gamma5 (gamma5 t - kappa^2 H_eo m), m = H_oe gamma5 t;
+// r -= alpha z, s -= alpha t, e += alpha p.
+__global__ void __launch_bounds__(kT, 6)
+k_cg_eo_k23b(const float4 *__restrict__ T, const float4 *__restrict__ M, float4 *__restrict__ R,
+             float4 *__restrict__ S, const float4 *__restrict__ P, float4 *__restrict__ E,
+             const float4 *__restrict__ links, Geom gf, float kappa2, int N, const CgFusedState *__restrict__ st,
+             double *__restrict__ partials) {
+    const int q = blockIdx.x % N;
+    const int cb = (blockIdx.x / N) * blockDim.x + threadIdx.x;
+    const int Vh = gf.V >> 1;
+    const size_t base = (size_t)q * 6 * Vh;
+    if (threadIdx.x == 0) {
+        const int c0 = (blockIdx.x / N) * blockDim.x, nb = min((int)blockDim.x, Vh - c0);
+        prefetch_planes_l2(T + base, 6, Vh, c0, nb);
+        prefetch_planes_l2(R + base, 6, Vh, c0, nb);
+        prefetch_planes_l2(S + base, 6, Vh, c0, nb);
+        prefetch_planes_l2(P + base, 6, Vh, c0, nb);
+        prefetch_planes_l2(E + base, 6, Vh, c0, nb);
+    }
+    float v[2] = {0.f, 0.f};
+    if (cb < Vh) {
+        const float al = st[q].f[0];
+        float2 z[12];
+        wilson_eo_schur_site<float, true, true>(cb, gf, kappa2, T + base, M + base, links, z);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const size_t i = base + (size_t)c * Vh + cb;
+            const float2 z0 = z[2 * c], z1 = z[2 * c + 1];
+            float4 r = R[i];
+            r.x = fmaf(-al, z0.x, r.x); r.y = fmaf(-al, z0.y, r.y);
+            r.z = fmaf(-al, z1.x, r.z); r.w = fmaf(-al, z1.y, r.w);
+            R[i] = r;
+            v[0] += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+            const float4 t = T[i];
+            float4 sv = S[i];
+            sv.x = fmaf(-al, t.x, sv.x); sv.y = fmaf(-al, t.y, sv.y);
+            sv.z = fmaf(-al, t.z, sv.z); sv.w = fmaf(-al, t.w, sv.w);
+            S[i] = sv;
+            v[1] += sv.x * sv.x + sv.y * sv.y + sv.z * sv.z + sv.w * sv.w;
+            const float4 pv = P[i];
+            float4 e = E[i];
+            e.x = fmaf(al, pv.x, e.x); e.y = fmaf(al, pv.y, e.y);
+            e.z = fmaf(al, pv.z, e.z); e.w = fmaf(al, pv.w, e.w);
+            E[i] = e;
+        }
     }
     const int nbq = gridDim.x / N;
     block_partials<2>(v, partials + (size_t)q * nbq + blockIdx.x / N, (size_t)N * nbq);
@@ -235,24 +301,56 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
     const float4 *links = op.gauge32.as<float4>();
     const unsigned blocks = (unsigned)(((g.V + kT - 1) / kT) * N);
     const int nbq = (int)(blocks / N);
-    float4 *S[2] = {s0, bufs[0]}, *P[2] = {bufs[1], bufs[2]}, *T = bufs[3], *R = bufs[4];
-    for (float4 *z : {P[0], P[1], T})
+    float4 *S = s0, *R = bufs[0], *P = bufs[1], *T = bufs[2];
+    // p = t = 0 so that the first K1 (beta = 0) gives p = r, t = D r
+    for (float4 *z : {P, T})
         DLZ_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)N * n * sizeof(float4), op.stream));
     DLZ_CUDA_TRY(cudaMemsetAsync(ms, 0, (size_t)N * sizeof(CgFusedState), op.stream));
-    // r = D^dag s0 (K23 with alpha = 0), gamma = |r|^2, beta = 0
-    k_cg_k23<<<blocks, kT, 0, op.stream>>>(S[0], T, S[1], P[0], e, R, links, g, kappa, N, ms, partials);
+    // r = D^dag s0; gamma = |r|^2, |s0|^2 (K23 with t = 0 and alpha = 0 would not form
+    // D^dag s0, so the plain batched stencil does it, and K23 with alpha = 0 sums)
+    DLZ_TRY(wilson32_batch(op, R, S, DLZ_DDAG, N));
+    if (op.eo) {
+        // t = 0: the odd hop of it is 0 and K23b only sums |r|^2 and |s|^2
+        float4 *M = op.eo_tmp32.as<float4>();
+        DLZ_CUDA_TRY(cudaMemsetAsync(M, 0, (size_t)N * n * sizeof(float4), op.stream));
+        k_cg_eo_k23b<<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, (float)(op.kappa * op.kappa), N,
+                                                   ms, partials);
+    } else {
+        k_cg_k23<<<blocks, kT, 0, op.stream>>>(T, R, S, P, e, links, g, kappa, N, ms, partials);
+    }
     k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 1, ms);
     op.prof.launches += 2;
     DLZ_CUDA_TRY(cudaGetLastError());
-    auto iteration = [&](const float4 *pold, float4 *pnew, const float4 *sc, float4 *sn) -> int {
-        // K1 moves 96 reals per site and RHS (r, p read; p_new, t written) + links
-        op.prof.stencil_start(op.stream, true, g.V, N, 96);
-        k_cg_k1<<<blocks, kT, 0, op.stream>>>(R, pold, pnew, T, links, g, kappa, N, ms, partials);
+    auto iteration = [&]() -> int {
+        if (op.eo) {
+            // even-odd: K1 = odd hop + K1b, K23 = odd hop + K23b (m: the odd work field).
+            // Per even site and RHS, K1 moves 192 reals (r gathered by the hop, m written,
+            // m gathered, r, t, p read, t, p written), K23 264; each pair reads every link
+            // twice (192 reals per even site)
+            float4 *M = op.eo_tmp32.as<float4>();
+            const float kappa2 = (float)(op.kappa * op.kappa);
+            op.prof.stencil_start(op.stream, true, g.V, N, 192, 1, 192);
+            DLZ_TRY(eo_hop32(op, M, R, 1, false, N));
+            k_cg_eo_k1b<<<blocks, kT, 0, op.stream>>>(R, M, P, T, links, op.gf, kappa2, N, ms, partials);
+            op.prof.stencil_stop(op.stream);
+            k_cg_alpha<<<N, 256, 0, op.stream>>>(partials, nbq, ms);
+            op.prof.stencil_start(op.stream, true, g.V, N, 264, 2, 192);
+            DLZ_TRY(eo_hop32(op, M, T, 1, true, N));
+            k_cg_eo_k23b<<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, kappa2, N, ms, partials);
+            op.prof.stencil_stop(op.stream);
+            k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 0, ms);
+            op.prof.launches += 4;
+            DLZ_CUDA_TRY(cudaGetLastError());
+            return DLZ_OK;
+        }
+        // K1 moves 120 reals per site and RHS (r gathered, t and p read and written) + links
+        op.prof.stencil_start(op.stream, true, g.V, N, 120, 1);
+        k_cg_k1<<<blocks, kT, 0, op.stream>>>(R, P, T, links, g, kappa, N, ms, partials);
         op.prof.stencil_stop(op.stream);
         k_cg_alpha<<<N, 256, 0, op.stream>>>(partials, nbq, ms);
-        // K23 moves 168 reals per site and RHS (s, t, p_new, e read; s_new, e, r written)
-        op.prof.stencil_start(op.stream, true, g.V, N, 168);
-        k_cg_k23<<<blocks, kT, 0, op.stream>>>(sc, T, sn, pnew, e, R, links, g, kappa, N, ms, partials);
+        // K23 moves 192 reals per site and RHS (t gathered; r, s, e read and written; p read)
+        op.prof.stencil_start(op.stream, true, g.V, N, 192, 2);
+        k_cg_k23<<<blocks, kT, 0, op.stream>>>(T, R, S, P, e, links, g, kappa, N, ms, partials);
         op.prof.stencil_stop(op.stream);
         k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 0, ms);
         op.prof.launches += 4;
@@ -261,11 +359,7 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
     };
     GraphExec ge;
     auto six = [&]() -> int {
-        // state entering the group: p in P[0], s in S[1]
-        for (int sub = 0; sub < 6; ++sub) {
-            const int a = sub & 1;
-            DLZ_TRY(iteration(P[a], P[1 - a], S[1 - a], S[a]));
-        }
+        for (int sub = 0; sub < 6; ++sub) DLZ_TRY(iteration());
         return DLZ_OK;
     };
     std::vector<CgFusedState> hsv(N);

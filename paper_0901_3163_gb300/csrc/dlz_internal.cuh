@@ -132,6 +132,14 @@ struct Profiler {
     long long launches = 0;         // all kernels
     long long stencils = 0;         // timed stencil launches (direct)
     double stencil_bytes = 0.0;     // their algorithmic bytes
+    // the same per kernel kind (tag): 0 plain stencil, 1 first fused stencil kernel of
+    // an inner solver (k_cg_k1, k_minres_k1, k_lanczos_k1), 2 second one (k_cg_k23)
+    static constexpr int kTags = 3;
+    double tag_ms[kTags] = {0, 0, 0}, tag_bytes[kTags] = {0, 0, 0};
+    long long tag_n[kTags] = {0, 0, 0};
+    std::vector<int> pair_tag;      // tag of each direct event pair
+    std::vector<double> pair_bytes; // bytes of each direct event pair
+    int cur_tag = 0;
     // stencils inside captured graphs: timed by external event nodes of the graph,
     // read after a host synchronisation (one replay sampled per read)
     GraphExec *capture = nullptr;
@@ -140,14 +148,50 @@ struct Profiler {
     void begin(bool on, bool f32);
     // reals_per_rhs: spinor reals moved per site and right-hand side (48 for a plain
     // stencil: read 24, write 24; more for a stencil with a fused epilogue)
-    void stencil_start(cudaStream_t s, bool f32, long long sites, int nrhs, int reals_per_rhs = 48);
+    // link_reals: link reals read per site (< 0: 48 in FP32, two rows of 4 links; 72 in FP64)
+    void stencil_start(cudaStream_t s, bool f32, long long sites, int nrhs, int reals_per_rhs = 48,
+                       int tag = 0, int link_reals = -1);
     void stencil_stop(cudaStream_t s);
     double stencil_ms();            // synchronises the events; sums pairs
     ~Profiler();
 };
 
+// Grow-only device buffer (never shrinks; no allocation while large enough).
+struct GrowBuf {
+    DevBuf b;
+    int reserve(size_t nbytes) {
+        if (b.bytes >= nbytes) return 0;
+        b.release();
+        return b.alloc(nbytes);
+    }
+    void *ptr() const { return b.p; }
+    template <typename T> T *as() const { return reinterpret_cast<T *>(b.p); }
+};
+// scratch of the tensor-core basis products (tc_gemm.cu)
+struct TcScratch {
+    GrowBuf coef, part, err;
+};
+// Tensor-core (tcgen05, 3xTF32) products of FP32 basis vectors on stream st:
+//   tc_combine32: out[j] (len floats, stride ldo) = sum_i c_ij in[i] (stride ldv), i < nin,
+//     j < nout <= 256; coef on the host, real [nin][nout] or complex interleaved
+//     [nin][nout][2] (cplx: the vectors are complex, c_ij multiplies each complex entry);
+//   tc_dots32: C_host[q][i] = <in_i, r_q> (complex; nin <= 128, nq <= 16, len % 32 == 0).
+// launches (may be null) counts the kernels.  Set-up outside graphs: tc_prepare().
+int tc_prepare();
+int tc_combine32(TcScratch &sc, cudaStream_t st, float *out, long ldo, const float *in, long ldv, int nin, long len,
+                 const double *coef, int nout, bool cplx, long long *launches);
+int tc_dots32(TcScratch &sc, cudaStream_t st, double2 *C_host, const float *V, long ldv, int nin, const float *R,
+              long ldr, int nq, long len, long long *launches);
+
+// even-odd operators: right-hand sides per launch of the batched even-odd stencil
+constexpr int kEoBatch = 16;
+
 struct Op {
-    Geom g;
+    Geom g;           // geometry of the operator's vectors (even-odd: g.V = V / 2 even sites)
+    bool eo = false;  // even-odd (Schur complement) operator on the even sites
+    Geom gf;          // full-lattice geometry (the stencil kernels of an even-odd operator)
+    DevBuf eo_tmp64;  // odd-site work fields of the even-odd stencil, kEoBatch FP64 ...
+    DevBuf eo_tmp32;  // ... and FP32 (allocated with the operator: no allocation inside graphs)
     double kappa;
     cudaStream_t stream;
     cudaStream_t cap_stream = nullptr;   // private stream used only to capture CUDA graphs
@@ -158,16 +202,11 @@ struct Op {
     RedScratch red;
     Profiler prof;
     DevBuf md_scratch;   // block partials of the FP32 multi-dot (grown on demand, outside graphs)
-    void *blas = nullptr;   // cuBLAS handle for the restart GEMM (created on first use, outside graphs)
+    int multi_choice = 0;   // launch form the multi-lattice autotuner chose last (100 form + 10 chunks + half)
+    TcScratch tc;           // scratch of the tensor-core basis products
 };
 
-// V_new = V P for the Rayleigh-Ritz restart of an FP32 basis as one cuBLAS SGEMM
-// (a plain dense product: (reals per vector) x (m+1) times (m+1) x (k+1), real
-// coefficients P row-major on the host; FP32 arithmetic, no TF32).
-// dev_scratch: >= nin * nout doubles on the device, alive until the GEMM has run.
-int restart_gemm32(Op &op, float4 *out, const float4 *in, long n, int nin, int nout, const double *P_host,
-                   void *dev_scratch);
-void blas_destroy(Op &op);
+
 
 // A CUDA event destroyed on every return path.
 struct Event {
@@ -191,6 +230,7 @@ struct GraphExec {
     long long launches = 0;
     std::vector<cudaEvent_t> ev;      // start/stop pairs of the timed stencils
     std::vector<double> bytes;        // algorithmic bytes of each timed stencil
+    std::vector<int> tags;            // kernel kind of each timed stencil (Profiler tags)
     bool fresh = false;               // replayed since the last sample
     GraphExec() = default;
     GraphExec(const GraphExec &) = delete;
@@ -209,6 +249,10 @@ struct GraphExec {
                 pr.sampled_ms += ms;
                 pr.sampled_bytes += bytes[i / 2];
                 pr.sampled++;
+                const int t = tags[i / 2];
+                pr.tag_ms[t] += ms;
+                pr.tag_bytes[t] += bytes[i / 2];
+                pr.tag_n[t]++;
             } else {
                 cudaGetLastError();   // a sample that cannot be read must not poison later checks
             }
@@ -254,6 +298,19 @@ int wilson64(Op &op, double2 *out, const double2 *in, int which);
 int wilson32(Op &op, float4 *out, const float4 *in, int which);
 // nrhs spinors stored one after another (FP32: 6V float4 each, FP64: 12V double2 each)
 int wilson32_batch(Op &op, float4 *out, const float4 *in, int which, int nrhs);
+// Even-odd operators (op.eo): out = A in on even-site fields for A = Dhat (DLZ_D),
+// Dhat^dag (DLZ_DDAG), Qhat = gamma5 Dhat (DLZ_Q), nrhs fields one after another.
+int eo_apply64(Op &op, double2 *out, const double2 *in, int which, int nrhs);
+int eo_apply32(Op &op, float4 *out, const float4 *in, int which, int nrhs);
+// out (parity par, nrhs fields) = H [gamma5]^g5in in (parity 1 - par), FP64
+int eo_hop64(Op &op, double2 *out, const double2 *in, int par, bool g5in, int nrhs);
+// FP32 hop for the fused even-odd CGNR (parity 1 - par input, parity par output)
+int eo_hop32(Op &op, float4 *out, const float4 *in, int par, bool g5in, int nrhs);
+// Full-lattice user vector (complex128 [V][12]) b -> be = b_e + kappa H_eo b_o (even
+// internal planes) and bo = b_o (odd planes); and x_e (even planes) + b -> the full
+// solution x = (x_e, b_o + kappa H_oe x_e) in the user layout (bo_work: odd planes).
+int eo_prepare64(Op &op, double2 *be, double2 *bo, const double2 *b_user);
+int eo_reconstruct64(Op &op, double2 *x_user, const double2 *xe, double2 *bo_work, const double2 *b_user);
 int wilson64_batch(Op &op, double2 *out, const double2 *in, int which, int nrhs);
 // A = D, D^dag, Q or D^dag D on internal FP64 vectors (tmp used for D^dag D).
 int apply64(Op &op, double2 *out, const double2 *in, int which, double2 *tmp);

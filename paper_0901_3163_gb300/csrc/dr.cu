@@ -196,7 +196,7 @@ int lanczos_fused_step(Op &op, bool ddagd, const float4 *u, const float *s_ib_pr
         DLZ_TRY(wilson32(op, tmp, u, DLZ_Q));      // first factor of Q Q
         in = tmp;
     }
-    op.prof.stencil_start(op.stream, true, g.V, 1, 96);
+    op.prof.stencil_start(op.stream, true, g.V, 1, 96, 1);
     unsigned *counter = reinterpret_cast<unsigned *>(partials + 2 * blocks);
     k_lanczos_k1<<<blocks, kLz, 0, op.stream>>>(in, s_ib_prev, u, vp, s_b_prev, vj, w_out, op.gauge32.as<float4>(),
                                                 g, (float)op.kappa, partials, counter, d_a, s_a);
@@ -309,7 +309,8 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         for (int j = j0; j < m; ++j) {
             const bool reorth_j = (j0 > 0) && rperiod > 0 && ((j - j0) % rperiod == 0);
             if constexpr (P::kF32) {
-                if (j > j0 && !reorth_j) {
+                // (an even-odd operator has no fused step: its stencil is two launches)
+                if (j > j0 && !reorth_j && !op.eo) {
                     DLZ_TRY(lanczos_fused_step(op, !harmonic, ucur, s_invbeta + (j - 1), V + (size_t)(j - 1) * n,
                                                s_beta + (j - 1), V + (size_t)j * n, uoth, tmp.as<E>(),
                                                fpart.as<double>(), d_alpha + j, s_alpha + j, d_beta + j,
@@ -413,12 +414,12 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         // FP32 basis: Ritz residuals below ~1e-5 ||A|| are under its rounding level
         const double tol_eig = p.tol_eig > 0 ? p.tol_eig : (P::kF32 ? 1e-5 : 1e-10) * Anorm;
         // ---------------- restart: V_{k+1} <- V_{m+1} P
-        // FP32: one cuBLAS SGEMM (HBM-bound; on 16^3x32 the restart-and-residual time of
-        // 150 cycles fell from 0.45 s with three 16-output combine passes to 0.24 s);
-        // FP64: the combine kernel (FP64-ALU-bound either way; the plain-form step took
-        // 39.1 s with DGEMM against 36.8 s with it)
+        // FP32: the tensor-core product (tc_gemm.cu: tcgen05, 3xTF32, FP32 accuracy);
+        // FP64: the combine kernel (FP64-ALU-bound; the plain-form step took 39.1 s with
+        // cuBLAS DGEMM against 36.8 s with it)
         if constexpr (P::kF32) {
-            DLZ_TRY(restart_gemm32(op, Vn, V, n, m + 1, k + 1, pl.P.data(), gcoef.p));
+            DLZ_TRY(tc_combine32(op.tc, op.stream, reinterpret_cast<float *>(Vn), 4 * n, reinterpret_cast<const float *>(V),
+                                 4 * n, m + 1, 4 * n, pl.P.data(), k + 1, false, &op.prof.launches));
         } else {
             DLZ_TRY(h2d(op, gcoef.p, pl.P.data(), pl.P.size() * sizeof(double)));
             DLZ_TRY(combine<P>(op, Vn, n, k + 1, V, n, m + 1, gcoef.p, k + 1, true, false));
@@ -468,14 +469,15 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         T.swap(pl.Tn);
         c.swap(pl.cn);
         j0 = k;
-        if (lin_ok && (eig_ok || over)) {
+        // eigensolver use: the kept pairs alone decide
+        if (p.eig_only ? eig_ok : (lin_ok && (eig_ok || over))) {
             converged = true;
             ++cycle;
             break;
         }
     }
     st.cycles = cycle;
-    st.converged = (converged && st.true_residual <= p.tol) ? 1 : 0;
+    st.converged = p.eig_only ? (converged ? 1 : 0) : ((converged && st.true_residual <= p.tol) ? 1 : 0);
     DLZ_TRY(v64::copy(op, x_out, x.as<double2>()));
     const auto td0 = now();
     if (defl_out) {
@@ -488,10 +490,17 @@ int dr_solve_t(Op &op, bool harmonic, const double2 *b_in, double2 *x_out, const
         } else {
             vk64 = reinterpret_cast<double2 *>(V);
         }
+        // FP64 basis: H = V_k^dag A V_k is the k x k block of the restarted T (the
+        // Lanczos relation holds to FP64 rounding).  FP32 basis: T carries the FP32
+        // rounding of the stencil and the vector updates (~1e-7 ||A||), as large as the
+        // smallest eigenvalues of D^dag D near the critical kappa (~1e-6 at
+        // sigma_min = 1e-3), so H is formed explicitly in FP64 from the FP64 copy of the
+        // kept vectors: the Galerkin projection of D-CG / D-MinRes is then exact for the
+        // kept subspace (k FP64 products with A)
         std::vector<double> Hk((size_t)k * k);
         for (int i = 0; i < k; ++i)
             for (int j = 0; j < k; ++j) Hk[(size_t)i * k + j] = T[(size_t)i * m + j];
-        DLZ_TRY(build_deflation(op, which, vk64, k, defl_out, Hk.data()));
+        DLZ_TRY(build_deflation(op, which, vk64, k, defl_out, P::kF32 ? nullptr : Hk.data()));
     }
     DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
     if (trace)
@@ -511,6 +520,11 @@ int prepare_kernels(Op &op) {
 
 int dr_solve(Op &op, bool harmonic, const double2 *b, double2 *x, const dlz_params &p,
              dlz_defl_s **defl_out, dlz_stats &st) {
+    if (p.eig_only) {
+        // eigensolver use: the restart cycles only, no finishing solve
+        if (p.precision == DLZ_F64) return dr_solve_t<P64>(op, harmonic, b, x, p, defl_out, st);
+        return dr_solve_t<P32>(op, harmonic, b, x, p, defl_out, st);
+    }
     if (p.precision == DLZ_F64) {
         if (!p.finish) return dr_solve_t<P64>(op, harmonic, b, x, p, defl_out, st);
         // restart cycles, then (if they ended short of tol) D-MinRes / D-CG from x

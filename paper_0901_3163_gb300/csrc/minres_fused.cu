@@ -168,7 +168,7 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
     auto iteration = [&](float4 *U, float4 *Up, float4 *W, float4 *D2, float4 *D3) -> int {
         // K1 moves 192 reals per site and right-hand side: u_j, u_{j-1}, d_{j-2}, d_{j-3}, e
         // read; w, d_{j-1}, e written (24 each), plus the links once per site
-        op.prof.stencil_start(op.stream, true, g.V, N, 192);
+        op.prof.stencil_start(op.stream, true, g.V, N, 192, 1);
         // one right-hand side: the sums are taken by the kernels' last blocks (latency);
         // several: by one-block-per-RHS kernels (cheaper than a tail in every block)
         unsigned *cn = N == 1 ? counters : nullptr;

@@ -185,6 +185,141 @@ k_mm_last(const float4 *__restrict__ Uj, const float4 *__restrict__ D2, const fl
     }
 }
 
+// ------------------------------------------------------------------ persistent form
+// One cooperative launch runs every stage of every iteration for all slots, the stages
+// separated by grid-wide barriers (all blocks are co-resident: the launch is
+// cooperative and sized by the occupancy calculator).  Each barrier wait is bounded:
+// a block that has waited `limit` polls sets the error word and returns, and so does
+// every block that later finds the word set, so a lost block can never hang the
+// kernel; the host turns the word into DLZ_ERR_DEVICE_TIMEOUT.
+struct GridBar {
+    unsigned count;      // blocks arrived at the current barrier
+    unsigned gen;        // barrier generation
+    int err;             // 1: a wait gave up
+    int groups;          // 6-iteration groups completed (written by block 0)
+};
+
+__device__ inline bool grid_wait(GridBar *gb, long long limit) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *genp = &gb->gen;
+        const unsigned g = *genp;
+        __threadfence();
+        if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            long long n = 0;
+            while (*genp == g) {
+                if (++n > limit) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (!ok) atomicExch(&gb->err, 1);
+        if (*(volatile int *)&gb->err) ok = 0;
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Up to `ngroups` groups of 6 fused MinRes iterations over all slots; at every
+// iteration count that is a multiple of `check` (a multiple of 6), slots whose inner
+// residual met their tolerance are frozen (as the host does between graph replays, so
+// both forms give the same bits), and the kernel ends once every slot is frozen.
+template <int B>
+__global__ void __launch_bounds__(B * kMT)
+k_mm_persistent(float4 *__restrict__ U0, float4 *__restrict__ Up0, float4 *__restrict__ W0, float4 *__restrict__ D20,
+                float4 *__restrict__ D30, float4 *__restrict__ E, const SlotDesc *__restrict__ sd,
+                const int2 *__restrict__ table, int ntab, int NS, FusedState *__restrict__ st, int *__restrict__ active,
+                double *__restrict__ partials, double *__restrict__ partials2, const double *__restrict__ tol,
+                int it0, int check, int ngroups, GridBar *gb, long long limit) {
+    float4 *U = U0, *Up = Up0, *W = W0, *D2 = D20, *D3 = D30;
+    for (int grp = 0; grp < ngroups; ++grp) {
+        for (int sub = 0; sub < 6; ++sub) {
+            for (int item = blockIdx.x; item < ntab; item += gridDim.x) {
+                const int2 t = table[item];
+                const SlotDesc d = sd[t.x];
+                if (!active[t.x]) {
+                    if (threadIdx.x % kMT == 0 && t.y + (int)(threadIdx.x / kMT) < d.nb)
+                        partials[d.blk0 + t.y + threadIdx.x / kMT] = 0.0;
+                    continue;
+                }
+                const int s = t.y * kMT + threadIdx.x;
+                float facc = 0.f;
+                if (s < d.g.V)
+                    facc = minres_k1_site(s, d.g, d.kappa, U + d.off, Up + d.off, W + d.off, D2 + d.off, D3 + d.off,
+                                          E + d.off, d.links, st[t.x]);
+                chunk_partials<B>(facc, partials + d.blk0 + t.y, d.nb - t.y);
+            }
+            if (!grid_wait(gb, limit)) return;
+            for (int q = blockIdx.x; q < NS; q += gridDim.x) {
+                if (!active[q]) continue;
+                const SlotDesc d = sd[q];
+                const double a = slot_sum(partials, d.blk0, d.nb);
+                if (threadIdx.x == 0) fused_alpha(st[q], a);
+                __syncthreads();
+            }
+            if (!grid_wait(gb, limit)) return;
+            for (int item = blockIdx.x; item < ntab; item += gridDim.x) {
+                const int2 t = table[item];
+                const SlotDesc d = sd[t.x];
+                if (!active[t.x]) {
+                    if (threadIdx.x % kMT == 0 && t.y + (int)(threadIdx.x / kMT) < d.nb)
+                        partials2[d.blk0 + t.y + threadIdx.x / kMT] = 0.0;
+                    continue;
+                }
+                const int s = t.y * kMT + threadIdx.x;
+                float facc = 0.f;
+                if (s < d.g.V) facc = minres_k2a_site(s, d.g.V, W + d.off, U + d.off, st[t.x]);
+                chunk_partials<B>(facc, partials2 + d.blk0 + t.y, d.nb - t.y);
+            }
+            if (!grid_wait(gb, limit)) return;
+            for (int q = blockIdx.x; q < NS; q += gridDim.x) {
+                if (!active[q]) continue;
+                const SlotDesc d = sd[q];
+                const double r2 = slot_sum(partials2, d.blk0, d.nb);
+                if (threadIdx.x == 0) {
+                    FusedState v = st[q];
+                    fused_givens(v, r2);
+                    st[q] = v;
+                }
+                __syncthreads();
+            }
+            if (!grid_wait(gb, limit)) return;
+            float4 *tUp = Up;
+            Up = U; U = W; W = tUp;
+            float4 *tD = D2; D2 = D3; D3 = tD;
+        }
+        const int it = it0 + 6 * (grp + 1);
+        if (blockIdx.x == 0 && threadIdx.x == 0) gb->groups = grp + 1;
+        if (it % check != 0) continue;
+        // freeze converged slots (the owner block of each slot decides), then all blocks
+        // read the same flags after the barrier
+        for (int q = blockIdx.x; q < NS; q += gridDim.x)
+            if (threadIdx.x == 0 && active[q]) {
+                const FusedState v = st[q];
+                if (fabs(v.phibar) <= tol[q] * v.r0 || v.beta_next == 0.0) active[q] = 0;
+            }
+        if (!grid_wait(gb, limit)) return;
+        __shared__ int any;
+        if (threadIdx.x == 0) {
+            int a = 0;
+            for (int q = 0; q < NS && !a; ++q) a = ((volatile int *)active)[q];
+            any = a;
+        }
+        __syncthreads();
+        if (!any) return;
+    }
+}
+
 }  // namespace
 
 // One block-table layout: blocks of B chunks (B * 128 sites) of one slot.
@@ -204,9 +339,43 @@ struct Tile {
 // 512 threads per block), the next three time one replay each (CUDA events), and the
 // fastest serves the rest (DLZ_MULTI_TILE=1|2|4 forces one).  The partials are per
 // 128-site chunk whatever the tile, so every tile gives bit-identical results.
+// persistent launch of up to `ngroups` 6-iteration groups with B chunks per work item and
+// `grid` blocks; returns the groups run (device count) or a DLZ error
+static int launch_persistent(Op &op, int B, int grid, float4 *U0, float4 *Up0, float4 *W0, float4 *D20, float4 *D30,
+                             float4 *e, const SlotDesc *sd, const Tile &t, int NS, FusedState *ms, int *active,
+                             double *partials, double *partials2, const double *d_tol, int it0, int check, int ngroups,
+                             GridBar *gb, long long limit, int &groups_run) {
+    DLZ_CUDA_TRY(cudaMemsetAsync(gb, 0, sizeof(GridBar), op.stream));
+    int ntab = t.nblocks;
+    const int2 *table = t.table;
+    void *args[] = {&U0, &Up0, &W0, &D20, &D30, &e, (void *)&sd, (void *)&table, &ntab, &NS, &ms, &active,
+                    &partials, &partials2, (void *)&d_tol, &it0, &check, &ngroups, &gb, &limit};
+    void *fn = B == 1 ? (void *)k_mm_persistent<1> : B == 2 ? (void *)k_mm_persistent<2> : (void *)k_mm_persistent<4>;
+    DLZ_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(B * kMT), args, 0, op.stream));
+    op.prof.launches += 1;
+    GridBar h;
+    DLZ_TRY(d2h_sync(op, &h, gb, sizeof(GridBar)));
+    if (h.err) return fail(DLZ_ERR_DEVICE_TIMEOUT, "a grid barrier of the persistent multi-lattice kernel gave up");
+    groups_run = h.groups;
+    return DLZ_OK;
+}
+
+// blocks of the persistent kernel: `frac` of the co-resident maximum on every SM
+static int persistent_grid(int B, int frac_half) {
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    const void *fn = B == 1 ? (const void *)k_mm_persistent<1> : B == 2 ? (const void *)k_mm_persistent<2>
+                                                                       : (const void *)k_mm_persistent<4>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, B * kMT, 0) != cudaSuccess) return 0;
+    if (frac_half) per = std::max(1, per / 2);
+    return per * nsm;
+}
+
 int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const Tile *tiles, int nchunks, size_t arena,
                        const float4 *r, float4 *e, float4 *const bufs[5], FusedState *ms, double *partials,
-                       int *active, const double *d_tol, const dlz_params &p, int &iters, bool e_init) {
+                       int *active, const double *d_tol, const dlz_params &p, int &iters, bool e_init,
+                       GridBar *gb) {
     double *partials2 = partials + nchunks;
     k_mm_norm<1><<<tiles[0].nblocks, kMT, 0, op.stream>>>(r, sd, tiles[0].table, partials);
     k_mm_init<<<NS, 256, 0, op.stream>>>(partials, sd, ms);
@@ -245,56 +414,111 @@ int minres_multi_batch(Op &op, int NS, const SlotDesc *sd, const Tile *tiles, in
         }
         return DLZ_OK;
     };
-    int forced = -1;
+    // Autotuner over the launch forms: the graph form with 1, 2 or 4 chunks of 128 sites
+    // per block (candidates 0-2; the first three groups capture their graphs, the next
+    // three time one replay each), and the persistent form with 1, 2 or 4 chunks per
+    // work item at the full or half co-resident grid (candidates 3-8, one timed group
+    // each).  The fastest candidate runs the rest.  Chunk partials and slot freezing do
+    // not depend on the candidate, so every choice gives the same bits.
+    // DLZ_MULTI_TILE=1|2|4 fixes the chunks per block; DLZ_MULTI_FORM=graph|persistent
+    // fixes the form (both: no search).
+    int tile_forced = -1, form_forced = -1;
     if (const char *env = std::getenv("DLZ_MULTI_TILE")) {
         const int b = std::atoi(env);
-        forced = b == 1 ? 0 : b == 2 ? 1 : b == 4 ? 2 : -1;
+        tile_forced = b == 1 ? 0 : b == 2 ? 1 : b == 4 ? 2 : -1;
     }
-    float tms[3] = {0.f, 0.f, 0.f};
-    Event ev0, ev1;
-    if (forced < 0) {
-        DLZ_CUDA_TRY(ev0.create());
-        DLZ_CUDA_TRY(ev1.create());
+    if (const char *env = std::getenv("DLZ_MULTI_FORM")) {
+        if (std::strcmp(env, "graph") == 0) form_forced = 0;
+        else if (std::strcmp(env, "persistent") == 0) form_forced = 1;
     }
+    long long limit = 1LL << 24;           // polls of a barrier wait (64 ns apart): about a second
+    if (const char *env = std::getenv("DLZ_WAIT_LIMIT")) limit = std::atoll(env);
     const int check = std::max(6, (p.check_every / 6) * 6);
+    struct Cand { int form, tile, half, grid; };
+    std::vector<Cand> cands;
+    for (int v = 0; v < 3; ++v)
+        if ((tile_forced < 0 || tile_forced == v) && form_forced != 1) cands.push_back({0, v, 0, 0});
+    for (int v = 0; v < 3; ++v)
+        for (int half = 0; half < 2; ++half)
+            if ((tile_forced < 0 || tile_forced == v) && form_forced != 0) {
+                const int grid = persistent_grid(1 << v, half);
+                if (grid > 0) cands.push_back({1, v, half, grid});
+            }
+    if (cands.empty()) return fail(DLZ_ERR_CUDA, "no launch form available for the multi-lattice kernel");
+    std::vector<float> tms(cands.size(), 0.f);
+    Event ev0, ev1;
+    DLZ_CUDA_TRY(ev0.create());
+    DLZ_CUDA_TRY(ev1.create());
     std::vector<FusedState> h(NS);
     std::vector<double> tol(NS);
     DLZ_TRY(d2h_sync(op, tol.data(), d_tol, NS * sizeof(double)));
     std::vector<int> act(NS, 1);
     DLZ_TRY(h2d(op, active, act.data(), NS * sizeof(int)));
-    int it = 0, group = 0, best = forced >= 0 ? forced : 0;
-    while (iters < p.max_iter) {
-        const bool timed = forced < 0 && group >= 3 && group < 6;
-        cur = forced >= 0 ? forced : (group < 6 ? group % 3 : best);
-        if (timed) DLZ_CUDA_TRY(cudaEventRecord(ev0.e, op.stream));
-        DLZ_TRY(run_graph(op, ge[cur], six));
+    // the schedule: capture (graph candidates), then one timed group per candidate, then the best
+    std::vector<int> sched;
+    for (size_t c = 0; c < cands.size(); ++c)
+        if (cands[c].form == 0 && cands.size() > 1) sched.push_back((int)c);      // capture groups (untimed)
+    const size_t ncapture = sched.size();
+    if (cands.size() > 1)
+        for (size_t c = 0; c < cands.size(); ++c) sched.push_back((int)c);        // timed groups
+    int it = 0, group = 0, best = 0;
+    bool all_done = false;
+    auto host_check = [&]() -> int {
+        DLZ_TRY(d2h_sync(op, h.data(), ms, NS * sizeof(FusedState)));
+        bool done = true, changed = false;
+        for (int q = 0; q < NS; ++q) {
+            if (!std::isfinite(h[q].phibar)) return fail(DLZ_ERR_NONFINITE, "MinRes residual not finite");
+            const bool ok = std::fabs(h[q].phibar) <= tol[q] * h[q].r0 || h[q].beta_next == 0.0;
+            if (!ok) done = false;
+            else if (act[q]) { act[q] = 0; changed = true; }
+        }
+        all_done = done;
+        if (!done && changed) DLZ_TRY(h2d(op, active, act.data(), NS * sizeof(int)));
+        return DLZ_OK;
+    };
+    while (iters < p.max_iter && !all_done) {
+        const bool tuning = (size_t)group < sched.size();
+        const int ci = tuning ? sched[group] : best;
+        const Cand &c = cands[ci];
+        const bool timed = tuning && (size_t)group >= ncapture;
+        if (c.form == 0) {
+            cur = c.tile;
+            if (timed) DLZ_CUDA_TRY(cudaEventRecord(ev0.e, op.stream));
+            DLZ_TRY(run_graph(op, ge[cur], six));
+            if (timed) DLZ_CUDA_TRY(cudaEventRecord(ev1.e, op.stream));
+            iters += 6;
+            it += 6;
+            if (it % check == 0 || iters >= p.max_iter) DLZ_TRY(host_check());
+        } else {
+            // one group while tuning, else every remaining group in one launch
+            const int ngroups = tuning ? 1 : std::max(1, (p.max_iter - iters + 5) / 6);
+            int ran = 0;
+            if (timed) DLZ_CUDA_TRY(cudaEventRecord(ev0.e, op.stream));
+            DLZ_TRY(launch_persistent(op, 1 << c.tile, c.grid, U0, Up0, W0, D20, D30, e, sd, tiles[c.tile], NS, ms,
+                                      active, partials, partials2, d_tol, it, check, ngroups, gb, limit, ran));
+            if (timed) DLZ_CUDA_TRY(cudaEventRecord(ev1.e, op.stream));
+            iters += 6 * ran;
+            it += 6 * ran;
+            // the kernel froze slots itself: bring the flags back, and see whether all are done
+            DLZ_TRY(d2h_sync(op, act.data(), active, NS * sizeof(int)));
+            bool any = false;
+            for (int q = 0; q < NS; ++q) any = any || act[q];
+            all_done = !any;
+            if (!all_done && (it % check == 0 || iters >= p.max_iter)) DLZ_TRY(host_check());
+        }
         if (timed) {
-            DLZ_CUDA_TRY(cudaEventRecord(ev1.e, op.stream));
             DLZ_CUDA_TRY(cudaEventSynchronize(ev1.e));
-            if (cudaEventElapsedTime(&tms[cur], ev0.e, ev1.e) != cudaSuccess) {
+            if (cudaEventElapsedTime(&tms[ci], ev0.e, ev1.e) != cudaSuccess) {
                 cudaGetLastError();
-                tms[cur] = 1e30f;
+                tms[ci] = 1e30f;
             }
-            if (group == 5)
-                for (int v = 1; v < 3; ++v)
-                    if (tms[v] < tms[best]) best = v;
+            if ((size_t)group + 1 == sched.size())
+                for (size_t v = 0; v < cands.size(); ++v)
+                    if (tms[v] < tms[best]) best = (int)v;
         }
         ++group;
-        iters += 6;
-        it += 6;
-        if (it % check == 0 || iters >= p.max_iter) {
-            DLZ_TRY(d2h_sync(op, h.data(), ms, NS * sizeof(FusedState)));
-            bool done = true, changed = false;
-            for (int q = 0; q < NS; ++q) {
-                if (!std::isfinite(h[q].phibar)) return fail(DLZ_ERR_NONFINITE, "MinRes residual not finite");
-                const bool ok = std::fabs(h[q].phibar) <= tol[q] * h[q].r0 || h[q].beta_next == 0.0;
-                if (!ok) done = false;
-                else if (act[q]) { act[q] = 0; changed = true; }
-            }
-            if (done) break;
-            if (changed) DLZ_TRY(h2d(op, active, act.data(), NS * sizeof(int)));
-        }
     }
+    op.multi_choice = cands[best].form * 100 + (1 << cands[best].tile) * 10 + cands[best].half;
     k_mm_last<1><<<tiles[0].nblocks, kMT, 0, op.stream>>>(Up0, D20, D30, e, sd, tiles[0].table, ms);
     op.prof.launches += 1;
     DLZ_CUDA_TRY(cudaGetLastError());
@@ -335,7 +559,8 @@ int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, cons
     const int NS = (int)hsd.size();
     if (NS == 0) return DLZ_OK;
     Op &op = *ops[0];
-    DevBuf dsd, dtab[3], f32, part, scal;
+    DevBuf dsd, dtab[3], f32, part, scal, gbar;
+    DLZ_TRY(gbar.alloc(sizeof(GridBar)));
     DLZ_TRY(dsd.alloc(NS * sizeof(SlotDesc)));
     Tile tiles[3];
     for (int v = 0; v < 3; ++v) {
@@ -488,7 +713,7 @@ int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, cons
         }
         DLZ_TRY(h2d(op, d_tol, tl.data(), NS * sizeof(double)));
         DLZ_TRY(minres_multi_batch(op, NS, dsd.as<SlotDesc>(), tiles, nchunks, arena, r32, e32, bufs, ms,
-                                   part.as<double>(), d_active, d_tol, p, iters, true));
+                                   part.as<double>(), d_active, d_tol, p, iters, true, gbar.as<GridBar>()));
         DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
         // x += ||r|| e, lattice by lattice
         for (int l = 0; l < nlat; ++l) {

@@ -392,6 +392,7 @@ extern "C" {
 
 int dlz_net_create(dlz_op_t h, int nlayers, const int *widths, const void *weights, dlz_net_t *out) {
     if (!h || !widths || !weights || !out) return fail(DLZ_ERR_BADARG, "null argument");
+    if (h->op.eo) return fail(DLZ_ERR_BADARG, "the network runs on full-lattice operators");
     if (nlayers < 1 || nlayers > kMaxLayersNet) return fail(DLZ_ERR_BADARG, "nlayers must be in [1, 8]");
     if (widths[0] != 1 || widths[nlayers] != 1) return fail(DLZ_ERR_BADARG, "first and last width must be 1");
     for (int l = 0; l <= nlayers; ++l)
@@ -574,8 +575,9 @@ int dlz_net_weight_count(dlz_net_t net, long long *count) {
     return DLZ_OK;
 }
 
-int dlz_subspace_loss(dlz_defl_t d, const void *f, int nvec, double *loss, void *grad) {
+int dlz_subspace_loss(dlz_defl_t d, const void *f, int nvec, double grad_scale, double *loss, void *grad) {
     if (!d || !f || !loss || nvec < 1) return fail(DLZ_ERR_BADARG, "subspace_loss arguments");
+    if (!std::isfinite(grad_scale)) return fail(DLZ_ERR_BADARG, "grad_scale is not finite");
     if (!device_ptr(f) || (grad && !device_ptr(grad))) return fail(DLZ_ERR_BADARG, "subspace_loss takes device pointers");
     Op &op = *d->op;
     op.prof.begin(false, false);
@@ -605,8 +607,8 @@ int dlz_subspace_loss(dlz_defl_t d, const void *f, int nvec, double *loss, void 
         const double L = h[1] / h[0];
         loss[v] = L;
         if (grad) {
-            // G(f) = 2 (perp - L f) / ||f||^2
-            const double a = 2.0 / h[0], b = -2.0 * L / h[0];
+            // G(f) = grad_scale * 2 (perp - L f) / ||f||^2
+            const double a = grad_scale * 2.0 / h[0], b = -grad_scale * 2.0 * L / h[0];
             double2 *pp = perp.as<double2>();
             const double2 *ff = f64.as<double2>();
             DLZ_TRY(map(op, n, [=] __device__(long i) {

@@ -29,7 +29,6 @@ struct dlz_op_s {
     dlz::Op op;
     ~dlz_op_s() {
         if (op.cap_stream) cudaStreamDestroy(op.cap_stream);
-        dlz::blas_destroy(op);
     }
 };
 

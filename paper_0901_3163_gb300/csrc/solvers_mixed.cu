@@ -58,6 +58,8 @@ constexpr int kMaxBatch = 16;
 int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *B, double2 *X, int N,
                        const dlz_params &p, dlz_stats *st, const double2 *X_init) {
     if (N < 1 || N > kMaxBatch) return fail(DLZ_ERR_BADARG, "batch size");
+    if (minres && op.eo)
+        return fail(DLZ_ERR_BADARG, "even-odd operators: FP32 D-MinRes is not built (use DLZ_F64, or D-CG)");
     const long n64 = 12L * op.g.V;
     const long n32 = 6L * op.g.V;
     DevBuf bp, x, r, tmp, corr, dots, scal, f32;
@@ -183,20 +185,42 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
                 DLZ_TRY(wilson32_batch(op, w32[2], w32[0], DLZ_DDAG, N));
                 rhs32 = w32[2];
             }
-            for (int q = 0; q < N; ++q)
-                DLZ_TRY(multidot<P32>(op, V32, n32, k, rhs32 + (size_t)q * n32, pdots + (size_t)q * k, 1.0));
+            // C = V_k^dag R for all N right-hand sides at once and E0 = V_k H^-1 C, both on
+            // the tensor cores (tc_gemm.cu) when the shapes tile (k <= 128, 24 V % 32 == 0);
+            // otherwise one CUDA-core multi-dot and combine per right-hand side
+            const long len = 4L * n32;
+            const bool tc = k <= 128 && len % 32 == 0;
             std::vector<double2> hc((size_t)N * k);
-            DLZ_TRY(d2h_sync(op, hc.data(), pdots, hc.size() * sizeof(double2)));
+            if (tc) {
+                DLZ_TRY(tc_dots32(op.tc, op.stream, hc.data(), reinterpret_cast<const float *>(V32), len, k,
+                                  reinterpret_cast<const float *>(rhs32), len, N, len, &op.prof.launches));
+            } else {
+                for (int q = 0; q < N; ++q)
+                    DLZ_TRY(multidot<P32>(op, V32, n32, k, rhs32 + (size_t)q * n32, pdots + (size_t)q * k, 1.0));
+                DLZ_TRY(d2h_sync(op, hc.data(), pdots, hc.size() * sizeof(double2)));
+            }
             std::vector<std::complex<double>> z(k);
             for (int q = 0; q < N; ++q) {
                 for (int i = 0; i < k; ++i) z[i] = std::complex<double>(hc[(size_t)q * k + i].x, hc[(size_t)q * k + i].y);
                 lu_solve(k, d->Hlu.data(), d->piv.data(), z.data());
                 for (int i = 0; i < k; ++i) hc[(size_t)q * k + i] = make_double2(z[i].real(), z[i].imag());
             }
-            DLZ_TRY(h2d(op, pdots, hc.data(), hc.size() * sizeof(double2)));
-            for (int q = 0; q < N; ++q)
-                DLZ_TRY(combine<P32>(op, w32[1] + (size_t)q * n32, n32, 1, V32, n32, k, pdots + (size_t)q * k, 1, false,
-                                     false));
+            if (tc) {
+                std::vector<double> cf((size_t)2 * k * N);          // complex [k][N]
+                for (int i = 0; i < k; ++i)
+                    for (int q = 0; q < N; ++q) {
+                        cf[2 * ((size_t)i * N + q)] = hc[(size_t)q * k + i].x;
+                        cf[2 * ((size_t)i * N + q) + 1] = hc[(size_t)q * k + i].y;
+                    }
+                DLZ_TRY(tc_combine32(op.tc, op.stream, reinterpret_cast<float *>(w32[1]), len,
+                                     reinterpret_cast<const float *>(V32), len, k, len, cf.data(), N, true,
+                                     &op.prof.launches));
+            } else {
+                DLZ_TRY(h2d(op, pdots, hc.data(), hc.size() * sizeof(double2)));
+                for (int q = 0; q < N; ++q)
+                    DLZ_TRY(combine<P32>(op, w32[1] + (size_t)q * n32, n32, 1, V32, n32, k, pdots + (size_t)q * k, 1,
+                                         false, false));
+            }
             float4 *qe = w32[2], *r32 = w32[0];
             DLZ_TRY(wilson32_batch(op, qe, w32[1], which, N));
             DLZ_TRY(map(op, n32 * N, [=] __device__(long i) {

@@ -38,6 +38,12 @@ __device__ inline void wilson_batch_body(typename Field<T>::vec *__restrict__ ou
                                          int nrhs, long nel) {
     const int r = blockIdx.x % nrhs;
     const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
+    if (sizeof(T) == 4 && threadIdx.x == 0) {
+        // the block's own sites of its right-hand side (and, once per site chunk, the links)
+        const int s0 = (blockIdx.x / nrhs) * blockDim.x, nb = min((int)blockDim.x, g.V - s0);
+        prefetch_planes_l2(in + (size_t)r * nel, 6, g.V, s0, nb);
+        if (r == 0) prefetch_planes_l2(U, 12, g.V, s0, nb);
+    }
     if (s >= g.V) return;
     cx<T> o[12];
     wilson_site<T, G5IN, G5OUT>(s, g, kappa, in + (size_t)r * nel, U, o);
@@ -157,18 +163,24 @@ inline int grid_for(long n, int threads) { return (int)((n + threads - 1) / thre
 
 }  // namespace
 
+// An even-odd operator applies its Schur complement (wilson_eo.cu) wherever a solver
+// asks for D, D^dag or Q: the solvers run unchanged on its even-site vectors.
 int wilson64(Op &op, double2 *out, const double2 *in, int which) {
+    if (op.eo) return eo_apply64(op, out, in, which, 1);
     return launch_wilson<double>(op, out, in, op.gauge64.as<double2>(), which, kStencilThreads64);
 }
 int wilson32(Op &op, float4 *out, const float4 *in, int which) {
+    if (op.eo) return eo_apply32(op, out, in, which, 1);
     return launch_wilson<float>(op, out, in, op.gauge32.as<float4>(), which, kStencilThreads32);
 }
 
 int wilson32_batch(Op &op, float4 *out, const float4 *in, int which, int nrhs) {
+    if (op.eo) return eo_apply32(op, out, in, which, nrhs);
     return launch_wilson_batch<float>(op, out, in, op.gauge32.as<float4>(), which, nrhs, 6L * op.g.V,
                                       kStencilThreads32);
 }
 int wilson64_batch(Op &op, double2 *out, const double2 *in, int which, int nrhs) {
+    if (op.eo) return eo_apply64(op, out, in, which, nrhs);
     return launch_wilson_batch<double>(op, out, in, op.gauge64.as<double2>(), which, nrhs, 12L * op.g.V,
                                        kStencilThreads64);
 }

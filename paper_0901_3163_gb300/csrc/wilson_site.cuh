@@ -27,6 +27,7 @@ namespace dlz {
 template <typename T> struct Field;
 template <> struct Field<double> {
     typedef double2 vec;
+    static constexpr int vec_per_site = 12;
     __host__ __device__ static inline void load(const double2 *__restrict__ p, int V, int s,
                                                 double2 (&v)[12]) {
 #pragma unroll
@@ -40,6 +41,7 @@ template <> struct Field<double> {
 };
 template <> struct Field<float> {
     typedef float4 vec;
+    static constexpr int vec_per_site = 6;
     __host__ __device__ static inline void load(const float4 *__restrict__ p, int V, int s,
                                                 float2 (&v)[12]) {
 #pragma unroll
@@ -165,6 +167,21 @@ __host__ __device__ inline void hop_bwd(const cx<T> (&p)[12], const cx<T> (&u)[9
         if (MU == 2) { acc[6 + i] = addI(acc[6 + i], H0); acc[9 + i] = subI(acc[9 + i], H1); }
         if (MU == 3) { acc[6 + i] = acc[6 + i] + H0;      acc[9 + i] = acc[9 + i] + H1; }
     }
+}
+
+// Bulk L2 prefetch (cp.async.bulk.prefetch.L2, a TMA operation) of a block's contiguous
+// chunk of sites [s0, s0 + n) in each of `planes` planes of stride V (16-byte elements):
+// one thread issues it at the start of a latency-bound stencil kernel, so the DRAM reads
+// of the block's own site data overlap the neighbour gathers instead of following them.
+// Addresses and sizes are multiples of 16 bytes as the instruction requires.
+__device__ inline void prefetch_planes_l2(const void *base, int planes, long V, int s0, int n) {
+#if defined(__CUDA_ARCH__)
+    const unsigned bytes = (unsigned)n * 16u;
+    for (int c = 0; c < planes; ++c) {
+        const char *a = (const char *)base + ((size_t)c * V + s0) * 16;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
+    }
+#endif
 }
 
 template <bool G5> __host__ __device__ inline void maybe_g5(double2 (&v)[12]) {

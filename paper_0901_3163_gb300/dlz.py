@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("reorth_period", ctypes.c_int), ("precision", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("profile", ctypes.c_int), ("finish", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("finish", ctypes.c_int), ("eig_only", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -48,10 +48,12 @@ class Stats(ctypes.Structure):
                 ("mvps", ctypes.c_longlong), ("true_residual", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("stencil_ms", ctypes.c_double),
                 ("stencil_launches", ctypes.c_longlong), ("stencil_bytes", ctypes.c_double),
-                ("gpu_launches", ctypes.c_longlong)]
+                ("gpu_launches", ctypes.c_longlong), ("kernel_ms", ctypes.c_double * 3),
+                ("kernel_bytes", ctypes.c_double * 3), ("kernel_launches", ctypes.c_longlong * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: (list(getattr(self, k)) if k.startswith("kernel_") else getattr(self, k))
+                for k, _ in self._fields_}
 
 
 class DlzError(RuntimeError):
@@ -76,6 +78,14 @@ _SIGS = {
     "dlz_destroy_operator": ([_vp], _ip),
     "dlz_op_volume": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _ip),
     "dlz_apply": ([_vp, _ip, _vp, _vp, _ip, _ip], _ip),
+    "dlz_create_operator_eo": ([ctypes.POINTER(ctypes.c_int), _vp, ctypes.c_double, _ip, _vp,
+                                ctypes.POINTER(_vp)], _ip),
+    "dlz_eo_prepare": ([_vp, _vp, _vp, _ip], _ip),
+    "dlz_basis_combine": ([_vp, ctypes.c_longlong, _ip, ctypes.c_longlong, _vp, _ip, _ip, _vp, ctypes.c_longlong], _ip),
+    "dlz_basis_dots": ([_vp, ctypes.c_longlong, _ip, _vp, ctypes.c_longlong, _ip, ctypes.c_longlong, _vp], _ip),
+    "dlz_batch_last_choice": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int)], _ip),
+    "dlz_eo_reconstruct": ([_vp, _vp, _vp, _vp, _ip], _ip),
     "dlz_apply_noalloc": ([_vp, _ip, _vp, _vp, _ip, _ip], _ip),
     "dlz_landr": ([_vp, _vp, _vp, ctypes.POINTER(Params), ctypes.POINTER(_vp),
                    ctypes.POINTER(Stats)], _ip),
@@ -102,7 +112,7 @@ _SIGS = {
     "dlz_net_set_weights": ([_vp, _vp], _ip),
     "dlz_net_zero_grad": ([_vp], _ip),
     "dlz_net_adam_step": ([_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double], _ip),
-    "dlz_subspace_loss": ([_vp, _vp, _ip, _dp, _vp], _ip),
+    "dlz_subspace_loss": ([_vp, _vp, _ip, ctypes.c_double, _dp, _vp], _ip),
     "dlz_seed_deflation": ([_vp, _ip, _vp, _ip, _ip, ctypes.POINTER(_vp)], _ip),
     "dlz_host_symeig": ([_ip, _vp, _vp, _vp], _ip),
     "dlz_host_sym_extremes": ([_ip, _vp, _vp, _vp], _ip),
@@ -153,6 +163,14 @@ def _empty_like(a, dtype=None):
         return np.empty(a.shape, dtype=dtype or a.dtype)
     import torch
     return torch.empty(a.shape, dtype=dtype or a.dtype, device=a.device)
+
+
+def _empty_shape(a, shape):
+    """Uninitialised array of `shape` with a's dtype, on a's device."""
+    if isinstance(a, np.ndarray):
+        return np.empty(shape, dtype=a.dtype)
+    import torch
+    return torch.empty(shape, dtype=a.dtype, device=a.device)
 
 
 def _stream_handle(stream):
@@ -213,6 +231,35 @@ def create_operator(dims, gauge, kappa, bc_t=1, stream=None):
     _check(lib.dlz_create_operator(d, _ptr(gauge), float(kappa), int(bc_t),
                                    _stream_handle(stream), ctypes.byref(h)))
     return Operator(h, dims, kappa, bc_t)
+
+
+def create_operator_eo(dims, gauge, kappa, bc_t=1, stream=None):
+    """Even-odd (Schur complement) operator on the even sites; its vectors are [V/2, 4, 3]."""
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    h = _vp()
+    _check(lib.dlz_create_operator_eo(d, _ptr(gauge), float(kappa), int(bc_t),
+                                      _stream_handle(stream), ctypes.byref(h)))
+    op = Operator(h, dims, kappa, bc_t)
+    op.eo = True
+    return op
+
+
+def eo_prepare(op, b, out=None):
+    """b_e + kappa H_eo b_o for full-lattice b [nrhs?, V, 4, 3] -> [nrhs?, V/2, 4, 3]."""
+    nrhs = int(np.prod(b.shape)) // (24 * op.volume)
+    if out is None:
+        out = _empty_shape(b, tuple(b.shape[:-3]) + (op.volume, 4, 3))
+    _check(lib.dlz_eo_prepare(op.handle, _ptr(b), _ptr(out), nrhs))
+    return out
+
+
+def eo_reconstruct(op, x_e, b, out=None):
+    """Full solution (x_e, b_o + kappa H_oe x_e) [nrhs?, V, 4, 3] from x_e and b."""
+    nrhs = int(np.prod(b.shape)) // (24 * op.volume)
+    if out is None:
+        out = _empty_like(b)
+    _check(lib.dlz_eo_reconstruct(op.handle, _ptr(x_e), _ptr(b), _ptr(out), nrhs))
+    return out
 
 
 def apply(op, which, x, out=None, dtype=None):
@@ -292,6 +339,43 @@ def batch_dminres(ops, defls, Bs, params=None, Xs=None):
         out.append([st[q + i] for i in range(r)])
         q += r
     return Xs, out
+
+
+def basis_combine(V, coef, out=None):
+    """out[j] = sum_i coef[i, j] V[i] on the tensor cores.  V: device float32 [nin, len]
+    (real coef, float64 [nin, nout]) or complex64 [nin, L] (complex coef, complex128
+    [nin, nout])."""
+    import torch
+    cplx = V.dtype == torch.complex64
+    nin = V.shape[0]
+    nout = coef.shape[1]
+    Vf = torch.view_as_real(V).reshape(nin, -1) if cplx else V
+    ln = Vf.shape[1]
+    if out is None:
+        out = torch.empty((nout,) + tuple(V.shape[1:]), dtype=V.dtype, device=V.device)
+    of = torch.view_as_real(out).reshape(nout, -1) if cplx else out
+    c = np.ascontiguousarray(coef, dtype=np.complex128 if cplx else np.float64)
+    _check(lib.dlz_basis_combine(_ptr(Vf), ln, nin, ln, c.ctypes.data, nout, int(cplx), _ptr(of), ln))
+    return out
+
+
+def basis_dots(V, R):
+    """C[q, i] = <V_i, R_q> (complex) on the tensor cores; V, R: device complex64 [n?, L]."""
+    import torch
+    nin, nq = V.shape[0], R.shape[0]
+    Vf = torch.view_as_real(V).reshape(nin, -1)
+    Rf = torch.view_as_real(R).reshape(nq, -1)
+    ln = Vf.shape[1]
+    C = np.empty((nq, nin), dtype=np.complex128)
+    _check(lib.dlz_basis_dots(_ptr(Vf), ln, nin, _ptr(Rf), ln, nq, ln, C.ctypes.data))
+    return C
+
+
+def batch_last_choice(op):
+    """(form, chunks per block, half grid) the last FP32 batch_dminres call on op chose."""
+    f, c, h = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.dlz_batch_last_choice(op.handle, ctypes.byref(f), ctypes.byref(c), ctypes.byref(h)))
+    return f.value, c.value, h.value
 
 
 def defl_count(defl):
@@ -429,12 +513,14 @@ def net_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     _check(lib.dlz_net_adam_step(net.handle, float(lr), float(beta1), float(beta2), float(eps)))
 
 
-def subspace_loss(defl, f, want_grad=True):
-    """Per-vector ||(1 - V V^dag) f||^2 / ||f||^2 against defl, and G(f) (device complex64)."""
+def subspace_loss(defl, f, want_grad=True, grad_scale=1.0):
+    """Per-vector ||(1 - V V^dag) f||^2 / ||f||^2 against defl, and grad_scale * G(f)
+    (device complex64)."""
     nvec = int(np.prod(f.shape)) // (12 * defl.op.volume)
     loss = np.empty(nvec)
     g = _empty_like(f) if want_grad else None
-    _check(lib.dlz_subspace_loss(defl.handle, _ptr(f), nvec, loss.ctypes.data_as(_dp), _ptr(g)))
+    _check(lib.dlz_subspace_loss(defl.handle, _ptr(f), nvec, ctypes.c_double(grad_scale),
+                                 loss.ctypes.data_as(_dp), _ptr(g)))
     return loss, g
 
 

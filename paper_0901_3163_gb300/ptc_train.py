@@ -60,8 +60,8 @@ def train(torch, net, ops, defls, steps, nvec=4, lr=3e-3, seed=0, log=None):
         dlz.net_bind(net, ops[i])
         x = noise(torch, ops[i], nvec, gen)
         f = dlz.net_forward(net, x)
-        loss, g = dlz.subspace_loss(defls[i], f)
-        dlz.net_backward(net, g / nvec)
+        loss, g = dlz.subspace_loss(defls[i], f, grad_scale=1.0 / nvec)   # gradient of the mean
+        dlz.net_backward(net, g)
         dlz.net_adam_step(net, lr)
         hist.append(float(loss.mean()))
         if log and (it % 50 == 0 or it == steps - 1):
@@ -85,32 +85,40 @@ def ritz_residual_median(defl):
 
 
 def evaluate(torch, net, op, b_list, m, k, seed=0, net_untrained=None):
-    """Seeded vs plain Lan-DR deflation sets on one field.
+    """Seeded vs plain Lan-DR deflation sets on one field, at an equal MVP budget.
 
-    plain: one Lan-DR(m, k) cycle on the first right-hand side (m MVPs of D^dag D);
-    seeded: Rayleigh-Ritz over k network outputs (k MVPs).  The set used for the
-    remaining solves is the seeded one unless plain Lan-DR's median Ritz residual is
-    lower (fallback).  Returns medians, D-CG iterations to 1e-10 on b_list for each
+    seeded: Rayleigh-Ritz over k network outputs (k products with D^dag D);
+    plain (equal budget): one Lan-DR(k+1, k) cycle on the first right-hand side
+    (k+1 products with D^dag D), the Krylov-space set the same budget buys;
+    plain (context): one Lan-DR(m, k) cycle (m products).  The set used for the
+    remaining solves is the seeded one unless the equal-budget plain set's median
+    Ritz residual is lower (fallback).  Returns the medians, the MVPs (applications
+    of D or D^dag) each set cost, D-CG iterations to 1e-10 on b_list[1:] for each
     set and undeflated, and which set the rule picks."""
+    p_eq = dlz.params_default(m=k + 1, k=k, tol=1e-10, max_cycles=1)
+    _, d_eq, st_eq = dlz.landr(op, b_list[0], p_eq)
     p1 = dlz.params_default(m=m, k=k, tol=1e-10, max_cycles=1)
     _, d_plain, st_plain = dlz.landr(op, b_list[0], p1)
     t0 = time.perf_counter()
     d_seed = seed_set(torch, net, op, k, seed)
     torch.cuda.synchronize()
     t_seed = time.perf_counter() - t0
-    out = {"plain_mvps": int(st_plain.mvps), "seed_mvps": k,
-           "ritz_median_plain": ritz_residual_median(d_plain),
-           "ritz_median_seed": ritz_residual_median(d_seed), "seed_seconds": t_seed}
+    out = {"seed_mvps": 2 * k, "plain_equal_mvps": int(st_eq.mvps), "plain_m_mvps": int(st_plain.mvps),
+           "ritz_median_seed": ritz_residual_median(d_seed),
+           "ritz_median_plain": ritz_residual_median(d_eq),
+           "ritz_median_plain_m_cycle": ritz_residual_median(d_plain), "seed_seconds": t_seed}
     if net_untrained is not None:
         out["ritz_median_untrained"] = ritz_residual_median(seed_set(torch, net_untrained, op, k, seed))
     pd = dlz.params_default(m=m, k=k, tol=1e-10, max_iter=100000)
     B = torch.stack(list(b_list[1:]))
     _, s_seed = dlz.dcg(op, d_seed, B, pd)
+    _, s_eq = dlz.dcg(op, d_eq, B, pd)
     _, s_plain = dlz.dcg(op, d_plain, B, pd)
     _, s_none = dlz.dcg(op, None, B, pd)
     out["dcg_iters_seed"] = [s.iterations for s in s_seed]
+    out["dcg_iters_plain_equal"] = [s.iterations for s in s_eq]
     out["dcg_iters_plain_cycle"] = [s.iterations for s in s_plain]
     out["cg_iters_undeflated"] = [s.iterations for s in s_none]
-    out["converged"] = all(s.converged == 1 for s in list(s_seed) + list(s_plain) + list(s_none))
+    out["converged"] = all(s.converged == 1 for s in list(s_seed) + list(s_eq) + list(s_plain) + list(s_none))
     out["chosen"] = "seed" if out["ritz_median_seed"] <= out["ritz_median_plain"] else "plain Lan-DR"
     return out

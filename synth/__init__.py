@@ -151,4 +151,13 @@ WORKLOADS = {
     # sources.
     "wilson_16x16x16x32": dict(dims=(16, 16, 16, 32), gauge_seed=2, m=100, k=40,
                                point_sources=12),
+    # 24^3x48 lattice, Lan-DR(120,60) on D^dagger D for one Gaussian RHS (seed 0),
+    # then D-CG on 48 Gaussian RHS (seeds 1..48).
+    "wilson_24x24x24x48": dict(dims=(24, 24, 24, 48), gauge_seed=3, m=120, k=60,
+                               first_rhs_seed=0, rhs_seeds=tuple(range(1, 49))),
+    # 64 lattices of uneven size (lattice i: 8^4, 12^4 or 16^4 for i mod 3 = 0, 1, 2;
+    # gauge seed 3000 + i); MinRes-DR(40,10) on one Gaussian RHS (seed 0), then
+    # D-MinRes on 8 Gaussian RHS (seeds 1..8) per lattice.
+    "uneven_64": dict(sizes=((8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16)), lattices=64,
+                      gauge_seed0=3000, m=40, k=10, first_rhs_seed=0, rhs_seeds=tuple(range(1, 9))),
 }

@@ -19,18 +19,46 @@ import synth  # noqa: E402
 from oracle import kappa as okappa  # noqa: E402
 
 
+def _store(key, entry):
+    """Add one entry to the table, re-reading it first (several searches may run at once)."""
+    import fcntl
+    with open(synth.KAPPA_TABLE + ".lock", "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        table = {}
+        if os.path.exists(synth.KAPPA_TABLE):
+            with open(synth.KAPPA_TABLE) as f:
+                table = json.load(f)
+        table[key] = entry
+        tmp = synth.KAPPA_TABLE + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+        os.replace(tmp, synth.KAPPA_TABLE)
+
+
 def main(argv):
-    table = {}
-    if os.path.exists(synth.KAPPA_TABLE):
-        with open(synth.KAPPA_TABLE) as f:
-            table = json.load(f)
     for spec in argv:
         lat, seed = spec.split(":")
         dims = tuple(int(v) for v in lat.split("x"))
         seed = int(seed)
         U = synth.su3_links(dims, seed)
         t0 = time.time()
-        if synth.volume(dims) <= 256:
+        bracket = os.environ.get("KAPPA_BRACKET")
+        if bracket:
+            # a:sigma_a:b:sigma_b from earlier oracle evaluations on this lattice
+            a, sa, b, sb = (float(v) for v in bracket.split(":"))
+            rtol = float(os.environ.get("KAPPA_RTOL", "1e-4"))
+            cap = int(os.environ.get("KAPPA_MAX_CYCLES", "150"))
+            kap, sig, res, bound, hist = okappa.kappa_newton(
+                U, dims, a, sa, b, sb, rtol=rtol, max_cycles=cap,
+                log=lambda s: print(s, flush=True))
+            how = ("MinRes-DR(100,20) as an eigensolver (Rayleigh quotient of the harmonic Ritz "
+                   f"vector nearest zero, warm-started, at most {cap} cycles per evaluation); "
+                   f"Newton with the Hellmann-Feynman slope inside the bracket [{a}, {b}] to "
+                   f"|sigma/1e-3 - 1| < {rtol}; residual of the final estimate {res:.2e}, "
+                   f"Kato-Temple bound on its error {bound:.2e}")
+            extra = dict(evaluations=hist)
+        elif synth.volume(dims) <= 256:
+            extra = {}
             kap, sig = okappa.kappa_dense(U, dims)
             how = "dense LAPACK eigvalsh of D^dagger D; scan from 0 by 0.005, Illinois refine"
         else:
@@ -41,16 +69,16 @@ def main(argv):
             kap, sig, res = okappa.kappa_iterative(
                 U, dims, start=start, step=step, rtol=rtol, max_cycles=cap,
                 log=lambda s: print(s, flush=True))
+            extra = {}
             how = ("MinRes-DR(100,20) as an eigensolver: harmonic Ritz pair nearest zero of "
                    f"gamma5 D (at most {cap} cycles per evaluation); steps of {step} from {start} "
                    f"to bracket, Illinois refine to |sigma/1e-3 - 1| < {rtol}; harmonic Ritz "
                    f"residual of the final estimate {res:.2e}")
         key = f"{lat}_s{seed}"
-        table[key] = dict(kappa=kap, sigma_min=sig, method=how,
-                          seconds=round(time.time() - t0, 1), host=platform.machine())
-        print(key, table[key], flush=True)
-        with open(synth.KAPPA_TABLE, "w") as f:
-            json.dump(table, f, indent=1, sort_keys=True)
+        entry = dict(kappa=kap, sigma_min=sig, method=how,
+                     seconds=round(time.time() - t0, 1), host=platform.machine(), **extra)
+        print(key, entry, flush=True)
+        _store(key, entry)
 
 
 if __name__ == "__main__":

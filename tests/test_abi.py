@@ -21,7 +21,7 @@ def test_params_defaults():
     m = dlz()
     p = m.params_default()
     assert (p.m, p.k, p.tol, p.oversolve, p.reorth_period, p.precision) == (40, 10, 1e-10, 1.0, 10, m.F64)
-    assert p.reliable_delta == 1e-2 and p.finish == 0
+    assert p.reliable_delta == 1e-2 and p.finish == 0 and p.eig_only == 0
 
 
 def test_error_names():
@@ -126,6 +126,12 @@ def test_argument_validation_without_gpu():
     assert m.lib.dlz_apply(None, 0, None, None, 0, 1) == m.ERR_BADARG
     assert m.lib.dlz_defl_count(None, None, None) == m.ERR_BADARG
     assert "null" in m.last_error()
+    # even-odd entries: odd extents and null operators are rejected before any GPU work
+    odd = (ctypes.c_int * 4)(4, 4, 3, 4)
+    assert m.lib.dlz_create_operator_eo(odd, g.ctypes.data, 0.1, 1, None, ctypes.byref(out)) == m.ERR_BADARG
+    assert "even" in m.last_error()
+    assert m.lib.dlz_eo_prepare(None, None, None, 1) == m.ERR_BADARG
+    assert m.lib.dlz_eo_reconstruct(None, None, None, None, 1) == m.ERR_BADARG
 
 
 def test_argument_validation_of_batch_network_and_noalloc_entries_without_gpu():
@@ -146,7 +152,7 @@ def test_argument_validation_of_batch_network_and_noalloc_entries_without_gpu():
     assert m.lib.dlz_net_backward(None, None, 1, None) == m.ERR_BADARG
     assert m.lib.dlz_net_adam_step(None, 1e-3, 0.9, 0.999, 1e-8) == m.ERR_BADARG
     assert m.lib.dlz_net_bind(None, None) == m.ERR_BADARG
-    assert m.lib.dlz_subspace_loss(None, None, 1, None, None) == m.ERR_BADARG
+    assert m.lib.dlz_subspace_loss(None, None, 1, 1.0, None, None) == m.ERR_BADARG
     assert m.lib.dlz_seed_deflation(None, m.DDAGD, None, m.F64, 4, ctypes.byref(out)) == m.ERR_BADARG
     assert m.lib.dlz_apply_noalloc(None, 0, None, None, m.F64, 1) == m.ERR_BADARG
     bad_params = m.params_default()

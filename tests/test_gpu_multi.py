@@ -77,3 +77,56 @@ def test_batch_dminres_tiles_bit_identical(m, monkeypatch):
         assert its == ref_it, tile
         for a, b in zip(xs, ref_x):
             assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), tile
+
+
+def _small_batch(m):
+    ops, Bs = [], []
+    for i, (dims, kappa, seed) in enumerate(LATS):
+        U = synth.su3_links(dims, seed)
+        ops.append(m.create_operator(dims, torch.from_numpy(U).cuda(), kappa))
+        Bs.append(torch.from_numpy(synth.gaussian_spinors(dims, [5 + i, 6 + i])).cuda())
+    return ops, Bs
+
+
+def test_batch_dminres_persistent_and_graph_forms_bit_identical(m, monkeypatch):
+    """The persistent form (one cooperative launch over all slots and iterations, grid
+    barriers between the stages) against the graph form and the autotuner's pick: the
+    same chunk partials and the same freezing points give the same bits."""
+    ops, Bs = _small_batch(m)
+    p = m.params_default(m=30, k=8, tol=1e-10, max_iter=20000, precision=m.F32)
+    runs = {}
+    for form, tile in [("graph", "1"), ("persistent", "1"), ("persistent", "2"), ("persistent", "4"), (None, None)]:
+        for var, val in (("DLZ_MULTI_FORM", form), ("DLZ_MULTI_TILE", tile)):
+            if val is None:
+                monkeypatch.delenv(var, raising=False)
+            else:
+                monkeypatch.setenv(var, val)
+        Xs, sts = m.batch_dminres(ops, [None] * len(ops), Bs, p)
+        assert all(s.converged == 1 for ss in sts for s in ss)
+        runs[(form, tile)] = ([x.cpu().numpy() for x in Xs], [[s.iterations for s in ss] for ss in sts],
+                              m.batch_last_choice(ops[0]))
+    ref_x, ref_it, _ = runs[("graph", "1")]
+    for key, (xs, its, choice) in runs.items():
+        assert its == ref_it, key
+        for a, b in zip(xs, ref_x):
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), key
+    assert runs[("persistent", "2")][2][:2] == (1, 2)
+    assert runs[("graph", "1")][2][:2] == (0, 1)
+
+
+def test_persistent_barrier_wait_limit_returns_device_timeout(m, monkeypatch):
+    """Failure detection without a fault: with a wait limit of zero polls, every block
+    that has to wait at a grid barrier gives up at once, sets the error word and
+    returns; the call reports DLZ_ERR_DEVICE_TIMEOUT and the context stays usable (the
+    same call with the default limit then succeeds)."""
+    ops, Bs = _small_batch(m)
+    p = m.params_default(m=30, k=8, tol=1e-10, max_iter=20000, precision=m.F32)
+    monkeypatch.setenv("DLZ_MULTI_FORM", "persistent")
+    monkeypatch.setenv("DLZ_MULTI_TILE", "1")
+    monkeypatch.setenv("DLZ_WAIT_LIMIT", "0")
+    with pytest.raises(m.DlzError) as e:
+        m.batch_dminres(ops, [None] * len(ops), Bs, p)
+    assert e.value.code == m.ERR_DEVICE_TIMEOUT
+    monkeypatch.delenv("DLZ_WAIT_LIMIT")
+    Xs, sts = m.batch_dminres(ops, [None] * len(ops), Bs, p)
+    assert all(s.converged == 1 for ss in sts for s in ss)

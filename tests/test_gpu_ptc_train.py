@@ -56,8 +56,20 @@ def test_training_lowers_held_out_loss_and_fallback_rule(m):
     op, _ = held[0]
     bl = [torch.from_numpy(synth.gaussian_spinor(DIMS, s)).cuda() for s in (10, 11, 12)]
     r = T.evaluate(torch, net, op, bl, M, K, net_untrained=net0)
+    print("learned seed vs plain Lan-DR at equal MVPs:", {k_: r[k_] for k_ in (
+        "seed_mvps", "plain_equal_mvps", "ritz_median_seed", "ritz_median_plain", "ritz_median_untrained",
+        "dcg_iters_seed", "dcg_iters_plain_equal", "cg_iters_undeflated", "chosen")})
     assert r["converged"]
+    # the two sets cost the same budget: 2k applications of D or D^dag against
+    # 2(k+1) + 2 (Lanczos steps, D^dag b and the true residual)
+    assert abs(r["plain_equal_mvps"] - r["seed_mvps"]) <= 4
     assert r["ritz_median_seed"] < r["ritz_median_untrained"]
     assert r["chosen"] == ("seed" if r["ritz_median_seed"] <= r["ritz_median_plain"] else "plain Lan-DR")
+    # what training gains over the method without it, at the same budget: nothing here.
+    # One Lan-DR(k+1, k) cycle's Krylov space beats the trained network's outputs (median
+    # Ritz residual 0.46 against 1.01 on GB300, a factor 2.2), so the fallback keeps
+    # plain Lan-DR; the assertion holds that margin with room for run-to-run noise
+    assert r["ritz_median_plain"] * 1.5 <= r["ritz_median_seed"]
+    assert r["chosen"] == "plain Lan-DR"
     # deflation by either set never costs iterations over undeflated CG
     assert max(r["dcg_iters_plain_cycle"]) <= max(r["cg_iters_undeflated"])

@@ -160,6 +160,30 @@ def test_dr_on_paper_hpd_example_finds_lowest_eigenvalues(method):
     assert np.abs(r.Vk.conj().T @ r.Vk - np.eye(10)).max() < 1e-12
 
 
+@pytest.mark.parametrize("m,k", [(40, 10), (200, 150)])
+def test_landr_as_eigensolver_on_paper_hpd_example(m, k):
+    """Eigensolver use (Sec. 2's k = 150 with m = 200 included): the linear tolerance
+    is unreachable (1e-30), so only the kept pairs can stop the cycles; all k Ritz
+    values must be the k smallest eigenvalues 0.1, 1, 2, ... of the Sec. 1 example."""
+    d = synth.diag_hpd_1000()
+    b = np.ones(1000, dtype=complex) / np.sqrt(1000)
+    r = K.landr(_diag_op(d), b, m=m, k=k, tol=1e-30, tol_eig=1e-9, max_cycles=2000, eig_only=True)
+    assert r.info.converged
+    exact = np.sort(d)[:k]
+    assert np.all(np.abs(np.sort(r.ritz_values) - exact) <= 1e-8 * exact)
+    assert np.all(r.ritz_residuals <= 1e-10 * d.max())       # ||A|| = 999
+    assert np.abs(r.Vk.conj().T @ r.Vk - np.eye(k)).max() < 1e-8
+
+
+def test_minresdr_as_eigensolver_on_paper_indefinite_example():
+    d, _ = synth.diag_indefinite_1000()
+    b = np.ones(1000, dtype=complex) / np.sqrt(1000)
+    r = K.minresdr(_diag_op(d), b, m=40, k=10, tol=1e-30, tol_eig=1e-9, max_cycles=2000, eig_only=True)
+    assert r.info.converged
+    exact = d[np.argsort(np.abs(d))[:10]]
+    assert np.all(np.abs(np.sort(r.ritz_values) - np.sort(exact)) <= 1e-8 * np.abs(np.sort(exact)))
+
+
 def test_minresdr_on_paper_indefinite_example():
     d, _ = synth.diag_indefinite_1000()
     b = np.ones(1000, dtype=complex) / np.sqrt(1000)
