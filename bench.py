@@ -872,6 +872,43 @@ def run_saturation(args):
     print(json.dumps(out), flush=True)
 
 
+def run_gmresdr(args):
+    """GMRES-DR(m,k) and D-GMRES(m) on D itself (FP64; the non-hermitian methods the
+    paper contrasts with) beside MinRes-DR(m,k) + D-MinRes (FP64, the paper's hermitian
+    method for the same D x = b) on one lattice: the first Gaussian RHS (seed 0) by the
+    DR method, then 4 Gaussian RHS (seeds 1..4) by the deflated solver; MVPs, seconds
+    and verified solves of each.  Lattice and kappa by --lattice / --kappa (default
+    8^4 at kappa 0.25, gauge seed 3000).  Prints one JSON line."""
+    import torch
+
+    import synth
+    from paper_0901_3163_gb300 import dlz
+    dims = tuple(int(v) for v in args.lattice.split("x")) if args.lattice else (8, 8, 8, 8)
+    kappa = args.kappa if args.kappa is not None else 0.25
+    op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, 3000)).cuda(), kappa)
+    b0 = torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda()
+    B = torch.from_numpy(synth.gaussian_spinors(dims, (1, 2, 3, 4))).cuda()
+    m, k = 40, 10
+    out = {"mode": "gmresdr", "lattice": list(dims), "kappa": kappa, "m": m, "k": k}
+    for name, dr, ds in (("gmresdr_dgmres", dlz.gmresdr, dlz.dgmres), ("minresdr_dminres", dlz.minresdr, dlz.dminres)):
+        p = dlz.params_default(m=m, k=k, tol=1e-10, max_cycles=2000, max_iter=200000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, d, st = dr(op, b0, p)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, sts = ds(op, d, B, p)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out[name] = {"first_rhs": {"seconds": round(t1 - t0, 3), "mvps": int(st.mvps), "cycles": st.cycles,
+                                   "verified": st.converged == 1},
+                     "later_rhs": {"seconds": round(t2 - t1, 3), "mvps": [int(s.mvps) for s in sts],
+                                   "verified": all(s.converged == 1 and s.true_residual <= 1e-10 for s in sts)}}
+    _, stp = dlz.dgmres(op, None, B, dlz.params_default(m=m, k=k, tol=1e-10, max_iter=200000))
+    out["plain_gmres_mvps"] = [int(s.mvps) for s in stp]
+    print(json.dumps(out), flush=True)
+
+
 def run_multi_lattice(args):
     """The uneven multi-lattice batch alone (the c4 key of the default line)."""
     import torch
@@ -909,6 +946,7 @@ def main():
     ap.add_argument("--learned-seed", action="store_true")
     ap.add_argument("--multi-lattice", action="store_true")
     ap.add_argument("--saturation", action="store_true")
+    ap.add_argument("--gmresdr", action="store_true")
     ap.add_argument("--sat-k", type=int, nargs="+", default=[20, 60, 100, 150])
     ap.add_argument("--ls-train", type=int, default=32)
     ap.add_argument("--ls-test", type=int, default=8)
@@ -926,6 +964,8 @@ def main():
         run_multi_lattice(args)
     elif args.saturation:
         run_saturation(args)
+    elif args.gmresdr:
+        run_gmresdr(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

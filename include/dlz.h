@@ -245,7 +245,14 @@ int dlz_apply(dlz_op_t op, int which, const void *in, void *out, int dtype, int 
  * operator's stream has finished the work), like dlz_apply.  The first call
  * on each device looks the array's address up (cudaGetSymbolAddress) and
  * should come before any stream capture that the caller starts.  Returns
- * DLZ_ERR_CUDA if that lookup fails.
+ * DLZ_ERR_CUDA if that lookup fails.  The address is kept per device for
+ * the life of the process: after a cudaDeviceReset (a new context, where the
+ * array may sit elsewhere) the kept address is stale, so a process that resets
+ * a device must not call dlz_apply_noalloc on it again.
+ *
+ * The array is part of the library's device code: every process that loads
+ * the library holds DLZ_NOALLOC_SCRATCH_BYTES on each device it uses, whether
+ * or not it ever calls dlz_apply_noalloc, until the process exits.
  */
 int dlz_apply_noalloc(dlz_op_t op, int which, const void *in, void *out, int dtype, int nrhs);
 
@@ -291,8 +298,32 @@ int dlz_dcg(dlz_op_t op, dlz_defl_t defl, const void *B, void *X, int nrhs,
 int dlz_dminres(dlz_op_t op, dlz_defl_t defl, const void *B, void *X, int nrhs,
                 const dlz_params *p, dlz_stats *stats);
 
+/*
+ * GMRES-DR(m,k) and D-GMRES(m) on D itself (non-hermitian), FP64 only
+ * (p->precision must be DLZ_F64) -- the deflated methods for non-hermitian systems
+ * that the paper contrasts its hermitian methods with (its refs. [1], [2]):
+ * dlz_gmresdr: restarted Arnoldi (Gram-Schmidt twice) with a least-squares solve per
+ *   cycle, keeping the k harmonic Ritz vectors of smallest |theta| (eigenpairs of
+ *   H_m + |h_{m+1,m}|^2 H_m^{-H} e_m e_m^H) across restarts; stops on the FP64
+ *   ||b - D x|| / ||b|| <= tol (checked once per cycle).  Arguments as dlz_landr; the
+ *   deflation set (which = DLZ_D) holds V_{k+1} and Hbar_k with D V_k = V_{k+1} Hbar_k,
+ *   and its pairs are the kept harmonic Ritz pairs: dlz_defl_get gives Re theta and the
+ *   FP64 residual ||D y - theta y||, dlz_defl_value_complex gives theta.  Not saved to
+ *   files (dlz_defl_save: DLZ_ERR_BADARG).
+ * dlz_dgmres: for each right-hand side, a minimum-residual projection over span(V_k)
+ *   (y = argmin ||V_{k+1}^H r - Hbar_k y||, x += V_k y) then one GMRES(m) cycle, repeated
+ *   until tol; p->max_iter bounds the Arnoldi steps.  defl NULL: plain GMRES(m).
+ *   Arguments as dlz_dcg; defl must come from dlz_gmresdr on the same operator.
+ */
+int dlz_gmresdr(dlz_op_t op, const void *b, void *x, const dlz_params *p, dlz_defl_t *defl_out, dlz_stats *stats);
+int dlz_dgmres(dlz_op_t op, dlz_defl_t defl, const void *B, void *X, int nrhs, const dlz_params *p,
+               dlz_stats *stats);
+/* The i-th value of a deflation set as a complex number: theta_i of a GMRES-DR set,
+ * (value_i, 0) of the hermitian sets. */
+int dlz_defl_value_complex(dlz_defl_t d, int i, double *re, double *im);
+
 /* Number k of vectors in a deflation set, and which operator it deflates
- * (DLZ_DDAGD from dlz_landr, DLZ_Q from dlz_minresdr). */
+ * (DLZ_DDAGD from dlz_landr, DLZ_Q from dlz_minresdr, DLZ_D from dlz_gmresdr). */
 int dlz_defl_count(dlz_defl_t d, int *k, int *which);
 /*
  * i-th Rayleigh-Ritz pair of the deflation set: eigenvalues of H in
@@ -454,6 +485,18 @@ int dlz_host_sym_extremes(int n, const double *A, double *lo, double *hi);
 int dlz_host_lstsq(int rows, int cols, const double *T, const double *c, double *y, double *q);
 int dlz_host_restart_plan(int harmonic, int m, int k, const double *Tbar, const double *c, double *y, double *P,
                           double *Tn, double *cn, double *theta, double *ritz_res, double *anorm);
+/*
+ * Complex host helpers of GMRES-DR (exported for testing; no GPU needed).  Complex
+ * values are interleaved (re, im) doubles, matrices row-major.
+ *   dlz_host_zgeev: eigenvalues w[n] and unit eigenvectors (column j of Z, n x n; Z
+ *     may be NULL) of a general complex n x n matrix A (Householder Hessenberg
+ *     reduction, single-shift QR to Schur form, back substitution).
+ *   dlz_host_zlstsq: y = argmin ||c - A y|| for A rows x cols, rows > cols, by
+ *     Householder QR; q[rows] (may be NULL; rows == cols + 1) receives the unit vector
+ *     spanning range(A)^perp.
+ */
+int dlz_host_zgeev(int n, const double *A, double *w, double *Z);
+int dlz_host_zlstsq(int rows, int cols, const double *A, const double *c, double *y, double *q);
 
 #ifdef __cplusplus
 }

@@ -290,7 +290,7 @@ class DRResult:
     ritz_vectors: np.ndarray | None = None  # n x k, unit Rayleigh-Ritz vectors of span(Vk)
 
 
-def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
+def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=1,
           full_reorth=False, residual=None, oversolve=1.0, eig_stop=None, progress=None,
           plan_hook=None, eig_only=False):
     """Lan-DR(m,k) for hermitian positive definite A (Sec. 1, Sec. 2).
@@ -321,9 +321,10 @@ def landr(A, b, m, k, tol=1e-10, tol_eig=None, max_cycles=500, reorth_period=10,
     """
     # Converged kept Ritz vectors attract rounding errors in every new Lanczos
     # vector (the loss of orthogonality grows like eps ||A|| / Ritz residual), so
-    # Lan-DR re-orthogonalises against the kept vectors at every step.
-    if reorth_period:
-        reorth_period = 1
+    # Lan-DR re-orthogonalises against the kept vectors at every step: reorth_period
+    # is 1 (every step) or 0 (off); any other value is refused rather than ignored.
+    if reorth_period not in (0, 1):
+        raise ValueError("Lan-DR re-orthogonalises at every step (reorth_period 1) or not at all (0)")
     return _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth,
                residual, oversolve, harmonic=False, eig_stop=eig_stop, progress=progress,
                plan_hook=plan_hook, eig_only=eig_only)

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdlz.so")
 SOURCES = ["wilson.cu", "wilson_eo.cu", "wilson_bf16.cu", "dr.cu", "solvers.cu", "solvers_mixed.cu", "minres_fused.cu",
-           "cg_fused.cu", "minres_multi.cu", "api.cu", "ptc.cu", "tc_gemm.cu", "small_dense.cpp", "restart_plan.cpp"]
+           "cg_fused.cu", "minres_multi.cu", "gmres.cu", "api.cu", "ptc.cu", "tc_gemm.cu", "small_dense.cpp", "small_dense_z.cpp", "restart_plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

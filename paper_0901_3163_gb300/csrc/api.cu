@@ -839,6 +839,84 @@ int dlz_dminres(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nrhs, cons
     return dsolve_entry(h, d, B, X, nrhs, p, stats, true);
 }
 
+int dlz_gmresdr(dlz_op_t h, const void *b, void *x, const dlz_params *p, dlz_defl_t *defl_out, dlz_stats *stats) {
+    DLZ_TRY(check_op(h));
+    DLZ_TRY(check_params(p));
+    if (p->precision != DLZ_F64) return fail(DLZ_ERR_BADARG, "GMRES-DR is built in FP64 (precision DLZ_F64)");
+    if (!b || !x) return fail(DLZ_ERR_BADARG, "null vector");
+    Op &op = h->op;
+    if (defl_out) *defl_out = nullptr;
+    dlz_stats st;
+    std::memset(&st, 0, sizeof(st));
+    CallStats cs(op, stats, p->profile != 0, false);
+    const long n = 12L * op.g.V;
+    Staged sb, sx;
+    DLZ_TRY(sb.in(op, b, n * sizeof(double2)));
+    DLZ_TRY(sx.out(op, x, n * sizeof(double2)));
+    DevBuf bi, xi;
+    DLZ_TRY(bi.alloc(n * sizeof(double2)));
+    DLZ_TRY(xi.alloc(n * sizeof(double2)));
+    DLZ_TRY(pack64(op, bi.as<double2>(), (const double2 *)sb.dev));
+    dlz_defl_s *d = nullptr;
+    const int rc = gmresdr64(op, bi.as<double2>(), xi.as<double2>(), *p, defl_out ? &d : nullptr, st);
+    if (rc != DLZ_OK && rc != DLZ_ERR_NOT_CONVERGED) {
+        delete d;
+        return rc;
+    }
+    DLZ_TRY(unpack64(op, (double2 *)sx.dev, xi.as<double2>()));
+    DLZ_TRY(sx.flush(op));
+    if (defl_out) *defl_out = d;
+    cs.finish(st);
+    if (stats) *stats = st;
+    if (rc == DLZ_ERR_NOT_CONVERGED) set_error(rc, "max_cycles reached");
+    return rc;
+}
+
+int dlz_dgmres(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nrhs, const dlz_params *p, dlz_stats *stats) {
+    DLZ_TRY(check_op(h));
+    DLZ_TRY(check_params(p));
+    if (p->precision != DLZ_F64) return fail(DLZ_ERR_BADARG, "D-GMRES is built in FP64 (precision DLZ_F64)");
+    if (nrhs < 0) return fail(DLZ_ERR_BADARG, "nrhs < 0");
+    if (nrhs == 0) return DLZ_OK;
+    if (!B || !X) return fail(DLZ_ERR_BADARG, "null vector");
+    Op &op = h->op;
+    if (d && (d->op != &op || d->which != DLZ_D))
+        return fail(DLZ_ERR_BADARG, "D-GMRES needs a GMRES-DR deflation set of this operator");
+    const long n = 12L * op.g.V;
+    Staged sb, sx;
+    DLZ_TRY(sb.in(op, B, (size_t)n * nrhs * sizeof(double2)));
+    DLZ_TRY(sx.out(op, X, (size_t)n * nrhs * sizeof(double2)));
+    DevBuf bi, xi;
+    DLZ_TRY(bi.alloc(n * sizeof(double2)));
+    DLZ_TRY(xi.alloc(n * sizeof(double2)));
+    int worst = DLZ_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        dlz_stats st;
+        std::memset(&st, 0, sizeof(st));
+        CallStats cs(op, nullptr, p->profile != 0, false);
+        DLZ_TRY(pack64(op, bi.as<double2>(), (const double2 *)sb.dev + (size_t)r * n));
+        const int rc = dgmres64(op, d, bi.as<double2>(), xi.as<double2>(), *p, st);
+        if (rc != DLZ_OK && rc != DLZ_ERR_NOT_CONVERGED) return rc;
+        if (rc != DLZ_OK) worst = rc;
+        DLZ_TRY(unpack64(op, (double2 *)sx.dev + (size_t)r * n, xi.as<double2>()));
+        DLZ_CUDA_TRY(cudaStreamSynchronize(op.stream));
+        cs.finish(st);
+        if (stats) stats[r] = st;
+    }
+    DLZ_TRY(sx.flush(op));
+    if (worst != DLZ_OK) set_error(worst, "max_iter reached for at least one right-hand side");
+    return worst;
+}
+
+int dlz_defl_value_complex(dlz_defl_t d, int i, double *re, double *im) {
+    if (!d) return fail(DLZ_ERR_BADARG, "null deflation set");
+    if (i < 0 || i >= d->k) return fail(DLZ_ERR_BADARG, "index out of range");
+    const std::complex<double> v = d->which == DLZ_D ? d->theta[i] : std::complex<double>(d->values[i], 0.0);
+    if (re) *re = v.real();
+    if (im) *im = v.imag();
+    return DLZ_OK;
+}
+
 int dlz_defl_count(dlz_defl_t d, int *k, int *which) {
     if (!d) return fail(DLZ_ERR_BADARG, "null deflation set");
     if (k) *k = d->k;
@@ -849,6 +927,37 @@ int dlz_defl_count(dlz_defl_t d, int *k, int *which) {
 int dlz_defl_get(dlz_defl_t d, int i, void *vec_out, double *value, double *residual) {
     if (!d) return fail(DLZ_ERR_BADARG, "null deflation set");
     if (i < 0 || i >= d->k) return fail(DLZ_ERR_BADARG, "index out of range");
+    if (d->which == DLZ_D) {
+        // GMRES-DR set: harmonic Ritz pair i (value: Re theta; dlz_defl_value_complex for theta)
+        Op &op = *d->op;
+        if (value) *value = d->theta[i].real();
+        if (residual) {
+            DLZ_TRY(gmres_deflation_residuals(op, d));
+            *residual = d->residuals[i];
+        }
+        if (!vec_out) return DLZ_OK;
+        const long n = 12L * op.g.V;
+        const int k = d->k;
+        DevBuf y, coef, nrm;
+        DLZ_TRY(y.alloc(n * sizeof(double2)));
+        DLZ_TRY(coef.alloc((size_t)(k + 1) * sizeof(double2)));
+        DLZ_TRY(nrm.alloc(sizeof(double)));
+        std::vector<double2> z(k + 1);
+        for (int a = 0; a <= k; ++a) z[a] = make_double2(d->Z[(size_t)a * k + i].real(), d->Z[(size_t)a * k + i].imag());
+        DLZ_CUDA_TRY(cudaMemcpyAsync(coef.p, z.data(), (k + 1) * sizeof(double2), cudaMemcpyHostToDevice, op.stream));
+        DLZ_TRY(combine64(op, y.as<double2>(), n, 1, d->V64.as<double2>(), n, k + 1, coef.p, 1, false, false));
+        DLZ_TRY(v64::norm2_diff(op, y.as<double2>(), nullptr, nrm.as<double>()));
+        double2 *py = y.as<double2>();
+        const double *pn = nrm.as<double>();
+        DLZ_TRY(map(op, n, [=] __device__(long j) {
+            const double s = 1.0 / sqrt(*pn);
+            py[j] = make_double2(s * py[j].x, s * py[j].y);
+        }));
+        Staged so;
+        DLZ_TRY(so.out(op, vec_out, n * sizeof(double2)));
+        DLZ_TRY(unpack64(op, (double2 *)so.dev, y.as<double2>()));
+        return so.flush(op);
+    }
     if (value) *value = d->values[i];
     if (residual) {
         DLZ_TRY(deflation_residuals(*d->op, d));
@@ -885,6 +994,7 @@ struct FileHeader {
 
 int dlz_defl_save(dlz_defl_t d, const char *path) {
     if (!d || !path) return fail(DLZ_ERR_BADARG, "null argument");
+    if (d->which == DLZ_D) return fail(DLZ_ERR_BADARG, "GMRES-DR deflation sets are not saved to files");
     Op &op = *d->op;
     const long n = 12L * op.g.V;
     FileHeader hd;

@@ -34,5 +34,14 @@ bool lu_factor(int n, std::complex<double> *A, int *piv);
 void lu_solve(int n, const std::complex<double> *LU, const int *piv, std::complex<double> *b);
 // Orthonormalise the columns of P (rows x cols) left to right, MGS twice.
 bool mgs_columns(int rows, int cols, double *P);
+// Complex helpers (small_dense_z.cpp).  zgeev: eigenvalues w[n] and unit eigenvectors
+// (column j of Z, may be null) of a general complex A (n x n); false on non-finite input
+// or no convergence.  zlstsq: y = argmin ||c - A y|| (rows > cols) and, if rows ==
+// cols + 1 and q is not null, the unit vector q spanning range(A)^perp.  zmgs_columns:
+// MGS twice on the columns of P (rows x cols); false on a zero column.
+bool zgeev(int n, const std::complex<double> *A, std::complex<double> *w, std::complex<double> *Z);
+bool zlstsq(int rows, int cols, const std::complex<double> *A, const std::complex<double> *c,
+            std::complex<double> *y, std::complex<double> *q);
+bool zmgs_columns(int rows, int cols, std::complex<double> *P);
 
 }  // namespace dlz

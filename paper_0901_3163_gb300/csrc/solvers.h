@@ -21,7 +21,12 @@ struct dlz_defl_s {
     std::vector<int> piv;
     std::vector<double> values;                 // Rayleigh-Ritz values (ascending)
     std::vector<double> residuals;              // ||A y - value y|| (empty until requested)
-    std::vector<std::complex<double>> Z;        // eigenvectors of H (column j <-> values[j])
+    std::vector<std::complex<double>> Z;        // eigenvectors of H (column j <-> values[j]); GMRES-DR
+                                                // sets: (k+1) x k coefficients of the harmonic Ritz
+                                                // vectors in V_{k+1}
+    // GMRES-DR sets (which == DLZ_D): V64 holds k + 1 vectors with D V_k = V_{k+1} Hbar
+    std::vector<std::complex<double>> Hbar;     // (k+1) x k, row-major
+    std::vector<std::complex<double>> theta;    // the kept harmonic Ritz values
 };
 
 // The operator object behind dlz_op_t.
@@ -68,6 +73,10 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
 // st: one entry per (lattice, right-hand side) in order.
 int dminres_multi(int nlat, Op *const *ops, const dlz_defl_s *const *defls, const double2 *const *B,
                   double2 *const *X, const int *nrhs, const dlz_params &p, dlz_stats *st);
+// GMRES-DR(m,k) and D-GMRES(m) on D, FP64 (gmres.cu); d may be null (plain GMRES(m)).
+int gmresdr64(Op &op, const double2 *b, double2 *x, const dlz_params &p, dlz_defl_s **defl_out, dlz_stats &st);
+int dgmres64(Op &op, const dlz_defl_s *d, const double2 *b, double2 *x, const dlz_params &p, dlz_stats &st);
+int gmres_deflation_residuals(Op &op, dlz_defl_s *d);
 // FP32 copy of the deflation basis (made on first use).
 int deflation_v32(Op &op, dlz_defl_s *d);
 int deflation_finish(Op &op, dlz_defl_s *d);

@@ -34,6 +34,7 @@ namespace {
 constexpr int kTcThreads = 256;     // 8 warps: staging, epilogue (two per TMEM lane quarter)
 constexpr int kKC = 32;             // K chunk staged per pipeline stage
 constexpr long long kWaitPolls = 1LL << 26;
+constexpr int kTcMaxSmem = 2 * (2 * 128 * kKC * 4 + 2 * 256 * kKC * 4);   // 192 KB
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -430,11 +431,13 @@ int check_err(TcScratch &sc, cudaStream_t st) {
 }  // namespace
 
 int tc_prepare() {
-    // dynamic shared memory beyond 48 KB (set once, outside any graph capture)
+    // dynamic shared memory beyond 48 KB (set once, outside any graph capture): at most
+    // two stages of 2 x 16 KB (A) + 2 x 32 KB (B, npad = 256) = 192 KB; the opt-in limit
+    // (227 KB) also covers the kernels' static shared memory
     static int done = 0;
     if (done) return DLZ_OK;
-    DLZ_CUDA_TRY(cudaFuncSetAttribute(k_tc_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    DLZ_CUDA_TRY(cudaFuncSetAttribute(k_tc_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    DLZ_CUDA_TRY(cudaFuncSetAttribute(k_tc_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem));
+    DLZ_CUDA_TRY(cudaFuncSetAttribute(k_tc_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem));
     done = 1;
     return DLZ_OK;
 }

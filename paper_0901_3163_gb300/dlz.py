@@ -93,6 +93,9 @@ _SIGS = {
                       ctypes.POINTER(Stats)], _ip),
     "dlz_dcg": ([_vp, _vp, _vp, _vp, _ip, ctypes.POINTER(Params), ctypes.POINTER(Stats)], _ip),
     "dlz_dminres": ([_vp, _vp, _vp, _vp, _ip, ctypes.POINTER(Params), ctypes.POINTER(Stats)], _ip),
+    "dlz_gmresdr": ([_vp, _vp, _vp, ctypes.POINTER(Params), ctypes.POINTER(_vp), ctypes.POINTER(Stats)], _ip),
+    "dlz_dgmres": ([_vp, _vp, _vp, _vp, _ip, ctypes.POINTER(Params), ctypes.POINTER(Stats)], _ip),
+    "dlz_defl_value_complex": ([_vp, _ip, _dp, _dp], _ip),
     "dlz_defl_count": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], _ip),
     "dlz_defl_get": ([_vp, _ip, _vp, _dp, _dp], _ip),
     "dlz_defl_save": ([_vp, ctypes.c_char_p], _ip),
@@ -117,6 +120,8 @@ _SIGS = {
     "dlz_host_symeig": ([_ip, _vp, _vp, _vp], _ip),
     "dlz_host_sym_extremes": ([_ip, _vp, _vp, _vp], _ip),
     "dlz_host_lstsq": ([_ip, _ip, _vp, _vp, _vp, _vp], _ip),
+    "dlz_host_zgeev": ([_ip, _vp, _vp, _vp], _ip),
+    "dlz_host_zlstsq": ([_ip, _ip, _vp, _vp, _vp, _vp], _ip),
     "dlz_host_restart_plan": ([_ip, _ip, _ip, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _ip),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -307,6 +312,23 @@ def _dsolve(fn, op, defl, B, params, X):
     _check(fn(op.handle, defl.handle if defl is not None else None, _ptr(B), _ptr(X), nrhs,
               ctypes.byref(p), st), allow=(ERR_NOT_CONVERGED,))
     return X, [st[i] for i in range(nrhs)]
+
+
+def gmresdr(op, b, params=None, x=None, deflate=True):
+    """GMRES-DR(m,k) on D for D x = b (FP64): returns (x, Deflation, Stats)."""
+    return _dr(lib.dlz_gmresdr, op, b, params, x, deflate)
+
+
+def dgmres(op, defl, B, params=None, X=None):
+    """D-GMRES(m) over a GMRES-DR set (None: plain GMRES(m)); returns (X, [Stats])."""
+    return _dsolve(lib.dlz_dgmres, op, defl, B, params, X)
+
+
+def defl_value_complex(defl, i):
+    """The i-th value of a deflation set as a complex number (GMRES-DR: theta_i)."""
+    re, im = ctypes.c_double(), ctypes.c_double()
+    _check(lib.dlz_defl_value_complex(defl.handle, int(i), ctypes.byref(re), ctypes.byref(im)))
+    return complex(re.value, im.value)
 
 
 def dcg(op, defl, B, params=None, X=None):
@@ -563,6 +585,28 @@ def host_restart_plan(T, c, k, harmonic, anorm=0.0):
                                      ctypes.byref(an)))
     out["anorm"] = an.value
     return out
+
+
+def host_zgeev(A):
+    """Eigenvalues and unit eigenvectors of a general complex matrix (library host code)."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    w = np.empty(n, dtype=np.complex128)
+    Z = np.empty((n, n), dtype=np.complex128)
+    _check(lib.dlz_host_zgeev(n, A.ctypes.data, w.ctypes.data, Z.ctypes.data))
+    return w, Z
+
+
+def host_zlstsq(A, c):
+    """argmin ||c - A y|| (complex) and the unit vector spanning range(A)^perp (rows = cols + 1)."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    c = np.ascontiguousarray(c, dtype=np.complex128)
+    rows, cols = A.shape
+    y = np.empty(cols, dtype=np.complex128)
+    q = np.empty(rows, dtype=np.complex128)
+    _check(lib.dlz_host_zlstsq(rows, cols, A.ctypes.data, c.ctypes.data, y.ctypes.data,
+                               q.ctypes.data if rows == cols + 1 else None))
+    return y, (q if rows == cols + 1 else None)
 
 
 def host_lstsq(T, c):

@@ -358,3 +358,12 @@ def test_landr_past_convergence_keeps_an_orthonormal_positive_kept_space():
     assert np.abs(G - np.eye(10)).max() <= 1e-13
     exact = np.linalg.eigvalsh(wilson.dense(A, 3072))[:10]
     assert np.allclose(np.sort(r.ritz_values), exact, rtol=1e-8)
+
+
+def test_landr_refuses_a_reorthogonalisation_period_it_would_not_honour():
+    d = synth.diag_hpd_1000()
+    b = np.ones(1000, dtype=complex) / np.sqrt(1000)
+    with pytest.raises(ValueError):
+        K.landr(_diag_op(d), b, m=20, k=5, reorth_period=10, max_cycles=1)
+    r = K.landr(_diag_op(d), b, m=20, k=5, reorth_period=0, max_cycles=1)   # off is allowed
+    assert r.cycles == 1
