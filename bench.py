@@ -319,7 +319,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e,
         "gpu_launches": int(launches), "gpu_launches_per_step": int(launches // max(args.steps, 1)),
-        "library_kernels": "cuBLAS SGEMM for the restart V P (3 kernels per restart, not counted above)",
+        "library_kernels": "none: the restart V P and the projections run on the library's own tcgen05 kernels (counted above)",
         "mvps_per_step": int(mvps), "iterations_first_steps": [s.iterations for s in stats[:4]],
         "phase_seconds": {"first_rhs_dr": round(dr_s, 4), "deflated_48_rhs": round(d_s, 4)},
         "d_phase_rhs_per_s": round((nrhs - 1) / d_s, 4) if d_s > 0 else None,
@@ -515,6 +515,8 @@ def run_c4(dlz, torch, nl=64):
     t_batch = time.perf_counter() - ta
     clk = clocks.stop()
     ok_batch = sum(1 for ss in sts for s in ss if s.converged == 1 and s.true_residual <= 1e-10)
+    form, chunks, half = dlz.batch_last_choice(ops[0])
+    choice = {"form": "persistent" if form == 1 else "graph", "chunks_per_block": chunks, "half_grid": bool(half)}
     ta = time.perf_counter()
     ok_seq = 0
     for o, d, B in zip(ops, defls, Bs):
@@ -543,7 +545,7 @@ def run_c4(dlz, torch, nl=64):
            "lattices": nl, "sites_total": int(sites), "rhs_total": int(sum(len(ss) for ss in sts)),
            "first_rhs_dr_seconds": round(dr_s, 3),
            "batched": {"seconds": round(t_batch, 3), "rhs_per_s": round(ok_batch / t_batch, 2), "solved": ok_batch,
-                       "iterations_max": int(max(iters))},
+                       "iterations_max": int(max(iters)), "autotuner_choice": choice},
            "lattice_by_lattice_f32": {"seconds": round(t_seq, 3), "rhs_per_s": round(ok_seq / t_seq, 2),
                                       "solved": ok_seq},
            "plain_fp64": {"sample": "one lattice of each size, 8 RHS each, one RHS at a time; extrapolated "
@@ -888,7 +890,7 @@ def run_gmresdr(args):
     op = dlz.create_operator(dims, torch.from_numpy(synth.su3_links(dims, 3000)).cuda(), kappa)
     b0 = torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda()
     B = torch.from_numpy(synth.gaussian_spinors(dims, (1, 2, 3, 4))).cuda()
-    m, k = 40, 10
+    m, k = args.gm_m, args.gm_k
     out = {"mode": "gmresdr", "lattice": list(dims), "kappa": kappa, "m": m, "k": k}
     for name, dr, ds in (("gmresdr_dgmres", dlz.gmresdr, dlz.dgmres), ("minresdr_dminres", dlz.minresdr, dlz.dminres)):
         p = dlz.params_default(m=m, k=k, tol=1e-10, max_cycles=2000, max_iter=200000)
@@ -947,6 +949,8 @@ def main():
     ap.add_argument("--multi-lattice", action="store_true")
     ap.add_argument("--saturation", action="store_true")
     ap.add_argument("--gmresdr", action="store_true")
+    ap.add_argument("--gm-m", type=int, default=40)
+    ap.add_argument("--gm-k", type=int, default=10)
     ap.add_argument("--sat-k", type=int, nargs="+", default=[20, 60, 100, 150])
     ap.add_argument("--ls-train", type=int, default=32)
     ap.add_argument("--ls-test", type=int, default=8)

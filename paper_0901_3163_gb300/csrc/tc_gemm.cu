@@ -151,6 +151,25 @@ __device__ __forceinline__ void tc_teardown(uint32_t taddr, int ncols) {
 
 __device__ __forceinline__ int tmem_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : 256; }
 
+// The combine's A operand for one thread: vectors 4 kq .. 4 kq + 3 of K chunk kc at rows
+// r .. r + 3 (zero beyond the data; for complex coefficients the second half of K holds
+// i times the vectors)
+__device__ __forceinline__ void combine_load_a(const CombineArgs &a, int kc, int kq, long r, float4 (&v)[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int k = kc * kKC + 4 * kq + j;
+        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < a.rows) {
+            if (k < a.nin) {
+                v[j] = *reinterpret_cast<const float4 *>(a.V + (size_t)k * a.ldv + r);
+            } else if (a.cplx && k < 2 * a.nin) {
+                const float4 u = *reinterpret_cast<const float4 *>(a.V + (size_t)(k - a.nin) * a.ldv + r);
+                v[j] = make_float4(-u.y, u.x, -u.w, u.z);        // i times the complex pairs
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_combine(CombineArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int a_bytes = 128 * kKC * 4, b_bytes = a.npad * kKC * 4;
@@ -167,6 +186,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_combine(CombineArgs a) {
     const int nkc = a.kpad / kKC;
     const uint32_t idesc = idesc_tf32(a.npad, 0u);
     StageSync ss;
+    // A chunk: 128 rows x 32 k, K-major.  Thread (row quad rq, k quad kq) loads the four
+    // vectors 4 kq .. 4 kq + 3 at rows 4 rq .. 4 rq + 3 (float4 each, 64 contiguous bytes
+    // per vector across the 4 lanes of equal kq), transposes the 4 x 4 block and stores
+    // one 16-byte k quad per row; lane l stores its rows in the order (c + l % 4) so that
+    // the eight lanes of a store instruction with equal row parity hit different banks.
+    // The loads of the next chunk (or of the next tile's first chunk) are issued right
+    // after the current chunk's MMAs, so they are in flight during the MMAs, the next
+    // stage's wait and the epilogue.
+    const int kq = tid & 7, rq = tid >> 3;                                    // 8 k quads x 32 row quads
+    float4 v[4];
+    if ((long)blockIdx.x < ntiles) combine_load_a(a, 0, kq, (long)blockIdx.x * 128 + 4 * rq, v);
     for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const long r0 = t * 128;
         for (int kc = 0; kc < nkc; ++kc) {
@@ -178,29 +208,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_combine(CombineArgs a) {
             if (!ss.drain(mbar, st) && tid == 0) fail_s = 1;
             __syncthreads();
             if (fail_s) break;
-            // A chunk: 128 rows x 32 k, K-major.  Thread (row quad rq, k quad kq) loads the
-            // four vectors 4 kq .. 4 kq + 3 at rows 4 rq .. 4 rq + 3 (float4 each, 64
-            // contiguous bytes per vector across the 4 lanes of equal kq), transposes the
-            // 4 x 4 block and stores one 16-byte k quad per row; lane l stores its rows in
-            // the order (c + l % 4) so that the eight lanes of a store instruction with
-            // equal row parity hit different banks
             {
-                const int kq = tid & 7, rq = tid >> 3;                        // 8 k quads x 32 row quads
-                const long r = r0 + 4 * rq;
-                float4 v[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int k = kc * kKC + 4 * kq + j;
-                    v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (r < a.rows) {
-                        if (k < a.nin) {
-                            v[j] = *reinterpret_cast<const float4 *>(a.V + (size_t)k * a.ldv + r);
-                        } else if (a.cplx && k < 2 * a.nin) {
-                            const float4 u = *reinterpret_cast<const float4 *>(a.V + (size_t)(k - a.nin) * a.ldv + r);
-                            v[j] = make_float4(-u.y, u.x, -u.w, u.z);        // i times the complex pairs
-                        }
-                    }
-                }
                 const int rot = tid & 3;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -239,6 +247,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_combine(CombineArgs a) {
                 commit_to(&mbar[st]);
             }
             ++ss.issued[st];
+            if (kc + 1 < nkc) combine_load_a(a, kc + 1, kq, r0 + 4 * rq, v);
+            else if (t + gridDim.x < ntiles) combine_load_a(a, 0, kq, (t + gridDim.x) * 128 + 4 * rq, v);
         }
         // epilogue: every MMA of the tile complete, then each warp reads its lane quarter
         // and half of the columns
@@ -287,6 +297,29 @@ struct DotsArgs {
 };
 constexpr int kSegChunks = 64;      // 64 chunks of 32 floats per segment
 
+// The dots' operands of one thread for chunk ch: A items w = tid + 256 i (i < 4; row
+// 8 (w >> 6) + (w & 7), k quad (w >> 3) & 7) and at most one B item w = tid (npad <= 32)
+__device__ __forceinline__ void dots_load(const DotsArgs &a, long ch, int tid, float4 (&va)[4], float4 &vb) {
+    const long k0 = ch * kKC;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int w = tid + kTcThreads * q;
+        const int i = 8 * (w >> 6) + (w & 7), kq = (w >> 3) & 7;
+        va[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < a.nin) va[q] = *reinterpret_cast<const float4 *>(a.V + (size_t)i * a.ldv + k0 + 4 * kq);
+    }
+    vb = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < a.npad * (kKC / 4)) {
+        const int c = 8 * (tid >> 6) + (tid & 7), kq = (tid >> 3) & 7;
+        if (c < a.nq) {
+            vb = *reinterpret_cast<const float4 *>(a.R + (size_t)c * a.ldr + k0 + 4 * kq);
+        } else if (c < 2 * a.nq) {
+            const float4 u = *reinterpret_cast<const float4 *>(a.R + (size_t)(c - a.nq) * a.ldr + k0 + 4 * kq);
+            vb = make_float4(u.y, -u.x, u.w, -u.z);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_dots(DotsArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int a_bytes = 128 * kKC * 4, b_bytes = a.npad * kKC * 4;
@@ -309,6 +342,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_dots(DotsArgs a) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) acc[j] = 0.0;
     StageSync ss;
+    // operands of the next chunk are loaded into registers while the current MMAs run
+    float4 va[4], vb;
+    if ((long)blockIdx.x < nseg) dots_load(a, (long)blockIdx.x * kSegChunks, tid, va, vb);
     for (long sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
         const long ch0 = sg * kSegChunks, ch1 = min(nchunks, ch0 + kSegChunks);
         for (long ch = ch0; ch < ch1; ++ch) {
@@ -320,27 +356,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_dots(DotsArgs a) {
             if (!ss.drain(mbar, st) && tid == 0) fail_s = 1;
             __syncthreads();
             if (fail_s) break;
-            const long k0 = ch * kKC;
             // A chunk: 128 rows x 32 k, K-major; a warp instruction covers 8 rows x 4 k quads
-            for (int w = tid; w < 128 * (kKC / 4); w += kTcThreads) {
-                const int i8 = w & 7, kq = (w >> 3) & 7, ig = w >> 6;       // row i = 8 ig + i8
-                const int i = 8 * ig + i8;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < a.nin) v = *reinterpret_cast<const float4 *>(a.V + (size_t)i * a.ldv + k0 + 4 * kq);
-                st_split(Ahi, Alo, ig * 256 + kq * 32 + i8 * 4, v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int w = tid + kTcThreads * q;
+                st_split(Ahi, Alo, (w >> 6) * 256 + ((w >> 3) & 7) * 32 + (w & 7) * 4, va[q]);
             }
-            for (int w = tid; w < a.npad * (kKC / 4); w += kTcThreads) {
-                const int c8 = w & 7, kq = (w >> 3) & 7, cg = w >> 6;       // row c = 8 cg + c8
-                const int c = 8 * cg + c8;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (c < a.nq) {
-                    v = *reinterpret_cast<const float4 *>(a.R + (size_t)c * a.ldr + k0 + 4 * kq);
-                } else if (c < 2 * a.nq) {
-                    const float4 u = *reinterpret_cast<const float4 *>(a.R + (size_t)(c - a.nq) * a.ldr + k0 + 4 * kq);
-                    v = make_float4(u.y, -u.x, u.w, -u.z);
-                }
-                st_split(Bhi, Blo, cg * 256 + kq * 32 + c8 * 4, v);
-            }
+            if (tid < a.npad * (kKC / 4))
+                st_split(Bhi, Blo, (tid >> 6) * 256 + ((tid >> 3) & 7) * 32 + (tid & 7) * 4, vb);
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
             if (tid == 0) {
@@ -358,6 +381,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_dots(DotsArgs a) {
                 commit_to(&mbar[st]);
             }
             ++ss.issued[st];
+            if (ch + 1 < ch1) dots_load(a, ch + 1, tid, va, vb);
+            else if (sg + gridDim.x < nseg) dots_load(a, (sg + gridDim.x) * kSegChunks, tid, va, vb);
         }
         if (fail_s) break;
         bool okd = ss.drain(mbar, 0);
