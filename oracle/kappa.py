@@ -103,8 +103,11 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5,
     MinRes-DR(100, 20) run as an eigensolver and warm-started from the previous
     eigenvector.  From `start` kappa is stepped by `step` (down while
     sigma_min < 1e-3, then up) to bracket the crossing, which is refined by
-    Illinois false position to |sigma_min/1e-3 - 1| < rtol, and re-evaluated
-    there.  Each eigensolve stops at a harmonic Ritz residual below
+    Illinois false position to |sigma_min/1e-3 - 1| < rtol; the returned
+    sigma_min and residual are those of the evaluation that met the tolerance
+    (a fresh warm-started evaluation at the same kappa may stop after a cycle or
+    two on an early harmonic Ritz value).  Each eigensolve stops at a harmonic Ritz
+    residual below
     max(res_tol, 5% of |sigma - 1e-3|) or after max_cycles restart cycles
     (the nearest-zero harmonic Ritz value of a capped run is then the
     estimate used).  Returns (kappa, sigma_min, residual of that estimate).
@@ -122,6 +125,7 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5,
         s, y, res, mv = sigma_min_iterative(U, kap, dims, state["v"], stop, bc_t=bc_t, log=log,
                                             max_cycles=max_cycles)
         state["res"] = res
+        state["sigma"] = s
         state["v"] = y + 1e-3 * (rng.standard_normal(V * 12) + 1j * rng.standard_normal(V * 12)) / np.sqrt(V * 12)
         if log:
             log(f"kappa={kap:.10f} sigma_min={s:.10e} res={res:.2e} mvps={mv}")
@@ -139,7 +143,7 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5,
         b = a + step
         fb = f(b)
     kap = _illinois(f, a, fa, b, fb, rtol)
-    return kap, f(kap, res_tol) + TARGET, state["res"]
+    return kap, state["sigma"], state["res"]
 
 
 def kappa_newton(U, dims, a, sa, b, sb, bc_t=1, rtol=1e-4, m=100, k=20, max_cycles=150,
