@@ -44,13 +44,13 @@ C4 = "uneven_64"
 # restart cycles of the 16^3x32 first right-hand side's MinRes-DR phase (both forms)
 C2_DR_CYCLES = 150
 # D-CG iterations per right-hand side of the FP64 form on the 24^3x48 workload, and
-# the MVPs of its first right-hand side (FP64 Lan-DR(120,60) with its D-CG finish):
-# the oracle runs the same FP64 algorithm but cannot finish this lattice in a bounded
-# sample, so the reference arm extrapolates its seconds per iteration with these counts
-# (taken from an FP64 run of the library on this workload; bench.py reports the counts
-# of its own FP64 run in plain_fp64)
-REF_ITERS_PER_RHS = 4400
-REF_FIRST_RHS_MVPS = 10000
+# the MVPs of its first right-hand side (FP64 Lan-DR(120,60) to its stopping rule, 217
+# cycles): the oracle runs the same FP64 algorithm but cannot finish this lattice in a
+# bounded sample, so the reference arm extrapolates its seconds per iteration with these
+# counts (taken from an FP64 run of the library on this workload; the default line
+# reports the counts of its own FP64 run in plain_fp64)
+REF_ITERS_PER_RHS = 2384
+REF_FIRST_RHS_MVPS = 26378
 # DRAM bytes (read + write) of one k_cg_k23 launch (16 RHS, 24^3x48) from the ncu
 # capture summarised in profiles/k_cg_k23_wilson_24x24x24x48_n16.md; None until taken
 # for the current kernel
@@ -689,7 +689,8 @@ def run_stencil_only(args):
 def run_ncu_case(args):
     """A short run of the benchmark's kernels for ncu captures.  cg (cg-eo): 48 fused
     FP32 CGNR iterations (full or even-odd operator) on 16 Gaussian RHS of the 16^3x32
-    lattice, the launch shape of the 24^3x48 step on ~3 GB of device memory.  minres: the 16^3x32 operator, MinRes-DR(100,40) for 2 cycles, then
+    lattice, the launch shape of the 24^3x48 step on ~3 GB of device memory; cg24: the
+    same on the 24^3x48 lattice (~7 GB).  minres: the 16^3x32 operator, MinRes-DR(100,40) for 2 cycles, then
     48 FP32 D-MinRes iterations on the 11 point sources.  ptc: one forward and
     backward of the learned-seed network on 16^4.  Prints the stats."""
     import torch
@@ -709,11 +710,15 @@ def run_ncu_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"mode": "ncu-case", "case": "ptc"}))
         return
-    if args.ncu_case in ("cg", "cg-eo"):
-        # the fused CGNR kernels as the 24^3x48 step launches them (16 RHS per launch), on
-        # the 16^3x32 lattice so that the device holds ~3 GB: FP32 CG on the normal
-        # equations without deflation, 48 iterations (inputs larger than L2)
-        w2, dims, U, kappa, _ = workload_inputs(name=C2)
+    if args.ncu_case in ("cg", "cg-eo", "cg24"):
+        # the fused CGNR kernels as the 24^3x48 step launches them (16 RHS per launch): on
+        # the 16^3x32 lattice so that the device holds ~3 GB (cg, cg-eo), or on the
+        # 24^3x48 lattice itself (cg24, ~7 GB); FP32 CG on the normal equations without
+        # deflation, 48 iterations (inputs larger than L2)
+        if args.ncu_case == "cg24":
+            w2, dims, U, kappa, _ = workload_inputs(args.kappa)
+        else:
+            w2, dims, U, kappa, _ = workload_inputs(name=C2)
         mk = dlz.create_operator_eo if args.ncu_case == "cg-eo" else dlz.create_operator
         op = mk(dims, torch.from_numpy(U).cuda(), kappa)
         B = synth.gaussian_spinors(dims, list(range(1, 17)))
@@ -944,7 +949,8 @@ def main():
     ap.add_argument("--lattice", default=None)
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--stencil-iters", type=int, default=50)
-    ap.add_argument("--ncu-case", nargs="?", const="minres", default=None, choices=["minres", "cg", "cg-eo", "ptc"])
+    ap.add_argument("--ncu-case", nargs="?", const="minres", default=None,
+                    choices=["minres", "cg", "cg-eo", "cg24", "ptc"])
     ap.add_argument("--learned-seed", action="store_true")
     ap.add_argument("--multi-lattice", action="store_true")
     ap.add_argument("--saturation", action="store_true")

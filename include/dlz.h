@@ -284,8 +284,12 @@ int dlz_minresdr(dlz_op_t op, const void *b, void *x, const dlz_params *p,
  * [nrhs][V][4][3]) the Galerkin projection x0 = V_k H^-1 V_k^dag D^dag b over
  * the deflation set, then CG on D^dagger D x = D^dagger b, stopping on the
  * FP64-verified ||b - D x|| / ||b|| <= tol.  defl may be NULL (plain CG on
- * the normal equations).  stats: array of nrhs entries or NULL.  Returns
- * DLZ_ERR_NOT_CONVERGED if any right-hand side missed tol within max_iter.
+ * the normal equations).  stats: array of nrhs entries or NULL.  In DLZ_F32
+ * the right-hand sides are solved in batches of up to 16; the time, launch and
+ * profile fields of a batch's entries are the batch's totals shared out over
+ * its right-hand sides (counts split so that they add up to the totals), while
+ * converged, iterations, mvps and true_residual are each right-hand side's own.
+ * Returns DLZ_ERR_NOT_CONVERGED if any right-hand side missed tol within max_iter.
  */
 int dlz_dcg(dlz_op_t op, dlz_defl_t defl, const void *B, void *X, int nrhs,
             const dlz_params *p, dlz_stats *stats);

@@ -367,7 +367,10 @@ int dlz_create_operator(const int dims[4], const void *gauge, double kappa, int 
     if (rc) return bail(rc);
     rc = op.gauge32.alloc((size_t)12 * V * sizeof(float4));
     if (rc) return bail(rc);
-    rc = op.red_mem.alloc((kMaxDots * kRedBlocks + kMaxDots + 8) * sizeof(double));
+    rc = op.stage_err.alloc(sizeof(int));
+    if (rc == DLZ_OK && cudaMemsetAsync(op.stage_err.p, 0, sizeof(int), op.stream) != cudaSuccess)
+        rc = fail(DLZ_ERR_CUDA, "memset");
+    if (rc == DLZ_OK) rc = op.red_mem.alloc((kMaxDots * kRedBlocks + kMaxDots + 8) * sizeof(double));
     if (rc) return bail(rc);
     op.red.partials = op.red_mem.as<double>();
     op.red.result = op.red.partials + kMaxDots * kRedBlocks;
@@ -789,16 +792,19 @@ static int dsolve_entry(dlz_op_t h, dlz_defl_t d, const void *B, void *X, int nr
             dlz_stats shared;
             std::memset(&shared, 0, sizeof(shared));
             cs.finish(shared);
+            // the batch's totals shared out over its right-hand sides; counts are split
+            // so that they add up to the batch's counts exactly
+            auto share = [nb](long long total, int q) { return total / nb + (q < total % nb ? 1 : 0); };
             for (int q = 0; q < nb; ++q) {
                 sts[q].seconds = shared.seconds / nb;
-                sts[q].gpu_launches = shared.gpu_launches / nb;
+                sts[q].gpu_launches = share(shared.gpu_launches, q);
                 sts[q].stencil_ms = shared.stencil_ms / nb;
-                sts[q].stencil_launches = shared.stencil_launches / nb;
+                sts[q].stencil_launches = share(shared.stencil_launches, q);
                 sts[q].stencil_bytes = shared.stencil_bytes / nb;
                 for (int t = 0; t < 3; ++t) {
                     sts[q].kernel_ms[t] = shared.kernel_ms[t] / nb;
                     sts[q].kernel_bytes[t] = shared.kernel_bytes[t] / nb;
-                    sts[q].kernel_launches[t] = shared.kernel_launches[t] / nb;
+                    sts[q].kernel_launches[t] = share(shared.kernel_launches[t], q);
                 }
                 if (stats) stats[r0 + q] = sts[q];
             }

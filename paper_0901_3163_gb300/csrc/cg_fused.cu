@@ -25,7 +25,9 @@
 #include "dlz_internal.cuh"
 #include "krylov_util.cuh"
 #include "reduce.cuh"
+#include "slab_walk.cuh"
 #include "solvers.h"
+#include "stage_gather.cuh"
 #include "wilson_eo_site.cuh"
 #include "wilson_site.cuh"
 
@@ -88,29 +90,39 @@ __device__ inline void axpy_store(float4 *__restrict__ P, size_t base, int V, in
 }
 
 // K1: t = D r + beta t, p = r + beta p; partial |t|^2.  Gathers r only.
-__global__ void __launch_bounds__(kT, 6)
+template <bool STAGED>
+__global__ void __launch_bounds__(kT, STAGED ? 3 : 6)
 k_cg_k1(const float4 *__restrict__ R, float4 *__restrict__ P, float4 *__restrict__ T,
-        const float4 *__restrict__ links, Geom g, float kappa, int N, const CgFusedState *__restrict__ st,
-        double *__restrict__ partials) {
+        const float4 *__restrict__ links, Geom g, SlabWalk w, float kappa, int N, const CgFusedState *__restrict__ st,
+        double *__restrict__ partials, int *__restrict__ err) {
+    extern __shared__ __align__(128) float4 stage_sm[];
+    __shared__ __align__(8) uint64_t mbar;
     const int q = blockIdx.x % N;
-    const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
+    int s0, nb;
+    slab_block(w, blockIdx.x / N, s0, nb);
+    const int s = s0 + threadIdx.x;
     const size_t base = (size_t)q * 6 * g.V;
-    if (threadIdx.x == 0) {
-        const int s0 = (blockIdx.x / N) * blockDim.x, nb = min((int)blockDim.x, g.V - s0);
-        prefetch_planes_l2(R + base, 6, g.V, s0, nb);
+    if (threadIdx.x == 0 && nb > 0) {
+        if (!STAGED) prefetch_planes_l2(R + base, 6, g.V, s0, nb);
         prefetch_planes_l2(T + base, 6, g.V, s0, nb);
         prefetch_planes_l2(P + base, 6, g.V, s0, nb);
         if (q == 0) prefetch_planes_l2(links, 12, g.V, s0, nb);
     }
+    const bool ok = stage_begin<STAGED>(R + base, g, s0, nb, stage_sm, &mbar, err);
     float v[1] = {0.f};
-    if (s < g.V) {
+    if ((int)threadIdx.x < nb && ok) {
         const float bt = st[q].f[1];
-        float2 o[12], t[12];
-        wilson_site<float, false, false>(s, g, kappa, R + base, links, o);
+        float2 o[12], t[12], r[12], pn[12];
+        if constexpr (STAGED) {
+            const StagedGather32 ga = staged_gather(R + base, g, s0, stage_sm);
+            wilson_site_g<float, false, false>(s, g, kappa, ga, links, o);
+            ga.get<0, 0>(s, false, r);
+        } else {
+            wilson_site<float, false, false>(s, g, kappa, R + base, links, o);
+            Field<float>::load(R + base, g.V, s, r);
+        }
         axpy_store(T, base, g.V, s, bt, o, t);
         v[0] = nrm(t);
-        float2 r[12], pn[12];
-        Field<float>::load(R + base, g.V, s, r);
         axpy_store(P, base, g.V, s, bt, r, pn);
     }
     const int nbq = gridDim.x / N;
@@ -118,27 +130,38 @@ k_cg_k1(const float4 *__restrict__ R, float4 *__restrict__ P, float4 *__restrict
 }
 
 // K23: r -= alpha D^dag t, s -= alpha t, e += alpha p; partials |r|^2, |s|^2.  Gathers t only.
-__global__ void __launch_bounds__(kT, 6)
+template <bool STAGED>
+__global__ void __launch_bounds__(kT, STAGED ? 3 : 6)
 k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restrict__ S, const float4 *__restrict__ P,
-         float4 *__restrict__ E, const float4 *__restrict__ links, Geom g, float kappa, int N,
-         const CgFusedState *__restrict__ st, double *__restrict__ partials) {
+         float4 *__restrict__ E, const float4 *__restrict__ links, Geom g, SlabWalk w, float kappa, int N,
+         const CgFusedState *__restrict__ st, double *__restrict__ partials, int *__restrict__ err) {
+    extern __shared__ __align__(128) float4 stage_sm[];
+    __shared__ __align__(8) uint64_t mbar;
     const int q = blockIdx.x % N;
-    const int s = (blockIdx.x / N) * blockDim.x + threadIdx.x;
+    int s0, nb;
+    slab_block(w, blockIdx.x / N, s0, nb);
+    const int s = s0 + threadIdx.x;
     const size_t base = (size_t)q * 6 * g.V;
-    if (threadIdx.x == 0) {
-        const int s0 = (blockIdx.x / N) * blockDim.x, nb = min((int)blockDim.x, g.V - s0);
-        prefetch_planes_l2(T + base, 6, g.V, s0, nb);
+    if (threadIdx.x == 0 && nb > 0) {
+        if (!STAGED) prefetch_planes_l2(T + base, 6, g.V, s0, nb);
         prefetch_planes_l2(R + base, 6, g.V, s0, nb);
         prefetch_planes_l2(S + base, 6, g.V, s0, nb);
         prefetch_planes_l2(P + base, 6, g.V, s0, nb);
         prefetch_planes_l2(E + base, 6, g.V, s0, nb);
         if (q == 0) prefetch_planes_l2(links, 12, g.V, s0, nb);
     }
+    const bool ok = stage_begin<STAGED>(T + base, g, s0, nb, stage_sm, &mbar, err);
     float v[2] = {0.f, 0.f};
-    if (s < g.V) {
+    if ((int)threadIdx.x < nb && ok) {
         const float al = st[q].f[0];
-        float2 z[12];
-        wilson_site<float, true, true>(s, g, kappa, T + base, links, z);
+        float2 z[12], tc[12];
+        if constexpr (STAGED) {
+            const StagedGather32 ga = staged_gather(T + base, g, s0, stage_sm);
+            wilson_site_g<float, true, true>(s, g, kappa, ga, links, z);
+            ga.get<0, 0>(s, false, tc);
+        } else {
+            wilson_site<float, true, true>(s, g, kappa, T + base, links, z);
+        }
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const size_t i = base + (size_t)c * g.V + s;
@@ -148,7 +171,9 @@ k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restric
             r.z = fmaf(-al, z1.x, r.z); r.w = fmaf(-al, z1.y, r.w);
             R[i] = r;
             v[0] += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
-            const float4 t = T[i];
+            float4 t;
+            if constexpr (STAGED) t = make_float4(tc[2 * c].x, tc[2 * c].y, tc[2 * c + 1].x, tc[2 * c + 1].y);
+            else t = T[i];
             float4 sv = S[i];
             sv.x = fmaf(-al, t.x, sv.x); sv.y = fmaf(-al, t.y, sv.y);
             sv.z = fmaf(-al, t.z, sv.z); sv.w = fmaf(-al, t.w, sv.w);
@@ -171,20 +196,21 @@ k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restric
 // K1b: t = Dhat r + beta t = (r - kappa^2 H_eo m) + beta t with m = H_oe r, p = r + beta p.
 __global__ void __launch_bounds__(kT, 6)
 k_cg_eo_k1b(const float4 *__restrict__ R, const float4 *__restrict__ M, float4 *__restrict__ P, float4 *__restrict__ T,
-            const float4 *__restrict__ links, Geom gf, float kappa2, int N, const CgFusedState *__restrict__ st,
-            double *__restrict__ partials) {
+            const float4 *__restrict__ links, Geom gf, SlabWalk w, float kappa2, int N,
+            const CgFusedState *__restrict__ st, double *__restrict__ partials) {
     const int q = blockIdx.x % N;
-    const int cb = (blockIdx.x / N) * blockDim.x + threadIdx.x;
+    int c0, nb;
+    slab_block(w, blockIdx.x / N, c0, nb);
+    const int cb = c0 + threadIdx.x;
     const int Vh = gf.V >> 1;
     const size_t base = (size_t)q * 6 * Vh;
-    if (threadIdx.x == 0) {
-        const int c0 = (blockIdx.x / N) * blockDim.x, nb = min((int)blockDim.x, Vh - c0);
+    if (threadIdx.x == 0 && nb > 0) {
         prefetch_planes_l2(R + base, 6, Vh, c0, nb);
         prefetch_planes_l2(T + base, 6, Vh, c0, nb);
         prefetch_planes_l2(P + base, 6, Vh, c0, nb);
     }
     float v[1] = {0.f};
-    if (cb < Vh) {
+    if ((int)threadIdx.x < nb) {
         const float bt = st[q].f[1];
         float2 o[12], t[12];
         wilson_eo_schur_site<float, false, false>(cb, gf, kappa2, R + base, M + base, links, o);
@@ -203,14 +229,15 @@ k_cg_eo_k1b(const float4 *__restrict__ R, const float4 *__restrict__ M, float4 *
 __global__ void __launch_bounds__(kT, 6)
 k_cg_eo_k23b(const float4 *__restrict__ T, const float4 *__restrict__ M, float4 *__restrict__ R,
              float4 *__restrict__ S, const float4 *__restrict__ P, float4 *__restrict__ E,
-             const float4 *__restrict__ links, Geom gf, float kappa2, int N, const CgFusedState *__restrict__ st,
-             double *__restrict__ partials) {
+             const float4 *__restrict__ links, Geom gf, SlabWalk w, float kappa2, int N,
+             const CgFusedState *__restrict__ st, double *__restrict__ partials) {
     const int q = blockIdx.x % N;
-    const int cb = (blockIdx.x / N) * blockDim.x + threadIdx.x;
+    int c0, nb;
+    slab_block(w, blockIdx.x / N, c0, nb);
+    const int cb = c0 + threadIdx.x;
     const int Vh = gf.V >> 1;
     const size_t base = (size_t)q * 6 * Vh;
-    if (threadIdx.x == 0) {
-        const int c0 = (blockIdx.x / N) * blockDim.x, nb = min((int)blockDim.x, Vh - c0);
+    if (threadIdx.x == 0 && nb > 0) {
         prefetch_planes_l2(T + base, 6, Vh, c0, nb);
         prefetch_planes_l2(R + base, 6, Vh, c0, nb);
         prefetch_planes_l2(S + base, 6, Vh, c0, nb);
@@ -218,7 +245,7 @@ k_cg_eo_k23b(const float4 *__restrict__ T, const float4 *__restrict__ M, float4 
         prefetch_planes_l2(E + base, 6, Vh, c0, nb);
     }
     float v[2] = {0.f, 0.f};
-    if (cb < Vh) {
+    if ((int)threadIdx.x < nb) {
         const float al = st[q].f[0];
         float2 z[12];
         wilson_eo_schur_site<float, true, true>(cb, gf, kappa2, T + base, M + base, links, z);
@@ -291,7 +318,42 @@ __global__ void __launch_bounds__(256) k_cg_beta(const double *__restrict__ part
     }
 }
 
+// The slab walk of the fused kernels for an N-RHS batch (~900 bytes per site and
+// right-hand side: K23's streams); the even-odd kernels walk the even sites
+SlabWalk cg_slab_walk(const Op &op, int N) {
+    const Geom &g = op.eo ? op.gf : op.g;
+    return make_slab_walk(g.L[0] * g.L[1] / (op.eo ? 2 : 1), g.L[2], g.L[3], N, 900.0);
+}
+
+// Whether the full-lattice kernels stage the gathered field in shared memory
+// (DLZ_CG_STAGE=1, when the block's ranges fit).  Off by default: on 24^3 x 48 with 16
+// right-hand sides the staged kernels took 2.17 (K23) and 1.67 ms (K1) per launch against
+// 1.54 and 1.04 ms reading the neighbours from global memory (both in slabs of 4
+// z-planes).  With 66 KB of shared memory per block only 3 blocks fit on an SM (12 warps
+// against 24), and a block computes nothing until all of its copies have landed.
+bool cg_staged(const Op &op) {
+    if (op.eo || stage_bytes(op.g.L[0]) > 200 * 1024) return false;
+    const char *env = std::getenv("DLZ_CG_STAGE");
+    return env && env[0] == '1';
+}
+
+// dynamic shared memory of the staged kernels beyond 48 KB (set once, outside any graph
+// capture)
+int cg_prepare() {
+    static int done = 0;
+    if (done) return DLZ_OK;
+    const int mx = 200 * 1024;
+    DLZ_CUDA_TRY(cudaFuncSetAttribute(k_cg_k1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    DLZ_CUDA_TRY(cudaFuncSetAttribute(k_cg_k23<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    done = 1;
+    return DLZ_OK;
+}
+
 }  // namespace
+
+long cgnr_blocks_per_rhs(const Op &op, int N) {
+    return slab_blocks(cg_slab_walk(op, N));
+}
 
 int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5], CgFusedState *ms,
                      double *partials, const double *d_tol, const dlz_params &p, int &iters) {
@@ -299,8 +361,29 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
     const Geom g = op.g;
     const float kappa = (float)op.kappa;
     const float4 *links = op.gauge32.as<float4>();
-    const unsigned blocks = (unsigned)(((g.V + kT - 1) / kT) * N);
+    const SlabWalk w = cg_slab_walk(op, N);
+    const unsigned blocks = (unsigned)(cgnr_blocks_per_rhs(op, N) * N);
     const int nbq = (int)(blocks / N);
+    const bool staged = cg_staged(op);
+    const int smem = staged ? stage_bytes(g.L[0]) : 0;
+    int *err = op.stage_err.as<int>();
+    if (staged) DLZ_TRY(cg_prepare());
+    auto k1 = [&]() {
+        if (staged)
+            k_cg_k1<true><<<blocks, kT, smem, op.stream>>>(bufs[0], bufs[1], bufs[2], links, g, w, kappa, N, ms,
+                                                          partials, err);
+        else
+            k_cg_k1<false><<<blocks, kT, 0, op.stream>>>(bufs[0], bufs[1], bufs[2], links, g, w, kappa, N, ms,
+                                                        partials, err);
+    };
+    auto k23 = [&]() {
+        if (staged)
+            k_cg_k23<true><<<blocks, kT, smem, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w, kappa, N,
+                                                           ms, partials, err);
+        else
+            k_cg_k23<false><<<blocks, kT, 0, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w, kappa, N,
+                                                         ms, partials, err);
+    };
     float4 *S = s0, *R = bufs[0], *P = bufs[1], *T = bufs[2];
     // p = t = 0 so that the first K1 (beta = 0) gives p = r, t = D r
     for (float4 *z : {P, T})
@@ -313,10 +396,10 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
         // t = 0: the odd hop of it is 0 and K23b only sums |r|^2 and |s|^2
         float4 *M = op.eo_tmp32.as<float4>();
         DLZ_CUDA_TRY(cudaMemsetAsync(M, 0, (size_t)N * n * sizeof(float4), op.stream));
-        k_cg_eo_k23b<<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, (float)(op.kappa * op.kappa), N,
-                                                   ms, partials);
+        k_cg_eo_k23b<<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, w, (float)(op.kappa * op.kappa),
+                                                   N, ms, partials);
     } else {
-        k_cg_k23<<<blocks, kT, 0, op.stream>>>(T, R, S, P, e, links, g, kappa, N, ms, partials);
+        k23();
     }
     k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 1, ms);
     op.prof.launches += 2;
@@ -331,12 +414,12 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
             const float kappa2 = (float)(op.kappa * op.kappa);
             op.prof.stencil_start(op.stream, true, g.V, N, 192, 1, 192);
             DLZ_TRY(eo_hop32(op, M, R, 1, false, N));
-            k_cg_eo_k1b<<<blocks, kT, 0, op.stream>>>(R, M, P, T, links, op.gf, kappa2, N, ms, partials);
+            k_cg_eo_k1b<<<blocks, kT, 0, op.stream>>>(R, M, P, T, links, op.gf, w, kappa2, N, ms, partials);
             op.prof.stencil_stop(op.stream);
             k_cg_alpha<<<N, 256, 0, op.stream>>>(partials, nbq, ms);
             op.prof.stencil_start(op.stream, true, g.V, N, 264, 2, 192);
             DLZ_TRY(eo_hop32(op, M, T, 1, true, N));
-            k_cg_eo_k23b<<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, kappa2, N, ms, partials);
+            k_cg_eo_k23b<<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, w, kappa2, N, ms, partials);
             op.prof.stencil_stop(op.stream);
             k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 0, ms);
             op.prof.launches += 4;
@@ -345,12 +428,12 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
         }
         // K1 moves 120 reals per site and RHS (r gathered, t and p read and written) + links
         op.prof.stencil_start(op.stream, true, g.V, N, 120, 1);
-        k_cg_k1<<<blocks, kT, 0, op.stream>>>(R, P, T, links, g, kappa, N, ms, partials);
+        k1();
         op.prof.stencil_stop(op.stream);
         k_cg_alpha<<<N, 256, 0, op.stream>>>(partials, nbq, ms);
         // K23 moves 192 reals per site and RHS (t gathered; r, s, e read and written; p read)
         op.prof.stencil_start(op.stream, true, g.V, N, 192, 2);
-        k_cg_k23<<<blocks, kT, 0, op.stream>>>(T, R, S, P, e, links, g, kappa, N, ms, partials);
+        k23();
         op.prof.stencil_stop(op.stream);
         k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 0, ms);
         op.prof.launches += 4;
@@ -382,6 +465,14 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
     }
     ge.sample(op.prof);
     iters += it;
+    if (staged) {
+        int h_err = 0;
+        DLZ_TRY(d2h_sync(op, &h_err, err, sizeof(int)));
+        if (h_err) {
+            DLZ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), op.stream));
+            return fail(DLZ_ERR_DEVICE_TIMEOUT, "a staging wait of the fused CGNR kernels gave up");
+        }
+    }
     return DLZ_OK;
 }
 

@@ -204,6 +204,7 @@ struct Op {
     DevBuf md_scratch;   // block partials of the FP32 multi-dot (grown on demand, outside graphs)
     int multi_choice = 0;   // launch form the multi-lattice autotuner chose last (100 form + 10 chunks + half)
     TcScratch tc;           // scratch of the tensor-core basis products
+    DevBuf stage_err;       // int: set by a stencil kernel whose staging wait gave up
 };
 
 

@@ -66,6 +66,9 @@ int minres_fused_batch(Op &op, int N, const float4 *r, float4 *e, float4 *const 
 // Fused FP32 CG on the normal equations for D e = s0 on N right-hand sides
 // (cg_fused.cu); s0 is overwritten, e is updated in place (holds the start).
 struct CgFusedState;
+// blocks per right-hand side of the fused CGNR kernels for an N-RHS batch (the size of
+// their partials arrays)
+long cgnr_blocks_per_rhs(const Op &op, int N);
 int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5], CgFusedState *ms,
                      double *partials, const double *d_tol, const dlz_params &p, int &iters);
 // FP32 D-MinRes with FP64 defect correction on many lattices at once

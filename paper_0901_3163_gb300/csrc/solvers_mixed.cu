@@ -78,7 +78,7 @@ int dsolve_mixed_batch(Op &op, const dlz_defl_s *d, bool minres, const double2 *
         DLZ_TRY(pdot.alloc((size_t)N * d->k * sizeof(double2)));
         DLZ_TRY(reserve_multidot(op, d->k));
     }
-    const long k1_blocks = (long)((op.g.V + 127) / 128) * N;
+    const long k1_blocks = std::max((long)((op.g.V + 127) / 128), minres ? 0L : cgnr_blocks_per_rhs(op, N)) * N;
     DLZ_TRY(fpart.alloc((size_t)2 * k1_blocks * sizeof(double)));   // K1 and K2a partials
     InnerState *ist = reinterpret_cast<InnerState *>(scal.as<double>());
     double *d_rn = scal.as<double>() + kMaxBatch * 24;        // ||r_q||

@@ -8,6 +8,7 @@
 // Lx*Ly*Lz sites away: a window of a few MB that stays in the 129 MB L2), so
 // DRAM sees each spinor and link about once per application.
 #include "dlz_internal.cuh"
+#include "slab_walk.cuh"
 #include "wilson_site.cuh"
 
 namespace dlz {
@@ -38,12 +39,6 @@ __device__ inline void wilson_batch_body(typename Field<T>::vec *__restrict__ ou
                                          int nrhs, long nel) {
     const int r = blockIdx.x % nrhs;
     const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
-    if (sizeof(T) == 4 && threadIdx.x == 0) {
-        // the block's own sites of its right-hand side (and, once per site chunk, the links)
-        const int s0 = (blockIdx.x / nrhs) * blockDim.x, nb = min((int)blockDim.x, g.V - s0);
-        prefetch_planes_l2(in + (size_t)r * nel, 6, g.V, s0, nb);
-        if (r == 0) prefetch_planes_l2(U, 12, g.V, s0, nb);
-    }
     if (s >= g.V) return;
     cx<T> o[12];
     wilson_site<T, G5IN, G5OUT>(s, g, kappa, in + (size_t)r * nel, U, o);
@@ -58,20 +53,32 @@ k_wilson_batch(typename Field<T>::vec *__restrict__ out, const typename Field<T>
 }
 
 // FP32: at most 80 registers (6 blocks per SM), measured 5% faster at 11-16
-// right-hand sides than without the bound
+// right-hand sides than without the bound.  Blocks of 128 sites in the slab walk
+// (slab_walk.cuh).
 template <bool G5IN, bool G5OUT>
-__global__ void __launch_bounds__(128, 6)
+__global__ void __launch_bounds__(kSlabBlock, 6)
 k_wilson_batch32(float4 *__restrict__ out, const float4 *__restrict__ in, const float4 *__restrict__ U, Geom g,
-                 float kappa, int nrhs, long nel) {
-    wilson_batch_body<float, G5IN, G5OUT>(out, in, U, g, kappa, nrhs, nel);
+                 SlabWalk w, float kappa, int nrhs, long nel) {
+    const int r = blockIdx.x % nrhs;
+    int s0, nb;
+    slab_block(w, blockIdx.x / nrhs, s0, nb);
+    if (threadIdx.x == 0 && nb > 0) {
+        prefetch_planes_l2(in + (size_t)r * nel, 6, g.V, s0, nb);
+        if (r == 0) prefetch_planes_l2(U, 12, g.V, s0, nb);
+    }
+    if ((int)threadIdx.x >= nb) return;
+    const int s = s0 + threadIdx.x;
+    float2 o[12];
+    wilson_site<float, G5IN, G5OUT>(s, g, kappa, in + (size_t)r * nel, U, o);
+    Field<float>::store(out + (size_t)r * nel, g.V, s, o);
 }
 
 template <typename T, bool G5IN, bool G5OUT>
 inline void launch_batch_kernel(unsigned blocks, int threads, cudaStream_t st, typename Field<T>::vec *out,
                                 const typename Field<T>::vec *in, const typename Link<T>::vec *U, const Geom &g,
-                                T kappa, int nrhs, long nel) {
+                                const SlabWalk &w, T kappa, int nrhs, long nel) {
     if constexpr (sizeof(T) == 4)
-        k_wilson_batch32<G5IN, G5OUT><<<blocks, threads, 0, st>>>(out, in, U, g, kappa, nrhs, nel);
+        k_wilson_batch32<G5IN, G5OUT><<<blocks, kSlabBlock, 0, st>>>(out, in, U, g, w, kappa, nrhs, nel);
     else
         k_wilson_batch<T, G5IN, G5OUT><<<blocks, threads, 0, st>>>(out, in, U, g, kappa, nrhs, nel);
 }
@@ -80,13 +87,15 @@ template <typename T>
 int launch_wilson_batch(Op &op, typename Field<T>::vec *out, const typename Field<T>::vec *in,
                         const typename Link<T>::vec *U, int which, int nrhs, long nel, int threads) {
     const Geom &g = op.g;
-    const long blocks = (long)((g.V + threads - 1) / threads) * nrhs;
+    // FP32: the slab walk for a stencil moving ~200 bytes per site and right-hand side
+    const SlabWalk w = make_slab_walk(g.L[0] * g.L[1], g.L[2], g.L[3], nrhs, 200.0);
+    const long blocks = sizeof(T) == 4 ? slab_blocks(w) * nrhs : (long)((g.V + threads - 1) / threads) * nrhs;
     const T kappa = (T)op.kappa;
     op.prof.stencil_start(op.stream, sizeof(T) == 4, g.V, nrhs);
     switch (which) {
-    case DLZ_D: launch_batch_kernel<T, false, false>((unsigned)blocks, threads, op.stream, out, in, U, g, kappa, nrhs, nel); break;
-    case DLZ_DDAG: launch_batch_kernel<T, true, true>((unsigned)blocks, threads, op.stream, out, in, U, g, kappa, nrhs, nel); break;
-    case DLZ_Q: launch_batch_kernel<T, false, true>((unsigned)blocks, threads, op.stream, out, in, U, g, kappa, nrhs, nel); break;
+    case DLZ_D: launch_batch_kernel<T, false, false>((unsigned)blocks, threads, op.stream, out, in, U, g, w, kappa, nrhs, nel); break;
+    case DLZ_DDAG: launch_batch_kernel<T, true, true>((unsigned)blocks, threads, op.stream, out, in, U, g, w, kappa, nrhs, nel); break;
+    case DLZ_Q: launch_batch_kernel<T, false, true>((unsigned)blocks, threads, op.stream, out, in, U, g, w, kappa, nrhs, nel); break;
     default: return fail(DLZ_ERR_BADARG, "stencil: which must be D, DDAG or Q");
     }
     op.prof.stencil_stop(op.stream);

@@ -11,23 +11,33 @@
 // [gamma5] ([gamma5] x - kappa^2 H_eo t); Dhat^dag = gamma5 Dhat gamma5 and
 // Qhat = gamma5 Dhat take the gamma5 variants of the same two kernels.
 #include "dlz_internal.cuh"
+#include "slab_walk.cuh"
 #include "wilson_eo_site.cuh"
 
 namespace dlz {
 
 namespace {
 
-constexpr int kEoThreads = 128;
+constexpr int kEoThreads = kSlabBlock;
+
+// The walk over one parity's sites for a kernel moving `bytes` per site and right-hand
+// side: slab_walk.cuh in FP32, the plain order in FP64 (FP64-ALU-bound kernels)
+SlabWalk eo_walk(const Geom &gf, int nrhs, double bytes, bool f32) {
+    const int plane = gf.L[0] * gf.L[1] / 2;
+    return f32 ? make_slab_walk(plane, gf.L[2], gf.L[3], nrhs, bytes) : slab_walk_of(plane, gf.L[2], gf.L[3], gf.L[2]);
+}
 
 // out (parity par) = H [gamma5]^G5IN in (parity 1 - par), nrhs fields; RHS fastest in
 // blockIdx so that blocks of the same sites share their links in L2
 template <typename T, bool G5IN>
 __global__ void __launch_bounds__(kEoThreads)
 k_eo_hop(typename Field<T>::vec *__restrict__ out, const typename Field<T>::vec *__restrict__ in,
-         const typename Link<T>::vec *__restrict__ U, Geom gf, int par, int nrhs, long nel) {
+         const typename Link<T>::vec *__restrict__ U, Geom gf, SlabWalk w, int par, int nrhs, long nel) {
     const int r = blockIdx.x % nrhs;
-    const int cb = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
-    if (cb >= (gf.V >> 1)) return;
+    int c0, nb;
+    slab_block(w, blockIdx.x / nrhs, c0, nb);
+    if ((int)threadIdx.x >= nb) return;
+    const int cb = c0 + threadIdx.x;
     cx<T> acc[12];
     wilson_eo_hop_site<T, G5IN>(cb, par, gf, in + (size_t)r * nel, U, acc);
     Field<T>::store(out + (size_t)r * nel, gf.V >> 1, cb, acc);
@@ -38,10 +48,12 @@ template <typename T, bool G5X, bool G5OUT>
 __global__ void __launch_bounds__(kEoThreads)
 k_eo_schur(typename Field<T>::vec *__restrict__ out, const typename Field<T>::vec *__restrict__ x,
            const typename Field<T>::vec *__restrict__ t, const typename Link<T>::vec *__restrict__ U, Geom gf,
-           T kappa2, int nrhs, long nel) {
+           SlabWalk w, T kappa2, int nrhs, long nel) {
     const int r = blockIdx.x % nrhs;
-    const int cb = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
-    if (cb >= (gf.V >> 1)) return;
+    int c0, nb;
+    slab_block(w, blockIdx.x / nrhs, c0, nb);
+    if ((int)threadIdx.x >= nb) return;
+    const int cb = c0 + threadIdx.x;
     cx<T> o[12];
     wilson_eo_schur_site<T, G5X, G5OUT>(cb, gf, kappa2, x + (size_t)r * nel, t + (size_t)r * nel, U, o);
     Field<T>::store(out + (size_t)r * nel, gf.V >> 1, cb, o);
@@ -93,7 +105,8 @@ int eo_apply_t(Op &op, typename Field<T>::vec *out, const typename Field<T>::vec
     const T kappa2 = (T)(op.kappa * op.kappa);
     for (int r0 = 0; r0 < nrhs; r0 += kEoBatch) {
         const int nb = nrhs - r0 < kEoBatch ? nrhs - r0 : kEoBatch;
-        const unsigned blocks = (unsigned)((((gf.V >> 1) + kEoThreads - 1) / kEoThreads) * nb);
+        const SlabWalk wh = eo_walk(gf, nb, 200.0, sizeof(T) == 4), ws = eo_walk(gf, nb, 300.0, sizeof(T) == 4);
+        const unsigned bh = (unsigned)(slab_blocks(wh) * nb), bs = (unsigned)(slab_blocks(ws) * nb);
         const typename Field<T>::vec *x = in + (size_t)r0 * nel;
         typename Field<T>::vec *o = out + (size_t)r0 * nel;
         const bool g5 = which == DLZ_DDAG;
@@ -102,12 +115,12 @@ int eo_apply_t(Op &op, typename Field<T>::vec *out, const typename Field<T>::vec
         // Each of the two passes reads every link once: 2 x 4 links per full site, i.e.
         // 4 x 48 (FP32, two rows) or 4 x 72 (FP64) reals per even site
         op.prof.stencil_start(op.stream, sizeof(T) == 4, gf.V >> 1, nb, 120, 0, sizeof(T) == 4 ? 192 : 288);
-        if (g5) k_eo_hop<T, true><<<blocks, kEoThreads, 0, op.stream>>>(tmp, x, U, gf, 1, nb, nel);
-        else k_eo_hop<T, false><<<blocks, kEoThreads, 0, op.stream>>>(tmp, x, U, gf, 1, nb, nel);
+        if (g5) k_eo_hop<T, true><<<bh, kEoThreads, 0, op.stream>>>(tmp, x, U, gf, wh, 1, nb, nel);
+        else k_eo_hop<T, false><<<bh, kEoThreads, 0, op.stream>>>(tmp, x, U, gf, wh, 1, nb, nel);
         switch (which) {
-        case DLZ_D: k_eo_schur<T, false, false><<<blocks, kEoThreads, 0, op.stream>>>(o, x, tmp, U, gf, kappa2, nb, nel); break;
-        case DLZ_DDAG: k_eo_schur<T, true, true><<<blocks, kEoThreads, 0, op.stream>>>(o, x, tmp, U, gf, kappa2, nb, nel); break;
-        case DLZ_Q: k_eo_schur<T, false, true><<<blocks, kEoThreads, 0, op.stream>>>(o, x, tmp, U, gf, kappa2, nb, nel); break;
+        case DLZ_D: k_eo_schur<T, false, false><<<bs, kEoThreads, 0, op.stream>>>(o, x, tmp, U, gf, ws, kappa2, nb, nel); break;
+        case DLZ_DDAG: k_eo_schur<T, true, true><<<bs, kEoThreads, 0, op.stream>>>(o, x, tmp, U, gf, ws, kappa2, nb, nel); break;
+        case DLZ_Q: k_eo_schur<T, false, true><<<bs, kEoThreads, 0, op.stream>>>(o, x, tmp, U, gf, ws, kappa2, nb, nel); break;
         default: return fail(DLZ_ERR_BADARG, "even-odd stencil: which must be D, DDAG or Q");
         }
         op.prof.stencil_stop(op.stream);
@@ -129,9 +142,10 @@ int eo_apply32(Op &op, float4 *out, const float4 *in, int which, int nrhs) {
 int eo_hop64(Op &op, double2 *out, const double2 *in, int par, bool g5in, int nrhs) {
     const Geom gf = op.gf;
     const long nel = 12L * (gf.V >> 1);
-    const unsigned blocks = (unsigned)((((gf.V >> 1) + kEoThreads - 1) / kEoThreads) * nrhs);
-    if (g5in) k_eo_hop<double, true><<<blocks, kEoThreads, 0, op.stream>>>(out, in, op.gauge64.as<double2>(), gf, par, nrhs, nel);
-    else k_eo_hop<double, false><<<blocks, kEoThreads, 0, op.stream>>>(out, in, op.gauge64.as<double2>(), gf, par, nrhs, nel);
+    const SlabWalk w = eo_walk(gf, nrhs, 200.0, false);
+    const unsigned blocks = (unsigned)(slab_blocks(w) * nrhs);
+    if (g5in) k_eo_hop<double, true><<<blocks, kEoThreads, 0, op.stream>>>(out, in, op.gauge64.as<double2>(), gf, w, par, nrhs, nel);
+    else k_eo_hop<double, false><<<blocks, kEoThreads, 0, op.stream>>>(out, in, op.gauge64.as<double2>(), gf, w, par, nrhs, nel);
     op.prof.launches++;
     DLZ_CUDA_TRY(cudaGetLastError());
     return DLZ_OK;
@@ -140,9 +154,10 @@ int eo_hop64(Op &op, double2 *out, const double2 *in, int par, bool g5in, int nr
 int eo_hop32(Op &op, float4 *out, const float4 *in, int par, bool g5in, int nrhs) {
     const Geom gf = op.gf;
     const long nel = 6L * (gf.V >> 1);
-    const unsigned blocks = (unsigned)((((gf.V >> 1) + kEoThreads - 1) / kEoThreads) * nrhs);
-    if (g5in) k_eo_hop<float, true><<<blocks, kEoThreads, 0, op.stream>>>(out, in, op.gauge32.as<float4>(), gf, par, nrhs, nel);
-    else k_eo_hop<float, false><<<blocks, kEoThreads, 0, op.stream>>>(out, in, op.gauge32.as<float4>(), gf, par, nrhs, nel);
+    const SlabWalk w = eo_walk(gf, nrhs, 200.0, true);
+    const unsigned blocks = (unsigned)(slab_blocks(w) * nrhs);
+    if (g5in) k_eo_hop<float, true><<<blocks, kEoThreads, 0, op.stream>>>(out, in, op.gauge32.as<float4>(), gf, w, par, nrhs, nel);
+    else k_eo_hop<float, false><<<blocks, kEoThreads, 0, op.stream>>>(out, in, op.gauge32.as<float4>(), gf, w, par, nrhs, nel);
     op.prof.launches++;
     DLZ_CUDA_TRY(cudaGetLastError());
     return DLZ_OK;

@@ -197,32 +197,43 @@ template <bool G5> __host__ __device__ inline void maybe_g5(float2 (&v)[12]) {
     }
 }
 
-template <typename T, int MU, bool G5IN>
-__host__ __device__ inline void hop_pair(int s, const int (&c)[4], const Geom &g, int stride,
-                                         const typename Field<T>::vec *__restrict__ in,
+// Where a site function reads the input spinors: get<MU, DIR>(n, wrapped, p) loads the
+// spinor of site n, reached by the hop in direction MU (DIR = +1 forward, -1 backward)
+// or the site itself (DIR = 0); `wrapped` when the hop crosses the lattice edge.  This
+// one reads the field in global memory; the staged kernels read a shared-memory copy.
+template <typename T> struct GlobalGather {
+    const typename Field<T>::vec *__restrict__ in;
+    int V;
+    template <int MU, int DIR>
+    __host__ __device__ inline void get(int n, bool, cx<T> (&p)[12]) const { Field<T>::load(in, V, n, p); }
+};
+
+template <typename T, int MU, bool G5IN, class G>
+__host__ __device__ inline void hop_pair(int s, const int (&c)[4], const Geom &g, int stride, const G &ld,
                                          const typename Link<T>::vec *__restrict__ U, cx<T> (&acc)[12]) {
     const int L = g.L[MU];
     // forward neighbour and the boundary phase of a hop across the time edge
-    const int sf = (c[MU] == L - 1) ? s - (L - 1) * stride : s + stride;
-    const T phf = (MU == 3 && c[3] == L - 1) ? (T)g.bc_t : (T)1;
-    const int sb = (c[MU] == 0) ? s + (L - 1) * stride : s - stride;
-    const T phb = (MU == 3 && c[3] == 0) ? (T)g.bc_t : (T)1;
+    const bool wf = c[MU] == L - 1, wb = c[MU] == 0;
+    const int sf = wf ? s - (L - 1) * stride : s + stride;
+    const T phf = (MU == 3 && wf) ? (T)g.bc_t : (T)1;
+    const int sb = wb ? s + (L - 1) * stride : s - stride;
+    const T phb = (MU == 3 && wb) ? (T)g.bc_t : (T)1;
     cx<T> p[12], u[9];
-    Field<T>::load(in, g.V, sf, p);
+    ld.template get<MU, 1>(sf, wf, p);
     maybe_g5<G5IN>(p);
     load_link<T>(U, g.V, MU, s, u);
     hop_fwd<T, MU>(p, u, phf, acc);
-    Field<T>::load(in, g.V, sb, p);
+    ld.template get<MU, -1>(sb, wb, p);
     maybe_g5<G5IN>(p);
     load_link<T>(U, g.V, MU, sb, u);
     hop_bwd<T, MU>(p, u, phb, acc);
 }
 
-// out(s) = [gamma5]^G5OUT (1 - kappa H) [gamma5]^G5IN in, at one site.
-template <typename T, bool G5IN, bool G5OUT>
-__host__ __device__ inline void wilson_site(int s, const Geom &g, T kappa,
-                                            const typename Field<T>::vec *__restrict__ in,
-                                            const typename Link<T>::vec *__restrict__ U, cx<T> (&out)[12]) {
+// out(s) = [gamma5]^G5OUT (1 - kappa H) [gamma5]^G5IN in, at one site, the input read
+// through the gather ld.
+template <typename T, bool G5IN, bool G5OUT, class G>
+__host__ __device__ inline void wilson_site_g(int s, const Geom &g, T kappa, const G &ld,
+                                              const typename Link<T>::vec *__restrict__ U, cx<T> (&out)[12]) {
     int c[4];
     int r = s;
     c[0] = r % g.L[0]; r /= g.L[0];
@@ -233,11 +244,11 @@ __host__ __device__ inline void wilson_site(int s, const Geom &g, T kappa,
     cx<T> acc[12];
 #pragma unroll
     for (int a = 0; a < 12; ++a) acc[a] = mk<T>(0, 0);
-    hop_pair<T, 0, G5IN>(s, c, g, 1, in, U, acc);
-    hop_pair<T, 1, G5IN>(s, c, g, st1, in, U, acc);
-    hop_pair<T, 2, G5IN>(s, c, g, st2, in, U, acc);
-    hop_pair<T, 3, G5IN>(s, c, g, st3, in, U, acc);
-    Field<T>::load(in, g.V, s, out);
+    hop_pair<T, 0, G5IN>(s, c, g, 1, ld, U, acc);
+    hop_pair<T, 1, G5IN>(s, c, g, st1, ld, U, acc);
+    hop_pair<T, 2, G5IN>(s, c, g, st2, ld, U, acc);
+    hop_pair<T, 3, G5IN>(s, c, g, st3, ld, U, acc);
+    ld.template get<0, 0>(s, false, out);
     maybe_g5<G5IN>(out);
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
@@ -245,6 +256,15 @@ __host__ __device__ inline void wilson_site(int s, const Geom &g, T kappa,
         out[a].y = out[a].y - kappa * acc[a].y;
     }
     maybe_g5<G5OUT>(out);
+}
+
+// out(s) = [gamma5]^G5OUT (1 - kappa H) [gamma5]^G5IN in, at one site.
+template <typename T, bool G5IN, bool G5OUT>
+__host__ __device__ inline void wilson_site(int s, const Geom &g, T kappa,
+                                            const typename Field<T>::vec *__restrict__ in,
+                                            const typename Link<T>::vec *__restrict__ U, cx<T> (&out)[12]) {
+    const GlobalGather<T> ld{in, g.V};
+    wilson_site_g<T, G5IN, G5OUT>(s, g, kappa, ld, U, out);
 }
 
 }  // namespace dlz
