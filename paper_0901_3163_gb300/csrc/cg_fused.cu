@@ -1,17 +1,18 @@
 // Fused FP32 CG on the normal equations (CGNR) for a batch of right-hand sides:
 // the inner solve of the mixed-precision D-CG (arXiv:0901.3163, Sec. 2: CG on
 // D^dag D).  For D e = s0 it iterates, per right-hand side, CG on D^dag D e = D^dag s0
-// with the residual of D e = s0 carried alongside:
+// with the norm of the residual of D e = s0 carried alongside:
 //   p = r + beta p,  t = D p,  alpha = |r|^2 / |t|^2,
-//   e += alpha p,  s -= alpha t,  r -= alpha D^dag t,  beta = |r_new|^2 / |r|^2,
-// s being the residual of D e = s0 (|s| is the quantity the outer FP64 loop needs)
+//   e += alpha p,  (s -= alpha t),  r -= alpha D^dag t,  beta = |r_new|^2 / |r|^2,
+// s being the residual of D e = s0 (|s| is the quantity the inner stopping test needs)
 // and r = D^dag s the CG residual (r starts as D^dag s0 and is then updated by the
 // recurrence, as in CG on any hermitian matrix).  Since D p = D r + beta D p_old, the
 // image t is carried too, so that each kernel applies its stencil to ONE vector:
 //   K1:  t = D r + beta t (the stencil gathers r), p = r + beta p;
 //        block partials of |t|^2.
-//   K23: z = D^dag t (the stencil gathers t); r -= alpha z, s -= alpha t, e += alpha p;
-//        block partials of |r|^2 and |s|^2.
+//   K23: z = D^dag t (the stencil gathers t); r -= alpha z, e += alpha p; block
+//        partials of |r|^2.  |s|^2 follows from |s_{k+1}|^2 = |s_k|^2 - alpha_k |r_k|^2,
+//        so s is updated (and summed) only by the first K23 of a solve.
 // Each kernel writes only vectors it does not gather (and only at its own site), so
 // every vector is updated in place.  One-block-per-RHS kernels sum the partials in a
 // fixed order and update the step lengths; six iterations form a CUDA graph that is
@@ -129,8 +130,10 @@ k_cg_k1(const float4 *__restrict__ R, float4 *__restrict__ P, float4 *__restrict
     block_partials<1>(v, partials + (size_t)q * nbq + blockIdx.x / N, 0);
 }
 
-// K23: r -= alpha D^dag t, s -= alpha t, e += alpha p; partials |r|^2, |s|^2.  Gathers t only.
-template <bool STAGED>
+// K23: r -= alpha D^dag t, e += alpha p; partial |r|^2.  Gathers t only.  WITH_S (the
+// first launch of a solve, alpha = 0): also s -= alpha t and the partial |s|^2; later
+// |s|^2 follows from the scalar recurrence in k_cg_beta and s itself is not needed.
+template <bool STAGED, bool WITH_S>
 __global__ void __launch_bounds__(kT, STAGED ? 3 : 6)
 k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restrict__ S, const float4 *__restrict__ P,
          float4 *__restrict__ E, const float4 *__restrict__ links, Geom g, SlabWalk w, float kappa, int N,
@@ -145,7 +148,7 @@ k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restric
     if (threadIdx.x == 0 && nb > 0) {
         if (!STAGED) prefetch_planes_l2(T + base, 6, g.V, s0, nb);
         prefetch_planes_l2(R + base, 6, g.V, s0, nb);
-        prefetch_planes_l2(S + base, 6, g.V, s0, nb);
+        if (WITH_S) prefetch_planes_l2(S + base, 6, g.V, s0, nb);
         prefetch_planes_l2(P + base, 6, g.V, s0, nb);
         prefetch_planes_l2(E + base, 6, g.V, s0, nb);
         if (q == 0) prefetch_planes_l2(links, 12, g.V, s0, nb);
@@ -158,7 +161,7 @@ k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restric
         if constexpr (STAGED) {
             const StagedGather32 ga = staged_gather(T + base, g, s0, stage_sm);
             wilson_site_g<float, true, true>(s, g, kappa, ga, links, z);
-            ga.get<0, 0>(s, false, tc);
+            if (WITH_S) ga.get<0, 0>(s, false, tc);
         } else {
             wilson_site<float, true, true>(s, g, kappa, T + base, links, z);
         }
@@ -171,14 +174,16 @@ k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restric
             r.z = fmaf(-al, z1.x, r.z); r.w = fmaf(-al, z1.y, r.w);
             R[i] = r;
             v[0] += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
-            float4 t;
-            if constexpr (STAGED) t = make_float4(tc[2 * c].x, tc[2 * c].y, tc[2 * c + 1].x, tc[2 * c + 1].y);
-            else t = T[i];
-            float4 sv = S[i];
-            sv.x = fmaf(-al, t.x, sv.x); sv.y = fmaf(-al, t.y, sv.y);
-            sv.z = fmaf(-al, t.z, sv.z); sv.w = fmaf(-al, t.w, sv.w);
-            S[i] = sv;
-            v[1] += sv.x * sv.x + sv.y * sv.y + sv.z * sv.z + sv.w * sv.w;
+            if constexpr (WITH_S) {
+                float4 t;
+                if constexpr (STAGED) t = make_float4(tc[2 * c].x, tc[2 * c].y, tc[2 * c + 1].x, tc[2 * c + 1].y);
+                else t = T[i];
+                float4 sv = S[i];
+                sv.x = fmaf(-al, t.x, sv.x); sv.y = fmaf(-al, t.y, sv.y);
+                sv.z = fmaf(-al, t.z, sv.z); sv.w = fmaf(-al, t.w, sv.w);
+                S[i] = sv;
+                v[1] += sv.x * sv.x + sv.y * sv.y + sv.z * sv.z + sv.w * sv.w;
+            }
             const float4 pv = P[i];
             float4 e = E[i];
             e.x = fmaf(al, pv.x, e.x); e.y = fmaf(al, pv.y, e.y);
@@ -187,7 +192,11 @@ k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restric
         }
     }
     const int nbq = gridDim.x / N;
-    block_partials<2>(v, partials + (size_t)q * nbq + blockIdx.x / N, (size_t)N * nbq);
+    if constexpr (WITH_S) block_partials<2>(v, partials + (size_t)q * nbq + blockIdx.x / N, (size_t)N * nbq);
+    else {
+        float v1[1] = {v[0]};
+        block_partials<1>(v1, partials + (size_t)q * nbq + blockIdx.x / N, 0);
+    }
 }
 
 // Even-odd operator (Dhat on the even sites): each stencil is two launches, the odd
@@ -225,7 +234,8 @@ k_cg_eo_k1b(const float4 *__restrict__ R, const float4 *__restrict__ M, float4 *
 }
 
 // K23b: z = Dhat^dag t = gamma5 (gamma5 t - kappa^2 H_eo m), m = H_oe gamma5 t;
-// r -= alpha z, s -= alpha t, e += alpha p.
+// r -= alpha z, e += alpha p (WITH_S: s -= alpha t as in K23).
+template <bool WITH_S>
 __global__ void __launch_bounds__(kT, 6)
 k_cg_eo_k23b(const float4 *__restrict__ T, const float4 *__restrict__ M, float4 *__restrict__ R,
              float4 *__restrict__ S, const float4 *__restrict__ P, float4 *__restrict__ E,
@@ -240,7 +250,7 @@ k_cg_eo_k23b(const float4 *__restrict__ T, const float4 *__restrict__ M, float4 
     if (threadIdx.x == 0 && nb > 0) {
         prefetch_planes_l2(T + base, 6, Vh, c0, nb);
         prefetch_planes_l2(R + base, 6, Vh, c0, nb);
-        prefetch_planes_l2(S + base, 6, Vh, c0, nb);
+        if (WITH_S) prefetch_planes_l2(S + base, 6, Vh, c0, nb);
         prefetch_planes_l2(P + base, 6, Vh, c0, nb);
         prefetch_planes_l2(E + base, 6, Vh, c0, nb);
     }
@@ -258,12 +268,14 @@ k_cg_eo_k23b(const float4 *__restrict__ T, const float4 *__restrict__ M, float4 
             r.z = fmaf(-al, z1.x, r.z); r.w = fmaf(-al, z1.y, r.w);
             R[i] = r;
             v[0] += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
-            const float4 t = T[i];
-            float4 sv = S[i];
-            sv.x = fmaf(-al, t.x, sv.x); sv.y = fmaf(-al, t.y, sv.y);
-            sv.z = fmaf(-al, t.z, sv.z); sv.w = fmaf(-al, t.w, sv.w);
-            S[i] = sv;
-            v[1] += sv.x * sv.x + sv.y * sv.y + sv.z * sv.z + sv.w * sv.w;
+            if constexpr (WITH_S) {
+                const float4 t = T[i];
+                float4 sv = S[i];
+                sv.x = fmaf(-al, t.x, sv.x); sv.y = fmaf(-al, t.y, sv.y);
+                sv.z = fmaf(-al, t.z, sv.z); sv.w = fmaf(-al, t.w, sv.w);
+                S[i] = sv;
+                v[1] += sv.x * sv.x + sv.y * sv.y + sv.z * sv.z + sv.w * sv.w;
+            }
             const float4 pv = P[i];
             float4 e = E[i];
             e.x = fmaf(al, pv.x, e.x); e.y = fmaf(al, pv.y, e.y);
@@ -272,7 +284,11 @@ k_cg_eo_k23b(const float4 *__restrict__ T, const float4 *__restrict__ M, float4 
         }
     }
     const int nbq = gridDim.x / N;
-    block_partials<2>(v, partials + (size_t)q * nbq + blockIdx.x / N, (size_t)N * nbq);
+    if constexpr (WITH_S) block_partials<2>(v, partials + (size_t)q * nbq + blockIdx.x / N, (size_t)N * nbq);
+    else {
+        float v1[1] = {v[0]};
+        block_partials<1>(v1, partials + (size_t)q * nbq + blockIdx.x / N, 0);
+    }
 }
 
 __device__ inline double block_total(const double *__restrict__ p, int n) {
@@ -302,17 +318,21 @@ __global__ void __launch_bounds__(256) k_cg_alpha(const double *__restrict__ par
     }
 }
 
-// |r_new|^2, |s_new|^2, beta (init: beta = 0)
+// |r_new|^2, |s_new|^2, beta (init: beta = 0, |s|^2 summed).  After the first step
+// |s|^2 follows from the recurrence of CG on the normal equations,
+//   |s_{k+1}|^2 = |s_k - alpha_k t_k|^2 = |s_k|^2 - alpha_k |r_k|^2,
+// since <s_k, t_k> = <s_k, D p_k> = <r_k, p_k> = |r_k|^2 and alpha_k |t_k|^2 = |r_k|^2; it
+// only steers the inner stopping test (the outer loop recomputes the residual in FP64).
 __global__ void __launch_bounds__(256) k_cg_beta(const double *__restrict__ partials, int nbq, int N, int init,
                                                  CgFusedState *st) {
     const int q = blockIdx.x;
     const double rr = block_total(partials + (size_t)q * nbq, nbq);
-    const double ss = block_total(partials + (size_t)N * nbq + (size_t)q * nbq, nbq);
+    const double ss = init ? block_total(partials + (size_t)N * nbq + (size_t)q * nbq, nbq) : 0.0;
     if (threadIdx.x == 0) {
         CgFusedState s = st[q];
         s.beta = (init || !(s.gam > 0.0)) ? 0.0 : rr / s.gam;
+        s.ss = init ? ss : fmax(0.0, s.ss - s.alpha * s.gam);
         s.gam = rr;
-        s.ss = ss;
         s.f[1] = (float)s.beta;
         st[q] = s;
     }
@@ -344,7 +364,8 @@ int cg_prepare() {
     if (done) return DLZ_OK;
     const int mx = 200 * 1024;
     DLZ_CUDA_TRY(cudaFuncSetAttribute(k_cg_k1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    DLZ_CUDA_TRY(cudaFuncSetAttribute(k_cg_k23<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    DLZ_CUDA_TRY(cudaFuncSetAttribute(k_cg_k23<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    DLZ_CUDA_TRY(cudaFuncSetAttribute(k_cg_k23<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     done = 1;
     return DLZ_OK;
 }
@@ -376,13 +397,19 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
             k_cg_k1<false><<<blocks, kT, 0, op.stream>>>(bufs[0], bufs[1], bufs[2], links, g, w, kappa, N, ms,
                                                         partials, err);
     };
-    auto k23 = [&]() {
-        if (staged)
-            k_cg_k23<true><<<blocks, kT, smem, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w, kappa, N,
-                                                           ms, partials, err);
+    auto k23 = [&](bool with_s) {
+        if (staged && with_s)
+            k_cg_k23<true, true><<<blocks, kT, smem, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w,
+                                                                 kappa, N, ms, partials, err);
+        else if (staged)
+            k_cg_k23<true, false><<<blocks, kT, smem, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w,
+                                                                  kappa, N, ms, partials, err);
+        else if (with_s)
+            k_cg_k23<false, true><<<blocks, kT, 0, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w, kappa,
+                                                               N, ms, partials, err);
         else
-            k_cg_k23<false><<<blocks, kT, 0, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w, kappa, N,
-                                                         ms, partials, err);
+            k_cg_k23<false, false><<<blocks, kT, 0, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w,
+                                                                kappa, N, ms, partials, err);
     };
     float4 *S = s0, *R = bufs[0], *P = bufs[1], *T = bufs[2];
     // p = t = 0 so that the first K1 (beta = 0) gives p = r, t = D r
@@ -396,10 +423,10 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
         // t = 0: the odd hop of it is 0 and K23b only sums |r|^2 and |s|^2
         float4 *M = op.eo_tmp32.as<float4>();
         DLZ_CUDA_TRY(cudaMemsetAsync(M, 0, (size_t)N * n * sizeof(float4), op.stream));
-        k_cg_eo_k23b<<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, w, (float)(op.kappa * op.kappa),
-                                                   N, ms, partials);
+        k_cg_eo_k23b<true><<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, w,
+                                                         (float)(op.kappa * op.kappa), N, ms, partials);
     } else {
-        k23();
+        k23(true);
     }
     k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 1, ms);
     op.prof.launches += 2;
@@ -408,7 +435,7 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
         if (op.eo) {
             // even-odd: K1 = odd hop + K1b, K23 = odd hop + K23b (m: the odd work field).
             // Per even site and RHS, K1 moves 192 reals (r gathered by the hop, m written,
-            // m gathered, r, t, p read, t, p written), K23 264; each pair reads every link
+            // m gathered, r, t, p read, t, p written), K23 216; each pair reads every link
             // twice (192 reals per even site)
             float4 *M = op.eo_tmp32.as<float4>();
             const float kappa2 = (float)(op.kappa * op.kappa);
@@ -417,9 +444,10 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
             k_cg_eo_k1b<<<blocks, kT, 0, op.stream>>>(R, M, P, T, links, op.gf, w, kappa2, N, ms, partials);
             op.prof.stencil_stop(op.stream);
             k_cg_alpha<<<N, 256, 0, op.stream>>>(partials, nbq, ms);
-            op.prof.stencil_start(op.stream, true, g.V, N, 264, 2, 192);
+            op.prof.stencil_start(op.stream, true, g.V, N, 216, 2, 192);
             DLZ_TRY(eo_hop32(op, M, T, 1, true, N));
-            k_cg_eo_k23b<<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, w, kappa2, N, ms, partials);
+            k_cg_eo_k23b<false><<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, w, kappa2, N, ms,
+                                                              partials);
             op.prof.stencil_stop(op.stream);
             k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 0, ms);
             op.prof.launches += 4;
@@ -431,9 +459,9 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
         k1();
         op.prof.stencil_stop(op.stream);
         k_cg_alpha<<<N, 256, 0, op.stream>>>(partials, nbq, ms);
-        // K23 moves 192 reals per site and RHS (t gathered; r, s, e read and written; p read)
-        op.prof.stencil_start(op.stream, true, g.V, N, 192, 2);
-        k23();
+        // K23 moves 144 reals per site and RHS (t gathered; r, e read and written; p read)
+        op.prof.stencil_start(op.stream, true, g.V, N, 144, 2);
+        k23(false);
         op.prof.stencil_stop(op.stream);
         k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 0, ms);
         op.prof.launches += 4;
