@@ -51,10 +51,10 @@ C2_DR_CYCLES = 150
 # reports the counts of its own FP64 run in plain_fp64)
 REF_ITERS_PER_RHS = 2384
 REF_FIRST_RHS_MVPS = 26378
-# DRAM bytes (read + write) of one k_cg_k23 launch (16 RHS, 24^3x48) from the ncu
-# capture summarised in profiles/k_cg_k23_wilson_24x24x24x48_n16.md; None until taken
-# for the current kernel
-K23_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one k_cg_k1 launch (16 RHS, 24^3x48), the dominant kernel,
+# from the ncu capture summarised in profiles/k_cg_wilson_24x24x24x48_n16.md; None until
+# taken for the current kernel
+K1_TRAFFIC_BYTES = None
 METRIC = "RHS solved/s to |r|/|b|<1e-10 (Lan-DR(120,60) + D-CG, 49 Gaussian RHS, 24^3x48)"
 UNIT = "RHS/s"
 
@@ -272,12 +272,15 @@ def run_ours(args):
     ms_max, solved_all = aggregate_ranks(ms, solved, world, dev)
     value = solved_all / (ms_max / 1e3)
     peaks, src = _peaks()
-    roof = kernel_roofline(pst, 2, peaks, src,
-                           "k_cg_k23 (fused FP32 CGNR: s - alpha t gathered, D^dag stencil, e += alpha p; 16 RHS per launch)",
-                           args.k23_traffic,
-                           "ncu capture of the current kernel (profiles/)" if args.k23_traffic else
+    roof = kernel_roofline(pst, 1, peaks, src,
+                           "k_cg_k1 (fused FP32 CGNR: r gathered, t = D r + beta t, p = r + beta p, "
+                           "e += alpha p_old; 16 RHS per launch)",
+                           args.k1_traffic,
+                           "ncu capture of the current kernel, one launch at this size "
+                           "(profiles/k_cg_wilson_24x24x24x48_n16.md)" if args.k1_traffic else
                            "not captured for the current kernel")
-    roof_k1 = kernel_roofline(pst, 1, peaks, src, "k_cg_k1 (fused FP32 CGNR: r + beta p gathered, D stencil; 16 RHS)")
+    roof_k23 = kernel_roofline(pst, 2, peaks, src,
+                               "k_cg_k23 (fused FP32 CGNR: t gathered, r -= alpha D^dag t; 16 RHS per launch)")
     it_ms = sum(s.kernel_ms[1] + s.kernel_ms[2] for s in pst)
     it_b = sum(s.kernel_bytes[1] + s.kernel_bytes[2] for s in pst)
     # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
@@ -320,7 +323,7 @@ def run_ours(args):
         "mvps_per_step": int(mvps), "iterations_first_steps": [s.iterations for s in stats[:4]],
         "phase_seconds": {"first_rhs_dr": round(dr_s, 4), "deflated_48_rhs": round(d_s, 4)},
         "d_phase_rhs_per_s": round((nrhs - 1) / d_s, 4) if d_s > 0 else None,
-        "roofline": roof, "roofline_k_cg_k1": roof_k1,
+        "roofline": roof, "roofline_k_cg_k23": roof_k23,
         "cg_iteration_hbm_gbs": round(it_b / (it_ms * 1e-3) / 1e9, 1) if it_ms > 0 else None,
         "clocks": clk,
     }
@@ -935,7 +938,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--plain-rhs", type=int, default=2,
                     help="D-CG right-hand sides of the plain FP64 form timed beside the chosen form")
-    ap.add_argument("--k23-traffic", type=float, default=K23_TRAFFIC_BYTES,
+    ap.add_argument("--k1-traffic", type=float, default=K1_TRAFFIC_BYTES,
                     help="ncu DRAM bytes per launch of the dominant kernel (None if not measured)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")

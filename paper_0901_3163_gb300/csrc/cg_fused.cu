@@ -8,10 +8,10 @@
 // and r = D^dag s the CG residual (r starts as D^dag s0 and is then updated by the
 // recurrence, as in CG on any hermitian matrix).  Since D p = D r + beta D p_old, the
 // image t is carried too, so that each kernel applies its stencil to ONE vector:
-//   K1:  t = D r + beta t (the stencil gathers r), p = r + beta p;
-//        block partials of |t|^2.
-//   K23: z = D^dag t (the stencil gathers t); r -= alpha z, e += alpha p; block
-//        partials of |r|^2.  |s|^2 follows from |s_{k+1}|^2 = |s_k|^2 - alpha_k |r_k|^2,
+//   K1:  t = D r + beta t (the stencil gathers r), p = r + beta p, and the previous
+//        step's e += alpha p_old (K1 reads p_old anyway, so e is carried one step
+//        behind and K23 touches neither p nor e); block partials of |t|^2.
+//   K23: z = D^dag t (the stencil gathers t); r -= alpha z; block partials of |r|^2.  |s|^2 follows from |s_{k+1}|^2 = |s_k|^2 - alpha_k |r_k|^2,
 //        so s is updated (and summed) only by the first K23 of a solve.
 // Each kernel writes only vectors it does not gather (and only at its own site), so
 // every vector is updated in place.  One-block-per-RHS kernels sum the partials in a
@@ -90,10 +90,28 @@ __device__ inline void axpy_store(float4 *__restrict__ P, size_t base, int V, in
     }
 }
 
-// K1: t = D r + beta t, p = r + beta p; partial |t|^2.  Gathers r only.
+// p = r + beta p at site s, and the deferred update of the previous step e += alpha p_old
+// (e is carried one step behind, so that the kernel that reads p_old also moves e)
+__device__ inline void pe_update(float4 *__restrict__ P, float4 *__restrict__ E, size_t base, int V, int s, float bt,
+                                 float al, const float2 (&r)[12]) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const size_t i = base + (size_t)c * V + s;
+        const float4 q = P[i];
+        float4 e = E[i];
+        e.x = fmaf(al, q.x, e.x); e.y = fmaf(al, q.y, e.y);
+        e.z = fmaf(al, q.z, e.z); e.w = fmaf(al, q.w, e.w);
+        E[i] = e;
+        const float2 r0 = r[2 * c], r1 = r[2 * c + 1];
+        P[i] = make_float4(fmaf(bt, q.x, r0.x), fmaf(bt, q.y, r0.y), fmaf(bt, q.z, r1.x), fmaf(bt, q.w, r1.y));
+    }
+}
+
+// K1: t = D r + beta t, p = r + beta p, e += alpha p_old (the previous step's update);
+// partial |t|^2.  Gathers r only.
 template <bool STAGED>
 __global__ void __launch_bounds__(kT, STAGED ? 3 : 6)
-k_cg_k1(const float4 *__restrict__ R, float4 *__restrict__ P, float4 *__restrict__ T,
+k_cg_k1(const float4 *__restrict__ R, float4 *__restrict__ P, float4 *__restrict__ T, float4 *__restrict__ E,
         const float4 *__restrict__ links, Geom g, SlabWalk w, float kappa, int N, const CgFusedState *__restrict__ st,
         double *__restrict__ partials, int *__restrict__ err) {
     extern __shared__ __align__(128) float4 stage_sm[];
@@ -107,13 +125,14 @@ k_cg_k1(const float4 *__restrict__ R, float4 *__restrict__ P, float4 *__restrict
         if (!STAGED) prefetch_planes_l2(R + base, 6, g.V, s0, nb);
         prefetch_planes_l2(T + base, 6, g.V, s0, nb);
         prefetch_planes_l2(P + base, 6, g.V, s0, nb);
+        prefetch_planes_l2(E + base, 6, g.V, s0, nb);
         if (q == 0) prefetch_planes_l2(links, 12, g.V, s0, nb);
     }
     const bool ok = stage_begin<STAGED>(R + base, g, s0, nb, stage_sm, &mbar, err);
     float v[1] = {0.f};
     if ((int)threadIdx.x < nb && ok) {
-        const float bt = st[q].f[1];
-        float2 o[12], t[12], r[12], pn[12];
+        const float bt = st[q].f[1], al = st[q].f[0];
+        float2 o[12], t[12], r[12];
         if constexpr (STAGED) {
             const StagedGather32 ga = staged_gather(R + base, g, s0, stage_sm);
             wilson_site_g<float, false, false>(s, g, kappa, ga, links, o);
@@ -124,19 +143,19 @@ k_cg_k1(const float4 *__restrict__ R, float4 *__restrict__ P, float4 *__restrict
         }
         axpy_store(T, base, g.V, s, bt, o, t);
         v[0] = nrm(t);
-        axpy_store(P, base, g.V, s, bt, r, pn);
+        pe_update(P, E, base, g.V, s, bt, al, r);
     }
     const int nbq = gridDim.x / N;
     block_partials<1>(v, partials + (size_t)q * nbq + blockIdx.x / N, 0);
 }
 
-// K23: r -= alpha D^dag t, e += alpha p; partial |r|^2.  Gathers t only.  WITH_S (the
-// first launch of a solve, alpha = 0): also s -= alpha t and the partial |s|^2; later
-// |s|^2 follows from the scalar recurrence in k_cg_beta and s itself is not needed.
+// K23: r -= alpha D^dag t; partial |r|^2.  Gathers t only.  WITH_S (the first launch of
+// a solve, alpha = 0): also s -= alpha t and the partial |s|^2; later |s|^2 follows from
+// the scalar recurrence in k_cg_beta and s itself is not needed.
 template <bool STAGED, bool WITH_S>
 __global__ void __launch_bounds__(kT, STAGED ? 3 : 6)
-k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restrict__ S, const float4 *__restrict__ P,
-         float4 *__restrict__ E, const float4 *__restrict__ links, Geom g, SlabWalk w, float kappa, int N,
+k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restrict__ S,
+         const float4 *__restrict__ links, Geom g, SlabWalk w, float kappa, int N,
          const CgFusedState *__restrict__ st, double *__restrict__ partials, int *__restrict__ err) {
     extern __shared__ __align__(128) float4 stage_sm[];
     __shared__ __align__(8) uint64_t mbar;
@@ -149,8 +168,6 @@ k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restric
         if (!STAGED) prefetch_planes_l2(T + base, 6, g.V, s0, nb);
         prefetch_planes_l2(R + base, 6, g.V, s0, nb);
         if (WITH_S) prefetch_planes_l2(S + base, 6, g.V, s0, nb);
-        prefetch_planes_l2(P + base, 6, g.V, s0, nb);
-        prefetch_planes_l2(E + base, 6, g.V, s0, nb);
         if (q == 0) prefetch_planes_l2(links, 12, g.V, s0, nb);
     }
     const bool ok = stage_begin<STAGED>(T + base, g, s0, nb, stage_sm, &mbar, err);
@@ -184,11 +201,6 @@ k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restric
                 S[i] = sv;
                 v[1] += sv.x * sv.x + sv.y * sv.y + sv.z * sv.z + sv.w * sv.w;
             }
-            const float4 pv = P[i];
-            float4 e = E[i];
-            e.x = fmaf(al, pv.x, e.x); e.y = fmaf(al, pv.y, e.y);
-            e.z = fmaf(al, pv.z, e.z); e.w = fmaf(al, pv.w, e.w);
-            E[i] = e;
         }
     }
     const int nbq = gridDim.x / N;
@@ -202,10 +214,11 @@ k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restric
 // Even-odd operator (Dhat on the even sites): each stencil is two launches, the odd
 // hop (eo_hop32, gathering r or gamma5 t) and these Schur-step kernels at the even
 // sites, which gather the odd field and carry the same updates as K1 and K23.
-// K1b: t = Dhat r + beta t = (r - kappa^2 H_eo m) + beta t with m = H_oe r, p = r + beta p.
+// K1b: t = Dhat r + beta t = (r - kappa^2 H_eo m) + beta t with m = H_oe r, p = r + beta p,
+// e += alpha p_old as in K1.
 __global__ void __launch_bounds__(kT, 6)
 k_cg_eo_k1b(const float4 *__restrict__ R, const float4 *__restrict__ M, float4 *__restrict__ P, float4 *__restrict__ T,
-            const float4 *__restrict__ links, Geom gf, SlabWalk w, float kappa2, int N,
+            float4 *__restrict__ E, const float4 *__restrict__ links, Geom gf, SlabWalk w, float kappa2, int N,
             const CgFusedState *__restrict__ st, double *__restrict__ partials) {
     const int q = blockIdx.x % N;
     int c0, nb;
@@ -217,29 +230,29 @@ k_cg_eo_k1b(const float4 *__restrict__ R, const float4 *__restrict__ M, float4 *
         prefetch_planes_l2(R + base, 6, Vh, c0, nb);
         prefetch_planes_l2(T + base, 6, Vh, c0, nb);
         prefetch_planes_l2(P + base, 6, Vh, c0, nb);
+        prefetch_planes_l2(E + base, 6, Vh, c0, nb);
     }
     float v[1] = {0.f};
     if ((int)threadIdx.x < nb) {
-        const float bt = st[q].f[1];
+        const float bt = st[q].f[1], al = st[q].f[0];
         float2 o[12], t[12];
         wilson_eo_schur_site<float, false, false>(cb, gf, kappa2, R + base, M + base, links, o);
         axpy_store(T, base, Vh, cb, bt, o, t);
         v[0] = nrm(t);
-        float2 r[12], pn[12];
+        float2 r[12];
         Field<float>::load(R + base, Vh, cb, r);
-        axpy_store(P, base, Vh, cb, bt, r, pn);
+        pe_update(P, E, base, Vh, cb, bt, al, r);
     }
     const int nbq = gridDim.x / N;
     block_partials<1>(v, partials + (size_t)q * nbq + blockIdx.x / N, 0);
 }
 
 // K23b: z = Dhat^dag t = gamma5 (gamma5 t - kappa^2 H_eo m), m = H_oe gamma5 t;
-// r -= alpha z, e += alpha p (WITH_S: s -= alpha t as in K23).
+// r -= alpha z (WITH_S: s -= alpha t as in K23).
 template <bool WITH_S>
 __global__ void __launch_bounds__(kT, 6)
 k_cg_eo_k23b(const float4 *__restrict__ T, const float4 *__restrict__ M, float4 *__restrict__ R,
-             float4 *__restrict__ S, const float4 *__restrict__ P, float4 *__restrict__ E,
-             const float4 *__restrict__ links, Geom gf, SlabWalk w, float kappa2, int N,
+             float4 *__restrict__ S, const float4 *__restrict__ links, Geom gf, SlabWalk w, float kappa2, int N,
              const CgFusedState *__restrict__ st, double *__restrict__ partials) {
     const int q = blockIdx.x % N;
     int c0, nb;
@@ -251,8 +264,6 @@ k_cg_eo_k23b(const float4 *__restrict__ T, const float4 *__restrict__ M, float4 
         prefetch_planes_l2(T + base, 6, Vh, c0, nb);
         prefetch_planes_l2(R + base, 6, Vh, c0, nb);
         if (WITH_S) prefetch_planes_l2(S + base, 6, Vh, c0, nb);
-        prefetch_planes_l2(P + base, 6, Vh, c0, nb);
-        prefetch_planes_l2(E + base, 6, Vh, c0, nb);
     }
     float v[2] = {0.f, 0.f};
     if ((int)threadIdx.x < nb) {
@@ -276,11 +287,6 @@ k_cg_eo_k23b(const float4 *__restrict__ T, const float4 *__restrict__ M, float4 
                 S[i] = sv;
                 v[1] += sv.x * sv.x + sv.y * sv.y + sv.z * sv.z + sv.w * sv.w;
             }
-            const float4 pv = P[i];
-            float4 e = E[i];
-            e.x = fmaf(al, pv.x, e.x); e.y = fmaf(al, pv.y, e.y);
-            e.z = fmaf(al, pv.z, e.z); e.w = fmaf(al, pv.w, e.w);
-            E[i] = e;
         }
     }
     const int nbq = gridDim.x / N;
@@ -304,6 +310,20 @@ __device__ inline double block_total(const double *__restrict__ p, int n) {
         for (int w = 0; w < (int)(blockDim.x / 32); ++w) a += sm[w];
     __syncthreads();
     return a;     // valid in thread 0
+}
+
+// e += alpha p for every right-hand side (n float4 per right-hand side): the update that
+// K1 carries one step behind, made once after an inner solve's last step
+__global__ void k_cg_flush_e(float4 *__restrict__ E, const float4 *__restrict__ P,
+                             const CgFusedState *__restrict__ st, long n, int N) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)N * n) return;
+    const float al = st[i / n].f[0];
+    const float4 q = P[i];
+    float4 e = E[i];
+    e.x = fmaf(al, q.x, e.x); e.y = fmaf(al, q.y, e.y);
+    e.z = fmaf(al, q.z, e.z); e.w = fmaf(al, q.w, e.w);
+    E[i] = e;
 }
 
 // alpha = |r|^2 / |t|^2 (one block per right-hand side)
@@ -391,24 +411,24 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
     if (staged) DLZ_TRY(cg_prepare());
     auto k1 = [&]() {
         if (staged)
-            k_cg_k1<true><<<blocks, kT, smem, op.stream>>>(bufs[0], bufs[1], bufs[2], links, g, w, kappa, N, ms,
+            k_cg_k1<true><<<blocks, kT, smem, op.stream>>>(bufs[0], bufs[1], bufs[2], e, links, g, w, kappa, N, ms,
                                                           partials, err);
         else
-            k_cg_k1<false><<<blocks, kT, 0, op.stream>>>(bufs[0], bufs[1], bufs[2], links, g, w, kappa, N, ms,
+            k_cg_k1<false><<<blocks, kT, 0, op.stream>>>(bufs[0], bufs[1], bufs[2], e, links, g, w, kappa, N, ms,
                                                         partials, err);
     };
     auto k23 = [&](bool with_s) {
         if (staged && with_s)
-            k_cg_k23<true, true><<<blocks, kT, smem, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w,
+            k_cg_k23<true, true><<<blocks, kT, smem, op.stream>>>(bufs[2], bufs[0], s0, links, g, w,
                                                                  kappa, N, ms, partials, err);
         else if (staged)
-            k_cg_k23<true, false><<<blocks, kT, smem, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w,
+            k_cg_k23<true, false><<<blocks, kT, smem, op.stream>>>(bufs[2], bufs[0], s0, links, g, w,
                                                                   kappa, N, ms, partials, err);
         else if (with_s)
-            k_cg_k23<false, true><<<blocks, kT, 0, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w, kappa,
+            k_cg_k23<false, true><<<blocks, kT, 0, op.stream>>>(bufs[2], bufs[0], s0, links, g, w, kappa,
                                                                N, ms, partials, err);
         else
-            k_cg_k23<false, false><<<blocks, kT, 0, op.stream>>>(bufs[2], bufs[0], s0, bufs[1], e, links, g, w,
+            k_cg_k23<false, false><<<blocks, kT, 0, op.stream>>>(bufs[2], bufs[0], s0, links, g, w,
                                                                 kappa, N, ms, partials, err);
     };
     float4 *S = s0, *R = bufs[0], *P = bufs[1], *T = bufs[2];
@@ -423,7 +443,7 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
         // t = 0: the odd hop of it is 0 and K23b only sums |r|^2 and |s|^2
         float4 *M = op.eo_tmp32.as<float4>();
         DLZ_CUDA_TRY(cudaMemsetAsync(M, 0, (size_t)N * n * sizeof(float4), op.stream));
-        k_cg_eo_k23b<true><<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, w,
+        k_cg_eo_k23b<true><<<blocks, kT, 0, op.stream>>>(T, M, R, S, links, op.gf, w,
                                                          (float)(op.kappa * op.kappa), N, ms, partials);
     } else {
         k23(true);
@@ -434,19 +454,20 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
     auto iteration = [&]() -> int {
         if (op.eo) {
             // even-odd: K1 = odd hop + K1b, K23 = odd hop + K23b (m: the odd work field).
-            // Per even site and RHS, K1 moves 192 reals (r gathered by the hop, m written,
-            // m gathered, r, t, p read, t, p written), K23 216; each pair reads every link
-            // twice (192 reals per even site)
+            // Per even site and RHS, K1 moves 240 reals (r gathered by the hop, m written,
+            // m gathered, r, t, p, e read, t, p, e written), K23 144 (t gathered by the hop,
+            // m written, m gathered, r read and written); each pair reads every link twice
+            // (192 reals per even site)
             float4 *M = op.eo_tmp32.as<float4>();
             const float kappa2 = (float)(op.kappa * op.kappa);
-            op.prof.stencil_start(op.stream, true, g.V, N, 192, 1, 192);
+            op.prof.stencil_start(op.stream, true, g.V, N, 240, 1, 192);
             DLZ_TRY(eo_hop32(op, M, R, 1, false, N));
-            k_cg_eo_k1b<<<blocks, kT, 0, op.stream>>>(R, M, P, T, links, op.gf, w, kappa2, N, ms, partials);
+            k_cg_eo_k1b<<<blocks, kT, 0, op.stream>>>(R, M, P, T, e, links, op.gf, w, kappa2, N, ms, partials);
             op.prof.stencil_stop(op.stream);
             k_cg_alpha<<<N, 256, 0, op.stream>>>(partials, nbq, ms);
-            op.prof.stencil_start(op.stream, true, g.V, N, 216, 2, 192);
+            op.prof.stencil_start(op.stream, true, g.V, N, 144, 2, 192);
             DLZ_TRY(eo_hop32(op, M, T, 1, true, N));
-            k_cg_eo_k23b<false><<<blocks, kT, 0, op.stream>>>(T, M, R, S, P, e, links, op.gf, w, kappa2, N, ms,
+            k_cg_eo_k23b<false><<<blocks, kT, 0, op.stream>>>(T, M, R, S, links, op.gf, w, kappa2, N, ms,
                                                               partials);
             op.prof.stencil_stop(op.stream);
             k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 0, ms);
@@ -454,13 +475,13 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
             DLZ_CUDA_TRY(cudaGetLastError());
             return DLZ_OK;
         }
-        // K1 moves 120 reals per site and RHS (r gathered, t and p read and written) + links
-        op.prof.stencil_start(op.stream, true, g.V, N, 120, 1);
+        // K1 moves 168 reals per site and RHS (r gathered, t, p and e read and written) + links
+        op.prof.stencil_start(op.stream, true, g.V, N, 168, 1);
         k1();
         op.prof.stencil_stop(op.stream);
         k_cg_alpha<<<N, 256, 0, op.stream>>>(partials, nbq, ms);
-        // K23 moves 144 reals per site and RHS (t gathered; r, e read and written; p read)
-        op.prof.stencil_start(op.stream, true, g.V, N, 144, 2);
+        // K23 moves 72 reals per site and RHS (t gathered; r read and written) + links
+        op.prof.stencil_start(op.stream, true, g.V, N, 72, 2);
         k23(false);
         op.prof.stencil_stop(op.stream);
         k_cg_beta<<<N, 256, 0, op.stream>>>(partials, nbq, N, 0, ms);
@@ -492,6 +513,10 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
         }
     }
     ge.sample(op.prof);
+    // the last step's e += alpha p, which the next K1 would have made
+    k_cg_flush_e<<<(unsigned)(((long)N * n + 255) / 256), 256, 0, op.stream>>>(e, P, ms, n, N);
+    op.prof.launches++;
+    DLZ_CUDA_TRY(cudaGetLastError());
     iters += it;
     if (staged) {
         int h_err = 0;
