@@ -54,7 +54,7 @@ REF_FIRST_RHS_MVPS = 26378
 # DRAM bytes (read + write) of one k_cg_k1 launch (16 RHS, 24^3x48), the dominant kernel,
 # from the ncu capture summarised in profiles/k_cg_wilson_24x24x24x48_n16.md; None until
 # taken for the current kernel
-K1_TRAFFIC_BYTES = None
+K1_TRAFFIC_BYTES = 8.30e9
 METRIC = "RHS solved/s to |r|/|b|<1e-10 (Lan-DR(120,60) + D-CG, 49 Gaussian RHS, 24^3x48)"
 UNIT = "RHS/s"
 

@@ -70,7 +70,9 @@ def _compare_dr(m, defl, st, r_or, xg, xo, bnorm, sigma):
     gv, gr = vals[order, 0], vals[order, 1]
     orr = r_or.ritz_residuals[np.argsort(r_or.ritz_values)]
     ok = (gr <= 1e-7) & (orr <= 1e-7)
-    assert ok.sum() >= 1
+    # the same FP64 algorithm converges the same pairs on both sides (allowing one pair
+    # at the threshold), and every pair converged on both sides agrees to 1e-8
+    assert ok.sum() >= max(1, int((orr <= 1e-7).sum()) - 1)
     assert np.all(np.abs(gv[ok] - ov[ok]) <= 1e-8 * np.abs(ov[ok]))
     return gv
 
