@@ -58,30 +58,60 @@ int deflation_finish(Op &op, dlz_defl_s *d) {
     const int k = d->k;
     const long n = 12L * op.g.V;
     if (k == 0) return DLZ_OK;
-    DevBuf AV, tmp, dots;
+    DevBuf AV, tmp, dots, gram;
     DLZ_TRY(AV.alloc((size_t)n * sizeof(double2)));
     DLZ_TRY(tmp.alloc((size_t)n * sizeof(double2)));
     DLZ_TRY(dots.alloc((size_t)k * k * sizeof(double2)));
+    DLZ_TRY(gram.alloc((size_t)k * k * sizeof(double2)));
     const double2 *V = d->V64.as<double2>();
     for (int j = 0; j < k; ++j) {
         double2 *avj = AV.as<double2>();
         DLZ_TRY(apply64(op, avj, V + (size_t)j * n, d->which, tmp.as<double2>()));
         DLZ_TRY(v64::multidot(op, V, n, k, avj, dots.as<double2>() + (size_t)j * k, 1.0));
+        DLZ_TRY(v64::multidot(op, V, n, k, V + (size_t)j * n, gram.as<double2>() + (size_t)j * k, 1.0));
     }
-    std::vector<double2> hd((size_t)k * k);
+    std::vector<double2> hd((size_t)k * k), gd((size_t)k * k);
     DLZ_TRY(d2h_sync(op, hd.data(), dots.p, hd.size() * sizeof(double2)));
-    // dots[j*k + i] = <v_i, A v_j> = H[i][j]; hermitise
+    DLZ_TRY(d2h_sync(op, gd.data(), gram.p, gd.size() * sizeof(double2)));
+    // dots[j*k + i] = <v_i, A v_j> = H[i][j]; hermitise (the same for the Gram matrix)
     d->H.assign((size_t)k * k, zc(0, 0));
+    d->G.assign((size_t)k * k, zc(0, 0));
     for (int i = 0; i < k; ++i)
         for (int j = 0; j < k; ++j) {
             const zc hij(hd[(size_t)j * k + i].x, hd[(size_t)j * k + i].y);
             const zc hji(hd[(size_t)i * k + j].x, hd[(size_t)i * k + j].y);
             d->H[(size_t)i * k + j] = 0.5 * (hij + std::conj(hji));
+            const zc gij(gd[(size_t)j * k + i].x, gd[(size_t)j * k + i].y);
+            const zc gji(gd[(size_t)i * k + j].x, gd[(size_t)i * k + j].y);
+            d->G[(size_t)i * k + j] = 0.5 * (gij + std::conj(gji));
         }
     return deflation_factor(op, d);
 }
 
-// LU factors of H and its eigen-decomposition (the Rayleigh-Ritz pairs).
+// Cholesky factor G = L L^dag of a hermitian positive definite k x k matrix (row-major,
+// L lower triangular); false if G is not positive definite.
+static bool chol_lower(int k, const std::vector<zc> &G, std::vector<zc> &L) {
+    L.assign((size_t)k * k, zc(0, 0));
+    for (int j = 0; j < k; ++j) {
+        double dj = G[(size_t)j * k + j].real();
+        for (int p = 0; p < j; ++p) dj -= std::norm(L[(size_t)j * k + p]);
+        if (!(dj > 0.0)) return false;
+        const double ljj = std::sqrt(dj);
+        L[(size_t)j * k + j] = ljj;
+        for (int i = j + 1; i < k; ++i) {
+            zc s = G[(size_t)i * k + j];
+            for (int p = 0; p < j; ++p) s -= L[(size_t)i * k + p] * std::conj(L[(size_t)j * k + p]);
+            L[(size_t)i * k + j] = s / ljj;
+        }
+    }
+    return true;
+}
+
+// LU factors of H and its eigen-decomposition (the Rayleigh-Ritz pairs).  With a Gram
+// matrix G = V^dag V (a basis orthonormal only to FP32 rounding) the pairs solve
+// H z = value G z, through C = L^-1 H L^-dag (G = L L^dag) and z = L^-dag u: each value is
+// then the Rayleigh quotient of y = V z, and |y| = 1.  The Galerkin projection with
+// H^-1 needs no orthonormality and is unchanged.
 int deflation_factor(Op &, dlz_defl_s *d) {
     const int k = d->k;
     if (k == 0) return DLZ_OK;
@@ -89,13 +119,40 @@ int deflation_factor(Op &, dlz_defl_s *d) {
     d->piv.assign(k, 0);
     if (!lu_factor(k, d->Hlu.data(), d->piv.data()))
         return fail(DLZ_ERR_BREAKDOWN, "deflation: H = V^dag A V is singular");
-    // Rayleigh-Ritz pairs: eigenvectors of the hermitian H via the real
-    // symmetric embedding [[Re H, -Im H], [Im H, Re H]] (each eigenvalue twice).
+    std::vector<zc> L, C = d->H;
+    const bool gen = !d->G.empty();
+    if (gen) {
+        if (!chol_lower(k, d->G, L)) return fail(DLZ_ERR_BREAKDOWN, "deflation: V^dag V is not positive definite");
+        // W = L^-1 H (forward substitution on every column), then C = L^-1 W^dag ...
+        std::vector<zc> W = d->H;
+        for (int c = 0; c < k; ++c)
+            for (int i = 0; i < k; ++i) {
+                zc s = W[(size_t)i * k + c];
+                for (int p = 0; p < i; ++p) s -= L[(size_t)i * k + p] * W[(size_t)p * k + c];
+                W[(size_t)i * k + c] = s / L[(size_t)i * k + i];
+            }
+        // ... C = (L^-1 (L^-1 H)^dag)^dag = L^-1 H L^-dag, hermitian
+        std::vector<zc> Wd((size_t)k * k);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) Wd[(size_t)i * k + j] = std::conj(W[(size_t)j * k + i]);
+        for (int c = 0; c < k; ++c)
+            for (int i = 0; i < k; ++i) {
+                zc s = Wd[(size_t)i * k + c];
+                for (int p = 0; p < i; ++p) s -= L[(size_t)i * k + p] * Wd[(size_t)p * k + c];
+                Wd[(size_t)i * k + c] = s / L[(size_t)i * k + i];
+            }
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j)
+                C[(size_t)i * k + j] = 0.5 * (std::conj(Wd[(size_t)j * k + i]) + Wd[(size_t)i * k + j]);
+    }
+    // Rayleigh-Ritz pairs: eigenvectors of the hermitian C (H itself without a Gram
+    // matrix) via the real symmetric embedding [[Re C, -Im C], [Im C, Re C]] (each
+    // eigenvalue twice).
     const int n2 = 2 * k;
     std::vector<double> E((size_t)n2 * n2), w(n2), Z((size_t)n2 * n2);
     for (int i = 0; i < k; ++i)
         for (int j = 0; j < k; ++j) {
-            const zc h = d->H[(size_t)i * k + j];
+            const zc h = C[(size_t)i * k + j];
             E[(size_t)i * n2 + j] = h.real();
             E[(size_t)i * n2 + k + j] = -h.imag();
             E[(size_t)(k + i) * n2 + j] = h.imag();
@@ -123,6 +180,15 @@ int deflation_factor(Op &, dlz_defl_s *d) {
         d->values.push_back(w[c]);
     }
     if ((int)chosen.size() < k) return fail(DLZ_ERR_NONFINITE, "deflation: eigenvectors of H");
+    if (gen) {
+        // z = L^-dag u (back substitution with the conjugate transpose of L)
+        for (auto &u : chosen)
+            for (int i = k - 1; i >= 0; --i) {
+                zc s = u[i];
+                for (int p = i + 1; p < k; ++p) s -= std::conj(L[(size_t)p * k + i]) * u[p];
+                u[i] = s / L[(size_t)i * k + i];
+            }
+    }
     d->Z.resize((size_t)k * k);
     for (int i = 0; i < k; ++i)
         for (int j = 0; j < k; ++j) d->Z[(size_t)i * k + j] = chosen[j][i];   // column j = vector j

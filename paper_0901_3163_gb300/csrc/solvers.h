@@ -17,6 +17,8 @@ struct dlz_defl_s {
     dlz::DevBuf V64;                            // k internal FP64 vectors
     dlz::DevBuf V32;                            // FP32 copy for the mixed-precision solvers
     std::vector<std::complex<double>> H;        // k x k, row-major
+    std::vector<std::complex<double>> G;        // k x k Gram matrix V_k^dag V_k (empty: V_k
+                                                // orthonormal to FP64 rounding)
     std::vector<std::complex<double>> Hlu;      // LU factors of H
     std::vector<int> piv;
     std::vector<double> values;                 // Rayleigh-Ritz values (ascending)
