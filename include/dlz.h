@@ -107,7 +107,9 @@ typedef struct {
                               in FP64 and projected over the deflation set again (defect
                               correction); 1e-2 (on the 16^3x32 workload 6444 D-MinRes
                               iterations against 9540 with 1e-5: the re-projection
-                              removes the deflated directions FP32 lets back in)        */
+                              removes the deflated directions FP32 lets back in).
+                              D-CG holds it at 2e-3 or more (its inner solve tracks the
+                              residual norm by a recurrence that levels off near 3e-4) */
     int check_every;     /* D-CG / D-MinRes: read the residual on the host every this
                             many iterations; 16                                          */
     int profile;         /* 1: time every stencil launch with CUDA events (stats)  ; 0   */

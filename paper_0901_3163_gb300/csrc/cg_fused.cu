@@ -133,12 +133,14 @@ k_cg_k1(const float4 *__restrict__ R, float4 *__restrict__ P, float4 *__restrict
     if ((int)threadIdx.x < nb && ok) {
         const float bt = st[q].f[1], al = st[q].f[0];
         float2 o[12], t[12], r[12];
+        const PackedLinks<float> lk{links, g.V};
         if constexpr (STAGED) {
             const StagedGather32 ga = staged_gather(R + base, g, s0, stage_sm);
-            wilson_site_g<float, false, false>(s, g, kappa, ga, links, o);
+            wilson_site_g<float, false, false>(s, g, kappa, ga, lk, o);
             ga.get<0, 0>(s, false, r);
         } else {
-            wilson_site<float, false, false>(s, g, kappa, R + base, links, o);
+            const GlobalGather<float> ga{R + base, g.V};
+            wilson_site_g<float, false, false>(s, g, kappa, ga, lk, o);
             Field<float>::load(R + base, g.V, s, r);
         }
         axpy_store(T, base, g.V, s, bt, o, t);
@@ -175,12 +177,14 @@ k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restric
     if ((int)threadIdx.x < nb && ok) {
         const float al = st[q].f[0];
         float2 z[12], tc[12];
+        const PackedLinks<float> lk{links, g.V};
         if constexpr (STAGED) {
             const StagedGather32 ga = staged_gather(T + base, g, s0, stage_sm);
-            wilson_site_g<float, true, true>(s, g, kappa, ga, links, z);
+            wilson_site_g<float, true, true>(s, g, kappa, ga, lk, z);
             if (WITH_S) ga.get<0, 0>(s, false, tc);
         } else {
-            wilson_site<float, true, true>(s, g, kappa, T + base, links, z);
+            const GlobalGather<float> ga{T + base, g.V};
+            wilson_site_g<float, true, true>(s, g, kappa, ga, lk, z);
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -411,10 +415,12 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
     if (staged) DLZ_TRY(cg_prepare());
     auto k1 = [&]() {
         if (staged)
-            k_cg_k1<true><<<blocks, kT, smem, op.stream>>>(bufs[0], bufs[1], bufs[2], e, links, g, w, kappa, N, ms,
+            k_cg_k1<true><<<blocks, kT, smem, op.stream>>>(bufs[0], bufs[1], bufs[2], e, links, g, w, kappa, N,
+                                                          ms,
                                                           partials, err);
         else
-            k_cg_k1<false><<<blocks, kT, 0, op.stream>>>(bufs[0], bufs[1], bufs[2], e, links, g, w, kappa, N, ms,
+            k_cg_k1<false><<<blocks, kT, 0, op.stream>>>(bufs[0], bufs[1], bufs[2], e, links, g, w, kappa, N,
+                                                          ms,
                                                         partials, err);
     };
     auto k23 = [&](bool with_s) {

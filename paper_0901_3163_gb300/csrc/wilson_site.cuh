@@ -107,6 +107,14 @@ __host__ __device__ inline void load_link(const typename Link<T>::vec *__restric
     Link<T>::load(U, V, mu, s, u);
 }
 
+// Where a site function reads its links: (mu, s, u) loads U_mu(s).  PackedLinks reads the
+// Link<T> storage (FP32: two rows, the third rebuilt in registers).
+template <typename T> struct PackedLinks {
+    const typename Link<T>::vec *__restrict__ U;
+    int V;
+    __host__ __device__ inline void operator()(int mu, int s, cx<T> (&u)[9]) const { Link<T>::load(U, V, mu, s, u); }
+};
+
 // Accumulate (1 - gamma_mu) U h-projection of p into acc (forward hop).
 template <typename T, int MU>
 __host__ __device__ inline void hop_fwd(const cx<T> (&p)[12], const cx<T> (&u)[9], T sign,
@@ -208,9 +216,9 @@ template <typename T> struct GlobalGather {
     __host__ __device__ inline void get(int n, bool, cx<T> (&p)[12]) const { Field<T>::load(in, V, n, p); }
 };
 
-template <typename T, int MU, bool G5IN, class G>
+template <typename T, int MU, bool G5IN, class G, class LK>
 __host__ __device__ inline void hop_pair(int s, const int (&c)[4], const Geom &g, int stride, const G &ld,
-                                         const typename Link<T>::vec *__restrict__ U, cx<T> (&acc)[12]) {
+                                         const LK &lk, cx<T> (&acc)[12]) {
     const int L = g.L[MU];
     // forward neighbour and the boundary phase of a hop across the time edge
     const bool wf = c[MU] == L - 1, wb = c[MU] == 0;
@@ -221,19 +229,19 @@ __host__ __device__ inline void hop_pair(int s, const int (&c)[4], const Geom &g
     cx<T> p[12], u[9];
     ld.template get<MU, 1>(sf, wf, p);
     maybe_g5<G5IN>(p);
-    load_link<T>(U, g.V, MU, s, u);
+    lk(MU, s, u);
     hop_fwd<T, MU>(p, u, phf, acc);
     ld.template get<MU, -1>(sb, wb, p);
     maybe_g5<G5IN>(p);
-    load_link<T>(U, g.V, MU, sb, u);
+    lk(MU, sb, u);
     hop_bwd<T, MU>(p, u, phb, acc);
 }
 
 // out(s) = [gamma5]^G5OUT (1 - kappa H) [gamma5]^G5IN in, at one site, the input read
-// through the gather ld.
-template <typename T, bool G5IN, bool G5OUT, class G>
-__host__ __device__ inline void wilson_site_g(int s, const Geom &g, T kappa, const G &ld,
-                                              const typename Link<T>::vec *__restrict__ U, cx<T> (&out)[12]) {
+// through the gather ld and the links through lk.
+template <typename T, bool G5IN, bool G5OUT, class G, class LK>
+__host__ __device__ inline void wilson_site_g(int s, const Geom &g, T kappa, const G &ld, const LK &lk,
+                                              cx<T> (&out)[12]) {
     int c[4];
     int r = s;
     c[0] = r % g.L[0]; r /= g.L[0];
@@ -244,10 +252,10 @@ __host__ __device__ inline void wilson_site_g(int s, const Geom &g, T kappa, con
     cx<T> acc[12];
 #pragma unroll
     for (int a = 0; a < 12; ++a) acc[a] = mk<T>(0, 0);
-    hop_pair<T, 0, G5IN>(s, c, g, 1, ld, U, acc);
-    hop_pair<T, 1, G5IN>(s, c, g, st1, ld, U, acc);
-    hop_pair<T, 2, G5IN>(s, c, g, st2, ld, U, acc);
-    hop_pair<T, 3, G5IN>(s, c, g, st3, ld, U, acc);
+    hop_pair<T, 0, G5IN>(s, c, g, 1, ld, lk, acc);
+    hop_pair<T, 1, G5IN>(s, c, g, st1, ld, lk, acc);
+    hop_pair<T, 2, G5IN>(s, c, g, st2, ld, lk, acc);
+    hop_pair<T, 3, G5IN>(s, c, g, st3, ld, lk, acc);
     ld.template get<0, 0>(s, false, out);
     maybe_g5<G5IN>(out);
 #pragma unroll
@@ -264,7 +272,8 @@ __host__ __device__ inline void wilson_site(int s, const Geom &g, T kappa,
                                             const typename Field<T>::vec *__restrict__ in,
                                             const typename Link<T>::vec *__restrict__ U, cx<T> (&out)[12]) {
     const GlobalGather<T> ld{in, g.V};
-    wilson_site_g<T, G5IN, G5OUT>(s, g, kappa, ld, U, out);
+    const PackedLinks<T> lk{U, g.V};
+    wilson_site_g<T, G5IN, G5OUT>(s, g, kappa, ld, lk, out);
 }
 
 }  // namespace dlz

@@ -370,3 +370,19 @@ def test_mixed_dcg_staged_gathers_bit_identical(m, monkeypatch, planes):
         assert sg[i].converged == 1 and ss[i].converged == 1
         assert sg[i].iterations == ss[i].iterations
     assert torch.equal(Xg, Xs)
+
+
+def test_mixed_dcg_inner_tolerance_below_the_recurrence_floor(m, case):
+    """The fused FP32 CG tracks |s| by a scalar recurrence whose rounding levels off near a
+    3e-4 reduction; an inner tolerance far below that (reliable_delta 1e-7) must not keep
+    the inner solve running to max_iter (D-CG holds it at 2e-3 or more), and every
+    solution still verifies to 1e-10."""
+    U, op, b = case
+    Aq, D, Dd, Ad = _ops(U, KAPPA)
+    B = synth.gaussian_spinors(DIMS, [41, 42])
+    p = m.params_default(m=40, k=10, tol=1e-10, max_iter=20000, precision=m.F32, reliable_delta=1e-7)
+    X, sts = m.dcg(op, None, torch.from_numpy(B).cuda(), p)
+    for i in range(2):
+        bi = B[i].reshape(-1)
+        assert sts[i].converged == 1 and sts[i].iterations < 20000
+        assert np.linalg.norm(bi - D(X[i].cpu().numpy().reshape(-1))) <= 1.01e-10 * np.linalg.norm(bi)
