@@ -52,8 +52,8 @@ C2_DR_CYCLES = 150
 REF_ITERS_PER_RHS = 2384
 REF_FIRST_RHS_MVPS = 26378
 # DRAM bytes (read + write) of one k_cg_k1 launch (16 RHS, 24^3x48), the dominant kernel,
-# from the ncu capture summarised in profiles/k_cg_wilson_24x24x24x48_n16.md; None until
-# taken for the current kernel
+# from one single-pass ncu capture of the kernel at this size (summarised under
+# profiles/); None until taken for the current kernel
 K1_TRAFFIC_BYTES = 8.30e9
 METRIC = "RHS solved/s to |r|/|b|<1e-10 (Lan-DR(120,60) + D-CG, 49 Gaussian RHS, 24^3x48)"
 UNIT = "RHS/s"
@@ -277,7 +277,7 @@ def run_ours(args):
                            "e += alpha p_old; 16 RHS per launch)",
                            args.k1_traffic,
                            "ncu capture of the current kernel, one launch at this size "
-                           "(profiles/k_cg_wilson_24x24x24x48_n16.md)" if args.k1_traffic else
+                           "(summary under profiles/)" if args.k1_traffic else
                            "not captured for the current kernel")
     roof_k23 = kernel_roofline(pst, 2, peaks, src,
                                "k_cg_k23 (fused FP32 CGNR: t gathered, r -= alpha D^dag t; 16 RHS per launch)")

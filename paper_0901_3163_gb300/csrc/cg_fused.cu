@@ -154,8 +154,10 @@ k_cg_k1(const float4 *__restrict__ R, float4 *__restrict__ P, float4 *__restrict
 // K23: r -= alpha D^dag t; partial |r|^2.  Gathers t only.  WITH_S (the first launch of
 // a solve, alpha = 0): also s -= alpha t and the partial |s|^2; later |s|^2 follows from
 // the scalar recurrence in k_cg_beta and s itself is not needed.
+// (7 blocks of 128 threads per SM: 0.757 against 0.801 ms per launch with 6, on 24^3 x 48
+// with 16 RHS; K1, which moves more vectors, is best at 6: 1.33 against 1.35 ms)
 template <bool STAGED, bool WITH_S>
-__global__ void __launch_bounds__(kT, STAGED ? 3 : 6)
+__global__ void __launch_bounds__(kT, STAGED ? 3 : 7)
 k_cg_k23(const float4 *__restrict__ T, float4 *__restrict__ R, float4 *__restrict__ S,
          const float4 *__restrict__ links, Geom g, SlabWalk w, float kappa, int N,
          const CgFusedState *__restrict__ st, double *__restrict__ partials, int *__restrict__ err) {
