@@ -37,8 +37,8 @@
  * C++ exception crosses the ABI.  dlz_strerror() names a code,
  * dlz_last_error() gives the message of the last failure on this thread.
  *
- * Environment (read at the call; none changes a result, apart from DLZ_WAIT_LIMIT's
- * error path):
+ * Environment (read at the call; none changes a result beyond the rounding of block
+ * sums, apart from DLZ_WAIT_LIMIT's error path):
  *   DLZ_NO_GRAPHS=1   launch kernels one by one instead of replaying CUDA graphs
  *                     (read when an operator is created);
  *   DLZ_TRACE=1       per-cycle and per-phase timing lines on stderr;
@@ -48,7 +48,14 @@
  *   DLZ_MULTI_FORM=graph|persistent  fix the launch form of dlz_batch_dminres
  *                     (see dlz_batch_last_choice); both forms give the same bits;
  *   DLZ_WAIT_LIMIT=n  polls before a grid-barrier wait of the persistent form gives up
- *                     (default 2^24, about a second); a test hook for the timeout path.
+ *                     (default 2^24, about a second); a test hook for the timeout path;
+ *   DLZ_SLAB=n        z-planes per slab of the block walk of the batched FP32 stencils
+ *                     (default: the largest divisor of Lz whose slab's traffic fits in
+ *                     36 MB; Lz is the plain site order); the block sums, and so the
+ *                     rounding, follow the blocks;
+ *   DLZ_CG_STAGE=1    the fused CGNR kernels copy their gather ranges into shared
+ *                     memory first (bulk asynchronous copies); same bits as the default,
+ *                     which reads the neighbours from global memory and is faster.
  */
 #ifndef DLZ_H
 #define DLZ_H
