@@ -34,12 +34,14 @@ struct SlabWalk {
 
 // first site s0 and site count nb of site block sb (nb = 0 for the spare blocks of a
 // short last z-slab)
-__device__ inline void slab_block(const SlabWalk &w, int sb, int &s0, int &nb) {
+__host__ __device__ inline void slab_block(const SlabWalk &w, int sb, int &s0, int &nb) {
     const int j = sb / w.bps, off = (sb % w.bps) * kSlabBlock;
     const int t = j % w.Lt, z0 = (j / w.Lt) * w.bz;
-    const int len = min(w.bz, w.Lz - z0) * w.plane;
+    const int planes = w.bz < w.Lz - z0 ? w.bz : w.Lz - z0;
+    const int len = planes * w.plane;
     s0 = (t * w.Lz + z0) * w.plane + off;
-    nb = max(0, min(kSlabBlock, len - off));
+    const int rest = len - off;
+    nb = rest <= 0 ? 0 : (rest < kSlabBlock ? rest : kSlabBlock);
 }
 
 // The walk with slabs of bz planes
