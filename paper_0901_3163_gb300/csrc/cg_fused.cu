@@ -511,6 +511,12 @@ int cgnr_fused_batch(Op &op, int N, float4 *s0, float4 *e, float4 *const bufs[5]
         it += 6;
         if (it % 12 == 0 || it >= p.max_iter - iters) {
             DLZ_TRY(d2h_sync(op, hsv.data(), ms, N * sizeof(CgFusedState)));
+            if (staged) {
+                // a staging wait that gave up leaves its block's sums out: stop at once
+                int h_err = 0;
+                DLZ_TRY(d2h_sync(op, &h_err, err, sizeof(int)));
+                if (h_err) break;
+            }
             bool all = true;
             for (int q = 0; q < N; ++q) {
                 if (!std::isfinite(hsv[q].ss) || !std::isfinite(hsv[q].gam))
