@@ -1,5 +1,5 @@
 """Host logic of bench.py that needs no GPU: the clock/throttle sampler (against a fake
-nvidia-smi) and the roofline peak source."""
+nvidia-smi), the roofline peak source and the roofline arithmetic."""
 import json
 import os
 import stat
@@ -57,3 +57,25 @@ def test_peaks_measured_or_fallback(tmp_path, monkeypatch):
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6674.2, "bf16_tflops": 2100.0}))
     peaks, src = bench._peaks()
     assert src == "measured" and peaks["hbm_gbs"] == 6674.2
+
+
+class _FakeStats:
+    def __init__(self, ms, nbytes, n):
+        self.kernel_ms = [0.0, ms, 0.0]
+        self.kernel_bytes = [0.0, nbytes, 0.0]
+        self.kernel_launches = [0, n, 0]
+
+
+def test_kernel_roofline_is_algorithmic_bytes_over_event_time():
+    # two RHS entries of one batch share its totals: 3 launches of 7.26 GB in 4.0 ms in all
+    stats = [_FakeStats(2.0, 3 * 7.26e9 / 2, 2), _FakeStats(2.0, 3 * 7.26e9 / 2, 1)]
+    peaks = {"hbm_gbs": 6776.3}
+    r = bench.kernel_roofline(stats, 1, peaks, "measured", "k", traffic=8.3e9, traffic_src="ncu")
+    assert r["launches_timed"] == 3
+    assert abs(r["avg_launch_ms"] - 4.0 / 3) < 1e-5          # reported to 5 decimals
+    assert abs(r["bytes_per_launch"] - 7.26e9) < 1
+    assert abs(r["achieved"] - 7.26e9 / (4.0e-3 / 3) / 1e9) < 0.1
+    assert abs(r["frac"] - r["achieved"] / 6776.3) < 1e-4
+    assert r["traffic"] == 8.3e9 and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    # no timed launch of that kind: no roofline
+    assert bench.kernel_roofline([_FakeStats(0.0, 0.0, 0)], 1, peaks, "measured", "k") is None
