@@ -510,6 +510,16 @@ int dlz_host_restart_plan(int harmonic, int m, int k, const double *Tbar, const 
  */
 int dlz_host_zgeev(int n, const double *A, double *w, double *Z);
 int dlz_host_zlstsq(int rows, int cols, const double *A, const double *c, double *y, double *q);
+/*
+ * The Rayleigh-Ritz step of a deflation set (Sec. 2: the eigenvectors handed from the
+ * first right-hand side to the others), exported for testing; no GPU needed.  H is the
+ * k x k hermitian projection V^dag A V, G the Gram matrix V^dag V of a basis that is
+ * orthonormal only to rounding (NULL: orthonormal), both complex interleaved row-major.
+ * values[k] (ascending) and Z (k x k complex, column j for values[j]; may be NULL) solve
+ * H z = value G z with z^dag G z = 1, by a Cholesky factor of G and the eigenvectors of
+ * L^-1 H L^-dag.  DLZ_ERR_BREAKDOWN if G is not positive definite.
+ */
+int dlz_host_rayleigh_ritz(int k, const double *H, const double *G, double *values, double *Z);
 
 #ifdef __cplusplus
 }

@@ -107,24 +107,19 @@ static bool chol_lower(int k, const std::vector<zc> &G, std::vector<zc> &L) {
     return true;
 }
 
-// LU factors of H and its eigen-decomposition (the Rayleigh-Ritz pairs).  With a Gram
-// matrix G = V^dag V (a basis orthonormal only to FP32 rounding) the pairs solve
-// H z = value G z, through C = L^-1 H L^-dag (G = L L^dag) and z = L^-dag u: each value is
-// then the Rayleigh quotient of y = V z, and |y| = 1.  The Galerkin projection with
-// H^-1 needs no orthonormality and is unchanged.
-int deflation_factor(Op &, dlz_defl_s *d) {
-    const int k = d->k;
-    if (k == 0) return DLZ_OK;
-    d->Hlu = d->H;
-    d->piv.assign(k, 0);
-    if (!lu_factor(k, d->Hlu.data(), d->piv.data()))
-        return fail(DLZ_ERR_BREAKDOWN, "deflation: H = V^dag A V is singular");
-    std::vector<zc> L, C = d->H;
-    const bool gen = !d->G.empty();
+// Rayleigh-Ritz pairs of a hermitian k x k H (row-major): the eigenpairs of H, or with a
+// Gram matrix G = V^dag V (a basis orthonormal only to FP32 rounding; G may be null)
+// those of H z = value G z, through C = L^-1 H L^-dag (G = L L^dag) and z = L^-dag u, so
+// that each value is the Rayleigh quotient of y = V z and |y| = 1.  values ascending;
+// Z row-major with column j the vector of values[j].  0, or a DLZ_ERR code with a message.
+int rayleigh_ritz(int k, const std::vector<zc> &H, const std::vector<zc> *G, std::vector<double> &values,
+                  std::vector<zc> &Zout) {
+    std::vector<zc> L, C = H;
+    const bool gen = G && !G->empty();
     if (gen) {
-        if (!chol_lower(k, d->G, L)) return fail(DLZ_ERR_BREAKDOWN, "deflation: V^dag V is not positive definite");
+        if (!chol_lower(k, *G, L)) return fail(DLZ_ERR_BREAKDOWN, "deflation: V^dag V is not positive definite");
         // W = L^-1 H (forward substitution on every column), then C = L^-1 W^dag ...
-        std::vector<zc> W = d->H;
+        std::vector<zc> W = H;
         for (int c = 0; c < k; ++c)
             for (int i = 0; i < k; ++i) {
                 zc s = W[(size_t)i * k + c];
@@ -145,9 +140,8 @@ int deflation_factor(Op &, dlz_defl_s *d) {
             for (int j = 0; j < k; ++j)
                 C[(size_t)i * k + j] = 0.5 * (std::conj(Wd[(size_t)j * k + i]) + Wd[(size_t)i * k + j]);
     }
-    // Rayleigh-Ritz pairs: eigenvectors of the hermitian C (H itself without a Gram
-    // matrix) via the real symmetric embedding [[Re C, -Im C], [Im C, Re C]] (each
-    // eigenvalue twice).
+    // eigenvectors of the hermitian C via the real symmetric embedding
+    // [[Re C, -Im C], [Im C, Re C]] (each eigenvalue twice)
     const int n2 = 2 * k;
     std::vector<double> E((size_t)n2 * n2), w(n2), Z((size_t)n2 * n2);
     for (int i = 0; i < k; ++i)
@@ -160,8 +154,7 @@ int deflation_factor(Op &, dlz_defl_s *d) {
         }
     if (!sym_eig(n2, E.data(), w.data(), Z.data()))
         return fail(DLZ_ERR_NONFINITE, "deflation: eigensolve of H failed");
-    d->values.clear();
-    d->Z.clear();
+    values.clear();
     std::vector<std::vector<zc>> chosen;
     for (int c = 0; c < n2 && (int)chosen.size() < k; ++c) {
         std::vector<zc> z(k);
@@ -177,7 +170,7 @@ int deflation_factor(Op &, dlz_defl_s *d) {
         if (nr < 0.5) continue;   // the twin of an eigenvector already taken
         for (int i = 0; i < k; ++i) z[i] /= nr;
         chosen.push_back(z);
-        d->values.push_back(w[c]);
+        values.push_back(w[c]);
     }
     if ((int)chosen.size() < k) return fail(DLZ_ERR_NONFINITE, "deflation: eigenvectors of H");
     if (gen) {
@@ -189,9 +182,22 @@ int deflation_factor(Op &, dlz_defl_s *d) {
                 u[i] = s / L[(size_t)i * k + i];
             }
     }
-    d->Z.resize((size_t)k * k);
+    Zout.resize((size_t)k * k);
     for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) d->Z[(size_t)i * k + j] = chosen[j][i];   // column j = vector j
+        for (int j = 0; j < k; ++j) Zout[(size_t)i * k + j] = chosen[j][i];   // column j = vector j
+    return DLZ_OK;
+}
+
+// LU factors of H (the Galerkin projection, which needs no orthonormality) and the
+// Rayleigh-Ritz pairs of the set.
+int deflation_factor(Op &, dlz_defl_s *d) {
+    const int k = d->k;
+    if (k == 0) return DLZ_OK;
+    d->Hlu = d->H;
+    d->piv.assign(k, 0);
+    if (!lu_factor(k, d->Hlu.data(), d->piv.data()))
+        return fail(DLZ_ERR_BREAKDOWN, "deflation: H = V^dag A V is singular");
+    DLZ_TRY(rayleigh_ritz(k, d->H, &d->G, d->values, d->Z));
     d->residuals.clear();   // computed on first request (deflation_residuals)
     return DLZ_OK;
 }
@@ -600,3 +606,26 @@ int dcg64(Op &op, const dlz_defl_s *d, const double2 *b_in, double2 *x_out, cons
 }
 
 }  // namespace dlz
+
+// Host entry of the Rayleigh-Ritz step (dlz.h: dlz_host_rayleigh_ritz).
+extern "C" int dlz_host_rayleigh_ritz(int k, const double *H, const double *G, double *values, double *Z) {
+    if (k < 1 || !H || !values) return dlz::fail(DLZ_ERR_BADARG, "rayleigh_ritz: k >= 1, H and values required");
+    std::vector<std::complex<double>> h((size_t)k * k), g;
+    for (size_t i = 0; i < h.size(); ++i) h[i] = std::complex<double>(H[2 * i], H[2 * i + 1]);
+    if (G) {
+        g.resize((size_t)k * k);
+        for (size_t i = 0; i < g.size(); ++i) g[i] = std::complex<double>(G[2 * i], G[2 * i + 1]);
+    }
+    std::vector<double> w;
+    std::vector<std::complex<double>> z;
+    const int rc = dlz::rayleigh_ritz(k, h, G ? &g : nullptr, w, z);
+    if (rc != DLZ_OK) return rc;
+    for (int j = 0; j < k; ++j) values[j] = w[j];
+    if (Z)
+        for (size_t i = 0; i < z.size(); ++i) {
+            Z[2 * i] = z[i].real();
+            Z[2 * i + 1] = z[i].imag();
+        }
+    return DLZ_OK;
+}
+

@@ -41,6 +41,11 @@ struct dlz_op_s {
 
 namespace dlz {
 
+// Rayleigh-Ritz pairs of a hermitian k x k H, with the Gram matrix G of a basis that is
+// not orthonormal (G null or empty: the plain eigenpairs of H)
+int rayleigh_ritz(int k, const std::vector<std::complex<double>> &H, const std::vector<std::complex<double>> *G,
+                  std::vector<double> &values, std::vector<std::complex<double>> &Z);
+
 int dr_solve(Op &op, bool harmonic, const double2 *b, double2 *x, const dlz_params &p,
              dlz_defl_s **defl_out, dlz_stats &st);
 // x_init (may alias x, may be null): starting guess, corrected by the projection of

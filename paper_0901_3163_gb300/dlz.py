@@ -121,6 +121,7 @@ _SIGS = {
     "dlz_host_sym_extremes": ([_ip, _vp, _vp, _vp], _ip),
     "dlz_host_lstsq": ([_ip, _ip, _vp, _vp, _vp, _vp], _ip),
     "dlz_host_zgeev": ([_ip, _vp, _vp, _vp], _ip),
+    "dlz_host_rayleigh_ritz": ([_ip, _vp, _vp, _vp, _vp], _ip),
     "dlz_host_zlstsq": ([_ip, _ip, _vp, _vp, _vp, _vp], _ip),
     "dlz_host_restart_plan": ([_ip, _ip, _ip, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _ip),
 }
@@ -594,6 +595,20 @@ def host_zgeev(A):
     w = np.empty(n, dtype=np.complex128)
     Z = np.empty((n, n), dtype=np.complex128)
     _check(lib.dlz_host_zgeev(n, A.ctypes.data, w.ctypes.data, Z.ctypes.data))
+    return w, Z
+
+
+def host_rayleigh_ritz(H, G=None):
+    """Rayleigh-Ritz pairs of a deflation set's H = V^dag A V, with the Gram matrix G =
+    V^dag V of a basis orthonormal only to rounding (None: orthonormal): ascending values
+    and vectors z (columns) with H z = value G z, z^dag G z = 1 (library host code)."""
+    H = np.ascontiguousarray(H, dtype=np.complex128)
+    k = H.shape[0]
+    Gc = None if G is None else np.ascontiguousarray(G, dtype=np.complex128)
+    w = np.empty(k, dtype=np.float64)
+    Z = np.empty((k, k), dtype=np.complex128)
+    _check(lib.dlz_host_rayleigh_ritz(k, H.ctypes.data, None if Gc is None else Gc.ctypes.data, w.ctypes.data,
+                                      Z.ctypes.data))
     return w, Z
 
 
