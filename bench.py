@@ -140,10 +140,19 @@ def aggregate_ranks(ms, solved, world, device):
     return float(mx[0]), float(t[1])
 
 
-def workload_inputs(kappa=None, name=WORKLOAD):
+def workload_rhs_count(name=WORKLOAD):
+    """Right-hand sides in one step of a named workload."""
+    import synth
+    w = synth.WORKLOADS[name]
+    return 12 if "point_sources" in w else 1 + len(w["rhs_seeds"])
+
+
+def workload_inputs(kappa=None, name=WORKLOAD, rhs=None):
     """Links, kappa and right-hand sides of a named workload (synth.WORKLOADS).
     24^3x48: B[0] is the first RHS (seed 0), B[1:] the 48 D-CG RHS.
-    16^3x32: the 12 spin-colour point sources at the origin."""
+    16^3x32: the 12 spin-colour point sources at the origin.
+    rhs: the indices (into that list) of the right-hand sides to make, in that order;
+    None makes all of them (49 x 127 MB on 24^3x48)."""
     import numpy as np
 
     import synth
@@ -153,12 +162,15 @@ def workload_inputs(kappa=None, name=WORKLOAD):
     if kappa is None:
         kappa = synth.kappa_for(dims, w["gauge_seed"])
     V = synth.volume(dims)
+    idx = list(range(workload_rhs_count(name))) if rhs is None else list(rhs)
+    B = np.zeros((len(idx), V, 4, 3), dtype=np.complex128)
     if "point_sources" in w:
-        B = np.zeros((12, V, 4, 3), dtype=np.complex128)
-        for a in range(12):
-            B[a] = synth.point_source(dims, a // 3, a % 3)
+        for j, a in enumerate(idx):
+            B[j] = synth.point_source(dims, a // 3, a % 3)
     else:
-        B = synth.gaussian_spinors(dims, (w["first_rhs_seed"],) + tuple(w["rhs_seeds"]))
+        seeds = (w["first_rhs_seed"],) + tuple(w["rhs_seeds"])
+        for j, a in enumerate(idx):
+            B[j] = synth.gaussian_spinor(dims, seeds[a])
     return w, dims, U, kappa, B
 
 
@@ -598,10 +610,10 @@ def cpu_baseline(iters_per_rhs, first_rhs_mvps, nrhs, budget_s=20.0, source=""):
     import numpy as np
 
     from oracle import cwilson, krylov
-    w, dims, U, kappa, B = workload_inputs()
+    w, dims, U, kappa, B = workload_inputs(rhs=(1,))
     D = cwilson.operator(U, kappa, dims, "D")
     Dd = cwilson.operator(U, kappa, dims, "Ddag")
-    b = B[1].reshape(-1)
+    b = B[0].reshape(-1)
     it = 2
     while True:
         t0 = time.perf_counter()
@@ -629,10 +641,10 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import cwilson, krylov
-    w, dims, U, kappa, B = workload_inputs(args.kappa)
+    w, dims, U, kappa, B = workload_inputs(args.kappa, rhs=(1,))
     D = cwilson.operator(U, kappa, dims, "D")
     Dd = cwilson.operator(U, kappa, dims, "Ddag")
-    b = B[1].reshape(-1)
+    b = B[0].reshape(-1)
     it = args.ref_iters
     for _ in range(args.warmup):
         krylov.cgnr(D, Dd, b, tol=1e-30, maxiter=2)
@@ -641,7 +653,7 @@ def run_reference(args):
         krylov.cgnr(D, Dd, b, tol=1e-30, maxiter=it)
     el = time.perf_counter() - t0
     mv = args.steps * (2 * it + 2)
-    nrhs = B.shape[0]
+    nrhs = workload_rhs_count()
     step_mvps = REF_FIRST_RHS_MVPS + (nrhs - 1) * (2 * REF_ITERS_PER_RHS + 2)
     value = nrhs / (el / mv * step_mvps)
     threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
@@ -720,9 +732,9 @@ def run_ncu_case(args):
         # 24^3x48 lattice itself (cg24, ~7 GB); FP32 CG on the normal equations without
         # deflation, 48 iterations (inputs larger than L2)
         if args.ncu_case == "cg24":
-            w2, dims, U, kappa, _ = workload_inputs(args.kappa)
+            w2, dims, U, kappa, _ = workload_inputs(args.kappa, rhs=())
         else:
-            w2, dims, U, kappa, _ = workload_inputs(name=C2)
+            w2, dims, U, kappa, _ = workload_inputs(name=C2, rhs=())
         mk = dlz.create_operator_eo if args.ncu_case == "cg-eo" else dlz.create_operator
         op = mk(dims, torch.from_numpy(U).cuda(), kappa)
         B = synth.gaussian_spinors(dims, list(range(1, 17)))
@@ -839,7 +851,7 @@ def run_saturation(args):
 
     import synth
     from paper_0901_3163_gb300 import dlz
-    w, dims, U, kappa, _ = workload_inputs(name=C2)
+    w, dims, U, kappa, _ = workload_inputs(name=C2, rhs=())
     op = dlz.create_operator(dims, torch.from_numpy(U).cuda(), kappa)
     b0 = torch.from_numpy(synth.gaussian_spinor(dims, 0)).cuda()
     B = torch.from_numpy(synth.gaussian_spinors(dims, (1, 2, 3, 4))).cuda()

@@ -1,5 +1,6 @@
 """Host logic of bench.py that needs no GPU: the clock/throttle sampler (against a fake
-nvidia-smi), the roofline peak source and the roofline arithmetic."""
+nvidia-smi), the roofline peak source and the roofline arithmetic, the workload's
+right-hand sides, and the reference arm's JSON line (the oracle on the host)."""
 import json
 import os
 import stat
@@ -79,3 +80,45 @@ def test_kernel_roofline_is_algorithmic_bytes_over_event_time():
     assert r["traffic"] == 8.3e9 and r["bound"] == "hbm" and r["unit"] == "GB/s"
     # no timed launch of that kind: no roofline
     assert bench.kernel_roofline([_FakeStats(0.0, 0.0, 0)], 1, peaks, "measured", "k") is None
+
+
+def test_workload_inputs_subset_equals_the_full_list():
+    # the legs that need one right-hand side make only that one; it is the same vector
+    import numpy as np
+
+    import synth
+    _, dims, _, _, B = bench.workload_inputs(name=bench.C2)
+    _, _, _, _, S = bench.workload_inputs(name=bench.C2, rhs=(7, 0))
+    assert B.shape[0] == bench.workload_rhs_count(bench.C2) == 12
+    assert np.array_equal(S, B[[7, 0]])
+    _, _, _, _, E = bench.workload_inputs(name=bench.C2, rhs=())
+    assert E.shape == (0,) + B.shape[1:]
+    assert bench.workload_rhs_count() == 49
+    small = "wilson_4x4x4x4"
+    w = synth.WORKLOADS[small]
+    _, dims, _, _, G = bench.workload_inputs(name=small)
+    assert G.shape[0] == bench.workload_rhs_count(small) == 5
+    assert np.array_equal(G[0], synth.gaussian_spinor(dims, w["first_rhs_seed"]))
+    assert np.array_equal(G[1:], synth.gaussian_spinors(dims, w["rhs_seeds"]))
+    _, _, _, _, one = bench.workload_inputs(name=small, rhs=(1,))
+    assert np.array_equal(one, G[1:2])
+
+
+def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
+    # one oracle CGNR iteration on the 24^3x48 workload: the line the contract asks for
+    import argparse
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    bench.run_reference(argparse.Namespace(steps=1, warmup=1, ref_iters=1, kappa=None))
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert out["impl"] == "reference" and out["metric"] == bench.METRIC and out["unit"] == bench.UNIT
+    assert out["value"] > 0 and out["higher_is_better"] is True and out["n_gpus"] == 1
+    assert out["steps"] == 1 and out["warmup"] == 1 and out["dtype"] == "f64"
+    assert out["config"]["workload"] == bench.WORKLOAD and out["config"]["rhs"] == 49
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == out["value"] and cb["cores"] >= 1 and cb["sample"]
+    e2e = out["e2e"]
+    assert e2e["value"] == out["value"] and e2e["unit"] == out["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
