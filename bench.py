@@ -942,7 +942,8 @@ def run_multi_lattice(args):
     print(json.dumps(out), flush=True)
 
 
-def main():
+def parser():
+    """The command line of bench.py."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
@@ -980,7 +981,11 @@ def main():
     ap.add_argument("--ls-steps", type=int, default=400)
     ap.add_argument("--kappa", type=float, default=None,
                     help="override the tabulated kappa (profiling and trial runs only)")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = parser().parse_args()
     if args.stencil_only:
         run_stencil_only(args)
     elif args.ncu_case is not None:

@@ -122,3 +122,34 @@ def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
     e2e = out["e2e"]
     assert e2e["value"] == out["value"] and e2e["unit"] == out["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def _profile_commands():
+    """Every `python bench.py ...` command line in the ncu summaries under profiles/
+    (continuation lines joined; redirections and what follows `&&` cut off)."""
+    import glob
+    import shlex
+    out = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read().replace("\\\n", " ")
+        for line in text.splitlines():
+            i = line.find("python bench.py")
+            while i >= 0:
+                rest = line[i + len("python bench.py"):]
+                for stop in ("&&", ">", "|", "`"):
+                    j = rest.find(stop)
+                    if j >= 0:
+                        rest = rest[:j]
+                out.append((os.path.basename(path), shlex.split(rest)))
+                i = line.find("python bench.py", i + 1)
+    return out
+
+
+def test_profile_commands_parse_with_the_current_command_line():
+    cmds = _profile_commands()
+    # each summary that times a bench case gives its command
+    assert {name for name, _ in cmds} >= {
+        "k_cg_wilson_24x24x24x48_n16.md", "k_eo_cgnr_wilson_16x16x16x32_n16.md",
+        "k_tc_combine_dots_wilson_16x16x16x32.md", "launches_wilson_24x24x24x48_step.md"}
+    for name, argv in cmds:
+        bench.parser().parse_args(argv)
