@@ -221,3 +221,50 @@ def kappa_newton(U, dims, a, sa, b, sb, bc_t=1, rtol=1e-4, m=100, k=20, max_cycl
             nxt = a + (sa - TARGET) * (b - a) / (sa - sb)
         kap = nxt
     raise RuntimeError("kappa_newton: no convergence within max_evals evaluations")
+
+
+def verify_sigma(U, kappa, dims, seed, rel_bound=1e-3, gap_guess=3e-4, m=100, k=20, bc_t=1,
+                 max_cycles=400, log=None):
+    """Independent re-verification of a stored kappa: one more eigensolve of
+    Q = gamma5 D at that kappa, sharing nothing with the search that found it.
+
+    MinRes-DR(m, k) as an eigensolver, cold-started from a fresh complex Gaussian
+    vector drawn with `seed`, runs until the harmonic Ritz pair nearest zero has a
+    residual r with r^2 / gap_guess <= rel_bound * |theta| (the Kato-Temple bound
+    with an assumed gap), or max_cycles.  Then, from its unit Ritz vector y, the
+    Rayleigh quotient rho = <y, Q y> and the residual ||Q y - rho y|| are formed
+    anew with one more application of Q, and the gap is the distance from rho to
+    the nearest other kept value.  For hermitian Q an eigenvalue lies within
+    residual^2 / gap of rho (Kato-Temple) and within the residual itself.
+    Returns dict(kappa, sigma = |rho|, residual, gap, bound, cycles, mvps, seed)."""
+    from .krylov import minresdr
+    V = int(np.prod(dims))
+    n = V * 12
+    rng = np.random.default_rng(seed)
+    v0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    A = cwilson.operator(U, kappa, dims, "Q", bc_t)
+
+    def stop(theta, res):
+        return res * res / gap_guess <= rel_bound * abs(theta)
+
+    def progress(cycle, mvps, rel, theta, res):
+        if log and cycle % 5 == 0:
+            i = int(np.argmin(np.abs(theta)))
+            log(f"   cycle {cycle} mvps {mvps} theta {theta[i]:.9e} res {res[i]:.2e}")
+
+    r = minresdr(A, v0, m, k, tol=0.0, max_cycles=max_cycles, eig_stop=stop, progress=progress)
+    vals = np.asarray(r.ritz_values)
+    i = int(np.argmin(np.abs(vals)))
+    y = r.ritz_vectors[:, i]
+    y = y / np.linalg.norm(y)
+    Qy = A(y)
+    rho = float(np.vdot(y, Qy).real)
+    res = float(np.linalg.norm(Qy - rho * y))
+    others = np.delete(vals, i)
+    gap = float(np.min(np.abs(others - rho))) if others.size else 1.0
+    out = dict(kappa=float(kappa), sigma=abs(rho), residual=res, gap=gap, bound=res * res / gap,
+               cycles=int(r.cycles), mvps=int(r.info.mvps) + 1, seed=int(seed))
+    if log:
+        log(f"verify kappa={kappa:.12f} sigma={abs(rho):.12e} res={res:.2e} gap={gap:.2e} "
+            f"bound={res * res / gap:.2e} cycles={r.cycles}")
+    return out

@@ -76,3 +76,34 @@ def test_entry_meets_the_rule_with_its_error_bound(key):
     assert abs(lo / 1e-3 - 1) < 0.10 and abs(hi / 1e-3 - 1) < 0.10
     # sigma falls as kappa grows towards the critical value
     assert last["dsigma_dkappa"] < 0
+
+
+def _stored_error_bound(e):
+    """A bound on |sigma_min - the stored sigma| from the entry's own record: the
+    Kato-Temple bound of its last evaluation, else the residual of its final
+    estimate (a Rayleigh quotient of Q, so within that residual of an eigenvalue)."""
+    evs = e.get("evaluations")
+    if evs:
+        return evs[-1]["bound"]
+    import re
+    got = re.search(r"residual of the final estimate ([0-9.]+e[-+][0-9]+)", e["method"])
+    return float(got.group(1)) if got else None
+
+
+@pytest.mark.parametrize("key", sorted(k for k, e in _table().items() if "verification" in e))
+def test_independent_verification_confirms_the_entry(key):
+    # a cold-started eigensolve at the stored kappa (oracle.kappa.verify_sigma): its
+    # residual and bound are formed from the returned vector itself
+    e = _table()[key]
+    v = e["verification"]
+    assert v["kappa"] == e["kappa"]
+    assert v["gap"] > v["residual"] > 0
+    assert abs(v["bound"] - v["residual"] ** 2 / v["gap"]) <= 1e-12 * v["bound"]
+    assert abs(v["sigma"] / 1e-3 - 1) < 0.05
+    assert abs((v["sigma"] - v["bound"]) / 1e-3 - 1) < 0.10
+    assert abs((v["sigma"] + v["bound"]) / 1e-3 - 1) < 0.10
+    # both estimates bound the same eigenvalue: their intervals overlap
+    b = _stored_error_bound(e)
+    assert b is not None
+    assert abs(v["sigma"] - e["sigma_min"]) <= v["bound"] + b
+

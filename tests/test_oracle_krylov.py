@@ -333,6 +333,24 @@ def test_kappa_rule_holds_on_the_4x4x4x4_workload():
     assert abs(np.sqrt(lam) / 1e-3 - 1) < 1e-5
 
 
+def test_kappa_verification_agrees_with_the_dense_eigensolve():
+    """The independent re-verification of a stored kappa (a cold-started MinRes-DR
+    eigensolve of gamma5 D) on the 4^4 workload: its |rho| lies within its own
+    Kato-Temple bound of the dense min |eig(gamma5 D)|, and within the residual."""
+    from oracle import kappa as okappa
+    w = synth.WORKLOADS["wilson_4x4x4x4"]
+    dims = w["dims"]
+    U = synth.su3_links(dims, w["gauge_seed"])
+    kappa = synth.kappa_for(dims, w["gauge_seed"])
+    v = okappa.verify_sigma(U, kappa, dims, seed=99, rel_bound=1e-2, max_cycles=300)
+    n = synth.volume(dims) * 12
+    ev = np.linalg.eigvalsh(wilson.dense(wilson.operator(U, kappa, dims, "Q"), n))
+    exact = np.min(np.abs(ev))
+    assert abs(v["sigma"] - exact) <= v["bound"] + 1e-15
+    assert abs(v["sigma"] - exact) <= v["residual"]
+    assert v["bound"] <= 1e-2 * v["sigma"] and abs(exact / 1e-3 - 1) < 1e-5
+
+
 def test_kappa_rule_free_field_limit():
     """At U = 1 the first crossing of sigma_min = 1e-3 is kappa = (1 - 1e-3)/8."""
     from oracle import kappa as okappa
