@@ -13,7 +13,9 @@ min |eig(gamma5 D)| = sigma_min(D) = 1e-3:
   * larger lattices: sigma_min = min |eig(Q)| from MinRes-DR run as an
     eigensolver (the harmonic Ritz pair nearest zero), stepping by 0.003
     from a start value near the expected crossing to bracket it, then
-    Illinois to 1e-3 and an independent re-verification.
+    Illinois (kappa_iterative) or Newton inside a known bracket
+    (kappa_newton); the stored value is then re-verified by one independent,
+    cold-started eigensolve at that kappa (verify_sigma).
 """
 from __future__ import annotations
 
