@@ -16,9 +16,11 @@ eigenproblem.  Beside it on the same operator:
   plain_fp64  the plain FP64 form (FP64 Lan-DR, then D-CG one right-hand side at a
               time, FP64 stencil), the first right-hand side in full and D-CG on a
               sample of right-hand sides, extrapolated to 48;
+  evenodd     the same step through the even-odd (Schur complement) operator;
   c4          64 lattices of uneven size (8^4, 12^4, 16^4), D-MinRes on 8 RHS each,
               all lattices in one batched call, against lattice by lattice and FP64;
-  c2          the 16^3x32 workload (MinRes-DR(100,40) + D-MinRes on 12 point sources);
+  c2          (with --c2) the 16^3x32 workload (MinRes-DR(100,40) + D-MinRes on 12
+              point sources);
   dslash      the Wilson stencil alone (FP32 and bfloat16, 16 RHS per launch).
 
 Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) solve independent
