@@ -25,6 +25,10 @@ import scipy.linalg as sla
 from . import cwilson, wilson
 
 TARGET = 1e-3
+# the scans give up beyond this kappa (every crossing of these links lies far below:
+# the hopping term has norm at most 8, so sigma_min >= 1 - 8 kappa, and the crossings
+# of the workloads lie near 0.26-0.27)
+KAPPA_MAX = 1.0
 
 
 def _dense_hop(U, dims, bc_t=1):
@@ -71,6 +75,8 @@ def kappa_dense(U, dims, bc_t=1, step=0.005, rtol=1e-6):
     a, fa = 0.0, f(0.0)
     while True:
         b = a + step
+        if b > KAPPA_MAX:
+            raise RuntimeError(f"sigma_min stays above {TARGET} for kappa <= {KAPPA_MAX}")
         fb = f(b)
         if fb < 0:
             break
@@ -137,12 +143,16 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5,
     fa = f(a)
     while fa < 0:
         a -= step
+        if a <= 0.0:
+            raise RuntimeError(f"sigma_min below {TARGET} down to kappa 0")
         fa = f(a)
     b = a + step
     fb = f(b)
     while fb > 0:
         a, fa = b, fb
         b = a + step
+        if b > KAPPA_MAX:
+            raise RuntimeError(f"sigma_min stays above {TARGET} for kappa <= {KAPPA_MAX}")
         fb = f(b)
     kap = _illinois(f, a, fa, b, fb, rtol)
     return kap, state["sigma"], state["res"]

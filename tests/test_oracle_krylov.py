@@ -351,6 +351,33 @@ def test_kappa_verification_agrees_with_the_dense_eigensolve():
     assert v["bound"] <= 1e-2 * v["sigma"] and abs(exact / 1e-3 - 1) < 1e-5
 
 
+def test_iterative_kappa_searches_find_the_dense_crossing():
+    """The two searches used past dense size (Illinois on MinRes-DR eigensolves, and
+    Newton inside a bracket) run on the 4^4 workload, where the dense eigensolve gives
+    the crossing exactly: each returns a kappa whose dense sigma_min meets the rule
+    to its tolerance, and a sigma that is the dense one at that kappa to within the
+    search's own error estimate."""
+    from oracle import kappa as okappa
+    w = synth.WORKLOADS["wilson_4x4x4x4"]
+    dims = w["dims"]
+    U = synth.su3_links(dims, w["gauge_seed"])
+    H = okappa._dense_hop(U, dims)
+    a, b = 0.2582, 0.2586
+    sa, sb = okappa.sigma_min_dense(H, a), okappa.sigma_min_dense(H, b)
+    assert sa > 1e-3 > sb
+    kap, sig, res, bound, hist = okappa.kappa_newton(U, dims, a, sa, b, sb, rtol=5e-2)
+    exact = okappa.sigma_min_dense(H, kap)
+    assert abs(exact / 1e-3 - 1) < 5e-2 and abs(sig - exact) <= bound + 1e-15
+    assert a < kap < b and hist[-1]["kappa"] == kap
+    kap2, sig2, res2 = okappa.kappa_iterative(U, dims, start=0.2583, step=0.0003, rtol=5e-2,
+                                              res_tol=1e-4, max_cycles=200)
+    exact2 = okappa.sigma_min_dense(H, kap2)
+    assert abs(exact2 / 1e-3 - 1) < 5e-2 and abs(sig2 - exact2) <= res2
+    # both within the Illinois-refined dense crossing's neighbourhood
+    kd = synth.kappa_for(dims, w["gauge_seed"])
+    assert abs(kap - kd) < 1e-4 and abs(kap2 - kd) < 1e-4
+
+
 def test_kappa_rule_free_field_limit():
     """At U = 1 the first crossing of sigma_min = 1e-3 is kappa = (1 - 1e-3)/8."""
     from oracle import kappa as okappa
