@@ -46,13 +46,14 @@ C4 = "uneven_64"
 # restart cycles of the 16^3x32 first right-hand side's MinRes-DR phase (both forms)
 C2_DR_CYCLES = 150
 # D-CG iterations per right-hand side of the FP64 form on the 24^3x48 workload, and
-# the MVPs of its first right-hand side (FP64 Lan-DR(120,60) to its stopping rule, 217
-# cycles): the oracle runs the same FP64 algorithm but cannot finish this lattice in a
-# bounded sample, so the reference arm extrapolates its seconds per iteration with these
-# counts (taken from an FP64 run of the library on this workload; the default line
-# reports the counts of its own FP64 run in plain_fp64)
-REF_ITERS_PER_RHS = 2384
-REF_FIRST_RHS_MVPS = 26378
+# the MVPs of its first right-hand side (FP64 Lan-DR(120,60) to its stopping rule, 229
+# cycles at the tabulated kappa): the oracle runs the same FP64 algorithm but cannot
+# finish this lattice in a bounded sample, so the reference arm extrapolates its seconds
+# per iteration with these counts (taken from the FP64 form of the library on this
+# workload, mean of 2 RHS; the default line reports the counts of its own FP64 run in
+# plain_fp64)
+REF_ITERS_PER_RHS = 2328
+REF_FIRST_RHS_MVPS = 27830
 # DRAM bytes (read + write) of one k_cg_k1 launch (16 RHS, 24^3x48), the dominant kernel,
 # from one single-pass ncu capture of the kernel at this size (summarised under
 # profiles/); None until taken for the current kernel
