@@ -160,12 +160,15 @@ typedef struct {
     long long kernel_launches[3]; /* their launch counts                                 */
 } dlz_stats;
 
-/* Fills *p with the defaults listed above. */
+/* Fills *p with the defaults listed above (library interface; no counterpart in the
+ * paper, which fixes m, k and the tolerance per experiment in Sec. 1-2). */
 int dlz_params_default(dlz_params *p);
 
-/* Name of an error code; static storage. */
+/* Name of an error code; static storage (library interface; no counterpart in the
+ * paper). */
 const char *dlz_strerror(int code);
-/* Message of the last failing call on this thread; static per-thread storage. */
+/* Message of the last failing call on this thread; static per-thread storage (library
+ * interface; no counterpart in the paper). */
 const char *dlz_last_error(void);
 
 /*
@@ -179,8 +182,11 @@ const char *dlz_last_error(void);
  */
 int dlz_create_operator(const int dims[4], const void *gauge, double kappa, int bc_t,
                         void *stream, dlz_op_t *out);
+/* Releases an operator and its device memory (library interface; no counterpart in the
+ * paper).  Deflation sets made on it must be destroyed first. */
 int dlz_destroy_operator(dlz_op_t op);
-/* Lattice volume V of the operator. */
+/* Lattice volume V of the operator: the sites of the Wilson matrix of Sec. 2 (V/2 for
+ * an even-odd operator). */
 int dlz_op_volume(dlz_op_t op, long long *V);
 
 /*
@@ -331,23 +337,26 @@ int dlz_dminres(dlz_op_t op, dlz_defl_t defl, const void *B, void *X, int nrhs,
 int dlz_gmresdr(dlz_op_t op, const void *b, void *x, const dlz_params *p, dlz_defl_t *defl_out, dlz_stats *stats);
 int dlz_dgmres(dlz_op_t op, dlz_defl_t defl, const void *B, void *X, int nrhs, const dlz_params *p,
                dlz_stats *stats);
-/* The i-th value of a deflation set as a complex number: theta_i of a GMRES-DR set,
- * (value_i, 0) of the hermitian sets. */
+/* The i-th value of a deflation set as a complex number: theta_i of a GMRES-DR set
+ * (the paper's refs. [1], [2]), (value_i, 0) of the hermitian sets (Sec. 2). */
 int dlz_defl_value_complex(dlz_defl_t d, int i, double *re, double *im);
 
-/* Number k of vectors in a deflation set, and which operator it deflates
+/* Number k of vectors in a deflation set -- the eigenvectors the first right-hand
+ * side computes and hands to the later ones (Sec. 2) -- and which operator it deflates
  * (DLZ_DDAGD from dlz_landr, DLZ_Q from dlz_minresdr, DLZ_D from dlz_gmresdr). */
 int dlz_defl_count(dlz_defl_t d, int *k, int *which);
 /*
- * i-th Rayleigh-Ritz pair of the deflation set: eigenvalues of H in
- * ascending order, the unit vector y_i = V_k z_i (complex128 [V][4][3], host
+ * i-th Rayleigh-Ritz pair of the deflation set (Sec. 2: the eigenvectors computed
+ * while solving the first right-hand side): eigenvalues of H in ascending order, the unit vector y_i = V_k z_i (complex128 [V][4][3], host
  * or device; NULL to skip), its value y_i^dag A y_i and its residual
  * ||A y_i - value y_i|| (either pointer may be NULL).  The residuals of all k
  * pairs are computed in FP64 on the first request for one (k MVPs).
  */
 int dlz_defl_get(dlz_defl_t d, int i, void *vec_out, double *value, double *residual);
 /* Writes the deflation set (header, H, V_k in FP64) to a file / reads it back
- * for the same operator geometry.  DLZ_ERR_IO on failure. */
+ * for the same operator geometry, so that the eigenvectors of Sec. 2 outlive the
+ * process (a checkpoint; no counterpart in the paper).  DLZ_ERR_IO on failure.
+ * dlz_defl_destroy releases a set. */
 int dlz_defl_save(dlz_defl_t d, const char *path);
 int dlz_defl_load(dlz_op_t op, const char *path, dlz_defl_t *out);
 int dlz_defl_destroy(dlz_defl_t d);
@@ -395,6 +404,7 @@ int dlz_basis_dots(const float *V, long long ldv, int nin, const float *R, long 
                    long long len, double *C);
 
 /*
+ * (Measurement of the uneven multi-lattice batch; no counterpart in the paper.)
  * The launch form the autotuner of the last DLZ_F32 dlz_batch_dminres call chose (op:
  * that call's ops[0]): form 0 = one launch per stage replayed from CUDA graphs, 1 = one
  * persistent cooperative launch over all slots and iterations (grid barriers whose waits
@@ -406,7 +416,8 @@ int dlz_basis_dots(const float *V, long long ldv, int nin, const float *R, long 
 int dlz_batch_last_choice(dlz_op_t op, int *form, int *chunks_per_block, int *half_grid);
 
 /*
- * Measurement entry point: packs `nrhs` spinors `in` (dtype DLZ_F64:
+ * Measurement entry point (the paper counts cost in matrix-vector products, Sec. 2;
+ * this times one): packs `nrhs` spinors `in` (dtype DLZ_F64:
  * complex128, DLZ_F32: complex64, [nrhs][V][4][3], host or device) into the
  * internal layout and launches the stencil `which` (DLZ_D, DLZ_DDAG or DLZ_Q)
  * the way the solvers do -- all nrhs right-hand sides in one launch -- `iters`
@@ -471,8 +482,8 @@ int dlz_subspace_loss(dlz_defl_t defl, const void *f, int nvec, double grad_scal
 int dlz_seed_deflation(dlz_op_t op, int which, const void *vecs, int dtype, int k, dlz_defl_t *defl_out);
 
 /*
- * Host-side dense helpers used by the restart (exported for testing; no
- * GPU needed).  Row-major n x n matrices.
+ * Host-side dense helpers used by the restart of Lan-DR and MinRes-DR (Sec. 1-2; exported
+ * for testing; no GPU needed).  Row-major n x n matrices.
  *   dlz_host_symeig: eigen-decomposition of a real symmetric matrix A
  *     (Householder tridiagonalisation + implicit QR with Wilkinson shifts):
  *     w[n] ascending, Z[n][n] with the eigenvector of w[j] in column j.
@@ -499,7 +510,8 @@ int dlz_host_lstsq(int rows, int cols, const double *T, const double *c, double 
 int dlz_host_restart_plan(int harmonic, int m, int k, const double *Tbar, const double *c, double *y, double *P,
                           double *Tn, double *cn, double *theta, double *ritz_res, double *anorm);
 /*
- * Complex host helpers of GMRES-DR (exported for testing; no GPU needed).  Complex
+ * Complex host helpers of GMRES-DR (the paper's refs. [1], [2]; exported for testing; no
+ * GPU needed).  Complex
  * values are interleaved (re, im) doubles, matrices row-major.
  *   dlz_host_zgeev: eigenvalues w[n] and unit eigenvectors (column j of Z, n x n; Z
  *     may be NULL) of a general complex n x n matrix A (Householder Hessenberg

@@ -17,6 +17,30 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(m.lib, s), s
 
 
+def test_every_declared_call_cites_its_passage():
+    """Each entry point of include/dlz.h sits under a comment that names the passage
+    of the paper defining the operation (a section, or one of the paper's references),
+    or says that the paper has no counterpart (interface, checkpoint, measurement)."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "dlz.h")
+    text = open(path).read()
+    body = text[text.index("#ifndef DLZ_H"):]
+    cite = re.compile(r"Sec\. ?\d|refs?\. \[\d|no counterpart|not in the paper")
+    missing = []
+    for m in re.finditer(r"^[a-z][\w \*]*?\b(dlz_\w+)\(", body, re.M):
+        before = body[: m.start()]
+        end = before.rfind("*/")
+        start = before.rfind("/*", 0, end)
+        # the comment must belong to this declaration's group: only declarations
+        # (and their continuation lines) between it and the call
+        between = before[end + 2:]
+        assert "{" not in between and "#define" not in between, m.group(1)
+        if not cite.search(before[start:end]):
+            missing.append(m.group(1))
+    assert not missing, missing
+
+
 def test_params_defaults():
     m = dlz()
     p = m.params_default()
