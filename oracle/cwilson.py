@@ -20,7 +20,8 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile cwilson.c into a shared object and return its path."""
+    """Compile cwilson.c into a shared object and return its path.
+    (Test infrastructure: builds the C form of the Sec. 2 operator.)"""
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
         return _SO
     os.makedirs(_OUT_DIR, exist_ok=True)
@@ -55,7 +56,8 @@ def _dp(a):
 
 
 def apply_D(U, psi, kappa, dims, bc_t=1, dagger=False):
-    """D psi (or D^dagger psi) for one spinor of shape (V, 4, 3) or (V*12,)."""
+    """D psi (or D^dagger psi) for one spinor of shape (V, 4, 3) or (V*12,).
+    (Sec. 2: the Wilson matrix M (D here), written as plain C site loops.)"""
     lib = _load()
     U = np.ascontiguousarray(U, dtype=np.complex128)
     psi = np.ascontiguousarray(psi, dtype=np.complex128)
@@ -66,7 +68,8 @@ def apply_D(U, psi, kappa, dims, bc_t=1, dagger=False):
 
 
 def apply_D_sites(U, psi, kappa, dims, sites, bc_t=1, dagger=False):
-    """(D psi)(s) for the listed sites only; returns (len(sites), 4, 3)."""
+    """(D psi)(s) for the listed sites only; returns (len(sites), 4, 3).
+    (Sec. 2: the Wilson matrix M (D here), written as plain C site loops.)"""
     lib = _load()
     U = np.ascontiguousarray(U, dtype=np.complex128)
     psi = np.ascontiguousarray(psi, dtype=np.complex128)
@@ -90,6 +93,7 @@ def operator(U, kappa, dims, which="D", bc_t=1):
 
     gamma5 = diag(1, 1, -1, -1) in the chiral basis (a property checked by
     the tests against the product gamma1 gamma2 gamma3 gamma4).
+    (Sec. 2: the Wilson matrix M (D here), written as plain C site loops.)
     """
     V = int(np.prod(dims))
 

@@ -65,7 +65,9 @@ def _mgs(P):
 def harmonic_ritz(Hbar, m, k):
     """The k harmonic Ritz pairs of smallest |theta| of an (m+1) x m Arnoldi matrix:
     eigenpairs of H_m + |h_{m+1,m}|^2 H_m^{-H} e_m e_m^H (theta ascending in |theta|,
-    unit vectors g)."""
+    unit vectors g).
+    (The paper's refs. [1], [2]: the non-hermitian deflated methods Sec. 1 contrasts
+    with.)"""
     Hm = Hbar[:m, :m]
     em = np.zeros(m, dtype=np.complex128)
     em[m - 1] = 1.0
@@ -88,7 +90,9 @@ class GmresDRResult:
 
 
 def gmresdr(A, b, m, k, tol=1e-10, max_cycles=500, progress=None):
-    """GMRES-DR(m, k) for A x = b (module docstring), x0 = 0."""
+    """GMRES-DR(m, k) for A x = b (module docstring), x0 = 0.
+    (The paper's refs. [1], [2]: the non-hermitian deflated methods Sec. 1 contrasts
+    with.)"""
     b = np.asarray(b, dtype=np.complex128).reshape(-1)
     n = b.size
     bn = _norm(b)
@@ -142,7 +146,9 @@ def gmresdr(A, b, m, k, tol=1e-10, max_cycles=500, progress=None):
 
 def gmres_cycle(A, r, m):
     """One GMRES(m) cycle from residual r: the correction minimising ||r - A dx|| over the
-    Krylov space of dimension m (returns dx and the MVPs)."""
+    Krylov space of dimension m (returns dx and the MVPs).
+    (The paper's refs. [1], [2]: the non-hermitian deflated methods Sec. 1 contrasts
+    with.)"""
     n = r.size
     beta = _norm(r)
     V = np.zeros((n, m + 1), dtype=np.complex128)
@@ -156,7 +162,9 @@ def gmres_cycle(A, r, m):
 
 
 def dgmres(A, b, Vk1, Hbar, m, tol=1e-10, max_cycles=1000):
-    """D-GMRES(m) over the kept space (V_{k+1}, Hbar_k) of GMRES-DR (module docstring)."""
+    """D-GMRES(m) over the kept space (V_{k+1}, Hbar_k) of GMRES-DR (module docstring).
+    (The paper's refs. [1], [2]: the non-hermitian deflated methods Sec. 1 contrasts
+    with.)"""
     b = np.asarray(b, dtype=np.complex128).reshape(-1)
     bn = _norm(b)
     info = SolveInfo()

@@ -39,7 +39,9 @@ def _dense_hop(U, dims, bc_t=1):
 
 
 def sigma_min_dense(H, kappa):
-    """sigma_min(1 - kappa H) from the lowest eigenvalue of D^dagger D (LAPACK)."""
+    """sigma_min(1 - kappa H) from the lowest eigenvalue of D^dagger D (LAPACK).
+    (Not in the paper (Sec. 2 runs at kappa critical on its ensemble): the kappa rule of
+    the synthetic workloads.)"""
     D = np.eye(H.shape[0]) - kappa * H
     lam = sla.eigvalsh(D.conj().T @ D, subset_by_index=[0, 0])[0]
     return float(np.sqrt(max(lam, 0.0)))
@@ -69,7 +71,9 @@ def _illinois(f, a, fa, b, fb, rtol):
 
 
 def kappa_dense(U, dims, bc_t=1, step=0.005, rtol=1e-6):
-    """kappa with sigma_min(D) = 1e-3 on a lattice small enough to be dense."""
+    """kappa with sigma_min(D) = 1e-3 on a lattice small enough to be dense.
+    (Not in the paper (Sec. 2 runs at kappa critical on its ensemble): the kappa rule of
+    the synthetic workloads.)"""
     H = _dense_hop(U, dims, bc_t)
     f = lambda kap: sigma_min_dense(H, kap) - TARGET  # noqa: E731
     a, fa = 0.0, f(0.0)
@@ -88,7 +92,9 @@ def kappa_dense(U, dims, bc_t=1, step=0.005, rtol=1e-6):
 def sigma_min_iterative(U, kappa, dims, v0, res_tol, m=100, k=20, bc_t=1, max_cycles=2000,
                         log=None):
     """min |eig(gamma5 D)| by MinRes-DR used as an eigensolver (harmonic Ritz pairs
-    nearest zero), started from v0.  Returns (sigma, eigenvector, residual, mvps)."""
+    nearest zero), started from v0.  Returns (sigma, eigenvector, residual, mvps).
+    (Not in the paper (Sec. 2 runs at kappa critical on its ensemble): the kappa rule of
+    the synthetic workloads.)"""
     from .krylov import minresdr
     A = cwilson.operator(U, kappa, dims, "Q", bc_t)
 
@@ -119,6 +125,8 @@ def kappa_iterative(U, dims, start, bc_t=1, step=0.003, rtol=1e-3, res_tol=1e-5,
     max(res_tol, 5% of |sigma - 1e-3|) or after max_cycles restart cycles
     (the nearest-zero harmonic Ritz value of a capped run is then the
     estimate used).  Returns (kappa, sigma_min, residual of that estimate).
+    (Not in the paper (Sec. 2 runs at kappa critical on its ensemble): the kappa rule of
+    the synthetic workloads.)
     """
     V = int(np.prod(dims))
     rng = np.random.default_rng(seed)
@@ -176,7 +184,9 @@ def kappa_newton(U, dims, a, sa, b, sb, bc_t=1, rtol=1e-4, m=100, k=20, max_cycl
     = (rho - <y, gamma5 y>) / kappa, and d sigma / d kappa = sign(rho) times that;
     a step that leaves the bracket is replaced by false position.  Stops when
     |sigma / 1e-3 - 1| < rtol.  Returns (kappa, sigma_min, residual, error bound,
-    list of evaluations)."""
+    list of evaluations).
+    (Not in the paper (Sec. 2 runs at kappa critical on its ensemble): the kappa rule of
+    the synthetic workloads.)"""
     from .krylov import minresdr
     from .wilson import apply_gamma5
     V = int(np.prod(dims))
@@ -248,7 +258,9 @@ def verify_sigma(U, kappa, dims, seed, rel_bound=1e-3, gap_guess=3e-4, m=100, k=
     anew with one more application of Q, and the gap is the distance from rho to
     the nearest other kept value.  For hermitian Q an eigenvalue lies within
     residual^2 / gap of rho (Kato-Temple) and within the residual itself.
-    Returns dict(kappa, sigma = |rho|, residual, gap, bound, cycles, mvps, seed)."""
+    Returns dict(kappa, sigma = |rho|, residual, gap, bound, cycles, mvps, seed).
+    (Not in the paper (Sec. 2 runs at kappa critical on its ensemble): the kappa rule of
+    the synthetic workloads.)"""
     from .krylov import minresdr
     V = int(np.prod(dims))
     n = V * 12

@@ -57,6 +57,7 @@ def cg(A, b, x0=None, tol=1e-10, maxiter=10000):
     r0 = b - A x0, p0 = r0; then alpha = <r,r>/<p,Ap>, x += alpha p,
     r -= alpha A p, beta = <r',r'>/<r,r>, p = r' + beta p.  Stops when
     ||r|| <= tol ||b||.  The residual history is the recursive ||r_j||/||b||.
+    (Sec. 1: the CG implementation of Lanczos (Hestenes-Stiefel).)
     """
     b = np.asarray(b, dtype=np.complex128)
     bn = _norm(b)
@@ -141,6 +142,7 @@ def minres(A, b, x0=None, tol=1e-10, maxiter=10000):
     R's column (eps_j, delta_j, gamma_j) the search directions are
     d_j = (v_j - delta_j d_{j-1} - eps_j d_{j-2}) / gamma_j, x_j = x_{j-1} + tau_j d_j,
     tau_j = c_j phibar_j, phibar_{j+1} = -s_j phibar_j and ||r_j|| = |phibar_{j+1}|.
+    (Sec. 1: the MinRes implementation of Lanczos (Paige-Saunders).)
     """
     b = np.asarray(b, dtype=np.complex128)
     bn = _norm(b)
@@ -264,7 +266,8 @@ def lanczos_extend(A, V, T, j0, m, kept=0, reorth_period=10, full_reorth=False,
 
 
 def lanczos(A, r0, m, full_reorth=False):
-    """Plain Lanczos: returns (V_{m+1} as an n x (m+1) array, Tbar_m (m+1) x m, beta0)."""
+    """Plain Lanczos: returns (V_{m+1} as an n x (m+1) array, Tbar_m (m+1) x m, beta0).
+    (Sec. 1: the Lanczos recurrence under both implementations.)"""
     beta0 = _norm(r0)
     V = [np.asarray(r0, dtype=np.complex128) / beta0]
     T = np.zeros((m + 1, m))
@@ -383,7 +386,8 @@ class RestartPlan:
 
 def restart_plan(T, c, m, k, harmonic):
     """Galerkin solve and regular Ritz pairs (Lan-DR) or least squares and harmonic
-    Ritz pairs (MinRes-DR) of one cycle, and the restart matrices P, Tbar_k, c."""
+    Ritz pairs (MinRes-DR) of one cycle, and the restart matrices P, Tbar_k, c.
+    (Sec. 1-2: the small problem at the end of each Lan-DR / MinRes-DR cycle.)"""
     Tm = T[:m, :m]
     if not harmonic:
         y = sla.solve(Tm, c[:m], assume_a="sym")
@@ -528,14 +532,16 @@ def _dr(A, b, m, k, tol, tol_eig, max_cycles, reorth_period, full_reorth, residu
 # --------------------------------------------------------------------------
 
 def deflation_space(A, Vk):
-    """H = V_k^dagger A V_k (k MVPs)."""
+    """H = V_k^dagger A V_k (k MVPs).
+    (Sec. 2: the projected matrix of the Galerkin projection of D-CG / D-MinRes.)"""
     AV = np.stack([A(Vk[:, i]) for i in range(Vk.shape[1])], axis=1)
     H = Vk.conj().T @ AV
     return 0.5 * (H + H.conj().T)
 
 
 def galerkin_x0(Vk, H, b):
-    """x0 = V_k H^{-1} V_k^dagger b: the Galerkin projection over the kept vectors."""
+    """x0 = V_k H^{-1} V_k^dagger b: the Galerkin projection over the kept vectors.
+    (Sec. 2: the Galerkin projection at the start of D-CG / D-MinRes.)"""
     return Vk @ np.linalg.solve(H, Vk.conj().T @ b)
 
 
@@ -544,6 +550,7 @@ def dcg(M, Mdag, b, Vk, H, tol=1e-10, maxiter=10000):
 
     A = M^dagger M, b' = M^dagger b, x0 = V_k H^{-1} V_k^dagger b', then cgnr
     from x0 (stopping on ||b - M x|| / ||b||).
+    (Sec. 2: D-CG.)
     """
     bp = Mdag(b)
     x0 = galerkin_x0(Vk, H, bp)

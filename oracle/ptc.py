@@ -37,19 +37,22 @@ N_OFFSETS = 9
 
 
 def offset_index(mu: int, sign: int) -> int:
-    """Index of offset +mu (sign = +1) or -mu (sign = -1); 0 is the site itself."""
+    """Index of offset +mu (sign = +1) or -mu (sign = -1); 0 is the site itself.
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     return 1 + 2 * mu + (0 if sign > 0 else 1)
 
 
 def opposite(o: int) -> int:
-    """Index of the offset opposite to o (0 is its own opposite)."""
+    """Index of the offset opposite to o (0 is its own opposite).
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     if o == 0:
         return 0
     return o + 1 if (o - 1) % 2 == 0 else o - 1
 
 
 def transport(U, psi, dims, o):
-    """T_o psi for a field psi (..., V, 4, 3)."""
+    """T_o psi for a field psi (..., V, 4, 3).
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     if o == 0:
         return psi.copy()
     mu, fwd = (o - 1) // 2, (o - 1) % 2 == 0
@@ -68,7 +71,8 @@ def transport(U, psi, dims, o):
 
 
 def layer(W, U, x, dims):
-    """out[c'] = sum_o sum_c W[o, c', c] (T_o x[c]); x (C_in, V, 4, 3)."""
+    """out[c'] = sum_o sum_c W[o, c', c] (T_o x[c]); x (C_in, V, 4, 3).
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     W = np.asarray(W, dtype=np.complex128)
     nout = W.shape[1]
     out = np.zeros((nout,) + x.shape[1:], dtype=np.complex128)
@@ -79,7 +83,8 @@ def layer(W, U, x, dims):
 
 
 def adjoint_weights(W):
-    """Weights of the adjoint layer: W'[o, c, c'] = W[opp(o), c', c]^H."""
+    """Weights of the adjoint layer: W'[o, c, c'] = W[opp(o), c', c]^H.
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     W = np.asarray(W, dtype=np.complex128)
     Wa = np.empty((W.shape[0], W.shape[2], W.shape[1], 4, 4), dtype=np.complex128)
     for o in range(N_OFFSETS):
@@ -88,12 +93,14 @@ def adjoint_weights(W):
 
 
 def layer_adjoint(W, U, g, dims):
-    """L^dagger g for the layer L with weights W."""
+    """L^dagger g for the layer L with weights W.
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     return layer(adjoint_weights(W), U, g, dims)
 
 
 def layer_weight_grad(U, x, g, dims):
-    """G(W)[o, c', c] = sum_{sites, colours} g[c'] (T_o x[c])^dagger (spin 4x4)."""
+    """G(W)[o, c', c] = sum_{sites, colours} g[c'] (T_o x[c])^dagger (spin 4x4).
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     G = np.empty((N_OFFSETS, g.shape[0], x.shape[0], 4, 4), dtype=np.complex128)
     for o in range(N_OFFSETS):
         t = transport(U, x, dims, o)
@@ -105,6 +112,7 @@ def forward(Ws, U, eta, dims):
     """Network output and the inputs of every layer (for the backward pass).
 
     eta: (V, 4, 3) one input vector; returns (f (V, 4, 3), [layer inputs]).
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)
     """
     x = np.asarray(eta, dtype=np.complex128)[None]
     inputs = []
@@ -115,7 +123,8 @@ def forward(Ws, U, eta, dims):
 
 
 def backward(Ws, U, inputs, g_out, dims):
-    """Weight gradients of every layer and G(eta), given G(f) = g_out (V, 4, 3)."""
+    """Weight gradients of every layer and G(eta), given G(f) = g_out (V, 4, 3).
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     g = np.asarray(g_out, dtype=np.complex128)[None]
     grads = [None] * len(Ws)
     for li in range(len(Ws) - 1, -1, -1):
@@ -125,7 +134,8 @@ def backward(Ws, U, inputs, g_out, dims):
 
 
 def subspace_loss(Vk, f):
-    """||(1 - V V^dag) f||^2 / ||f||^2 for orthonormal columns Vk (n, k), and G(f)."""
+    """||(1 - V V^dag) f||^2 / ||f||^2 for orthonormal columns Vk (n, k), and G(f).
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     f = np.asarray(f, dtype=np.complex128).reshape(-1)
     h = Vk.conj().T @ f
     perp = f - Vk @ h
@@ -136,7 +146,8 @@ def subspace_loss(Vk, f):
 
 
 def wilson_weights(kappa):
-    """Weights of the one-channel layer that equals the Wilson matrix D."""
+    """Weights of the one-channel layer that equals the Wilson matrix D.
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     from .wilson import gamma_matrices
     G = gamma_matrices()
     one = np.eye(4, dtype=np.complex128)
@@ -149,7 +160,8 @@ def wilson_weights(kappa):
 
 
 def round_bf16(a):
-    """Round real and imaginary parts to bfloat16 (nearest even), returned as complex128."""
+    """Round real and imaginary parts to bfloat16 (nearest even), returned as complex128.
+    (Not in the paper: the learned seed for the deflation space of Sec. 2.)"""
     a = np.asarray(a, dtype=np.complex128)
 
     def r(x):

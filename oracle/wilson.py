@@ -29,7 +29,8 @@ _SIGMA = (
 
 
 def gamma_matrices():
-    """(gamma_1, gamma_2, gamma_3, gamma_4, gamma_5) in the chiral basis."""
+    """(gamma_1, gamma_2, gamma_3, gamma_4, gamma_5) in the chiral basis.
+    (Sec. 2: the Wilson matrix M (D here), used as M^dagger M and gamma5 M.)"""
     z = np.zeros((2, 2), dtype=np.complex128)
     one = np.eye(2, dtype=np.complex128)
     g = [np.block([[z, -1j * s], [1j * s, z]]) for s in _SIGMA]
@@ -86,12 +87,14 @@ def apply_D(U, psi, kappa, dims, bc_t=1):
 
 
 def apply_Ddag(U, psi, kappa, dims, bc_t=1):
-    """D^dagger written out directly (gamma_mu -> -gamma_mu in the hopping term)."""
+    """D^dagger written out directly (gamma_mu -> -gamma_mu in the hopping term).
+    (Sec. 2: the Wilson matrix M (D here), used as M^dagger M and gamma5 M.)"""
     return psi - kappa * _hop_sum(U, psi, dims, bc_t, -1)
 
 
 def apply_gamma5(psi):
-    """gamma5 on the spin index of (..., 4, 3) spinors."""
+    """gamma5 on the spin index of (..., 4, 3) spinors.
+    (Sec. 2: the Wilson matrix M (D here), used as M^dagger M and gamma5 M.)"""
     return np.einsum("ab,...bc->...ac", _G[4], psi)
 
 
@@ -106,7 +109,8 @@ def apply_DdagD(U, psi, kappa, dims, bc_t=1):
 
 
 def dense(apply, n, chunk=256):
-    """Dense n x n matrix of a linear map on flat complex vectors (tiny lattices)."""
+    """Dense n x n matrix of a linear map on flat complex vectors (tiny lattices).
+    (Sec. 2: the Wilson matrix M (D here), used as M^dagger M and gamma5 M.)"""
     out = np.empty((n, n), dtype=np.complex128)
     for c0 in range(0, n, chunk):
         c1 = min(n, c0 + chunk)
@@ -117,7 +121,8 @@ def dense(apply, n, chunk=256):
 
 
 def operator(U, kappa, dims, which="D", bc_t=1):
-    """Flat-vector closure x -> A x for which in {'D', 'Ddag', 'Q', 'DdagD'}."""
+    """Flat-vector closure x -> A x for which in {'D', 'Ddag', 'Q', 'DdagD'}.
+    (Sec. 2: the Wilson matrix M (D here), used as M^dagger M and gamma5 M.)"""
     V = int(np.prod(dims))
     f = {"D": apply_D, "Ddag": apply_Ddag, "Q": apply_Q, "DdagD": apply_DdagD}[which]
 
@@ -137,6 +142,7 @@ def free_spectrum_Q(kappa, dims, bc_t=1):
     for antiperiodic time), D acts as a(p) - i*kappa*2 sum gamma_mu sin p_mu
     up to sign with a(p) = 1 - 2 kappa sum cos p_mu, so eigenvalues of Q are
     +-sqrt(a(p)^2 + 4 kappa^2 sum sin^2 p_mu).  Returns them sorted.
+    (Sec. 2: the Wilson matrix M (D here), used as M^dagger M and gamma5 M.)
     """
     lx, ly, lz, lt = dims
     ps = []
