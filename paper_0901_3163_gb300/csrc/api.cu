@@ -1,5 +1,6 @@
-// C ABI of the dlz library (include/dlz.h): operator objects, host/device
-// staging of user vectors, the solver and deflation-set entry points.
+// C ABI of the dlz library (include/dlz.h, where each entry point names the
+// passage of the paper it implements): operator objects, host/device staging of
+// user vectors, the solver and deflation-set entry points.
 #include <algorithm>
 #include <chrono>
 #include <cmath>

@@ -1,4 +1,5 @@
-// Internal declarations of the dlz library (not part of the C ABI).
+// Internal declarations of the dlz library (not part of the C ABI): the
+// Wilson operator of Sec. 2 and the state the solvers of Sec. 1-2 share.
 //
 // Device data layout ("field order"): a spinor of V sites is stored as
 // component-major planes so that thread s of a warp touches consecutive

@@ -1,5 +1,5 @@
-// Shared helpers of the solver drivers: FP64 vector kernels on internal
-// planes, pinned host scratch and stream-ordered copies.
+// Shared helpers of the solver drivers of Sec. 1-2: FP64 vector kernels on
+// internal planes, pinned host scratch and stream-ordered copies.
 #pragma once
 
 #include <algorithm>

@@ -1,4 +1,5 @@
-// Precision traits of the Krylov vectors: FP64 (double2 elements, 12 per site)
+// Precision traits of the Krylov vectors of the Lanczos, CG and MinRes
+// recurrences (Sec. 1-2): FP64 (double2 elements, 12 per site)
 // and FP32 (float4 elements, 6 per site).  Reductions sum across threads and
 // blocks in FP64 (FP32 vectors accumulate each thread's few elements in float
 // first); element updates run in the vector precision.

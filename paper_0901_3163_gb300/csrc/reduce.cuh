@@ -1,5 +1,6 @@
 // Deterministic fused vector kernels: element-wise bodies with up to kMaxDots
-// double accumulators, reduced in a fixed order.
+// double accumulators, reduced in a fixed order (the inner products and norms of
+// the Lanczos, CG and MinRes recurrences, Sec. 1-2).
 //
 // Every reduction runs on a fixed grid of kRedBlocks blocks with a
 // grid-stride loop, so each element always lands in the same thread and

@@ -1,4 +1,5 @@
-// Host FP64 dense helpers for the small projected problems (row-major).
+// Host FP64 dense helpers for the small projected problems at the end of each
+// Lan-DR / MinRes-DR cycle (Sec. 1-2; row-major).
 #pragma once
 
 #include <complex>
